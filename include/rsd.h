@@ -1,0 +1,184 @@
+/*
+ * rsd.h -- C ABI of the GB300 Recursive Schur Decomposition (RSD) library.
+ *
+ * The method (Sampath, Philip, Allu, Simunovic, "Recursive Schur Decomposition"):
+ * a tree of nested sub-domains (Sec. 2); at every internal node the two (here: eight)
+ * children are eliminated onto their shared interface I through the Schur complement
+ * S = K_II - sum_c K_Ic K_cc^-1 K_cI (Eq. 3.2), and the children's unknowns are
+ * recovered by back-substitution (Eq. 3.3); applied recursively down to the true
+ * (leaf) sub-domains (Sec. 3.2, Algorithm 2), it preconditions a Krylov solve of K u = f.
+ *
+ * Conventions shared by every call:
+ *   - Return value: RSD_OK (0) or a negative RSD_ERR_* code.  No call throws or aborts;
+ *     rsd_strerror() names a code.  After RSD_ERR_CUDA the CUDA context may be unusable.
+ *   - Matrices are CSR, 0-based, column indices sorted ascending within each row,
+ *     FP64 values, symmetric positive definite (the SPD systems of Sec. 4).
+ *   - "device" pointers are CUDA global memory of the current device; "host" pointers
+ *     are ordinary (preferably pinned) host memory.  Each argument says which.
+ *   - Vectors are FP64, length n, in the caller's DOF numbering.
+ *   - Work is ordered on the stream given in rsd_options (or on the stream argument);
+ *     calls on one handle must not run concurrently from several host threads.
+ *   - The library never keeps a pointer the caller passed in: it copies what it needs.
+ */
+#ifndef RSD_H
+#define RSD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------- */
+#define RSD_OK              0
+#define RSD_ERR_ARG        (-1)  /* bad argument: null pointer, size, tree, option value */
+#define RSD_ERR_PARTITION  (-2)  /* K couples DOFs of two sub-domains that are not
+                                    ancestor-related: the block structure of Eq. 3.1
+                                    (K_LR = 0) does not hold for the given ownership */
+#define RSD_ERR_NOT_SPD    (-3)  /* a pivot <= 0 (or NaN) in a sub-domain or interface
+                                    factorisation */
+#define RSD_ERR_NOMEM      (-4)  /* device or host allocation failed */
+#define RSD_ERR_CUDA       (-5)  /* a CUDA runtime call failed */
+#define RSD_ERR_TIMEOUT    (-6)  /* a bounded device-side wait gave up (see rsd_apply) */
+#define RSD_ERR_NOCONV     (-7)  /* Krylov solve hit maxit; x and stats still filled */
+
+/* ---- precisions of the stored factors and the arithmetic on them ----------------- */
+#define RSD_PREC_FP64  0   /* FP64 storage, FP64 arithmetic on CUDA cores                */
+#define RSD_PREC_FP32  1   /* FP32 storage, FP32 arithmetic on CUDA cores                */
+#define RSD_PREC_TF32  2   /* FP32 storage; GEMM/TRSM updates on tcgen05 tensor cores in
+                              TF32 with FP32 accumulation; diagonal blocks in FP32       */
+
+#define RSD_MODE_EXACT 0   /* exact recursive Schur complements (gamma -> infinity,
+                              V-hat = V limit of Algorithm 2): the preconditioner is K^-1
+                              up to the rounding of the stored factors                  */
+
+#define RSD_MEM_HOST   0
+#define RSD_MEM_DEVICE 1
+
+/* ---- inputs ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t        n;       /* rows = columns                                            */
+    int64_t        nnz;
+    const int64_t* rowptr;  /* n + 1 entries                                             */
+    const int32_t* col;     /* nnz entries, ascending within a row                       */
+    const double*  val;     /* nnz entries                                               */
+    int32_t        mem;     /* RSD_MEM_HOST or RSD_MEM_DEVICE: where all three arrays live */
+} rsd_csr;
+
+/* Sub-domain tree of Sec. 2: node 0 is the whole domain; parent[t] < t for t > 0
+ * (breadth-first ids), parent[0] = -1.  Leaves are the true sub-domains; every
+ * internal node owns the interface DOFs that separate its children.               */
+typedef struct {
+    int32_t        n_nodes;
+    const int32_t* parent;  /* host, n_nodes entries                                     */
+} rsd_tree;
+
+typedef struct {
+    int32_t mode;        /* RSD_MODE_EXACT                                                */
+    int32_t prec_leaf;   /* RSD_PREC_* of the leaf (true sub-domain) fronts               */
+    int32_t prec_mid;    /* RSD_PREC_* of internal fronts below the root                  */
+    int32_t prec_root;   /* RSD_PREC_* of the root interface                              */
+    int32_t maxit;       /* rsd_solve iteration cap (<= 0: 200)                            */
+    void*   stream;      /* cudaStream_t for every call on the handle (NULL: legacy default) */
+} rsd_options;
+
+typedef struct {
+    int32_t iterations;      /* PCG iterations taken                                      */
+    double  relres;          /* ||f - K u|| / ||f|| recomputed in FP64 after the last step */
+    double  relres_recursive;/* the recursively updated residual norm at exit             */
+    double  history[64];     /* ||r_k|| / ||f|| for k = 0 .. min(iterations, 63)          */
+} rsd_stats;
+
+typedef struct {
+    int32_t n;               /* DOFs                                                      */
+    int32_t n_nodes;         /* tree nodes                                                */
+    int32_t n_levels;        /* tree depth + 1                                            */
+    int64_t factor_elems;    /* stored factor elements, sum_t (s_t^2/2 + s_t b_t)          */
+    int64_t factor_bytes;    /* the same in bytes at each level's storage width           */
+    double  setup_flops;     /* sum_t (s_t^3/3 + s_t^2 b_t + s_t b_t^2)                    */
+    int64_t device_bytes;    /* bytes of device memory the handle holds                   */
+    int32_t notspd_node;     /* first node whose pivot failed, or -1                      */
+} rsd_info_t;
+
+typedef struct rsd_handle_s* rsd_handle;
+
+/* ---- the three calls of the method --------------------------------------------- */
+
+/* rsd_setup -- build the RSD hierarchy for K (Sec. 2 and Sec. 3.2; Eqs. 3.1-3.2).
+ *   K        : the SPD matrix (host or device CSR, see rsd_csr.mem).
+ *   dof_node : owner tree node of every DOF (n entries, same memory kind as K).
+ *   T        : the sub-domain tree (host).
+ *   opt      : options (host; NULL = exact mode, TF32 leaves/middle, FP64 root).
+ *   out      : receives the handle; the handle owns all device memory it allocates.
+ * Steps: validate the tree and the block structure of Eq. 3.1 (RSD_ERR_PARTITION),
+ * form the interface index sets, then, level by level from the leaves up, assemble each
+ * node's front from K and its children's Schur contributions, factor the interface block
+ * and form the Schur contribution to the ancestors (Eq. 3.2).  All numeric work runs
+ * in this library's CUDA kernels on opt->stream; the call returns after the stream has
+ * drained and reports RSD_ERR_NOT_SPD if any pivot failed.  The caller may free K,
+ * dof_node and T as soon as the call returns.                                         */
+int rsd_setup(const rsd_csr* K, const int32_t* dof_node, const rsd_tree* T,
+              const rsd_options* opt, rsd_handle* out);
+
+/* rsd_apply -- z = M r, one application of the preconditioner (Algorithm 2 in the exact
+ * limit): an upward sweep that forms the interface right-hand sides g of Eq. 3.2 level by
+ * level, and a downward sweep of back-substitutions (Eq. 3.3).
+ *   r, z : device, n FP64 entries each, may not alias.  Stream-ordered on the handle's
+ *          stream; returns without synchronising.  A device-side wait that exceeds its
+ *          bound is reported as RSD_ERR_TIMEOUT by the next rsd_solve / rsd_check call. */
+int rsd_apply(rsd_handle h, const double* r, double* z);
+
+/* rsd_solve -- preconditioned CG in FP64 on K u = f from u = 0 (the paper's outer Krylov
+ * solve with RSD as preconditioner, Sec. 3 and Sec. 4), stopping when the recursively
+ * updated residual satisfies ||r_k|| / ||f|| <= tol; then recomputes the true residual.
+ *   f, u : device, n FP64 entries.   st : host, may be NULL.
+ * Synchronises the stream once per iteration to test convergence.
+ * Returns RSD_ERR_NOCONV if maxit iterations did not reach tol (u, st still valid).      */
+int rsd_solve(rsd_handle h, const double* f, double* u, double tol, rsd_stats* st);
+
+/* rsd_check -- synchronise the handle's stream and report any device-side error flag
+ * (timeout of a bounded wait, failed pivot) raised since setup.                        */
+int rsd_check(rsd_handle h);
+
+void        rsd_destroy(rsd_handle h);
+const char* rsd_strerror(int code);
+
+/* ---- introspection (tests and benchmarks) --------------------------------------- */
+int rsd_get_info(rsd_handle h, rsd_info_t* out);
+/* s = |I_t| (interface / interior DOFs owned by node t), b = |B_t| (ancestor DOFs
+ * coupled to the subtree of t); level = depth of t.                                   */
+int rsd_front_dims(rsd_handle h, int32_t node, int32_t* s, int32_t* b, int32_t* level);
+/* front DOF list I_t ++ B_t (host out, s + b entries, each part ascending).           */
+int rsd_front_dofs(rsd_handle h, int32_t node, int32_t* out);
+/* extend-add map of node t: positions of B_t inside its parent's front (host out, b). */
+int rsd_front_map(rsd_handle h, int32_t node, int32_t* out);
+/* factor of node t as FP64 row-major (s + b) x s (host out): rows 0..s-1 hold L_t,
+ * the Cholesky factor of the interface Schur complement (lower triangle, zeros above);
+ * rows s..s+b-1 hold X_t = K~_BI L_t^-T, the coupling to the ancestors.              */
+int rsd_front_factor(rsd_handle h, int32_t node, double* out);
+
+/* ---- structured-grid FEM problems (the synthetic workloads) ---------------------- *
+ * Unit cube, n x n x n nodes (h = 1/(n-1)), trilinear hexahedra, homogeneous Dirichlet
+ * on the boundary (Sec. 4's setting in 3-D); unknowns are the (n-2)^3 interior nodes,
+ * numbered x-1 + (n-2)*((y-1) + (n-2)*(z-1)).                                          */
+
+/* sizes of the -div(kappa grad u) system: n_dof = (n-2)^3 and its nonzero count.       */
+int rsd_grid_sizes(int32_t n, int64_t* n_dof, int64_t* nnz);
+/* assemble K for kappa constant per element (element (ex,ey,ez) at ex + (n-1)*(ey +
+ * (n-1)*ez)): kappa device ((n-1)^3), rowptr/col/val device (n_dof+1, nnz, nnz).      */
+int rsd_grid_assemble(int32_t n, const double* kappa, int64_t* rowptr, int32_t* col,
+                      double* val, void* stream);
+/* load vector b = h^3 f (lumped mass) from nodal f; both device, n_dof entries.         */
+int rsd_grid_load(int32_t n, const double* f, double* b, void* stream);
+/* octree decomposition of the grid to the given depth (Sec. 2 generalised to 3-D: each
+ * box splits at its integer mid-planes; a node belongs to the first box whose
+ * mid-planes contain it, else to its leaf).  dof_node device (n_dof); parent host
+ * ((8^(depth+1)-1)/7 entries, breadth-first ids).                                       */
+int rsd_grid_partition(int32_t n, int32_t depth, int32_t* dof_node, int32_t* parent,
+                       void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RSD_H */

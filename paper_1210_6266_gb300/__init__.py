@@ -1,0 +1,152 @@
+"""GB300 Recursive Schur Decomposition preconditioner: Python binding of include/rsd.h.
+
+Thin marshalling over the C ABI (librsd.so).  PyTorch provides device memory and the
+stream; every step of setup, apply and solve runs in the library's CUDA kernels.
+
+    prob = grid_problem(n, depth, kappa, f)           # K, b, ownership, tree on the GPU
+    h = RSD.setup(prob["rowptr"], prob["col"], prob["val"], prob["dof_node"], prob["parent"])
+    u, stats = h.solve(prob["b"], tol=1e-8)
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import (RSD_MEM_DEVICE, RSD_MEM_HOST, RSD_MODE_EXACT, RSD_PREC_FP32, RSD_PREC_FP64,
+                   RSD_PREC_TF32, RSDError, check)
+
+__all__ = ["RSD", "grid_problem", "grid_sizes", "RSDError", "RSD_PREC_FP64", "RSD_PREC_FP32",
+           "RSD_PREC_TF32"]
+
+
+def _ptr(t: torch.Tensor) -> int:
+    return t.data_ptr()
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def grid_sizes(n: int) -> tuple[int, int]:
+    lib = _lib.load()
+    nd, nz = C.c_int64(), C.c_int64()
+    check(lib.rsd_grid_sizes(n, C.byref(nd), C.byref(nz)), "rsd_grid_sizes")
+    return nd.value, nz.value
+
+
+def grid_problem(n: int, depth: int, kappa, f, device: str = "cuda") -> dict:
+    """Assemble K (CSR, FP64), b = h^3 f, the octree ownership and tree on the GPU.
+    kappa: (n-1)^3 per-element coefficients; f: (n-2)^3 nodal loads."""
+    lib = _lib.load()
+    nd, nz = grid_sizes(n)
+    kap = torch.as_tensor(np.ascontiguousarray(kappa), dtype=torch.float64).to(device)
+    fn = torch.as_tensor(np.ascontiguousarray(f), dtype=torch.float64).to(device)
+    rowptr = torch.empty(nd + 1, dtype=torch.int64, device=device)
+    col = torch.empty(nz, dtype=torch.int32, device=device)
+    val = torch.empty(nz, dtype=torch.float64, device=device)
+    b = torch.empty(nd, dtype=torch.float64, device=device)
+    dof_node = torch.empty(nd, dtype=torch.int32, device=device)
+    n_nodes = (8 ** (depth + 1) - 1) // 7
+    parent = np.empty(n_nodes, dtype=np.int32)
+    st = _stream()
+    check(lib.rsd_grid_assemble(n, _ptr(kap), _ptr(rowptr), _ptr(col), _ptr(val), st), "rsd_grid_assemble")
+    check(lib.rsd_grid_load(n, _ptr(fn), _ptr(b), st), "rsd_grid_load")
+    check(lib.rsd_grid_partition(n, depth, _ptr(dof_node), parent.ctypes.data, st), "rsd_grid_partition")
+    return dict(n=n, depth=depth, n_dof=nd, nnz=nz, rowptr=rowptr, col=col, val=val, b=b,
+                dof_node=dof_node, parent=parent)
+
+
+class RSD:
+    """A built hierarchy (rsd_handle).  Use RSD.setup(...)."""
+
+    def __init__(self, handle: int, n: int):
+        self._h = C.c_void_p(handle)
+        self.n = n
+
+    @classmethod
+    def setup(cls, rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor,
+              dof_node: torch.Tensor, parent, prec_leaf: int = RSD_PREC_TF32,
+              prec_mid: int = RSD_PREC_TF32, prec_root: int = RSD_PREC_FP64,
+              maxit: int = 200) -> "RSD":
+        lib = _lib.load()
+        dev = rowptr.is_cuda
+        if not (col.is_cuda == dev and val.is_cuda == dev and dof_node.is_cuda == dev):
+            raise ValueError("rowptr, col, val and dof_node must all be on the device or all on the host")
+        rowptr = rowptr.to(torch.int64).contiguous()
+        col = col.to(torch.int32).contiguous()
+        val = val.to(torch.float64).contiguous()
+        dof_node = dof_node.to(torch.int32).contiguous()
+        par = np.ascontiguousarray(np.asarray(parent, dtype=np.int32))
+        n = rowptr.numel() - 1
+        csr = _lib.rsd_csr(n, col.numel(), _ptr(rowptr), _ptr(col), _ptr(val),
+                           RSD_MEM_DEVICE if dev else RSD_MEM_HOST)
+        tree = _lib.rsd_tree(len(par), par.ctypes.data)
+        opt = _lib.rsd_options(RSD_MODE_EXACT, prec_leaf, prec_mid, prec_root, maxit,
+                               _stream() if torch.cuda.is_available() else 0)
+        out = C.c_void_p()
+        rc = lib.rsd_setup(C.byref(csr), _ptr(dof_node), C.byref(tree), C.byref(opt), C.byref(out))
+        if rc != 0:
+            if out.value:
+                lib.rsd_destroy(out)
+            raise RSDError(rc, "rsd_setup")
+        return cls(out.value, n)
+
+    def __del__(self):
+        try:
+            if self._h and self._h.value:
+                _lib.load().rsd_destroy(self._h)
+                self._h = C.c_void_p()
+        except Exception:
+            pass
+
+    close = __del__
+
+    def apply(self, r: torch.Tensor, z: torch.Tensor | None = None) -> torch.Tensor:
+        z = torch.empty_like(r) if z is None else z
+        check(_lib.load().rsd_apply(self._h, _ptr(r), _ptr(z)), "rsd_apply")
+        return z
+
+    def solve(self, f: torch.Tensor, tol: float = 1e-8, u: torch.Tensor | None = None,
+              allow_noconv: bool = False):
+        u = torch.empty_like(f) if u is None else u
+        st = _lib.rsd_stats()
+        rc = _lib.load().rsd_solve(self._h, _ptr(f), _ptr(u), tol, C.byref(st))
+        if rc != 0 and not (allow_noconv and rc == _lib.RSD_ERR_NOCONV):
+            raise RSDError(rc, "rsd_solve")
+        hist = [st.history[i] for i in range(min(st.iterations + 1, 64))]
+        return u, dict(iterations=st.iterations, relres=st.relres,
+                       relres_recursive=st.relres_recursive, history=hist)
+
+    def check(self) -> None:
+        check(_lib.load().rsd_check(self._h), "rsd_check")
+
+    def info(self) -> dict:
+        inf = _lib.rsd_info_t()
+        check(_lib.load().rsd_get_info(self._h, C.byref(inf)), "rsd_get_info")
+        return {k: getattr(inf, k) for k, _ in _lib.rsd_info_t._fields_}
+
+    def front_dims(self, node: int) -> tuple[int, int, int]:
+        s, b, lv = C.c_int32(), C.c_int32(), C.c_int32()
+        check(_lib.load().rsd_front_dims(self._h, node, C.byref(s), C.byref(b), C.byref(lv)), "rsd_front_dims")
+        return s.value, b.value, lv.value
+
+    def front_dofs(self, node: int) -> np.ndarray:
+        s, b, _ = self.front_dims(node)
+        out = np.empty(s + b, dtype=np.int32)
+        check(_lib.load().rsd_front_dofs(self._h, node, out.ctypes.data), "rsd_front_dofs")
+        return out
+
+    def front_map(self, node: int) -> np.ndarray:
+        _, b, _ = self.front_dims(node)
+        out = np.empty(max(b, 1), dtype=np.int32)
+        check(_lib.load().rsd_front_map(self._h, node, out.ctypes.data), "rsd_front_map")
+        return out[:b]
+
+    def front_factor(self, node: int) -> np.ndarray:
+        s, b, _ = self.front_dims(node)
+        out = np.empty((s + b) * max(s, 1), dtype=np.float64)
+        check(_lib.load().rsd_front_factor(self._h, node, out.ctypes.data), "rsd_front_factor")
+        return out[: (s + b) * s].reshape(s + b, s)

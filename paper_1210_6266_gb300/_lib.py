@@ -1,0 +1,112 @@
+"""ctypes binding of librsd.so: the C ABI of include/rsd.h, names unchanged.
+
+Argument marshalling only.  Every numerical step runs in the library's CUDA kernels;
+there is no Python or CPU fallback, and loading fails loudly if the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librsd.so")
+
+RSD_OK = 0
+RSD_ERR_ARG = -1
+RSD_ERR_PARTITION = -2
+RSD_ERR_NOT_SPD = -3
+RSD_ERR_NOMEM = -4
+RSD_ERR_CUDA = -5
+RSD_ERR_TIMEOUT = -6
+RSD_ERR_NOCONV = -7
+
+RSD_PREC_FP64 = 0
+RSD_PREC_FP32 = 1
+RSD_PREC_TF32 = 2
+
+RSD_MODE_EXACT = 0
+RSD_MEM_HOST = 0
+RSD_MEM_DEVICE = 1
+
+# every function include/rsd.h declares (checked by the tests)
+EXPORTS = [
+    "rsd_setup", "rsd_apply", "rsd_solve", "rsd_check", "rsd_destroy", "rsd_strerror",
+    "rsd_get_info", "rsd_front_dims", "rsd_front_dofs", "rsd_front_map", "rsd_front_factor",
+    "rsd_grid_sizes", "rsd_grid_assemble", "rsd_grid_load", "rsd_grid_partition",
+]
+
+
+class rsd_csr(C.Structure):
+    _fields_ = [("n", C.c_int32), ("nnz", C.c_int64), ("rowptr", C.c_void_p),
+                ("col", C.c_void_p), ("val", C.c_void_p), ("mem", C.c_int32)]
+
+
+class rsd_tree(C.Structure):
+    _fields_ = [("n_nodes", C.c_int32), ("parent", C.c_void_p)]
+
+
+class rsd_options(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("prec_leaf", C.c_int32), ("prec_mid", C.c_int32),
+                ("prec_root", C.c_int32), ("maxit", C.c_int32), ("stream", C.c_void_p)]
+
+
+class rsd_stats(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("relres", C.c_double),
+                ("relres_recursive", C.c_double), ("history", C.c_double * 64)]
+
+
+class rsd_info_t(C.Structure):
+    _fields_ = [("n", C.c_int32), ("n_nodes", C.c_int32), ("n_levels", C.c_int32),
+                ("factor_elems", C.c_int64), ("factor_bytes", C.c_int64),
+                ("setup_flops", C.c_double), ("device_bytes", C.c_int64),
+                ("notspd_node", C.c_int32)]
+
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it first (paper_1210_6266_gb300/build.py)")
+        lib = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        sig = {
+            "rsd_setup": (C.c_int, [C.POINTER(rsd_csr), P, C.POINTER(rsd_tree), C.POINTER(rsd_options), C.POINTER(P)]),
+            "rsd_apply": (C.c_int, [P, P, P]),
+            "rsd_solve": (C.c_int, [P, P, P, C.c_double, C.POINTER(rsd_stats)]),
+            "rsd_check": (C.c_int, [P]),
+            "rsd_destroy": (None, [P]),
+            "rsd_strerror": (C.c_char_p, [C.c_int]),
+            "rsd_last_error_detail": (C.c_char_p, []),
+            "rsd_get_info": (C.c_int, [P, C.POINTER(rsd_info_t)]),
+            "rsd_front_dims": (C.c_int, [P, C.c_int32, P, P, P]),
+            "rsd_front_dofs": (C.c_int, [P, C.c_int32, P]),
+            "rsd_front_map": (C.c_int, [P, C.c_int32, P]),
+            "rsd_front_factor": (C.c_int, [P, C.c_int32, P]),
+            "rsd_grid_sizes": (C.c_int, [C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+            "rsd_grid_assemble": (C.c_int, [C.c_int32, P, P, P, P, P]),
+            "rsd_grid_load": (C.c_int, [C.c_int32, P, P, P]),
+            "rsd_grid_partition": (C.c_int, [C.c_int32, C.c_int32, P, P, P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class RSDError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        lib = load()
+        detail = lib.rsd_last_error_detail().decode()
+        super().__init__(f"{where}: {lib.rsd_strerror(code).decode()} ({code}) {detail}")
+        self.code = code
+
+
+def check(code: int, where: str) -> int:
+    if code != RSD_OK:
+        raise RSDError(code, where)
+    return code

@@ -1,0 +1,604 @@
+// C ABI entry points and the host-side analysis of the sub-domain hierarchy.
+//
+// Analysis (integer work, multithreaded C++ on the host):
+//   1. the tree of Sec. 2: depth, children, Euler-tour intervals (ancestor tests);
+//   2. I_t: the DOFs each node owns, ascending (stable counting sort);
+//   3. Eq. 3.1's block structure: every nonzero K_ij couples ancestor-related owners;
+//   4. B_t = (adj(I_t) u B_children) restricted to proper ancestors' DOFs, ascending;
+//      equivalently the ancestor DOFs adjacent to the subtree of t;
+//   5. extend-add maps ea_t: position of each B_t DOF inside the parent's front I_p ++ B_p.
+// Numeric setup and every later step run in the CUDA kernels of this library.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <thread>
+
+#include "rsd_internal.cuh"
+
+namespace rsd {
+
+static thread_local std::string g_last_error;
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+int pcg(Handle& h, const double* f, double* u, double tol, rsd_stats* st);
+int gemm_tc_prepare(Handle& h);     // tensor maps for the tensor-core levels (gemm_tc.cu)
+void gemm_tc_release(Handle& h);
+
+namespace {
+
+template <typename F>
+void parallel_for(int64_t n, F fn) {
+    const int nt = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    if (n < 2 || nt == 1) {
+        for (int64_t i = 0; i < n; ++i) fn(i);
+        return;
+    }
+    std::atomic<int64_t> next(0);
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t)
+        th.emplace_back([&]() {
+            for (int64_t i; (i = next.fetch_add(1)) < n;) fn(i);
+        });
+    for (auto& x : th) x.join();
+}
+
+template <typename F>
+void parallel_chunks(int64_t n, F fn) {   // fn(begin, end)
+    const int nt = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    const int64_t chunks = std::min<int64_t>(n, nt * 8);
+    if (chunks <= 1) { fn((int64_t)0, n); return; }
+    parallel_for(chunks, [&](int64_t c) { fn(n * c / chunks, n * (c + 1) / chunks); });
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+int round_up(int v, int a) { return (v + a - 1) / a * a; }
+
+struct Analysis {
+    int n = 0, n_nodes = 0;
+    std::vector<int> parent, depth, tin, tout;
+    std::vector<std::vector<int>> children;
+    std::vector<int> owner, rank;
+    std::vector<int> I_off, I_dofs;
+    std::vector<std::vector<int>> B, ea;
+    int max_depth = 0;
+};
+
+int analyse_tree(Analysis& a, const rsd_tree* T) {
+    a.n_nodes = T->n_nodes;
+    if (a.n_nodes <= 0 || a.n_nodes > (1 << 24) || !T->parent) return RSD_ERR_ARG;
+    a.parent.assign(T->parent, T->parent + a.n_nodes);
+    if (a.parent[0] != -1) return RSD_ERR_ARG;
+    a.children.assign(a.n_nodes, {});
+    a.depth.assign(a.n_nodes, 0);
+    for (int t = 1; t < a.n_nodes; ++t) {
+        const int p = a.parent[t];
+        if (p < 0 || p >= t) return RSD_ERR_ARG;
+        a.children[p].push_back(t);
+        a.depth[t] = a.depth[p] + 1;
+        a.max_depth = std::max(a.max_depth, a.depth[t]);
+    }
+    a.tin.assign(a.n_nodes, 0);
+    a.tout.assign(a.n_nodes, 0);
+    int clock = 0;
+    std::vector<std::pair<int, size_t>> stack{{0, 0}};
+    a.tin[0] = clock++;
+    while (!stack.empty()) {
+        auto& [t, k] = stack.back();
+        if (k < a.children[t].size()) {
+            const int c = a.children[t][k++];
+            a.tin[c] = clock++;
+            stack.push_back({c, 0});
+        } else {
+            a.tout[t] = clock++;
+            stack.pop_back();
+        }
+    }
+    return RSD_OK;
+}
+
+inline bool anc_or_self(const Analysis& a, int x, int y) {   // x is ancestor-or-self of y
+    return a.tin[x] <= a.tin[y] && a.tout[y] <= a.tout[x];
+}
+
+int analyse_structure(Analysis& a, const int64_t* rowptr, const int* col, const int* owner) {
+    const int n = a.n;
+    a.owner.assign(owner, owner + n);
+    for (int i = 0; i < n; ++i)
+        if (a.owner[i] < 0 || a.owner[i] >= a.n_nodes) return RSD_ERR_ARG;
+    if (rowptr[0] != 0) return RSD_ERR_ARG;
+    for (int i = 0; i < n; ++i)
+        if (rowptr[i + 1] < rowptr[i]) return RSD_ERR_ARG;
+    // stable counting sort by owner
+    a.I_off.assign(a.n_nodes + 1, 0);
+    for (int i = 0; i < n; ++i) a.I_off[a.owner[i] + 1]++;
+    for (int t = 0; t < a.n_nodes; ++t) a.I_off[t + 1] += a.I_off[t];
+    a.I_dofs.resize(n);
+    a.rank.resize(n);
+    {
+        std::vector<int> fill(a.I_off.begin(), a.I_off.end() - 1);
+        for (int i = 0; i < n; ++i) {
+            const int t = a.owner[i];
+            a.rank[i] = fill[t] - a.I_off[t];
+            a.I_dofs[fill[t]++] = i;
+        }
+    }
+    // Eq. 3.1: no coupling between owners that are not ancestor-related
+    std::atomic<int> bad(0);
+    parallel_chunks(n, [&](int64_t b, int64_t e) {
+        for (int64_t i = b; i < e && !bad.load(std::memory_order_relaxed); ++i) {
+            const int oi = a.owner[i];
+            for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+                const int j = col[k];
+                if (j < 0 || j >= n) { bad = 2; break; }
+                const int oj = a.owner[j];
+                if (oi != oj && !anc_or_self(a, oi, oj) && !anc_or_self(a, oj, oi)) { bad = 1; break; }
+            }
+        }
+    });
+    if (bad == 2) return RSD_ERR_ARG;
+    if (bad == 1) return RSD_ERR_PARTITION;
+    // B sets, bottom-up by depth, nodes of one depth in parallel
+    a.B.assign(a.n_nodes, {});
+    std::vector<std::vector<int>> by_depth(a.max_depth + 1);
+    for (int t = 0; t < a.n_nodes; ++t) by_depth[a.depth[t]].push_back(t);
+    for (int d = a.max_depth; d >= 0; --d) {
+        const auto& nodes = by_depth[d];
+        parallel_for((int64_t)nodes.size(), [&](int64_t idx) {
+            const int t = nodes[idx];
+            std::vector<int> cand;
+            for (int p = a.I_off[t]; p < a.I_off[t + 1]; ++p) {
+                const int i = a.I_dofs[p];
+                for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+                    const int o = a.owner[col[k]];
+                    if (o != t && anc_or_self(a, o, t)) cand.push_back(col[k]);
+                }
+            }
+            for (int c : a.children[t])
+                for (int j : a.B[c]) {
+                    const int o = a.owner[j];
+                    if (o != t && anc_or_self(a, o, t)) cand.push_back(j);
+                }
+            std::sort(cand.begin(), cand.end());
+            cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+            a.B[t] = std::move(cand);
+        });
+    }
+    // extend-add maps
+    a.ea.assign(a.n_nodes, {});
+    parallel_for(a.n_nodes, [&](int64_t tt) {
+        const int t = (int)tt;
+        const int p = a.parent[t];
+        if (p < 0) return;
+        const int sp = a.I_off[p + 1] - a.I_off[p];
+        auto& m = a.ea[t];
+        m.resize(a.B[t].size());
+        for (size_t k = 0; k < a.B[t].size(); ++k) {
+            const int j = a.B[t][k];
+            if (a.owner[j] == p) m[k] = a.rank[j];
+            else m[k] = sp + (int)(std::lower_bound(a.B[p].begin(), a.B[p].end(), j) - a.B[p].begin());
+        }
+    });
+    return RSD_OK;
+}
+
+int level_precision(const rsd_options& o, int depth, bool all_leaves) {
+    if (depth == 0) return o.prec_root;
+    return all_leaves ? o.prec_leaf : o.prec_mid;
+}
+
+bool valid_prec(int p) { return p == RSD_PREC_FP64 || p == RSD_PREC_FP32 || p == RSD_PREC_TF32; }
+
+}  // namespace
+
+// Build the handle's levels, memory plan and device copies from an analysis.
+static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int* col, const double* val) {
+    h.n = a.n;
+    h.n_nodes = a.n_nodes;
+    h.parent = a.parent;
+    h.depth = a.depth;
+    h.I_off = a.I_off;
+    h.I_dofs = a.I_dofs;
+    h.B_off.assign(a.n_nodes + 1, 0);
+    for (int t = 0; t < a.n_nodes; ++t) h.B_off[t + 1] = h.B_off[t] + (int)a.B[t].size();
+    h.B_dofs.resize(h.B_off.back());
+    for (int t = 0; t < a.n_nodes; ++t) std::copy(a.B[t].begin(), a.B[t].end(), h.B_dofs.begin() + h.B_off[t]);
+    std::vector<int> ea_all(h.B_off.back());
+    for (int t = 0; t < a.n_nodes; ++t) std::copy(a.ea[t].begin(), a.ea[t].end(), ea_all.begin() + h.B_off[t]);
+
+    const int nl = a.max_depth + 1;
+    h.levels.assign(nl, Level{});
+    h.node_level.assign(a.n_nodes, 0);
+    h.node_slot.assign(a.n_nodes, 0);
+    for (int t = 0; t < a.n_nodes; ++t) {
+        Level& L = h.levels[a.depth[t]];
+        h.node_level[t] = a.depth[t];
+        h.node_slot[t] = (int)L.nodes.size();
+        L.nodes.push_back(t);
+    }
+    for (int d = 0; d < nl; ++d) {
+        Level& L = h.levels[d];
+        L.depth = d;
+        bool leaves = true;
+        for (int t : L.nodes) leaves &= a.children[t].empty();
+        L.prec = level_precision(h.opt, d, leaves);
+        if (!valid_prec(L.prec)) return RSD_ERR_ARG;
+    }
+    // ---- memory plan ----
+    size_t off = 0;
+    auto take = [&](size_t bytes) { const size_t o = off; off = align_up(off + bytes, 1024); return o; };
+    const size_t o_rowptr = take(sizeof(int64_t) * (a.n + 1));
+    const size_t o_col = take(sizeof(int) * h.nnz);
+    const size_t o_val = take(sizeof(double) * h.nnz);
+    const size_t o_owner = take(sizeof(int) * a.n);
+    const size_t o_rank = take(sizeof(int) * a.n);
+    const size_t o_tin = take(sizeof(int) * a.n_nodes);
+    const size_t o_tout = take(sizeof(int) * a.n_nodes);
+    const size_t o_I = take(sizeof(int) * a.n);
+    const size_t o_B = take(sizeof(int) * std::max<size_t>(1, h.B_dofs.size()));
+    const size_t o_ea = take(sizeof(int) * std::max<size_t>(1, ea_all.size()));
+    const size_t o_flags = take(sizeof(int) * 2 * a.n_nodes);
+    struct FrontPlan { size_t P, U, D, V; };
+    std::vector<FrontPlan> fp(a.n_nodes);
+    std::vector<size_t> lvlP(nl), lvlU(nl);
+    h.factor_elems = 0; h.factor_bytes = 0; h.setup_flops = 0;
+    for (int d = nl - 1; d >= 0; --d) {
+        Level& L = h.levels[d];
+        const size_t es = elem_bytes(L.prec);
+        // P regions of a level are contiguous, then the U regions
+        lvlP[d] = off;
+        for (int t : L.nodes) {
+            const int s = a.I_off[t + 1] - a.I_off[t], b = (int)a.B[t].size();
+            const int ldp = std::max(32, round_up(s, 32));
+            fp[t].P = take((size_t)(s + b) * ldp * es);
+            h.factor_elems += (int64_t)s * (s + 1) / 2 + (int64_t)s * b;
+            h.factor_bytes += ((int64_t)s * (s + 1) / 2 + (int64_t)s * b) * (int64_t)es;
+            h.setup_flops += (double)s * s * s / 3.0 + (double)s * s * b + (double)s * b * b;
+        }
+        L.bytes_P = off - lvlP[d];
+        lvlU[d] = off;
+        for (int t : L.nodes) {
+            const int b = (int)a.B[t].size();
+            const int ldu = std::max(32, round_up(b, 32));
+            fp[t].U = take((size_t)b * ldu * es);
+        }
+        L.bytes_U = off - lvlU[d];
+        for (int t : L.nodes) {
+            const int s = a.I_off[t + 1] - a.I_off[t], b = (int)a.B[t].size();
+            const int nd = (s + NB - 1) / NB;
+            fp[t].D = take((size_t)std::max(1, nd) * NB * NB * es);
+            fp[t].V = take((size_t)(s + b + 32) * es);
+        }
+    }
+    const size_t o_fronts = take(sizeof(FrontDesc) * a.n_nodes);
+    size_t n_items = 16;
+    for (int t = 0; t < a.n_nodes; ++t) {
+        const size_t s = a.I_off[t + 1] - a.I_off[t], b = a.B[t].size();
+        n_items += 2 * ((s + NB - 1) / NB) + (b + NB - 1) / NB;
+    }
+    const size_t o_items = take(sizeof(int) * n_items);
+    const size_t o_child = take(sizeof(int) * a.n_nodes);
+    const size_t o_vecs = take(sizeof(double) * 4 * (size_t)a.n + 4096);
+    const size_t o_partial = take(sizeof(double) * 2048);
+    const size_t o_scal = take(sizeof(double) * 16);
+    const size_t o_err = take(sizeof(int) * ERR_SLOTS);
+    const size_t o_ticket = take(sizeof(int) * 2 * nl + 16);
+    h.arena_bytes = off;
+    if (cudaMalloc((void**)&h.arena, h.arena_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        h.arena = nullptr;
+        set_last_error("device arena of " + std::to_string(h.arena_bytes) + " bytes");
+        return RSD_ERR_NOMEM;
+    }
+    char* A = h.arena;
+    h.d_rowptr = (int64_t*)(A + o_rowptr);
+    h.d_col = (int*)(A + o_col);
+    h.d_val = (double*)(A + o_val);
+    h.d_err = (int*)(A + o_err);
+    h.d_ticket = (int*)(A + o_ticket);
+    h.d_partial = (double*)(A + o_partial);
+    h.d_scal = (double*)(A + o_scal);
+    double* vecs = (double*)(A + o_vecs);
+    h.d_r = vecs; h.d_p = vecs + a.n; h.d_q = vecs + 2 * (size_t)a.n; h.d_z = vecs + 3 * (size_t)a.n;
+    int* d_owner = (int*)(A + o_owner);
+    int* d_rank = (int*)(A + o_rank);
+    int* d_tin = (int*)(A + o_tin);
+    int* d_tout = (int*)(A + o_tout);
+    int* d_I = (int*)(A + o_I);
+    int* d_B = (int*)(A + o_B);
+    int* d_ea = (int*)(A + o_ea);
+    int* d_flags = (int*)(A + o_flags);
+    FrontDesc* d_fronts = (FrontDesc*)(A + o_fronts);
+    int* d_items = (int*)(A + o_items);
+    int* d_child = (int*)(A + o_child);
+    cudaStream_t st = h.stream;
+    RSD_CUDA_TRY(cudaMemcpyAsync(h.d_rowptr, rowptr, sizeof(int64_t) * (a.n + 1), cudaMemcpyDefault, st));
+    RSD_CUDA_TRY(cudaMemcpyAsync(h.d_col, col, sizeof(int) * h.nnz, cudaMemcpyDefault, st));
+    RSD_CUDA_TRY(cudaMemcpyAsync(h.d_val, val, sizeof(double) * h.nnz, cudaMemcpyDefault, st));
+    RSD_CUDA_TRY(cudaMemcpyAsync(d_owner, a.owner.data(), sizeof(int) * a.n, cudaMemcpyHostToDevice, st));
+    RSD_CUDA_TRY(cudaMemcpyAsync(d_rank, a.rank.data(), sizeof(int) * a.n, cudaMemcpyHostToDevice, st));
+    RSD_CUDA_TRY(cudaMemcpyAsync(d_tin, a.tin.data(), sizeof(int) * a.n_nodes, cudaMemcpyHostToDevice, st));
+    RSD_CUDA_TRY(cudaMemcpyAsync(d_tout, a.tout.data(), sizeof(int) * a.n_nodes, cudaMemcpyHostToDevice, st));
+    RSD_CUDA_TRY(cudaMemcpyAsync(d_I, a.I_dofs.data(), sizeof(int) * a.n, cudaMemcpyHostToDevice, st));
+    if (!h.B_dofs.empty()) {
+        RSD_CUDA_TRY(cudaMemcpyAsync(d_B, h.B_dofs.data(), sizeof(int) * h.B_dofs.size(), cudaMemcpyHostToDevice, st));
+        RSD_CUDA_TRY(cudaMemcpyAsync(d_ea, ea_all.data(), sizeof(int) * ea_all.size(), cudaMemcpyHostToDevice, st));
+    }
+    RSD_CUDA_TRY(cudaMemsetAsync(h.d_err, 0, sizeof(int) * ERR_SLOTS, st));
+    {
+        const int big = 0x7fffffff;
+        RSD_CUDA_TRY(cudaMemcpyAsync(h.d_err + ERR_NOT_SPD_NODE, &big, sizeof(int), cudaMemcpyHostToDevice, st));
+    }
+    // ---- fronts, child tables, work lists ----
+    size_t front_cursor = 0, item_cursor = 0;
+    std::vector<int> child_tab;
+    std::vector<int> items_all;
+    for (int d = 0; d < nl; ++d) {
+        Level& L = h.levels[d];
+        L.fronts.resize(L.nodes.size());
+        L.max_s = L.max_b = L.max_N = 0;
+        L.max_children = 0;
+        const size_t child_base = child_tab.size();
+        for (size_t sidx = 0; sidx < L.nodes.size(); ++sidx) {
+            const int t = L.nodes[sidx];
+            FrontDesc& f = L.fronts[sidx];
+            f.node = t;
+            f.s = a.I_off[t + 1] - a.I_off[t];
+            f.b = (int)a.B[t].size();
+            f.N = f.s + f.b;
+            f.ldp = std::max(32, round_up(f.s, 32));
+            f.ldu = std::max(32, round_up(f.b, 32));
+            f.nd = (f.s + NB - 1) / NB;
+            f.parent_slot = a.parent[t] >= 0 ? h.node_slot[a.parent[t]] : -1;
+            f.P = A + fp[t].P;
+            f.U = A + fp[t].U;
+            f.Dinv = A + fp[t].D;
+            f.vec = A + fp[t].V;
+            f.I = d_I + a.I_off[t];
+            f.Bd = d_B + h.B_off[t];
+            f.ea = d_ea + h.B_off[t];
+            f.flag = d_flags + 2 * t;
+            f.child_begin = (int)(child_tab.size() - child_base);
+            f.child_count = (int)a.children[t].size();
+            for (int c : a.children[t]) child_tab.push_back(h.node_slot[c]);
+            L.max_s = std::max(L.max_s, f.s);
+            L.max_b = std::max(L.max_b, f.b);
+            L.max_N = std::max(L.max_N, f.N);
+            L.max_children = std::max(L.max_children, f.child_count);
+        }
+        L.d_fronts = d_fronts + front_cursor;
+        front_cursor += L.fronts.size();
+        L.d_child_slots = d_child + child_base;
+        // forward items: key = block index (I blocks, then B blocks), fronts interleaved
+        std::vector<std::pair<int, int>> fw, bw;   // (key, item)
+        for (size_t sidx = 0; sidx < L.fronts.size(); ++sidx) {
+            const FrontDesc& f = L.fronts[sidx];
+            const int nbB = (f.b + NB - 1) / NB;
+            for (int blk = 0; blk < f.nd + nbB; ++blk) fw.push_back({blk, (int)(sidx << 16) | blk});
+            for (int cb = f.nd - 1; cb >= 0; --cb) bw.push_back({f.nd - 1 - cb, (int)(sidx << 16) | cb});
+        }
+        std::stable_sort(fw.begin(), fw.end(), [](auto& x, auto& y) { return x.first < y.first; });
+        std::stable_sort(bw.begin(), bw.end(), [](auto& x, auto& y) { return x.first < y.first; });
+        L.d_fwd_items = d_items + item_cursor;
+        L.n_fwd_items = (int)fw.size();
+        for (auto& x : fw) items_all.push_back(x.second);
+        item_cursor += fw.size();
+        L.d_bwd_items = d_items + item_cursor;
+        L.n_bwd_items = (int)bw.size();
+        for (auto& x : bw) items_all.push_back(x.second);
+        item_cursor += bw.size();
+    }
+    if (items_all.size() > n_items) { set_last_error("work list overflow"); return RSD_ERR_ARG; }
+    for (int d = 0; d < nl; ++d) {
+        Level& L = h.levels[d];
+        RSD_CUDA_TRY(cudaMemcpyAsync(L.d_fronts, L.fronts.data(), sizeof(FrontDesc) * L.fronts.size(), cudaMemcpyHostToDevice, st));
+    }
+    if (!items_all.empty())
+        RSD_CUDA_TRY(cudaMemcpyAsync(d_items, items_all.data(), sizeof(int) * items_all.size(), cudaMemcpyHostToDevice, st));
+    if (!child_tab.empty())
+        RSD_CUDA_TRY(cudaMemcpyAsync(d_child, child_tab.data(), sizeof(int) * child_tab.size(), cudaMemcpyHostToDevice, st));
+    RSD_CUDA_TRY(cudaMemsetAsync(d_flags, 0, sizeof(int) * 2 * a.n_nodes, st));
+    // the tensor-core levels need tensor maps over the fronts just placed
+    RSD_TRY(gemm_tc_prepare(h));
+    // ---- numeric setup, deepest level first ----
+    for (int d = nl - 1; d >= 0; --d) {
+        RSD_TRY(launch_assemble_fronts(h, d, h.d_rowptr, h.d_col, h.d_val, d_owner, d_rank, d_tin, d_tout));
+        RSD_TRY(launch_extend_add(h, d));
+        RSD_TRY(run_factor_level(h, d));
+    }
+    RSD_CUDA_TRY(cudaStreamSynchronize(st));
+    int err[ERR_SLOTS];
+    RSD_CUDA_TRY(cudaMemcpy(err, h.d_err, sizeof(err), cudaMemcpyDeviceToHost));
+    if (err[ERR_NOT_SPD]) {
+        h.notspd_node = err[ERR_NOT_SPD_NODE];
+        set_last_error("pivot <= 0 in node " + std::to_string(h.notspd_node));
+        return RSD_ERR_NOT_SPD;
+    }
+    return RSD_OK;
+}
+
+}  // namespace rsd
+
+using namespace rsd;
+
+struct rsd_handle_s {
+    Handle h;
+};
+
+extern "C" const char* rsd_strerror(int code) {
+    switch (code) {
+        case RSD_OK: return "ok";
+        case RSD_ERR_ARG: return "invalid argument";
+        case RSD_ERR_PARTITION: return "matrix couples sub-domains that are not ancestor-related (Eq. 3.1 violated)";
+        case RSD_ERR_NOT_SPD: return "non-positive pivot in a factorisation";
+        case RSD_ERR_NOMEM: return "out of memory";
+        case RSD_ERR_CUDA: return "CUDA error";
+        case RSD_ERR_TIMEOUT: return "bounded device wait timed out";
+        case RSD_ERR_NOCONV: return "Krylov solve did not converge within maxit";
+        default: return "unknown error";
+    }
+}
+
+extern "C" const char* rsd_last_error_detail(void) { return g_last_error.c_str(); }
+
+extern "C" void rsd_destroy(rsd_handle hh) {
+    if (!hh) return;
+    Handle& h = hh->h;
+    if (h.stream) cudaStreamSynchronize(h.stream);
+    gemm_tc_release(h);
+    if (h.arena) cudaFree(h.arena);
+    if (h.h_scal) cudaFreeHost(h.h_scal);
+    delete hh;
+}
+
+extern "C" int rsd_setup(const rsd_csr* K, const int32_t* dof_node, const rsd_tree* T,
+                         const rsd_options* opt, rsd_handle* out) {
+    if (!K || !dof_node || !T || !out || K->n <= 0 || K->nnz <= 0 || !K->rowptr || !K->col || !K->val)
+        return RSD_ERR_ARG;
+    if (K->mem != RSD_MEM_HOST && K->mem != RSD_MEM_DEVICE) return RSD_ERR_ARG;
+    *out = nullptr;
+    rsd_options o{};
+    o.mode = RSD_MODE_EXACT;
+    o.prec_leaf = RSD_PREC_TF32;
+    o.prec_mid = RSD_PREC_TF32;
+    o.prec_root = RSD_PREC_FP64;
+    o.maxit = 200;
+    if (opt) o = *opt;
+    if (o.mode != RSD_MODE_EXACT) return RSD_ERR_ARG;
+    Analysis a;
+    a.n = K->n;
+    RSD_TRY(analyse_tree(a, T));
+    // host views of the inputs
+    std::vector<int64_t> rp;
+    std::vector<int> cl, ow;
+    std::vector<double> vl;
+    const int64_t* rowptr = K->rowptr;
+    const int* col = K->col;
+    const int* owner = dof_node;
+    cudaStream_t st = (cudaStream_t)o.stream;
+    if (K->mem == RSD_MEM_DEVICE) {
+        rp.resize(K->n + 1);
+        cl.resize(K->nnz);
+        ow.resize(K->n);
+        RSD_CUDA_TRY(cudaMemcpyAsync(rp.data(), K->rowptr, sizeof(int64_t) * (K->n + 1), cudaMemcpyDeviceToHost, st));
+        RSD_CUDA_TRY(cudaMemcpyAsync(cl.data(), K->col, sizeof(int) * K->nnz, cudaMemcpyDeviceToHost, st));
+        RSD_CUDA_TRY(cudaMemcpyAsync(ow.data(), dof_node, sizeof(int) * K->n, cudaMemcpyDeviceToHost, st));
+        RSD_CUDA_TRY(cudaStreamSynchronize(st));
+        rowptr = rp.data();
+        col = cl.data();
+        owner = ow.data();
+    }
+    if (rowptr[K->n] != K->nnz) return RSD_ERR_ARG;
+    RSD_TRY(analyse_structure(a, rowptr, col, owner));
+    auto* hh = new (std::nothrow) rsd_handle_s();
+    if (!hh) return RSD_ERR_NOMEM;
+    Handle& h = hh->h;
+    h.opt = o;
+    h.stream = st;
+    h.nnz = K->nnz;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&h.num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaMallocHost((void**)&h.h_scal, sizeof(double) * 16) != cudaSuccess) {
+        cudaGetLastError();
+        delete hh;
+        return RSD_ERR_NOMEM;
+    }
+    // numeric values come from the caller's memory directly (device or host)
+    const int rc = build_handle(h, a, rowptr, col, K->val);
+    if (rc != RSD_OK) {
+        h.notspd_node = h.notspd_node;
+        if (rc == RSD_ERR_NOT_SPD) { *out = hh; return rc; }   // handle kept for introspection
+        rsd_destroy(hh);
+        return rc;
+    }
+    *out = hh;
+    return RSD_OK;
+}
+
+extern "C" int rsd_apply(rsd_handle hh, const double* r, double* z) {
+    if (!hh || !r || !z || r == z) return RSD_ERR_ARG;
+    return run_apply(hh->h, r, z);
+}
+
+extern "C" int rsd_check(rsd_handle hh) {
+    if (!hh) return RSD_ERR_ARG;
+    Handle& h = hh->h;
+    RSD_CUDA_TRY(cudaStreamSynchronize(h.stream));
+    int err[ERR_SLOTS];
+    RSD_CUDA_TRY(cudaMemcpy(err, h.d_err, sizeof(err), cudaMemcpyDeviceToHost));
+    if (err[ERR_TIMEOUT]) return RSD_ERR_TIMEOUT;
+    if (err[ERR_NOT_SPD]) return RSD_ERR_NOT_SPD;
+    return RSD_OK;
+}
+
+extern "C" int rsd_solve(rsd_handle hh, const double* f, double* u, double tol, rsd_stats* st) {
+    if (!hh || !f || !u || !(tol > 0)) return RSD_ERR_ARG;
+    const int rc = pcg(hh->h, f, u, tol, st);
+    const int chk = rsd_check(hh);
+    if (chk != RSD_OK) return chk;
+    return rc;
+}
+
+extern "C" int rsd_get_info(rsd_handle hh, rsd_info_t* out) {
+    if (!hh || !out) return RSD_ERR_ARG;
+    const Handle& h = hh->h;
+    out->n = h.n;
+    out->n_nodes = h.n_nodes;
+    out->n_levels = (int)h.levels.size();
+    out->factor_elems = h.factor_elems;
+    out->factor_bytes = h.factor_bytes;
+    out->setup_flops = h.setup_flops;
+    out->device_bytes = (int64_t)h.arena_bytes;
+    out->notspd_node = h.notspd_node;
+    return RSD_OK;
+}
+
+extern "C" int rsd_front_dims(rsd_handle hh, int32_t node, int32_t* s, int32_t* b, int32_t* level) {
+    if (!hh || node < 0 || node >= hh->h.n_nodes) return RSD_ERR_ARG;
+    const Handle& h = hh->h;
+    if (s) *s = h.I_off[node + 1] - h.I_off[node];
+    if (b) *b = h.B_off[node + 1] - h.B_off[node];
+    if (level) *level = h.depth[node];
+    return RSD_OK;
+}
+
+extern "C" int rsd_front_dofs(rsd_handle hh, int32_t node, int32_t* out) {
+    if (!hh || !out || node < 0 || node >= hh->h.n_nodes) return RSD_ERR_ARG;
+    const Handle& h = hh->h;
+    const int s = h.I_off[node + 1] - h.I_off[node];
+    std::copy(h.I_dofs.begin() + h.I_off[node], h.I_dofs.begin() + h.I_off[node + 1], out);
+    std::copy(h.B_dofs.begin() + h.B_off[node], h.B_dofs.begin() + h.B_off[node + 1], out + s);
+    return RSD_OK;
+}
+
+extern "C" int rsd_front_map(rsd_handle hh, int32_t node, int32_t* out) {
+    if (!hh || !out || node < 0 || node >= hh->h.n_nodes) return RSD_ERR_ARG;
+    Handle& h = hh->h;
+    const Level& L = h.levels[h.node_level[node]];
+    const FrontDesc& f = L.fronts[h.node_slot[node]];
+    if (f.b == 0) return RSD_OK;
+    RSD_CUDA_TRY(cudaMemcpy(out, f.ea, sizeof(int) * f.b, cudaMemcpyDeviceToHost));
+    return RSD_OK;
+}
+
+extern "C" int rsd_front_factor(rsd_handle hh, int32_t node, double* out) {
+    if (!hh || !out || node < 0 || node >= hh->h.n_nodes) return RSD_ERR_ARG;
+    Handle& h = hh->h;
+    RSD_CUDA_TRY(cudaStreamSynchronize(h.stream));
+    const Level& L = h.levels[h.node_level[node]];
+    const FrontDesc& f = L.fronts[h.node_slot[node]];
+    const size_t es = elem_bytes(L.prec);
+    std::vector<char> buf((size_t)f.N * f.ldp * es);
+    if (!buf.empty()) RSD_CUDA_TRY(cudaMemcpy(buf.data(), f.P, buf.size(), cudaMemcpyDeviceToHost));
+    for (int r = 0; r < f.N; ++r)
+        for (int c = 0; c < f.s; ++c) {
+            double v = es == 8 ? ((const double*)buf.data())[(size_t)r * f.ldp + c]
+                               : (double)((const float*)buf.data())[(size_t)r * f.ldp + c];
+            out[(size_t)r * f.s + c] = (r < f.s && c > r) ? 0.0 : v;
+        }
+    return RSD_OK;
+}

@@ -1,0 +1,317 @@
+// Preconditioner application z = M r (Algorithm 2 in its exact limit).
+//
+// Upward sweep, deepest level first: each front gathers r on I_t and adds its children's
+// contributions (the K_IL K_LL^-1 f_L terms of g in Eq. 3.2), solves L y = v_I and forms
+// its own contribution v_B - X y for the parent.  Downward sweep, root first: each front
+// gathers the ancestors' solution on B_t and back-substitutes L^T x_I = y - X^T x_B
+// (Eq. 3.3), writing x_I into z.
+//
+// The triangular solves are split into NB-row (upward) / NB-column (downward) blocks.
+// Blocks of all fronts of a level form one work list; a persistent grid takes blocks
+// from the list with an atomic ticket, so a block only ever waits for blocks with a
+// smaller ticket, which are already held by running CTAs (no deadlock without
+// co-residency).  A block that consumes a result from another block polls that front's
+// progress counter with a bounded wait; on timeout it raises ERR_TIMEOUT and proceeds.
+// The factor is streamed once per sweep with 16-byte non-coherent loads.
+#include <algorithm>
+
+#include "rsd_internal.cuh"
+
+namespace rsd {
+namespace {
+
+constexpr int AT = 256;                  // threads per CTA
+constexpr int AW = AT / 32;              // warps
+constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
+
+template <typename T> struct Vec;
+template <> struct Vec<float> { using V = float4; static constexpr int W = 4; };
+template <> struct Vec<double> { using V = double2; static constexpr int W = 2; };
+
+__device__ __forceinline__ float vget(const float4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
+__device__ __forceinline__ double vget(const double2& v, int i) { return i == 0 ? v.x : v.y; }
+
+template <typename T> __device__ __forceinline__ T ld_cg(const T* p);
+template <> __device__ __forceinline__ float ld_cg(const float* p) { return __ldcg(p); }
+template <> __device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
+
+__device__ __forceinline__ int ld_volatile(const int* p) { return *(volatile const int*)p; }
+
+// Wait until *flag >= target; returns the last value seen.  Thread 0 polls, the block syncs.
+__device__ int wait_flag(const int* flag, int target, int* err, int* s_val) {
+    if (threadIdx.x == 0) {
+        int v = ld_volatile(flag);
+        if (v < target) {
+            const long long t0 = clock64();
+            while ((v = ld_volatile(flag)) < target) {
+                if (ld_volatile(&err[ERR_TIMEOUT]) || clock64() - t0 > WAIT_CYCLES) {
+                    atomicExch(&err[ERR_TIMEOUT], 1);
+                    v = target;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        *s_val = v;
+    }
+    __syncthreads();
+    return *s_val;
+}
+
+__device__ void publish_flag(int* flag, int value) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) atomicExch(flag, value);
+}
+
+// ---- upward sweep ------------------------------------------------------------------
+template <typename A, typename Ac>
+__global__ void k_fwd_gather(const FrontDesc* __restrict__ fronts, const FrontDesc* __restrict__ kids,
+                             const int* __restrict__ child_slots, const double* __restrict__ r) {
+    const FrontDesc f = fronts[blockIdx.x];
+    A* v = (A*)f.vec;
+    for (int p = threadIdx.x; p < f.N; p += blockDim.x) v[p] = p < f.s ? (A)r[f.I[p]] : (A)0;
+    if (threadIdx.x == 0) { f.flag[0] = 0; f.flag[1] = 0; }
+    for (int ci = 0; ci < f.child_count; ++ci) {
+        __syncthreads();
+        const FrontDesc c = kids[child_slots[f.child_begin + ci]];
+        const Ac* cv = (const Ac*)c.vec;
+        for (int i = threadIdx.x; i < c.b; i += blockDim.x) v[c.ea[i]] += (A)cv[c.s + i];
+    }
+}
+
+// Row block item: rows [r0, r1) of front f.  acc_row = v_row - sum_{cb < ncb} P[row, cb] y_cb;
+// for a diagonal block y = Dinv * acc (published), else the contribution v_row = acc.
+template <typename T, typename A>
+__global__ void __launch_bounds__(AT) k_fwd_sweep(const FrontDesc* __restrict__ fronts,
+                                                  const int* __restrict__ items, int n_items,
+                                                  int* __restrict__ ticket, int* __restrict__ err) {
+    using V = typename Vec<T>::V;
+    constexpr int VW = Vec<T>::W;
+    constexpr int PASSES = NB / (32 * VW);
+    constexpr int RPW = NB / AW;                 // rows per warp
+    __shared__ int s_item, s_flag;
+    __shared__ A s_t[NB];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(ticket, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= n_items) return;
+        const int slot = items[it] >> 16, blk = items[it] & 0xffff;
+        const FrontDesc f = fronts[slot];
+        const bool diag = blk < f.nd;
+        const int r0 = diag ? blk * NB : f.s + (blk - f.nd) * NB;
+        const int r1 = diag ? min(r0 + NB, f.s) : min(r0 + NB, f.N);
+        const int ncb = diag ? blk : f.nd;
+        const T* P = (const T*)f.P;
+        A* v = (A*)f.vec;
+        A acc[RPW];
+#pragma unroll
+        for (int u = 0; u < RPW; ++u) acc[u] = 0;
+        int seen = 0;
+        for (int cb = 0; cb < ncb; ++cb) {
+            if (seen < cb + 1) seen = wait_flag(&f.flag[0], cb + 1, err, &s_flag);
+            const int c0 = cb * NB;
+            const int cw = min(NB, f.s - c0);
+#pragma unroll
+            for (int ps = 0; ps < PASSES; ++ps) {
+                const int cl = ps * 32 * VW + lane * VW;   // column inside the block
+                A y[VW];
+#pragma unroll
+                for (int e = 0; e < VW; ++e) y[e] = (cl + e < cw) ? ld_cg(v + c0 + cl + e) : (A)0;
+                if (cl < cw) {
+                    V l[RPW];
+#pragma unroll
+                    for (int u = 0; u < RPW; ++u) {
+                        const int row = r0 + warp + AW * u;
+                        l[u] = row < r1 ? __ldg((const V*)(P + (int64_t)row * f.ldp + c0 + cl)) : V{};
+                    }
+#pragma unroll
+                    for (int u = 0; u < RPW; ++u)
+#pragma unroll
+                        for (int e = 0; e < VW; ++e) acc[u] += (A)vget(l[u], e) * y[e];
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < RPW; ++u) {
+            A a = acc[u];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            const int row = r0 + warp + AW * u;
+            if (lane == 0 && row < r1) s_t[row - r0] = ld_cg(v + row) - a;
+        }
+        __syncthreads();
+        if (diag) {
+            const int w = r1 - r0;
+            const T* D = (const T*)f.Dinv + (int64_t)blk * NB * NB;
+            for (int rr = warp; rr < w; rr += AW) {
+                A s = 0;
+                for (int c = lane; c <= rr; c += 32) s += (A)D[rr * NB + c] * s_t[c];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                if (lane == 0) __stcg(v + r0 + rr, s);
+            }
+            publish_flag(&f.flag[0], blk + 1);
+        } else {
+            for (int rr = threadIdx.x; rr < r1 - r0; rr += AT) __stcg(v + r0 + rr, s_t[rr]);
+        }
+        __syncthreads();
+    }
+}
+
+// ---- downward sweep ----------------------------------------------------------------
+template <typename A>
+__global__ void k_bwd_gather(const FrontDesc* __restrict__ fronts, const double* __restrict__ z) {
+    const FrontDesc f = fronts[blockIdx.x];
+    A* v = (A*)f.vec;
+    for (int i = threadIdx.x; i < f.b; i += blockDim.x) v[f.s + i] = (A)z[f.Bd[i]];
+}
+
+// Column block item cb: t = y_cb - sum_{rows i >= c1} P[i, cb]^T x_i, x_cb = Dinv^T t.
+template <typename T, typename A>
+__global__ void __launch_bounds__(AT) k_bwd_sweep(const FrontDesc* __restrict__ fronts,
+                                                  const int* __restrict__ items, int n_items,
+                                                  int* __restrict__ ticket, int* __restrict__ err,
+                                                  double* __restrict__ z) {
+    using V = typename Vec<T>::V;
+    constexpr int VW = Vec<T>::W;
+    constexpr int PASSES = NB / (32 * VW);
+    constexpr int RB = 16 / PASSES;              // rows per warp per batch
+    __shared__ int s_item, s_flag;
+    __shared__ A s_red[AW][NB];
+    __shared__ A s_t[NB];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(ticket, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= n_items) return;
+        const int slot = items[it] >> 16, cb = items[it] & 0xffff;
+        const FrontDesc f = fronts[slot];
+        const int c0 = cb * NB, c1 = min(c0 + NB, f.s), cw = c1 - c0;
+        const T* P = (const T*)f.P;
+        A* v = (A*)f.vec;
+        A acc[PASSES][VW];
+#pragma unroll
+        for (int ps = 0; ps < PASSES; ++ps)
+#pragma unroll
+            for (int e = 0; e < VW; ++e) acc[ps][e] = 0;
+        // rows below the diagonal block, processed bottom-up in NB-row groups so that the
+        // interface rows of later blocks are consumed as their owners finish
+        int seen = 0;
+        const int n_groups_B = (f.b + NB - 1) / NB;
+        const int n_groups = n_groups_B + (f.nd - 1 - cb);
+        for (int g = 0; g < n_groups; ++g) {
+            int g0, g1;
+            if (g < n_groups_B) {
+                g0 = f.s + (n_groups_B - 1 - g) * NB; g1 = min(g0 + NB, f.N);
+            } else {
+                const int rb = f.nd - 1 - (g - n_groups_B);      // I row block > cb
+                const int need = f.nd - rb;                        // blocks finished from the top
+                if (seen < need) seen = wait_flag(&f.flag[1], need, err, &s_flag);
+                g0 = rb * NB; g1 = min(g0 + NB, f.s);
+            }
+            for (int rbase = g0 + warp; rbase < g1; rbase += AW * RB) {
+                V l[RB][PASSES];
+                A x[RB];
+#pragma unroll
+                for (int u = 0; u < RB; ++u) {
+                    const int row = rbase + AW * u;
+                    const bool ok = row < g1;
+                    x[u] = ok ? ld_cg(v + row) : (A)0;
+#pragma unroll
+                    for (int ps = 0; ps < PASSES; ++ps) {
+                        const int cl = ps * 32 * VW + lane * VW;
+                        l[u][ps] = (ok && cl < cw) ? __ldg((const V*)(P + (int64_t)row * f.ldp + c0 + cl)) : V{};
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < RB; ++u)
+#pragma unroll
+                    for (int ps = 0; ps < PASSES; ++ps)
+#pragma unroll
+                        for (int e = 0; e < VW; ++e) acc[ps][e] += (A)vget(l[u][ps], e) * x[u];
+            }
+        }
+#pragma unroll
+        for (int ps = 0; ps < PASSES; ++ps)
+#pragma unroll
+            for (int e = 0; e < VW; ++e) s_red[warp][ps * 32 * VW + lane * VW + e] = acc[ps][e];
+        __syncthreads();
+        for (int c = threadIdx.x; c < cw; c += AT) {
+            A s = 0;
+#pragma unroll
+            for (int w = 0; w < AW; ++w) s += s_red[w][c];
+            s_t[c] = ld_cg(v + c0 + c) - s;
+        }
+        __syncthreads();
+        // x = Dinv^T t : x_c = sum_{r >= c} Dinv[r][c] t_r  (column sums, warps over rows)
+        const T* D = (const T*)f.Dinv + (int64_t)cb * NB * NB;
+        for (int c = lane; c < NB; c += 32) {
+            A s = 0;
+            for (int rr = warp; rr < cw; rr += AW) s += (A)D[rr * NB + c] * s_t[rr];
+            s_red[warp][c] = s;
+        }
+        __syncthreads();
+        for (int c = threadIdx.x; c < cw; c += AT) {
+            A s = 0;
+#pragma unroll
+            for (int w = 0; w < AW; ++w) s += s_red[w][c];
+            __stcg(v + c0 + c, s);
+            z[f.I[c0 + c]] = (double)s;
+        }
+        publish_flag(&f.flag[1], f.nd - cb);
+        __syncthreads();
+    }
+}
+
+template <typename T, typename A>
+int sweep_level(Handle& h, int li, bool forward, const double* r, double* z, int tk) {
+    Level& L = h.levels[li];
+    const int nf = (int)L.fronts.size();
+    const int grid = std::max(1, std::min(forward ? L.n_fwd_items : L.n_bwd_items, h.num_sms * 4));
+    if (forward) {
+        if (li + 1 < (int)h.levels.size()) {
+            const Level& Lc = h.levels[li + 1];
+            if (is_fp64(Lc.prec)) k_fwd_gather<A, double><<<nf, 256, 0, h.stream>>>(L.d_fronts, Lc.d_fronts, L.d_child_slots, r);
+            else k_fwd_gather<A, float><<<nf, 256, 0, h.stream>>>(L.d_fronts, Lc.d_fronts, L.d_child_slots, r);
+        } else {
+            k_fwd_gather<A, A><<<nf, 256, 0, h.stream>>>(L.d_fronts, L.d_fronts, L.d_child_slots, r);
+        }
+        RSD_CUDA_TRY(cudaGetLastError());
+        if (L.n_fwd_items)
+            k_fwd_sweep<T, A><<<grid, AT, 0, h.stream>>>(L.d_fronts, L.d_fwd_items, L.n_fwd_items, h.d_ticket + tk, h.d_err);
+    } else {
+        k_bwd_gather<A><<<nf, 256, 0, h.stream>>>(L.d_fronts, z);
+        RSD_CUDA_TRY(cudaGetLastError());
+        if (L.n_bwd_items)
+            k_bwd_sweep<T, A><<<grid, AT, 0, h.stream>>>(L.d_fronts, L.d_bwd_items, L.n_bwd_items, h.d_ticket + tk, h.d_err, z);
+    }
+    RSD_CUDA_TRY(cudaGetLastError());
+    return RSD_OK;
+}
+
+}  // namespace
+
+int run_apply(Handle& h, const double* r, double* z) {
+    const int nl = (int)h.levels.size();
+    RSD_CUDA_TRY(cudaMemsetAsync(h.d_ticket, 0, sizeof(int) * 2 * nl, h.stream));
+    for (int li = nl - 1; li >= 0; --li) {
+        const int rc = is_fp64(h.levels[li].prec) ? sweep_level<double, double>(h, li, true, r, z, li)
+                                                  : sweep_level<float, float>(h, li, true, r, z, li);
+        if (rc != RSD_OK) return rc;
+    }
+    for (int li = 0; li < nl; ++li) {
+        const int rc = is_fp64(h.levels[li].prec) ? sweep_level<double, double>(h, li, false, r, z, nl + li)
+                                                  : sweep_level<float, float>(h, li, false, r, z, nl + li);
+        if (rc != RSD_OK) return rc;
+    }
+    return RSD_OK;
+}
+
+}  // namespace rsd

@@ -1,0 +1,478 @@
+// Setup-phase kernels: front assembly, extend-add of the children's Schur contributions,
+// and the blocked partial Cholesky that eliminates each node's interface block.
+//
+// Per tree node t with interface/interior DOFs I (s of them) and ancestor DOFs B (b):
+//   F_t = K[I u B, I u B] restricted to rows/columns of I, plus sum_c U_c placed by the
+//   extend-add maps; F_t[I,I] is then the interface Schur complement S_t of Eq. 3.2 (the
+//   children's sub-domains already eliminated, Sec. 3.2).
+//   L L^T = F_t[I,I],  X = F_t[B,I] L^-T,  U_t = -X X^T  (U_t's B x B block also carries the
+//   children's contributions that land on B).
+// Storage (row-major, lower triangles): P = [L; X] is N x ldp, U is b x ldu.
+//
+// The partial Cholesky is left-looking by NB-wide column panels:
+//   (a) P[k:N, k:k+w] -= P[k:N, 0:k] P[k:k+w, 0:k]^T          (GEMM, K = k)
+//   (b) L_kk L_kk^T = P[k:k+w, k:k+w]; Dinv_k = L_kk^-1         (one CTA per front)
+//   (c) P[k+w:N, k:k+w] <- P[k+w:N, k:k+w] Dinv_k^T             (TRSM as a GEMM, K = w)
+// and after the last panel
+//   (d) U -= X X^T (lower tiles only)                           (GEMM, K = s)
+#include <algorithm>
+#include <cmath>
+
+#include "rsd_internal.cuh"
+
+namespace rsd {
+
+int gemm_tc_launch(Handle& h, int li, const std::vector<GemmTask>& tasks, int kind,
+                   cudaStream_t st);   // tensor-core path (gemm_tc.cu)
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ T ld_nc(const T* p) { return __ldg(p); }
+
+// ---------------------------------------------------------------------------------
+// Front assembly: each warp takes rows of I_t and scatters K's entries into P.
+// Entry (p, q) of row p (DOF I_t[p]) goes to the lower triangle at (q, p) when q >= p:
+// q is the local index of the column DOF in I_t (q >= p) or s + position in B_t.
+// Columns owned by descendants of t were placed by those descendants; entries with
+// q < p inside I are placed by row q.  Every target is written exactly once.
+// ---------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_scatter_K(const FrontDesc* __restrict__ fronts, const int64_t* __restrict__ rowptr,
+                            const int* __restrict__ col, const double* __restrict__ val,
+                            const int* __restrict__ owner, const int* __restrict__ rank,
+                            const int* __restrict__ tin, const int* __restrict__ tout) {
+    const FrontDesc f = fronts[blockIdx.y];
+    const int lane = threadIdx.x & 31;
+    const int warps = blockDim.x >> 5;
+    const int t = f.node;
+    const int tin_t = tin[t], tout_t = tout[t];
+    T* P = (T*)f.P;
+    for (int p = blockIdx.x * warps + (threadIdx.x >> 5); p < f.s; p += gridDim.x * warps) {
+        const int i = f.I[p];
+        for (int64_t k = rowptr[i] + lane; k < rowptr[i + 1]; k += 32) {
+            const int j = col[k];
+            const int o = owner[j];
+            int q;
+            if (o == t) {
+                q = rank[j];
+                if (q < p) continue;
+            } else if (tin[o] < tin_t && tout_t <= tout[o]) {      // proper ancestor of t
+                int lo = 0, hi = f.b;                                 // lower_bound in B_t
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (f.Bd[mid] < j) lo = mid + 1; else hi = mid;
+                }
+                q = f.s + lo;
+            } else {
+                continue;                                            // a descendant's DOF
+            }
+            P[(int64_t)q * f.ldp + p] = (T)val[k];
+        }
+    }
+}
+
+// Extend-add of child number `ci` of every front of the level: U_c (lower) is added at
+// the parent positions ea_c, into P (column inside I) or U (both in B).  One launch per
+// child index keeps the accumulation order fixed and race-free.
+template <typename Tc, typename Tp>
+__global__ void k_extend_add(const FrontDesc* __restrict__ parents, const FrontDesc* __restrict__ kids,
+                             const int* __restrict__ child_slots, int ci) {
+    const FrontDesc fp = parents[blockIdx.y];
+    if (ci >= fp.child_count) return;
+    const FrontDesc fc = kids[child_slots[fp.child_begin + ci]];
+    const Tc* U = (const Tc*)fc.U;
+    Tp* P = (Tp*)fp.P;
+    Tp* Up = (Tp*)fp.U;
+    for (int i = blockIdx.x; i < fc.b; i += gridDim.x) {
+        const int pi = fc.ea[i];
+        for (int j = threadIdx.x; j <= i; j += blockDim.x) {
+            const int pj = fc.ea[j];
+            const Tp v = (Tp)U[(int64_t)i * fc.ldu + j];
+            const int r = max(pi, pj), c = min(pi, pj);
+            if (c < fp.s) P[(int64_t)r * fp.ldp + c] += v;
+            else Up[(int64_t)(r - fp.s) * fp.ldu + (c - fp.s)] += v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// SIMT batched GEMM:  C = beta*C + alpha * A B^T, 64x64 tiles, 256 threads, 4x4 per thread.
+// ---------------------------------------------------------------------------------
+constexpr int SB = 64;     // tile edge
+template <typename T> struct SimtK { static constexpr int BK = 16; };
+template <> struct SimtK<float> { static constexpr int BK = 32; };
+
+__device__ __forceinline__ int find_task(const GemmTask* tasks, int ntask, int g) {
+    int lo = 0, hi = ntask - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tasks[mid].tile_begin <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void decode_tile(const GemmTask& tk, int local, int& tm, int& tn) {
+    if (tk.lower) {
+        int r = (int)((sqrtf(8.0f * local + 1.0f) - 1.0f) * 0.5f);
+        while ((r + 1) * (r + 2) / 2 <= local) ++r;
+        while (r * (r + 1) / 2 > local) --r;
+        tm = r;
+        tn = local - r * (r + 1) / 2;
+    } else {
+        tm = local / tk.tiles_n;
+        tn = local % tk.tiles_n;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm_simt(const GemmTask* __restrict__ tasks, int ntask, T alpha) {
+    constexpr int BK = SimtK<T>::BK;
+    __shared__ T As[BK][SB + 1];
+    __shared__ T Bs[BK][SB + 1];
+    const int ti = find_task(tasks, ntask, blockIdx.x);
+    const GemmTask tk = tasks[ti];
+    int tm, tn;
+    decode_tile(tk, blockIdx.x - tk.tile_begin, tm, tn);
+    const int m0 = tm * SB, n0 = tn * SB;
+    const T* A = (const T*)tk.A;
+    const T* B = (const T*)tk.B;
+    T* C = (T*)tk.C;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+    for (int k0 = 0; k0 < tk.K; k0 += BK) {
+        for (int e = threadIdx.x; e < SB * BK; e += 256) {
+            const int r = e / BK, kk = e % BK;
+            const int gk = k0 + kk;
+            const int ga = m0 + r, gb = n0 + r;
+            As[kk][r] = (ga < tk.M && gk < tk.K) ? A[(int64_t)ga * tk.lda + gk] : (T)0;
+            Bs[kk][r] = (gb < tk.N && gk < tk.K) ? B[(int64_t)gb * tk.ldb + gk] : (T)0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { a[u] = As[kk][ty + 16 * u]; b[u] = Bs[kk][tx + 16 * u]; }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int r = m0 + ty + 16 * u;
+        if (r >= tk.M) continue;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int c = n0 + tx + 16 * v;
+            if (c >= tk.N || (tk.lower && c > r)) continue;
+            T* pc = C + (int64_t)r * tk.ldc + c;
+            *pc = tk.beta ? (*pc + alpha * acc[u][v]) : alpha * acc[u][v];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Diagonal block: Cholesky of P[k:k+w, k:k+w] in shared memory, written back to P, then
+// inverted in place (lower triangular) and stored as Dinv_k (NB x NB, zero padded).
+// One CTA per front whose interface extends past k.
+// ---------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_potrf_diag(const FrontDesc* __restrict__ fronts, int k,
+                                                   int* __restrict__ err) {
+    extern __shared__ unsigned char smem_raw[];
+    T* A = (T*)smem_raw;                     // NB x (NB+1)
+    constexpr int LD = NB + 1;
+    const FrontDesc f = fronts[blockIdx.x];
+    if (f.s <= k) return;
+    const int w = min(NB, f.s - k);
+    T* P = (T*)f.P;
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+        const int r = e / w, c = e % w;
+        A[r * LD + c] = (c <= r) ? P[(int64_t)(k + r) * f.ldp + (k + c)] : (T)0;
+    }
+    __shared__ int bad;
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    for (int j = 0; j < w; ++j) {
+        if (threadIdx.x == 0) {
+            const T d = A[j * LD + j];
+            if (!(d > (T)0)) { bad = 1; A[j * LD + j] = (T)1; }
+            else A[j * LD + j] = sqrt(d);
+        }
+        __syncthreads();
+        const T djj = A[j * LD + j];
+        for (int i = j + 1 + threadIdx.x; i < w; i += blockDim.x) A[i * LD + j] /= djj;
+        __syncthreads();
+        const int rem = w - j - 1;
+        for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
+            const int i = j + 1 + e / rem, l = j + 1 + e % rem;
+            if (l <= i) A[i * LD + l] -= A[i * LD + j] * A[l * LD + j];
+        }
+        __syncthreads();
+    }
+    if (bad && threadIdx.x == 0) {
+        atomicExch(&err[ERR_NOT_SPD], 1);
+        atomicMin(&err[ERR_NOT_SPD_NODE], f.node);
+    }
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+        const int r = e / w, c = e % w;
+        if (c <= r) P[(int64_t)(k + r) * f.ldp + (k + c)] = A[r * LD + c];
+    }
+    __syncthreads();
+    // in-place inverse of the lower triangular block, columns right to left:
+    // column j of L^-1 below the diagonal is -(1/L_jj) * Linv[j+1:, j+1:] L[j+1:, j]
+    __shared__ T tmp[NB];
+    for (int j = w - 1; j >= 0; --j) {
+        const T ajj = (T)1 / A[j * LD + j];
+        for (int i = j + 1 + threadIdx.x; i < w; i += blockDim.x) {
+            T s = 0;
+            for (int l = j + 1; l <= i; ++l) s += A[i * LD + l] * A[l * LD + j];
+            tmp[i] = -s * ajj;
+        }
+        __syncthreads();
+        for (int i = j + 1 + threadIdx.x; i < w; i += blockDim.x) A[i * LD + j] = tmp[i];
+        if (threadIdx.x == 0) A[j * LD + j] = ajj;
+        __syncthreads();
+    }
+    T* D = (T*)f.Dinv + (int64_t)(k / NB) * NB * NB;
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int r = e / NB, c = e % NB;
+        D[e] = (r < w && c <= r) ? A[r * LD + c] : (T)0;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Panel solve in place: rows P[k+w:N, k:k+w] <- rows * Dinv_k^T (Dinv_k lower triangular).
+// Each CTA owns 32 full-width rows, so reading and overwriting them cannot race.
+// ---------------------------------------------------------------------------------
+constexpr int TR_ROWS = 32;
+template <typename T>
+__global__ void __launch_bounds__(256) k_trsm_simt(const FrontDesc* __restrict__ fronts, int k) {
+    extern __shared__ unsigned char smem_raw[];
+    T* D = (T*)smem_raw;                     // NB x NB
+    T* R = D + NB * NB;                      // TR_ROWS x (NB + 1)
+    constexpr int LDR = NB + 1;
+    const FrontDesc f = fronts[blockIdx.y];
+    if (f.s <= k) return;
+    const int w = min(NB, f.s - k);
+    const int r0 = k + w + blockIdx.x * TR_ROWS;
+    if (r0 >= f.N) return;
+    const int nr = min(TR_ROWS, f.N - r0);
+    const T* Dg = (const T*)f.Dinv + (int64_t)(k / NB) * NB * NB;
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) D[e] = Dg[e];
+    T* P = (T*)f.P;
+    for (int e = threadIdx.x; e < TR_ROWS * NB; e += blockDim.x) {
+        const int r = e / NB, c = e % NB;
+        R[r * LDR + c] = (r < nr && c < w) ? P[(int64_t)(r0 + r) * f.ldp + k + c] : (T)0;
+    }
+    __syncthreads();
+    // thread -> (row group of 4, column group of 4): 8 x 32 threads
+    const int rg = threadIdx.x >> 5, cg = threadIdx.x & 31;
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+    for (int l = 0; l < w; ++l) {
+        T a[4], d[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a[u] = R[(rg + 8 * u) * LDR + l];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) d[v] = D[(cg + 32 * v) * NB + l];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], d[v], acc[u][v]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int r = rg + 8 * u;
+        if (r >= nr) continue;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int c = cg + 32 * v;
+            if (c < w) P[(int64_t)(r0 + r) * f.ldp + k + c] = acc[u][v];
+        }
+    }
+}
+
+template <typename T>
+int launch_gemm_simt(const std::vector<GemmTask>& tasks, GemmTask* d_tasks, T alpha, cudaStream_t st) {
+    if (tasks.empty()) return RSD_OK;
+    RSD_CUDA_TRY(cudaMemcpyAsync(d_tasks, tasks.data(), tasks.size() * sizeof(GemmTask),
+                                 cudaMemcpyHostToDevice, st));
+    const GemmTask& last = tasks.back();
+    const int tiles_last = last.lower ? ((last.M + SB - 1) / SB) * ((last.M + SB - 1) / SB + 1) / 2
+                                      : ((last.M + SB - 1) / SB) * last.tiles_n;
+    const int total = last.tile_begin + tiles_last;
+    if (total <= 0) return RSD_OK;
+    k_gemm_simt<T><<<total, 256, 0, st>>>(d_tasks, (int)tasks.size(), alpha);
+    RSD_CUDA_TRY(cudaGetLastError());
+    return RSD_OK;
+}
+
+// Fill tile bookkeeping of a task list for tile edge `tile`; returns total tiles.
+int finalize_tasks(std::vector<GemmTask>& tasks, int tile_m, int tile_n) {
+    int total = 0;
+    for (auto& t : tasks) {
+        const int tm = (t.M + tile_m - 1) / tile_m;
+        const int tn = (t.N + tile_n - 1) / tile_n;
+        t.tiles_n = tn;
+        t.tile_begin = total;
+        total += t.lower ? tm * (tm + 1) / 2 : tm * tn;
+    }
+    return total;
+}
+
+}  // namespace
+
+int launch_assemble_fronts(Handle& h, int li, const int64_t* rowptr, const int* col,
+                           const double* val, const int* owner, const int* rank, const int* tin,
+                           const int* tout) {
+    Level& L = h.levels[li];
+    if (L.fronts.empty()) return RSD_OK;
+    RSD_CUDA_TRY(cudaMemsetAsync(L.fronts[0].P, 0, L.bytes_P, h.stream));
+    if (L.bytes_U) RSD_CUDA_TRY(cudaMemsetAsync(L.fronts[0].U, 0, L.bytes_U, h.stream));
+    dim3 grid((unsigned)std::max(1, std::min(64, (L.max_s + 7) / 8)), (unsigned)L.fronts.size());
+    if (is_fp64(L.prec))
+        k_scatter_K<double><<<grid, 256, 0, h.stream>>>(L.d_fronts, rowptr, col, val, owner, rank, tin, tout);
+    else
+        k_scatter_K<float><<<grid, 256, 0, h.stream>>>(L.d_fronts, rowptr, col, val, owner, rank, tin, tout);
+    RSD_CUDA_TRY(cudaGetLastError());
+    return RSD_OK;
+}
+
+int launch_extend_add(Handle& h, int li) {
+    if (li + 1 >= (int)h.levels.size()) return RSD_OK;
+    Level& Lp = h.levels[li];
+    Level& Lc = h.levels[li + 1];
+    if (Lp.fronts.empty() || Lc.fronts.empty()) return RSD_OK;
+    const bool p64 = is_fp64(Lp.prec), c64 = is_fp64(Lc.prec);
+    dim3 grid((unsigned)std::max(1, std::min(256, Lc.max_b)), (unsigned)Lp.fronts.size());
+    for (int ci = 0; ci < Lp.max_children; ++ci) {
+        if (p64 && c64) k_extend_add<double, double><<<grid, 256, 0, h.stream>>>(Lp.d_fronts, Lc.d_fronts, Lp.d_child_slots, ci);
+        else if (p64 && !c64) k_extend_add<float, double><<<grid, 256, 0, h.stream>>>(Lp.d_fronts, Lc.d_fronts, Lp.d_child_slots, ci);
+        else if (!p64 && c64) k_extend_add<double, float><<<grid, 256, 0, h.stream>>>(Lp.d_fronts, Lc.d_fronts, Lp.d_child_slots, ci);
+        else k_extend_add<float, float><<<grid, 256, 0, h.stream>>>(Lp.d_fronts, Lc.d_fronts, Lp.d_child_slots, ci);
+        RSD_CUDA_TRY(cudaGetLastError());
+    }
+    return RSD_OK;
+}
+
+// Partial Cholesky of every front of level li (steps (a)-(d) above).
+int run_factor_level(Handle& h, int li) {
+    Level& L = h.levels[li];
+    if (L.fronts.empty()) return RSD_OK;
+    const bool f64 = is_fp64(L.prec);
+    const bool tc = L.prec == RSD_PREC_TF32;
+    const size_t es = f64 ? 8 : 4;
+    // task buffer for this level: one slot per front per launch kind
+    GemmTask* d_tasks = nullptr;
+    RSD_CUDA_TRY(cudaMallocAsync((void**)&d_tasks, sizeof(GemmTask) * L.fronts.size() * 2 + 64, h.stream));
+    const size_t potrf_smem = (size_t)NB * (NB + 1) * es;
+    const size_t trsm_smem = (size_t)NB * NB * es + (size_t)TR_ROWS * (NB + 1) * es;
+    if (f64) {
+        RSD_CUDA_TRY(cudaFuncSetAttribute(k_potrf_diag<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)potrf_smem));
+        RSD_CUDA_TRY(cudaFuncSetAttribute(k_trsm_simt<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem));
+    } else {
+        RSD_CUDA_TRY(cudaFuncSetAttribute(k_potrf_diag<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)potrf_smem));
+        RSD_CUDA_TRY(cudaFuncSetAttribute(k_trsm_simt<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem));
+    }
+    std::vector<GemmTask> tasks;
+    int rc = RSD_OK;
+    for (int k = 0; k < L.max_s && rc == RSD_OK; k += NB) {
+        // (a) panel update from all previous panels
+        if (k > 0) {
+            tasks.clear();
+            for (auto& f : L.fronts) {
+                if (f.s <= k) continue;
+                const int w = std::min(NB, f.s - k);
+                GemmTask t{};
+                t.A = (const char*)f.P + ((int64_t)k * f.ldp) * es;
+                t.B = t.A;
+                t.C = (char*)f.P + ((int64_t)k * f.ldp + k) * es;
+                t.lda = t.ldb = t.ldc = f.ldp;
+                t.M = f.N - k; t.N = w; t.K = k;
+                t.lower = 0; t.beta = 1;
+                t.map_a = t.map_b = f.node;   // slot resolved by the tensor-core path
+                t.a_r0 = k; t.a_c0 = 0; t.b_r0 = k; t.b_c0 = 0;
+                tasks.push_back(t);
+            }
+            if (tc) rc = gemm_tc_launch(h, li, tasks, 0, h.stream);
+            else {
+                finalize_tasks(tasks, SB, SB);
+                rc = f64 ? launch_gemm_simt<double>(tasks, d_tasks, -1.0, h.stream)
+                         : launch_gemm_simt<float>(tasks, d_tasks, -1.0f, h.stream);
+            }
+            if (rc != RSD_OK) break;
+        }
+        // (b) diagonal block factor + inverse
+        if (f64) k_potrf_diag<double><<<(unsigned)L.fronts.size(), 256, potrf_smem, h.stream>>>(L.d_fronts, k, h.d_err);
+        else k_potrf_diag<float><<<(unsigned)L.fronts.size(), 256, potrf_smem, h.stream>>>(L.d_fronts, k, h.d_err);
+        if (cudaGetLastError() != cudaSuccess) { rc = RSD_ERR_CUDA; break; }
+        // (c) panel solve below the diagonal block
+        if (tc) {
+            tasks.clear();
+            for (auto& f : L.fronts) {
+                if (f.s <= k) continue;
+                const int w = std::min(NB, f.s - k);
+                if (f.N - k - w <= 0) continue;
+                GemmTask t{};
+                t.A = (const char*)f.P + ((int64_t)(k + w) * f.ldp + k) * es;
+                t.B = (const char*)f.Dinv + (int64_t)(k / NB) * NB * NB * es;
+                t.C = (char*)t.A;
+                t.lda = t.ldc = f.ldp; t.ldb = NB;
+                t.M = f.N - k - w; t.N = w; t.K = w;
+                t.lower = 0; t.beta = 0;
+                t.map_a = f.node; t.map_b = f.node;
+                t.a_r0 = k + w; t.a_c0 = k; t.b_r0 = (k / NB) * NB; t.b_c0 = 0;
+                tasks.push_back(t);
+            }
+            rc = gemm_tc_launch(h, li, tasks, 1, h.stream);
+            if (rc != RSD_OK) break;
+        } else {
+            const int rows = L.max_N;   // upper bound on rows below the diagonal
+            dim3 grid((unsigned)std::max(1, (rows - k + TR_ROWS - 1) / TR_ROWS), (unsigned)L.fronts.size());
+            if (f64) k_trsm_simt<double><<<grid, 256, trsm_smem, h.stream>>>(L.d_fronts, k);
+            else k_trsm_simt<float><<<grid, 256, trsm_smem, h.stream>>>(L.d_fronts, k);
+            if (cudaGetLastError() != cudaSuccess) { rc = RSD_ERR_CUDA; break; }
+        }
+    }
+    // (d) Schur contribution to the ancestors: U -= X X^T
+    if (rc == RSD_OK) {
+        tasks.clear();
+        for (auto& f : L.fronts) {
+            if (f.b == 0 || f.s == 0) continue;
+            GemmTask t{};
+            t.A = (const char*)f.P + ((int64_t)f.s * f.ldp) * es;
+            t.B = t.A;
+            t.C = f.U;
+            t.lda = t.ldb = f.ldp; t.ldc = f.ldu;
+            t.M = f.b; t.N = f.b; t.K = f.s;
+            t.lower = 1; t.beta = 1;
+            t.map_a = t.map_b = f.node;
+            t.a_r0 = f.s; t.a_c0 = 0; t.b_r0 = f.s; t.b_c0 = 0;
+            tasks.push_back(t);
+        }
+        if (!tasks.empty()) {
+            if (tc) rc = gemm_tc_launch(h, li, tasks, 2, h.stream);
+            else {
+                finalize_tasks(tasks, SB, SB);
+                rc = f64 ? launch_gemm_simt<double>(tasks, d_tasks, -1.0, h.stream)
+                         : launch_gemm_simt<float>(tasks, d_tasks, -1.0f, h.stream);
+            }
+        }
+    }
+    cudaFreeAsync(d_tasks, h.stream);
+    return rc;
+}
+
+}  // namespace rsd

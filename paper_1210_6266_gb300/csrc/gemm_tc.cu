@@ -1,0 +1,384 @@
+// Tensor-core (tcgen05, TF32 in / FP32 accumulate) batched GEMM for the partial Cholesky
+// of the fronts: the panel update (a), the panel solve by the inverted diagonal block (c)
+// and the Schur contribution U -= X X^T (d) (see factor.cu).
+//
+//   C[M x N] = beta * C + alpha * A[M x K] * B[N x K]^T      (row-major, FP32 storage)
+//
+// One CTA computes one BM x BN tile:
+//   warp 0      : TMA producer.  A and B tiles (32 FP32 = 128 B of K per row) are copied by
+//                 cp.async.bulk.tensor with 128-byte swizzle into a STAGES-deep ring.
+//   warp 1      : allocates the TMEM accumulator (BN columns x 128 lanes) and, from one
+//                 thread, issues tcgen05.mma.kind::tf32 (M = 128, N = BN, K = 8) for each
+//                 K slice; tcgen05.commit frees ring slots and finally signals the epilogue.
+//   warps 2..5  : epilogue.  tcgen05.ld moves each accumulator row into registers (TMEM
+//                 lane = tile row), then C is read-modified-written with 16-byte accesses.
+// Operands stay in the front matrices: one 2-D tensor map per front covers its [L; X]
+// panel (N rows x s columns) and one covers its stacked inverted diagonal blocks; TMA's
+// zero fill handles ragged edges.  Every mbarrier wait is bounded; on timeout the CTA
+// raises ERR_TIMEOUT, drains, frees its TMEM and exits.
+#include <cuda.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "rsd_internal.cuh"
+
+namespace rsd {
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 32;                       // FP32 elements per 128-byte swizzle row
+constexpr int STAGES = 4;
+constexpr int TC_THREADS = 192;
+constexpr long long TC_WAIT_CYCLES = 2000000000LL;   // ~1 s
+
+struct TcTile { int task, tm, tn, pad; };
+
+struct TcTask {               // device view of one GEMM task
+    float* C;
+    int ldc, M, N, K;
+    int lower, beta;
+    int map_a, map_b;
+    int a_r0, a_c0, b_r0, b_c0;
+    float alpha;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait; returns false (and raises the error flag) on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try(bar, parity)) {
+        if (clock64() - t0 > TC_WAIT_CYCLES || *(volatile int*)&err[ERR_TIMEOUT]) {
+            atomicExch(&err[ERR_TIMEOUT], 1);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst), "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);          // start address
+    d |= (uint64_t)0 << 16;                           // leading byte offset (unused, swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;                 // stride byte offset
+    d |= (uint64_t)1 << 46;                           // descriptor version
+    d |= (uint64_t)2 << 61;                           // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = bn.
+__host__ __device__ constexpr uint32_t idesc_tf32(int bn) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <int BN>
+struct Smem {
+    static constexpr int A_BYTES = BM * BK * 4;
+    static constexpr int B_BYTES = BN * BK * 4;
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int TOTAL = STAGES * STAGE + 1024 /*align*/ + 256 /*barriers*/;
+};
+
+template <int BN>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+k_gemm_tc(const TcTask* __restrict__ tasks, const TcTile* __restrict__ tiles,
+          const CUtensorMap* __restrict__ maps, int* __restrict__ err) {
+    extern __shared__ unsigned char smem_raw[];
+    using S = Smem<BN>;
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023) & ~1023u;
+    unsigned char* sbase = smem_raw + (base - raw);
+    const uint32_t bar_full = base + STAGES * S::STAGE;            // STAGES x 8 B
+    const uint32_t bar_empty = bar_full + 8 * STAGES;
+    const uint32_t bar_done = bar_empty + 8 * STAGES;
+    uint32_t* tmem_slot = (uint32_t*)(sbase + STAGES * S::STAGE + 24 * STAGES + 16);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    const TcTile tl = tiles[blockIdx.x];
+    const TcTask tk = tasks[tl.task];
+    const int m0 = tl.tm * BM, n0 = tl.tn * BN;
+    const int nk = (tk.K + BK - 1) / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(bar_full + 8 * s, 1);
+            mbar_init(bar_empty + 8 * s, 1);
+        }
+        mbar_init(bar_done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(tmem_slot)), "r"(BN) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            const CUtensorMap* ma = maps + tk.map_a;
+            const CUtensorMap* mb = maps + tk.map_b;
+            for (int kb = 0; kb < nk; ++kb) {
+                const int s = kb % STAGES;
+                const uint32_t ph = (kb / STAGES) & 1;
+                if (!mbar_wait(bar_empty + 8 * s, ph ^ 1, err)) break;
+                const uint32_t sa = base + s * S::STAGE;
+                const uint32_t sb = sa + S::A_BYTES;
+                mbar_expect_tx(bar_full + 8 * s, S::STAGE);
+                tma_load_2d(sa, ma, tk.a_c0 + kb * BK, tk.a_r0 + m0, bar_full + 8 * s);
+#pragma unroll
+                for (int h = 0; h < BN / 128; ++h)
+                    tma_load_2d(sb + h * 128 * BK * 4, mb, tk.b_c0 + kb * BK, tk.b_r0 + n0 + h * 128, bar_full + 8 * s);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_tf32(BN);
+            bool ok = true;
+            for (int kb = 0; kb < nk && ok; ++kb) {
+                const int s = kb % STAGES;
+                const uint32_t ph = (kb / STAGES) & 1;
+                ok = mbar_wait(bar_full + 8 * s, ph, err);
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t sa = base + s * S::STAGE;
+                const uint32_t sb = sa + S::A_BYTES;
+#pragma unroll
+                for (int k = 0; k < BK / 8; ++k)
+                    mma_tf32(tmem, smem_desc(sa + k * 32), smem_desc(sb + k * 32), idesc, (kb | k) != 0);
+                mma_commit(bar_empty + 8 * s);
+            }
+            mma_commit(bar_done);
+        }
+    } else {
+        // epilogue: warp (2..5) reads TMEM lanes 32*(warp%4) .. +31
+        const int quarter = warp & 3;
+        const int row = quarter * 32 + lane;
+        const bool ok = mbar_wait(bar_done, 0, err);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int gr = m0 + row;
+        float* crow = tk.C + (int64_t)gr * tk.ldc;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+            uint32_t r[32];
+            tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + c0, r);
+            if (!ok || gr >= tk.M) continue;
+            const int gc0 = n0 + c0;
+            if (gc0 >= tk.N) continue;
+            if (tk.lower && gc0 > gr) continue;
+            if (gc0 + 32 <= tk.N && (!tk.lower || gc0 + 31 <= gr)) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    float4* p = (float4*)(crow + gc0 + 4 * q);
+                    float4 o = tk.beta ? *p : make_float4(0.f, 0.f, 0.f, 0.f);
+                    o.x += tk.alpha * __uint_as_float(r[4 * q + 0]);
+                    o.y += tk.alpha * __uint_as_float(r[4 * q + 1]);
+                    o.z += tk.alpha * __uint_as_float(r[4 * q + 2]);
+                    o.w += tk.alpha * __uint_as_float(r[4 * q + 3]);
+                    *p = o;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const int gc = gc0 + q;
+                    if (gc < tk.N && (!tk.lower || gc <= gr)) {
+                        float* p = crow + gc;
+                        *p = (tk.beta ? *p : 0.f) + tk.alpha * __uint_as_float(r[q]);
+                    }
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    }
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+    }
+}
+
+// ---- host side ---------------------------------------------------------------------
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn get_encode() {
+    static EncodeFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeFn)p;
+    }
+    return fn;
+}
+
+int encode_2d(CUtensorMap* m, void* base, int cols, int rows, int ld_elems) {
+    EncodeFn enc = get_encode();
+    if (!enc) { set_last_error("cuTensorMapEncodeTiled unavailable"); return RSD_ERR_CUDA; }
+    cuuint64_t dims[2] = {(cuuint64_t)std::max(cols, 1), (cuuint64_t)std::max(rows, 1)};
+    cuuint64_t strides[1] = {(cuuint64_t)ld_elems * 4};
+    cuuint32_t box[2] = {(cuuint32_t)BK, 128};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) { set_last_error("cuTensorMapEncodeTiled failed: " + std::to_string((int)r)); return RSD_ERR_CUDA; }
+    return RSD_OK;
+}
+
+struct TcState {
+    CUtensorMap* d_maps = nullptr;      // 2 per tree node: [L; X] panel, inverted diagonal blocks
+    TcTask* d_tasks = nullptr;
+    TcTile* d_tiles = nullptr;
+    size_t cap_tasks = 0, cap_tiles = 0;
+    bool attr_set = false;
+};
+
+std::vector<TcState*>& states() { static std::vector<TcState*> v; return v; }
+
+TcState* state_of(Handle& h) { return (TcState*)h.tc_state; }
+
+}  // namespace
+
+int gemm_tc_prepare(Handle& h) {
+    bool any = false;
+    for (auto& L : h.levels) any |= L.prec == RSD_PREC_TF32;
+    if (!any) return RSD_OK;
+    auto* st = new TcState();
+    h.tc_state = st;
+    std::vector<CUtensorMap> maps(2 * (size_t)h.n_nodes);
+    std::memset(maps.data(), 0, maps.size() * sizeof(CUtensorMap));
+    for (auto& L : h.levels) {
+        if (L.prec != RSD_PREC_TF32) continue;
+        for (auto& f : L.fronts) {
+            RSD_TRY(encode_2d(&maps[2 * (size_t)f.node], f.P, f.s, f.N, f.ldp));
+            RSD_TRY(encode_2d(&maps[2 * (size_t)f.node + 1], f.Dinv, NB, std::max(1, f.nd) * NB, NB));
+        }
+    }
+    RSD_CUDA_TRY(cudaMalloc((void**)&st->d_maps, maps.size() * sizeof(CUtensorMap)));
+    RSD_CUDA_TRY(cudaMemcpy(st->d_maps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
+    return RSD_OK;
+}
+
+void gemm_tc_release(Handle& h) {
+    TcState* st = state_of(h);
+    if (!st) return;
+    cudaFree(st->d_maps);
+    cudaFree(st->d_tasks);
+    cudaFree(st->d_tiles);
+    delete st;
+    h.tc_state = nullptr;
+}
+
+// kind 0: panel update, 1: panel solve (B = inverted diagonal block), 2: U -= X X^T.
+int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, int kind, cudaStream_t stream) {
+    TcState* st = state_of(h);
+    if (!st || tasks.empty()) return st ? RSD_OK : RSD_ERR_ARG;
+    const int bn = kind == 2 ? 256 : 128;
+    std::vector<TcTask> tt(tasks.size());
+    std::vector<TcTile> tl;
+    for (size_t i = 0; i < tasks.size(); ++i) {
+        const GemmTask& g = tasks[i];
+        TcTask& t = tt[i];
+        t.C = (float*)g.C;
+        t.ldc = g.ldc; t.M = g.M; t.N = g.N; t.K = g.K;
+        t.lower = g.lower; t.beta = g.beta;
+        t.map_a = 2 * g.map_a;
+        t.map_b = 2 * g.map_b + (kind == 1 ? 1 : 0);
+        t.a_r0 = g.a_r0; t.a_c0 = g.a_c0; t.b_r0 = g.b_r0; t.b_c0 = g.b_c0;
+        t.alpha = kind == 1 ? 1.0f : -1.0f;
+        const int tm = (g.M + BM - 1) / BM, tn = (g.N + bn - 1) / bn;
+        for (int a = 0; a < tm; ++a)
+            for (int b = 0; b < tn; ++b) {
+                if (g.lower && b * bn > a * BM + BM - 1) continue;
+                tl.push_back({(int)i, a, b, 0});
+            }
+    }
+    if (tl.empty()) return RSD_OK;
+    if (tt.size() > st->cap_tasks) {
+        cudaFreeAsync(st->d_tasks, stream);
+        st->cap_tasks = std::max(tt.size(), 2 * st->cap_tasks);
+        RSD_CUDA_TRY(cudaMallocAsync((void**)&st->d_tasks, st->cap_tasks * sizeof(TcTask), stream));
+    }
+    if (tl.size() > st->cap_tiles) {
+        cudaFreeAsync(st->d_tiles, stream);
+        st->cap_tiles = std::max(tl.size(), 2 * st->cap_tiles);
+        RSD_CUDA_TRY(cudaMallocAsync((void**)&st->d_tiles, st->cap_tiles * sizeof(TcTile), stream));
+    }
+    RSD_CUDA_TRY(cudaMemcpyAsync(st->d_tasks, tt.data(), tt.size() * sizeof(TcTask), cudaMemcpyHostToDevice, stream));
+    RSD_CUDA_TRY(cudaMemcpyAsync(st->d_tiles, tl.data(), tl.size() * sizeof(TcTile), cudaMemcpyHostToDevice, stream));
+    if (!st->attr_set) {
+        RSD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<128>::TOTAL));
+        RSD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<256>::TOTAL));
+        st->attr_set = true;
+    }
+    if (bn == 128)
+        k_gemm_tc<128><<<(unsigned)tl.size(), TC_THREADS, Smem<128>::TOTAL, stream>>>(st->d_tasks, st->d_tiles, st->d_maps, h.d_err);
+    else
+        k_gemm_tc<256><<<(unsigned)tl.size(), TC_THREADS, Smem<256>::TOTAL, stream>>>(st->d_tasks, st->d_tiles, st->d_maps, h.d_err);
+    RSD_CUDA_TRY(cudaGetLastError());
+    return RSD_OK;
+}
+
+}  // namespace rsd

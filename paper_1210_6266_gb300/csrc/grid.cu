@@ -1,0 +1,161 @@
+// Structured-grid FEM problems: assembly of -div(kappa grad u) with trilinear hexahedra on
+// the unit cube, the lumped load vector, and the octree decomposition of Sec. 2 (binary
+// halving of a strip there; mid-plane octree splits here, as the paper's conclusions
+// propose for 3-D).  Row-parallel kernels: each thread builds one CSR row by gathering the
+// (up to 8) elements around its node, so no atomics and a deterministic result.
+#include "rsd_internal.cuh"
+
+namespace rsd {
+namespace {
+
+// 1-D linear-element matrices on the unit interval: stiffness [[1,-1],[-1,1]] and mass
+// [[1/3,1/6],[1/6,1/3]].  The trilinear stiffness on the unit cube is the sum of the three
+// tensor products with the stiffness factor in one direction.
+__device__ __forceinline__ double k1(int a, int b) { return a == b ? 1.0 : -1.0; }
+__device__ __forceinline__ double m1(int a, int b) { return a == b ? (1.0 / 3.0) : (1.0 / 6.0); }
+
+__device__ __forceinline__ double khat(int a, int b) {
+    int ax = a & 1, ay = (a >> 1) & 1, az = a >> 2;
+    int bx = b & 1, by = (b >> 1) & 1, bz = b >> 2;
+    return k1(ax, bx) * m1(ay, by) * m1(az, bz) + m1(ax, bx) * k1(ay, by) * m1(az, bz) +
+           m1(ax, bx) * m1(ay, by) * k1(az, bz);
+}
+
+__device__ __forceinline__ int cnt1(int v, int m) {   // valid offsets of coordinate v in 1..m
+    return 3 - (v == 1) - (v == m);
+}
+
+__device__ __forceinline__ int64_t prefix1(int v, int m) {   // sum of cnt1 over 1..v-1
+    if (v <= 1) return 0;
+    return 2 + 3 * (int64_t)(v - 2);
+}
+
+__global__ void k_grid_assemble(int n, const double* __restrict__ kappa, int64_t* rowptr,
+                                int* col, double* val) {
+    const int m = n - 2;
+    const int64_t ndof = (int64_t)m * m * m;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= ndof) return;
+    const int x = (int)(i % m) + 1, y = (int)((i / m) % m) + 1, z = (int)(i / ((int64_t)m * m)) + 1;
+    const int64_t C = (m >= 2) ? 3 * (int64_t)m - 2 : 1;
+    const int cx = m >= 2 ? cnt1(x, m) : 1, cy = m >= 2 ? cnt1(y, m) : 1, cz = m >= 2 ? cnt1(z, m) : 1;
+    int64_t start = prefix1(z, m) * C * C + cz * (prefix1(y, m) * C + cy * prefix1(x, m));
+    if (m < 2) start = 0;
+    rowptr[i] = start;
+    if (i == ndof - 1) rowptr[ndof] = C * C * C;
+    const double h = 1.0 / (n - 1);
+    const int ne = n - 1;
+    int64_t k = start;
+    for (int dz = -1; dz <= 1; ++dz) {
+        const int zj = z + dz;
+        if (zj < 1 || zj > m) continue;
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int yj = y + dy;
+            if (yj < 1 || yj > m) continue;
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int xj = x + dx;
+                if (xj < 1 || xj > m) continue;
+                double v = 0.0;
+                // elements with origin (x-1+ax, y-1+ay, z-1+az)
+                for (int az = 0; az < 2; ++az) {
+                    const int lzi = 1 - az, lzj = lzi + dz;
+                    if (lzj < 0 || lzj > 1) continue;
+                    for (int ay = 0; ay < 2; ++ay) {
+                        const int lyi = 1 - ay, lyj = lyi + dy;
+                        if (lyj < 0 || lyj > 1) continue;
+                        for (int ax = 0; ax < 2; ++ax) {
+                            const int lxi = 1 - ax, lxj = lxi + dx;
+                            if (lxj < 0 || lxj > 1) continue;
+                            const int64_t e = (x - 1 + ax) + (int64_t)ne * ((y - 1 + ay) + (int64_t)ne * (z - 1 + az));
+                            v += kappa[e] * khat(lxi + 2 * lyi + 4 * lzi, lxj + 2 * lyj + 4 * lzj);
+                        }
+                    }
+                }
+                col[k] = (xj - 1) + m * ((yj - 1) + m * (zj - 1));
+                val[k] = h * v;
+                ++k;
+            }
+        }
+    }
+}
+
+__global__ void k_grid_load(int64_t ndof, double h3, const double* __restrict__ f, double* b) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < ndof) b[i] = h3 * f[i];
+}
+
+__global__ void k_grid_partition(int n, int depth, int* owner) {
+    const int m = n - 2;
+    const int64_t ndof = (int64_t)m * m * m;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= ndof) return;
+    int p[3] = {(int)(i % m) + 1, (int)((i / m) % m) + 1, (int)(i / ((int64_t)m * m)) + 1};
+    int lo[3] = {0, 0, 0}, hi[3] = {n - 1, n - 1, n - 1};
+    int node = 0;
+    for (int level = 0; level < depth; ++level) {
+        int mid[3];
+        bool on_plane = false;
+        for (int d = 0; d < 3; ++d) {
+            mid[d] = lo[d] + (hi[d] - lo[d]) / 2;
+            on_plane |= (p[d] == mid[d]);
+        }
+        if (on_plane) { owner[i] = node; return; }
+        int c = 0;
+        for (int d = 0; d < 3; ++d) {
+            if (p[d] > mid[d]) { c |= 1 << d; lo[d] = mid[d]; } else { hi[d] = mid[d]; }
+        }
+        node = 8 * node + 1 + c;
+    }
+    owner[i] = node;
+}
+
+}  // namespace
+}  // namespace rsd
+
+using namespace rsd;
+
+extern "C" int rsd_grid_sizes(int32_t n, int64_t* n_dof, int64_t* nnz) {
+    if (n < 3 || !n_dof || !nnz) return RSD_ERR_ARG;
+    const int64_t m = n - 2;
+    if (m * m * m > INT32_MAX) return RSD_ERR_ARG;
+    *n_dof = m * m * m;
+    const int64_t C = m >= 2 ? 3 * m - 2 : 1;
+    *nnz = C * C * C;
+    return RSD_OK;
+}
+
+extern "C" int rsd_grid_assemble(int32_t n, const double* kappa, int64_t* rowptr, int32_t* col,
+                                 double* val, void* stream) {
+    int64_t ndof, nnz;
+    RSD_TRY(rsd_grid_sizes(n, &ndof, &nnz));
+    if (!kappa || !rowptr || !col || !val) return RSD_ERR_ARG;
+    const int T = 256;
+    k_grid_assemble<<<(unsigned)((ndof + T - 1) / T), T, 0, (cudaStream_t)stream>>>(n, kappa, rowptr, col, val);
+    RSD_CUDA_TRY(cudaGetLastError());
+    return RSD_OK;
+}
+
+extern "C" int rsd_grid_load(int32_t n, const double* f, double* b, void* stream) {
+    int64_t ndof, nnz;
+    RSD_TRY(rsd_grid_sizes(n, &ndof, &nnz));
+    if (!f || !b) return RSD_ERR_ARG;
+    const double h = 1.0 / (n - 1);
+    const int T = 256;
+    k_grid_load<<<(unsigned)((ndof + T - 1) / T), T, 0, (cudaStream_t)stream>>>(ndof, h * h * h, f, b);
+    RSD_CUDA_TRY(cudaGetLastError());
+    return RSD_OK;
+}
+
+extern "C" int rsd_grid_partition(int32_t n, int32_t depth, int32_t* dof_node, int32_t* parent,
+                                  void* stream) {
+    int64_t ndof, nnz;
+    RSD_TRY(rsd_grid_sizes(n, &ndof, &nnz));
+    if (depth < 0 || depth > 6 || !dof_node || !parent) return RSD_ERR_ARG;
+    int64_t n_nodes = 0, w = 1;
+    for (int d = 0; d <= depth; ++d) { n_nodes += w; w *= 8; }
+    for (int64_t t = 0; t < n_nodes; ++t) parent[t] = t == 0 ? -1 : (int32_t)((t - 1) / 8);
+    const int T = 256;
+    k_grid_partition<<<(unsigned)((ndof + T - 1) / T), T, 0, (cudaStream_t)stream>>>(n, depth, dof_node);
+    RSD_CUDA_TRY(cudaGetLastError());
+    return RSD_OK;
+}

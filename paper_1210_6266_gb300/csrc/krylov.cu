@@ -1,0 +1,184 @@
+// Outer Krylov solve: preconditioned CG in FP64 with the RSD preconditioner (the paper
+// wraps RSD in GMRES on K u = f, zero initial guess, relative 2-norm stopping test,
+// Sec. 3 and Sec. 4; K and M are SPD here, so CG is the short-recurrence choice).
+// Dot products use a fixed grid and a fixed-order second pass, so results are
+// bitwise reproducible run to run.  Step lengths stay on the device.
+#include <cmath>
+
+#include "rsd_internal.cuh"
+
+namespace rsd {
+namespace {
+
+constexpr int RT = 256;          // threads per block for vector kernels
+constexpr int RED_BLOCKS = 1024; // fixed first-pass grid of the reductions
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum; result valid in thread 0.
+__device__ double block_sum(double v) {
+    __shared__ double s[RT / 32];
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0;
+    if (threadIdx.x < 32) {
+        t = threadIdx.x < RT / 32 ? s[threadIdx.x] : 0.0;
+        t = warp_sum(t);
+    }
+    __syncthreads();
+    return t;
+}
+
+// y = K x, four lanes per row.
+__global__ void k_spmv(int n, const int64_t* __restrict__ rowptr, const int* __restrict__ col,
+                       const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ y) {
+    const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t row = gt >> 2;
+    const int sub = threadIdx.x & 3;
+    double s = 0;
+    if (row < n) {
+        for (int64_t k = rowptr[row] + sub; k < rowptr[row + 1]; k += 4) s += val[k] * __ldg(x + col[k]);
+    }
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    if (row < n && sub == 0) y[row] = s;
+}
+
+__global__ void k_dot_partial(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+                              double* __restrict__ partial) {
+    double s = 0;
+    for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) s += a[i] * b[i];
+    s = block_sum(s);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void k_reduce_final(const double* __restrict__ partial, int np, double* __restrict__ out) {
+    double s = 0;
+    for (int i = threadIdx.x; i < np; i += RT) s += partial[i];
+    s = block_sum(s);
+    if (threadIdx.x == 0) *out = s;
+}
+
+// alpha = rz / pq;  u += alpha p;  r -= alpha q;  partial sums of r.r
+__global__ void k_cg_update(int64_t n, const double* __restrict__ scal, int rz_slot, double* __restrict__ u,
+                            double* __restrict__ r, const double* __restrict__ p, const double* __restrict__ q,
+                            double* __restrict__ partial) {
+    const double alpha = scal[rz_slot] / scal[1];
+    double s = 0;
+    for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) {
+        u[i] += alpha * p[i];
+        const double ri = r[i] - alpha * q[i];
+        r[i] = ri;
+        s += ri * ri;
+    }
+    s = block_sum(s);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// beta = rz_new / rz_old;  p = z + beta p
+__global__ void k_cg_direction(int64_t n, const double* __restrict__ scal, int new_slot, int old_slot,
+                               const double* __restrict__ z, double* __restrict__ p) {
+    const double beta = scal[new_slot] / scal[old_slot];
+    for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT)
+        p[i] = z[i] + beta * p[i];
+}
+
+__global__ void k_residual(int n, const int64_t* __restrict__ rowptr, const int* __restrict__ col,
+                           const double* __restrict__ val, const double* __restrict__ x,
+                           const double* __restrict__ f, double* __restrict__ r) {
+    const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t row = gt >> 2;
+    const int sub = threadIdx.x & 3;
+    double s = 0;
+    if (row < n)
+        for (int64_t k = rowptr[row] + sub; k < rowptr[row + 1]; k += 4) s += val[k] * __ldg(x + col[k]);
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    if (row < n && sub == 0) r[row] = f[row] - s;
+}
+
+int dot(Handle& h, const double* a, const double* b, int slot) {
+    k_dot_partial<<<RED_BLOCKS, RT, 0, h.stream>>>(h.n, a, b, h.d_partial);
+    k_reduce_final<<<1, RT, 0, h.stream>>>(h.d_partial, RED_BLOCKS, h.d_scal + slot);
+    RSD_CUDA_TRY(cudaGetLastError());
+    return RSD_OK;
+}
+
+int fetch(Handle& h, int slot, double* out) {
+    RSD_CUDA_TRY(cudaMemcpyAsync(h.h_scal + slot, h.d_scal + slot, sizeof(double), cudaMemcpyDeviceToHost, h.stream));
+    RSD_CUDA_TRY(cudaStreamSynchronize(h.stream));
+    *out = h.h_scal[slot];
+    return RSD_OK;
+}
+
+}  // namespace
+
+int spmv(Handle& h, const double* x, double* y) {
+    const int64_t threads = (int64_t)h.n * 4;
+    k_spmv<<<(unsigned)((threads + RT - 1) / RT), RT, 0, h.stream>>>(h.n, h.d_rowptr, h.d_col, h.d_val, x, y);
+    RSD_CUDA_TRY(cudaGetLastError());
+    return RSD_OK;
+}
+
+// Scalar slots: 0 rz (even iterations), 1 pq, 2 rr, 3 rz (odd iterations), 4 ff, 5 true rr
+int pcg(Handle& h, const double* f, double* u, double tol, rsd_stats* st) {
+    const int64_t n = h.n;
+    double* r = h.d_r;
+    double* p = h.d_p;
+    double* q = h.d_q;
+    double* z = h.d_z;
+    const int maxit = h.opt.maxit > 0 ? h.opt.maxit : 200;
+    rsd_stats local{};
+    rsd_stats* S = st ? st : &local;
+    *S = rsd_stats{};
+    RSD_CUDA_TRY(cudaMemsetAsync(u, 0, sizeof(double) * n, h.stream));
+    RSD_CUDA_TRY(cudaMemcpyAsync(r, f, sizeof(double) * n, cudaMemcpyDeviceToDevice, h.stream));
+    RSD_TRY(dot(h, f, f, 4));
+    double ff;
+    RSD_TRY(fetch(h, 4, &ff));
+    const double fnorm = std::sqrt(ff);
+    S->history[0] = 1.0;
+    if (fnorm == 0.0) { S->relres = 0; return RSD_OK; }
+    RSD_TRY(run_apply(h, r, z));
+    RSD_CUDA_TRY(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, h.stream));
+    RSD_TRY(dot(h, r, z, 0));
+    int it = 0;
+    double rel = 1.0;
+    int rc = RSD_ERR_NOCONV;
+    for (it = 1; it <= maxit; ++it) {
+        const int old_slot = (it & 1) ? 0 : 3, new_slot = (it & 1) ? 3 : 0;
+        RSD_TRY(spmv(h, p, q));
+        RSD_TRY(dot(h, p, q, 1));
+        k_cg_update<<<RED_BLOCKS, RT, 0, h.stream>>>(n, h.d_scal, old_slot, u, r, p, q, h.d_partial);
+        k_reduce_final<<<1, RT, 0, h.stream>>>(h.d_partial, RED_BLOCKS, h.d_scal + 2);
+        RSD_CUDA_TRY(cudaGetLastError());
+        double rr;
+        RSD_TRY(fetch(h, 2, &rr));
+        rel = std::sqrt(std::max(rr, 0.0)) / fnorm;
+        if (it < 64) S->history[it] = rel;
+        if (!(rel == rel)) { rc = RSD_ERR_NOT_SPD; break; }
+        if (rel <= tol) { rc = RSD_OK; break; }
+        RSD_TRY(run_apply(h, r, z));
+        RSD_TRY(dot(h, r, z, new_slot));
+        k_cg_direction<<<RED_BLOCKS, RT, 0, h.stream>>>(n, h.d_scal, new_slot, old_slot, z, p);
+        RSD_CUDA_TRY(cudaGetLastError());
+    }
+    S->iterations = std::min(it, maxit);
+    S->relres_recursive = rel;
+    // true residual in FP64
+    const int64_t threads = n * 4;
+    k_residual<<<(unsigned)((threads + RT - 1) / RT), RT, 0, h.stream>>>(h.n, h.d_rowptr, h.d_col, h.d_val, u, f, q);
+    RSD_CUDA_TRY(cudaGetLastError());
+    RSD_TRY(dot(h, q, q, 5));
+    double tr;
+    RSD_TRY(fetch(h, 5, &tr));
+    S->relres = std::sqrt(tr) / fnorm;
+    return rc;
+}
+
+}  // namespace rsd

@@ -1,0 +1,136 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "rsd.h"
+
+namespace rsd {
+
+// Diagonal block size of the blocked partial Cholesky and of the substitution sweeps.
+constexpr int NB = 128;
+
+// Device-side error flags (one int array per handle).
+enum ErrSlot { ERR_NOT_SPD = 0, ERR_TIMEOUT = 1, ERR_NOT_SPD_NODE = 2, ERR_SLOTS = 4 };
+
+#define RSD_CUDA_TRY(expr)                                           \
+    do {                                                             \
+        cudaError_t _e = (expr);                                     \
+        if (_e != cudaSuccess) {                                     \
+            rsd::set_last_error(std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+            return RSD_ERR_CUDA;                                     \
+        }                                                            \
+    } while (0)
+
+#define RSD_TRY(expr)                      \
+    do {                                   \
+        int _rc = (expr);                  \
+        if (_rc != RSD_OK) return _rc;     \
+    } while (0)
+
+void set_last_error(const std::string& msg);
+
+inline int elem_bytes(int prec) { return prec == RSD_PREC_FP64 ? 8 : 4; }
+inline bool is_fp64(int prec) { return prec == RSD_PREC_FP64; }
+
+// One tree node's dense front and factor, as the kernels see it.
+// P is row-major N x ldp with N = s + b: rows 0..s-1 hold L (lower triangle; the
+// diagonal NB x NB blocks are also kept inverted in Dinv), rows s..N-1 hold X = K_BI L^-T.
+// U is row-major b x ldu (lower triangle): the Schur contribution to the ancestors.
+struct FrontDesc {
+    int node, s, b, N;
+    int ldp, ldu, nd;          // row strides; nd = number of diagonal blocks
+    int parent_slot;           // index of the parent in the next level's front array
+    void* P;
+    void* U;
+    void* Dinv;                // nd x NB x NB, each block lower triangular (inverse of L_kk)
+    const int* I;              // global DOFs of I_t (s)
+    const int* Bd;             // global DOFs of B_t (b)
+    const int* ea;             // positions of B_t in the parent front (b)
+    void* vec;                 // apply: front vector (N entries, level accumulator type)
+    int* flag;                 // apply: progress counters [forward, backward]
+    int child_begin, child_count;   // into the level's child-slot table (previous level)
+};
+
+// Batched GEMM task: C = beta*C - A * B^T over an M x N block (row-major operands,
+// A is M x K, B is N x K).  beta is 0 or 1.  lower: C is symmetric, only tiles that
+// meet the lower triangle are computed.
+struct GemmTask {
+    const void* A;
+    const void* B;
+    void* C;
+    int lda, ldb, ldc;
+    int M, N, K;
+    int tiles_n;         // tiles along N
+    int tile_begin;      // first global tile of this task
+    int lower;
+    int beta;
+    int map_a, map_b;    // tensor-map slots (tensor-core path); -1 when unused
+    int a_r0, a_c0, b_r0, b_c0;   // operand origins inside the tensor maps
+};
+
+struct Level {
+    int depth = 0;
+    int prec = RSD_PREC_FP64;
+    std::vector<int> nodes;              // tree node ids, in slot order
+    std::vector<FrontDesc> fronts;       // host copy
+    FrontDesc* d_fronts = nullptr;       // device copy
+    int max_s = 0, max_b = 0, max_N = 0;
+    int max_children = 0;
+    // apply work lists (device): forward/backward items, (slot << 16 | block)
+    int* d_fwd_items = nullptr;
+    int n_fwd_items = 0;
+    int* d_bwd_items = nullptr;
+    int n_bwd_items = 0;
+    // child slot table (device): for slot i of this level, child_begin.. -> slots of
+    // the level below
+    int* d_child_slots = nullptr;
+    size_t bytes_P = 0, bytes_U = 0;
+};
+
+struct Handle {
+    int n = 0;
+    int n_nodes = 0;
+    cudaStream_t stream = nullptr;
+    rsd_options opt{};
+    std::vector<int> parent, depth;
+    std::vector<Level> levels;           // index 0 = root level, back() = deepest
+    std::vector<int> node_level, node_slot;
+    // host copies of the symbolic structure (introspection)
+    std::vector<int> I_off, I_dofs, B_off, B_dofs;   // CSR-like per node
+    // device buffers
+    char* arena = nullptr;
+    size_t arena_bytes = 0;
+    int* d_err = nullptr;
+    int* d_ticket = nullptr;             // per-sweep ticket counters
+    // CSR of K on the device (FP64), owned copy for the Krylov SpMV
+    int64_t nnz = 0;
+    int64_t* d_rowptr = nullptr;
+    int* d_col = nullptr;
+    double* d_val = nullptr;
+    // Krylov work vectors
+    double *d_r = nullptr, *d_p = nullptr, *d_q = nullptr, *d_z = nullptr;
+    double* d_scal = nullptr;            // device scalars
+    double* d_partial = nullptr;         // reduction partials
+    double* h_scal = nullptr;            // pinned host mirror
+    int64_t factor_elems = 0, factor_bytes = 0;
+    double setup_flops = 0;
+    int notspd_node = -1;
+    int num_sms = 148;
+    void* tc_state = nullptr;            // tensor-core GEMM state (tensor maps, task buffers)
+};
+
+// ---- kernels launched from the host orchestration -------------------------------
+int launch_assemble_fronts(Handle& h, int li, const int64_t* rowptr, const int* col,
+                           const double* val, const int* owner, const int* rank,
+                           const int* tin, const int* tout);
+int launch_extend_add(Handle& h, int li);
+int run_factor_level(Handle& h, int li);
+int run_apply(Handle& h, const double* r, double* z);
+int spmv(Handle& h, const double* x, double* y);
+
+}  // namespace rsd

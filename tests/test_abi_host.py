@@ -1,0 +1,105 @@
+"""The C ABI without a GPU: the library loads, exports every symbol include/rsd.h
+declares, and rejects bad inputs on the host before any device work."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import fem, partition
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1210_6266_gb300 import build
+    build.build()
+    from paper_1210_6266_gb300 import _lib
+    return _lib
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "rsd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rsd_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    so = lib.load()
+    names = _declared()
+    assert "rsd_setup" in names and "rsd_apply" in names and "rsd_solve" in names
+    for name in names:
+        assert hasattr(so, name), name
+    assert sorted(lib.EXPORTS) == sorted(names)
+
+
+def test_strerror_and_grid_sizes(lib):
+    so = lib.load()
+    for code in range(-7, 1):
+        assert so.rsd_strerror(code)
+    nd, nz = C.c_int64(), C.c_int64()
+    assert so.rsd_grid_sizes(129, C.byref(nd), C.byref(nz)) == 0
+    assert nd.value == 2_048_383 and nz.value == (3 * 127 - 2) ** 3
+    assert so.rsd_grid_sizes(2, C.byref(nd), C.byref(nz)) == lib.RSD_ERR_ARG
+
+
+def test_grid_nnz_matches_oracle(lib):
+    so = lib.load()
+    for n in (5, 9, 13):
+        nd, nz = C.c_int64(), C.c_int64()
+        so.rsd_grid_sizes(n, C.byref(nd), C.byref(nz))
+        A = fem.assemble(n, np.ones((n - 1) ** 3))
+        assert (nd.value, nz.value) == (A.shape[0], A.nnz)
+
+
+def _host_setup(lib, A, owner, parent):
+    so = lib.load()
+    rowptr = np.ascontiguousarray(A.indptr.astype(np.int64))
+    col = np.ascontiguousarray(A.indices.astype(np.int32))
+    val = np.ascontiguousarray(A.data.astype(np.float64))
+    own = np.ascontiguousarray(owner.astype(np.int32))
+    par = np.ascontiguousarray(parent.astype(np.int32))
+    csr = lib.rsd_csr(A.shape[0], A.nnz, rowptr.ctypes.data, col.ctypes.data, val.ctypes.data, lib.RSD_MEM_HOST)
+    tree = lib.rsd_tree(len(par), par.ctypes.data)
+    opt = lib.rsd_options(0, lib.RSD_PREC_FP64, lib.RSD_PREC_FP64, lib.RSD_PREC_FP64, 10, None)
+    out = C.c_void_p()
+    return so.rsd_setup(C.byref(csr), own.ctypes.data, C.byref(tree), C.byref(opt), C.byref(out))
+
+
+def test_partition_violation_rejected_on_host(lib):
+    n = 9
+    A = fem.assemble(n, np.ones((n - 1) ** 3)).tolil()
+    owner = partition.octree_owner(n, 1, fem.interior_coords(n))
+    parent = partition.octree_parent(1)
+    i, j = int(np.nonzero(owner == 1)[0][0]), int(np.nonzero(owner == 8)[0][-1])
+    A[i, j] = A[j, i] = -0.01
+    assert _host_setup(lib, A.tocsr(), owner, parent) == lib.RSD_ERR_PARTITION
+
+
+def test_bad_tree_and_owner_rejected_on_host(lib):
+    n = 7
+    A = fem.assemble(n, np.ones((n - 1) ** 3))
+    owner = partition.octree_owner(n, 1, fem.interior_coords(n))
+    parent = partition.octree_parent(1)
+    bad_parent = parent.copy()
+    bad_parent[3] = 5                       # parent id not smaller than the child id
+    assert _host_setup(lib, A, owner, bad_parent) == lib.RSD_ERR_ARG
+    root_parent = parent.copy()
+    root_parent[0] = 0
+    assert _host_setup(lib, A, owner, root_parent) == lib.RSD_ERR_ARG
+    bad_owner = owner.copy()
+    bad_owner[0] = 99
+    assert _host_setup(lib, A, bad_owner, parent) == lib.RSD_ERR_ARG
+
+
+def test_null_arguments(lib):
+    so = lib.load()
+    out = C.c_void_p()
+    assert so.rsd_setup(None, None, None, None, C.byref(out)) == lib.RSD_ERR_ARG
+    assert so.rsd_apply(None, None, None) == lib.RSD_ERR_ARG
+    assert so.rsd_solve(None, None, None, 1e-8, None) == lib.RSD_ERR_ARG
+    assert so.rsd_check(None) == lib.RSD_ERR_ARG
+    so.rsd_destroy(None)

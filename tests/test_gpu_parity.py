@@ -1,0 +1,163 @@
+"""CUDA path vs the CPU oracle, through the C ABI.
+
+Integer work (assembly structure, ownership, interface sets, extend-add maps) must be
+bit-exact; the FP64 path must match the oracle to 1e-10 relative; the FP32/TF32 paths
+must reach an FP64-checked relative residual of 1e-8 under FP64 PCG.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import fem, partition
+from oracle.krylov import pcg
+from oracle.rsd_exact import ExactFactor
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rsd():
+    from paper_1210_6266_gb300 import build
+    build.build()
+    import paper_1210_6266_gb300 as m
+    return m
+
+
+def _work(n, depth, lognormal, seed=41):
+    kappa = np.exp(synth.normal(seed, (n - 1) ** 3)) if lognormal else np.ones((n - 1) ** 3)
+    f = synth.uniform(seed + 1, (n - 2) ** 3)
+    return dict(n=n, depth=depth, kappa=kappa, f=f)
+
+
+_ORACLE = {}
+
+
+def _oracle(w):
+    key = (w["n"], w["depth"], float(w["kappa"][0]), float(w["f"][0]))
+    if key not in _ORACLE:
+        n, depth = w["n"], w["depth"]
+        A = fem.assemble(n, w["kappa"])
+        b = fem.load_vector(n, w["f"])
+        owner = partition.octree_owner(n, depth, fem.interior_coords(n))
+        parent = partition.octree_parent(depth)
+        sym = partition.Symbolic(A, owner, parent)
+        _ORACLE[key] = (A, b, owner, parent, sym, ExactFactor(A, sym))
+    return _ORACLE[key]
+
+
+# (n, depth, lognormal): several tiles per front, ragged tails, uneven octree splits
+CASES = [(13, 1, False), (17, 2, True), (20, 2, True), (11, 2, False), (26, 1, True), (9, 0, True)]
+
+
+@pytest.mark.parametrize("n,depth,logn", CASES)
+def test_grid_assembly_and_partition_bitexact(rsd, n, depth, logn):
+    w = _work(n, depth, logn)
+    A, b, owner, parent, sym, _ = _oracle(w)
+    prob = rsd.grid_problem(n, depth, w["kappa"], w["f"])
+    assert np.array_equal(prob["rowptr"].cpu().numpy(), A.indptr)
+    assert np.array_equal(prob["col"].cpu().numpy(), A.indices)
+    val = prob["val"].cpu().numpy()
+    assert np.abs(val - A.data).max() <= 1e-14 * np.abs(A.data).max()
+    assert np.abs(prob["b"].cpu().numpy() - b).max() <= 1e-15 * np.abs(b).max()
+    assert np.array_equal(prob["dof_node"].cpu().numpy(), owner)
+    assert np.array_equal(prob["parent"], parent)
+
+
+def _setup(rsd, prob, prec, root=None):
+    root = rsd.RSD_PREC_FP64 if root is None else root
+    return rsd.RSD.setup(prob["rowptr"], prob["col"], prob["val"], prob["dof_node"], prob["parent"],
+                         prec_leaf=prec, prec_mid=prec, prec_root=root)
+
+
+@pytest.mark.parametrize("n,depth,logn", CASES)
+def test_interface_sets_and_maps_bitexact(rsd, n, depth, logn):
+    w = _work(n, depth, logn)
+    A, b, owner, parent, sym, _ = _oracle(w)
+    prob = rsd.grid_problem(n, depth, w["kappa"], w["f"])
+    h = _setup(rsd, prob, rsd.RSD_PREC_FP64)
+    for t in range(sym.n_nodes):
+        s, bb, lv = h.front_dims(t)
+        assert (s, bb, lv) == (sym.s(t), sym.b(t), sym.depth[t])
+        assert np.array_equal(h.front_dofs(t), sym.front[t])
+        if t > 0:
+            assert np.array_equal(h.front_map(t), sym.ea[t])
+
+
+@pytest.mark.parametrize("n,depth,logn", CASES)
+def test_fp64_factors_and_apply_match_oracle(rsd, n, depth, logn):
+    w = _work(n, depth, logn)
+    A, b, owner, parent, sym, fac = _oracle(w)
+    prob = rsd.grid_problem(n, depth, w["kappa"], w["f"])
+    h = _setup(rsd, prob, rsd.RSD_PREC_FP64)
+    for t in range(sym.n_nodes):
+        s = sym.s(t)
+        F = h.front_factor(t)
+        ref = np.vstack([fac.L[t], fac.X[t]])
+        scale = max(np.abs(ref).max(), 1e-300)
+        assert np.abs(F - ref).max() <= 1e-10 * scale, t
+    r = torch.as_tensor(synth.uniform(77, A.shape[0]), device="cuda")
+    z = h.apply(r).cpu().numpy()
+    zr = fac.apply(r.cpu().numpy())
+    assert np.abs(z - zr).max() <= 1e-10 * np.abs(zr).max()
+    h.check()
+
+
+@pytest.mark.parametrize("n,depth,logn", CASES)
+def test_fp64_pcg_one_iteration(rsd, n, depth, logn):
+    w = _work(n, depth, logn)
+    A, b, owner, parent, sym, fac = _oracle(w)
+    prob = rsd.grid_problem(n, depth, w["kappa"], w["f"])
+    h = _setup(rsd, prob, rsd.RSD_PREC_FP64)
+    u, st = h.solve(prob["b"], tol=1e-10)
+    assert st["iterations"] == 1 and st["relres"] <= 1e-10
+    x, it, _ = pcg(A, b, fac.apply, 1e-10)
+    assert np.abs(u.cpu().numpy() - x).max() <= 1e-10 * np.abs(x).max()
+
+
+@pytest.mark.parametrize("prec", ["FP32", "TF32"])
+@pytest.mark.parametrize("n,depth,logn", [(17, 2, True), (20, 2, True), (26, 1, True)])
+def test_low_precision_factors_reach_fp64_residual(rsd, prec, n, depth, logn):
+    w = _work(n, depth, logn)
+    A, b, owner, parent, sym, fac = _oracle(w)
+    prob = rsd.grid_problem(n, depth, w["kappa"], w["f"])
+    p = getattr(rsd, "RSD_PREC_" + prec)
+    h = _setup(rsd, prob, p)
+    # factors agree with the oracle to single-precision accuracy
+    for t in sym.leaves()[:3] + [0]:
+        F = h.front_factor(t)
+        ref = np.vstack([fac.L[t], fac.X[t]])
+        tol = 1e-4 if prec == "FP32" else 3e-2
+        assert np.abs(F - ref).max() <= tol * np.abs(ref).max(), (t, np.abs(F - ref).max() / np.abs(ref).max())
+    u, st = h.solve(prob["b"], tol=1e-8)
+    assert st["relres"] <= 1e-8 and st["iterations"] <= 30, st
+    x = np.linalg.solve(A.toarray(), b)
+    assert np.abs(u.cpu().numpy() - x).max() <= 1e-6 * np.abs(x).max()
+
+
+def test_not_spd_is_reported(rsd):
+    w = _work(9, 1, False)
+    prob = rsd.grid_problem(9, 1, w["kappa"], w["f"])
+    with pytest.raises(rsd.RSDError) as e:
+        rsd.RSD.setup(prob["rowptr"], prob["col"], -prob["val"], prob["dof_node"], prob["parent"],
+                      prec_leaf=rsd.RSD_PREC_FP64, prec_mid=rsd.RSD_PREC_FP64)
+    assert e.value.code == -3
+
+
+def test_host_csr_input_matches_device_input(rsd):
+    w = _work(13, 1, True)
+    prob = rsd.grid_problem(13, 1, w["kappa"], w["f"])
+    h1 = _setup(rsd, prob, rsd.RSD_PREC_FP64)
+    h2 = rsd.RSD.setup(prob["rowptr"].cpu(), prob["col"].cpu(), prob["val"].cpu(), prob["dof_node"].cpu(),
+                       prob["parent"], prec_leaf=rsd.RSD_PREC_FP64, prec_mid=rsd.RSD_PREC_FP64)
+    r = prob["b"]
+    assert torch.equal(h1.apply(r), h2.apply(r))
+
+
+def test_apply_is_deterministic(rsd):
+    w = _work(20, 2, True)
+    prob = rsd.grid_problem(20, 2, w["kappa"], w["f"])
+    h = _setup(rsd, prob, rsd.RSD_PREC_TF32)
+    z1 = h.apply(prob["b"]).clone()
+    z2 = h.apply(prob["b"])
+    assert torch.equal(z1, z2)
