@@ -161,3 +161,20 @@ def test_apply_is_deterministic(rsd):
     z1 = h.apply(prob["b"]).clone()
     z2 = h.apply(prob["b"])
     assert torch.equal(z1, z2)
+
+
+@pytest.mark.parametrize("n,depth", [(9, 0), (17, 2), (26, 1), (20, 2)])
+def test_tf32_tensor_core_factors_track_fp32(rsd, n, depth):
+    """The tcgen05 TF32 GEMMs must reproduce the FP32 CUDA-core factors to TF32 rounding
+    (10-bit mantissa products, FP32 accumulation) at every node, root included."""
+    w = _work(n, depth, True)
+    prob = rsd.grid_problem(n, depth, w["kappa"], w["f"])
+    h32 = _setup(rsd, prob, rsd.RSD_PREC_FP32, root=rsd.RSD_PREC_FP32)
+    htf = _setup(rsd, prob, rsd.RSD_PREC_TF32, root=rsd.RSD_PREC_TF32)
+    n_nodes = len(prob["parent"])
+    for t in range(n_nodes):
+        a, b = h32.front_factor(t), htf.front_factor(t)
+        scale = np.abs(a).max()
+        assert np.abs(a - b).max() <= 5e-3 * scale, (t, np.abs(a - b).max() / scale)
+    u, st = htf.solve(prob["b"], tol=1e-8)
+    assert st["relres"] <= 1e-8, st
