@@ -81,6 +81,8 @@ typedef struct {
     int32_t prec_root;   /* RSD_PREC_* of the root interface                              */
     int32_t maxit;       /* rsd_solve iteration cap (<= 0: 200)                            */
     void*   stream;      /* cudaStream_t for every call on the handle (NULL: legacy default) */
+    int32_t profile;     /* nonzero: record a CUDA event pair around every kernel launch of the
+                            handle (see rsd_profile); adds ~2 us of host time per launch     */
 } rsd_options;
 
 typedef struct {
@@ -100,6 +102,21 @@ typedef struct {
     int64_t device_bytes;    /* bytes of device memory the handle holds                   */
     int32_t notspd_node;     /* first node whose pivot failed, or -1                      */
 } rsd_info_t;
+
+/* Per kernel class: launches, summed device time (CUDA events on the handle's stream)
+ * and the algorithmic work of those launches (dense-front method: GEMM 2MNK flops;
+ * substitution sweeps read every stored factor element once).  Classes:
+ * 0 front assembly, 1 extend-add, 2 tcgen05 GEMM, 3 CUDA-core GEMM, 4 diagonal block
+ * factor+inverse, 5 CUDA-core panel solve, 6 upward sweep, 7 downward sweep,
+ * 8 sweep gathers, 9 Krylov vector/SpMV kernels.                                    */
+#define RSD_PROFILE_CLASSES 10
+typedef struct {
+    int64_t launches[RSD_PROFILE_CLASSES];
+    double  ms[RSD_PROFILE_CLASSES];
+    double  flops[RSD_PROFILE_CLASSES];
+    double  bytes[RSD_PROFILE_CLASSES];
+    double  host_analysis_ms;    /* host-side analysis of the last rsd_setup             */
+} rsd_profile_t;
 
 typedef struct rsd_handle_s* rsd_handle;
 
@@ -157,6 +174,14 @@ int rsd_front_map(rsd_handle h, int32_t node, int32_t* out);
  * the Cholesky factor of the interface Schur complement (lower triangle, zeros above);
  * rows s..s+b-1 hold X_t = K~_BI L_t^-T, the coupling to the ancestors.              */
 int rsd_front_factor(rsd_handle h, int32_t node, double* out);
+
+/* rsd_profile -- synchronise the handle's stream and sum the profile recorded since
+ * setup or the last reset (all zeros unless rsd_options.profile was set).  reset != 0
+ * clears it afterwards.                                                               */
+int rsd_profile(rsd_handle h, rsd_profile_t* out, int32_t reset);
+
+/* rsd_launch_count -- kernels this library has launched in this process so far.       */
+int64_t rsd_launch_count(void);
 
 /* ---- structured-grid FEM problems (the synthetic workloads) ---------------------- *
  * Unit cube, n x n x n nodes (h = 1/(n-1)), trilinear hexahedra, homogeneous Dirichlet

@@ -18,8 +18,13 @@ from . import _lib
 from ._lib import (RSD_MEM_DEVICE, RSD_MEM_HOST, RSD_MODE_EXACT, RSD_PREC_FP32, RSD_PREC_FP64,
                    RSD_PREC_TF32, RSDError, check)
 
-__all__ = ["RSD", "grid_problem", "grid_sizes", "RSDError", "RSD_PREC_FP64", "RSD_PREC_FP32",
-           "RSD_PREC_TF32"]
+__all__ = ["RSD", "grid_problem", "grid_sizes", "launch_count", "RSDError", "RSD_PREC_FP64",
+           "RSD_PREC_FP32", "RSD_PREC_TF32"]
+
+
+def launch_count() -> int:
+    """Kernels librsd has launched in this process."""
+    return int(_lib.load().rsd_launch_count())
 
 
 def _ptr(t: torch.Tensor) -> int:
@@ -70,7 +75,7 @@ class RSD:
     def setup(cls, rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor,
               dof_node: torch.Tensor, parent, prec_leaf: int = RSD_PREC_TF32,
               prec_mid: int = RSD_PREC_TF32, prec_root: int = RSD_PREC_FP64,
-              maxit: int = 200) -> "RSD":
+              maxit: int = 200, profile: bool = False) -> "RSD":
         lib = _lib.load()
         dev = rowptr.is_cuda
         if not (col.is_cuda == dev and val.is_cuda == dev and dof_node.is_cuda == dev):
@@ -85,7 +90,7 @@ class RSD:
                            RSD_MEM_DEVICE if dev else RSD_MEM_HOST)
         tree = _lib.rsd_tree(len(par), par.ctypes.data)
         opt = _lib.rsd_options(RSD_MODE_EXACT, prec_leaf, prec_mid, prec_root, maxit,
-                               _stream() if torch.cuda.is_available() else 0)
+                               _stream() if torch.cuda.is_available() else 0, int(profile))
         out = C.c_void_p()
         rc = lib.rsd_setup(C.byref(csr), _ptr(dof_node), C.byref(tree), C.byref(opt), C.byref(out))
         if rc != 0:
@@ -122,6 +127,15 @@ class RSD:
 
     def check(self) -> None:
         check(_lib.load().rsd_check(self._h), "rsd_check")
+
+    def profile(self, reset: bool = True) -> dict:
+        """Per kernel class: launches, device ms (CUDA events), algorithmic flops and bytes."""
+        p = _lib.rsd_profile_t()
+        check(_lib.load().rsd_profile(self._h, C.byref(p), int(reset)), "rsd_profile")
+        out = {name: dict(launches=p.launches[i], ms=p.ms[i], flops=p.flops[i], bytes=p.bytes[i])
+               for i, name in enumerate(_lib.PROFILE_CLASSES)}
+        out["host_analysis_ms"] = p.host_analysis_ms
+        return out
 
     def info(self) -> dict:
         inf = _lib.rsd_info_t()

@@ -33,6 +33,7 @@ EXPORTS = [
     "rsd_setup", "rsd_apply", "rsd_solve", "rsd_check", "rsd_destroy", "rsd_strerror",
     "rsd_get_info", "rsd_front_dims", "rsd_front_dofs", "rsd_front_map", "rsd_front_factor",
     "rsd_grid_sizes", "rsd_grid_assemble", "rsd_grid_load", "rsd_grid_partition",
+    "rsd_profile", "rsd_launch_count",
 ]
 
 
@@ -47,7 +48,8 @@ class rsd_tree(C.Structure):
 
 class rsd_options(C.Structure):
     _fields_ = [("mode", C.c_int32), ("prec_leaf", C.c_int32), ("prec_mid", C.c_int32),
-                ("prec_root", C.c_int32), ("maxit", C.c_int32), ("stream", C.c_void_p)]
+                ("prec_root", C.c_int32), ("maxit", C.c_int32), ("stream", C.c_void_p),
+                ("profile", C.c_int32)]
 
 
 class rsd_stats(C.Structure):
@@ -60,6 +62,15 @@ class rsd_info_t(C.Structure):
                 ("factor_elems", C.c_int64), ("factor_bytes", C.c_int64),
                 ("setup_flops", C.c_double), ("device_bytes", C.c_int64),
                 ("notspd_node", C.c_int32)]
+
+
+PROFILE_CLASSES = ["assemble", "extend_add", "gemm_tcgen05", "gemm_simt", "diag_factor",
+                   "panel_solve_simt", "sweep_up", "sweep_down", "sweep_gather", "krylov"]
+
+
+class rsd_profile_t(C.Structure):
+    _fields_ = [("launches", C.c_int64 * 10), ("ms", C.c_double * 10), ("flops", C.c_double * 10),
+                ("bytes", C.c_double * 10), ("host_analysis_ms", C.c_double)]
 
 
 _lib = None
@@ -89,6 +100,8 @@ def load() -> C.CDLL:
             "rsd_grid_assemble": (C.c_int, [C.c_int32, P, P, P, P, P]),
             "rsd_grid_load": (C.c_int, [C.c_int32, P, P, P]),
             "rsd_grid_partition": (C.c_int, [C.c_int32, C.c_int32, P, P, P]),
+            "rsd_profile": (C.c_int, [P, C.POINTER(rsd_profile_t), C.c_int32]),
+            "rsd_launch_count": (C.c_int64, []),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)

@@ -10,6 +10,7 @@
 // Numeric setup and every later step run in the CUDA kernels of this library.
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -23,6 +24,29 @@ namespace rsd {
 
 static thread_local std::string g_last_error;
 void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+static std::atomic<long long> g_launches(0);
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int prof_begin(Handle& h, int cls) {
+    if (!h.prof.on) return -1;
+    Prof::Rec r{cls, 0.0, 0.0, nullptr, nullptr};
+    for (cudaEvent_t* e : {&r.a, &r.b}) {
+        if (!h.prof.pool.empty()) { *e = h.prof.pool.back(); h.prof.pool.pop_back(); }
+        else if (cudaEventCreate(e) != cudaSuccess) { cudaGetLastError(); return -1; }
+    }
+    cudaEventRecord(r.a, h.stream);
+    h.prof.recs.push_back(r);
+    return (int)h.prof.recs.size() - 1;
+}
+
+void prof_end(Handle& h, int idx, double flops, double bytes) {
+    if (idx < 0 || idx >= (int)h.prof.recs.size()) return;
+    Prof::Rec& r = h.prof.recs[idx];
+    r.flops = flops;
+    r.bytes = bytes;
+    cudaEventRecord(r.b, h.stream);
+}
 
 int pcg(Handle& h, const double* f, double* u, double tol, rsd_stats* st);
 int gemm_tc_prepare(Handle& h);     // tensor maps for the tensor-core levels (gemm_tc.cu)
@@ -444,11 +468,36 @@ extern "C" const char* rsd_strerror(int code) {
 
 extern "C" const char* rsd_last_error_detail(void) { return g_last_error.c_str(); }
 
+extern "C" int64_t rsd_launch_count(void) { return (int64_t)g_launches.load(); }
+
+extern "C" int rsd_profile(rsd_handle hh, rsd_profile_t* out, int32_t reset) {
+    if (!hh || !out) return RSD_ERR_ARG;
+    Handle& h = hh->h;
+    std::memset(out, 0, sizeof(*out));
+    RSD_CUDA_TRY(cudaStreamSynchronize(h.stream));
+    for (auto& r : h.prof.recs) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) { cudaGetLastError(); ms = 0; }
+        out->launches[r.cls] += 1;
+        out->ms[r.cls] += ms;
+        out->flops[r.cls] += r.flops;
+        out->bytes[r.cls] += r.bytes;
+    }
+    out->host_analysis_ms = h.prof.host_ms;
+    if (reset) {
+        for (auto& r : h.prof.recs) { h.prof.pool.push_back(r.a); h.prof.pool.push_back(r.b); }
+        h.prof.recs.clear();
+    }
+    return RSD_OK;
+}
+
 extern "C" void rsd_destroy(rsd_handle hh) {
     if (!hh) return;
     Handle& h = hh->h;
     if (h.stream) cudaStreamSynchronize(h.stream);
     gemm_tc_release(h);
+    for (auto& r : h.prof.recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : h.prof.pool) cudaEventDestroy(e);
     if (h.arena) cudaFree(h.arena);
     if (h.h_scal) cudaFreeHost(h.h_scal);
     delete hh;
@@ -468,6 +517,7 @@ extern "C" int rsd_setup(const rsd_csr* K, const int32_t* dof_node, const rsd_tr
     o.maxit = 200;
     if (opt) o = *opt;
     if (o.mode != RSD_MODE_EXACT) return RSD_ERR_ARG;
+    const auto t_host0 = std::chrono::steady_clock::now();
     Analysis a;
     a.n = K->n;
     RSD_TRY(analyse_tree(a, T));
@@ -498,6 +548,8 @@ extern "C" int rsd_setup(const rsd_csr* K, const int32_t* dof_node, const rsd_tr
     Handle& h = hh->h;
     h.opt = o;
     h.stream = st;
+    h.prof.on = o.profile != 0;
+    h.prof.host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_host0).count();
     h.nnz = K->nnz;
     int dev = 0;
     cudaGetDevice(&dev);

@@ -270,12 +270,22 @@ __global__ void __launch_bounds__(AT) k_bwd_sweep(const FrontDesc* __restrict__ 
     }
 }
 
+double level_factor_bytes(const Level& L) {
+    double e = 0;
+    for (auto& f : L.fronts) e += 0.5 * f.s * (f.s + 1.0) + (double)f.s * f.b;
+    return e * elem_bytes(L.prec);
+}
+
 template <typename T, typename A>
 int sweep_level(Handle& h, int li, bool forward, const double* r, double* z, int tk) {
     Level& L = h.levels[li];
     const int nf = (int)L.fronts.size();
+    double gbytes = 0;
+    for (auto& f : L.fronts) gbytes += (double)f.N * (sizeof(A) + 8.0);
+    const double fbytes = level_factor_bytes(L);
     const int grid = std::max(1, std::min(forward ? L.n_fwd_items : L.n_bwd_items, h.num_sms * 4));
     if (forward) {
+        const int gi = prof_begin(h, K_GATHER);
         if (li + 1 < (int)h.levels.size()) {
             const Level& Lc = h.levels[li + 1];
             if (is_fp64(Lc.prec)) k_fwd_gather<A, double><<<nf, 256, 0, h.stream>>>(L.d_fronts, Lc.d_fronts, L.d_child_slots, r);
@@ -283,14 +293,27 @@ int sweep_level(Handle& h, int li, bool forward, const double* r, double* z, int
         } else {
             k_fwd_gather<A, A><<<nf, 256, 0, h.stream>>>(L.d_fronts, L.d_fronts, L.d_child_slots, r);
         }
+        count_launch();
+        prof_end(h, gi, 0.0, gbytes);
         RSD_CUDA_TRY(cudaGetLastError());
-        if (L.n_fwd_items)
+        if (L.n_fwd_items) {
+            const int pi = prof_begin(h, K_FWD);
             k_fwd_sweep<T, A><<<grid, AT, 0, h.stream>>>(L.d_fronts, L.d_fwd_items, L.n_fwd_items, h.d_ticket + tk, h.d_err);
+            count_launch();
+            prof_end(h, pi, fbytes / sizeof(T) * 2.0, fbytes);
+        }
     } else {
+        const int gi = prof_begin(h, K_GATHER);
         k_bwd_gather<A><<<nf, 256, 0, h.stream>>>(L.d_fronts, z);
+        count_launch();
+        prof_end(h, gi, 0.0, gbytes);
         RSD_CUDA_TRY(cudaGetLastError());
-        if (L.n_bwd_items)
+        if (L.n_bwd_items) {
+            const int pi = prof_begin(h, K_BWD);
             k_bwd_sweep<T, A><<<grid, AT, 0, h.stream>>>(L.d_fronts, L.d_bwd_items, L.n_bwd_items, h.d_ticket + tk, h.d_err, z);
+            count_launch();
+            prof_end(h, pi, fbytes / sizeof(T) * 2.0, fbytes);
+        }
     }
     RSD_CUDA_TRY(cudaGetLastError());
     return RSD_OK;

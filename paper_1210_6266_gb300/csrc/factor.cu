@@ -304,8 +304,24 @@ __global__ void __launch_bounds__(256) k_trsm_simt(const FrontDesc* __restrict__
     }
 }
 
+double gemm_flops(const std::vector<GemmTask>& tasks) {
+    double f = 0;
+    for (auto& t : tasks)
+        f += t.lower ? (double)t.M * (t.M + 1) * t.K : 2.0 * t.M * t.N * t.K;
+    return f;
+}
+
+double gemm_bytes(const std::vector<GemmTask>& tasks, size_t es) {
+    double b = 0;
+    for (auto& t : tasks) {
+        const double c = t.lower ? 0.5 * t.M * (t.M + 1.0) : (double)t.M * t.N;
+        b += es * ((double)t.M * t.K + (t.A == t.B && t.lower ? 0.0 : (double)t.N * t.K) + c * (t.beta ? 2 : 1));
+    }
+    return b;
+}
+
 template <typename T>
-int launch_gemm_simt(const std::vector<GemmTask>& tasks, GemmTask* d_tasks, T alpha, cudaStream_t st) {
+int launch_gemm_simt(Handle& h, const std::vector<GemmTask>& tasks, GemmTask* d_tasks, T alpha, cudaStream_t st) {
     if (tasks.empty()) return RSD_OK;
     RSD_CUDA_TRY(cudaMemcpyAsync(d_tasks, tasks.data(), tasks.size() * sizeof(GemmTask),
                                  cudaMemcpyHostToDevice, st));
@@ -314,7 +330,10 @@ int launch_gemm_simt(const std::vector<GemmTask>& tasks, GemmTask* d_tasks, T al
                                       : ((last.M + SB - 1) / SB) * last.tiles_n;
     const int total = last.tile_begin + tiles_last;
     if (total <= 0) return RSD_OK;
+    const int pi = prof_begin(h, K_GEMM_SIMT);
     k_gemm_simt<T><<<total, 256, 0, st>>>(d_tasks, (int)tasks.size(), alpha);
+    count_launch();
+    prof_end(h, pi, gemm_flops(tasks), gemm_bytes(tasks, sizeof(T)));
     RSD_CUDA_TRY(cudaGetLastError());
     return RSD_OK;
 }
@@ -342,10 +361,17 @@ int launch_assemble_fronts(Handle& h, int li, const int64_t* rowptr, const int* 
     RSD_CUDA_TRY(cudaMemsetAsync(L.fronts[0].P, 0, L.bytes_P, h.stream));
     if (L.bytes_U) RSD_CUDA_TRY(cudaMemsetAsync(L.fronts[0].U, 0, L.bytes_U, h.stream));
     dim3 grid((unsigned)std::max(1, std::min(64, (L.max_s + 7) / 8)), (unsigned)L.fronts.size());
+    const int pi = prof_begin(h, K_ASSEMBLE);
     if (is_fp64(L.prec))
         k_scatter_K<double><<<grid, 256, 0, h.stream>>>(L.d_fronts, rowptr, col, val, owner, rank, tin, tout);
     else
         k_scatter_K<float><<<grid, 256, 0, h.stream>>>(L.d_fronts, rowptr, col, val, owner, rank, tin, tout);
+    count_launch();
+    {
+        double rows = 0;
+        for (auto& f : L.fronts) rows += f.s;
+        prof_end(h, pi, 0.0, rows * 27.0 * (12.0 + elem_bytes(L.prec)));
+    }
     RSD_CUDA_TRY(cudaGetLastError());
     return RSD_OK;
 }
@@ -357,11 +383,17 @@ int launch_extend_add(Handle& h, int li) {
     if (Lp.fronts.empty() || Lc.fronts.empty()) return RSD_OK;
     const bool p64 = is_fp64(Lp.prec), c64 = is_fp64(Lc.prec);
     dim3 grid((unsigned)std::max(1, std::min(256, Lc.max_b)), (unsigned)Lp.fronts.size());
+    double ea_bytes = 0;
+    for (auto& f : Lc.fronts) ea_bytes += 0.5 * f.b * (f.b + 1.0) * (elem_bytes(Lc.prec) + 2.0 * elem_bytes(Lp.prec));
+    ea_bytes /= std::max(1, Lp.max_children);
     for (int ci = 0; ci < Lp.max_children; ++ci) {
+        const int pi = prof_begin(h, K_EXTEND);
         if (p64 && c64) k_extend_add<double, double><<<grid, 256, 0, h.stream>>>(Lp.d_fronts, Lc.d_fronts, Lp.d_child_slots, ci);
         else if (p64 && !c64) k_extend_add<float, double><<<grid, 256, 0, h.stream>>>(Lp.d_fronts, Lc.d_fronts, Lp.d_child_slots, ci);
         else if (!p64 && c64) k_extend_add<double, float><<<grid, 256, 0, h.stream>>>(Lp.d_fronts, Lc.d_fronts, Lp.d_child_slots, ci);
         else k_extend_add<float, float><<<grid, 256, 0, h.stream>>>(Lp.d_fronts, Lc.d_fronts, Lp.d_child_slots, ci);
+        count_launch();
+        prof_end(h, pi, 0.0, ea_bytes);
         RSD_CUDA_TRY(cudaGetLastError());
     }
     return RSD_OK;
@@ -409,14 +441,20 @@ int run_factor_level(Handle& h, int li) {
             if (tc) rc = gemm_tc_launch(h, li, tasks, 0, h.stream);
             else {
                 finalize_tasks(tasks, SB, SB);
-                rc = f64 ? launch_gemm_simt<double>(tasks, d_tasks, -1.0, h.stream)
-                         : launch_gemm_simt<float>(tasks, d_tasks, -1.0f, h.stream);
+                rc = f64 ? launch_gemm_simt<double>(h, tasks, d_tasks, -1.0, h.stream)
+                         : launch_gemm_simt<float>(h, tasks, d_tasks, -1.0f, h.stream);
             }
             if (rc != RSD_OK) break;
         }
         // (b) diagonal block factor + inverse
+        double pf = 0, pb = 0;
+        for (auto& f : L.fronts)
+            if (f.s > k) { const double w = std::min(NB, f.s - k); pf += 2.0 * w * w * w / 3.0; pb += (2.0 * w * w + NB * NB) * es; }
+        const int ppi = prof_begin(h, K_POTRF);
         if (f64) k_potrf_diag<double><<<(unsigned)L.fronts.size(), 256, potrf_smem, h.stream>>>(L.d_fronts, k, h.d_err);
         else k_potrf_diag<float><<<(unsigned)L.fronts.size(), 256, potrf_smem, h.stream>>>(L.d_fronts, k, h.d_err);
+        count_launch();
+        prof_end(h, ppi, pf, pb);
         if (cudaGetLastError() != cudaSuccess) { rc = RSD_ERR_CUDA; break; }
         // (c) panel solve below the diagonal block
         if (tc) {
@@ -441,8 +479,14 @@ int run_factor_level(Handle& h, int li) {
         } else {
             const int rows = L.max_N;   // upper bound on rows below the diagonal
             dim3 grid((unsigned)std::max(1, (rows - k + TR_ROWS - 1) / TR_ROWS), (unsigned)L.fronts.size());
+            double tf = 0, tb = 0;
+            for (auto& f : L.fronts)
+                if (f.s > k) { const double w = std::min(NB, f.s - k), m = f.N - k - w; tf += m * w * w; tb += 2.0 * m * w * es; }
+            const int tpi = prof_begin(h, K_TRSM);
             if (f64) k_trsm_simt<double><<<grid, 256, trsm_smem, h.stream>>>(L.d_fronts, k);
             else k_trsm_simt<float><<<grid, 256, trsm_smem, h.stream>>>(L.d_fronts, k);
+            count_launch();
+            prof_end(h, tpi, tf, tb);
             if (cudaGetLastError() != cudaSuccess) { rc = RSD_ERR_CUDA; break; }
         }
     }
@@ -466,8 +510,8 @@ int run_factor_level(Handle& h, int li) {
             if (tc) rc = gemm_tc_launch(h, li, tasks, 2, h.stream);
             else {
                 finalize_tasks(tasks, SB, SB);
-                rc = f64 ? launch_gemm_simt<double>(tasks, d_tasks, -1.0, h.stream)
-                         : launch_gemm_simt<float>(tasks, d_tasks, -1.0f, h.stream);
+                rc = f64 ? launch_gemm_simt<double>(h, tasks, d_tasks, -1.0, h.stream)
+                         : launch_gemm_simt<float>(h, tasks, d_tasks, -1.0f, h.stream);
             }
         }
     }

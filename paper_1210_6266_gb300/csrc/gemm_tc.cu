@@ -373,10 +373,19 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
         RSD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<256>::TOTAL));
         st->attr_set = true;
     }
+    double fl = 0, by = 0;
+    for (auto& g : tasks) {
+        const double c = g.lower ? 0.5 * g.M * (g.M + 1.0) : (double)g.M * g.N;
+        fl += 2.0 * c * g.K;
+        by += 4.0 * ((double)g.M * g.K + (g.lower ? 0.0 : (double)g.N * g.K) + c * (g.beta ? 2 : 1));
+    }
+    const int pi = prof_begin(h, K_GEMM_TC);
     if (bn == 128)
         k_gemm_tc<128><<<(unsigned)tl.size(), TC_THREADS, Smem<128>::TOTAL, stream>>>(st->d_tasks, st->d_tiles, st->d_maps, h.d_err);
     else
         k_gemm_tc<256><<<(unsigned)tl.size(), TC_THREADS, Smem<256>::TOTAL, stream>>>(st->d_tasks, st->d_tiles, st->d_maps, h.d_err);
+    count_launch();
+    prof_end(h, pi, fl, by);
     RSD_CUDA_TRY(cudaGetLastError());
     return RSD_OK;
 }

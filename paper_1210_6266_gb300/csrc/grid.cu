@@ -131,6 +131,7 @@ extern "C" int rsd_grid_assemble(int32_t n, const double* kappa, int64_t* rowptr
     if (!kappa || !rowptr || !col || !val) return RSD_ERR_ARG;
     const int T = 256;
     k_grid_assemble<<<(unsigned)((ndof + T - 1) / T), T, 0, (cudaStream_t)stream>>>(n, kappa, rowptr, col, val);
+    count_launch();
     RSD_CUDA_TRY(cudaGetLastError());
     return RSD_OK;
 }
@@ -142,6 +143,7 @@ extern "C" int rsd_grid_load(int32_t n, const double* f, double* b, void* stream
     const double h = 1.0 / (n - 1);
     const int T = 256;
     k_grid_load<<<(unsigned)((ndof + T - 1) / T), T, 0, (cudaStream_t)stream>>>(ndof, h * h * h, f, b);
+    count_launch();
     RSD_CUDA_TRY(cudaGetLastError());
     return RSD_OK;
 }
@@ -156,6 +158,7 @@ extern "C" int rsd_grid_partition(int32_t n, int32_t depth, int32_t* dof_node, i
     for (int64_t t = 0; t < n_nodes; ++t) parent[t] = t == 0 ? -1 : (int32_t)((t - 1) / 8);
     const int T = 256;
     k_grid_partition<<<(unsigned)((ndof + T - 1) / T), T, 0, (cudaStream_t)stream>>>(n, depth, dof_node);
+    count_launch();
     RSD_CUDA_TRY(cudaGetLastError());
     return RSD_OK;
 }

@@ -103,8 +103,11 @@ __global__ void k_residual(int n, const int64_t* __restrict__ rowptr, const int*
 }
 
 int dot(Handle& h, const double* a, const double* b, int slot) {
+    const int pi = prof_begin(h, K_KRYLOV);
     k_dot_partial<<<RED_BLOCKS, RT, 0, h.stream>>>(h.n, a, b, h.d_partial);
     k_reduce_final<<<1, RT, 0, h.stream>>>(h.d_partial, RED_BLOCKS, h.d_scal + slot);
+    count_launch(2);
+    prof_end(h, pi, 2.0 * h.n, 16.0 * h.n);
     RSD_CUDA_TRY(cudaGetLastError());
     return RSD_OK;
 }
@@ -120,7 +123,10 @@ int fetch(Handle& h, int slot, double* out) {
 
 int spmv(Handle& h, const double* x, double* y) {
     const int64_t threads = (int64_t)h.n * 4;
+    const int pi = prof_begin(h, K_KRYLOV);
     k_spmv<<<(unsigned)((threads + RT - 1) / RT), RT, 0, h.stream>>>(h.n, h.d_rowptr, h.d_col, h.d_val, x, y);
+    count_launch();
+    prof_end(h, pi, 2.0 * h.nnz, 12.0 * h.nnz + 24.0 * h.n);
     RSD_CUDA_TRY(cudaGetLastError());
     return RSD_OK;
 }
@@ -154,8 +160,11 @@ int pcg(Handle& h, const double* f, double* u, double tol, rsd_stats* st) {
         const int old_slot = (it & 1) ? 0 : 3, new_slot = (it & 1) ? 3 : 0;
         RSD_TRY(spmv(h, p, q));
         RSD_TRY(dot(h, p, q, 1));
+        const int pu = prof_begin(h, K_KRYLOV);
         k_cg_update<<<RED_BLOCKS, RT, 0, h.stream>>>(n, h.d_scal, old_slot, u, r, p, q, h.d_partial);
         k_reduce_final<<<1, RT, 0, h.stream>>>(h.d_partial, RED_BLOCKS, h.d_scal + 2);
+        count_launch(2);
+        prof_end(h, pu, 6.0 * n, 48.0 * n);
         RSD_CUDA_TRY(cudaGetLastError());
         double rr;
         RSD_TRY(fetch(h, 2, &rr));
@@ -165,14 +174,20 @@ int pcg(Handle& h, const double* f, double* u, double tol, rsd_stats* st) {
         if (rel <= tol) { rc = RSD_OK; break; }
         RSD_TRY(run_apply(h, r, z));
         RSD_TRY(dot(h, r, z, new_slot));
+        const int pd = prof_begin(h, K_KRYLOV);
         k_cg_direction<<<RED_BLOCKS, RT, 0, h.stream>>>(n, h.d_scal, new_slot, old_slot, z, p);
+        count_launch();
+        prof_end(h, pd, 2.0 * n, 24.0 * n);
         RSD_CUDA_TRY(cudaGetLastError());
     }
     S->iterations = std::min(it, maxit);
     S->relres_recursive = rel;
     // true residual in FP64
     const int64_t threads = n * 4;
+    const int pr = prof_begin(h, K_KRYLOV);
     k_residual<<<(unsigned)((threads + RT - 1) / RT), RT, 0, h.stream>>>(h.n, h.d_rowptr, h.d_col, h.d_val, u, f, q);
+    count_launch();
+    prof_end(h, pr, 2.0 * h.nnz, 12.0 * h.nnz + 32.0 * h.n);
     RSD_CUDA_TRY(cudaGetLastError());
     RSD_TRY(dot(h, q, q, 5));
     double tr;

@@ -73,6 +73,22 @@ struct GemmTask {
     int a_r0, a_c0, b_r0, b_c0;   // operand origins inside the tensor maps
 };
 
+// Kernel classes for launch counting and the optional CUDA-event profile.
+enum KClass { K_ASSEMBLE = 0, K_EXTEND, K_GEMM_TC, K_GEMM_SIMT, K_POTRF, K_TRSM, K_FWD, K_BWD,
+              K_GATHER, K_KRYLOV, K_CLASSES };
+
+// Per-handle profile: one event pair per launch of a class, with the algorithmic
+// flops and bytes of that launch; reduced on demand by rsd_profile().
+struct Prof {
+    bool on = false;
+    struct Rec { int cls; double flops, bytes; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    double host_ms = 0;                  // host-side analysis time of the last setup
+};
+
+void count_launch(int n = 1);
+
 struct Level {
     int depth = 0;
     int prec = RSD_PREC_FP64;
@@ -122,7 +138,13 @@ struct Handle {
     int notspd_node = -1;
     int num_sms = 148;
     void* tc_state = nullptr;            // tensor-core GEMM state (tensor maps, task buffers)
+    Prof prof;
 };
+
+// Profile helpers: prof_begin records the start event (if profiling) and returns a
+// record index; prof_end records the stop event and the launch's algorithmic work.
+int prof_begin(Handle& h, int cls);
+void prof_end(Handle& h, int idx, double flops, double bytes);
 
 // ---- kernels launched from the host orchestration -------------------------------
 int launch_assemble_fronts(Handle& h, int li, const int64_t* rowptr, const int* col,

@@ -64,7 +64,7 @@ def _host_setup(lib, A, owner, parent):
     par = np.ascontiguousarray(parent.astype(np.int32))
     csr = lib.rsd_csr(A.shape[0], A.nnz, rowptr.ctypes.data, col.ctypes.data, val.ctypes.data, lib.RSD_MEM_HOST)
     tree = lib.rsd_tree(len(par), par.ctypes.data)
-    opt = lib.rsd_options(0, lib.RSD_PREC_FP64, lib.RSD_PREC_FP64, lib.RSD_PREC_FP64, 10, None)
+    opt = lib.rsd_options(0, lib.RSD_PREC_FP64, lib.RSD_PREC_FP64, lib.RSD_PREC_FP64, 10, None, 0)
     out = C.c_void_p()
     return so.rsd_setup(C.byref(csr), own.ctypes.data, C.byref(tree), C.byref(opt), C.byref(out))
 
