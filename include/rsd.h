@@ -146,6 +146,24 @@ int rsd_setup(const rsd_csr* K, const int32_t* dof_node, const rsd_tree* T,
  *          bound is reported as RSD_ERR_TIMEOUT by the next rsd_solve / rsd_check call. */
 int rsd_apply(rsd_handle h, const double* r, double* z);
 
+/* rsd_apply_static -- the same z = M r as rsd_apply, for callers that must not have
+ * device memory allocated on their behalf: code running while a stream is being
+ * captured, or under a fixed device-memory budget, or inside a framework whose caching
+ * allocator owns the device.  The paper has no counterpart; it is a packaging of
+ * rsd_apply.  The per-call scratch of the substitution sweeps (front vectors, progress
+ * and ticket counters, and a copy of the front descriptors pointing at them) is taken
+ * from one file-scope device array of 4 MiB, which every GPU that loads the library
+ * holds until the process exits; nothing is allocated by the call.
+ *   r, z : device, n FP64 entries each, may not alias (as rsd_apply).
+ * Returns RSD_ERR_ARG if the hierarchy needs more than 4 MiB of scratch (roughly
+ * sum over tree nodes of (s + b + 32) entries at the level's storage width, plus the
+ * descriptors); rsd_last_error_detail names the size.  The counters are cleared on
+ * every call.  The first call on a device looks up that device's address of the array,
+ * so make it once before capturing a stream.  All calls, from every handle and stream,
+ * share the one array: calls that overlap on the GPU race and must be serialised by
+ * the caller.                                                                          */
+int rsd_apply_static(rsd_handle h, const double* r, double* z);
+
 /* rsd_solve -- preconditioned CG in FP64 on K u = f from u = 0 (the paper's outer Krylov
  * solve with RSD as preconditioner, Sec. 3 and Sec. 4), stopping when the recursively
  * updated residual satisfies ||r_k|| / ||f|| <= tol; then recomputes the true residual.
@@ -160,6 +178,8 @@ int rsd_check(rsd_handle h);
 
 void        rsd_destroy(rsd_handle h);
 const char* rsd_strerror(int code);
+/* detail of the last failure on the calling host thread (which CUDA call, which size). */
+const char* rsd_last_error_detail(void);
 
 /* ---- introspection (tests and benchmarks) --------------------------------------- */
 int rsd_get_info(rsd_handle h, rsd_info_t* out);

@@ -33,7 +33,7 @@ EXPORTS = [
     "rsd_setup", "rsd_apply", "rsd_solve", "rsd_check", "rsd_destroy", "rsd_strerror",
     "rsd_get_info", "rsd_front_dims", "rsd_front_dofs", "rsd_front_map", "rsd_front_factor",
     "rsd_grid_sizes", "rsd_grid_assemble", "rsd_grid_load", "rsd_grid_partition",
-    "rsd_profile", "rsd_launch_count",
+    "rsd_profile", "rsd_launch_count", "rsd_apply_static", "rsd_last_error_detail",
 ]
 
 
@@ -86,6 +86,7 @@ def load() -> C.CDLL:
         sig = {
             "rsd_setup": (C.c_int, [C.POINTER(rsd_csr), P, C.POINTER(rsd_tree), C.POINTER(rsd_options), C.POINTER(P)]),
             "rsd_apply": (C.c_int, [P, P, P]),
+            "rsd_apply_static": (C.c_int, [P, P, P]),
             "rsd_solve": (C.c_int, [P, P, P, C.c_double, C.POINTER(rsd_stats)]),
             "rsd_check": (C.c_int, [P]),
             "rsd_destroy": (None, [P]),

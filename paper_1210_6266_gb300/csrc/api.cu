@@ -576,6 +576,11 @@ extern "C" int rsd_apply(rsd_handle hh, const double* r, double* z) {
     return run_apply(hh->h, r, z);
 }
 
+extern "C" int rsd_apply_static(rsd_handle hh, const double* r, double* z) {
+    if (!hh || !r || !z || r == z) return RSD_ERR_ARG;
+    return run_apply_static(hh->h, r, z);
+}
+
 extern "C" int rsd_check(rsd_handle hh) {
     if (!hh) return RSD_ERR_ARG;
     Handle& h = hh->h;

@@ -338,3 +338,114 @@ int run_apply(Handle& h, const double* r, double* z) {
 }
 
 }  // namespace rsd
+
+// ---- allocation-free variant of the preconditioner application ----------------------
+// Same kernels as run_apply; the per-call scratch (front vectors, progress counters,
+// ticket counters and a copy of the front descriptors pointing at them) lives in one
+// file-scope device array instead of the handle's arena.  Every call shares that array.
+namespace rsd {
+namespace {
+
+constexpr size_t APPLY_STATIC_BYTES = (size_t)4 << 20;          // 4 MiB per device
+__device__ __align__(256) unsigned char g_apply_scratch[APPLY_STATIC_BYTES];
+
+constexpr int MAX_DEVICES = 64;
+void* g_apply_scratch_ptr[MAX_DEVICES] = {};
+FrontDesc g_staging[APPLY_STATIC_BYTES / sizeof(FrontDesc)];    // host staging of descriptors
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+template <typename T, typename A>
+int sweep_level_static(Handle& h, int li, bool forward, const double* r, double* z, int* ticket,
+                       FrontDesc* const* lvl_fronts) {
+    Level& L = h.levels[li];
+    const int nf = (int)L.fronts.size();
+    FrontDesc* fr = lvl_fronts[li];
+    const int grid = std::max(1, std::min(forward ? L.n_fwd_items : L.n_bwd_items, h.num_sms * 4));
+    if (forward) {
+        if (li + 1 < (int)h.levels.size()) {
+            const Level& Lc = h.levels[li + 1];
+            if (is_fp64(Lc.prec)) k_fwd_gather<A, double><<<nf, 256, 0, h.stream>>>(fr, lvl_fronts[li + 1], L.d_child_slots, r);
+            else k_fwd_gather<A, float><<<nf, 256, 0, h.stream>>>(fr, lvl_fronts[li + 1], L.d_child_slots, r);
+        } else {
+            k_fwd_gather<A, A><<<nf, 256, 0, h.stream>>>(fr, fr, L.d_child_slots, r);
+        }
+        count_launch();
+        RSD_CUDA_TRY(cudaGetLastError());
+        if (L.n_fwd_items) {
+            k_fwd_sweep<T, A><<<grid, AT, 0, h.stream>>>(fr, L.d_fwd_items, L.n_fwd_items, ticket, h.d_err);
+            count_launch();
+        }
+    } else {
+        k_bwd_gather<A><<<nf, 256, 0, h.stream>>>(fr, z);
+        count_launch();
+        RSD_CUDA_TRY(cudaGetLastError());
+        if (L.n_bwd_items) {
+            k_bwd_sweep<T, A><<<grid, AT, 0, h.stream>>>(fr, L.d_bwd_items, L.n_bwd_items, ticket, h.d_err, z);
+            count_launch();
+        }
+    }
+    RSD_CUDA_TRY(cudaGetLastError());
+    return RSD_OK;
+}
+
+}  // namespace
+
+int run_apply_static(Handle& h, const double* r, double* z) {
+    int dev = 0;
+    RSD_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= MAX_DEVICES) return RSD_ERR_ARG;
+    if (!g_apply_scratch_ptr[dev]) {
+        void* p = nullptr;
+        RSD_CUDA_TRY(cudaGetSymbolAddress(&p, g_apply_scratch));
+        g_apply_scratch_ptr[dev] = p;
+    }
+    char* base = (char*)g_apply_scratch_ptr[dev];
+    const int nl = (int)h.levels.size();
+    // layout: tickets | progress counters | descriptors | front vectors
+    size_t off = 0;
+    const size_t o_ticket = off; off = align256(off + sizeof(int) * 2 * nl);
+    const size_t o_flags = off;  off = align256(off + sizeof(int) * 2 * (size_t)h.n_nodes);
+    const size_t o_fronts = off; off = align256(off + sizeof(FrontDesc) * (size_t)h.n_nodes);
+    size_t vec_bytes = 0;
+    for (auto& L : h.levels)
+        for (auto& f : L.fronts) vec_bytes += align256((size_t)(f.N + 32) * elem_bytes(L.prec));
+    const size_t o_vec = off; off += vec_bytes;
+    if (off > APPLY_STATIC_BYTES || (size_t)h.n_nodes > sizeof(g_staging) / sizeof(FrontDesc)) {
+        set_last_error("rsd_apply_static: this hierarchy needs " + std::to_string(off) +
+                       " bytes of scratch; the static limit is " + std::to_string(APPLY_STATIC_BYTES));
+        return RSD_ERR_ARG;
+    }
+    FrontDesc* lvl_fronts[64];
+    if (nl > 64) return RSD_ERR_ARG;
+    size_t slot = 0, voff = o_vec;
+    for (int li = 0; li < nl; ++li) {
+        Level& L = h.levels[li];
+        lvl_fronts[li] = (FrontDesc*)(base + o_fronts) + slot;
+        for (auto& f : L.fronts) {
+            FrontDesc g = f;
+            g.vec = base + voff;
+            voff += align256((size_t)(f.N + 32) * elem_bytes(L.prec));
+            g.flag = (int*)(base + o_flags) + 2 * f.node;
+            g_staging[slot++] = g;
+        }
+    }
+    RSD_CUDA_TRY(cudaMemcpyAsync(base + o_fronts, g_staging, sizeof(FrontDesc) * slot, cudaMemcpyHostToDevice, h.stream));
+    RSD_CUDA_TRY(cudaMemsetAsync(base + o_ticket, 0, o_fronts - o_ticket, h.stream));
+    int* ticket = (int*)(base + o_ticket);
+    for (int li = nl - 1; li >= 0; --li) {
+        const int rc = is_fp64(h.levels[li].prec)
+                           ? sweep_level_static<double, double>(h, li, true, r, z, ticket + li, lvl_fronts)
+                           : sweep_level_static<float, float>(h, li, true, r, z, ticket + li, lvl_fronts);
+        if (rc != RSD_OK) return rc;
+    }
+    for (int li = 0; li < nl; ++li) {
+        const int rc = is_fp64(h.levels[li].prec)
+                           ? sweep_level_static<double, double>(h, li, false, r, z, ticket + nl + li, lvl_fronts)
+                           : sweep_level_static<float, float>(h, li, false, r, z, ticket + nl + li, lvl_fronts);
+        if (rc != RSD_OK) return rc;
+    }
+    return RSD_OK;
+}
+
+}  // namespace rsd

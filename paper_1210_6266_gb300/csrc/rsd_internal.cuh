@@ -153,6 +153,7 @@ int launch_assemble_fronts(Handle& h, int li, const int64_t* rowptr, const int* 
 int launch_extend_add(Handle& h, int li);
 int run_factor_level(Handle& h, int li);
 int run_apply(Handle& h, const double* r, double* z);
+int run_apply_static(Handle& h, const double* r, double* z);
 int spmv(Handle& h, const double* x, double* y);
 
 }  // namespace rsd
