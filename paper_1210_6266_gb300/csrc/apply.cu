@@ -37,6 +37,20 @@ template <> __device__ __forceinline__ double ld_cg(const double* p) { return __
 
 __device__ __forceinline__ int ld_volatile(const int* p) { return *(volatile const int*)p; }
 
+// Asynchronous copy of one NB x NB inverted diagonal block into shared memory (16 B per
+// cp.async, L2 only); completed by cp_async_wait() before use.
+template <typename T>
+__device__ __forceinline__ void prefetch_block(T* dst, const T* src) {
+    constexpr int CHUNKS = NB * NB * (int)sizeof(T) / 16;
+    const uint32_t d0 = (uint32_t)__cvta_generic_to_shared(dst);
+    for (int c = threadIdx.x; c < CHUNKS; c += blockDim.x)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d0 + 16 * c), "l"((const char*)src + 16 * c)
+                     : "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Wait until *flag >= target; returns the last value seen.  Thread 0 polls, the block syncs.
 __device__ int wait_flag(const int* flag, int target, int* err, int* s_val) {
     if (threadIdx.x == 0) {
@@ -93,6 +107,8 @@ __global__ void __launch_bounds__(AT) k_fwd_sweep(const FrontDesc* __restrict__ 
     constexpr int RPW = NB / AW;                 // rows per warp
     __shared__ int s_item, s_flag;
     __shared__ A s_t[NB];
+    extern __shared__ __align__(16) unsigned char sweep_smem[];
+    T* Ds = (T*)sweep_smem;                      // NB x NB inverted diagonal block
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(ticket, 1);
@@ -103,6 +119,7 @@ __global__ void __launch_bounds__(AT) k_fwd_sweep(const FrontDesc* __restrict__ 
         const int slot = items[it] >> 16, blk = items[it] & 0xffff;
         const FrontDesc f = fronts[slot];
         const bool diag = blk < f.nd;
+        if (diag) prefetch_block(Ds, (const T*)f.Dinv + (int64_t)blk * NB * NB);
         const int r0 = diag ? blk * NB : f.s + (blk - f.nd) * NB;
         const int r1 = diag ? min(r0 + NB, f.s) : min(r0 + NB, f.N);
         const int ncb = diag ? blk : f.nd;
@@ -147,10 +164,11 @@ __global__ void __launch_bounds__(AT) k_fwd_sweep(const FrontDesc* __restrict__ 
         __syncthreads();
         if (diag) {
             const int w = r1 - r0;
-            const T* D = (const T*)f.Dinv + (int64_t)blk * NB * NB;
+            cp_async_wait();
+            __syncthreads();
             for (int rr = warp; rr < w; rr += AW) {
                 A s = 0;
-                for (int c = lane; c <= rr; c += 32) s += (A)D[rr * NB + c] * s_t[c];
+                for (int c = lane; c <= rr; c += 32) s += (A)Ds[rr * NB + c] * s_t[c];
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
                 if (lane == 0) __stcg(v + r0 + rr, s);
@@ -184,6 +202,8 @@ __global__ void __launch_bounds__(AT) k_bwd_sweep(const FrontDesc* __restrict__ 
     __shared__ int s_item, s_flag;
     __shared__ A s_red[AW][NB];
     __shared__ A s_t[NB];
+    extern __shared__ __align__(16) unsigned char sweep_smem[];
+    T* Ds = (T*)sweep_smem;                      // NB x NB inverted diagonal block
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(ticket, 1);
@@ -193,6 +213,7 @@ __global__ void __launch_bounds__(AT) k_bwd_sweep(const FrontDesc* __restrict__ 
         if (it >= n_items) return;
         const int slot = items[it] >> 16, cb = items[it] & 0xffff;
         const FrontDesc f = fronts[slot];
+        prefetch_block(Ds, (const T*)f.Dinv + (int64_t)cb * NB * NB);
         const int c0 = cb * NB, c1 = min(c0 + NB, f.s), cw = c1 - c0;
         const T* P = (const T*)f.P;
         A* v = (A*)f.vec;
@@ -251,10 +272,11 @@ __global__ void __launch_bounds__(AT) k_bwd_sweep(const FrontDesc* __restrict__ 
         }
         __syncthreads();
         // x = Dinv^T t : x_c = sum_{r >= c} Dinv[r][c] t_r  (column sums, warps over rows)
-        const T* D = (const T*)f.Dinv + (int64_t)cb * NB * NB;
+        cp_async_wait();
+        __syncthreads();
         for (int c = lane; c < NB; c += 32) {
             A s = 0;
-            for (int rr = warp; rr < cw; rr += AW) s += (A)D[rr * NB + c] * s_t[rr];
+            for (int rr = warp; rr < cw; rr += AW) s += (A)Ds[rr * NB + c] * s_t[rr];
             s_red[warp][c] = s;
         }
         __syncthreads();
@@ -277,7 +299,21 @@ double level_factor_bytes(const Level& L) {
 }
 
 template <typename T, typename A>
+int sweep_smem_setup() {
+    static bool done = false;
+    const int bytes = NB * NB * (int)sizeof(T);
+    if (!done) {
+        RSD_CUDA_TRY(cudaFuncSetAttribute(k_fwd_sweep<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        RSD_CUDA_TRY(cudaFuncSetAttribute(k_bwd_sweep<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        done = true;
+    }
+    return RSD_OK;
+}
+
+template <typename T, typename A>
 int sweep_level(Handle& h, int li, bool forward, const double* r, double* z, int tk) {
+    RSD_TRY((sweep_smem_setup<T, A>()));
+    const int dsm = NB * NB * (int)sizeof(T);
     Level& L = h.levels[li];
     const int nf = (int)L.fronts.size();
     double gbytes = 0;
@@ -298,7 +334,7 @@ int sweep_level(Handle& h, int li, bool forward, const double* r, double* z, int
         RSD_CUDA_TRY(cudaGetLastError());
         if (L.n_fwd_items) {
             const int pi = prof_begin(h, K_FWD);
-            k_fwd_sweep<T, A><<<grid, AT, 0, h.stream>>>(L.d_fronts, L.d_fwd_items, L.n_fwd_items, h.d_ticket + tk, h.d_err);
+            k_fwd_sweep<T, A><<<grid, AT, dsm, h.stream>>>(L.d_fronts, L.d_fwd_items, L.n_fwd_items, h.d_ticket + tk, h.d_err);
             count_launch();
             prof_end(h, pi, fbytes / sizeof(T) * 2.0, fbytes);
         }
@@ -310,7 +346,7 @@ int sweep_level(Handle& h, int li, bool forward, const double* r, double* z, int
         RSD_CUDA_TRY(cudaGetLastError());
         if (L.n_bwd_items) {
             const int pi = prof_begin(h, K_BWD);
-            k_bwd_sweep<T, A><<<grid, AT, 0, h.stream>>>(L.d_fronts, L.d_bwd_items, L.n_bwd_items, h.d_ticket + tk, h.d_err, z);
+            k_bwd_sweep<T, A><<<grid, AT, dsm, h.stream>>>(L.d_fronts, L.d_bwd_items, L.n_bwd_items, h.d_ticket + tk, h.d_err, z);
             count_launch();
             prof_end(h, pi, fbytes / sizeof(T) * 2.0, fbytes);
         }
@@ -358,6 +394,8 @@ size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 template <typename T, typename A>
 int sweep_level_static(Handle& h, int li, bool forward, const double* r, double* z, int* ticket,
                        FrontDesc* const* lvl_fronts) {
+    RSD_TRY((sweep_smem_setup<T, A>()));
+    const int dsm = NB * NB * (int)sizeof(T);
     Level& L = h.levels[li];
     const int nf = (int)L.fronts.size();
     FrontDesc* fr = lvl_fronts[li];
@@ -373,7 +411,7 @@ int sweep_level_static(Handle& h, int li, bool forward, const double* r, double*
         count_launch();
         RSD_CUDA_TRY(cudaGetLastError());
         if (L.n_fwd_items) {
-            k_fwd_sweep<T, A><<<grid, AT, 0, h.stream>>>(fr, L.d_fwd_items, L.n_fwd_items, ticket, h.d_err);
+            k_fwd_sweep<T, A><<<grid, AT, dsm, h.stream>>>(fr, L.d_fwd_items, L.n_fwd_items, ticket, h.d_err);
             count_launch();
         }
     } else {
@@ -381,7 +419,7 @@ int sweep_level_static(Handle& h, int li, bool forward, const double* r, double*
         count_launch();
         RSD_CUDA_TRY(cudaGetLastError());
         if (L.n_bwd_items) {
-            k_bwd_sweep<T, A><<<grid, AT, 0, h.stream>>>(fr, L.d_bwd_items, L.n_bwd_items, ticket, h.d_err, z);
+            k_bwd_sweep<T, A><<<grid, AT, dsm, h.stream>>>(fr, L.d_bwd_items, L.n_bwd_items, ticket, h.d_err, z);
             count_launch();
         }
     }

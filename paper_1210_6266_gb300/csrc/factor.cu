@@ -9,8 +9,10 @@
 //   children's contributions that land on B).
 // Storage (row-major, lower triangles): P = [L; X] is N x ldp, U is b x ldu.
 //
-// The partial Cholesky is left-looking by NB-wide column panels:
-//   (a) P[k:N, k:k+w] -= P[k:N, 0:k] P[k:k+w, 0:k]^T          (GEMM, K = k)
+// The partial Cholesky is left-looking by NB-wide column panels, blocked in two levels
+// (outer panels of WOUT = 4 NB columns starting at K0):
+//   (a0) at k = K0: P[K0:N, K0:K0+WOUT] -= P[K0:N, 0:K0] P[K0:K0+WOUT, 0:K0]^T  (K = K0)
+//   (a) P[k:N, k:k+w] -= P[k:N, K0:k] P[k:k+w, K0:k]^T      (GEMM, K = k - K0 < WOUT)
 //   (b) L_kk L_kk^T = P[k:k+w, k:k+w]; Dinv_k = L_kk^-1         (one CTA per front)
 //   (c) P[k+w:N, k:k+w] <- P[k+w:N, k:k+w] Dinv_k^T             (TRSM as a GEMM, K = w)
 // and after the last panel
@@ -100,6 +102,7 @@ __global__ void k_extend_add(const FrontDesc* __restrict__ parents, const FrontD
 // SIMT batched GEMM:  C = beta*C + alpha * A B^T, 64x64 tiles, 256 threads, 4x4 per thread.
 // ---------------------------------------------------------------------------------
 constexpr int SB = 64;     // tile edge
+constexpr int WOUT = 4 * NB;   // outer panel width of the two-level left-looking update
 template <typename T> struct SimtK { static constexpr int BK = 16; };
 template <> struct SimtK<float> { static constexpr int BK = 32; };
 
@@ -180,72 +183,169 @@ __global__ void __launch_bounds__(256) k_gemm_simt(const GemmTask* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------------
-// Diagonal block: Cholesky of P[k:k+w, k:k+w] in shared memory, written back to P, then
-// inverted in place (lower triangular) and stored as Dinv_k (NB x NB, zero padded).
+// Diagonal block: Cholesky of P[k:k+w, k:k+w] (w <= NB) in shared memory, written back to
+// P, then inverted in place and stored as Dinv_k (NB x NB, zero padded).  Blocked by
+// 32-wide sub-panels: a sub-panel's 32 x 32 diagonal block is factored in registers by one
+// warp (row per lane, shuffles), the rows below it are solved one row per thread, and the
+// trailing block is updated with 4 x 4 register tiles.  The inverse inverts the 32 x 32
+// diagonal blocks in parallel (one warp each, column per lane) and then fills the block
+// columns right to left: X_21 = -X_22 L_21 X_11.
 // One CTA per front whose interface extends past k.
 // ---------------------------------------------------------------------------------
+constexpr int DLD = NB + 1;     // shared-memory row stride of the block
+constexpr int TLD = 33;         // row stride of the 32-column scratch panel
+
+template <typename T>
+__device__ __forceinline__ T shfl(T v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_potrf_diag(const FrontDesc* __restrict__ fronts, int k,
                                                    int* __restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
-    T* A = (T*)smem_raw;                     // NB x (NB+1)
-    constexpr int LD = NB + 1;
+    T* A = (T*)smem_raw;                      // NB x DLD
+    T* Tm = A + NB * DLD;                     // (NB - 32) x TLD scratch
     const FrontDesc f = fronts[blockIdx.x];
     if (f.s <= k) return;
     const int w = min(NB, f.s - k);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     T* P = (T*)f.P;
-    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-        const int r = e / w, c = e % w;
-        A[r * LD + c] = (c <= r) ? P[(int64_t)(k + r) * f.ldp + (k + c)] : (T)0;
-    }
     __shared__ int bad;
-    if (threadIdx.x == 0) bad = 0;
+    if (tid == 0) bad = 0;
+    for (int e = tid; e < NB * NB; e += 256) {
+        const int r = e / NB, c = e % NB;
+        A[r * DLD + c] = (r < w && c <= r) ? P[(int64_t)(k + r) * f.ldp + (k + c)] : (T)0;
+    }
     __syncthreads();
-    for (int j = 0; j < w; ++j) {
-        if (threadIdx.x == 0) {
-            const T d = A[j * LD + j];
-            if (!(d > (T)0)) { bad = 1; A[j * LD + j] = (T)1; }
-            else A[j * LD + j] = sqrt(d);
+    const int npb = (w + 31) / 32;
+    // ---- Cholesky ----
+    for (int p = 0; p < npb; ++p) {
+        const int c0 = p * 32, pw = min(32, w - c0);
+        if (warp == 0) {
+            T v[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = (lane < pw && j <= lane) ? A[(c0 + lane) * DLD + c0 + j] : (T)0;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                if (j < pw) {
+                    T d = shfl(v[j], j);
+                    if (!(d > (T)0)) { if (lane == 0) bad = 1; d = (T)1; }
+                    const T piv = sqrt(d), inv = (T)1 / piv;
+                    if (lane == j) v[j] = piv;
+                    else if (lane > j) v[j] *= inv;
+#pragma unroll
+                    for (int kk = j + 1; kk < 32; ++kk) {
+                        const T lk = shfl(v[j], kk);
+                        if (lane >= kk) v[kk] -= v[j] * lk;
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (lane < pw && j <= lane) A[(c0 + lane) * DLD + c0 + j] = v[j];
         }
         __syncthreads();
-        const T djj = A[j * LD + j];
-        for (int i = j + 1 + threadIdx.x; i < w; i += blockDim.x) A[i * LD + j] /= djj;
+        const int r0 = c0 + pw;
+        for (int r = r0 + tid; r < w; r += 256) {          // rows below: x L_pp^T = a
+            T x[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                if (j < pw) {
+                    T s = A[r * DLD + c0 + j];
+#pragma unroll
+                    for (int kk = 0; kk < j; ++kk) s -= x[kk] * A[(c0 + j) * DLD + c0 + kk];
+                    x[j] = s / A[(c0 + j) * DLD + c0 + j];
+                } else {
+                    x[j] = (T)0;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (j < pw) A[r * DLD + c0 + j] = x[j];
+        }
         __syncthreads();
-        const int rem = w - j - 1;
-        for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
-            const int i = j + 1 + e / rem, l = j + 1 + e % rem;
-            if (l <= i) A[i * LD + l] -= A[i * LD + j] * A[l * LD + j];
+        const int rem = w - r0;                              // trailing update, 4 x 4 tiles
+        const int nt = (rem + 3) / 4;
+        for (int t = tid; t < nt * nt; t += 256) {
+            const int tr = t / nt, tc = t % nt;
+            if (tc > tr) continue;
+            T acc[4][4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+            const int ra = r0 + 4 * tr, cb = r0 + 4 * tc;
+            for (int kk = 0; kk < pw; ++kk) {
+                T av[4], bv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    av[u] = ra + u < w ? A[(ra + u) * DLD + c0 + kk] : (T)0;
+                    bv[u] = cb + u < w ? A[(cb + u) * DLD + c0 + kk] : (T)0;
+                }
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    if (ra + a < w && cb + b <= ra + a) A[(ra + a) * DLD + cb + b] -= acc[a][b];
         }
         __syncthreads();
     }
-    if (bad && threadIdx.x == 0) {
+    if (bad && tid == 0) {
         atomicExch(&err[ERR_NOT_SPD], 1);
         atomicMin(&err[ERR_NOT_SPD_NODE], f.node);
     }
-    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+    for (int e = tid; e < w * w; e += 256) {
         const int r = e / w, c = e % w;
-        if (c <= r) P[(int64_t)(k + r) * f.ldp + (k + c)] = A[r * LD + c];
+        if (c <= r) P[(int64_t)(k + r) * f.ldp + (k + c)] = A[r * DLD + c];
+    }
+    // ---- inverse: 32 x 32 diagonal blocks, one warp each, column c per lane ----
+    if (warp < npb) {
+        const int c0 = warp * 32, pw = min(32, w - c0);
+        T x[32];
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+            if (r < pw && r >= lane) {
+                T s = (r == lane) ? (T)1 : (T)0;
+#pragma unroll
+                for (int m = 0; m < r; ++m)
+                    if (m >= lane) s -= A[(c0 + r) * DLD + c0 + m] * x[m];
+                x[r] = s / A[(c0 + r) * DLD + c0 + r];
+            } else {
+                x[r] = (T)0;
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < 32; ++r)
+            if (r < pw && lane < pw && r >= lane) A[(c0 + r) * DLD + c0 + lane] = x[r];
     }
     __syncthreads();
-    // in-place inverse of the lower triangular block, columns right to left:
-    // column j of L^-1 below the diagonal is -(1/L_jj) * Linv[j+1:, j+1:] L[j+1:, j]
-    __shared__ T tmp[NB];
-    for (int j = w - 1; j >= 0; --j) {
-        const T ajj = (T)1 / A[j * LD + j];
-        for (int i = j + 1 + threadIdx.x; i < w; i += blockDim.x) {
+    // ---- block columns right to left: X_21 = -(X_22 L_21) X_11 ----
+    for (int j = npb - 2; j >= 0; --j) {
+        const int c0 = j * 32, b0 = c0 + 32, rows = w - b0;
+        for (int e = tid; e < rows * 32; e += 256) {          // Tm = X_22 * L_21
+            const int i = e / 32, c = e % 32;
             T s = 0;
-            for (int l = j + 1; l <= i; ++l) s += A[i * LD + l] * A[l * LD + j];
-            tmp[i] = -s * ajj;
+            for (int m = b0; m <= b0 + i; ++m) s += A[(b0 + i) * DLD + m] * A[m * DLD + c0 + c];
+            Tm[i * TLD + c] = s;
         }
         __syncthreads();
-        for (int i = j + 1 + threadIdx.x; i < w; i += blockDim.x) A[i * LD + j] = tmp[i];
-        if (threadIdx.x == 0) A[j * LD + j] = ajj;
+        for (int e = tid; e < rows * 32; e += 256) {          // A_21 = -Tm * X_11
+            const int i = e / 32, c = e % 32;
+            T s = 0;
+            for (int m = c; m < 32; ++m) s += Tm[i * TLD + m] * A[(c0 + m) * DLD + c0 + c];
+            A[(b0 + i) * DLD + c0 + c] = -s;
+        }
         __syncthreads();
     }
     T* D = (T*)f.Dinv + (int64_t)(k / NB) * NB * NB;
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    for (int e = tid; e < NB * NB; e += 256) {
         const int r = e / NB, c = e % NB;
-        D[e] = (r < w && c <= r) ? A[r * LD + c] : (T)0;
+        D[e] = (r < w && c <= r) ? A[r * DLD + c] : (T)0;
     }
 }
 
@@ -409,7 +509,7 @@ int run_factor_level(Handle& h, int li) {
     // task buffer for this level: one slot per front per launch kind
     GemmTask* d_tasks = nullptr;
     RSD_CUDA_TRY(cudaMallocAsync((void**)&d_tasks, sizeof(GemmTask) * L.fronts.size() * 2 + 64, h.stream));
-    const size_t potrf_smem = (size_t)NB * (NB + 1) * es;
+    const size_t potrf_smem = (size_t)NB * DLD * es + (size_t)(NB - 32) * TLD * es;
     const size_t trsm_smem = (size_t)NB * NB * es + (size_t)TR_ROWS * (NB + 1) * es;
     if (f64) {
         RSD_CUDA_TRY(cudaFuncSetAttribute(k_potrf_diag<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)potrf_smem));
@@ -420,30 +520,55 @@ int run_factor_level(Handle& h, int li) {
     }
     std::vector<GemmTask> tasks;
     int rc = RSD_OK;
+    auto run_gemm = [&](int kind) -> int {
+        if (tasks.empty()) return RSD_OK;
+        if (tc) return gemm_tc_launch(h, li, tasks, kind, h.stream);
+        finalize_tasks(tasks, SB, SB);
+        return f64 ? launch_gemm_simt<double>(h, tasks, d_tasks, -1.0, h.stream)
+                   : launch_gemm_simt<float>(h, tasks, d_tasks, -1.0f, h.stream);
+    };
     for (int k = 0; k < L.max_s && rc == RSD_OK; k += NB) {
-        // (a) panel update from all previous panels
-        if (k > 0) {
+        const int K0 = (k / WOUT) * WOUT;               // start of the enclosing outer panel
+        // (a0) at an outer panel start: update the whole WOUT-wide panel from all columns
+        //      left of it (one large-K GEMM per outer panel)
+        if (k == K0 && K0 > 0) {
+            tasks.clear();
+            for (auto& f : L.fronts) {
+                if (f.s <= K0) continue;
+                const int W = std::min(WOUT, f.s - K0);
+                GemmTask t{};
+                t.A = (const char*)f.P + ((int64_t)K0 * f.ldp) * es;
+                t.B = t.A;
+                t.C = (char*)f.P + ((int64_t)K0 * f.ldp + K0) * es;
+                t.lda = t.ldb = t.ldc = f.ldp;
+                t.M = f.N - K0; t.N = W; t.K = K0;
+                t.lower = 0; t.beta = 1;
+                t.map_a = t.map_b = f.node;
+                t.a_r0 = K0; t.a_c0 = 0; t.b_r0 = K0; t.b_c0 = 0;
+                tasks.push_back(t);
+            }
+            rc = run_gemm(3);
+            if (rc != RSD_OK) break;
+        }
+        // (a) inner update of the NB-wide panel from the finished columns K0..k of its
+        //     outer panel
+        if (k > K0) {
             tasks.clear();
             for (auto& f : L.fronts) {
                 if (f.s <= k) continue;
                 const int w = std::min(NB, f.s - k);
                 GemmTask t{};
-                t.A = (const char*)f.P + ((int64_t)k * f.ldp) * es;
+                t.A = (const char*)f.P + ((int64_t)k * f.ldp + K0) * es;
                 t.B = t.A;
                 t.C = (char*)f.P + ((int64_t)k * f.ldp + k) * es;
                 t.lda = t.ldb = t.ldc = f.ldp;
-                t.M = f.N - k; t.N = w; t.K = k;
+                t.M = f.N - k; t.N = w; t.K = k - K0;
                 t.lower = 0; t.beta = 1;
-                t.map_a = t.map_b = f.node;   // slot resolved by the tensor-core path
-                t.a_r0 = k; t.a_c0 = 0; t.b_r0 = k; t.b_c0 = 0;
+                t.map_a = t.map_b = f.node;
+                t.a_r0 = k; t.a_c0 = K0; t.b_r0 = k; t.b_c0 = K0;
                 tasks.push_back(t);
             }
-            if (tc) rc = gemm_tc_launch(h, li, tasks, 0, h.stream);
-            else {
-                finalize_tasks(tasks, SB, SB);
-                rc = f64 ? launch_gemm_simt<double>(h, tasks, d_tasks, -1.0, h.stream)
-                         : launch_gemm_simt<float>(h, tasks, d_tasks, -1.0f, h.stream);
-            }
+            rc = run_gemm(0);
             if (rc != RSD_OK) break;
         }
         // (b) diagonal block factor + inverse
