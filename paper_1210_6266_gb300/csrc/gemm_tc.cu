@@ -19,6 +19,7 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <array>
 #include <cstring>
 #include <vector>
 
@@ -30,11 +31,16 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int BK = 32;                       // FP32 elements per 128-byte swizzle row
-constexpr int STAGES = 4;
 constexpr int TC_THREADS = 192;
 constexpr long long TC_WAIT_CYCLES = 2000000000LL;   // ~1 s
+constexpr int SPLIT_MIN_KB = 16;             // at least 16 x 32 K per split-K slice
 
-struct TcTile { int task, tm, tn, pad; };
+// One CTA's work: output tile (tm, tn) of a task over K blocks [kb0, kb1).  ws_slot < 0:
+// write C directly; otherwise write the raw partial product to workspace slot ws_slot
+// (split-K), to be summed in fixed order by k_splitk_reduce.
+struct TcTile { int task, tm, tn, kb0, kb1, ws_slot, pad0, pad1; };
+// One split-K output tile: partials in slots [slot0, slot0 + nsplit).
+struct TcRed { int task, tm, tn, slot0, nsplit, pad0, pad1, pad2; };
 
 struct TcTask {               // device view of one GEMM task
     float* C;
@@ -129,6 +135,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 
 template <int BN>
 struct Smem {
+    static constexpr int STAGES = BN == 128 ? 6 : 4;
     static constexpr int A_BYTES = BM * BK * 4;
     static constexpr int B_BYTES = BN * BK * 4;
     static constexpr int STAGE = A_BYTES + B_BYTES;
@@ -138,9 +145,10 @@ struct Smem {
 template <int BN>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_gemm_tc(const TcTask* __restrict__ tasks, const TcTile* __restrict__ tiles,
-          const CUtensorMap* __restrict__ maps, int* __restrict__ err) {
+          const CUtensorMap* __restrict__ maps, float* __restrict__ ws, int* __restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
     using S = Smem<BN>;
+    constexpr int STAGES = S::STAGES;
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023) & ~1023u;
     unsigned char* sbase = smem_raw + (base - raw);
@@ -153,7 +161,7 @@ k_gemm_tc(const TcTask* __restrict__ tasks, const TcTile* __restrict__ tiles,
     const TcTile tl = tiles[blockIdx.x];
     const TcTask tk = tasks[tl.task];
     const int m0 = tl.tm * BM, n0 = tl.tn * BN;
-    const int nk = (tk.K + BK - 1) / BK;
+    const int kb0 = tl.kb0, nk = tl.kb1 - tl.kb0;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -184,10 +192,11 @@ k_gemm_tc(const TcTask* __restrict__ tasks, const TcTile* __restrict__ tiles,
                 const uint32_t sa = base + s * S::STAGE;
                 const uint32_t sb = sa + S::A_BYTES;
                 mbar_expect_tx(bar_full + 8 * s, S::STAGE);
-                tma_load_2d(sa, ma, tk.a_c0 + kb * BK, tk.a_r0 + m0, bar_full + 8 * s);
+                const int kx = (kb0 + kb) * BK;
+                tma_load_2d(sa, ma, tk.a_c0 + kx, tk.a_r0 + m0, bar_full + 8 * s);
 #pragma unroll
                 for (int h = 0; h < BN / 128; ++h)
-                    tma_load_2d(sb + h * 128 * BK * 4, mb, tk.b_c0 + kb * BK, tk.b_r0 + n0 + h * 128, bar_full + 8 * s);
+                    tma_load_2d(sb + h * 128 * BK * 4, mb, tk.b_c0 + kx, tk.b_r0 + n0 + h * 128, bar_full + 8 * s);
             }
         }
     } else if (warp == 1) {
@@ -217,11 +226,20 @@ k_gemm_tc(const TcTask* __restrict__ tasks, const TcTile* __restrict__ tiles,
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int gr = m0 + row;
         float* crow = tk.C + (int64_t)gr * tk.ldc;
+        float* wrow = tl.ws_slot >= 0 ? ws + ((int64_t)tl.ws_slot * BM + row) * BN : nullptr;
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 32) {
             uint32_t r[32];
             tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + c0, r);
-            if (!ok || gr >= tk.M) continue;
+            if (!ok) continue;
+            if (wrow) {                                   // split-K partial: raw product
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    *(float4*)(wrow + c0 + 4 * q) = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                                                                __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+                continue;
+            }
+            if (gr >= tk.M) continue;
             const int gc0 = n0 + c0;
             if (gc0 >= tk.N) continue;
             if (tk.lower && gc0 > gr) continue;
@@ -253,6 +271,24 @@ k_gemm_tc(const TcTask* __restrict__ tasks, const TcTile* __restrict__ tiles,
     if (warp == 1) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+    }
+}
+
+// Split-K reduction: C = beta*C + alpha * sum_s partial_s, summed in slot order.
+template <int BN>
+__global__ void __launch_bounds__(256) k_splitk_reduce(const TcTask* __restrict__ tasks, const TcRed* __restrict__ reds,
+                                                       const float* __restrict__ ws) {
+    const TcRed rd = reds[blockIdx.x];
+    const TcTask tk = tasks[rd.task];
+    const int m0 = rd.tm * BM, n0 = rd.tn * BN;
+    for (int e = threadIdx.x; e < BM * BN; e += blockDim.x) {
+        const int row = e / BN, col = e % BN;
+        const int gr = m0 + row, gc = n0 + col;
+        if (gr >= tk.M || gc >= tk.N || (tk.lower && gc > gr)) continue;
+        float v = 0.f;
+        for (int sp = 0; sp < rd.nsplit; ++sp) v += ws[((int64_t)(rd.slot0 + sp) * BM + row) * BN + col];
+        float* p = tk.C + (int64_t)gr * tk.ldc + gc;
+        *p = (tk.beta ? *p : 0.f) + tk.alpha * v;
     }
 }
 
@@ -291,7 +327,10 @@ struct TcState {
     CUtensorMap* d_maps = nullptr;      // 2 per tree node: [L; X] panel, inverted diagonal blocks
     TcTask* d_tasks = nullptr;
     TcTile* d_tiles = nullptr;
-    size_t cap_tasks = 0, cap_tiles = 0;
+    TcRed* d_reds = nullptr;
+    float* d_ws = nullptr;              // split-K partial products
+    size_t cap_tasks = 0, cap_tiles = 0, cap_reds = 0;
+    int ws_slots = 0;                   // capacity in BM x 256 tiles
     bool attr_set = false;
 };
 
@@ -317,6 +356,8 @@ int gemm_tc_prepare(Handle& h) {
         }
     }
     RSD_CUDA_TRY(cudaMalloc((void**)&st->d_maps, maps.size() * sizeof(CUtensorMap)));
+    st->ws_slots = 2 * h.num_sms;
+    RSD_CUDA_TRY(cudaMalloc((void**)&st->d_ws, (size_t)st->ws_slots * BM * 256 * sizeof(float)));
     RSD_CUDA_TRY(cudaMemcpy(st->d_maps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
     return RSD_OK;
 }
@@ -327,17 +368,20 @@ void gemm_tc_release(Handle& h) {
     cudaFree(st->d_maps);
     cudaFree(st->d_tasks);
     cudaFree(st->d_tiles);
+    cudaFree(st->d_reds);
+    cudaFree(st->d_ws);
     delete st;
     h.tc_state = nullptr;
 }
 
-// kind 0: panel update, 1: panel solve (B = inverted diagonal block), 2: U -= X X^T.
+// kind 0: inner panel update, 1: panel solve (B = inverted diagonal block),
+// 2: U -= X X^T (lower tiles), 3: outer panel update.
 int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, int kind, cudaStream_t stream) {
     TcState* st = state_of(h);
     if (!st || tasks.empty()) return st ? RSD_OK : RSD_ERR_ARG;
-    const int bn = kind == 2 ? 256 : 128;
+    const int bn = (kind == 2 || kind == 3) ? 256 : 128;
     std::vector<TcTask> tt(tasks.size());
-    std::vector<TcTile> tl;
+    std::vector<std::array<int, 3>> out;            // (task, tm, tn) output tiles
     for (size_t i = 0; i < tasks.size(); ++i) {
         const GemmTask& g = tasks[i];
         TcTask& t = tt[i];
@@ -352,22 +396,45 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
         for (int a = 0; a < tm; ++a)
             for (int b = 0; b < tn; ++b) {
                 if (g.lower && b * bn > a * BM + BM - 1) continue;
-                tl.push_back({(int)i, a, b, 0});
+                out.push_back({(int)i, a, b});
             }
     }
-    if (tl.empty()) return RSD_OK;
-    if (tt.size() > st->cap_tasks) {
-        cudaFreeAsync(st->d_tasks, stream);
-        st->cap_tasks = std::max(tt.size(), 2 * st->cap_tasks);
-        RSD_CUDA_TRY(cudaMallocAsync((void**)&st->d_tasks, st->cap_tasks * sizeof(TcTask), stream));
+    if (out.empty()) return RSD_OK;
+    // split K when the output tiles cannot fill the GPU (never for the in-place panel solve)
+    int max_kb = 0;
+    for (auto& g : tasks) max_kb = std::max(max_kb, (g.K + BK - 1) / BK);
+    int nsplit = 1;
+    if (kind != 1 && (int)out.size() < h.num_sms)
+        nsplit = std::max(1, std::min(h.num_sms / (int)out.size(), max_kb / SPLIT_MIN_KB));
+    if ((int)out.size() * nsplit * (bn / 256 > 0 ? bn / 256 : 1) > st->ws_slots * (256 / bn)) nsplit = 1;
+    std::vector<TcTile> tl;
+    std::vector<TcRed> rd;
+    int slot = 0;
+    for (auto& o : out) {
+        const int nkb = (tasks[o[0]].K + BK - 1) / BK;
+        const int ns = std::max(1, std::min(nsplit, nkb / SPLIT_MIN_KB));
+        if (ns == 1) {
+            tl.push_back({o[0], o[1], o[2], 0, nkb, -1, 0, 0});
+            continue;
+        }
+        rd.push_back({o[0], o[1], o[2], slot, ns, 0, 0, 0});
+        for (int sp = 0; sp < ns; ++sp)
+            tl.push_back({o[0], o[1], o[2], (int)((int64_t)nkb * sp / ns), (int)((int64_t)nkb * (sp + 1) / ns), slot++, 0, 0});
     }
-    if (tl.size() > st->cap_tiles) {
-        cudaFreeAsync(st->d_tiles, stream);
-        st->cap_tiles = std::max(tl.size(), 2 * st->cap_tiles);
-        RSD_CUDA_TRY(cudaMallocAsync((void**)&st->d_tiles, st->cap_tiles * sizeof(TcTile), stream));
-    }
+    auto grow = [&](auto*& ptr, size_t& cap, size_t need, size_t elem) -> int {
+        if (need <= cap) return RSD_OK;
+        cudaFreeAsync(ptr, stream);
+        cap = std::max(need, 2 * cap);
+        RSD_CUDA_TRY(cudaMallocAsync((void**)&ptr, cap * elem, stream));
+        return RSD_OK;
+    };
+    RSD_TRY(grow(st->d_tasks, st->cap_tasks, tt.size(), sizeof(TcTask)));
+    RSD_TRY(grow(st->d_tiles, st->cap_tiles, tl.size(), sizeof(TcTile)));
+    if (!rd.empty()) RSD_TRY(grow(st->d_reds, st->cap_reds, rd.size(), sizeof(TcRed)));
     RSD_CUDA_TRY(cudaMemcpyAsync(st->d_tasks, tt.data(), tt.size() * sizeof(TcTask), cudaMemcpyHostToDevice, stream));
     RSD_CUDA_TRY(cudaMemcpyAsync(st->d_tiles, tl.data(), tl.size() * sizeof(TcTile), cudaMemcpyHostToDevice, stream));
+    if (!rd.empty())
+        RSD_CUDA_TRY(cudaMemcpyAsync(st->d_reds, rd.data(), rd.size() * sizeof(TcRed), cudaMemcpyHostToDevice, stream));
     if (!st->attr_set) {
         RSD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<128>::TOTAL));
         RSD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<256>::TOTAL));
@@ -381,10 +448,15 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
     }
     const int pi = prof_begin(h, K_GEMM_TC);
     if (bn == 128)
-        k_gemm_tc<128><<<(unsigned)tl.size(), TC_THREADS, Smem<128>::TOTAL, stream>>>(st->d_tasks, st->d_tiles, st->d_maps, h.d_err);
+        k_gemm_tc<128><<<(unsigned)tl.size(), TC_THREADS, Smem<128>::TOTAL, stream>>>(st->d_tasks, st->d_tiles, st->d_maps, st->d_ws, h.d_err);
     else
-        k_gemm_tc<256><<<(unsigned)tl.size(), TC_THREADS, Smem<256>::TOTAL, stream>>>(st->d_tasks, st->d_tiles, st->d_maps, h.d_err);
+        k_gemm_tc<256><<<(unsigned)tl.size(), TC_THREADS, Smem<256>::TOTAL, stream>>>(st->d_tasks, st->d_tiles, st->d_maps, st->d_ws, h.d_err);
     count_launch();
+    if (!rd.empty()) {
+        if (bn == 128) k_splitk_reduce<128><<<(unsigned)rd.size(), 256, 0, stream>>>(st->d_tasks, st->d_reds, st->d_ws);
+        else k_splitk_reduce<256><<<(unsigned)rd.size(), 256, 0, stream>>>(st->d_tasks, st->d_reds, st->d_ws);
+        count_launch();
+    }
     prof_end(h, pi, fl, by);
     RSD_CUDA_TRY(cudaGetLastError());
     return RSD_OK;
