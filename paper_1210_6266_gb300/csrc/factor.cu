@@ -199,8 +199,20 @@ template <typename T>
 __device__ __forceinline__ T shfl(T v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 
 template <typename T>
+__device__ __forceinline__ T store_round(T x, bool rnd);
+template <>
+__device__ __forceinline__ double store_round(double x, bool) { return x; }
+template <>
+__device__ __forceinline__ float store_round(float x, bool rnd) {
+    if (!rnd) return x;
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+template <typename T>
 __global__ void __launch_bounds__(256) k_potrf_diag(const FrontDesc* __restrict__ fronts, int k,
-                                                   int* __restrict__ err) {
+                                                   int* __restrict__ err, int round_tf32) {
     extern __shared__ unsigned char smem_raw[];
     T* A = (T*)smem_raw;                      // NB x DLD
     T* Tm = A + NB * DLD;                     // (NB - 32) x TLD scratch
@@ -300,7 +312,7 @@ __global__ void __launch_bounds__(256) k_potrf_diag(const FrontDesc* __restrict_
     }
     for (int e = tid; e < w * w; e += 256) {
         const int r = e / w, c = e % w;
-        if (c <= r) P[(int64_t)(k + r) * f.ldp + (k + c)] = A[r * DLD + c];
+        if (c <= r) P[(int64_t)(k + r) * f.ldp + (k + c)] = store_round(A[r * DLD + c], round_tf32 != 0);
     }
     // ---- inverse: 32 x 32 diagonal blocks, one warp each, column c per lane ----
     if (warp < npb) {
@@ -345,7 +357,7 @@ __global__ void __launch_bounds__(256) k_potrf_diag(const FrontDesc* __restrict_
     T* D = (T*)f.Dinv + (int64_t)(k / NB) * NB * NB;
     for (int e = tid; e < NB * NB; e += 256) {
         const int r = e / NB, c = e % NB;
-        D[e] = (r < w && c <= r) ? A[r * DLD + c] : (T)0;
+        D[e] = (r < w && c <= r) ? store_round(A[r * DLD + c], round_tf32 != 0) : (T)0;
     }
 }
 
@@ -576,8 +588,8 @@ int run_factor_level(Handle& h, int li) {
         for (auto& f : L.fronts)
             if (f.s > k) { const double w = std::min(NB, f.s - k); pf += 2.0 * w * w * w / 3.0; pb += (2.0 * w * w + NB * NB) * es; }
         const int ppi = prof_begin(h, K_POTRF);
-        if (f64) k_potrf_diag<double><<<(unsigned)L.fronts.size(), 256, potrf_smem, h.stream>>>(L.d_fronts, k, h.d_err);
-        else k_potrf_diag<float><<<(unsigned)L.fronts.size(), 256, potrf_smem, h.stream>>>(L.d_fronts, k, h.d_err);
+        if (f64) k_potrf_diag<double><<<(unsigned)L.fronts.size(), 256, potrf_smem, h.stream>>>(L.d_fronts, k, h.d_err, 0);
+        else k_potrf_diag<float><<<(unsigned)L.fronts.size(), 256, potrf_smem, h.stream>>>(L.d_fronts, k, h.d_err, tc ? 1 : 0);
         count_launch();
         prof_end(h, ppi, pf, pb);
         if (cudaGetLastError() != cudaSuccess) { rc = RSD_ERR_CUDA; break; }

@@ -49,7 +49,15 @@ struct TcTask {               // device view of one GEMM task
     int map_a, map_b;
     int a_r0, a_c0, b_r0, b_c0;
     float alpha;
+    int round_tf32;           // round stored results to the nearest TF32 value
 };
+
+// Round to the nearest TF32 value (10-bit mantissa), kept as an FP32 bit pattern.
+__device__ __forceinline__ float tf32_rn(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -252,6 +260,7 @@ k_gemm_tc(const TcTask* __restrict__ tasks, const TcTile* __restrict__ tiles,
                     o.y += tk.alpha * __uint_as_float(r[4 * q + 1]);
                     o.z += tk.alpha * __uint_as_float(r[4 * q + 2]);
                     o.w += tk.alpha * __uint_as_float(r[4 * q + 3]);
+                    if (tk.round_tf32) { o.x = tf32_rn(o.x); o.y = tf32_rn(o.y); o.z = tf32_rn(o.z); o.w = tf32_rn(o.w); }
                     *p = o;
                 }
             } else {
@@ -260,7 +269,8 @@ k_gemm_tc(const TcTask* __restrict__ tasks, const TcTile* __restrict__ tiles,
                     const int gc = gc0 + q;
                     if (gc < tk.N && (!tk.lower || gc <= gr)) {
                         float* p = crow + gc;
-                        *p = (tk.beta ? *p : 0.f) + tk.alpha * __uint_as_float(r[q]);
+                        const float o = (tk.beta ? *p : 0.f) + tk.alpha * __uint_as_float(r[q]);
+                        *p = tk.round_tf32 ? tf32_rn(o) : o;
                     }
                 }
             }
@@ -288,7 +298,8 @@ __global__ void __launch_bounds__(256) k_splitk_reduce(const TcTask* __restrict_
         float v = 0.f;
         for (int sp = 0; sp < rd.nsplit; ++sp) v += ws[((int64_t)(rd.slot0 + sp) * BM + row) * BN + col];
         float* p = tk.C + (int64_t)gr * tk.ldc + gc;
-        *p = (tk.beta ? *p : 0.f) + tk.alpha * v;
+        const float o = (tk.beta ? *p : 0.f) + tk.alpha * v;
+        *p = tk.round_tf32 ? tf32_rn(o) : o;
     }
 }
 
@@ -392,6 +403,7 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
         t.map_b = 2 * g.map_b + (kind == 1 ? 1 : 0);
         t.a_r0 = g.a_r0; t.a_c0 = g.a_c0; t.b_r0 = g.b_r0; t.b_c0 = g.b_c0;
         t.alpha = kind == 1 ? 1.0f : -1.0f;
+        t.round_tf32 = kind == 1;          // panel-solve results are final factor entries
         const int tm = (g.M + BM - 1) / BM, tn = (g.N + bn - 1) / bn;
         for (int a = 0; a < tm; ++a)
             for (int b = 0; b < tn; ++b) {
