@@ -176,7 +176,11 @@ int rsd_solve(rsd_handle h, const double* f, double* u, double tol, rsd_stats* s
  * (timeout of a bounded wait, failed pivot) raised since setup.                        */
 int rsd_check(rsd_handle h);
 
+/* rsd_destroy -- release the handle.  Its device arena is kept in a one-slot per-device
+ * cache and reused by the next rsd_setup on that device if large enough (the previously
+ * cached block, if smaller, is freed); rsd_release_cache() frees the cached blocks.      */
 void        rsd_destroy(rsd_handle h);
+void        rsd_release_cache(void);
 const char* rsd_strerror(int code);
 /* detail of the last failure on the calling host thread (which CUDA call, which size). */
 const char* rsd_last_error_detail(void);

@@ -34,6 +34,7 @@ EXPORTS = [
     "rsd_get_info", "rsd_front_dims", "rsd_front_dofs", "rsd_front_map", "rsd_front_factor",
     "rsd_grid_sizes", "rsd_grid_assemble", "rsd_grid_load", "rsd_grid_partition",
     "rsd_profile", "rsd_launch_count", "rsd_apply_static", "rsd_last_error_detail",
+    "rsd_release_cache",
 ]
 
 
@@ -103,6 +104,7 @@ def load() -> C.CDLL:
             "rsd_grid_partition": (C.c_int, [C.c_int32, C.c_int32, P, P, P]),
             "rsd_profile": (C.c_int, [P, C.POINTER(rsd_profile_t), C.c_int32]),
             "rsd_launch_count": (C.c_int64, []),
+            "rsd_release_cache": (None, []),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)

@@ -26,6 +26,41 @@ static thread_local std::string g_last_error;
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 
 static std::atomic<long long> g_launches(0);
+
+// One cached arena per device: rsd_destroy parks its arena here instead of freeing it and
+// the next rsd_setup on that device reuses it when it is large enough (the arena of a
+// factorisation is tens of GB; mapping and unmapping it costs tens of milliseconds).
+// rsd_release_cache() returns it to the driver.
+struct ArenaCache { char* ptr = nullptr; size_t bytes = 0; };
+static std::mutex g_cache_mu;
+static ArenaCache g_cache[64];
+
+static char* arena_take(size_t bytes, int dev, size_t* got) {
+    {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        ArenaCache& c = g_cache[dev & 63];
+        if (c.ptr && c.bytes >= bytes) {
+            char* p = c.ptr;
+            *got = c.bytes;
+            c = ArenaCache{};
+            return p;
+        }
+        if (c.ptr) { cudaFree(c.ptr); c = ArenaCache{}; }   // too small: give it back first
+    }
+    char* p = nullptr;
+    if (cudaMalloc((void**)&p, bytes) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    *got = bytes;
+    return p;
+}
+
+static void arena_give(char* p, size_t bytes, int dev) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    ArenaCache& c = g_cache[dev & 63];
+    if (c.ptr && c.bytes >= bytes) { cudaFree(p); return; }
+    if (c.ptr) cudaFree(c.ptr);
+    c.ptr = p;
+    c.bytes = bytes;
+}
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 int prof_begin(Handle& h, int cls) {
@@ -311,11 +346,17 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
     const size_t o_err = take(sizeof(int) * ERR_SLOTS);
     const size_t o_ticket = take(sizeof(int) * 2 * nl + 16);
     h.arena_bytes = off;
-    if (cudaMalloc((void**)&h.arena, h.arena_bytes) != cudaSuccess) {
-        cudaGetLastError();
-        h.arena = nullptr;
-        set_last_error("device arena of " + std::to_string(h.arena_bytes) + " bytes");
-        return RSD_ERR_NOMEM;
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        h.device = dev;
+        size_t got = 0;
+        h.arena = arena_take(h.arena_bytes, dev, &got);
+        if (!h.arena) {
+            set_last_error("device arena of " + std::to_string(h.arena_bytes) + " bytes");
+            return RSD_ERR_NOMEM;
+        }
+        h.arena_capacity = got;
     }
     char* A = h.arena;
     h.d_rowptr = (int64_t*)(A + o_rowptr);
@@ -470,6 +511,19 @@ extern "C" const char* rsd_last_error_detail(void) { return g_last_error.c_str()
 
 extern "C" int64_t rsd_launch_count(void) { return (int64_t)g_launches.load(); }
 
+extern "C" void rsd_release_cache(void) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (int d = 0; d < 64; ++d) {
+        if (!g_cache[d].ptr) continue;
+        cudaSetDevice(d);
+        cudaFree(g_cache[d].ptr);
+        g_cache[d] = ArenaCache{};
+    }
+    cudaSetDevice(cur);
+}
+
 extern "C" int rsd_profile(rsd_handle hh, rsd_profile_t* out, int32_t reset) {
     if (!hh || !out) return RSD_ERR_ARG;
     Handle& h = hh->h;
@@ -498,7 +552,7 @@ extern "C" void rsd_destroy(rsd_handle hh) {
     gemm_tc_release(h);
     for (auto& r : h.prof.recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : h.prof.pool) cudaEventDestroy(e);
-    if (h.arena) cudaFree(h.arena);
+    if (h.arena) arena_give(h.arena, h.arena_capacity, h.device);
     if (h.h_scal) cudaFreeHost(h.h_scal);
     delete hh;
 }

@@ -63,7 +63,7 @@ __device__ int wait_flag(const int* flag, int target, int* err, int* s_val) {
                     v = target;
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(20);
             }
         }
         __threadfence();
@@ -97,6 +97,8 @@ __global__ void k_fwd_gather(const FrontDesc* __restrict__ fronts, const FrontDe
 
 // Row block item: rows [r0, r1) of front f.  acc_row = v_row - sum_{cb < ncb} P[row, cb] y_cb;
 // for a diagonal block y = Dinv * acc (published), else the contribution v_row = acc.
+// The factor tile of a column block is requested before waiting for that block's y, so
+// the item at the head of the dependency chain only pays for y and the arithmetic.
 template <typename T, typename A>
 __global__ void __launch_bounds__(AT) k_fwd_sweep(const FrontDesc* __restrict__ fronts,
                                                   const int* __restrict__ items, int n_items,
@@ -106,7 +108,7 @@ __global__ void __launch_bounds__(AT) k_fwd_sweep(const FrontDesc* __restrict__ 
     constexpr int PASSES = NB / (32 * VW);
     constexpr int RPW = NB / AW;                 // rows per warp
     __shared__ int s_item, s_flag;
-    __shared__ A s_t[NB];
+    __shared__ __align__(16) A s_t[NB];
     extern __shared__ __align__(16) unsigned char sweep_smem[];
     T* Ds = (T*)sweep_smem;                      // NB x NB inverted diagonal block
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -130,48 +132,70 @@ __global__ void __launch_bounds__(AT) k_fwd_sweep(const FrontDesc* __restrict__ 
         for (int u = 0; u < RPW; ++u) acc[u] = 0;
         int seen = 0;
         for (int cb = 0; cb < ncb; ++cb) {
-            if (seen < cb + 1) seen = wait_flag(&f.flag[0], cb + 1, err, &s_flag);
             const int c0 = cb * NB;
             const int cw = min(NB, f.s - c0);
 #pragma unroll
             for (int ps = 0; ps < PASSES; ++ps) {
                 const int cl = ps * 32 * VW + lane * VW;   // column inside the block
+                V l[RPW];
+#pragma unroll
+                for (int u = 0; u < RPW; ++u) {
+                    const int row = r0 + warp + AW * u;
+                    l[u] = (row < r1 && cl < cw) ? __ldg((const V*)(P + (int64_t)row * f.ldp + c0 + cl)) : V{};
+                }
+                if (ps == 0 && seen < cb + 1) seen = wait_flag(&f.flag[0], cb + 1, err, &s_flag);
                 A y[VW];
 #pragma unroll
                 for (int e = 0; e < VW; ++e) y[e] = (cl + e < cw) ? ld_cg(v + c0 + cl + e) : (A)0;
-                if (cl < cw) {
-                    V l[RPW];
 #pragma unroll
-                    for (int u = 0; u < RPW; ++u) {
-                        const int row = r0 + warp + AW * u;
-                        l[u] = row < r1 ? __ldg((const V*)(P + (int64_t)row * f.ldp + c0 + cl)) : V{};
-                    }
+                for (int u = 0; u < RPW; ++u)
 #pragma unroll
-                    for (int u = 0; u < RPW; ++u)
-#pragma unroll
-                        for (int e = 0; e < VW; ++e) acc[u] += (A)vget(l[u], e) * y[e];
-                }
+                    for (int e = 0; e < VW; ++e) acc[u] += (A)vget(l[u], e) * y[e];
             }
         }
 #pragma unroll
-        for (int u = 0; u < RPW; ++u) {
-            A a = acc[u];
+        for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-            const int row = r0 + warp + AW * u;
-            if (lane == 0 && row < r1) s_t[row - r0] = ld_cg(v + row) - a;
+            for (int u = 0; u < RPW; ++u) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
+        if (lane == 0) {
+#pragma unroll
+            for (int u = 0; u < RPW; ++u) {
+                const int row = r0 + warp + AW * u;
+                if (row < r1) s_t[row - r0] = ld_cg(v + row) - acc[u];
+            }
         }
         __syncthreads();
         if (diag) {
             const int w = r1 - r0;
             cp_async_wait();
             __syncthreads();
-            for (int rr = warp; rr < w; rr += AW) {
-                A s = 0;
-                for (int c = lane; c <= rr; c += 32) s += (A)Ds[rr * NB + c] * s_t[c];
+            // y = Dinv t: each thread takes RPW rows x VW columns per pass, then a warp sum
+            A part[RPW];
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                if (lane == 0) __stcg(v + r0 + rr, s);
+            for (int u = 0; u < RPW; ++u) part[u] = 0;
+#pragma unroll
+            for (int ps = 0; ps < PASSES; ++ps) {
+                const int cl = ps * 32 * VW + lane * VW;
+                A t[VW];
+#pragma unroll
+                for (int e = 0; e < VW; ++e) t[e] = cl + e < w ? s_t[cl + e] : (A)0;
+#pragma unroll
+                for (int u = 0; u < RPW; ++u) {
+                    const V d = *(const V*)(Ds + (warp + AW * u) * NB + cl);
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) part[u] += (A)vget(d, e) * t[e];
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int u = 0; u < RPW; ++u) part[u] += __shfl_xor_sync(0xffffffffu, part[u], o);
+            if (lane == 0) {
+#pragma unroll
+                for (int u = 0; u < RPW; ++u) {
+                    const int rr = warp + AW * u;
+                    if (rr < w) __stcg(v + r0 + rr, part[u]);
+                }
             }
             publish_flag(&f.flag[0], blk + 1);
         } else {
@@ -190,6 +214,9 @@ __global__ void k_bwd_gather(const FrontDesc* __restrict__ fronts, const double*
 }
 
 // Column block item cb: t = y_cb - sum_{rows i >= c1} P[i, cb]^T x_i, x_cb = Dinv^T t.
+// Rows are consumed in NB-row groups from the bottom (ancestor rows first, then the
+// interface rows of later blocks as their owners finish); each group's factor rows are
+// requested before waiting for the group's x.
 template <typename T, typename A>
 __global__ void __launch_bounds__(AT) k_bwd_sweep(const FrontDesc* __restrict__ fronts,
                                                   const int* __restrict__ items, int n_items,
@@ -222,34 +249,35 @@ __global__ void __launch_bounds__(AT) k_bwd_sweep(const FrontDesc* __restrict__ 
         for (int ps = 0; ps < PASSES; ++ps)
 #pragma unroll
             for (int e = 0; e < VW; ++e) acc[ps][e] = 0;
-        // rows below the diagonal block, processed bottom-up in NB-row groups so that the
-        // interface rows of later blocks are consumed as their owners finish
         int seen = 0;
         const int n_groups_B = (f.b + NB - 1) / NB;
         const int n_groups = n_groups_B + (f.nd - 1 - cb);
         for (int g = 0; g < n_groups; ++g) {
-            int g0, g1;
+            int g0, g1, need = 0;
             if (g < n_groups_B) {
                 g0 = f.s + (n_groups_B - 1 - g) * NB; g1 = min(g0 + NB, f.N);
             } else {
                 const int rb = f.nd - 1 - (g - n_groups_B);      // I row block > cb
-                const int need = f.nd - rb;                        // blocks finished from the top
-                if (seen < need) seen = wait_flag(&f.flag[1], need, err, &s_flag);
+                need = f.nd - rb;                                  // blocks finished from the top
                 g0 = rb * NB; g1 = min(g0 + NB, f.s);
             }
-            for (int rbase = g0 + warp; rbase < g1; rbase += AW * RB) {
+            for (int base = g0; base < g1; base += AW * RB) {
                 V l[RB][PASSES];
-                A x[RB];
 #pragma unroll
                 for (int u = 0; u < RB; ++u) {
-                    const int row = rbase + AW * u;
-                    const bool ok = row < g1;
-                    x[u] = ok ? ld_cg(v + row) : (A)0;
+                    const int row = base + warp + AW * u;
 #pragma unroll
                     for (int ps = 0; ps < PASSES; ++ps) {
                         const int cl = ps * 32 * VW + lane * VW;
-                        l[u][ps] = (ok && cl < cw) ? __ldg((const V*)(P + (int64_t)row * f.ldp + c0 + cl)) : V{};
+                        l[u][ps] = (row < g1 && cl < cw) ? __ldg((const V*)(P + (int64_t)row * f.ldp + c0 + cl)) : V{};
                     }
+                }
+                if (base == g0 && seen < need) seen = wait_flag(&f.flag[1], need, err, &s_flag);
+                A x[RB];
+#pragma unroll
+                for (int u = 0; u < RB; ++u) {
+                    const int row = base + warp + AW * u;
+                    x[u] = row < g1 ? ld_cg(v + row) : (A)0;
                 }
 #pragma unroll
                 for (int u = 0; u < RB; ++u)
@@ -265,27 +293,41 @@ __global__ void __launch_bounds__(AT) k_bwd_sweep(const FrontDesc* __restrict__ 
             for (int e = 0; e < VW; ++e) s_red[warp][ps * 32 * VW + lane * VW + e] = acc[ps][e];
         __syncthreads();
         for (int c = threadIdx.x; c < cw; c += AT) {
-            A s = 0;
+            A sum = 0;
 #pragma unroll
-            for (int w = 0; w < AW; ++w) s += s_red[w][c];
-            s_t[c] = ld_cg(v + c0 + c) - s;
+            for (int w = 0; w < AW; ++w) sum += s_red[w][c];
+            s_t[c] = ld_cg(v + c0 + c) - sum;
         }
-        __syncthreads();
-        // x = Dinv^T t : x_c = sum_{r >= c} Dinv[r][c] t_r  (column sums, warps over rows)
         cp_async_wait();
         __syncthreads();
-        for (int c = lane; c < NB; c += 32) {
-            A s = 0;
-            for (int rr = warp; rr < cw; rr += AW) s += (A)Ds[rr * NB + c] * s_t[rr];
-            s_red[warp][c] = s;
+        // x = Dinv^T t : x_c = sum_{r >= c} Dinv[r][c] t_r  (lanes over columns, warps over rows)
+        {
+            A part[PASSES][VW];
+#pragma unroll
+            for (int ps = 0; ps < PASSES; ++ps)
+#pragma unroll
+                for (int e = 0; e < VW; ++e) part[ps][e] = 0;
+            for (int rr = warp; rr < cw; rr += AW) {
+                const A tr = s_t[rr];
+#pragma unroll
+                for (int ps = 0; ps < PASSES; ++ps) {
+                    const V d = *(const V*)(Ds + rr * NB + ps * 32 * VW + lane * VW);
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) part[ps][e] += (A)vget(d, e) * tr;
+                }
+            }
+#pragma unroll
+            for (int ps = 0; ps < PASSES; ++ps)
+#pragma unroll
+                for (int e = 0; e < VW; ++e) s_red[warp][ps * 32 * VW + lane * VW + e] = part[ps][e];
         }
         __syncthreads();
         for (int c = threadIdx.x; c < cw; c += AT) {
-            A s = 0;
+            A sum = 0;
 #pragma unroll
-            for (int w = 0; w < AW; ++w) s += s_red[w][c];
-            __stcg(v + c0 + c, s);
-            z[f.I[c0 + c]] = (double)s;
+            for (int w = 0; w < AW; ++w) sum += s_red[w][c];
+            __stcg(v + c0 + c, sum);
+            z[f.I[c0 + c]] = (double)sum;
         }
         publish_flag(&f.flag[1], f.nd - cb);
         __syncthreads();

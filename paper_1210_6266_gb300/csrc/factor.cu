@@ -337,20 +337,59 @@ __global__ void __launch_bounds__(256) k_potrf_diag(const FrontDesc* __restrict_
     }
     __syncthreads();
     // ---- block columns right to left: X_21 = -(X_22 L_21) X_11 ----
+    // 4 x 4 register tiles: thread t owns rows 4*(t/8).., columns 4*(t%8).. of the block
+    // column (upper triangles in shared memory are zero, so full-range sums are exact).
     for (int j = npb - 2; j >= 0; --j) {
         const int c0 = j * 32, b0 = c0 + 32, rows = w - b0;
-        for (int e = tid; e < rows * 32; e += 256) {          // Tm = X_22 * L_21
-            const int i = e / 32, c = e % 32;
-            T s = 0;
-            for (int m = b0; m <= b0 + i; ++m) s += A[(b0 + i) * DLD + m] * A[m * DLD + c0 + c];
-            Tm[i * TLD + c] = s;
+        const int ti = tid >> 3, tc = tid & 7;
+        const bool active = 4 * ti < rows;
+        if (active) {                                          // Tm = X_22 * L_21
+            T acc[4][4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+            const int mend = min(w, b0 + 4 * ti + 4);
+            for (int m = b0; m < mend; ++m) {
+                T xa[4], lb[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) xa[a] = A[(b0 + 4 * ti + a) * DLD + m];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) lb[b] = A[m * DLD + c0 + 4 * tc + b];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b] += xa[a] * lb[b];
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) Tm[(4 * ti + a) * TLD + 4 * tc + b] = acc[a][b];
         }
         __syncthreads();
-        for (int e = tid; e < rows * 32; e += 256) {          // A_21 = -Tm * X_11
-            const int i = e / 32, c = e % 32;
-            T s = 0;
-            for (int m = c; m < 32; ++m) s += Tm[i * TLD + m] * A[(c0 + m) * DLD + c0 + c];
-            A[(b0 + i) * DLD + c0 + c] = -s;
+        if (active) {                                          // A_21 = -Tm * X_11
+            T acc[4][4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+#pragma unroll 8
+            for (int m = 0; m < 32; ++m) {
+                T ta[4], xb[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) ta[a] = Tm[(4 * ti + a) * TLD + m];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) xb[b] = A[(c0 + m) * DLD + c0 + 4 * tc + b];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b] += ta[a] * xb[b];
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+                if (4 * ti + a < rows)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) A[(b0 + 4 * ti + a) * DLD + c0 + 4 * tc + b] = -acc[a][b];
         }
         __syncthreads();
     }
@@ -494,7 +533,7 @@ int launch_extend_add(Handle& h, int li) {
     Level& Lc = h.levels[li + 1];
     if (Lp.fronts.empty() || Lc.fronts.empty()) return RSD_OK;
     const bool p64 = is_fp64(Lp.prec), c64 = is_fp64(Lc.prec);
-    dim3 grid((unsigned)std::max(1, std::min(256, Lc.max_b)), (unsigned)Lp.fronts.size());
+    dim3 grid((unsigned)std::max(1, std::min(4096, Lc.max_b)), (unsigned)Lp.fronts.size());
     double ea_bytes = 0;
     for (auto& f : Lc.fronts) ea_bytes += 0.5 * f.b * (f.b + 1.0) * (elem_bytes(Lc.prec) + 2.0 * elem_bytes(Lp.prec));
     ea_bytes /= std::max(1, Lp.max_children);

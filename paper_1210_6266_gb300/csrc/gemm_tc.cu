@@ -141,21 +141,21 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-template <int BN>
+template <int BN, int ST>
 struct Smem {
-    static constexpr int STAGES = BN == 128 ? 6 : 4;
+    static constexpr int STAGES = ST;
     static constexpr int A_BYTES = BM * BK * 4;
     static constexpr int B_BYTES = BN * BK * 4;
     static constexpr int STAGE = A_BYTES + B_BYTES;
     static constexpr int TOTAL = STAGES * STAGE + 1024 /*align*/ + 256 /*barriers*/;
 };
 
-template <int BN>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+template <int BN, int ST>
+__global__ void __launch_bounds__(TC_THREADS, ST <= 3 ? 2 : 1)
 k_gemm_tc(const TcTask* __restrict__ tasks, const TcTile* __restrict__ tiles,
           const CUtensorMap* __restrict__ maps, float* __restrict__ ws, int* __restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
-    using S = Smem<BN>;
+    using S = Smem<BN, ST>;
     constexpr int STAGES = S::STAGES;
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023) & ~1023u;
@@ -448,8 +448,9 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
     if (!rd.empty())
         RSD_CUDA_TRY(cudaMemcpyAsync(st->d_reds, rd.data(), rd.size() * sizeof(TcRed), cudaMemcpyHostToDevice, stream));
     if (!st->attr_set) {
-        RSD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<128>::TOTAL));
-        RSD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<256>::TOTAL));
+        RSD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<128, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<128, 3>::TOTAL));
+        RSD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<128, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<128, 6>::TOTAL));
+        RSD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<256, 4>::TOTAL));
         st->attr_set = true;
     }
     double fl = 0, by = 0;
@@ -459,10 +460,14 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
         by += 4.0 * ((double)g.M * g.K + (g.lower ? 0.0 : (double)g.N * g.K) + c * (g.beta ? 2 : 1));
     }
     const int pi = prof_begin(h, K_GEMM_TC);
-    if (bn == 128)
-        k_gemm_tc<128><<<(unsigned)tl.size(), TC_THREADS, Smem<128>::TOTAL, stream>>>(st->d_tasks, st->d_tiles, st->d_maps, st->d_ws, h.d_err);
+    // short K (inner panel update, panel solve): 3-stage ring, two CTAs per SM so one
+    // tile's epilogue overlaps the other's main loop; long K: deeper rings, one CTA per SM
+    if (bn == 128 && max_kb <= 16)
+        k_gemm_tc<128, 3><<<(unsigned)tl.size(), TC_THREADS, Smem<128, 3>::TOTAL, stream>>>(st->d_tasks, st->d_tiles, st->d_maps, st->d_ws, h.d_err);
+    else if (bn == 128)
+        k_gemm_tc<128, 6><<<(unsigned)tl.size(), TC_THREADS, Smem<128, 6>::TOTAL, stream>>>(st->d_tasks, st->d_tiles, st->d_maps, st->d_ws, h.d_err);
     else
-        k_gemm_tc<256><<<(unsigned)tl.size(), TC_THREADS, Smem<256>::TOTAL, stream>>>(st->d_tasks, st->d_tiles, st->d_maps, st->d_ws, h.d_err);
+        k_gemm_tc<256, 4><<<(unsigned)tl.size(), TC_THREADS, Smem<256, 4>::TOTAL, stream>>>(st->d_tasks, st->d_tiles, st->d_maps, st->d_ws, h.d_err);
     count_launch();
     if (!rd.empty()) {
         if (bn == 128) k_splitk_reduce<128><<<(unsigned)rd.size(), 256, 0, stream>>>(st->d_tasks, st->d_reds, st->d_ws);

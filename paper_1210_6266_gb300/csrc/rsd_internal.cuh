@@ -121,6 +121,8 @@ struct Handle {
     // device buffers
     char* arena = nullptr;
     size_t arena_bytes = 0;
+    size_t arena_capacity = 0;          // bytes of the block actually held (cache reuse)
+    int device = 0;
     int* d_err = nullptr;
     int* d_ticket = nullptr;             // per-sweep ticket counters
     // CSR of K on the device (FP64), owned copy for the Krylov SpMV
