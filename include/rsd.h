@@ -116,6 +116,9 @@ typedef struct {
     double  flops[RSD_PROFILE_CLASSES];
     double  bytes[RSD_PROFILE_CLASSES];
     double  host_analysis_ms;    /* host-side analysis of the last rsd_setup             */
+    double  host_parts_ms[6];    /* of which: structure copy to the host, ownership sort,
+                                    Eq. 3.1 check, interface sets, extend-add maps, and the
+                                    memory plan with its uploads                          */
 } rsd_profile_t;
 
 typedef struct rsd_handle_s* rsd_handle;

@@ -135,6 +135,7 @@ class RSD:
         out = {name: dict(launches=p.launches[i], ms=p.ms[i], flops=p.flops[i], bytes=p.bytes[i])
                for i, name in enumerate(_lib.PROFILE_CLASSES)}
         out["host_analysis_ms"] = p.host_analysis_ms
+        out["host_parts_ms"] = dict(zip(["copy", "sort", "check", "sets", "maps", "plan"], list(p.host_parts_ms)))
         return out
 
     def info(self) -> dict:

@@ -71,7 +71,8 @@ PROFILE_CLASSES = ["assemble", "extend_add", "gemm_tcgen05", "gemm_simt", "diag_
 
 class rsd_profile_t(C.Structure):
     _fields_ = [("launches", C.c_int64 * 10), ("ms", C.c_double * 10), ("flops", C.c_double * 10),
-                ("bytes", C.c_double * 10), ("host_analysis_ms", C.c_double)]
+                ("bytes", C.c_double * 10), ("host_analysis_ms", C.c_double),
+                ("host_parts_ms", C.c_double * 6)]
 
 
 _lib = None

@@ -53,6 +53,84 @@ static char* arena_take(size_t bytes, int dev, size_t* got) {
     return p;
 }
 
+static std::mutex g_pin_mu;
+static char* g_pin_ptr = nullptr;
+static size_t g_pin_bytes = 0;
+
+static char* pinned_take(size_t bytes, size_t* got) {
+    {
+        std::lock_guard<std::mutex> lk(g_pin_mu);
+        if (g_pin_ptr && g_pin_bytes >= bytes) {
+            char* p = g_pin_ptr;
+            *got = g_pin_bytes;
+            g_pin_ptr = nullptr;
+            g_pin_bytes = 0;
+            return p;
+        }
+    }
+    char* p = nullptr;
+    if (cudaMallocHost((void**)&p, bytes) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    *got = bytes;
+    return p;
+}
+
+static void pinned_give(char* p, size_t bytes) {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    if (g_pin_ptr && g_pin_bytes >= bytes) { cudaFreeHost(p); return; }
+    if (g_pin_ptr) cudaFreeHost(g_pin_ptr);
+    g_pin_ptr = p;
+    g_pin_bytes = bytes;
+}
+
+// Second one-slot pinned cache: host copies of a device CSR structure for the analysis.
+static std::mutex g_pin2_mu;
+static char* g_pin2_ptr = nullptr;
+static size_t g_pin2_bytes = 0;
+
+static char* pinned2_take(size_t bytes, size_t* got) {
+    {
+        std::lock_guard<std::mutex> lk(g_pin2_mu);
+        if (g_pin2_ptr && g_pin2_bytes >= bytes) {
+            char* p = g_pin2_ptr;
+            *got = g_pin2_bytes;
+            g_pin2_ptr = nullptr;
+            g_pin2_bytes = 0;
+            return p;
+        }
+    }
+    char* p = nullptr;
+    if (cudaMallocHost((void**)&p, bytes) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    *got = bytes;
+    return p;
+}
+
+static void pinned2_give(char* p, size_t bytes) {
+    std::lock_guard<std::mutex> lk(g_pin2_mu);
+    if (g_pin2_ptr && g_pin2_bytes >= bytes) { cudaFreeHost(p); return; }
+    if (g_pin2_ptr) cudaFreeHost(g_pin2_ptr);
+    g_pin2_ptr = p;
+    g_pin2_bytes = bytes;
+}
+
+const void* stage_host(Handle& h, const void* src, size_t bytes) {
+    const size_t need = (bytes + 255) & ~(size_t)255;
+    if (h.stage_off + need > h.stage_cap) {
+        cudaStreamSynchronize(h.stream);              // every earlier copy has completed
+        h.stage_off = 0;
+        if (need > h.stage_cap) {
+            if (h.stage) pinned_give(h.stage, h.stage_cap);
+            size_t got = 0;
+            h.stage = pinned_take(std::max(need, (size_t)64 << 20), &got);
+            h.stage_cap = h.stage ? got : 0;
+            if (!h.stage) return src;                  // fall back to a pageable (staged) copy
+        }
+    }
+    char* dst = h.stage + h.stage_off;
+    std::memcpy(dst, src, bytes);
+    h.stage_off += need;
+    return dst;
+}
+
 static void arena_give(char* p, size_t bytes, int dev) {
     std::lock_guard<std::mutex> lk(g_cache_mu);
     ArenaCache& c = g_cache[dev & 63];
@@ -163,7 +241,10 @@ inline bool anc_or_self(const Analysis& a, int x, int y) {   // x is ancestor-or
     return a.tin[x] <= a.tin[y] && a.tout[y] <= a.tout[x];
 }
 
-int analyse_structure(Analysis& a, const int64_t* rowptr, const int* col, const int* owner) {
+int analyse_structure(Analysis& a, const int64_t* rowptr, const int* col, const int* owner, double* part) {
+    using clk = std::chrono::steady_clock;
+    auto ms_since = [](clk::time_point t) { return std::chrono::duration<double, std::milli>(clk::now() - t).count(); };
+    auto t0 = clk::now();
     const int n = a.n;
     a.owner.assign(owner, owner + n);
     for (int i = 0; i < n; ++i)
@@ -185,6 +266,8 @@ int analyse_structure(Analysis& a, const int64_t* rowptr, const int* col, const 
             a.I_dofs[fill[t]++] = i;
         }
     }
+    part[0] = ms_since(t0);
+    t0 = clk::now();
     // Eq. 3.1: no coupling between owners that are not ancestor-related
     std::atomic<int> bad(0);
     parallel_chunks(n, [&](int64_t b, int64_t e) {
@@ -200,6 +283,8 @@ int analyse_structure(Analysis& a, const int64_t* rowptr, const int* col, const 
     });
     if (bad == 2) return RSD_ERR_ARG;
     if (bad == 1) return RSD_ERR_PARTITION;
+    part[1] = ms_since(t0);
+    t0 = clk::now();
     // B sets, bottom-up by depth, nodes of one depth in parallel
     a.B.assign(a.n_nodes, {});
     std::vector<std::vector<int>> by_depth(a.max_depth + 1);
@@ -226,6 +311,8 @@ int analyse_structure(Analysis& a, const int64_t* rowptr, const int* col, const 
             a.B[t] = std::move(cand);
         });
     }
+    part[2] = ms_since(t0);
+    t0 = clk::now();
     // extend-add maps
     a.ea.assign(a.n_nodes, {});
     parallel_for(a.n_nodes, [&](int64_t tt) {
@@ -241,6 +328,7 @@ int analyse_structure(Analysis& a, const int64_t* rowptr, const int* col, const 
             else m[k] = sp + (int)(std::lower_bound(a.B[p].begin(), a.B[p].end(), j) - a.B[p].begin());
         }
     });
+    part[3] = ms_since(t0);
     return RSD_OK;
 }
 
@@ -255,6 +343,7 @@ bool valid_prec(int p) { return p == RSD_PREC_FP64 || p == RSD_PREC_FP32 || p ==
 
 // Build the handle's levels, memory plan and device copies from an analysis.
 static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int* col, const double* val) {
+    const auto t_plan = std::chrono::steady_clock::now();
     h.n = a.n;
     h.n_nodes = a.n_nodes;
     h.parent = a.parent;
@@ -468,6 +557,7 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
     RSD_CUDA_TRY(cudaMemsetAsync(d_flags, 0, sizeof(int) * 2 * a.n_nodes, st));
     // the tensor-core levels need tensor maps over the fronts just placed
     RSD_TRY(gemm_tc_prepare(h));
+    h.prof.host_part[5] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_plan).count();
     // ---- numeric setup, deepest level first ----
     for (int d = nl - 1; d >= 0; --d) {
         RSD_TRY(launch_assemble_fronts(h, d, h.d_rowptr, h.d_col, h.d_val, d_owner, d_rank, d_tin, d_tout));
@@ -512,6 +602,18 @@ extern "C" const char* rsd_last_error_detail(void) { return g_last_error.c_str()
 extern "C" int64_t rsd_launch_count(void) { return (int64_t)g_launches.load(); }
 
 extern "C" void rsd_release_cache(void) {
+    {
+        std::lock_guard<std::mutex> lk(g_pin2_mu);
+        if (g_pin2_ptr) cudaFreeHost(g_pin2_ptr);
+        g_pin2_ptr = nullptr;
+        g_pin2_bytes = 0;
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_pin_mu);
+        if (g_pin_ptr) cudaFreeHost(g_pin_ptr);
+        g_pin_ptr = nullptr;
+        g_pin_bytes = 0;
+    }
     std::lock_guard<std::mutex> lk(g_cache_mu);
     int cur = 0;
     cudaGetDevice(&cur);
@@ -537,7 +639,8 @@ extern "C" int rsd_profile(rsd_handle hh, rsd_profile_t* out, int32_t reset) {
         out->flops[r.cls] += r.flops;
         out->bytes[r.cls] += r.bytes;
     }
-    out->host_analysis_ms = h.prof.host_ms;
+    out->host_analysis_ms = h.prof.host_ms + h.prof.host_part[5];
+    for (int i = 0; i < 6; ++i) out->host_parts_ms[i] = h.prof.host_part[i];
     if (reset) {
         for (auto& r : h.prof.recs) { h.prof.pool.push_back(r.a); h.prof.pool.push_back(r.b); }
         h.prof.recs.clear();
@@ -553,6 +656,7 @@ extern "C" void rsd_destroy(rsd_handle hh) {
     for (auto& r : h.prof.recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : h.prof.pool) cudaEventDestroy(e);
     if (h.arena) arena_give(h.arena, h.arena_capacity, h.device);
+    if (h.stage) pinned_give(h.stage, h.stage_cap);
     if (h.h_scal) cudaFreeHost(h.h_scal);
     delete hh;
 }
@@ -583,26 +687,47 @@ extern "C" int rsd_setup(const rsd_csr* K, const int32_t* dof_node, const rsd_tr
     const int* col = K->col;
     const int* owner = dof_node;
     cudaStream_t st = (cudaStream_t)o.stream;
+    char* pin = nullptr;
+    size_t pin_bytes = 0;
+    using clk = std::chrono::steady_clock;
+    auto ms_since = [](clk::time_point t) { return std::chrono::duration<double, std::milli>(clk::now() - t).count(); };
+    double part[6] = {0, 0, 0, 0, 0, 0};
+    auto t_copy = clk::now();
     if (K->mem == RSD_MEM_DEVICE) {
-        rp.resize(K->n + 1);
-        cl.resize(K->nnz);
-        ow.resize(K->n);
-        RSD_CUDA_TRY(cudaMemcpyAsync(rp.data(), K->rowptr, sizeof(int64_t) * (K->n + 1), cudaMemcpyDeviceToHost, st));
-        RSD_CUDA_TRY(cudaMemcpyAsync(cl.data(), K->col, sizeof(int) * K->nnz, cudaMemcpyDeviceToHost, st));
-        RSD_CUDA_TRY(cudaMemcpyAsync(ow.data(), dof_node, sizeof(int) * K->n, cudaMemcpyDeviceToHost, st));
-        RSD_CUDA_TRY(cudaStreamSynchronize(st));
-        rowptr = rp.data();
-        col = cl.data();
-        owner = ow.data();
+        const size_t b_rp = sizeof(int64_t) * (K->n + 1), b_cl = sizeof(int) * K->nnz, b_ow = sizeof(int) * K->n;
+        pin = pinned2_take(b_rp + b_cl + b_ow + 64, &pin_bytes);
+        if (pin) {
+            RSD_CUDA_TRY(cudaMemcpyAsync(pin, K->rowptr, b_rp, cudaMemcpyDeviceToHost, st));
+            RSD_CUDA_TRY(cudaMemcpyAsync(pin + b_rp, K->col, b_cl, cudaMemcpyDeviceToHost, st));
+            RSD_CUDA_TRY(cudaMemcpyAsync(pin + b_rp + b_cl, dof_node, b_ow, cudaMemcpyDeviceToHost, st));
+            RSD_CUDA_TRY(cudaStreamSynchronize(st));
+            rowptr = (const int64_t*)pin;
+            col = (const int*)(pin + b_rp);
+            owner = (const int*)(pin + b_rp + b_cl);
+        } else {
+            rp.resize(K->n + 1);
+            cl.resize(K->nnz);
+            ow.resize(K->n);
+            RSD_CUDA_TRY(cudaMemcpyAsync(rp.data(), K->rowptr, b_rp, cudaMemcpyDeviceToHost, st));
+            RSD_CUDA_TRY(cudaMemcpyAsync(cl.data(), K->col, b_cl, cudaMemcpyDeviceToHost, st));
+            RSD_CUDA_TRY(cudaMemcpyAsync(ow.data(), dof_node, b_ow, cudaMemcpyDeviceToHost, st));
+            RSD_CUDA_TRY(cudaStreamSynchronize(st));
+            rowptr = rp.data();
+            col = cl.data();
+            owner = ow.data();
+        }
     }
+    part[0] = ms_since(t_copy);
+    struct PinGuard { char* p; size_t b; ~PinGuard() { if (p) pinned2_give(p, b); } } guard{pin, pin_bytes};
     if (rowptr[K->n] != K->nnz) return RSD_ERR_ARG;
-    RSD_TRY(analyse_structure(a, rowptr, col, owner));
+    RSD_TRY(analyse_structure(a, rowptr, col, owner, part + 1));
     auto* hh = new (std::nothrow) rsd_handle_s();
     if (!hh) return RSD_ERR_NOMEM;
     Handle& h = hh->h;
     h.opt = o;
     h.stream = st;
     h.prof.on = o.profile != 0;
+    for (int i = 0; i < 5; ++i) h.prof.host_part[i] = part[i];
     h.prof.host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_host0).count();
     h.nnz = K->nnz;
     int dev = 0;
@@ -614,7 +739,7 @@ extern "C" int rsd_setup(const rsd_csr* K, const int32_t* dof_node, const rsd_tr
         return RSD_ERR_NOMEM;
     }
     // numeric values come from the caller's memory directly (device or host)
-    const int rc = build_handle(h, a, rowptr, col, K->val);
+    const int rc = build_handle(h, a, K->rowptr, K->col, K->val);
     if (rc != RSD_OK) {
         h.notspd_node = h.notspd_node;
         if (rc == RSD_ERR_NOT_SPD) { *out = hh; return rc; }   // handle kept for introspection

@@ -19,6 +19,7 @@
 //   (d) U -= X X^T (lower tiles only)                           (GEMM, K = s)
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "rsd_internal.cuh"
 
@@ -193,6 +194,9 @@ __global__ void __launch_bounds__(256) k_gemm_simt(const GemmTask* __restrict__ 
 // One CTA per front whose interface extends past k.
 // ---------------------------------------------------------------------------------
 constexpr int DLD = NB + 1;     // shared-memory row stride of the block
+
+__device__ __forceinline__ float vcomp(const float4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
+__device__ __forceinline__ double vcomp(const double2& v, int i) { return i == 0 ? v.x : v.y; }
 constexpr int TLD = 33;         // row stride of the 32-column scratch panel
 
 template <typename T>
@@ -223,9 +227,23 @@ __global__ void __launch_bounds__(256) k_potrf_diag(const FrontDesc* __restrict_
     T* P = (T*)f.P;
     __shared__ int bad;
     if (tid == 0) bad = 0;
-    for (int e = tid; e < NB * NB; e += 256) {
-        const int r = e / NB, c = e % NB;
-        A[r * DLD + c] = (r < w && c <= r) ? P[(int64_t)(k + r) * f.ldp + (k + c)] : (T)0;
+    {   // 16-byte loads, all issued before any is used (the block is NB x NB, rows ldp apart)
+        constexpr int VE = 16 / (int)sizeof(T);                 // elements per 16 bytes
+        constexpr int PER = NB * NB / VE / 256;                 // vectors per thread
+        using V4 = typename std::conditional<sizeof(T) == 8, double2, float4>::type;
+        V4 buf[PER];
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int e = (tid + 256 * q) * VE, r = e / NB, c = e % NB;
+            buf[q] = (r < w && c < w) ? *(const V4*)(P + (int64_t)(k + r) * f.ldp + (k + c)) : V4{};
+        }
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int e = (tid + 256 * q) * VE, r = e / NB, c = e % NB;
+#pragma unroll
+            for (int x = 0; x < VE; ++x)
+                A[r * DLD + c + x] = (r < w && c + x <= r && c + x < w) ? (T)vcomp(buf[q], x) : (T)0;
+        }
     }
     __syncthreads();
     const int npb = (w + 31) / 32;
@@ -474,8 +492,8 @@ double gemm_bytes(const std::vector<GemmTask>& tasks, size_t es) {
 template <typename T>
 int launch_gemm_simt(Handle& h, const std::vector<GemmTask>& tasks, GemmTask* d_tasks, T alpha, cudaStream_t st) {
     if (tasks.empty()) return RSD_OK;
-    RSD_CUDA_TRY(cudaMemcpyAsync(d_tasks, tasks.data(), tasks.size() * sizeof(GemmTask),
-                                 cudaMemcpyHostToDevice, st));
+    RSD_CUDA_TRY(cudaMemcpyAsync(d_tasks, stage_host(h, tasks.data(), tasks.size() * sizeof(GemmTask)),
+                                 tasks.size() * sizeof(GemmTask), cudaMemcpyHostToDevice, st));
     const GemmTask& last = tasks.back();
     const int tiles_last = last.lower ? ((last.M + SB - 1) / SB) * ((last.M + SB - 1) / SB + 1) / 2
                                       : ((last.M + SB - 1) / SB) * last.tiles_n;

@@ -443,10 +443,13 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
     RSD_TRY(grow(st->d_tasks, st->cap_tasks, tt.size(), sizeof(TcTask)));
     RSD_TRY(grow(st->d_tiles, st->cap_tiles, tl.size(), sizeof(TcTile)));
     if (!rd.empty()) RSD_TRY(grow(st->d_reds, st->cap_reds, rd.size(), sizeof(TcRed)));
-    RSD_CUDA_TRY(cudaMemcpyAsync(st->d_tasks, tt.data(), tt.size() * sizeof(TcTask), cudaMemcpyHostToDevice, stream));
-    RSD_CUDA_TRY(cudaMemcpyAsync(st->d_tiles, tl.data(), tl.size() * sizeof(TcTile), cudaMemcpyHostToDevice, stream));
+    RSD_CUDA_TRY(cudaMemcpyAsync(st->d_tasks, stage_host(h, tt.data(), tt.size() * sizeof(TcTask)),
+                                 tt.size() * sizeof(TcTask), cudaMemcpyHostToDevice, stream));
+    RSD_CUDA_TRY(cudaMemcpyAsync(st->d_tiles, stage_host(h, tl.data(), tl.size() * sizeof(TcTile)),
+                                 tl.size() * sizeof(TcTile), cudaMemcpyHostToDevice, stream));
     if (!rd.empty())
-        RSD_CUDA_TRY(cudaMemcpyAsync(st->d_reds, rd.data(), rd.size() * sizeof(TcRed), cudaMemcpyHostToDevice, stream));
+        RSD_CUDA_TRY(cudaMemcpyAsync(st->d_reds, stage_host(h, rd.data(), rd.size() * sizeof(TcRed)),
+                                     rd.size() * sizeof(TcRed), cudaMemcpyHostToDevice, stream));
     if (!st->attr_set) {
         RSD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<128, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<128, 3>::TOTAL));
         RSD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<128, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<128, 6>::TOTAL));

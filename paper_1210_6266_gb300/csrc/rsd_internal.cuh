@@ -85,6 +85,7 @@ struct Prof {
     std::vector<Rec> recs;
     std::vector<cudaEvent_t> pool;
     double host_ms = 0;                  // host-side analysis time of the last setup
+    double host_part[6] = {0, 0, 0, 0, 0, 0};   // copy, sort, check, sets, maps, plan
 };
 
 void count_launch(int n = 1);
@@ -141,7 +142,15 @@ struct Handle {
     int num_sms = 148;
     void* tc_state = nullptr;            // tensor-core GEMM state (tensor maps, task buffers)
     Prof prof;
+    // pinned host staging for per-launch uploads (append-only; see stage_host)
+    char* stage = nullptr;
+    size_t stage_cap = 0, stage_off = 0;
 };
+
+// Copy `bytes` from host memory into the handle's pinned staging area and return the
+// pinned copy, so that a following cudaMemcpyAsync is truly asynchronous.  The area is
+// used append-only; when it is full the stream is synchronised and it restarts.
+const void* stage_host(Handle& h, const void* src, size_t bytes);
 
 // Profile helpers: prof_begin records the start event (if profiling) and returns a
 // record index; prof_end records the stop event and the launch's algorithmic work.
