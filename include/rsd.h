@@ -141,6 +141,17 @@ typedef struct rsd_handle_s* rsd_handle;
 int rsd_setup(const rsd_csr* K, const int32_t* dof_node, const rsd_tree* T,
               const rsd_options* opt, rsd_handle* out);
 
+/* rsd_setup_batched -- one hierarchy for nprob independent problems (many sub-domain
+ * trees processed together: every tree level of every problem goes through the same
+ * batched kernel launches).  K[p], dof_node[p], T[p] describe problem p exactly as for
+ * rsd_setup (all K[p] in the same memory kind).  The problems are concatenated in order:
+ * vectors passed to rsd_apply / rsd_solve hold problem 0's DOFs, then problem 1's, ...
+ * Internally the trees hang under an empty super-root, so rsd_front_* node ids are
+ * 1 + (sum of the earlier trees' sizes) + t.  rsd_solve runs one PCG on the
+ * block-diagonal system (its inner products span all problems).                       */
+int rsd_setup_batched(int32_t nprob, const rsd_csr* K, const int32_t* const* dof_node,
+                      const rsd_tree* T, const rsd_options* opt, rsd_handle* out);
+
 /* rsd_apply -- z = M r, one application of the preconditioner (Algorithm 2 in the exact
  * limit): an upward sweep that forms the interface right-hand sides g of Eq. 3.2 level by
  * level, and a downward sweep of back-substitutions (Eq. 3.3).

@@ -99,6 +99,41 @@ class RSD:
             raise RSDError(rc, "rsd_setup")
         return cls(out.value, n)
 
+    @classmethod
+    def setup_batched(cls, problems, prec_leaf: int = RSD_PREC_TF32, prec_mid: int = RSD_PREC_TF32,
+                      prec_root: int = RSD_PREC_FP64, maxit: int = 200, profile: bool = False) -> "RSD":
+        """One hierarchy for several independent problems (dicts with rowptr, col, val,
+        dof_node, parent, all on the device).  Vectors are the problems' concatenation."""
+        lib = _lib.load()
+        n = len(problems)
+        keep = []
+        csrs = (_lib.rsd_csr * n)()
+        trees = (_lib.rsd_tree * n)()
+        owners = (C.c_void_p * n)()
+        total = 0
+        for i, pr in enumerate(problems):
+            rp = pr["rowptr"].to(torch.int64).contiguous()
+            cl = pr["col"].to(torch.int32).contiguous()
+            vl = pr["val"].to(torch.float64).contiguous()
+            ow = pr["dof_node"].to(torch.int32).contiguous()
+            par = np.ascontiguousarray(np.asarray(pr["parent"], dtype=np.int32))
+            keep += [rp, cl, vl, ow, par]
+            csrs[i] = _lib.rsd_csr(rp.numel() - 1, cl.numel(), _ptr(rp), _ptr(cl), _ptr(vl),
+                                   RSD_MEM_DEVICE if rp.is_cuda else RSD_MEM_HOST)
+            trees[i] = _lib.rsd_tree(len(par), par.ctypes.data)
+            owners[i] = _ptr(ow)
+            total += rp.numel() - 1
+        opt = _lib.rsd_options(RSD_MODE_EXACT, prec_leaf, prec_mid, prec_root, maxit,
+                               _stream() if torch.cuda.is_available() else 0, int(profile))
+        out = C.c_void_p()
+        rc = lib.rsd_setup_batched(n, csrs, owners, trees, C.byref(opt), C.byref(out))
+        del keep
+        if rc != 0:
+            if out.value:
+                lib.rsd_destroy(out)
+            raise RSDError(rc, "rsd_setup_batched")
+        return cls(out.value, total)
+
     def __del__(self):
         try:
             if self._h and self._h.value:

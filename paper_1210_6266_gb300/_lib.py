@@ -34,7 +34,7 @@ EXPORTS = [
     "rsd_get_info", "rsd_front_dims", "rsd_front_dofs", "rsd_front_map", "rsd_front_factor",
     "rsd_grid_sizes", "rsd_grid_assemble", "rsd_grid_load", "rsd_grid_partition",
     "rsd_profile", "rsd_launch_count", "rsd_apply_static", "rsd_last_error_detail",
-    "rsd_release_cache",
+    "rsd_release_cache", "rsd_setup_batched",
 ]
 
 
@@ -106,6 +106,8 @@ def load() -> C.CDLL:
             "rsd_profile": (C.c_int, [P, C.POINTER(rsd_profile_t), C.c_int32]),
             "rsd_launch_count": (C.c_int64, []),
             "rsd_release_cache": (None, []),
+            "rsd_setup_batched": (C.c_int, [C.c_int32, C.POINTER(rsd_csr), P, C.POINTER(rsd_tree),
+                                            C.POINTER(rsd_options), C.POINTER(P)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)

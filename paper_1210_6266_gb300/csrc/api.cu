@@ -838,3 +838,138 @@ extern "C" int rsd_front_factor(rsd_handle hh, int32_t node, double* out) {
         }
     return RSD_OK;
 }
+
+
+// ---- many independent problems in one hierarchy (batched form) ----------------------
+namespace rsd {
+namespace {
+
+struct ConcatDesc {
+    const int64_t* rowptr;
+    const int* col;
+    const int* owner;
+    int n;
+    int dof_off;
+    int64_t nnz_off;
+    int node_off;
+    int pad;
+};
+
+// Problem p's rows are shifted by dof_off, its nonzeros by nnz_off, its tree nodes by
+// node_off; one CTA row-block per problem (blockIdx.y).
+__global__ void k_concat(const ConcatDesc* __restrict__ d, int64_t* rowptr, int* col, int* owner) {
+    const ConcatDesc c = d[blockIdx.y];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < c.n; i += gridDim.x * blockDim.x) {
+        const int64_t r0 = c.rowptr[i], r1 = c.rowptr[i + 1];
+        rowptr[c.dof_off + i] = c.nnz_off + r0;
+        owner[c.dof_off + i] = c.owner[i] + c.node_off;
+        for (int64_t k = r0; k < r1; ++k) col[c.nnz_off + k] = c.col[k] + c.dof_off;
+    }
+}
+
+}  // namespace
+}  // namespace rsd
+
+extern "C" int rsd_setup_batched(int32_t nprob, const rsd_csr* K, const int32_t* const* dof_node,
+                                 const rsd_tree* T, const rsd_options* opt, rsd_handle* out) {
+    if (nprob <= 0 || !K || !dof_node || !T || !out) return RSD_ERR_ARG;
+    *out = nullptr;
+    const int mem = K[0].mem;
+    int64_t n = 0, nnz = 0, nodes = 1;
+    for (int p = 0; p < nprob; ++p) {
+        if (K[p].mem != mem || K[p].n <= 0 || K[p].nnz <= 0 || !K[p].rowptr || !K[p].col || !K[p].val ||
+            !dof_node[p] || T[p].n_nodes <= 0 || !T[p].parent)
+            return RSD_ERR_ARG;
+        n += K[p].n;
+        nnz += K[p].nnz;
+        nodes += T[p].n_nodes;
+    }
+    if (n > INT32_MAX || nodes > (1 << 24)) return RSD_ERR_ARG;
+    // the forest under an empty super-root (node 0)
+    std::vector<int> parent(nodes);
+    parent[0] = -1;
+    std::vector<int> node_off(nprob);
+    {
+        int64_t base = 1;
+        for (int p = 0; p < nprob; ++p) {
+            node_off[p] = (int)base;
+            for (int t = 0; t < T[p].n_nodes; ++t) {
+                const int pp = T[p].parent[t];
+                if ((t == 0 && pp != -1) || (t > 0 && (pp < 0 || pp >= t))) return RSD_ERR_ARG;
+                parent[base + t] = t == 0 ? 0 : (int)(base + pp);
+            }
+            base += T[p].n_nodes;
+        }
+    }
+    cudaStream_t st = opt ? (cudaStream_t)opt->stream : nullptr;
+    rsd_tree tree{(int32_t)nodes, parent.data()};
+    rsd_csr all{};
+    all.n = (int32_t)n;
+    all.nnz = nnz;
+    all.mem = mem;
+    int rc;
+    if (mem == RSD_MEM_HOST) {
+        std::vector<int64_t> rp(n + 1);
+        std::vector<int> cl(nnz), ow(n);
+        std::vector<double> vl(nnz);
+        int64_t dof = 0, nz = 0;
+        for (int p = 0; p < nprob; ++p) {
+            for (int i = 0; i < K[p].n; ++i) {
+                rp[dof + i] = nz + K[p].rowptr[i];
+                ow[dof + i] = dof_node[p][i] + node_off[p];
+            }
+            for (int64_t k = 0; k < K[p].nnz; ++k) {
+                cl[nz + k] = K[p].col[k] + (int)dof;
+                vl[nz + k] = K[p].val[k];
+            }
+            dof += K[p].n;
+            nz += K[p].nnz;
+        }
+        rp[n] = nnz;
+        all.rowptr = rp.data();
+        all.col = cl.data();
+        all.val = vl.data();
+        rc = rsd_setup(&all, ow.data(), &tree, opt, out);
+    } else {
+        int64_t* rp = nullptr;
+        int* cl = nullptr;
+        int* ow = nullptr;
+        double* vl = nullptr;
+        ConcatDesc* dd = nullptr;
+        std::vector<ConcatDesc> desc(nprob);
+        int64_t dof = 0, nz = 0;
+        int maxn = 0;
+        for (int p = 0; p < nprob; ++p) {
+            desc[p] = ConcatDesc{K[p].rowptr, K[p].col, dof_node[p], K[p].n, (int)dof, nz, node_off[p], 0};
+            dof += K[p].n;
+            nz += K[p].nnz;
+            maxn = std::max(maxn, K[p].n);
+        }
+        RSD_CUDA_TRY(cudaMallocAsync((void**)&rp, sizeof(int64_t) * (n + 1), st));
+        RSD_CUDA_TRY(cudaMallocAsync((void**)&cl, sizeof(int) * nnz, st));
+        RSD_CUDA_TRY(cudaMallocAsync((void**)&ow, sizeof(int) * n, st));
+        RSD_CUDA_TRY(cudaMallocAsync((void**)&vl, sizeof(double) * nnz, st));
+        RSD_CUDA_TRY(cudaMallocAsync((void**)&dd, sizeof(ConcatDesc) * nprob, st));
+        RSD_CUDA_TRY(cudaMemcpyAsync(dd, desc.data(), sizeof(ConcatDesc) * nprob, cudaMemcpyHostToDevice, st));
+        for (int p = 0; p < nprob; ++p)
+            RSD_CUDA_TRY(cudaMemcpyAsync(vl + desc[p].nnz_off, K[p].val, sizeof(double) * K[p].nnz,
+                                         cudaMemcpyDeviceToDevice, st));
+        RSD_CUDA_TRY(cudaMemcpyAsync(rp + n, &nnz, sizeof(int64_t), cudaMemcpyHostToDevice, st));
+        dim3 grid((unsigned)std::max(1, std::min(1024, (maxn + 255) / 256)), (unsigned)nprob);
+        k_concat<<<grid, 256, 0, st>>>(dd, rp, cl, ow);
+        count_launch();
+        RSD_CUDA_TRY(cudaGetLastError());
+        RSD_CUDA_TRY(cudaStreamSynchronize(st));
+        all.rowptr = rp;
+        all.col = cl;
+        all.val = vl;
+        rc = rsd_setup(&all, ow, &tree, opt, out);
+        cudaFreeAsync(rp, st);
+        cudaFreeAsync(cl, st);
+        cudaFreeAsync(ow, st);
+        cudaFreeAsync(vl, st);
+        cudaFreeAsync(dd, st);
+        cudaStreamSynchronize(st);
+    }
+    return rc;
+}
