@@ -155,6 +155,7 @@ def main() -> None:
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--mode", default="exact", choices=["exact", "paper"])
     ap.add_argument("--workload", default="diffusion129")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -168,7 +169,8 @@ def main() -> None:
     import torch
     import torch.distributed as dist
 
-    from paper_1210_6266_gb300 import RSD, RSD_PREC_FP64, RSD_PREC_TF32, grid_problem, launch_count
+    from paper_1210_6266_gb300 import (RSD, RSD_MODE_EXACT, RSD_MODE_PAPER, RSD_PREC_FP64, RSD_PREC_TF32,
+                                       grid_problem, launch_count)
     from paper_1210_6266_gb300 import build as _build
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -198,6 +200,7 @@ def main() -> None:
     else:
         prec = dict(prec_leaf=RSD_PREC_FP64, prec_mid=RSD_PREC_FP64, prec_root=RSD_PREC_FP64)
         dtype = "f64"
+    mode = RSD_MODE_PAPER if args.mode == "paper" else RSD_MODE_EXACT
     stream = torch.cuda.current_stream()
 
     def merge_prof(a, b):
@@ -216,7 +219,7 @@ def main() -> None:
     def step(profile=False):
         if not batched:
             h = RSD.setup(prob["rowptr"], prob["col"], prob["val"], prob["dof_node"], prob["parent"],
-                          profile=profile, **prec)
+                          profile=profile, mode=mode, **prec)
             u, st = h.solve(prob["b"], tol=TOL)
             prof = h.profile() if profile else None
             info = h.info()
@@ -279,7 +282,8 @@ def main() -> None:
             if batched:
                 h = RSD.setup_batched(hp, **prec)
             else:
-                h = RSD.setup(hp[0]["rowptr"], hp[0]["col"], hp[0]["val"], hp[0]["dof_node"], hp[0]["parent"], **prec)
+                h = RSD.setup(hp[0]["rowptr"], hp[0]["col"], hp[0]["val"], hp[0]["dof_node"], hp[0]["parent"],
+                              mode=mode, **prec)
             b = torch.cat([x["b"] for x in hp]).to("cuda", non_blocking=True)
             u, _ = h.solve(b, tol=TOL)
             u_host[off:off + u.numel()].copy_(u, non_blocking=True)
@@ -338,7 +342,7 @@ def main() -> None:
                    "n_dof": n_dof,
                    "subdomains": sum(8 ** w["depth"] for w in work) if batched else 8 ** work["depth"],
                    "merge_levels": max(w["depth"] for w in work) if batched else work["depth"],
-                   "form": args.form, "precisions": {k: v for k, v in prec.items()}, "tol": TOL,
+                   "form": args.form, "mode": args.mode, "precisions": {k: v for k, v in prec.items()}, "tol": TOL,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (factors are tens of GB)"},
         "roofline": roof,

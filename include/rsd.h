@@ -52,6 +52,13 @@ extern "C" {
 #define RSD_MODE_EXACT 0   /* exact recursive Schur complements (gamma -> infinity,
                               V-hat = V limit of Algorithm 2): the preconditioner is K^-1
                               up to the rounding of the stored factors                  */
+#define RSD_MODE_PAPER 1   /* Algorithm 2 with the V-hat truncation of Sec. 3.2: each
+                              interface solves S~ u_I = g exactly, S~ = K_II minus the
+                              leaf terms sum_l K_Il K_ll^-1 K_lI (Algorithm 1 with V-hat =
+                              the leaves coupled to I); g and the back-substitution use
+                              leaf unknowns only.  Needs every leaf on the deepest level.
+                              Not symmetric in general; PCG still converges on the SPD
+                              systems here, GMRES is the paper's outer solver.           */
 
 #define RSD_MEM_HOST   0
 #define RSD_MEM_DEVICE 1
@@ -75,7 +82,7 @@ typedef struct {
 } rsd_tree;
 
 typedef struct {
-    int32_t mode;        /* RSD_MODE_EXACT                                                */
+    int32_t mode;        /* RSD_MODE_EXACT or RSD_MODE_PAPER                              */
     int32_t prec_leaf;   /* RSD_PREC_* of the leaf (true sub-domain) fronts               */
     int32_t prec_mid;    /* RSD_PREC_* of internal fronts below the root                  */
     int32_t prec_root;   /* RSD_PREC_* of the root interface                              */

@@ -15,11 +15,11 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (RSD_MEM_DEVICE, RSD_MEM_HOST, RSD_MODE_EXACT, RSD_PREC_FP32, RSD_PREC_FP64,
-                   RSD_PREC_TF32, RSDError, check)
+from ._lib import (RSD_MEM_DEVICE, RSD_MEM_HOST, RSD_MODE_EXACT, RSD_MODE_PAPER, RSD_PREC_FP32,
+                   RSD_PREC_FP64, RSD_PREC_TF32, RSDError, check)
 
 __all__ = ["RSD", "grid_problem", "grid_sizes", "launch_count", "RSDError", "RSD_PREC_FP64",
-           "RSD_PREC_FP32", "RSD_PREC_TF32"]
+           "RSD_PREC_FP32", "RSD_PREC_TF32", "RSD_MODE_EXACT", "RSD_MODE_PAPER"]
 
 
 def launch_count() -> int:
@@ -75,7 +75,7 @@ class RSD:
     def setup(cls, rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor,
               dof_node: torch.Tensor, parent, prec_leaf: int = RSD_PREC_TF32,
               prec_mid: int = RSD_PREC_TF32, prec_root: int = RSD_PREC_FP64,
-              maxit: int = 200, profile: bool = False) -> "RSD":
+              maxit: int = 200, profile: bool = False, mode: int = RSD_MODE_EXACT) -> "RSD":
         lib = _lib.load()
         dev = rowptr.is_cuda
         if not (col.is_cuda == dev and val.is_cuda == dev and dof_node.is_cuda == dev):
@@ -89,7 +89,7 @@ class RSD:
         csr = _lib.rsd_csr(n, col.numel(), _ptr(rowptr), _ptr(col), _ptr(val),
                            RSD_MEM_DEVICE if dev else RSD_MEM_HOST)
         tree = _lib.rsd_tree(len(par), par.ctypes.data)
-        opt = _lib.rsd_options(RSD_MODE_EXACT, prec_leaf, prec_mid, prec_root, maxit,
+        opt = _lib.rsd_options(mode, prec_leaf, prec_mid, prec_root, maxit,
                                _stream() if torch.cuda.is_available() else 0, int(profile))
         out = C.c_void_p()
         rc = lib.rsd_setup(C.byref(csr), _ptr(dof_node), C.byref(tree), C.byref(opt), C.byref(out))

@@ -25,6 +25,7 @@ RSD_PREC_FP32 = 1
 RSD_PREC_TF32 = 2
 
 RSD_MODE_EXACT = 0
+RSD_MODE_PAPER = 1
 RSD_MEM_HOST = 0
 RSD_MEM_DEVICE = 1
 

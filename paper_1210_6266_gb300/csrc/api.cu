@@ -358,6 +358,17 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
     for (int t = 0; t < a.n_nodes; ++t) std::copy(a.ea[t].begin(), a.ea[t].end(), ea_all.begin() + h.B_off[t]);
 
     const int nl = a.max_depth + 1;
+    const bool paper = h.opt.mode == RSD_MODE_PAPER;
+    h.paper = paper;
+    // paper mode keeps only the interface block of internal fronts (V-hat truncation);
+    // leaves keep their coupling block, which yields the updates scattered into S~
+    auto beff = [&](int t) { return (paper && !a.children[t].empty()) ? 0 : (int)a.B[t].size(); };
+    if (paper)
+        for (int t = 0; t < a.n_nodes; ++t)
+            if (a.children[t].empty() && a.depth[t] != a.max_depth) {
+                set_last_error("paper mode needs every leaf on the deepest tree level");
+                return RSD_ERR_ARG;
+            }
     h.levels.assign(nl, Level{});
     h.node_level.assign(a.n_nodes, 0);
     h.node_slot.assign(a.n_nodes, 0);
@@ -399,7 +410,7 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
         // P regions of a level are contiguous, then the U regions
         lvlP[d] = off;
         for (int t : L.nodes) {
-            const int s = a.I_off[t + 1] - a.I_off[t], b = (int)a.B[t].size();
+            const int s = a.I_off[t + 1] - a.I_off[t], b = beff(t);
             const int ldp = std::max(32, round_up(s, 32));
             fp[t].P = take((size_t)(s + b) * ldp * es);
             h.factor_elems += (int64_t)s * (s + 1) / 2 + (int64_t)s * b;
@@ -409,13 +420,13 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
         L.bytes_P = off - lvlP[d];
         lvlU[d] = off;
         for (int t : L.nodes) {
-            const int b = (int)a.B[t].size();
+            const int b = beff(t);
             const int ldu = std::max(32, round_up(b, 32));
             fp[t].U = take((size_t)b * ldu * es);
         }
         L.bytes_U = off - lvlU[d];
         for (int t : L.nodes) {
-            const int s = a.I_off[t + 1] - a.I_off[t], b = (int)a.B[t].size();
+            const int s = a.I_off[t + 1] - a.I_off[t], b = beff(t);
             const int nd = (s + NB - 1) / NB;
             fp[t].D = take((size_t)std::max(1, nd) * NB * NB * es);
             fp[t].V = take((size_t)(s + b + 32) * es);
@@ -424,10 +435,17 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
     const size_t o_fronts = take(sizeof(FrontDesc) * a.n_nodes);
     size_t n_items = 16;
     for (int t = 0; t < a.n_nodes; ++t) {
-        const size_t s = a.I_off[t + 1] - a.I_off[t], b = a.B[t].size();
-        n_items += 2 * ((s + NB - 1) / NB) + (b + NB - 1) / NB;
+        const size_t s = a.I_off[t + 1] - a.I_off[t], b = beff(t);
+        n_items += 3 * ((s + NB - 1) / NB) + (b + NB - 1) / NB;
     }
     const size_t o_items = take(sizeof(int) * n_items);
+    // paper mode extras
+    const size_t o_pvec = paper ? take(sizeof(double) * 3 * (size_t)a.n) : 0;
+    const size_t o_nref = paper ? take(sizeof(NodeRef) * a.n_nodes) : 0;
+    const size_t o_nleaf = paper ? take(a.n_nodes) : 0;
+    const size_t o_ndepth = paper ? take(sizeof(int) * a.n_nodes) : 0;
+    const size_t o_fsolve = paper ? take(sizeof(FrontDesc) * a.n_nodes) : 0;
+    const size_t o_tpaper = paper ? take(sizeof(int) * (2 + 4 * nl)) : 0;
     const size_t o_child = take(sizeof(int) * a.n_nodes);
     const size_t o_vecs = take(sizeof(double) * 4 * (size_t)a.n + 4096);
     const size_t o_partial = take(sizeof(double) * 2048);
@@ -501,7 +519,7 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
             FrontDesc& f = L.fronts[sidx];
             f.node = t;
             f.s = a.I_off[t + 1] - a.I_off[t];
-            f.b = (int)a.B[t].size();
+            f.b = beff(t);
             f.N = f.s + f.b;
             f.ldp = std::max(32, round_up(f.s, 32));
             f.ldu = std::max(32, round_up(f.b, 32));
@@ -544,6 +562,16 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
         L.n_bwd_items = (int)bw.size();
         for (auto& x : bw) items_all.push_back(x.second);
         item_cursor += bw.size();
+        if (paper) {
+            std::vector<std::pair<int, int>> fs;
+            for (size_t sidx = 0; sidx < L.fronts.size(); ++sidx)
+                for (int blk = 0; blk < L.fronts[sidx].nd; ++blk) fs.push_back({blk, (int)(sidx << 16) | blk});
+            std::stable_sort(fs.begin(), fs.end(), [](auto& x, auto& y) { return x.first < y.first; });
+            L.d_fwd_items_solve = d_items + item_cursor;
+            L.n_fwd_items_solve = (int)fs.size();
+            for (auto& x : fs) items_all.push_back(x.second);
+            item_cursor += fs.size();
+        }
     }
     if (items_all.size() > n_items) { set_last_error("work list overflow"); return RSD_ERR_ARG; }
     for (int d = 0; d < nl; ++d) {
@@ -555,14 +583,57 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
     if (!child_tab.empty())
         RSD_CUDA_TRY(cudaMemcpyAsync(d_child, child_tab.data(), sizeof(int) * child_tab.size(), cudaMemcpyHostToDevice, st));
     RSD_CUDA_TRY(cudaMemsetAsync(d_flags, 0, sizeof(int) * 2 * a.n_nodes, st));
+    h.d_owner = d_owner;
+    h.d_rank = d_rank;
+    if (paper) {
+        h.d_pg = (double*)(A + o_pvec);
+        h.d_pw = h.d_pg + a.n;
+        h.d_pz = h.d_pw + a.n;
+        h.d_node_ref = (NodeRef*)(A + o_nref);
+        h.d_node_leaf = (unsigned char*)(A + o_nleaf);
+        h.d_node_depth = (int*)(A + o_ndepth);
+        h.d_ticket_paper = (int*)(A + o_tpaper);
+        std::vector<NodeRef> refs(a.n_nodes);
+        std::vector<unsigned char> leaf(a.n_nodes);
+        std::vector<FrontDesc> solve;
+        FrontDesc* d_solve = (FrontDesc*)(A + o_fsolve);
+        for (int d = 0; d < nl; ++d) {
+            Level& L = h.levels[d];
+            L.d_fronts_solve = d_solve + solve.size();
+            for (auto& f : L.fronts) {
+                refs[f.node] = NodeRef{f.P, f.ldp, is_fp64(L.prec) ? 1 : 0};
+                FrontDesc g = f;
+                g.b = 0;
+                g.N = g.s;
+                g.child_count = 0;
+                solve.push_back(g);
+            }
+        }
+        for (int t = 0; t < a.n_nodes; ++t) leaf[t] = a.children[t].empty() ? 1 : 0;
+        RSD_CUDA_TRY(cudaMemcpyAsync(h.d_node_ref, refs.data(), sizeof(NodeRef) * refs.size(), cudaMemcpyHostToDevice, st));
+        RSD_CUDA_TRY(cudaMemcpyAsync(h.d_node_leaf, leaf.data(), leaf.size(), cudaMemcpyHostToDevice, st));
+        RSD_CUDA_TRY(cudaMemcpyAsync(h.d_node_depth, a.depth.data(), sizeof(int) * a.n_nodes, cudaMemcpyHostToDevice, st));
+        RSD_CUDA_TRY(cudaMemcpyAsync(d_solve, solve.data(), sizeof(FrontDesc) * solve.size(), cudaMemcpyHostToDevice, st));
+        RSD_CUDA_TRY(cudaStreamSynchronize(st));     // host vectors above go out of scope
+    }
     // the tensor-core levels need tensor maps over the fronts just placed
     RSD_TRY(gemm_tc_prepare(h));
     h.prof.host_part[5] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_plan).count();
     // ---- numeric setup, deepest level first ----
-    for (int d = nl - 1; d >= 0; --d) {
-        RSD_TRY(launch_assemble_fronts(h, d, h.d_rowptr, h.d_col, h.d_val, d_owner, d_rank, d_tin, d_tout));
-        RSD_TRY(launch_extend_add(h, d));
-        RSD_TRY(run_factor_level(h, d));
+    if (!paper) {
+        for (int d = nl - 1; d >= 0; --d) {
+            RSD_TRY(launch_assemble_fronts(h, d, h.d_rowptr, h.d_col, h.d_val, d_owner, d_rank, d_tin, d_tout));
+            RSD_TRY(launch_extend_add(h, d));
+            RSD_TRY(run_factor_level(h, d));
+        }
+    } else {
+        // every interface front is K_II plus leaf updates: assemble all, factor the
+        // leaves, scatter their updates into S~, then factor the interfaces
+        for (int d = nl - 1; d >= 0; --d)
+            RSD_TRY(launch_assemble_fronts(h, d, h.d_rowptr, h.d_col, h.d_val, d_owner, d_rank, d_tin, d_tout));
+        RSD_TRY(run_factor_level(h, nl - 1));
+        RSD_TRY(paper_extend_add(h));
+        for (int d = nl - 2; d >= 0; --d) RSD_TRY(run_factor_level(h, d));
     }
     RSD_CUDA_TRY(cudaStreamSynchronize(st));
     int err[ERR_SLOTS];
@@ -674,7 +745,7 @@ extern "C" int rsd_setup(const rsd_csr* K, const int32_t* dof_node, const rsd_tr
     o.prec_root = RSD_PREC_FP64;
     o.maxit = 200;
     if (opt) o = *opt;
-    if (o.mode != RSD_MODE_EXACT) return RSD_ERR_ARG;
+    if (o.mode != RSD_MODE_EXACT && o.mode != RSD_MODE_PAPER) return RSD_ERR_ARG;
     const auto t_host0 = std::chrono::steady_clock::now();
     Analysis a;
     a.n = K->n;
@@ -752,11 +823,11 @@ extern "C" int rsd_setup(const rsd_csr* K, const int32_t* dof_node, const rsd_tr
 
 extern "C" int rsd_apply(rsd_handle hh, const double* r, double* z) {
     if (!hh || !r || !z || r == z) return RSD_ERR_ARG;
-    return run_apply(hh->h, r, z);
+    return hh->h.paper ? run_apply_paper(hh->h, r, z) : run_apply(hh->h, r, z);
 }
 
 extern "C" int rsd_apply_static(rsd_handle hh, const double* r, double* z) {
-    if (!hh || !r || !z || r == z) return RSD_ERR_ARG;
+    if (!hh || !r || !z || r == z || hh->h.paper) return RSD_ERR_ARG;
     return run_apply_static(hh->h, r, z);
 }
 
@@ -796,8 +867,9 @@ extern "C" int rsd_get_info(rsd_handle hh, rsd_info_t* out) {
 extern "C" int rsd_front_dims(rsd_handle hh, int32_t node, int32_t* s, int32_t* b, int32_t* level) {
     if (!hh || node < 0 || node >= hh->h.n_nodes) return RSD_ERR_ARG;
     const Handle& h = hh->h;
-    if (s) *s = h.I_off[node + 1] - h.I_off[node];
-    if (b) *b = h.B_off[node + 1] - h.B_off[node];
+    const FrontDesc& f = h.levels[h.node_level[node]].fronts[h.node_slot[node]];
+    if (s) *s = f.s;
+    if (b) *b = f.b;
     if (level) *level = h.depth[node];
     return RSD_OK;
 }
@@ -805,9 +877,9 @@ extern "C" int rsd_front_dims(rsd_handle hh, int32_t node, int32_t* s, int32_t* 
 extern "C" int rsd_front_dofs(rsd_handle hh, int32_t node, int32_t* out) {
     if (!hh || !out || node < 0 || node >= hh->h.n_nodes) return RSD_ERR_ARG;
     const Handle& h = hh->h;
-    const int s = h.I_off[node + 1] - h.I_off[node];
+    const FrontDesc& f = h.levels[h.node_level[node]].fronts[h.node_slot[node]];
     std::copy(h.I_dofs.begin() + h.I_off[node], h.I_dofs.begin() + h.I_off[node + 1], out);
-    std::copy(h.B_dofs.begin() + h.B_off[node], h.B_dofs.begin() + h.B_off[node + 1], out + s);
+    std::copy(h.B_dofs.begin() + h.B_off[node], h.B_dofs.begin() + h.B_off[node] + f.b, out + f.s);
     return RSD_OK;
 }
 

@@ -529,3 +529,35 @@ int run_apply_static(Handle& h, const double* r, double* z) {
 }
 
 }  // namespace rsd
+
+// ---- one level of a sweep with explicit descriptors (paper-mode leaf/interface solves) --
+namespace rsd {
+
+int sweep_with(Handle& h, int li, bool forward, const FrontDesc* fronts, const int* items, int n_items,
+               const double* in, double* out, int* ticket) {
+    Level& L = h.levels[li];
+    const int nf = (int)L.fronts.size();
+    const int grid = std::max(1, std::min(n_items, h.num_sms * 4));
+    const bool f64 = is_fp64(L.prec);
+    const int dsm = NB * NB * (f64 ? 8 : 4);
+    if (f64) { RSD_TRY((sweep_smem_setup<double, double>())); } else { RSD_TRY((sweep_smem_setup<float, float>())); }
+    if (forward) {
+        if (f64) k_fwd_gather<double, double><<<nf, 256, 0, h.stream>>>(fronts, fronts, L.d_child_slots, in);
+        else k_fwd_gather<float, float><<<nf, 256, 0, h.stream>>>(fronts, fronts, L.d_child_slots, in);
+        count_launch();
+        RSD_CUDA_TRY(cudaGetLastError());
+        if (n_items) {
+            if (f64) k_fwd_sweep<double, double><<<grid, AT, dsm, h.stream>>>(fronts, items, n_items, ticket, h.d_err);
+            else k_fwd_sweep<float, float><<<grid, AT, dsm, h.stream>>>(fronts, items, n_items, ticket, h.d_err);
+            count_launch();
+        }
+    } else if (n_items) {
+        if (f64) k_bwd_sweep<double, double><<<grid, AT, dsm, h.stream>>>(fronts, items, n_items, ticket, h.d_err, out);
+        else k_bwd_sweep<float, float><<<grid, AT, dsm, h.stream>>>(fronts, items, n_items, ticket, h.d_err, out);
+        count_launch();
+    }
+    RSD_CUDA_TRY(cudaGetLastError());
+    return RSD_OK;
+}
+
+}  // namespace rsd

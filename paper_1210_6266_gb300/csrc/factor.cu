@@ -66,6 +66,7 @@ __global__ void k_scatter_K(const FrontDesc* __restrict__ fronts, const int64_t*
                     const int mid = (lo + hi) >> 1;
                     if (f.Bd[mid] < j) lo = mid + 1; else hi = mid;
                 }
+                if (lo >= f.b || f.Bd[lo] != j) continue;            // not in this front
                 q = f.s + lo;
             } else {
                 continue;                                            // a descendant's DOF

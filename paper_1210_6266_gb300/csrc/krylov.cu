@@ -150,7 +150,7 @@ int pcg(Handle& h, const double* f, double* u, double tol, rsd_stats* st) {
     const double fnorm = std::sqrt(ff);
     S->history[0] = 1.0;
     if (fnorm == 0.0) { S->relres = 0; return RSD_OK; }
-    RSD_TRY(run_apply(h, r, z));
+    RSD_TRY(h.paper ? run_apply_paper(h, r, z) : run_apply(h, r, z));
     RSD_CUDA_TRY(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, h.stream));
     RSD_TRY(dot(h, r, z, 0));
     int it = 0;
@@ -172,7 +172,7 @@ int pcg(Handle& h, const double* f, double* u, double tol, rsd_stats* st) {
         if (it < 64) S->history[it] = rel;
         if (!(rel == rel)) { rc = RSD_ERR_NOT_SPD; break; }
         if (rel <= tol) { rc = RSD_OK; break; }
-        RSD_TRY(run_apply(h, r, z));
+        RSD_TRY(h.paper ? run_apply_paper(h, r, z) : run_apply(h, r, z));
         RSD_TRY(dot(h, r, z, new_slot));
         const int pd = prof_begin(h, K_KRYLOV);
         k_cg_direction<<<RED_BLOCKS, RT, 0, h.stream>>>(n, h.d_scal, new_slot, old_slot, z, p);

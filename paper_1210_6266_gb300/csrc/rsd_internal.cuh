@@ -107,6 +107,19 @@ struct Level {
     // the level below
     int* d_child_slots = nullptr;
     size_t bytes_P = 0, bytes_U = 0;
+    // paper mode: descriptors of the same fronts restricted to their interface block
+    // (b = 0, no children) and forward items over interface blocks only, used by the
+    // leaf and interface solves of the level-wise Algorithm 2
+    FrontDesc* d_fronts_solve = nullptr;
+    int* d_fwd_items_solve = nullptr;
+    int n_fwd_items_solve = 0;
+};
+
+// Per tree node: where its front lives (paper-mode scatter of leaf updates).
+struct NodeRef {
+    void* P;
+    int ldp;
+    int f64;
 };
 
 struct Handle {
@@ -142,6 +155,15 @@ struct Handle {
     int num_sms = 148;
     void* tc_state = nullptr;            // tensor-core GEMM state (tensor maps, task buffers)
     Prof prof;
+    // paper mode (V-hat truncation, dense S~ per interface)
+    bool paper = false;
+    int* d_owner = nullptr;
+    int* d_rank = nullptr;
+    int* d_node_depth = nullptr;
+    unsigned char* d_node_leaf = nullptr;
+    NodeRef* d_node_ref = nullptr;
+    double *d_pg = nullptr, *d_pw = nullptr, *d_pz = nullptr;   // g, w and leaf-solve scratch
+    int* d_ticket_paper = nullptr;
     // pinned host staging for per-launch uploads (append-only; see stage_host)
     char* stage = nullptr;
     size_t stage_cap = 0, stage_off = 0;
@@ -165,6 +187,12 @@ int launch_extend_add(Handle& h, int li);
 int run_factor_level(Handle& h, int li);
 int run_apply(Handle& h, const double* r, double* z);
 int run_apply_static(Handle& h, const double* r, double* z);
+// one level of a substitution sweep with explicit descriptors/items: forward reads the
+// right-hand side from `in` (through I), backward writes the solution to `out`
+int sweep_with(Handle& h, int li, bool forward, const FrontDesc* fronts, const int* items, int n_items,
+               const double* in, double* out, int* ticket);
+int paper_extend_add(Handle& h);
+int run_apply_paper(Handle& h, const double* r, double* z);
 int spmv(Handle& h, const double* x, double* y);
 
 }  // namespace rsd
