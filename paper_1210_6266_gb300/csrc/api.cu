@@ -11,6 +11,8 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <condition_variable>
+#include <functional>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -167,20 +169,78 @@ void gemm_tc_release(Handle& h);
 
 namespace {
 
+// Persistent worker pool (created on first use) for the host analysis loops.
+class Pool {
+public:
+    static Pool& get() { static Pool p; return p; }
+    int size() const { return (int)workers_.size() + 1; }
+    // run fn(i) for i in [0, n) on the pool and the calling thread
+    void run(int64_t n, const std::function<void(int64_t)>& fn) {
+        std::unique_lock<std::mutex> lk(mu_);
+        job_ = &fn;
+        n_ = n;
+        next_.store(0);
+        active_ = (int)workers_.size();
+        ++gen_;
+        cv_.notify_all();
+        lk.unlock();
+        for (int64_t i; (i = next_.fetch_add(1)) < n;) fn(i);
+        lk.lock();
+        done_.wait(lk, [&] { return active_ == 0; });
+        job_ = nullptr;
+    }
+    ~Pool() {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            stop_ = true;
+            ++gen_;
+        }
+        cv_.notify_all();
+        for (auto& t : workers_) t.join();
+    }
+
+private:
+    Pool() {
+        const int nt = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+        for (int t = 0; t + 1 < nt; ++t)
+            workers_.emplace_back([this] {
+                uint64_t seen = 0;
+                for (;;) {
+                    std::unique_lock<std::mutex> lk(mu_);
+                    cv_.wait(lk, [&] { return stop_ || gen_ != seen; });
+                    if (stop_) return;
+                    seen = gen_;
+                    const std::function<void(int64_t)>* fn = job_;
+                    const int64_t n = n_;
+                    lk.unlock();
+                    for (int64_t i; (i = next_.fetch_add(1)) < n;) (*fn)(i);
+                    lk.lock();
+                    if (--active_ == 0) done_.notify_all();
+                }
+            });
+    }
+    std::vector<std::thread> workers_;
+    std::mutex mu_;
+    std::condition_variable cv_, done_;
+    const std::function<void(int64_t)>* job_ = nullptr;
+    int64_t n_ = 0;
+    std::atomic<int64_t> next_{0};
+    int active_ = 0;
+    uint64_t gen_ = 0;
+    bool stop_ = false;
+};
+
+std::mutex g_pool_mu;     // one analysis at a time uses the pool
+
 template <typename F>
 void parallel_for(int64_t n, F fn) {
-    const int nt = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
-    if (n < 2 || nt == 1) {
+    if (n < 2) {
         for (int64_t i = 0; i < n; ++i) fn(i);
         return;
     }
-    std::atomic<int64_t> next(0);
-    std::vector<std::thread> th;
-    for (int t = 0; t < nt; ++t)
-        th.emplace_back([&]() {
-            for (int64_t i; (i = next.fetch_add(1)) < n;) fn(i);
-        });
-    for (auto& x : th) x.join();
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    const std::function<void(int64_t)> f = fn;
+    Pool::get().run(n, f);
 }
 
 template <typename F>
@@ -252,19 +312,35 @@ int analyse_structure(Analysis& a, const int64_t* rowptr, const int* col, const 
     if (rowptr[0] != 0) return RSD_ERR_ARG;
     for (int i = 0; i < n; ++i)
         if (rowptr[i + 1] < rowptr[i]) return RSD_ERR_ARG;
-    // stable counting sort by owner
+    // stable counting sort by owner, in parallel over DOF chunks (per-chunk histograms)
     a.I_off.assign(a.n_nodes + 1, 0);
-    for (int i = 0; i < n; ++i) a.I_off[a.owner[i] + 1]++;
-    for (int t = 0; t < a.n_nodes; ++t) a.I_off[t + 1] += a.I_off[t];
     a.I_dofs.resize(n);
     a.rank.resize(n);
     {
-        std::vector<int> fill(a.I_off.begin(), a.I_off.end() - 1);
-        for (int i = 0; i < n; ++i) {
-            const int t = a.owner[i];
-            a.rank[i] = fill[t] - a.I_off[t];
-            a.I_dofs[fill[t]++] = i;
+        const int nc = (int)std::max<int64_t>(1, std::min<int64_t>(32, n / 65536 + 1));
+        std::vector<int> cnt((size_t)nc * a.n_nodes, 0);
+        parallel_for(nc, [&](int64_t c) {
+            int* h = cnt.data() + (size_t)c * a.n_nodes;
+            for (int64_t i = n * c / nc; i < n * (c + 1) / nc; ++i) h[a.owner[i]]++;
+        });
+        for (int t = 0; t < a.n_nodes; ++t) {
+            int run = 0;
+            for (int c = 0; c < nc; ++c) {
+                const int v = cnt[(size_t)c * a.n_nodes + t];
+                cnt[(size_t)c * a.n_nodes + t] = run;           // chunk start within node t
+                run += v;
+            }
+            a.I_off[t + 1] = a.I_off[t] + run;
         }
+        parallel_for(nc, [&](int64_t c) {
+            int* h = cnt.data() + (size_t)c * a.n_nodes;
+            for (int64_t i = n * c / nc; i < n * (c + 1) / nc; ++i) {
+                const int t = a.owner[i];
+                const int r = h[t]++;
+                a.rank[i] = r;
+                a.I_dofs[a.I_off[t] + r] = (int)i;
+            }
+        });
     }
     part[0] = ms_since(t0);
     t0 = clk::now();
@@ -293,22 +369,53 @@ int analyse_structure(Analysis& a, const int64_t* rowptr, const int* col, const 
         const auto& nodes = by_depth[d];
         parallel_for((int64_t)nodes.size(), [&](int64_t idx) {
             const int t = nodes[idx];
-            std::vector<int> cand;
+            // one bitmap per proper ancestor, indexed by the DOF's rank in that ancestor
+            thread_local std::vector<uint64_t> bits;
+            thread_local std::vector<int> anc, base;
+            anc.clear();
+            base.clear();
+            size_t words = 0;
+            for (int x = a.parent[t]; x >= 0; x = a.parent[x]) {
+                anc.push_back(x);
+                base.push_back((int)words);
+                words += (size_t)(a.I_off[x + 1] - a.I_off[x] + 63) / 64;
+            }
+            bits.assign(words, 0);
+            auto mark = [&](int j) {
+                const int o = a.owner[j];
+                for (size_t q = 0; q < anc.size(); ++q)
+                    if (anc[q] == o) {
+                        const int r = a.rank[j];
+                        bits[base[q] + (r >> 6)] |= (uint64_t)1 << (r & 63);
+                        return;
+                    }
+            };
             for (int p = a.I_off[t]; p < a.I_off[t + 1]; ++p) {
                 const int i = a.I_dofs[p];
                 for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
                     const int o = a.owner[col[k]];
-                    if (o != t && anc_or_self(a, o, t)) cand.push_back(col[k]);
+                    if (o != t && anc_or_self(a, o, t)) mark(col[k]);
                 }
             }
             for (int c : a.children[t])
-                for (int j : a.B[c]) {
-                    const int o = a.owner[j];
-                    if (o != t && anc_or_self(a, o, t)) cand.push_back(j);
+                for (int j : a.B[c]) mark(j);
+            // each ancestor's list is ascending (I lists are); merge them
+            std::vector<int> out;
+            for (size_t q = 0; q < anc.size(); ++q) {
+                const int x = anc[q];
+                const int sx = a.I_off[x + 1] - a.I_off[x];
+                const size_t mid = out.size();
+                for (int wd = 0; wd < (sx + 63) / 64; ++wd) {
+                    uint64_t m = bits[base[q] + wd];
+                    while (m) {
+                        const int bt = __builtin_ctzll(m);
+                        m &= m - 1;
+                        out.push_back(a.I_dofs[a.I_off[x] + wd * 64 + bt]);
+                    }
                 }
-            std::sort(cand.begin(), cand.end());
-            cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
-            a.B[t] = std::move(cand);
+                std::inplace_merge(out.begin(), out.begin() + mid, out.end());
+            }
+            a.B[t] = std::move(out);
         });
     }
     part[2] = ms_since(t0);
@@ -490,14 +597,14 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
     RSD_CUDA_TRY(cudaMemcpyAsync(h.d_rowptr, rowptr, sizeof(int64_t) * (a.n + 1), cudaMemcpyDefault, st));
     RSD_CUDA_TRY(cudaMemcpyAsync(h.d_col, col, sizeof(int) * h.nnz, cudaMemcpyDefault, st));
     RSD_CUDA_TRY(cudaMemcpyAsync(h.d_val, val, sizeof(double) * h.nnz, cudaMemcpyDefault, st));
-    RSD_CUDA_TRY(cudaMemcpyAsync(d_owner, a.owner.data(), sizeof(int) * a.n, cudaMemcpyHostToDevice, st));
-    RSD_CUDA_TRY(cudaMemcpyAsync(d_rank, a.rank.data(), sizeof(int) * a.n, cudaMemcpyHostToDevice, st));
-    RSD_CUDA_TRY(cudaMemcpyAsync(d_tin, a.tin.data(), sizeof(int) * a.n_nodes, cudaMemcpyHostToDevice, st));
-    RSD_CUDA_TRY(cudaMemcpyAsync(d_tout, a.tout.data(), sizeof(int) * a.n_nodes, cudaMemcpyHostToDevice, st));
-    RSD_CUDA_TRY(cudaMemcpyAsync(d_I, a.I_dofs.data(), sizeof(int) * a.n, cudaMemcpyHostToDevice, st));
+    RSD_CUDA_TRY(cudaMemcpyAsync(d_owner, stage_host(h, a.owner.data(), sizeof(int) * a.n), sizeof(int) * a.n, cudaMemcpyHostToDevice, st));
+    RSD_CUDA_TRY(cudaMemcpyAsync(d_rank, stage_host(h, a.rank.data(), sizeof(int) * a.n), sizeof(int) * a.n, cudaMemcpyHostToDevice, st));
+    RSD_CUDA_TRY(cudaMemcpyAsync(d_tin, stage_host(h, a.tin.data(), sizeof(int) * a.n_nodes), sizeof(int) * a.n_nodes, cudaMemcpyHostToDevice, st));
+    RSD_CUDA_TRY(cudaMemcpyAsync(d_tout, stage_host(h, a.tout.data(), sizeof(int) * a.n_nodes), sizeof(int) * a.n_nodes, cudaMemcpyHostToDevice, st));
+    RSD_CUDA_TRY(cudaMemcpyAsync(d_I, stage_host(h, a.I_dofs.data(), sizeof(int) * a.n), sizeof(int) * a.n, cudaMemcpyHostToDevice, st));
     if (!h.B_dofs.empty()) {
-        RSD_CUDA_TRY(cudaMemcpyAsync(d_B, h.B_dofs.data(), sizeof(int) * h.B_dofs.size(), cudaMemcpyHostToDevice, st));
-        RSD_CUDA_TRY(cudaMemcpyAsync(d_ea, ea_all.data(), sizeof(int) * ea_all.size(), cudaMemcpyHostToDevice, st));
+        RSD_CUDA_TRY(cudaMemcpyAsync(d_B, stage_host(h, h.B_dofs.data(), sizeof(int) * h.B_dofs.size()), sizeof(int) * h.B_dofs.size(), cudaMemcpyHostToDevice, st));
+        RSD_CUDA_TRY(cudaMemcpyAsync(d_ea, stage_host(h, ea_all.data(), sizeof(int) * ea_all.size()), sizeof(int) * ea_all.size(), cudaMemcpyHostToDevice, st));
     }
     RSD_CUDA_TRY(cudaMemsetAsync(h.d_err, 0, sizeof(int) * ERR_SLOTS, st));
     {
@@ -576,12 +683,12 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
     if (items_all.size() > n_items) { set_last_error("work list overflow"); return RSD_ERR_ARG; }
     for (int d = 0; d < nl; ++d) {
         Level& L = h.levels[d];
-        RSD_CUDA_TRY(cudaMemcpyAsync(L.d_fronts, L.fronts.data(), sizeof(FrontDesc) * L.fronts.size(), cudaMemcpyHostToDevice, st));
+        RSD_CUDA_TRY(cudaMemcpyAsync(L.d_fronts, stage_host(h, L.fronts.data(), sizeof(FrontDesc) * L.fronts.size()), sizeof(FrontDesc) * L.fronts.size(), cudaMemcpyHostToDevice, st));
     }
     if (!items_all.empty())
-        RSD_CUDA_TRY(cudaMemcpyAsync(d_items, items_all.data(), sizeof(int) * items_all.size(), cudaMemcpyHostToDevice, st));
+        RSD_CUDA_TRY(cudaMemcpyAsync(d_items, stage_host(h, items_all.data(), sizeof(int) * items_all.size()), sizeof(int) * items_all.size(), cudaMemcpyHostToDevice, st));
     if (!child_tab.empty())
-        RSD_CUDA_TRY(cudaMemcpyAsync(d_child, child_tab.data(), sizeof(int) * child_tab.size(), cudaMemcpyHostToDevice, st));
+        RSD_CUDA_TRY(cudaMemcpyAsync(d_child, stage_host(h, child_tab.data(), sizeof(int) * child_tab.size()), sizeof(int) * child_tab.size(), cudaMemcpyHostToDevice, st));
     RSD_CUDA_TRY(cudaMemsetAsync(d_flags, 0, sizeof(int) * 2 * a.n_nodes, st));
     h.d_owner = d_owner;
     h.d_rank = d_rank;
@@ -610,10 +717,10 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
             }
         }
         for (int t = 0; t < a.n_nodes; ++t) leaf[t] = a.children[t].empty() ? 1 : 0;
-        RSD_CUDA_TRY(cudaMemcpyAsync(h.d_node_ref, refs.data(), sizeof(NodeRef) * refs.size(), cudaMemcpyHostToDevice, st));
-        RSD_CUDA_TRY(cudaMemcpyAsync(h.d_node_leaf, leaf.data(), leaf.size(), cudaMemcpyHostToDevice, st));
-        RSD_CUDA_TRY(cudaMemcpyAsync(h.d_node_depth, a.depth.data(), sizeof(int) * a.n_nodes, cudaMemcpyHostToDevice, st));
-        RSD_CUDA_TRY(cudaMemcpyAsync(d_solve, solve.data(), sizeof(FrontDesc) * solve.size(), cudaMemcpyHostToDevice, st));
+        RSD_CUDA_TRY(cudaMemcpyAsync(h.d_node_ref, stage_host(h, refs.data(), sizeof(NodeRef) * refs.size()), sizeof(NodeRef) * refs.size(), cudaMemcpyHostToDevice, st));
+        RSD_CUDA_TRY(cudaMemcpyAsync(h.d_node_leaf, stage_host(h, leaf.data(), leaf.size()), leaf.size(), cudaMemcpyHostToDevice, st));
+        RSD_CUDA_TRY(cudaMemcpyAsync(h.d_node_depth, stage_host(h, a.depth.data(), sizeof(int) * a.n_nodes), sizeof(int) * a.n_nodes, cudaMemcpyHostToDevice, st));
+        RSD_CUDA_TRY(cudaMemcpyAsync(d_solve, stage_host(h, solve.data(), sizeof(FrontDesc) * solve.size()), sizeof(FrontDesc) * solve.size(), cudaMemcpyHostToDevice, st));
         RSD_CUDA_TRY(cudaStreamSynchronize(st));     // host vectors above go out of scope
     }
     // the tensor-core levels need tensor maps over the fronts just placed

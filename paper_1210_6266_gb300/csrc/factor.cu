@@ -185,23 +185,21 @@ __global__ void __launch_bounds__(256) k_gemm_simt(const GemmTask* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------------
-// Diagonal block: Cholesky of P[k:k+w, k:k+w] (w <= NB) in shared memory, written back to
-// P, then inverted in place and stored as Dinv_k (NB x NB, zero padded).  Blocked by
-// 32-wide sub-panels: a sub-panel's 32 x 32 diagonal block is factored in registers by one
-// warp (row per lane, shuffles), the rows below it are solved one row per thread, and the
-// trailing block is updated with 4 x 4 register tiles.  The inverse inverts the 32 x 32
-// diagonal blocks in parallel (one warp each, column per lane) and then fills the block
-// columns right to left: X_21 = -X_22 L_21 X_11.
-// One CTA per front whose interface extends past k.
+// Diagonal block: Cholesky of P[k:k+w, k:k+w] (w <= NB), written back to P, and its
+// inverse stored as Dinv_k (NB x NB, zero padded).  One CTA per front whose interface
+// extends past k.  The block lives in registers, distributed over a 16 x 16 thread grid:
+// thread (tr, tc) holds e[a][b] = A[16a + tr][16b + tc].  The factorisation takes NB
+// right-looking column steps (the owners of column j broadcast it through shared memory,
+// every thread updates its 8 x 8 elements); the inverse takes NB right-looking row steps
+// of X = L^-1 on the identity.  Entries above the diagonal of the broadcast vectors are
+// zero, so the full-square updates leave finished columns intact; the upper triangle of
+// the register block is never read back.  Beyond w the block is padded with the identity.
 // ---------------------------------------------------------------------------------
-constexpr int DLD = NB + 1;     // shared-memory row stride of the block
+constexpr int DLD = NB + 1;     // shared-memory row stride of L
 
-__device__ __forceinline__ float vcomp(const float4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
-__device__ __forceinline__ double vcomp(const double2& v, int i) { return i == 0 ? v.x : v.y; }
-constexpr int TLD = 33;         // row stride of the 32-column scratch panel
-
-template <typename T>
-__device__ __forceinline__ T shfl(T v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+template <typename T> __device__ __forceinline__ T rsqrt_t(T x);
+template <> __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ double rsqrt_t(double x) { return 1.0 / sqrt(x); }
 
 template <typename T>
 __device__ __forceinline__ T store_round(T x, bool rnd);
@@ -219,204 +217,111 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_potrf_diag(const FrontDesc* __restrict__ fronts, int k,
                                                    int* __restrict__ err, int round_tf32) {
     extern __shared__ unsigned char smem_raw[];
-    T* A = (T*)smem_raw;                      // NB x DLD
-    T* Tm = A + NB * DLD;                     // (NB - 32) x TLD scratch
+    T* A = (T*)smem_raw;                 // L after the factorisation (upper part zero)
+    T* vb = A + NB * DLD;                // two broadcast vectors
     const FrontDesc f = fronts[blockIdx.x];
     if (f.s <= k) return;
     const int w = min(NB, f.s - k);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, tr = tid >> 4, tc = tid & 15;
     T* P = (T*)f.P;
-    __shared__ int bad;
-    if (tid == 0) bad = 0;
-    {   // 16-byte loads, all issued before any is used (the block is NB x NB, rows ldp apart)
-        constexpr int VE = 16 / (int)sizeof(T);                 // elements per 16 bytes
-        constexpr int PER = NB * NB / VE / 256;                 // vectors per thread
-        using V4 = typename std::conditional<sizeof(T) == 8, double2, float4>::type;
-        V4 buf[PER];
+    T e[8][8];
 #pragma unroll
-        for (int q = 0; q < PER; ++q) {
-            const int e = (tid + 256 * q) * VE, r = e / NB, c = e % NB;
-            buf[q] = (r < w && c < w) ? *(const V4*)(P + (int64_t)(k + r) * f.ldp + (k + c)) : V4{};
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const int i = 16 * a + tr, c = 16 * b + tc;
+            e[a][b] = (i < w && c <= i) ? P[(int64_t)(k + i) * f.ldp + (k + c)] : (i == c ? (T)1 : (T)0);
         }
-#pragma unroll
-        for (int q = 0; q < PER; ++q) {
-            const int e = (tid + 256 * q) * VE, r = e / NB, c = e % NB;
-#pragma unroll
-            for (int x = 0; x < VE; ++x)
-                A[r * DLD + c + x] = (r < w && c + x <= r && c + x < w) ? (T)vcomp(buf[q], x) : (T)0;
-        }
-    }
-    __syncthreads();
-    const int npb = (w + 31) / 32;
+    int bad = 0;
     // ---- Cholesky ----
-    for (int p = 0; p < npb; ++p) {
-        const int c0 = p * 32, pw = min(32, w - c0);
-        if (warp == 0) {
-            T v[32];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] = (lane < pw && j <= lane) ? A[(c0 + lane) * DLD + c0 + j] : (T)0;
+    for (int jb = 0; jb < 8; ++jb) {
+#pragma unroll 1
+        for (int jj = 0; jj < 16; ++jj) {
+            const int j = 16 * jb + jj;
+            T* col = vb + (j & 1) * NB;
+            T own[8];
+            if (tc == jj) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                if (j < pw) {
-                    T d = shfl(v[j], j);
-                    if (!(d > (T)0)) { if (lane == 0) bad = 1; d = (T)1; }
-                    const T piv = sqrt(d), inv = (T)1 / piv;
-                    if (lane == j) v[j] = piv;
-                    else if (lane > j) v[j] *= inv;
-#pragma unroll
-                    for (int kk = j + 1; kk < 32; ++kk) {
-                        const T lk = shfl(v[j], kk);
-                        if (lane >= kk) v[kk] -= v[j] * lk;
-                    }
+                for (int a = 0; a < 8; ++a) {
+                    own[a] = e[a][jb];
+                    col[16 * a + tr] = (16 * a + tr >= j) ? own[a] : (T)0;
                 }
             }
+            __syncthreads();
+            T d = col[j];
+            if (!(d > (T)0)) { bad = 1; d = (T)1; }
+            const T inv = rsqrt_t(d), inv2 = inv * inv;
+            T ci[8], ck[8];
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
-                if (lane < pw && j <= lane) A[(c0 + lane) * DLD + c0 + j] = v[j];
-        }
-        __syncthreads();
-        const int r0 = c0 + pw;
-        for (int r = r0 + tid; r < w; r += 256) {          // rows below: x L_pp^T = a
-            T x[32];
+            for (int a = 0; a < 8; ++a) ci[a] = col[16 * a + tr] * inv2;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                if (j < pw) {
-                    T s = A[r * DLD + c0 + j];
+            for (int b = 0; b < 8; ++b) ck[b] = col[16 * b + tc];
 #pragma unroll
-                    for (int kk = 0; kk < j; ++kk) s -= x[kk] * A[(c0 + j) * DLD + c0 + kk];
-                    x[j] = s / A[(c0 + j) * DLD + c0 + j];
-                } else {
-                    x[j] = (T)0;
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int b = 0; b < 8; ++b) e[a][b] -= ci[a] * ck[b];
+            if (tc == jj) {
+#pragma unroll
+                for (int a = 0; a < 8; ++a) {
+                    const int i = 16 * a + tr;
+                    e[a][jb] = i > j ? own[a] * inv : (i == j ? d * inv : own[a]);
                 }
             }
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-                if (j < pw) A[r * DLD + c0 + j] = x[j];
         }
-        __syncthreads();
-        const int rem = w - r0;                              // trailing update, 4 x 4 tiles
-        const int nt = (rem + 3) / 4;
-        for (int t = tid; t < nt * nt; t += 256) {
-            const int tr = t / nt, tc = t % nt;
-            if (tc > tr) continue;
-            T acc[4][4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] = 0;
-            const int ra = r0 + 4 * tr, cb = r0 + 4 * tc;
-            for (int kk = 0; kk < pw; ++kk) {
-                T av[4], bv[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    av[u] = ra + u < w ? A[(ra + u) * DLD + c0 + kk] : (T)0;
-                    bv[u] = cb + u < w ? A[(cb + u) * DLD + c0 + kk] : (T)0;
-                }
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
-            }
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b)
-                    if (ra + a < w && cb + b <= ra + a) A[(ra + a) * DLD + cb + b] -= acc[a][b];
-        }
-        __syncthreads();
     }
-    if (bad && tid == 0) {
+    if (bad) {
         atomicExch(&err[ERR_NOT_SPD], 1);
         atomicMin(&err[ERR_NOT_SPD_NODE], f.node);
     }
-    for (int e = tid; e < w * w; e += 256) {
-        const int r = e / w, c = e % w;
-        if (c <= r) P[(int64_t)(k + r) * f.ldp + (k + c)] = store_round(A[r * DLD + c], round_tf32 != 0);
-    }
-    // ---- inverse: 32 x 32 diagonal blocks, one warp each, column c per lane ----
-    if (warp < npb) {
-        const int c0 = warp * 32, pw = min(32, w - c0);
-        T x[32];
 #pragma unroll
-        for (int r = 0; r < 32; ++r) {
-            if (r < pw && r >= lane) {
-                T s = (r == lane) ? (T)1 : (T)0;
+    for (int a = 0; a < 8; ++a)
 #pragma unroll
-                for (int m = 0; m < r; ++m)
-                    if (m >= lane) s -= A[(c0 + r) * DLD + c0 + m] * x[m];
-                x[r] = s / A[(c0 + r) * DLD + c0 + r];
-            } else {
-                x[r] = (T)0;
-            }
+        for (int b = 0; b < 8; ++b) {
+            const int i = 16 * a + tr, c = 16 * b + tc;
+            A[i * DLD + c] = c <= i ? e[a][b] : (T)0;
+            if (i < w && c <= i) P[(int64_t)(k + i) * f.ldp + (k + c)] = store_round(e[a][b], round_tf32 != 0);
         }
-        __syncwarp();
+    // ---- inverse X = L^-1 ----
 #pragma unroll
-        for (int r = 0; r < 32; ++r)
-            if (r < pw && lane < pw && r >= lane) A[(c0 + r) * DLD + c0 + lane] = x[r];
-    }
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) e[a][b] = (16 * a + tr == 16 * b + tc) ? (T)1 : (T)0;
     __syncthreads();
-    // ---- block columns right to left: X_21 = -(X_22 L_21) X_11 ----
-    // 4 x 4 register tiles: thread t owns rows 4*(t/8).., columns 4*(t%8).. of the block
-    // column (upper triangles in shared memory are zero, so full-range sums are exact).
-    for (int j = npb - 2; j >= 0; --j) {
-        const int c0 = j * 32, b0 = c0 + 32, rows = w - b0;
-        const int ti = tid >> 3, tc = tid & 7;
-        const bool active = 4 * ti < rows;
-        if (active) {                                          // Tm = X_22 * L_21
-            T acc[4][4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+    for (int rb = 0; rb < 8; ++rb) {
+#pragma unroll 1
+        for (int rr = 0; rr < 16; ++rr) {
+            const int r = 16 * rb + rr;
+            T* row = vb + (r & 1) * NB;
+            const T ir = (T)1 / A[r * DLD + r];
+            if (tr == rr) {
 #pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] = 0;
-            const int mend = min(w, b0 + 4 * ti + 4);
-            for (int m = b0; m < mend; ++m) {
-                T xa[4], lb[4];
-#pragma unroll
-                for (int a = 0; a < 4; ++a) xa[a] = A[(b0 + 4 * ti + a) * DLD + m];
-#pragma unroll
-                for (int b = 0; b < 4; ++b) lb[b] = A[m * DLD + c0 + 4 * tc + b];
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) acc[a][b] += xa[a] * lb[b];
+                for (int b = 0; b < 8; ++b) {
+                    e[rb][b] *= ir;
+                    row[16 * b + tc] = e[rb][b];
+                }
             }
+            __syncthreads();
+            T li[8], xr[8];
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+            for (int a = 0; a < 8; ++a) li[a] = (16 * a + tr > r) ? A[(16 * a + tr) * DLD + r] : (T)0;
 #pragma unroll
-                for (int b = 0; b < 4; ++b) Tm[(4 * ti + a) * TLD + 4 * tc + b] = acc[a][b];
+            for (int b = 0; b < 8; ++b) xr[b] = row[16 * b + tc];
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int b = 0; b < 8; ++b) e[a][b] -= li[a] * xr[b];
         }
-        __syncthreads();
-        if (active) {                                          // A_21 = -Tm * X_11
-            T acc[4][4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] = 0;
-#pragma unroll 8
-            for (int m = 0; m < 32; ++m) {
-                T ta[4], xb[4];
-#pragma unroll
-                for (int a = 0; a < 4; ++a) ta[a] = Tm[(4 * ti + a) * TLD + m];
-#pragma unroll
-                for (int b = 0; b < 4; ++b) xb[b] = A[(c0 + m) * DLD + c0 + 4 * tc + b];
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) acc[a][b] += ta[a] * xb[b];
-            }
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-                if (4 * ti + a < rows)
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) A[(b0 + 4 * ti + a) * DLD + c0 + 4 * tc + b] = -acc[a][b];
-        }
-        __syncthreads();
     }
     T* D = (T*)f.Dinv + (int64_t)(k / NB) * NB * NB;
-    for (int e = tid; e < NB * NB; e += 256) {
-        const int r = e / NB, c = e % NB;
-        D[e] = (r < w && c <= r) ? store_round(A[r * DLD + c], round_tf32 != 0) : (T)0;
-    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const int i = 16 * a + tr, c = 16 * b + tc;
+            D[i * NB + c] = (i < w && c <= i) ? store_round(e[a][b], round_tf32 != 0) : (T)0;
+        }
 }
 
 // ---------------------------------------------------------------------------------
@@ -579,7 +484,7 @@ int run_factor_level(Handle& h, int li) {
     // task buffer for this level: one slot per front per launch kind
     GemmTask* d_tasks = nullptr;
     RSD_CUDA_TRY(cudaMallocAsync((void**)&d_tasks, sizeof(GemmTask) * L.fronts.size() * 2 + 64, h.stream));
-    const size_t potrf_smem = (size_t)NB * DLD * es + (size_t)(NB - 32) * TLD * es;
+    const size_t potrf_smem = (size_t)NB * DLD * es + (size_t)2 * NB * es;
     const size_t trsm_smem = (size_t)NB * NB * es + (size_t)TR_ROWS * (NB + 1) * es;
     if (f64) {
         RSD_CUDA_TRY(cudaFuncSetAttribute(k_potrf_diag<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)potrf_smem));
