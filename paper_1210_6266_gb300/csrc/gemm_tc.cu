@@ -284,6 +284,166 @@ k_gemm_tc(const TcTask* __restrict__ tasks, const TcTile* __restrict__ tiles,
     }
 }
 
+// Persistent variant for the long-K 128 x 256 tiles: one CTA per SM walks the tile list
+// with stride gridDim.x.  The smem ring runs continuously across tiles, and the TMEM
+// accumulator is double-buffered (2 x 256 columns), so the epilogue of one tile overlaps
+// the main loop of the next.  Barriers: full/empty per ring stage, and acc_full/acc_empty
+// per accumulator buffer (acc_empty counts the 128 epilogue threads).
+template <int BN, int ST>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+k_gemm_tc_persist(const TcTask* __restrict__ tasks, const TcTile* __restrict__ tiles, int n_tiles,
+                  const CUtensorMap* __restrict__ maps, float* __restrict__ ws, int* __restrict__ err) {
+    extern __shared__ unsigned char smem_raw[];
+    using S = Smem<BN, ST>;
+    constexpr int STAGES = S::STAGES;
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023) & ~1023u;
+    unsigned char* sbase = smem_raw + (base - raw);
+    const uint32_t bar_full = base + STAGES * S::STAGE;            // STAGES x 8 B
+    const uint32_t bar_empty = bar_full + 8 * STAGES;               // STAGES x 8 B
+    const uint32_t bar_accf = bar_empty + 8 * STAGES;               // 2 x 8 B
+    const uint32_t bar_acce = bar_accf + 16;                        // 2 x 8 B
+    uint32_t* tmem_slot = (uint32_t*)(sbase + STAGES * S::STAGE + 16 * STAGES + 32 + 16);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(bar_full + 8 * s, 1);
+            mbar_init(bar_empty + 8 * s, 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(bar_accf + 8 * b, 1);
+            mbar_init(bar_acce + 8 * b, 128);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(tmem_slot)), "r"(2 * BN) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+                const TcTile tl = tiles[t];
+                const TcTask tk = tasks[tl.task];
+                const CUtensorMap* ma = maps + tk.map_a;
+                const CUtensorMap* mb = maps + tk.map_b;
+                const int m0 = tl.tm * BM, n0 = tl.tn * BN;
+                for (int kb = tl.kb0; kb < tl.kb1; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (it / STAGES) & 1;
+                    if (!mbar_wait(bar_empty + 8 * s, ph ^ 1, err)) { ok = false; break; }
+                    const uint32_t sa = base + s * S::STAGE;
+                    const uint32_t sb = sa + S::A_BYTES;
+                    mbar_expect_tx(bar_full + 8 * s, S::STAGE);
+                    const int kx = kb * BK;
+                    tma_load_2d(sa, ma, tk.a_c0 + kx, tk.a_r0 + m0, bar_full + 8 * s);
+#pragma unroll
+                    for (int hh = 0; hh < BN / 128; ++hh)
+                        tma_load_2d(sb + hh * 128 * BK * 4, mb, tk.b_c0 + kx, tk.b_r0 + n0 + hh * 128, bar_full + 8 * s);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_tf32(BN);
+            uint32_t it = 0, tcount = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++tcount) {
+                const TcTile tl = tiles[t];
+                const uint32_t buf = tcount & 1, use = (tcount >> 1) & 1;
+                if (!mbar_wait(bar_acce + 8 * buf, use ^ 1, err)) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t acc = tmem + buf * BN;
+                for (int kb = tl.kb0; kb < tl.kb1; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (it / STAGES) & 1;
+                    if (!mbar_wait(bar_full + 8 * s, ph, err)) { ok = false; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t sa = base + s * S::STAGE;
+                    const uint32_t sb = sa + S::A_BYTES;
+#pragma unroll
+                    for (int k = 0; k < BK / 8; ++k)
+                        mma_tf32(acc, smem_desc(sa + k * 32), smem_desc(sb + k * 32), idesc, (kb != tl.kb0 || k) ? 1u : 0u);
+                    mma_commit(bar_empty + 8 * s);
+                }
+                mma_commit(bar_accf + 8 * buf);
+            }
+        }
+    } else {
+        const int quarter = warp & 3;
+        const int row = quarter * 32 + lane;
+        uint32_t tcount = 0;
+        for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++tcount) {
+            const TcTile tl = tiles[t];
+            const TcTask tk = tasks[tl.task];
+            const uint32_t buf = tcount & 1, use = (tcount >> 1) & 1;
+            const bool ok = mbar_wait(bar_accf + 8 * buf, use, err);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int m0 = tl.tm * BM, n0 = tl.tn * BN;
+            const int gr = m0 + row;
+            float* crow = tk.C + (int64_t)gr * tk.ldc;
+            float* wrow = tl.ws_slot >= 0 ? ws + ((int64_t)tl.ws_slot * BM + row) * BN : nullptr;
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 32) {
+                uint32_t r[32];
+                tmem_ld32(tmem + buf * BN + ((uint32_t)(quarter * 32) << 16) + c0, r);
+                if (!ok) continue;
+                if (wrow) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        *(float4*)(wrow + c0 + 4 * q) = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                                                                    __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+                    continue;
+                }
+                if (gr >= tk.M) continue;
+                const int gc0 = n0 + c0;
+                if (gc0 >= tk.N) continue;
+                if (tk.lower && gc0 > gr) continue;
+                if (gc0 + 32 <= tk.N && (!tk.lower || gc0 + 31 <= gr)) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        float4* p = (float4*)(crow + gc0 + 4 * q);
+                        float4 o = tk.beta ? *p : make_float4(0.f, 0.f, 0.f, 0.f);
+                        o.x += tk.alpha * __uint_as_float(r[4 * q + 0]);
+                        o.y += tk.alpha * __uint_as_float(r[4 * q + 1]);
+                        o.z += tk.alpha * __uint_as_float(r[4 * q + 2]);
+                        o.w += tk.alpha * __uint_as_float(r[4 * q + 3]);
+                        if (tk.round_tf32) { o.x = tf32_rn(o.x); o.y = tf32_rn(o.y); o.z = tf32_rn(o.z); o.w = tf32_rn(o.w); }
+                        *p = o;
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        const int gc = gc0 + q;
+                        if (gc < tk.N && (!tk.lower || gc <= gr)) {
+                            float* p = crow + gc;
+                            const float o = (tk.beta ? *p : 0.f) + tk.alpha * __uint_as_float(r[q]);
+                            *p = tk.round_tf32 ? tf32_rn(o) : o;
+                        }
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar_acce + 8 * buf) : "memory");
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    }
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN) : "memory");
+    }
+}
+
 // Split-K reduction: C = beta*C + alpha * sum_s partial_s, summed in slot order.
 template <int BN>
 __global__ void __launch_bounds__(256) k_splitk_reduce(const TcTask* __restrict__ tasks, const TcRed* __restrict__ reds,
@@ -454,6 +614,7 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
         RSD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<128, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<128, 3>::TOTAL));
         RSD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<128, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<128, 6>::TOTAL));
         RSD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<256, 4>::TOTAL));
+        RSD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc_persist<256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<256, 4>::TOTAL));
         st->attr_set = true;
     }
     double fl = 0, by = 0;
@@ -469,8 +630,11 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
         k_gemm_tc<128, 3><<<(unsigned)tl.size(), TC_THREADS, Smem<128, 3>::TOTAL, stream>>>(st->d_tasks, st->d_tiles, st->d_maps, st->d_ws, h.d_err);
     else if (bn == 128)
         k_gemm_tc<128, 6><<<(unsigned)tl.size(), TC_THREADS, Smem<128, 6>::TOTAL, stream>>>(st->d_tasks, st->d_tiles, st->d_maps, st->d_ws, h.d_err);
-    else
-        k_gemm_tc<256, 4><<<(unsigned)tl.size(), TC_THREADS, Smem<256, 4>::TOTAL, stream>>>(st->d_tasks, st->d_tiles, st->d_maps, st->d_ws, h.d_err);
+    else {
+        const int ctas = std::min((int)tl.size(), h.num_sms);
+        k_gemm_tc_persist<256, 4><<<(unsigned)ctas, TC_THREADS, Smem<256, 4>::TOTAL, stream>>>(
+            st->d_tasks, st->d_tiles, (int)tl.size(), st->d_maps, st->d_ws, h.d_err);
+    }
     count_launch();
     if (!rd.empty()) {
         if (bn == 128) k_splitk_reduce<128><<<(unsigned)rd.size(), 256, 0, stream>>>(st->d_tasks, st->d_reds, st->d_ws);
