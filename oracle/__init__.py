@@ -11,6 +11,7 @@ Modules and what each follows:
   rsd_paper  Algorithm 2 with the V-hat truncation and Algorithm 1 (Sec. 3.2-3.3)
   krylov     PCG and flexible GMRES (the outer solver of Sec. 3)
   problem    convenience: a synthetic workload -> matrix, load, owner map, tree
+  adjoint    adjoint solve and per-element coefficient gradient of u = K(kappa)^-1 b
 
 Functions with no independent pin are marked "parity unpinned" in their docstring;
 currently there are none.
