@@ -18,8 +18,9 @@ from . import _lib
 from ._lib import (RSD_MEM_DEVICE, RSD_MEM_HOST, RSD_MODE_EXACT, RSD_MODE_PAPER, RSD_PREC_FP32,
                    RSD_PREC_FP64, RSD_PREC_TF32, RSDError, check)
 
-__all__ = ["RSD", "grid_problem", "grid_sizes", "launch_count", "RSDError", "RSD_PREC_FP64",
-           "RSD_PREC_FP32", "RSD_PREC_TF32", "RSD_MODE_EXACT", "RSD_MODE_PAPER"]
+__all__ = ["RSD", "grid_problem", "grid_sizes", "grid_exp", "coef_grad", "diffusion_solve",
+           "DiffusionSolve", "launch_count", "RSDError", "RSD_PREC_FP64", "RSD_PREC_FP32",
+           "RSD_PREC_TF32", "RSD_MODE_EXACT", "RSD_MODE_PAPER"]
 
 
 def launch_count() -> int:
@@ -46,22 +47,52 @@ def grid_problem(n: int, depth: int, kappa, f, device: str = "cuda") -> dict:
     """Assemble K (CSR, FP64), b = h^3 f, the octree ownership and tree on the GPU.
     kappa: (n-1)^3 per-element coefficients; f: (n-2)^3 nodal loads."""
     lib = _lib.load()
-    nd, nz = grid_sizes(n)
+    nd, _ = grid_sizes(n)
     kap = torch.as_tensor(np.ascontiguousarray(kappa), dtype=torch.float64).to(device)
     fn = torch.as_tensor(np.ascontiguousarray(f), dtype=torch.float64).to(device)
+    prob = _grid_system(n, depth, kap)
+    b = torch.empty(nd, dtype=torch.float64, device=device)
+    check(lib.rsd_grid_load(n, _ptr(fn), _ptr(b), _stream()), "rsd_grid_load")
+    prob["b"] = b
+    return prob
+
+
+def _grid_system(n: int, depth: int, kappa: torch.Tensor) -> dict:
+    """K(kappa) in CSR and the octree ownership, assembled on kappa's device."""
+    lib = _lib.load()
+    nd, nz = grid_sizes(n)
+    device = kappa.device
     rowptr = torch.empty(nd + 1, dtype=torch.int64, device=device)
     col = torch.empty(nz, dtype=torch.int32, device=device)
     val = torch.empty(nz, dtype=torch.float64, device=device)
-    b = torch.empty(nd, dtype=torch.float64, device=device)
     dof_node = torch.empty(nd, dtype=torch.int32, device=device)
     n_nodes = (8 ** (depth + 1) - 1) // 7
     parent = np.empty(n_nodes, dtype=np.int32)
     st = _stream()
-    check(lib.rsd_grid_assemble(n, _ptr(kap), _ptr(rowptr), _ptr(col), _ptr(val), st), "rsd_grid_assemble")
-    check(lib.rsd_grid_load(n, _ptr(fn), _ptr(b), st), "rsd_grid_load")
+    check(lib.rsd_grid_assemble(n, _ptr(kappa), _ptr(rowptr), _ptr(col), _ptr(val), st), "rsd_grid_assemble")
     check(lib.rsd_grid_partition(n, depth, _ptr(dof_node), parent.ctypes.data, st), "rsd_grid_partition")
-    return dict(n=n, depth=depth, n_dof=nd, nnz=nz, rowptr=rowptr, col=col, val=val, b=b,
+    return dict(n=n, depth=depth, n_dof=nd, nnz=nz, rowptr=rowptr, col=col, val=val,
                 dof_node=dof_node, parent=parent)
+
+
+def grid_exp(n: int, m: torch.Tensor) -> torch.Tensor:
+    """kappa = exp(m) per element, on the device (rsd_grid_exp)."""
+    m = m.to(torch.float64).contiguous()
+    kappa = torch.empty_like(m)
+    check(_lib.load().rsd_grid_exp(n, _ptr(m), _ptr(kappa), _stream()), "rsd_grid_exp")
+    return kappa
+
+
+def coef_grad(n: int, u: torch.Tensor, lam: torch.Tensor, kappa: torch.Tensor | None = None):
+    """Per-element dL/dkappa = -lam_e^T K_e u_e and, given kappa, dL/dm = kappa * dL/dkappa
+    (rsd_grid_coef_grad).  Returns (dkappa, dm or None)."""
+    ne3 = (n - 1) ** 3
+    dk = torch.empty(ne3, dtype=torch.float64, device=u.device)
+    dm = torch.empty_like(dk) if kappa is not None else None
+    check(_lib.load().rsd_grid_coef_grad(n, _ptr(u), _ptr(lam), _ptr(kappa) if kappa is not None else None,
+                                         _ptr(dk), _ptr(dm) if dm is not None else None, _stream()),
+          "rsd_grid_coef_grad")
+    return dk, dm
 
 
 class RSD:
@@ -160,6 +191,16 @@ class RSD:
         return u, dict(iterations=st.iterations, relres=st.relres,
                        relres_recursive=st.relres_recursive, history=hist)
 
+    def solve_adjoint(self, g: torch.Tensor, tol: float = 1e-8, lam: torch.Tensor | None = None,
+                      allow_noconv: bool = False):
+        """lam with K^T lam = g on the same hierarchy (rsd_solve_adjoint)."""
+        lam = torch.empty_like(g) if lam is None else lam
+        st = _lib.rsd_stats()
+        rc = _lib.load().rsd_solve_adjoint(self._h, _ptr(g), _ptr(lam), tol, C.byref(st))
+        if rc != 0 and not (allow_noconv and rc == _lib.RSD_ERR_NOCONV):
+            raise RSDError(rc, "rsd_solve_adjoint")
+        return lam, dict(iterations=st.iterations, relres=st.relres)
+
     def check(self) -> None:
         check(_lib.load().rsd_check(self._h), "rsd_check")
 
@@ -172,6 +213,17 @@ class RSD:
         out["host_analysis_ms"] = p.host_analysis_ms
         out["host_parts_ms"] = dict(zip(["copy", "sort", "check", "sets", "maps", "plan"], list(p.host_parts_ms)))
         return out
+
+    def trace(self) -> list[dict]:
+        """Per-launch profile records (class, stream, start/end ms, flops, bytes) in issue
+        order; call before a resetting profile()."""
+        lib = _lib.load()
+        n = C.c_int64()
+        check(lib.rsd_profile_trace(self._h, None, 0, C.byref(n)), "rsd_profile_trace")
+        recs = (_lib.rsd_trace_rec * max(n.value, 1))()
+        check(lib.rsd_profile_trace(self._h, recs, n.value, C.byref(n)), "rsd_profile_trace")
+        return [dict(cls=_lib.PROFILE_CLASSES[r.cls], stream=r.stream, start_ms=r.start_ms, end_ms=r.end_ms,
+                     flops=r.flops, bytes=r.bytes) for r in recs[: n.value]]
 
     def info(self) -> dict:
         inf = _lib.rsd_info_t()
@@ -200,3 +252,34 @@ class RSD:
         out = np.empty((s + b) * max(s, 1), dtype=np.float64)
         check(_lib.load().rsd_front_factor(self._h, node, out.ctypes.data), "rsd_front_factor")
         return out[: (s + b) * s].reshape(s + b, s)
+
+
+class DiffusionSolve(torch.autograd.Function):
+    """u = K(exp(m))^-1 b for -div(kappa grad u) = f on the n^3 grid, differentiable in the
+    per-element log-coefficient m and the load b.  Forward: rsd_grid_exp, rsd_grid_assemble,
+    rsd_setup, rsd_solve.  Backward (the adjoint method): lam = rsd_solve_adjoint(dL/du) on
+    the forward's hierarchy, dL/dm = rsd_grid_coef_grad(u, lam, kappa), dL/db = lam."""
+
+    @staticmethod
+    def forward(ctx, m, b, n, depth, tol, precs, maxit):
+        kappa = grid_exp(n, m.detach())
+        prob = _grid_system(n, depth, kappa)
+        h = RSD.setup(prob["rowptr"], prob["col"], prob["val"], prob["dof_node"], prob["parent"],
+                      prec_leaf=precs[0], prec_mid=precs[1], prec_root=precs[2], maxit=maxit)
+        u, st = h.solve(b.detach().to(torch.float64).contiguous(), tol=tol)
+        ctx.h, ctx.n, ctx.tol, ctx.stats = h, n, tol, st
+        ctx.save_for_backward(kappa, u)
+        return u
+
+    @staticmethod
+    def backward(ctx, gu):
+        kappa, u = ctx.saved_tensors
+        lam, _ = ctx.h.solve_adjoint(gu.to(torch.float64).contiguous(), tol=ctx.tol)
+        _, dm = coef_grad(ctx.n, u, lam, kappa)
+        return dm, lam, None, None, None, None, None
+
+
+def diffusion_solve(m: torch.Tensor, b: torch.Tensor, n: int, depth: int, tol: float = 1e-10,
+                    precs=(RSD_PREC_FP64, RSD_PREC_FP64, RSD_PREC_FP64), maxit: int = 500) -> torch.Tensor:
+    """Differentiable solve (DiffusionSolve.apply); m: (n-1)^3 elements, b: (n-2)^3 nodes."""
+    return DiffusionSolve.apply(m, b, n, depth, tol, tuple(precs), maxit)

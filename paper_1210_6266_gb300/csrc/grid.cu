@@ -109,6 +109,46 @@ __global__ void k_grid_partition(int n, int depth, int* owner) {
     owner[i] = node;
 }
 
+// kappa_e = exp(m_e): the log-coefficient parametrisation used by the gradient workload.
+__global__ void k_grid_exp(int64_t ne3, const double* __restrict__ m, double* __restrict__ kappa) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < ne3) kappa[e] = exp(m[e]);
+}
+
+// Adjoint coefficient gradient, one thread per element e: K depends linearly on kappa_e
+// through K_e = h Khat (Sec. 4's discretisation), so d(lam^T K u)/dkappa_e = lam_e^T K_e u_e
+// and dL/dkappa_e = -lam_e^T K_e u_e when K^T lam = dL/du.  Boundary nodes carry 0.
+// Threads of a warp take consecutive ex, so the nodal gathers are coalesced rows.
+__global__ void k_grid_coef_grad(int n, const double* __restrict__ u, const double* __restrict__ lam,
+                                 const double* __restrict__ kappa, double* __restrict__ dkappa,
+                                 double* __restrict__ dm) {
+    const int m = n - 2, ne = n - 1;
+    const int64_t ne3 = (int64_t)ne * ne * ne;
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= ne3) return;
+    const int ex = (int)(e % ne), ey = (int)((e / ne) % ne), ez = (int)(e / ((int64_t)ne * ne));
+    double ue[8], le[8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        const int x = ex + (a & 1), y = ey + ((a >> 1) & 1), z = ez + (a >> 2);
+        const bool in = x >= 1 && x <= m && y >= 1 && y <= m && z >= 1 && z <= m;
+        const int64_t id = (x - 1) + (int64_t)m * ((y - 1) + (int64_t)m * (z - 1));
+        ue[a] = in ? u[id] : 0.0;
+        le[a] = in ? lam[id] : 0.0;
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        double w = 0.0;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) w += khat(a, b) * ue[b];
+        s += le[a] * w;
+    }
+    const double g = -s / (n - 1);                          // h = 1/(n-1)
+    if (dkappa) dkappa[e] = g;
+    if (dm) dm[e] = kappa[e] * g;
+}
+
 }  // namespace
 }  // namespace rsd
 
@@ -158,6 +198,29 @@ extern "C" int rsd_grid_partition(int32_t n, int32_t depth, int32_t* dof_node, i
     for (int64_t t = 0; t < n_nodes; ++t) parent[t] = t == 0 ? -1 : (int32_t)((t - 1) / 8);
     const int T = 256;
     k_grid_partition<<<(unsigned)((ndof + T - 1) / T), T, 0, (cudaStream_t)stream>>>(n, depth, dof_node);
+    count_launch();
+    RSD_CUDA_TRY(cudaGetLastError());
+    return RSD_OK;
+}
+
+extern "C" int rsd_grid_exp(int32_t n, const double* m, double* kappa, void* stream) {
+    if (n < 3 || !m || !kappa) return RSD_ERR_ARG;
+    const int64_t ne3 = (int64_t)(n - 1) * (n - 1) * (n - 1);
+    const int T = 256;
+    k_grid_exp<<<(unsigned)((ne3 + T - 1) / T), T, 0, (cudaStream_t)stream>>>(ne3, m, kappa);
+    count_launch();
+    RSD_CUDA_TRY(cudaGetLastError());
+    return RSD_OK;
+}
+
+extern "C" int rsd_grid_coef_grad(int32_t n, const double* u, const double* lam, const double* kappa,
+                                  double* dkappa, double* dm, void* stream) {
+    int64_t ndof, nnz;
+    RSD_TRY(rsd_grid_sizes(n, &ndof, &nnz));
+    if (!u || !lam || (!dkappa && !dm) || (dm && !kappa)) return RSD_ERR_ARG;
+    const int64_t ne3 = (int64_t)(n - 1) * (n - 1) * (n - 1);
+    const int T = 256;
+    k_grid_coef_grad<<<(unsigned)((ne3 + T - 1) / T), T, 0, (cudaStream_t)stream>>>(n, u, lam, kappa, dkappa, dm);
     count_launch();
     RSD_CUDA_TRY(cudaGetLastError());
     return RSD_OK;
