@@ -128,6 +128,17 @@ typedef struct {
                                     memory plan with its uploads                          */
 } rsd_profile_t;
 
+/* one profiled launch (rsd_profile_trace): its class (as above), the stream it ran on
+ * (0 = the caller's stream, 1 = the library's look-ahead stream used while factoring
+ * levels with few fronts), start and end in ms from the first recorded launch, and its
+ * algorithmic flops and bytes.                                                        */
+typedef struct {
+    int32_t cls;
+    int32_t stream;
+    double  start_ms, end_ms;
+    double  flops, bytes;
+} rsd_trace_rec;
+
 typedef struct rsd_handle_s* rsd_handle;
 
 /* ---- the three calls of the method --------------------------------------------- */
@@ -193,6 +204,14 @@ int rsd_apply_static(rsd_handle h, const double* r, double* z);
  * Returns RSD_ERR_NOCONV if maxit iterations did not reach tol (u, st still valid).      */
 int rsd_solve(rsd_handle h, const double* f, double* u, double tol, rsd_stats* st);
 
+/* rsd_solve_adjoint -- the adjoint system K^T lam = g of the gradient of a loss L(u) with
+ * u = K^-1 f (dL/df = lam, dL/dK = -lam u^T).  The paper has no counterpart: it is the
+ * standard adjoint method applied to the solve above.  The hierarchy only holds
+ * symmetric K (its fronts are Cholesky-factored), so K^T = K and the call runs the same
+ * preconditioned CG on the same fronts, with no second setup.
+ *   g, lam : device, n FP64 entries.  st : host, may be NULL.  Errors as rsd_solve.     */
+int rsd_solve_adjoint(rsd_handle h, const double* g, double* lam, double tol, rsd_stats* st);
+
 /* rsd_check -- synchronise the handle's stream and report any device-side error flag
  * (timeout of a bounded wait, failed pivot) raised since setup.                        */
 int rsd_check(rsd_handle h);
@@ -225,6 +244,12 @@ int rsd_front_factor(rsd_handle h, int32_t node, double* out);
  * clears it afterwards.                                                               */
 int rsd_profile(rsd_handle h, rsd_profile_t* out, int32_t reset);
 
+/* rsd_profile_trace -- the individual launch records behind rsd_profile, in issue order
+ * (a timeline of setup and solve).  Synchronises like rsd_profile and must be called
+ * before a resetting rsd_profile.  Writes min(cap, count) records to out (host; may be
+ * NULL when cap = 0) and the total count to *n.                                       */
+int rsd_profile_trace(rsd_handle h, rsd_trace_rec* out, int64_t cap, int64_t* n);
+
 /* rsd_launch_count -- kernels this library has launched in this process so far.       */
 int64_t rsd_launch_count(void);
 
@@ -247,6 +272,18 @@ int rsd_grid_load(int32_t n, const double* f, double* b, void* stream);
  * ((8^(depth+1)-1)/7 entries, breadth-first ids).                                       */
 int rsd_grid_partition(int32_t n, int32_t depth, int32_t* dof_node, int32_t* parent,
                        void* stream);
+/* kappa = exp(m) per element, both device, (n-1)^3 entries (kappa's log parametrisation). */
+int rsd_grid_exp(int32_t n, const double* m, double* kappa, void* stream);
+/* per-element coefficient gradient for -div(kappa grad u) with kappa constant per
+ * element: K = sum_e kappa_e K_e with K_e = h Khat on the element's interior nodes, so
+ * for K^T lam = dL/du the gradient is dL/dkappa_e = -lam_e^T K_e u_e, and with kappa =
+ * exp(m), dL/dm_e = kappa_e dL/dkappa_e.  The paper has no counterpart (the adjoint
+ * method applied to Sec. 4's discretisation).
+ *   u, lam : device, n_dof entries; kappa : device, (n-1)^3 (only read for dm);
+ *   dkappa, dm : device, (n-1)^3 outputs, either may be NULL (not both).  One thread per
+ * element, deterministic.  RSD_ERR_ARG on a bad n or pointer.                             */
+int rsd_grid_coef_grad(int32_t n, const double* u, const double* lam, const double* kappa,
+                       double* dkappa, double* dm, void* stream);
 
 #ifdef __cplusplus
 }

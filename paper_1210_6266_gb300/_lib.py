@@ -35,7 +35,8 @@ EXPORTS = [
     "rsd_get_info", "rsd_front_dims", "rsd_front_dofs", "rsd_front_map", "rsd_front_factor",
     "rsd_grid_sizes", "rsd_grid_assemble", "rsd_grid_load", "rsd_grid_partition",
     "rsd_profile", "rsd_launch_count", "rsd_apply_static", "rsd_last_error_detail",
-    "rsd_release_cache", "rsd_setup_batched",
+    "rsd_release_cache", "rsd_setup_batched", "rsd_solve_adjoint", "rsd_grid_exp",
+    "rsd_grid_coef_grad", "rsd_profile_trace",
 ]
 
 
@@ -76,6 +77,11 @@ class rsd_profile_t(C.Structure):
                 ("host_parts_ms", C.c_double * 6)]
 
 
+class rsd_trace_rec(C.Structure):
+    _fields_ = [("cls", C.c_int32), ("stream", C.c_int32), ("start_ms", C.c_double),
+                ("end_ms", C.c_double), ("flops", C.c_double), ("bytes", C.c_double)]
+
+
 _lib = None
 
 
@@ -91,6 +97,7 @@ def load() -> C.CDLL:
             "rsd_apply": (C.c_int, [P, P, P]),
             "rsd_apply_static": (C.c_int, [P, P, P]),
             "rsd_solve": (C.c_int, [P, P, P, C.c_double, C.POINTER(rsd_stats)]),
+            "rsd_solve_adjoint": (C.c_int, [P, P, P, C.c_double, C.POINTER(rsd_stats)]),
             "rsd_check": (C.c_int, [P]),
             "rsd_destroy": (None, [P]),
             "rsd_strerror": (C.c_char_p, [C.c_int]),
@@ -104,7 +111,10 @@ def load() -> C.CDLL:
             "rsd_grid_assemble": (C.c_int, [C.c_int32, P, P, P, P, P]),
             "rsd_grid_load": (C.c_int, [C.c_int32, P, P, P]),
             "rsd_grid_partition": (C.c_int, [C.c_int32, C.c_int32, P, P, P]),
+            "rsd_grid_exp": (C.c_int, [C.c_int32, P, P, P]),
+            "rsd_grid_coef_grad": (C.c_int, [C.c_int32, P, P, P, P, P, P]),
             "rsd_profile": (C.c_int, [P, C.POINTER(rsd_profile_t), C.c_int32]),
+            "rsd_profile_trace": (C.c_int, [P, P, C.c_int64, C.POINTER(C.c_int64)]),
             "rsd_launch_count": (C.c_int64, []),
             "rsd_release_cache": (None, []),
             "rsd_setup_batched": (C.c_int, [C.c_int32, C.POINTER(rsd_csr), P, C.POINTER(rsd_tree),

@@ -118,6 +118,7 @@ const void* stage_host(Handle& h, const void* src, size_t bytes) {
     const size_t need = (bytes + 255) & ~(size_t)255;
     if (h.stage_off + need > h.stage_cap) {
         cudaStreamSynchronize(h.stream);              // every earlier copy has completed
+        if (h.chain) cudaStreamSynchronize(h.chain);
         h.stage_off = 0;
         if (need > h.stage_cap) {
             if (h.stage) pinned_give(h.stage, h.stage_cap);
@@ -143,24 +144,24 @@ static void arena_give(char* p, size_t bytes, int dev) {
 }
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
-int prof_begin(Handle& h, int cls) {
+int prof_begin(Handle& h, int cls, cudaStream_t stream) {
     if (!h.prof.on) return -1;
-    Prof::Rec r{cls, 0.0, 0.0, nullptr, nullptr};
+    Prof::Rec r{cls, 0.0, 0.0, nullptr, nullptr, (h.chain && stream == h.chain) ? 1 : 0};
     for (cudaEvent_t* e : {&r.a, &r.b}) {
         if (!h.prof.pool.empty()) { *e = h.prof.pool.back(); h.prof.pool.pop_back(); }
         else if (cudaEventCreate(e) != cudaSuccess) { cudaGetLastError(); return -1; }
     }
-    cudaEventRecord(r.a, h.stream);
+    cudaEventRecord(r.a, stream);
     h.prof.recs.push_back(r);
     return (int)h.prof.recs.size() - 1;
 }
 
-void prof_end(Handle& h, int idx, double flops, double bytes) {
+void prof_end(Handle& h, int idx, double flops, double bytes, cudaStream_t stream) {
     if (idx < 0 || idx >= (int)h.prof.recs.size()) return;
     Prof::Rec& r = h.prof.recs[idx];
     r.flops = flops;
     r.bytes = bytes;
-    cudaEventRecord(r.b, h.stream);
+    cudaEventRecord(r.b, stream);
 }
 
 int pcg(Handle& h, const double* f, double* u, double tol, rsd_stats* st);
@@ -826,10 +827,32 @@ extern "C" int rsd_profile(rsd_handle hh, rsd_profile_t* out, int32_t reset) {
     return RSD_OK;
 }
 
+extern "C" int rsd_profile_trace(rsd_handle hh, rsd_trace_rec* out, int64_t cap, int64_t* n) {
+    if (!hh || !n || cap < 0 || (cap > 0 && !out)) return RSD_ERR_ARG;
+    Handle& h = hh->h;
+    RSD_CUDA_TRY(cudaStreamSynchronize(h.stream));
+    if (h.chain) RSD_CUDA_TRY(cudaStreamSynchronize(h.chain));
+    *n = (int64_t)h.prof.recs.size();
+    for (int64_t i = 0; i < std::min(cap, *n); ++i) {
+        const Prof::Rec& r = h.prof.recs[i];
+        float t0 = 0, t1 = 0;
+        if (cudaEventElapsedTime(&t0, h.prof.recs[0].a, r.a) != cudaSuccess) { cudaGetLastError(); t0 = 0; }
+        if (cudaEventElapsedTime(&t1, h.prof.recs[0].a, r.b) != cudaSuccess) { cudaGetLastError(); t1 = 0; }
+        out[i] = rsd_trace_rec{r.cls, r.stream, t0, t1, r.flops, r.bytes};
+    }
+    return RSD_OK;
+}
+
 extern "C" void rsd_destroy(rsd_handle hh) {
     if (!hh) return;
     Handle& h = hh->h;
     if (h.stream) cudaStreamSynchronize(h.stream);
+    if (h.chain) {
+        cudaStreamSynchronize(h.chain);
+        cudaStreamDestroy(h.chain);
+    }
+    for (cudaEvent_t e : {h.ev_ready, h.ev_join, h.ev_diag[0], h.ev_diag[1], h.ev_diag[2], h.ev_diag[3]})
+        if (e) cudaEventDestroy(e);
     gemm_tc_release(h);
     for (auto& r : h.prof.recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : h.prof.pool) cudaEventDestroy(e);
@@ -955,6 +978,12 @@ extern "C" int rsd_solve(rsd_handle hh, const double* f, double* u, double tol, 
     const int chk = rsd_check(hh);
     if (chk != RSD_OK) return chk;
     return rc;
+}
+
+extern "C" int rsd_solve_adjoint(rsd_handle hh, const double* g, double* lam, double tol, rsd_stats* st) {
+    // Every matrix the hierarchy holds is symmetric (its fronts are Cholesky-factored), so
+    // K^T lam = g is the same system as K lam = g: same fronts, same PCG, no new setup.
+    return rsd_solve(hh, g, lam, tol, st);
 }
 
 extern "C" int rsd_get_info(rsd_handle hh, rsd_info_t* out) {

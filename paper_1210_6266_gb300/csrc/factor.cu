@@ -25,9 +25,6 @@
 
 namespace rsd {
 
-int gemm_tc_launch(Handle& h, int li, const std::vector<GemmTask>& tasks, int kind,
-                   cudaStream_t st);   // tensor-core path (gemm_tc.cu)
-
 namespace {
 
 template <typename T>
@@ -474,6 +471,137 @@ int launch_extend_add(Handle& h, int li) {
     return RSD_OK;
 }
 
+// ---------------------------------------------------------------------------------
+// Look-ahead order for tensor-core levels with few fronts (the root and the level below
+// it), where the diagonal factor+inverse of one front runs on a single SM and would
+// otherwise idle the GPU: per outer panel p (columns K0 .. K0+W),
+//   chain stream (high priority): the steps (a)-(c) restricted to the W x W diagonal
+//     block of the panel -- small GEMMs and the 128-block factor+inverse;
+//   bulk stream (the caller's): the same steps for the rows below the block, each
+//     released by an event after the diagonal block it needs; and, one panel ahead, the
+//     part of the next panel's outer update (a0) whose K range [0, K0) covers finished
+//     panels only -- it overlaps the chain.  The remaining K range [K0, K0+W) of that
+//     update runs when panel p is done.
+// Every entry receives the same products as in the single-stream order; only the outer
+// update's K range is summed in two parts.  The bulk persistent GEMM leaves a few SMs
+// to the chain.
+constexpr int LOOKAHEAD_FRONTS = 16;
+
+static int ensure_chain(Handle& h) {
+    if (h.chain) return RSD_OK;
+    int lo = 0, hi = 0;
+    RSD_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    RSD_CUDA_TRY(cudaStreamCreateWithPriority(&h.chain, cudaStreamNonBlocking, hi));
+    for (cudaEvent_t* e : {&h.ev_ready, &h.ev_join, &h.ev_diag[0], &h.ev_diag[1], &h.ev_diag[2], &h.ev_diag[3]})
+        RSD_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    return RSD_OK;
+}
+
+static int factor_level_lookahead(Handle& h, int li) {
+    static_assert(WOUT / NB == 4, "one diagonal event per inner block of an outer panel");
+    Level& L = h.levels[li];
+    const size_t es = 4;
+    const size_t potrf_smem = (size_t)NB * DLD * es + (size_t)2 * NB * es;
+    RSD_CUDA_TRY(cudaFuncSetAttribute(k_potrf_diag<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)potrf_smem));
+    RSD_TRY(ensure_chain(h));
+    const int nf = (int)L.fronts.size();
+    const int bulk_ctas = h.num_sms - std::min(h.num_sms / 4, nf + 1);
+    cudaStream_t B = h.stream, Cs = h.chain;
+    std::vector<GemmTask> tasks;
+    auto wend = [](const FrontDesc& f, int K0) { return std::min(K0 + WOUT, f.s); };
+    auto P = [&](const FrontDesc& f, int r, int c) { return (char*)f.P + ((int64_t)r * f.ldp + c) * es; };
+    // (a) rows [r0, r1) of column block k from the finished columns [K0, k)
+    auto add_update = [&](const FrontDesc& f, int k, int K0, int r0, int r1) {
+        if (f.s <= k || k <= K0 || r1 <= r0) return;
+        GemmTask t{};
+        t.A = P(f, r0, K0); t.B = P(f, k, K0); t.C = P(f, r0, k);
+        t.lda = t.ldb = t.ldc = f.ldp;
+        t.M = r1 - r0; t.N = std::min(NB, f.s - k); t.K = k - K0;
+        t.lower = 0; t.beta = 1;
+        t.map_a = t.map_b = f.node;
+        t.a_r0 = r0; t.a_c0 = K0; t.b_r0 = k; t.b_c0 = K0;
+        tasks.push_back(t);
+    };
+    // (c) rows [r0, r1) of column block k times the inverted diagonal block
+    auto add_solve = [&](const FrontDesc& f, int k, int r0, int r1) {
+        if (f.s <= k || r1 <= r0) return;
+        GemmTask t{};
+        t.A = P(f, r0, k); t.B = (const char*)f.Dinv + (int64_t)(k / NB) * NB * NB * es; t.C = P(f, r0, k);
+        t.lda = t.ldc = f.ldp; t.ldb = NB;
+        t.M = r1 - r0; t.N = std::min(NB, f.s - k); t.K = t.N;
+        t.lower = 0; t.beta = 0;
+        t.map_a = t.map_b = f.node;
+        t.a_r0 = r0; t.a_c0 = k; t.b_r0 = (k / NB) * NB; t.b_c0 = 0;
+        tasks.push_back(t);
+    };
+    // (a0) the panel at K0, all its rows, from the columns [kb, ke)
+    auto add_outer = [&](const FrontDesc& f, int K0, int kb, int ke) {
+        if (f.s <= K0 || ke <= kb) return;
+        GemmTask t{};
+        t.A = P(f, K0, kb); t.B = t.A; t.C = P(f, K0, K0);
+        t.lda = t.ldb = t.ldc = f.ldp;
+        t.M = f.N - K0; t.N = std::min(WOUT, f.s - K0); t.K = ke - kb;
+        t.lower = 0; t.beta = 1;
+        t.map_a = t.map_b = f.node;
+        t.a_r0 = K0; t.a_c0 = kb; t.b_r0 = K0; t.b_c0 = kb;
+        tasks.push_back(t);
+    };
+    const int np = (L.max_s + WOUT - 1) / WOUT;
+    RSD_CUDA_TRY(cudaEventRecord(h.ev_ready, B));          // the fronts are assembled
+    for (int p = 0; p < np; ++p) {
+        const int K0 = p * WOUT;
+        // (1) bulk: the K range [K0-W, K0) of this panel's outer update; release the panel
+        if (p >= 1) {
+            tasks.clear();
+            for (auto& f : L.fronts) add_outer(f, K0, K0 - WOUT, K0);
+            RSD_TRY(gemm_tc_launch(h, li, tasks, 3, B, 0, bulk_ctas));
+            RSD_CUDA_TRY(cudaEventRecord(h.ev_ready, B));
+        }
+        // (2) chain: the diagonal W x W block of every front
+        RSD_CUDA_TRY(cudaStreamWaitEvent(Cs, h.ev_ready, 0));
+        for (int j = 0; j < WOUT / NB; ++j) {
+            const int k = K0 + j * NB;
+            if (k >= L.max_s) break;
+            tasks.clear();
+            for (auto& f : L.fronts) add_update(f, k, K0, k, wend(f, K0));
+            RSD_TRY(gemm_tc_launch(h, li, tasks, 0, Cs, 1));
+            double pf = 0, pb = 0;
+            for (auto& f : L.fronts)
+                if (f.s > k) { const double w = std::min(NB, f.s - k); pf += 2.0 * w * w * w / 3.0; pb += (2.0 * w * w + NB * NB) * es; }
+            const int ppi = prof_begin(h, K_POTRF, Cs);
+            k_potrf_diag<float><<<(unsigned)nf, 256, potrf_smem, Cs>>>(L.d_fronts, k, h.d_err, 1);
+            count_launch();
+            prof_end(h, ppi, pf, pb, Cs);
+            RSD_CUDA_TRY(cudaGetLastError());
+            RSD_CUDA_TRY(cudaEventRecord(h.ev_diag[j], Cs));
+            tasks.clear();
+            for (auto& f : L.fronts) add_solve(f, k, k + std::min(NB, std::max(0, f.s - k)), wend(f, K0));
+            RSD_TRY(gemm_tc_launch(h, li, tasks, 1, Cs, 1));
+        }
+        // (3) bulk, one panel ahead: the K range [0, K0) of the next panel's outer update
+        if (p + 1 < np && K0 > 0) {
+            tasks.clear();
+            for (auto& f : L.fronts) add_outer(f, K0 + WOUT, 0, K0);
+            RSD_TRY(gemm_tc_launch(h, li, tasks, 3, B, 0, bulk_ctas));
+        }
+        // (4) bulk: this panel's update and solve for the rows below the diagonal block
+        for (int j = 0; j < WOUT / NB; ++j) {
+            const int k = K0 + j * NB;
+            if (k >= L.max_s) break;
+            RSD_CUDA_TRY(cudaStreamWaitEvent(B, h.ev_diag[j], 0));
+            tasks.clear();
+            for (auto& f : L.fronts) add_update(f, k, K0, wend(f, K0), f.N);
+            RSD_TRY(gemm_tc_launch(h, li, tasks, 0, B, 0));
+            tasks.clear();
+            for (auto& f : L.fronts) add_solve(f, k, wend(f, K0), f.N);
+            RSD_TRY(gemm_tc_launch(h, li, tasks, 1, B, 0));
+        }
+    }
+    RSD_CUDA_TRY(cudaEventRecord(h.ev_join, Cs));           // the chain's last solves
+    RSD_CUDA_TRY(cudaStreamWaitEvent(B, h.ev_join, 0));
+    return RSD_OK;
+}
+
 // Partial Cholesky of every front of level li (steps (a)-(d) above).
 int run_factor_level(Handle& h, int li) {
     Level& L = h.levels[li];
@@ -502,7 +630,9 @@ int run_factor_level(Handle& h, int li) {
         return f64 ? launch_gemm_simt<double>(h, tasks, d_tasks, -1.0, h.stream)
                    : launch_gemm_simt<float>(h, tasks, d_tasks, -1.0f, h.stream);
     };
-    for (int k = 0; k < L.max_s && rc == RSD_OK; k += NB) {
+    const bool lookahead = tc && (int)L.fronts.size() <= LOOKAHEAD_FRONTS && L.max_s > WOUT;
+    if (lookahead) rc = factor_level_lookahead(h, li);
+    for (int k = 0; !lookahead && k < L.max_s && rc == RSD_OK; k += NB) {
         const int K0 = (k / WOUT) * WOUT;               // start of the enclosing outer panel
         // (a0) at an outer panel start: update the whole WOUT-wide panel from all columns
         //      left of it (one large-K GEMM per outer panel)

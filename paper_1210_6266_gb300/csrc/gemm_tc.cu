@@ -59,6 +59,12 @@ __device__ __forceinline__ float tf32_rn(float x) {
     return __uint_as_float(r);
 }
 
+// Pull the C rows an epilogue thread will read into L2 while the main loop runs, so the
+// read-modify-write of the tile waits on L2 rather than on DRAM.
+__device__ __forceinline__ void prefetch_c_row(const float* crow, int c_lo, int c_hi) {
+    for (int c = c_lo; c < c_hi; c += 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(crow + c));
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -230,10 +236,12 @@ k_gemm_tc(const TcTask* __restrict__ tasks, const TcTile* __restrict__ tiles,
         // epilogue: warp (2..5) reads TMEM lanes 32*(warp%4) .. +31
         const int quarter = warp & 3;
         const int row = quarter * 32 + lane;
-        const bool ok = mbar_wait(bar_done, 0, err);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int gr = m0 + row;
         float* crow = tk.C + (int64_t)gr * tk.ldc;
+        if (tk.beta && tl.ws_slot < 0 && gr < tk.M)
+            prefetch_c_row(crow, n0, min(n0 + BN, tk.lower ? min(tk.N, gr + 1) : tk.N));
+        const bool ok = mbar_wait(bar_done, 0, err);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         float* wrow = tl.ws_slot >= 0 ? ws + ((int64_t)tl.ws_slot * BM + row) * BN : nullptr;
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 32) {
@@ -386,11 +394,13 @@ k_gemm_tc_persist(const TcTask* __restrict__ tasks, const TcTile* __restrict__ t
             const TcTile tl = tiles[t];
             const TcTask tk = tasks[tl.task];
             const uint32_t buf = tcount & 1, use = (tcount >> 1) & 1;
-            const bool ok = mbar_wait(bar_accf + 8 * buf, use, err);
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int m0 = tl.tm * BM, n0 = tl.tn * BN;
             const int gr = m0 + row;
             float* crow = tk.C + (int64_t)gr * tk.ldc;
+            if (tk.beta && tl.ws_slot < 0 && gr < tk.M)
+                prefetch_c_row(crow, n0, min(n0 + BN, tk.lower ? min(tk.N, gr + 1) : tk.N));
+            const bool ok = mbar_wait(bar_accf + 8 * buf, use, err);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             float* wrow = tl.ws_slot >= 0 ? ws + ((int64_t)tl.ws_slot * BM + row) * BN : nullptr;
 #pragma unroll 1
             for (int c0 = 0; c0 < BN; c0 += 32) {
@@ -494,14 +504,20 @@ int encode_2d(CUtensorMap* m, void* base, int cols, int rows, int ld_elems) {
     return RSD_OK;
 }
 
-struct TcState {
-    CUtensorMap* d_maps = nullptr;      // 2 per tree node: [L; X] panel, inverted diagonal blocks
+// Per-stream launch buffers: task/tile lists and the split-K workspace are rewritten by
+// every launch, so two streams that launch concurrently each need their own set.
+struct TcBuf {
     TcTask* d_tasks = nullptr;
     TcTile* d_tiles = nullptr;
     TcRed* d_reds = nullptr;
     float* d_ws = nullptr;              // split-K partial products
     size_t cap_tasks = 0, cap_tiles = 0, cap_reds = 0;
-    int ws_slots = 0;                   // capacity in BM x 256 tiles
+};
+
+struct TcState {
+    CUtensorMap* d_maps = nullptr;      // 2 per tree node: [L; X] panel, inverted diagonal blocks
+    TcBuf buf[TC_SLOTS];
+    int ws_slots = 0;                   // split-K capacity per slot, in BM x 256 tiles
     bool attr_set = false;
 };
 
@@ -528,7 +544,8 @@ int gemm_tc_prepare(Handle& h) {
     }
     RSD_CUDA_TRY(cudaMalloc((void**)&st->d_maps, maps.size() * sizeof(CUtensorMap)));
     st->ws_slots = 2 * h.num_sms;
-    RSD_CUDA_TRY(cudaMalloc((void**)&st->d_ws, (size_t)st->ws_slots * BM * 256 * sizeof(float)));
+    for (auto& b : st->buf)
+        RSD_CUDA_TRY(cudaMalloc((void**)&b.d_ws, (size_t)st->ws_slots * BM * 256 * sizeof(float)));
     RSD_CUDA_TRY(cudaMemcpy(st->d_maps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
     return RSD_OK;
 }
@@ -537,19 +554,25 @@ void gemm_tc_release(Handle& h) {
     TcState* st = state_of(h);
     if (!st) return;
     cudaFree(st->d_maps);
-    cudaFree(st->d_tasks);
-    cudaFree(st->d_tiles);
-    cudaFree(st->d_reds);
-    cudaFree(st->d_ws);
+    for (auto& b : st->buf) {
+        cudaFree(b.d_tasks);
+        cudaFree(b.d_tiles);
+        cudaFree(b.d_reds);
+        cudaFree(b.d_ws);
+    }
     delete st;
     h.tc_state = nullptr;
 }
 
 // kind 0: inner panel update, 1: panel solve (B = inverted diagonal block),
 // 2: U -= X X^T (lower tiles), 3: outer panel update.
-int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, int kind, cudaStream_t stream) {
+int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, int kind, cudaStream_t stream,
+                   int buf_slot, int max_ctas) {
     TcState* st = state_of(h);
     if (!st || tasks.empty()) return st ? RSD_OK : RSD_ERR_ARG;
+    if (buf_slot < 0 || buf_slot >= TC_SLOTS) return RSD_ERR_ARG;
+    TcBuf& bf = st->buf[buf_slot];
+    const int sms = max_ctas > 0 ? std::min(max_ctas, h.num_sms) : h.num_sms;
     const int bn = (kind == 2 || kind == 3) ? 256 : 128;
     std::vector<TcTask> tt(tasks.size());
     std::vector<std::array<int, 3>> out;            // (task, tm, tn) output tiles
@@ -576,8 +599,8 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
     int max_kb = 0;
     for (auto& g : tasks) max_kb = std::max(max_kb, (g.K + BK - 1) / BK);
     int nsplit = 1;
-    if (kind != 1 && (int)out.size() < h.num_sms)
-        nsplit = std::max(1, std::min(h.num_sms / (int)out.size(), max_kb / SPLIT_MIN_KB));
+    if (kind != 1 && (int)out.size() < sms)
+        nsplit = std::max(1, std::min(sms / (int)out.size(), max_kb / SPLIT_MIN_KB));
     if ((int)out.size() * nsplit * (bn / 256 > 0 ? bn / 256 : 1) > st->ws_slots * (256 / bn)) nsplit = 1;
     std::vector<TcTile> tl;
     std::vector<TcRed> rd;
@@ -600,15 +623,15 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
         RSD_CUDA_TRY(cudaMallocAsync((void**)&ptr, cap * elem, stream));
         return RSD_OK;
     };
-    RSD_TRY(grow(st->d_tasks, st->cap_tasks, tt.size(), sizeof(TcTask)));
-    RSD_TRY(grow(st->d_tiles, st->cap_tiles, tl.size(), sizeof(TcTile)));
-    if (!rd.empty()) RSD_TRY(grow(st->d_reds, st->cap_reds, rd.size(), sizeof(TcRed)));
-    RSD_CUDA_TRY(cudaMemcpyAsync(st->d_tasks, stage_host(h, tt.data(), tt.size() * sizeof(TcTask)),
+    RSD_TRY(grow(bf.d_tasks, bf.cap_tasks, tt.size(), sizeof(TcTask)));
+    RSD_TRY(grow(bf.d_tiles, bf.cap_tiles, tl.size(), sizeof(TcTile)));
+    if (!rd.empty()) RSD_TRY(grow(bf.d_reds, bf.cap_reds, rd.size(), sizeof(TcRed)));
+    RSD_CUDA_TRY(cudaMemcpyAsync(bf.d_tasks, stage_host(h, tt.data(), tt.size() * sizeof(TcTask)),
                                  tt.size() * sizeof(TcTask), cudaMemcpyHostToDevice, stream));
-    RSD_CUDA_TRY(cudaMemcpyAsync(st->d_tiles, stage_host(h, tl.data(), tl.size() * sizeof(TcTile)),
+    RSD_CUDA_TRY(cudaMemcpyAsync(bf.d_tiles, stage_host(h, tl.data(), tl.size() * sizeof(TcTile)),
                                  tl.size() * sizeof(TcTile), cudaMemcpyHostToDevice, stream));
     if (!rd.empty())
-        RSD_CUDA_TRY(cudaMemcpyAsync(st->d_reds, stage_host(h, rd.data(), rd.size() * sizeof(TcRed)),
+        RSD_CUDA_TRY(cudaMemcpyAsync(bf.d_reds, stage_host(h, rd.data(), rd.size() * sizeof(TcRed)),
                                      rd.size() * sizeof(TcRed), cudaMemcpyHostToDevice, stream));
     if (!st->attr_set) {
         RSD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<128, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<128, 3>::TOTAL));
@@ -623,25 +646,25 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
         fl += 2.0 * c * g.K;
         by += 4.0 * ((double)g.M * g.K + (g.lower ? 0.0 : (double)g.N * g.K) + c * (g.beta ? 2 : 1));
     }
-    const int pi = prof_begin(h, K_GEMM_TC);
+    const int pi = prof_begin(h, K_GEMM_TC, stream);
     // short K (inner panel update, panel solve): 3-stage ring, two CTAs per SM so one
     // tile's epilogue overlaps the other's main loop; long K: deeper rings, one CTA per SM
     if (bn == 128 && max_kb <= 16)
-        k_gemm_tc<128, 3><<<(unsigned)tl.size(), TC_THREADS, Smem<128, 3>::TOTAL, stream>>>(st->d_tasks, st->d_tiles, st->d_maps, st->d_ws, h.d_err);
+        k_gemm_tc<128, 3><<<(unsigned)tl.size(), TC_THREADS, Smem<128, 3>::TOTAL, stream>>>(bf.d_tasks, bf.d_tiles, st->d_maps, bf.d_ws, h.d_err);
     else if (bn == 128)
-        k_gemm_tc<128, 6><<<(unsigned)tl.size(), TC_THREADS, Smem<128, 6>::TOTAL, stream>>>(st->d_tasks, st->d_tiles, st->d_maps, st->d_ws, h.d_err);
+        k_gemm_tc<128, 6><<<(unsigned)tl.size(), TC_THREADS, Smem<128, 6>::TOTAL, stream>>>(bf.d_tasks, bf.d_tiles, st->d_maps, bf.d_ws, h.d_err);
     else {
-        const int ctas = std::min((int)tl.size(), h.num_sms);
+        const int ctas = std::min((int)tl.size(), sms);
         k_gemm_tc_persist<256, 4><<<(unsigned)ctas, TC_THREADS, Smem<256, 4>::TOTAL, stream>>>(
-            st->d_tasks, st->d_tiles, (int)tl.size(), st->d_maps, st->d_ws, h.d_err);
+            bf.d_tasks, bf.d_tiles, (int)tl.size(), st->d_maps, bf.d_ws, h.d_err);
     }
     count_launch();
     if (!rd.empty()) {
-        if (bn == 128) k_splitk_reduce<128><<<(unsigned)rd.size(), 256, 0, stream>>>(st->d_tasks, st->d_reds, st->d_ws);
-        else k_splitk_reduce<256><<<(unsigned)rd.size(), 256, 0, stream>>>(st->d_tasks, st->d_reds, st->d_ws);
+        if (bn == 128) k_splitk_reduce<128><<<(unsigned)rd.size(), 256, 0, stream>>>(bf.d_tasks, bf.d_reds, bf.d_ws);
+        else k_splitk_reduce<256><<<(unsigned)rd.size(), 256, 0, stream>>>(bf.d_tasks, bf.d_reds, bf.d_ws);
         count_launch();
     }
-    prof_end(h, pi, fl, by);
+    prof_end(h, pi, fl, by, stream);
     RSD_CUDA_TRY(cudaGetLastError());
     return RSD_OK;
 }

@@ -81,7 +81,7 @@ enum KClass { K_ASSEMBLE = 0, K_EXTEND, K_GEMM_TC, K_GEMM_SIMT, K_POTRF, K_TRSM,
 // flops and bytes of that launch; reduced on demand by rsd_profile().
 struct Prof {
     bool on = false;
-    struct Rec { int cls; double flops, bytes; cudaEvent_t a, b; };
+    struct Rec { int cls; double flops, bytes; cudaEvent_t a, b; int stream; };
     std::vector<Rec> recs;
     std::vector<cudaEvent_t> pool;
     double host_ms = 0;                  // host-side analysis time of the last setup
@@ -167,6 +167,11 @@ struct Handle {
     // pinned host staging for per-launch uploads (append-only; see stage_host)
     char* stage = nullptr;
     size_t stage_cap = 0, stage_off = 0;
+    // look-ahead factorisation of levels with few fronts: a high-priority stream runs the
+    // diagonal-block chain beside the bulk updates on `stream` (created on first use)
+    cudaStream_t chain = nullptr;
+    cudaEvent_t ev_ready = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_diag[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 // Copy `bytes` from host memory into the handle's pinned staging area and return the
@@ -176,8 +181,18 @@ const void* stage_host(Handle& h, const void* src, size_t bytes);
 
 // Profile helpers: prof_begin records the start event (if profiling) and returns a
 // record index; prof_end records the stop event and the launch's algorithmic work.
-int prof_begin(Handle& h, int cls);
-void prof_end(Handle& h, int idx, double flops, double bytes);
+int prof_begin(Handle& h, int cls, cudaStream_t stream);
+void prof_end(Handle& h, int idx, double flops, double bytes, cudaStream_t stream);
+inline int prof_begin(Handle& h, int cls) { return prof_begin(h, cls, h.stream); }
+inline void prof_end(Handle& h, int idx, double flops, double bytes) { prof_end(h, idx, flops, bytes, h.stream); }
+
+// Tensor-core GEMM launch (gemm_tc.cu).  kind 0: inner panel update, 1: panel solve with
+// an inverted diagonal block, 2: U -= X X^T (lower tiles), 3: outer panel update.
+// `slot` selects the launch buffers (one per stream that launches concurrently);
+// max_ctas > 0 caps the CTAs of the persistent kernel (leaving SMs to another stream).
+constexpr int TC_SLOTS = 2;
+int gemm_tc_launch(Handle& h, int li, const std::vector<GemmTask>& tasks, int kind, cudaStream_t stream,
+                   int slot = 0, int max_ctas = 0);
 
 // ---- kernels launched from the host orchestration -------------------------------
 int launch_assemble_fronts(Handle& h, int li, const int64_t* rowptr, const int* col,
