@@ -472,20 +472,68 @@ int launch_extend_add(Handle& h, int li) {
 }
 
 // ---------------------------------------------------------------------------------
-// Look-ahead order for tensor-core levels with few fronts (the root and the level below
-// it), where the diagonal factor+inverse of one front runs on a single SM and would
-// otherwise idle the GPU: per outer panel p (columns K0 .. K0+W),
-//   chain stream (high priority): the steps (a)-(c) restricted to the W x W diagonal
-//     block of the panel -- small GEMMs and the 128-block factor+inverse;
-//   bulk stream (the caller's): the same steps for the rows below the block, each
-//     released by an event after the diagonal block it needs; and, one panel ahead, the
-//     part of the next panel's outer update (a0) whose K range [0, K0) covers finished
-//     panels only -- it overlaps the chain.  The remaining K range [K0, K0+W) of that
-//     update runs when panel p is done.
-// Every entry receives the same products as in the single-stream order; only the outer
-// update's K range is summed in two parts.  The bulk persistent GEMM leaves a few SMs
-// to the chain.
+// Tensor-core levels: block-inverse panel solve and look-ahead.
+//
+// For each outer panel (columns K0 .. K0+W, W <= WOUT):
+//   (a0) the outer update of the whole panel, as above;
+//   (a)-(c) restricted to the W x W diagonal block of the panel (its 128-blocks factored
+//        one after another: small GEMMs and the diagonal factor+inverse);
+//   (e)  Mt = L_pp^-T for the W x W block L_pp, from its inverted diagonal blocks:
+//        Mt_jj = Dinv_j^T and, block column i after block column i, for the rows j < i
+//        Mt[j, i] = -(sum_{k<i} Mt[j, k] L_ik^T) Dinv_i^T    (from Mt L_pp^T = I);
+//        then Linv = Mt^T;
+//   (f)  the rows below the block in one step, X = A L_pp^-T = A Linv^T, in place: the
+//        column tile [256, W) first (it reads A[:, 0:W]), then [0, 256) (it reads only
+//        A[:, 0:256], which the first launch left untouched).
+// (e)-(f) replace the per-128-column updates and solves of the rows below the block
+// (many thin, memory-bound GEMMs) by two K = W GEMMs.
+//
+// Levels with few fronts (the root and the level below it) also look ahead: the
+// diagonal-block work (a)-(c) and (e) runs on a high-priority stream (the "chain"),
+// beside the bulk stream (the caller's), which meanwhile applies the part of the NEXT
+// panel's outer update whose K range [0, K0) covers finished panels only; the remaining
+// range [K0, K0+W) runs once panel p is complete.  The bulk persistent GEMM leaves a few
+// SMs to the chain.  Every entry receives the same products in either order; only the
+// outer update's K range is summed in two parts.
 constexpr int LOOKAHEAD_FRONTS = 16;
+constexpr int64_t SCR_MT = 512 * 512, SCR_TT = 512 * 128, SCR_LINV = 512 * 512;
+constexpr int64_t SCR_FRONT = SCR_MT + SCR_TT + SCR_LINV;        // floats per front slot
+static_assert(WOUT == 512, "scratch blocks are sized for 512-wide outer panels");
+
+// Mt's diagonal blocks: Mt[j, j] = Dinv_j^T (upper triangular), j < ceil(W / NB).
+__global__ void k_mt_diag(const FrontDesc* __restrict__ fronts, int K0, float* __restrict__ scr) {
+    const FrontDesc f = fronts[blockIdx.z];
+    if (f.s <= K0) return;
+    const int W = min(WOUT, f.s - K0);
+    const int j = blockIdx.y;
+    if (j * NB >= W) return;
+    float* Mt = scr + (int64_t)blockIdx.z * SCR_FRONT;
+    const float* D = (const float*)f.Dinv + (int64_t)(K0 / NB + j) * NB * NB;
+    __shared__ float t[32][33];
+    const int bx = blockIdx.x & 3, by = blockIdx.x >> 2;     // 4 x 4 tiles of 32 x 32
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) t[r][threadIdx.x] = D[(by * 32 + r) * NB + bx * 32 + threadIdx.x];
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y)
+        Mt[(int64_t)(j * NB + bx * 32 + r) * 512 + j * NB + by * 32 + threadIdx.x] = t[threadIdx.x][r];
+}
+
+// Linv = Mt^T on the W x W block, zero elsewhere in the 512 x 512 slot.
+__global__ void k_linv_transpose(const FrontDesc* __restrict__ fronts, int K0, float* __restrict__ scr) {
+    const FrontDesc f = fronts[blockIdx.z];
+    if (f.s <= K0) return;
+    const int W = min(WOUT, f.s - K0);
+    const float* Mt = scr + (int64_t)blockIdx.z * SCR_FRONT;
+    float* Li = scr + (int64_t)blockIdx.z * SCR_FRONT + SCR_MT + SCR_TT;
+    __shared__ float t[32][33];
+    const int bx = blockIdx.x, by = blockIdx.y;               // 16 x 16 tiles of 32 x 32
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int row = by * 32 + r, col = bx * 32 + threadIdx.x;
+        t[r][threadIdx.x] = (row < W && col < W) ? Mt[(int64_t)row * 512 + col] : 0.f;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y)
+        Li[(int64_t)(bx * 32 + r) * 512 + by * 32 + threadIdx.x] = t[threadIdx.x][r];
+}
 
 static int ensure_chain(Handle& h) {
     if (h.chain) return RSD_OK;
@@ -497,16 +545,32 @@ static int ensure_chain(Handle& h) {
     return RSD_OK;
 }
 
-static int factor_level_lookahead(Handle& h, int li) {
-    static_assert(WOUT / NB == 4, "one diagonal event per inner block of an outer panel");
+static int factor_level_tc(Handle& h, int li, bool lookahead) {
     Level& L = h.levels[li];
     const size_t es = 4;
     const size_t potrf_smem = (size_t)NB * DLD * es + (size_t)2 * NB * es;
     RSD_CUDA_TRY(cudaFuncSetAttribute(k_potrf_diag<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)potrf_smem));
-    RSD_TRY(ensure_chain(h));
     const int nf = (int)L.fronts.size();
-    const int bulk_ctas = h.num_sms - std::min(h.num_sms / 4, nf + 1);
-    cudaStream_t B = h.stream, Cs = h.chain;
+    if (lookahead) RSD_TRY(ensure_chain(h));
+    cudaStream_t B = h.stream, Cs = lookahead ? h.chain : h.stream;
+    const int cslot = lookahead ? 1 : 0;
+    const int bulk_ctas = lookahead ? h.num_sms - std::min(h.num_sms / 4, nf + 1) : 0;
+    // per-front scratch: Mt, Tt, Linv (Mt's lower part stays zero)
+    float* scr = nullptr;
+    RSD_CUDA_TRY(cudaMallocAsync((void**)&scr, sizeof(float) * SCR_FRONT * nf, B));
+    RSD_CUDA_TRY(cudaMemsetAsync(scr, 0, sizeof(float) * SCR_FRONT * nf, B));
+    std::vector<float*> mt(nf), tt(nf), lv(nf);
+    for (int i = 0; i < nf; ++i) {
+        mt[i] = scr + SCR_FRONT * i;
+        tt[i] = mt[i] + SCR_MT;
+        lv[i] = tt[i] + SCR_TT;
+    }
+    int mbase = 0;
+    RSD_TRY(gemm_tc_scratch_maps(h, mt, tt, lv, B, &mbase));
+    auto map_mt = [&](int i) { return mbase + 3 * i; };
+    auto map_tt = [&](int i) { return mbase + 3 * i + 1; };
+    auto map_lv = [&](int i) { return mbase + 3 * i + 2; };
+
     std::vector<GemmTask> tasks;
     auto wend = [](const FrontDesc& f, int K0) { return std::min(K0 + WOUT, f.s); };
     auto P = [&](const FrontDesc& f, int r, int c) { return (char*)f.P + ((int64_t)r * f.ldp + c) * es; };
@@ -546,25 +610,38 @@ static int factor_level_lookahead(Handle& h, int li) {
         t.a_r0 = K0; t.a_c0 = kb; t.b_r0 = K0; t.b_c0 = kb;
         tasks.push_back(t);
     };
+    auto general = [&](int ma, int a_r0, int a_c0, int mb, int b_r0, int b_c0, void* C, int ldc,
+                       int M, int N, int K, float alpha) {
+        GemmTask t{};
+        t.C = C; t.ldc = ldc; t.M = M; t.N = N; t.K = K;
+        t.lower = 0; t.beta = 0; t.alpha = alpha; t.round = 1;
+        t.map_a = ma; t.map_b = mb;
+        t.a_r0 = a_r0; t.a_c0 = a_c0; t.b_r0 = b_r0; t.b_c0 = b_c0;
+        tasks.push_back(t);
+    };
+
     const int np = (L.max_s + WOUT - 1) / WOUT;
-    RSD_CUDA_TRY(cudaEventRecord(h.ev_ready, B));          // the fronts are assembled
+    if (lookahead) RSD_CUDA_TRY(cudaEventRecord(h.ev_ready, B));     // the fronts are assembled
     for (int p = 0; p < np; ++p) {
         const int K0 = p * WOUT;
-        // (1) bulk: the K range [K0-W, K0) of this panel's outer update; release the panel
+        // (a0) bulk: this panel's outer update (with look-ahead only its K range
+        //      [K0-W, K0); the rest ran one panel earlier), then release the panel
         if (p >= 1) {
             tasks.clear();
-            for (auto& f : L.fronts) add_outer(f, K0, K0 - WOUT, K0);
+            for (auto& f : L.fronts) add_outer(f, K0, lookahead ? K0 - WOUT : 0, K0);
             RSD_TRY(gemm_tc_launch(h, li, tasks, 3, B, 0, bulk_ctas));
-            RSD_CUDA_TRY(cudaEventRecord(h.ev_ready, B));
         }
-        // (2) chain: the diagonal W x W block of every front
-        RSD_CUDA_TRY(cudaStreamWaitEvent(Cs, h.ev_ready, 0));
+        if (lookahead) {
+            RSD_CUDA_TRY(cudaEventRecord(h.ev_ready, B));
+            RSD_CUDA_TRY(cudaStreamWaitEvent(Cs, h.ev_ready, 0));
+        }
+        // (a)-(c) chain: the diagonal W x W block of every front
         for (int j = 0; j < WOUT / NB; ++j) {
             const int k = K0 + j * NB;
             if (k >= L.max_s) break;
             tasks.clear();
             for (auto& f : L.fronts) add_update(f, k, K0, k, wend(f, K0));
-            RSD_TRY(gemm_tc_launch(h, li, tasks, 0, Cs, 1));
+            RSD_TRY(gemm_tc_launch(h, li, tasks, 0, Cs, cslot));
             double pf = 0, pb = 0;
             for (auto& f : L.fronts)
                 if (f.s > k) { const double w = std::min(NB, f.s - k); pf += 2.0 * w * w * w / 3.0; pb += (2.0 * w * w + NB * NB) * es; }
@@ -573,32 +650,68 @@ static int factor_level_lookahead(Handle& h, int li) {
             count_launch();
             prof_end(h, ppi, pf, pb, Cs);
             RSD_CUDA_TRY(cudaGetLastError());
-            RSD_CUDA_TRY(cudaEventRecord(h.ev_diag[j], Cs));
             tasks.clear();
             for (auto& f : L.fronts) add_solve(f, k, k + std::min(NB, std::max(0, f.s - k)), wend(f, K0));
-            RSD_TRY(gemm_tc_launch(h, li, tasks, 1, Cs, 1));
+            RSD_TRY(gemm_tc_launch(h, li, tasks, 1, Cs, cslot));
         }
-        // (3) bulk, one panel ahead: the K range [0, K0) of the next panel's outer update
-        if (p + 1 < np && K0 > 0) {
-            tasks.clear();
-            for (auto& f : L.fronts) add_outer(f, K0 + WOUT, 0, K0);
-            RSD_TRY(gemm_tc_launch(h, li, tasks, 3, B, 0, bulk_ctas));
-        }
-        // (4) bulk: this panel's update and solve for the rows below the diagonal block
-        for (int j = 0; j < WOUT / NB; ++j) {
-            const int k = K0 + j * NB;
+        // (e) chain: Mt = L_pp^-T, then Linv = Mt^T
+        k_mt_diag<<<dim3(16, WOUT / NB, (unsigned)nf), dim3(32, 8), 0, Cs>>>(L.d_fronts, K0, scr);
+        count_launch();
+        RSD_CUDA_TRY(cudaGetLastError());
+        for (int i = 1; i < WOUT / NB; ++i) {
+            const int k = K0 + i * NB;
             if (k >= L.max_s) break;
-            RSD_CUDA_TRY(cudaStreamWaitEvent(B, h.ev_diag[j], 0));
+            tasks.clear();                              // Tt = Mt[0:i NB, 0:i NB] L_{i,<i}^T
+            for (int q = 0; q < nf; ++q) {
+                const FrontDesc& f = L.fronts[q];
+                if (f.s <= k) continue;
+                general(map_mt(q), 0, 0, tc_map_panel(f.node), k, K0, tt[q], 128,
+                        i * NB, std::min(NB, f.s - k), i * NB, 1.0f);
+            }
+            RSD_TRY(gemm_tc_launch(h, li, tasks, TC_GENERAL, Cs, cslot));
+            tasks.clear();                              // Mt[0:i NB, i] = -Tt Dinv_i^T
+            for (int q = 0; q < nf; ++q) {
+                const FrontDesc& f = L.fronts[q];
+                if (f.s <= k) continue;
+                const int w = std::min(NB, f.s - k);
+                general(map_tt(q), 0, 0, tc_map_dinv(f.node), k, 0, mt[q] + i * NB, 512,
+                        i * NB, w, w, -1.0f);
+            }
+            RSD_TRY(gemm_tc_launch(h, li, tasks, TC_GENERAL, Cs, cslot));
+        }
+        k_linv_transpose<<<dim3(16, 16, (unsigned)nf), dim3(32, 8), 0, Cs>>>(L.d_fronts, K0, scr);
+        count_launch();
+        RSD_CUDA_TRY(cudaGetLastError());
+        if (lookahead) {
+            RSD_CUDA_TRY(cudaEventRecord(h.ev_diag[0], Cs));
+            // bulk, one panel ahead: the K range [0, K0) of the next panel's outer update
+            if (p + 1 < np && K0 > 0) {
+                tasks.clear();
+                for (auto& f : L.fronts) add_outer(f, K0 + WOUT, 0, K0);
+                RSD_TRY(gemm_tc_launch(h, li, tasks, 3, B, 0, bulk_ctas));
+            }
+            RSD_CUDA_TRY(cudaStreamWaitEvent(B, h.ev_diag[0], 0));
+        }
+        // (f) bulk: X = A Linv^T for the rows below the diagonal block, in place
+        for (int half = 1; half >= 0; --half) {
             tasks.clear();
-            for (auto& f : L.fronts) add_update(f, k, K0, wend(f, K0), f.N);
-            RSD_TRY(gemm_tc_launch(h, li, tasks, 0, B, 0));
-            tasks.clear();
-            for (auto& f : L.fronts) add_solve(f, k, wend(f, K0), f.N);
-            RSD_TRY(gemm_tc_launch(h, li, tasks, 1, B, 0));
+            for (int q = 0; q < nf; ++q) {
+                const FrontDesc& f = L.fronts[q];
+                if (f.s <= K0) continue;
+                const int W = std::min(WOUT, f.s - K0), r0 = K0 + W;
+                const int c0 = half * 256, c1 = std::min(W, c0 + 256);
+                if (c1 <= c0 || f.N <= r0) continue;
+                general(tc_map_panel(f.node), r0, K0, map_lv(q), c0, 0, P(f, r0, K0 + c0), f.ldp,
+                        f.N - r0, c1 - c0, c1, 1.0f);
+            }
+            RSD_TRY(gemm_tc_launch(h, li, tasks, TC_GENERAL, B, 0, bulk_ctas));
         }
     }
-    RSD_CUDA_TRY(cudaEventRecord(h.ev_join, Cs));           // the chain's last solves
-    RSD_CUDA_TRY(cudaStreamWaitEvent(B, h.ev_join, 0));
+    if (lookahead) {
+        RSD_CUDA_TRY(cudaEventRecord(h.ev_join, Cs));
+        RSD_CUDA_TRY(cudaStreamWaitEvent(B, h.ev_join, 0));
+    }
+    cudaFreeAsync(scr, B);
     return RSD_OK;
 }
 
@@ -630,9 +743,8 @@ int run_factor_level(Handle& h, int li) {
         return f64 ? launch_gemm_simt<double>(h, tasks, d_tasks, -1.0, h.stream)
                    : launch_gemm_simt<float>(h, tasks, d_tasks, -1.0f, h.stream);
     };
-    const bool lookahead = tc && (int)L.fronts.size() <= LOOKAHEAD_FRONTS && L.max_s > WOUT;
-    if (lookahead) rc = factor_level_lookahead(h, li);
-    for (int k = 0; !lookahead && k < L.max_s && rc == RSD_OK; k += NB) {
+    if (tc) rc = factor_level_tc(h, li, (int)L.fronts.size() <= LOOKAHEAD_FRONTS && L.max_s > WOUT);
+    for (int k = 0; !tc && k < L.max_s && rc == RSD_OK; k += NB) {
         const int K0 = (k / WOUT) * WOUT;               // start of the enclosing outer panel
         // (a0) at an outer panel start: update the whole WOUT-wide panel from all columns
         //      left of it (one large-K GEMM per outer panel)

@@ -515,7 +515,9 @@ struct TcBuf {
 };
 
 struct TcState {
-    CUtensorMap* d_maps = nullptr;      // 2 per tree node: [L; X] panel, inverted diagonal blocks
+    CUtensorMap* d_maps = nullptr;      // 2 per tree node: [L; X] panel, inverted diagonal blocks;
+                                        // then 3 per front slot of the widest level (scratch)
+    int scr_base = 0, scr_slots = 0;
     TcBuf buf[TC_SLOTS];
     int ws_slots = 0;                   // split-K capacity per slot, in BM x 256 tiles
     bool attr_set = false;
@@ -533,7 +535,12 @@ int gemm_tc_prepare(Handle& h) {
     if (!any) return RSD_OK;
     auto* st = new TcState();
     h.tc_state = st;
-    std::vector<CUtensorMap> maps(2 * (size_t)h.n_nodes);
+    int widest = 0;
+    for (auto& L : h.levels)
+        if (L.prec == RSD_PREC_TF32) widest = std::max(widest, (int)L.fronts.size());
+    st->scr_base = 2 * h.n_nodes;
+    st->scr_slots = widest;
+    std::vector<CUtensorMap> maps(2 * (size_t)h.n_nodes + 3 * (size_t)widest);
     std::memset(maps.data(), 0, maps.size() * sizeof(CUtensorMap));
     for (auto& L : h.levels) {
         if (L.prec != RSD_PREC_TF32) continue;
@@ -547,6 +554,24 @@ int gemm_tc_prepare(Handle& h) {
     for (auto& b : st->buf)
         RSD_CUDA_TRY(cudaMalloc((void**)&b.d_ws, (size_t)st->ws_slots * BM * 256 * sizeof(float)));
     RSD_CUDA_TRY(cudaMemcpy(st->d_maps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
+    return RSD_OK;
+}
+
+int gemm_tc_scratch_maps(Handle& h, const std::vector<float*>& mt, const std::vector<float*>& tt,
+                         const std::vector<float*>& linv, cudaStream_t stream, int* base) {
+    TcState* st = state_of(h);
+    const size_t n = mt.size();
+    if (!st || tt.size() != n || linv.size() != n || (int)n > st->scr_slots) return RSD_ERR_ARG;
+    std::vector<CUtensorMap> maps(3 * n);
+    for (size_t i = 0; i < n; ++i) {
+        RSD_TRY(encode_2d(&maps[3 * i + 0], mt[i], 512, 512, 512));
+        RSD_TRY(encode_2d(&maps[3 * i + 1], tt[i], 128, 512, 128));
+        RSD_TRY(encode_2d(&maps[3 * i + 2], linv[i], 512, 512, 512));
+    }
+    if (n)
+        RSD_CUDA_TRY(cudaMemcpyAsync(st->d_maps + st->scr_base, stage_host(h, maps.data(), maps.size() * sizeof(CUtensorMap)),
+                                     maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, stream));
+    *base = st->scr_base;
     return RSD_OK;
 }
 
@@ -565,7 +590,8 @@ void gemm_tc_release(Handle& h) {
 }
 
 // kind 0: inner panel update, 1: panel solve (B = inverted diagonal block),
-// 2: U -= X X^T (lower tiles), 3: outer panel update.
+// 2: U -= X X^T (lower tiles), 3: outer panel update, TC_GENERAL: map indices, alpha and
+// rounding taken from the task (128- or 256-wide tiles by the widest N).
 int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, int kind, cudaStream_t stream,
                    int buf_slot, int max_ctas) {
     TcState* st = state_of(h);
@@ -573,7 +599,9 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
     if (buf_slot < 0 || buf_slot >= TC_SLOTS) return RSD_ERR_ARG;
     TcBuf& bf = st->buf[buf_slot];
     const int sms = max_ctas > 0 ? std::min(max_ctas, h.num_sms) : h.num_sms;
-    const int bn = (kind == 2 || kind == 3) ? 256 : 128;
+    int max_n = 0;
+    for (auto& g : tasks) max_n = std::max(max_n, g.N);
+    const int bn = (kind == 2 || kind == 3 || (kind == TC_GENERAL && max_n > 128)) ? 256 : 128;
     std::vector<TcTask> tt(tasks.size());
     std::vector<std::array<int, 3>> out;            // (task, tm, tn) output tiles
     for (size_t i = 0; i < tasks.size(); ++i) {
@@ -582,11 +610,12 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
         t.C = (float*)g.C;
         t.ldc = g.ldc; t.M = g.M; t.N = g.N; t.K = g.K;
         t.lower = g.lower; t.beta = g.beta;
-        t.map_a = 2 * g.map_a;
-        t.map_b = 2 * g.map_b + (kind == 1 ? 1 : 0);
+        t.map_a = kind == TC_GENERAL ? g.map_a : tc_map_panel(g.map_a);
+        t.map_b = kind == TC_GENERAL ? g.map_b : (kind == 1 ? tc_map_dinv(g.map_b) : tc_map_panel(g.map_b));
         t.a_r0 = g.a_r0; t.a_c0 = g.a_c0; t.b_r0 = g.b_r0; t.b_c0 = g.b_c0;
-        t.alpha = kind == 1 ? 1.0f : -1.0f;
-        t.round_tf32 = kind == 1;          // panel-solve results are final factor entries
+        t.alpha = kind == TC_GENERAL ? g.alpha : (kind == 1 ? 1.0f : -1.0f);
+        // panel-solve results are final factor entries
+        t.round_tf32 = kind == TC_GENERAL ? g.round : (kind == 1);
         const int tm = (g.M + BM - 1) / BM, tn = (g.N + bn - 1) / bn;
         for (int a = 0; a < tm; ++a)
             for (int b = 0; b < tn; ++b) {
@@ -599,7 +628,7 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
     int max_kb = 0;
     for (auto& g : tasks) max_kb = std::max(max_kb, (g.K + BK - 1) / BK);
     int nsplit = 1;
-    if (kind != 1 && (int)out.size() < sms)
+    if (kind != 1 && kind != TC_GENERAL && (int)out.size() < sms)
         nsplit = std::max(1, std::min(sms / (int)out.size(), max_kb / SPLIT_MIN_KB));
     if ((int)out.size() * nsplit * (bn / 256 > 0 ? bn / 256 : 1) > st->ws_slots * (256 / bn)) nsplit = 1;
     std::vector<TcTile> tl;

@@ -71,6 +71,8 @@ struct GemmTask {
     int beta;
     int map_a, map_b;    // tensor-map slots (tensor-core path); -1 when unused
     int a_r0, a_c0, b_r0, b_c0;   // operand origins inside the tensor maps
+    float alpha;         // general tensor-core kind only: C = alpha A B^T + beta C
+    int round;           // general kind only: round stored results to TF32
 };
 
 // Kernel classes for launch counting and the optional CUDA-event profile.
@@ -191,6 +193,15 @@ inline void prof_end(Handle& h, int idx, double flops, double bytes) { prof_end(
 // `slot` selects the launch buffers (one per stream that launches concurrently);
 // max_ctas > 0 caps the CTAs of the persistent kernel (leaving SMs to another stream).
 constexpr int TC_SLOTS = 2;
+constexpr int TC_GENERAL = 4;        // kind: explicit map indices, alpha and rounding
+// Tensor maps for per-front scratch of the level being factored (the block-inverse panel
+// solve): three per front slot -- Mt (512 x 512), Tt (512 x 128), Linv (512 x 512) --
+// encoded and uploaded on `stream`; returns the index of slot 0's first map.
+int gemm_tc_scratch_maps(Handle& h, const std::vector<float*>& mt, const std::vector<float*>& tt,
+                         const std::vector<float*>& linv, cudaStream_t stream, int* base);
+// map index of a node's [L; X] panel (P) and of its inverted diagonal blocks
+inline int tc_map_panel(int node) { return 2 * node; }
+inline int tc_map_dinv(int node) { return 2 * node + 1; }
 int gemm_tc_launch(Handle& h, int li, const std::vector<GemmTask>& tasks, int kind, cudaStream_t stream,
                    int slot = 0, int max_ctas = 0);
 
