@@ -302,17 +302,13 @@ inline bool anc_or_self(const Analysis& a, int x, int y) {   // x is ancestor-or
     return a.tin[x] <= a.tin[y] && a.tout[y] <= a.tout[x];
 }
 
-int analyse_structure(Analysis& a, const int64_t* rowptr, const int* col, const int* owner, double* part) {
-    using clk = std::chrono::steady_clock;
-    auto ms_since = [](clk::time_point t) { return std::chrono::duration<double, std::milli>(clk::now() - t).count(); };
-    auto t0 = clk::now();
+// Ownership: validate the owner array and sort the DOFs stably by owner (I_t lists in
+// natural order, rank = position within I_t), in parallel over DOF chunks.
+int sort_owners(Analysis& a, const int* owner) {
     const int n = a.n;
     a.owner.assign(owner, owner + n);
     for (int i = 0; i < n; ++i)
         if (a.owner[i] < 0 || a.owner[i] >= a.n_nodes) return RSD_ERR_ARG;
-    if (rowptr[0] != 0) return RSD_ERR_ARG;
-    for (int i = 0; i < n; ++i)
-        if (rowptr[i + 1] < rowptr[i]) return RSD_ERR_ARG;
     // stable counting sort by owner, in parallel over DOF chunks (per-chunk histograms)
     a.I_off.assign(a.n_nodes + 1, 0);
     a.I_dofs.resize(n);
@@ -343,6 +339,37 @@ int analyse_structure(Analysis& a, const int64_t* rowptr, const int* col, const 
             }
         });
     }
+    return RSD_OK;
+}
+
+// Extend-add maps: position of each of B_c's DOFs in the parent's front (I_p then B_p).
+void ea_maps(Analysis& a) {
+    a.ea.assign(a.n_nodes, {});
+    parallel_for(a.n_nodes, [&](int64_t tt) {
+        const int t = (int)tt;
+        const int p = a.parent[t];
+        if (p < 0) return;
+        const int sp = a.I_off[p + 1] - a.I_off[p];
+        auto& m = a.ea[t];
+        m.resize(a.B[t].size());
+        for (size_t k = 0; k < a.B[t].size(); ++k) {
+            const int j = a.B[t][k];
+            if (a.owner[j] == p) m[k] = a.rank[j];
+            else m[k] = sp + (int)(std::lower_bound(a.B[p].begin(), a.B[p].end(), j) - a.B[p].begin());
+        }
+    });
+}
+
+// Host structure pass (CSR in host memory): Eq. 3.1 check and B sets.
+int analyse_structure(Analysis& a, const int64_t* rowptr, const int* col, const int* owner, double* part) {
+    using clk = std::chrono::steady_clock;
+    auto ms_since = [](clk::time_point t) { return std::chrono::duration<double, std::milli>(clk::now() - t).count(); };
+    auto t0 = clk::now();
+    const int n = a.n;
+    if (rowptr[0] != 0) return RSD_ERR_ARG;
+    for (int i = 0; i < n; ++i)
+        if (rowptr[i + 1] < rowptr[i]) return RSD_ERR_ARG;
+    RSD_TRY(sort_owners(a, owner));
     part[0] = ms_since(t0);
     t0 = clk::now();
     // Eq. 3.1: no coupling between owners that are not ancestor-related
@@ -421,22 +448,194 @@ int analyse_structure(Analysis& a, const int64_t* rowptr, const int* col, const 
     }
     part[2] = ms_since(t0);
     t0 = clk::now();
-    // extend-add maps
-    a.ea.assign(a.n_nodes, {});
-    parallel_for(a.n_nodes, [&](int64_t tt) {
-        const int t = (int)tt;
-        const int p = a.parent[t];
-        if (p < 0) return;
-        const int sp = a.I_off[p + 1] - a.I_off[p];
-        auto& m = a.ea[t];
-        m.resize(a.B[t].size());
-        for (size_t k = 0; k < a.B[t].size(); ++k) {
-            const int j = a.B[t][k];
-            if (a.owner[j] == p) m[k] = a.rank[j];
-            else m[k] = sp + (int)(std::lower_bound(a.B[p].begin(), a.B[p].end(), j) - a.B[p].begin());
+    ea_maps(a);
+    part[3] = ms_since(t0);
+    return RSD_OK;
+}
+
+// ---- device structure pass (CSR in device memory) ---------------------------------
+// Only the ownership array crosses to the host (for the sort); the Eq. 3.1 check and
+// the B sets run on the GPU over the CSR, and the sets come back as bitmaps: for every
+// node t one bitmap per proper ancestor x (parent first), bit r set when the DOF of rank
+// r in I_x belongs to B_t.  A row of t marks the ancestor DOFs it couples to; then,
+// level by level from the deepest, every node ORs its bitmaps for the ancestors beyond
+// its parent into its parent's (B_parent contains B_child minus I_parent).
+
+enum { SF_ROWPTR = 0, SF_COL, SF_PARTITION, SF_SLOTS };
+
+__global__ void k_struct_mark(int n, int64_t nnz, const int64_t* __restrict__ rowptr, const int* __restrict__ col,
+                              const int* __restrict__ owner, const int* __restrict__ rank,
+                              const int* __restrict__ tin, const int* __restrict__ tout,
+                              const int* __restrict__ depth, const int64_t* __restrict__ anc_word,
+                              const int* __restrict__ anc_first, uint32_t* __restrict__ bm, int* __restrict__ flags) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (rowptr[0] != 0 || rowptr[n] != nnz)) flags[SF_ROWPTR] = 1;
+    for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+        const int64_t b = rowptr[i], e = rowptr[i + 1];
+        if (b < 0 || e < b || e > nnz) { if (lane == 0) flags[SF_ROWPTR] = 1; continue; }
+        const int oi = owner[i];
+        const int ti = tin[oi], to = tout[oi], di = depth[oi];
+        for (int64_t k = b + lane; k < e; k += 32) {
+            const int j = col[k];
+            if (j < 0 || j >= n) { flags[SF_COL] = 1; continue; }
+            const int oj = owner[j];
+            if (oj == oi) continue;
+            if (tin[oj] <= ti && to <= tout[oj]) {            // oj is a proper ancestor of oi
+                const int r = rank[j];
+                const int64_t w = anc_word[anc_first[oi] + (di - depth[oj] - 1)] + (r >> 5);
+                atomicOr(bm + w, 1u << (r & 31));
+            } else if (!(ti <= tin[oj] && tout[oj] <= to)) {
+                flags[SF_PARTITION] = 1;                       // neither ancestor nor descendant
+            }
         }
+    }
+}
+
+// bm[parent's words] |= bm[child's words beyond its parent's bitmap], one CTA per child
+__global__ void k_struct_up(const int* __restrict__ nodes, const int* __restrict__ parent,
+                            const int64_t* __restrict__ anc_word, const int* __restrict__ anc_first,
+                            const int64_t* __restrict__ words_total, uint32_t* __restrict__ bm) {
+    const int c = nodes[blockIdx.x];
+    const int t = parent[c];
+    const int64_t n = words_total[t];
+    if (n == 0) return;
+    const uint32_t* src = bm + anc_word[anc_first[c] + 1];
+    uint32_t* dst = bm + anc_word[anc_first[t]];
+    for (int64_t w = threadIdx.x; w < n; w += blockDim.x) {
+        const uint32_t v = src[w];
+        if (v) atomicOr(dst + w, v);
+    }
+}
+
+int analyse_structure_device(Analysis& a, const rsd_csr* K, const int* d_owner, cudaStream_t st, double* part) {
+    using clk = std::chrono::steady_clock;
+    auto ms_since = [](clk::time_point t) { return std::chrono::duration<double, std::milli>(clk::now() - t).count(); };
+    auto t0 = clk::now();
+    const int n = a.n, nn = a.n_nodes;
+    // ownership to the host, stable sort there
+    size_t pin_bytes = 0;
+    char* pin = pinned2_take(sizeof(int) * (size_t)n, &pin_bytes);
+    struct PinGuard { char* p; size_t b; ~PinGuard() { if (p) pinned2_give(p, b); } } guard{pin, pin_bytes};
+    std::vector<int> own_pageable;
+    int* own = (int*)pin;
+    if (!own) { own_pageable.resize(n); own = own_pageable.data(); }
+    RSD_CUDA_TRY(cudaMemcpyAsync(own, d_owner, sizeof(int) * n, cudaMemcpyDeviceToHost, st));
+    RSD_CUDA_TRY(cudaStreamSynchronize(st));
+    part[0] = ms_since(t0);
+    t0 = clk::now();
+    RSD_TRY(sort_owners(a, own));
+    // bitmap layout: node t holds depth(t) bitmaps (parent first), words(x) = ceil(s_x / 32)
+    std::vector<int> anc_first(nn + 1, 0);
+    for (int t = 0; t < nn; ++t) anc_first[t + 1] = anc_first[t] + a.depth[t];
+    std::vector<int64_t> anc_word(std::max(1, anc_first[nn])), words_total(nn, 0);
+    int64_t W = 0;
+    for (int t = 0; t < nn; ++t) {
+        int q = 0;
+        for (int x = a.parent[t]; x >= 0; x = a.parent[x], ++q) {
+            anc_word[anc_first[t] + q] = W;
+            const int64_t wx = (a.I_off[x + 1] - a.I_off[x] + 31) / 32;
+            W += wx;
+            words_total[t] += wx;
+        }
+    }
+    part[1] = ms_since(t0);
+    t0 = clk::now();
+    // device buffers: rank, tree arrays, layout, bitmaps, flags
+    const size_t b_rank = sizeof(int) * n, b_tree = sizeof(int) * nn;
+    const size_t b_aw = sizeof(int64_t) * anc_word.size(), b_af = sizeof(int) * (nn + 1);
+    const size_t b_wt = sizeof(int64_t) * nn, b_bm = sizeof(uint32_t) * std::max<int64_t>(W, 1);
+    auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    const size_t total = al(b_rank) + 4 * al(b_tree) + al(b_aw) + al(b_af) + al(b_wt) + al(b_bm) + al(sizeof(int) * SF_SLOTS);
+    char* dbuf = nullptr;
+    RSD_CUDA_TRY(cudaMallocAsync((void**)&dbuf, total, st));
+    struct Free { char* p; cudaStream_t s; ~Free() { if (p) cudaFreeAsync(p, s); } } fr{dbuf, st};
+    char* cur = dbuf;
+    auto take = [&](size_t b) { char* r = cur; cur += al(b); return r; };
+    int* d_rank = (int*)take(b_rank);
+    int* d_tin = (int*)take(b_tree);
+    int* d_tout = (int*)take(b_tree);
+    int* d_depth = (int*)take(b_tree);
+    int* d_parent = (int*)take(b_tree);
+    int64_t* d_aw = (int64_t*)take(b_aw);
+    int* d_af = (int*)take(b_af);
+    int64_t* d_wt = (int64_t*)take(b_wt);
+    uint32_t* d_bm = (uint32_t*)take(b_bm);
+    int* d_flags = (int*)take(sizeof(int) * SF_SLOTS);
+    std::vector<int> parent_tab(a.parent);
+    RSD_CUDA_TRY(cudaMemcpyAsync(d_rank, a.rank.data(), b_rank, cudaMemcpyHostToDevice, st));
+    RSD_CUDA_TRY(cudaMemcpyAsync(d_tin, a.tin.data(), b_tree, cudaMemcpyHostToDevice, st));
+    RSD_CUDA_TRY(cudaMemcpyAsync(d_tout, a.tout.data(), b_tree, cudaMemcpyHostToDevice, st));
+    RSD_CUDA_TRY(cudaMemcpyAsync(d_depth, a.depth.data(), b_tree, cudaMemcpyHostToDevice, st));
+    RSD_CUDA_TRY(cudaMemcpyAsync(d_parent, parent_tab.data(), b_tree, cudaMemcpyHostToDevice, st));
+    RSD_CUDA_TRY(cudaMemcpyAsync(d_aw, anc_word.data(), b_aw, cudaMemcpyHostToDevice, st));
+    RSD_CUDA_TRY(cudaMemcpyAsync(d_af, anc_first.data(), b_af, cudaMemcpyHostToDevice, st));
+    RSD_CUDA_TRY(cudaMemcpyAsync(d_wt, words_total.data(), b_wt, cudaMemcpyHostToDevice, st));
+    RSD_CUDA_TRY(cudaMemsetAsync(d_bm, 0, b_bm, st));
+    RSD_CUDA_TRY(cudaMemsetAsync(d_flags, 0, sizeof(int) * SF_SLOTS, st));
+    int sms = 148, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    k_struct_mark<<<(unsigned)(sms * 8), 256, 0, st>>>(n, K->nnz, K->rowptr, K->col, d_owner, d_rank, d_tin, d_tout,
+                                                        d_depth, d_aw, d_af, d_bm, d_flags);
+    count_launch();
+    RSD_CUDA_TRY(cudaGetLastError());
+    // propagate level by level, deepest first (children of depth d into depth d-1)
+    std::vector<int> nodes_by_depth;
+    std::vector<int> doff(a.max_depth + 2, 0);
+    for (int t = 0; t < nn; ++t) doff[a.depth[t] + 1]++;
+    for (int d = 0; d <= a.max_depth; ++d) doff[d + 1] += doff[d];
+    nodes_by_depth.resize(nn);
+    {
+        std::vector<int> fill(doff.begin(), doff.end() - 1);
+        for (int t = 0; t < nn; ++t) nodes_by_depth[fill[a.depth[t]]++] = t;
+    }
+    int* d_nodes = nullptr;
+    RSD_CUDA_TRY(cudaMallocAsync((void**)&d_nodes, sizeof(int) * nn, st));
+    struct Free2 { int* p; cudaStream_t s; ~Free2() { if (p) cudaFreeAsync(p, s); } } fr2{d_nodes, st};
+    RSD_CUDA_TRY(cudaMemcpyAsync(d_nodes, nodes_by_depth.data(), sizeof(int) * nn, cudaMemcpyHostToDevice, st));
+    for (int d = a.max_depth; d >= 2; --d) {
+        const int cnt = doff[d + 1] - doff[d];
+        if (cnt == 0) continue;
+        k_struct_up<<<(unsigned)cnt, 256, 0, st>>>(d_nodes + doff[d], d_parent, d_aw, d_af, d_wt, d_bm);
+        count_launch();
+        RSD_CUDA_TRY(cudaGetLastError());
+    }
+    std::vector<uint32_t> bm((size_t)std::max<int64_t>(W, 1));
+    int flags[SF_SLOTS];
+    RSD_CUDA_TRY(cudaMemcpyAsync(flags, d_flags, sizeof(flags), cudaMemcpyDeviceToHost, st));
+    RSD_CUDA_TRY(cudaMemcpyAsync(bm.data(), d_bm, b_bm, cudaMemcpyDeviceToHost, st));
+    RSD_CUDA_TRY(cudaStreamSynchronize(st));
+    if (flags[SF_ROWPTR] || flags[SF_COL]) return RSD_ERR_ARG;
+    if (flags[SF_PARTITION]) return RSD_ERR_PARTITION;
+    part[2] = ms_since(t0);
+    t0 = clk::now();
+    // B lists: each ancestor's bits in rank order are ascending natural ids; merge them
+    a.B.assign(nn, {});
+    parallel_for(nn, [&](int64_t tt) {
+        const int t = (int)tt;
+        std::vector<int> out;
+        int q = 0;
+        for (int x = a.parent[t]; x >= 0; x = a.parent[x], ++q) {
+            const int sx = a.I_off[x + 1] - a.I_off[x];
+            const uint32_t* bits = bm.data() + anc_word[anc_first[t] + q];
+            const size_t mid = out.size();
+            for (int wd = 0; wd < (sx + 31) / 32; ++wd) {
+                uint32_t m = bits[wd];
+                while (m) {
+                    const int bt = __builtin_ctz(m);
+                    m &= m - 1;
+                    out.push_back(a.I_dofs[a.I_off[x] + wd * 32 + bt]);
+                }
+            }
+            std::inplace_merge(out.begin(), out.begin() + mid, out.end());
+        }
+        a.B[t] = std::move(out);
     });
     part[3] = ms_since(t0);
+    t0 = clk::now();
+    ea_maps(a);
+    part[4] = ms_since(t0);
     return RSD_OK;
 }
 
@@ -880,48 +1079,18 @@ extern "C" int rsd_setup(const rsd_csr* K, const int32_t* dof_node, const rsd_tr
     Analysis a;
     a.n = K->n;
     RSD_TRY(analyse_tree(a, T));
-    // host views of the inputs
-    std::vector<int64_t> rp;
-    std::vector<int> cl, ow;
-    std::vector<double> vl;
-    const int64_t* rowptr = K->rowptr;
-    const int* col = K->col;
-    const int* owner = dof_node;
     cudaStream_t st = (cudaStream_t)o.stream;
-    char* pin = nullptr;
-    size_t pin_bytes = 0;
     using clk = std::chrono::steady_clock;
     auto ms_since = [](clk::time_point t) { return std::chrono::duration<double, std::milli>(clk::now() - t).count(); };
     double part[6] = {0, 0, 0, 0, 0, 0};
-    auto t_copy = clk::now();
     if (K->mem == RSD_MEM_DEVICE) {
-        const size_t b_rp = sizeof(int64_t) * (K->n + 1), b_cl = sizeof(int) * K->nnz, b_ow = sizeof(int) * K->n;
-        pin = pinned2_take(b_rp + b_cl + b_ow + 64, &pin_bytes);
-        if (pin) {
-            RSD_CUDA_TRY(cudaMemcpyAsync(pin, K->rowptr, b_rp, cudaMemcpyDeviceToHost, st));
-            RSD_CUDA_TRY(cudaMemcpyAsync(pin + b_rp, K->col, b_cl, cudaMemcpyDeviceToHost, st));
-            RSD_CUDA_TRY(cudaMemcpyAsync(pin + b_rp + b_cl, dof_node, b_ow, cudaMemcpyDeviceToHost, st));
-            RSD_CUDA_TRY(cudaStreamSynchronize(st));
-            rowptr = (const int64_t*)pin;
-            col = (const int*)(pin + b_rp);
-            owner = (const int*)(pin + b_rp + b_cl);
-        } else {
-            rp.resize(K->n + 1);
-            cl.resize(K->nnz);
-            ow.resize(K->n);
-            RSD_CUDA_TRY(cudaMemcpyAsync(rp.data(), K->rowptr, b_rp, cudaMemcpyDeviceToHost, st));
-            RSD_CUDA_TRY(cudaMemcpyAsync(cl.data(), K->col, b_cl, cudaMemcpyDeviceToHost, st));
-            RSD_CUDA_TRY(cudaMemcpyAsync(ow.data(), dof_node, b_ow, cudaMemcpyDeviceToHost, st));
-            RSD_CUDA_TRY(cudaStreamSynchronize(st));
-            rowptr = rp.data();
-            col = cl.data();
-            owner = ow.data();
-        }
+        RSD_TRY(analyse_structure_device(a, K, dof_node, st, part));
+    } else {
+        const auto t0 = clk::now();
+        if (K->rowptr[K->n] != K->nnz) return RSD_ERR_ARG;
+        part[0] = ms_since(t0);
+        RSD_TRY(analyse_structure(a, K->rowptr, K->col, dof_node, part + 1));
     }
-    part[0] = ms_since(t_copy);
-    struct PinGuard { char* p; size_t b; ~PinGuard() { if (p) pinned2_give(p, b); } } guard{pin, pin_bytes};
-    if (rowptr[K->n] != K->nnz) return RSD_ERR_ARG;
-    RSD_TRY(analyse_structure(a, rowptr, col, owner, part + 1));
     auto* hh = new (std::nothrow) rsd_handle_s();
     if (!hh) return RSD_ERR_NOMEM;
     Handle& h = hh->h;

@@ -154,6 +154,45 @@ def test_host_csr_input_matches_device_input(rsd):
     assert torch.equal(h1.apply(r), h2.apply(r))
 
 
+def test_device_structure_pass_matches_host_pass(rsd):
+    """A device CSR goes through the GPU structure pass (Eq. 3.1 check, B-set bitmaps), a
+    host CSR through the host pass: identical interface sets and extend-add maps."""
+    w = _work(20, 2, True)
+    prob = rsd.grid_problem(20, 2, w["kappa"], w["f"])
+    hd = _setup(rsd, prob, rsd.RSD_PREC_FP64)
+    hh = rsd.RSD.setup(prob["rowptr"].cpu(), prob["col"].cpu(), prob["val"].cpu(), prob["dof_node"].cpu(),
+                       prob["parent"], prec_leaf=rsd.RSD_PREC_FP64, prec_mid=rsd.RSD_PREC_FP64)
+    for t in range(len(prob["parent"])):
+        assert hd.front_dims(t) == hh.front_dims(t)
+        assert np.array_equal(hd.front_dofs(t), hh.front_dofs(t))
+        assert np.array_equal(hd.front_map(t), hh.front_map(t))
+
+
+def test_device_structure_pass_rejects_bad_input(rsd):
+    from paper_1210_6266_gb300 import _lib
+    n = 9
+    A = fem.assemble(n, np.ones((n - 1) ** 3)).tolil()
+    owner = partition.octree_owner(n, 1, fem.interior_coords(n))
+    parent = partition.octree_parent(1)
+    i, j = int(np.nonzero(owner == 1)[0][0]), int(np.nonzero(owner == 8)[0][-1])
+    A[i, j] = A[j, i] = -0.01                       # couples two leaves: violates Eq. 3.1
+    A = A.tocsr()
+    dev = lambda a, dt: torch.tensor(a, dtype=dt, device="cuda")
+    args = (dev(A.indptr, torch.int64), dev(A.indices, torch.int32), dev(A.data, torch.float64),
+            dev(owner, torch.int32), parent)
+    with pytest.raises(rsd.RSDError) as e:
+        rsd.RSD.setup(*args, prec_leaf=rsd.RSD_PREC_FP64, prec_mid=rsd.RSD_PREC_FP64)
+    assert e.value.code == _lib.RSD_ERR_PARTITION
+    B = fem.assemble(n, np.ones((n - 1) ** 3))
+    col = B.indices.copy()
+    col[5] = B.shape[0]                             # column index out of range
+    args = (dev(B.indptr, torch.int64), dev(col, torch.int32), dev(B.data, torch.float64),
+            dev(owner, torch.int32), parent)
+    with pytest.raises(rsd.RSDError) as e:
+        rsd.RSD.setup(*args, prec_leaf=rsd.RSD_PREC_FP64, prec_mid=rsd.RSD_PREC_FP64)
+    assert e.value.code == _lib.RSD_ERR_ARG
+
+
 def test_apply_is_deterministic(rsd):
     w = _work(20, 2, True)
     prob = rsd.grid_problem(20, 2, w["kappa"], w["f"])
