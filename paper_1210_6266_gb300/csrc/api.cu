@@ -852,12 +852,16 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
         front_cursor += L.fronts.size();
         L.d_child_slots = d_child + child_base;
         // forward items: key = block index (I blocks, then B blocks), fronts interleaved
+        // a diagonal item covers gd consecutive blocks: forward groups start at multiples
+        // of gd from the top-left, backward groups are counted from the last block up
+        const int gd = sweep_group(L);
         std::vector<std::pair<int, int>> fw, bw;   // (key, item)
         for (size_t sidx = 0; sidx < L.fronts.size(); ++sidx) {
             const FrontDesc& f = L.fronts[sidx];
             const int nbB = (f.b + NB - 1) / NB;
-            for (int blk = 0; blk < f.nd + nbB; ++blk) fw.push_back({blk, (int)(sidx << 16) | blk});
-            for (int cb = f.nd - 1; cb >= 0; --cb) bw.push_back({f.nd - 1 - cb, (int)(sidx << 16) | cb});
+            for (int blk = 0; blk < f.nd; blk += gd) fw.push_back({blk, (int)(sidx << 16) | blk});
+            for (int blk = f.nd; blk < f.nd + nbB; ++blk) fw.push_back({blk, (int)(sidx << 16) | blk});
+            for (int hi = f.nd - 1; hi >= 0; hi -= gd) bw.push_back({f.nd - 1 - hi, (int)(sidx << 16) | hi});
         }
         std::stable_sort(fw.begin(), fw.end(), [](auto& x, auto& y) { return x.first < y.first; });
         std::stable_sort(bw.begin(), bw.end(), [](auto& x, auto& y) { return x.first < y.first; });
@@ -872,7 +876,7 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
         if (paper) {
             std::vector<std::pair<int, int>> fs;
             for (size_t sidx = 0; sidx < L.fronts.size(); ++sidx)
-                for (int blk = 0; blk < L.fronts[sidx].nd; ++blk) fs.push_back({blk, (int)(sidx << 16) | blk});
+                for (int blk = 0; blk < L.fronts[sidx].nd; blk += gd) fs.push_back({blk, (int)(sidx << 16) | blk});
             std::stable_sort(fs.begin(), fs.end(), [](auto& x, auto& y) { return x.first < y.first; });
             L.d_fwd_items_solve = d_items + item_cursor;
             L.n_fwd_items_solve = (int)fs.size();

@@ -37,17 +37,31 @@ template <> __device__ __forceinline__ double ld_cg(const double* p) { return __
 
 __device__ __forceinline__ int ld_volatile(const int* p) { return *(volatile const int*)p; }
 
-// Asynchronous copy of one NB x NB inverted diagonal block into shared memory (16 B per
-// cp.async, L2 only); completed by cp_async_wait() before use.
+// Asynchronous copies into shared memory (16 B per cp.async, L2 only), committed by
+// cp_async_commit() and completed by cp_async_wait() before use: `count` consecutive
+// NB x NB inverted diagonal blocks, or `rows` rows of NB entries from a row-major panel.
 template <typename T>
-__device__ __forceinline__ void prefetch_block(T* dst, const T* src) {
-    constexpr int CHUNKS = NB * NB * (int)sizeof(T) / 16;
+__device__ __forceinline__ void prefetch_blocks(T* dst, const T* src, int count) {
+    const int chunks = count * NB * NB * (int)sizeof(T) / 16;
     const uint32_t d0 = (uint32_t)__cvta_generic_to_shared(dst);
-    for (int c = threadIdx.x; c < CHUNKS; c += blockDim.x)
+    for (int c = threadIdx.x; c < chunks; c += blockDim.x)
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d0 + 16 * c), "l"((const char*)src + 16 * c)
                      : "memory");
-    asm volatile("cp.async.commit_group;" ::: "memory");
 }
+
+template <typename T>
+__device__ __forceinline__ void prefetch_rows(T* dst, const T* src, int ld, int rows) {
+    constexpr int RC = NB * (int)sizeof(T) / 16;         // 16-byte chunks per row
+    const uint32_t d0 = (uint32_t)__cvta_generic_to_shared(dst);
+    for (int c = threadIdx.x; c < rows * RC; c += blockDim.x) {
+        const int r = c / RC, q = c % RC;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                     ::"r"(d0 + (uint32_t)(r * NB * (int)sizeof(T) + 16 * q)),
+                       "l"((const char*)(src + (int64_t)r * ld) + 16 * q) : "memory");
+    }
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
@@ -73,44 +87,61 @@ __device__ int wait_flag(const int* flag, int target, int* err, int* s_val) {
     return *s_val;
 }
 
-__device__ void publish_flag(int* flag, int value) {
-    __threadfence();
+// Threads that stored results fence them; after the barrier one thread raises the flag.
+__device__ void publish_flag(int* flag, int value, bool wrote) {
+    if (wrote) __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) atomicExch(flag, value);
 }
 
 // ---- upward sweep ------------------------------------------------------------------
+// Front vector of the upward sweep: v = r on I (0 on B) plus the children's
+// contributions, children added in a fixed order.  blockIdx.y splits the front's
+// positions into disjoint ranges; a CTA scans every child's map and applies the entries
+// that land in its range (a child's map is injective, so no two threads of a CTA touch
+// the same position).
 template <typename A, typename Ac>
 __global__ void k_fwd_gather(const FrontDesc* __restrict__ fronts, const FrontDesc* __restrict__ kids,
                              const int* __restrict__ child_slots, const double* __restrict__ r) {
     const FrontDesc f = fronts[blockIdx.x];
+    const int len = (f.N + gridDim.y - 1) / gridDim.y;
+    const int p0 = blockIdx.y * len, p1 = min(f.N, p0 + len);
     A* v = (A*)f.vec;
-    for (int p = threadIdx.x; p < f.N; p += blockDim.x) v[p] = p < f.s ? (A)r[f.I[p]] : (A)0;
-    if (threadIdx.x == 0) { f.flag[0] = 0; f.flag[1] = 0; }
+    for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) v[p] = p < f.s ? (A)r[f.I[p]] : (A)0;
+    if (blockIdx.y == 0 && threadIdx.x == 0) { f.flag[0] = 0; f.flag[1] = 0; }
     for (int ci = 0; ci < f.child_count; ++ci) {
         __syncthreads();
         const FrontDesc c = kids[child_slots[f.child_begin + ci]];
         const Ac* cv = (const Ac*)c.vec;
-        for (int i = threadIdx.x; i < c.b; i += blockDim.x) v[c.ea[i]] += (A)cv[c.s + i];
+        for (int i = threadIdx.x; i < c.b; i += blockDim.x) {
+            const int p = c.ea[i];
+            if (p >= p0 && p < p1) v[p] += (A)cv[c.s + i];
+        }
     }
 }
 
-// Row block item: rows [r0, r1) of front f.  acc_row = v_row - sum_{cb < ncb} P[row, cb] y_cb;
-// for a diagonal block y = Dinv * acc (published), else the contribution v_row = acc.
-// The factor tile of a column block is requested before waiting for that block's y, so
-// the item at the head of the dependency chain only pays for y and the arithmetic.
-template <typename T, typename A>
-__global__ void __launch_bounds__(AT) k_fwd_sweep(const FrontDesc* __restrict__ fronts,
-                                                  const int* __restrict__ items, int n_items,
-                                                  int* __restrict__ ticket, int* __restrict__ err) {
+// Forward item: either a group of up to GD consecutive diagonal row blocks [b0, b0 + nb)
+// of one front (item code = b0), or one NB-row block of its B rows.  The item first
+// streams acc_row = sum_{cb < ncb} P[row, cb] y_cb over the finished column blocks (the
+// factor tile of a column block is requested before waiting for that block's y); a B
+// block then stores its contribution v_row - acc_row.  A diagonal group finishes its
+// blocks inside the CTA -- t_g = v_g - acc_g - sum_{g' < g} P[g, g'] y_g', y_g = Dinv_g t_g
+// -- and publishes the front's progress counter once for the whole group, so the
+// dependency chain between CTAs has one hand-off per GD blocks.
+template <typename T, typename A, int GD>
+__global__ void __launch_bounds__(AT, GD == 1 ? 2 : 1) k_fwd_sweep(const FrontDesc* __restrict__ fronts,
+                                                     const int* __restrict__ items, int n_items,
+                                                     int* __restrict__ ticket, int* __restrict__ err) {
     using V = typename Vec<T>::V;
     constexpr int VW = Vec<T>::W;
     constexpr int PASSES = NB / (32 * VW);
-    constexpr int RPW = NB / AW;                 // rows per warp
+    constexpr int RPW = NB / AW;                 // rows per warp and block
     __shared__ int s_item, s_flag;
-    __shared__ __align__(16) A s_t[NB];
+    __shared__ __align__(16) A s_t[GD * NB];
+    __shared__ __align__(16) A s_y[NB];
     extern __shared__ __align__(16) unsigned char sweep_smem[];
-    T* Ds = (T*)sweep_smem;                      // NB x NB inverted diagonal block
+    T* Ds = (T*)sweep_smem;                      // GD inverted diagonal blocks
+    T* Ls = Ds + GD * NB * NB;                   // P[block b0+1 rows, block b0 columns]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(ticket, 1);
@@ -121,15 +152,23 @@ __global__ void __launch_bounds__(AT) k_fwd_sweep(const FrontDesc* __restrict__ 
         const int slot = items[it] >> 16, blk = items[it] & 0xffff;
         const FrontDesc f = fronts[slot];
         const bool diag = blk < f.nd;
-        if (diag) prefetch_block(Ds, (const T*)f.Dinv + (int64_t)blk * NB * NB);
-        const int r0 = diag ? blk * NB : f.s + (blk - f.nd) * NB;
-        const int r1 = diag ? min(r0 + NB, f.s) : min(r0 + NB, f.N);
-        const int ncb = diag ? blk : f.nd;
+        const int nb = diag ? min(GD, f.nd - blk) : 1;
         const T* P = (const T*)f.P;
         A* v = (A*)f.vec;
-        A acc[RPW];
+        const int r0 = diag ? blk * NB : f.s + (blk - f.nd) * NB;
+        const int r1 = diag ? min(r0 + nb * NB, f.s) : min(r0 + NB, f.N);
+        if (diag) {
+            prefetch_blocks(Ds, (const T*)f.Dinv + (int64_t)blk * NB * NB, nb);
+            if (GD > 1 && nb > 1) prefetch_rows(Ls, P + (int64_t)(r0 + NB) * f.ldp + r0, f.ldp, r1 - r0 - NB);
+            cp_async_commit();
+        }
+        for (int q = threadIdx.x; q < GD * NB; q += AT) s_t[q] = (r0 + q < r1) ? ld_cg(v + r0 + q) : (A)0;
+        const int ncb = diag ? blk : f.nd;
+        A acc[GD][RPW];
 #pragma unroll
-        for (int u = 0; u < RPW; ++u) acc[u] = 0;
+        for (int g = 0; g < GD; ++g)
+#pragma unroll
+            for (int u = 0; u < RPW; ++u) acc[g][u] = 0;
         int seen = 0;
         for (int cb = 0; cb < ncb; ++cb) {
             const int c0 = cb * NB;
@@ -137,40 +176,85 @@ __global__ void __launch_bounds__(AT) k_fwd_sweep(const FrontDesc* __restrict__ 
 #pragma unroll
             for (int ps = 0; ps < PASSES; ++ps) {
                 const int cl = ps * 32 * VW + lane * VW;   // column inside the block
-                V l[RPW];
+                V l[GD][RPW];
 #pragma unroll
-                for (int u = 0; u < RPW; ++u) {
-                    const int row = r0 + warp + AW * u;
-                    l[u] = (row < r1 && cl < cw) ? __ldg((const V*)(P + (int64_t)row * f.ldp + c0 + cl)) : V{};
-                }
+                for (int g = 0; g < GD; ++g)
+#pragma unroll
+                    for (int u = 0; u < RPW; ++u) {
+                        const int row = r0 + g * NB + warp + AW * u;
+                        l[g][u] = (g < nb && row < r1 && cl < cw) ? __ldg((const V*)(P + (int64_t)row * f.ldp + c0 + cl)) : V{};
+                    }
                 if (ps == 0 && seen < cb + 1) seen = wait_flag(&f.flag[0], cb + 1, err, &s_flag);
                 A y[VW];
 #pragma unroll
                 for (int e = 0; e < VW; ++e) y[e] = (cl + e < cw) ? ld_cg(v + c0 + cl + e) : (A)0;
 #pragma unroll
-                for (int u = 0; u < RPW; ++u)
+                for (int g = 0; g < GD; ++g)
 #pragma unroll
-                    for (int e = 0; e < VW; ++e) acc[u] += (A)vget(l[u], e) * y[e];
+                    for (int u = 0; u < RPW; ++u)
+#pragma unroll
+                        for (int e = 0; e < VW; ++e) acc[g][u] += (A)vget(l[g][u], e) * y[e];
             }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-            for (int u = 0; u < RPW; ++u) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
+            for (int g = 0; g < GD; ++g)
+#pragma unroll
+                for (int u = 0; u < RPW; ++u) acc[g][u] += __shfl_xor_sync(0xffffffffu, acc[g][u], o);
+        __syncthreads();                             // s_t holds v on the item's rows
         if (lane == 0) {
 #pragma unroll
-            for (int u = 0; u < RPW; ++u) {
-                const int row = r0 + warp + AW * u;
-                if (row < r1) s_t[row - r0] = ld_cg(v + row) - acc[u];
-            }
+            for (int g = 0; g < GD; ++g)
+#pragma unroll
+                for (int u = 0; u < RPW; ++u) {
+                    const int q = g * NB + warp + AW * u;
+                    if (r0 + q < r1) s_t[q] -= acc[g][u];
+                }
         }
         __syncthreads();
-        if (diag) {
-            const int w = r1 - r0;
-            cp_async_wait();
+        if (!diag) {
+            for (int q = threadIdx.x; q < r1 - r0; q += AT) __stcg(v + r0 + q, s_t[q]);
             __syncthreads();
-            // y = Dinv t: each thread takes RPW rows x VW columns per pass, then a warp sum
+            continue;
+        }
+        cp_async_wait();
+        __syncthreads();
+        for (int g = 0; g < nb; ++g) {
+            const int w = min(NB, r1 - r0 - g * NB);
             A part[RPW];
+            if (g > 0) {
+                // t_g -= P[g rows, g-1 columns] y_{g-1}   (only g = 1: GD <= 2)
+#pragma unroll
+                for (int u = 0; u < RPW; ++u) part[u] = 0;
+#pragma unroll
+                for (int ps = 0; ps < PASSES; ++ps) {
+                    const int cl = ps * 32 * VW + lane * VW;
+                    A yv[VW];
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) yv[e] = s_y[cl + e];
+#pragma unroll
+                    for (int u = 0; u < RPW; ++u) {
+                        const V d = *(const V*)(Ls + (warp + AW * u) * NB + cl);
+#pragma unroll
+                        for (int e = 0; e < VW; ++e) part[u] += (A)vget(d, e) * yv[e];
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                    for (int u = 0; u < RPW; ++u) part[u] += __shfl_xor_sync(0xffffffffu, part[u], o);
+                if (lane == 0) {
+#pragma unroll
+                    for (int u = 0; u < RPW; ++u) {
+                        const int rr = warp + AW * u;
+                        if (rr < w) s_t[g * NB + rr] -= part[u];
+                    }
+                }
+                __syncthreads();
+            }
+            // y_g = Dinv_g t_g: each thread takes RPW rows x VW columns per pass, then a warp sum
+            const T* D = Ds + g * NB * NB;
 #pragma unroll
             for (int u = 0; u < RPW; ++u) part[u] = 0;
 #pragma unroll
@@ -178,10 +262,10 @@ __global__ void __launch_bounds__(AT) k_fwd_sweep(const FrontDesc* __restrict__ 
                 const int cl = ps * 32 * VW + lane * VW;
                 A t[VW];
 #pragma unroll
-                for (int e = 0; e < VW; ++e) t[e] = cl + e < w ? s_t[cl + e] : (A)0;
+                for (int e = 0; e < VW; ++e) t[e] = cl + e < w ? s_t[g * NB + cl + e] : (A)0;
 #pragma unroll
                 for (int u = 0; u < RPW; ++u) {
-                    const V d = *(const V*)(Ds + (warp + AW * u) * NB + cl);
+                    const V d = *(const V*)(D + (warp + AW * u) * NB + cl);
 #pragma unroll
                     for (int e = 0; e < VW; ++e) part[u] += (A)vget(d, e) * t[e];
                 }
@@ -194,13 +278,15 @@ __global__ void __launch_bounds__(AT) k_fwd_sweep(const FrontDesc* __restrict__ 
 #pragma unroll
                 for (int u = 0; u < RPW; ++u) {
                     const int rr = warp + AW * u;
-                    if (rr < w) __stcg(v + r0 + rr, part[u]);
+                    if (rr < w) {
+                        __stcg(v + r0 + g * NB + rr, part[u]);
+                        s_y[rr] = part[u];
+                    }
                 }
             }
-            publish_flag(&f.flag[0], blk + 1);
-        } else {
-            for (int rr = threadIdx.x; rr < r1 - r0; rr += AT) __stcg(v + r0 + rr, s_t[rr]);
+            __syncthreads();
         }
+        publish_flag(&f.flag[0], blk + nb, lane == 0);
         __syncthreads();
     }
 }
@@ -213,24 +299,28 @@ __global__ void k_bwd_gather(const FrontDesc* __restrict__ fronts, const double*
     for (int i = threadIdx.x; i < f.b; i += blockDim.x) v[f.s + i] = (A)z[f.Bd[i]];
 }
 
-// Column block item cb: t = y_cb - sum_{rows i >= c1} P[i, cb]^T x_i, x_cb = Dinv^T t.
-// Rows are consumed in NB-row groups from the bottom (ancestor rows first, then the
-// interface rows of later blocks as their owners finish); each group's factor rows are
-// requested before waiting for the group's x.
-template <typename T, typename A>
-__global__ void __launch_bounds__(AT) k_bwd_sweep(const FrontDesc* __restrict__ fronts,
-                                                  const int* __restrict__ items, int n_items,
-                                                  int* __restrict__ ticket, int* __restrict__ err,
-                                                  double* __restrict__ z) {
+// Backward item: a group of up to GD consecutive column blocks [lo, hi] (item code = hi,
+// lo = hi - nb + 1), solved from the highest: t = y - sum over the rows below the group of
+// P[rows, group columns]^T x_rows (ancestor rows first, then the interface row blocks
+// above hi as their owners finish; each row group's factor rows are requested before
+// waiting for its x); then inside the CTA x_hi = Dinv_hi^T t_hi,
+// t_lo -= P[hi rows, lo columns]^T x_hi, x_lo = Dinv_lo^T t_lo, and one publish.
+template <typename T, typename A, int GD>
+__global__ void __launch_bounds__(AT, GD == 1 ? 2 : 1) k_bwd_sweep(const FrontDesc* __restrict__ fronts,
+                                                     const int* __restrict__ items, int n_items,
+                                                     int* __restrict__ ticket, int* __restrict__ err,
+                                                     double* __restrict__ z) {
     using V = typename Vec<T>::V;
     constexpr int VW = Vec<T>::W;
     constexpr int PASSES = NB / (32 * VW);
-    constexpr int RB = 16 / PASSES;              // rows per warp per batch
+    constexpr int RB = 16 / PASSES;              // rows per warp per batch (a whole row block for FP32)
     __shared__ int s_item, s_flag;
-    __shared__ A s_red[AW][NB];
-    __shared__ A s_t[NB];
+    __shared__ A s_red[AW][GD * NB];
+    __shared__ A s_t[GD * NB];
+    __shared__ A s_x[NB];
     extern __shared__ __align__(16) unsigned char sweep_smem[];
-    T* Ds = (T*)sweep_smem;                      // NB x NB inverted diagonal block
+    T* Ds = (T*)sweep_smem;                      // Dinv_hi, Dinv_lo
+    T* Ls = Ds + GD * NB * NB;                   // P[hi rows, lo columns]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(ticket, 1);
@@ -238,39 +328,50 @@ __global__ void __launch_bounds__(AT) k_bwd_sweep(const FrontDesc* __restrict__ 
         const int it = s_item;
         __syncthreads();
         if (it >= n_items) return;
-        const int slot = items[it] >> 16, cb = items[it] & 0xffff;
+        const int slot = items[it] >> 16, hi = items[it] & 0xffff;
         const FrontDesc f = fronts[slot];
-        prefetch_block(Ds, (const T*)f.Dinv + (int64_t)cb * NB * NB);
-        const int c0 = cb * NB, c1 = min(c0 + NB, f.s), cw = c1 - c0;
+        const int nb = min(GD, hi + 1), lo = hi - nb + 1;
         const T* P = (const T*)f.P;
         A* v = (A*)f.vec;
-        A acc[PASSES][VW];
+        const int c0 = lo * NB, c1 = min((hi + 1) * NB, f.s), cw = c1 - c0;
+        const int whi = min(NB, f.s - hi * NB);
+        prefetch_blocks(Ds, (const T*)f.Dinv + (int64_t)hi * NB * NB, 1);
+        if (GD > 1 && nb > 1) {
+            prefetch_blocks(Ds + NB * NB, (const T*)f.Dinv + (int64_t)lo * NB * NB, 1);
+            prefetch_rows(Ls, P + (int64_t)hi * NB * f.ldp + lo * NB, f.ldp, whi);
+        }
+        cp_async_commit();
+        A acc[GD][PASSES][VW];
 #pragma unroll
-        for (int ps = 0; ps < PASSES; ++ps)
+        for (int g = 0; g < GD; ++g)
 #pragma unroll
-            for (int e = 0; e < VW; ++e) acc[ps][e] = 0;
+            for (int ps = 0; ps < PASSES; ++ps)
+#pragma unroll
+                for (int e = 0; e < VW; ++e) acc[g][ps][e] = 0;
         int seen = 0;
         const int n_groups_B = (f.b + NB - 1) / NB;
-        const int n_groups = n_groups_B + (f.nd - 1 - cb);
-        for (int g = 0; g < n_groups; ++g) {
+        const int n_groups = n_groups_B + (f.nd - 1 - hi);
+        for (int gr = 0; gr < n_groups; ++gr) {
             int g0, g1, need = 0;
-            if (g < n_groups_B) {
-                g0 = f.s + (n_groups_B - 1 - g) * NB; g1 = min(g0 + NB, f.N);
+            if (gr < n_groups_B) {
+                g0 = f.s + (n_groups_B - 1 - gr) * NB; g1 = min(g0 + NB, f.N);
             } else {
-                const int rb = f.nd - 1 - (g - n_groups_B);      // I row block > cb
+                const int rb = f.nd - 1 - (gr - n_groups_B);     // I row block > hi
                 need = f.nd - rb;                                  // blocks finished from the top
                 g0 = rb * NB; g1 = min(g0 + NB, f.s);
             }
             for (int base = g0; base < g1; base += AW * RB) {
-                V l[RB][PASSES];
+                V l[RB][GD][PASSES];
 #pragma unroll
                 for (int u = 0; u < RB; ++u) {
                     const int row = base + warp + AW * u;
 #pragma unroll
-                    for (int ps = 0; ps < PASSES; ++ps) {
-                        const int cl = ps * 32 * VW + lane * VW;
-                        l[u][ps] = (row < g1 && cl < cw) ? __ldg((const V*)(P + (int64_t)row * f.ldp + c0 + cl)) : V{};
-                    }
+                    for (int g = 0; g < GD; ++g)
+#pragma unroll
+                        for (int ps = 0; ps < PASSES; ++ps) {
+                            const int cl = g * NB + ps * 32 * VW + lane * VW;
+                            l[u][g][ps] = (row < g1 && cl < cw) ? __ldg((const V*)(P + (int64_t)row * f.ldp + c0 + cl)) : V{};
+                        }
                 }
                 if (base == g0 && seen < need) seen = wait_flag(&f.flag[1], need, err, &s_flag);
                 A x[RB];
@@ -282,54 +383,94 @@ __global__ void __launch_bounds__(AT) k_bwd_sweep(const FrontDesc* __restrict__ 
 #pragma unroll
                 for (int u = 0; u < RB; ++u)
 #pragma unroll
-                    for (int ps = 0; ps < PASSES; ++ps)
+                    for (int g = 0; g < GD; ++g)
 #pragma unroll
-                        for (int e = 0; e < VW; ++e) acc[ps][e] += (A)vget(l[u][ps], e) * x[u];
+                        for (int ps = 0; ps < PASSES; ++ps)
+#pragma unroll
+                            for (int e = 0; e < VW; ++e) acc[g][ps][e] += (A)vget(l[u][g][ps], e) * x[u];
             }
         }
 #pragma unroll
-        for (int ps = 0; ps < PASSES; ++ps)
+        for (int g = 0; g < GD; ++g)
 #pragma unroll
-            for (int e = 0; e < VW; ++e) s_red[warp][ps * 32 * VW + lane * VW + e] = acc[ps][e];
+            for (int ps = 0; ps < PASSES; ++ps)
+#pragma unroll
+                for (int e = 0; e < VW; ++e) s_red[warp][g * NB + ps * 32 * VW + lane * VW + e] = acc[g][ps][e];
         __syncthreads();
-        for (int c = threadIdx.x; c < cw; c += AT) {
+        for (int c = threadIdx.x; c < GD * NB; c += AT) {
             A sum = 0;
 #pragma unroll
             for (int w = 0; w < AW; ++w) sum += s_red[w][c];
-            s_t[c] = ld_cg(v + c0 + c) - sum;
+            s_t[c] = c < cw ? ld_cg(v + c0 + c) - sum : (A)0;
         }
         cp_async_wait();
         __syncthreads();
-        // x = Dinv^T t : x_c = sum_{r >= c} Dinv[r][c] t_r  (lanes over columns, warps over rows)
-        {
-            A part[PASSES][VW];
+        // blocks from the highest: x_g = Dinv_g^T t_g (lanes over columns, warps over rows)
+        for (int k = 0; k < nb; ++k) {
+            const int g = nb - 1 - k;                    // position of the block inside the group
+            const int w = min(NB, cw - g * NB);
+            const T* D = Ds + k * NB * NB;               // Dinv_hi first, then Dinv_lo
+            if (k > 0) {
+                // t_lo -= P[hi rows, lo columns]^T x_hi
+                A part[PASSES][VW];
 #pragma unroll
-            for (int ps = 0; ps < PASSES; ++ps)
+                for (int ps = 0; ps < PASSES; ++ps)
 #pragma unroll
-                for (int e = 0; e < VW; ++e) part[ps][e] = 0;
-            for (int rr = warp; rr < cw; rr += AW) {
-                const A tr = s_t[rr];
+                    for (int e = 0; e < VW; ++e) part[ps][e] = 0;
+                for (int rr = warp; rr < whi; rr += AW) {
+                    const A xr = s_x[rr];
 #pragma unroll
-                for (int ps = 0; ps < PASSES; ++ps) {
-                    const V d = *(const V*)(Ds + rr * NB + ps * 32 * VW + lane * VW);
+                    for (int ps = 0; ps < PASSES; ++ps) {
+                        const V d = *(const V*)(Ls + rr * NB + ps * 32 * VW + lane * VW);
 #pragma unroll
-                    for (int e = 0; e < VW; ++e) part[ps][e] += (A)vget(d, e) * tr;
+                        for (int e = 0; e < VW; ++e) part[ps][e] += (A)vget(d, e) * xr;
+                    }
                 }
+#pragma unroll
+                for (int ps = 0; ps < PASSES; ++ps)
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) s_red[warp][ps * 32 * VW + lane * VW + e] = part[ps][e];
+                __syncthreads();
+                for (int c = threadIdx.x; c < w; c += AT) {
+                    A sum = 0;
+#pragma unroll
+                    for (int q = 0; q < AW; ++q) sum += s_red[q][c];
+                    s_t[g * NB + c] -= sum;
+                }
+                __syncthreads();
             }
+            {
+                A part[PASSES][VW];
 #pragma unroll
-            for (int ps = 0; ps < PASSES; ++ps)
+                for (int ps = 0; ps < PASSES; ++ps)
 #pragma unroll
-                for (int e = 0; e < VW; ++e) s_red[warp][ps * 32 * VW + lane * VW + e] = part[ps][e];
+                    for (int e = 0; e < VW; ++e) part[ps][e] = 0;
+                for (int rr = warp; rr < w; rr += AW) {
+                    const A tr = s_t[g * NB + rr];
+#pragma unroll
+                    for (int ps = 0; ps < PASSES; ++ps) {
+                        const V d = *(const V*)(D + rr * NB + ps * 32 * VW + lane * VW);
+#pragma unroll
+                        for (int e = 0; e < VW; ++e) part[ps][e] += (A)vget(d, e) * tr;
+                    }
+                }
+#pragma unroll
+                for (int ps = 0; ps < PASSES; ++ps)
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) s_red[warp][ps * 32 * VW + lane * VW + e] = part[ps][e];
+            }
+            __syncthreads();
+            for (int c = threadIdx.x; c < w; c += AT) {
+                A sum = 0;
+#pragma unroll
+                for (int q = 0; q < AW; ++q) sum += s_red[q][c];
+                __stcg(v + c0 + g * NB + c, sum);
+                z[f.I[c0 + g * NB + c]] = (double)sum;
+                s_x[c] = sum;
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        for (int c = threadIdx.x; c < cw; c += AT) {
-            A sum = 0;
-#pragma unroll
-            for (int w = 0; w < AW; ++w) sum += s_red[w][c];
-            __stcg(v + c0 + c, sum);
-            z[f.I[c0 + c]] = (double)sum;
-        }
-        publish_flag(&f.flag[1], f.nd - cb);
+        publish_flag(&f.flag[1], f.nd - lo, true);
         __syncthreads();
     }
 }
@@ -340,22 +481,46 @@ double level_factor_bytes(const Level& L) {
     return e * elem_bytes(L.prec);
 }
 
+// Dynamic shared memory of the sweep kernels: GD inverted diagonal blocks plus, for
+// GD = 2, one factor block.
+template <typename T, int GD> constexpr int sweep_dsm() { return (GD + (GD > 1 ? 1 : 0)) * NB * NB * (int)sizeof(T); }
+
 template <typename T, typename A>
 int sweep_smem_setup() {
     static bool done = false;
-    const int bytes = NB * NB * (int)sizeof(T);
     if (!done) {
-        RSD_CUDA_TRY(cudaFuncSetAttribute(k_fwd_sweep<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-        RSD_CUDA_TRY(cudaFuncSetAttribute(k_bwd_sweep<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        RSD_CUDA_TRY(cudaFuncSetAttribute(k_fwd_sweep<T, A, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sweep_dsm<T, 1>()));
+        RSD_CUDA_TRY(cudaFuncSetAttribute(k_bwd_sweep<T, A, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sweep_dsm<T, 1>()));
+        if constexpr (sizeof(T) == 4) {
+            RSD_CUDA_TRY(cudaFuncSetAttribute(k_fwd_sweep<T, A, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sweep_dsm<T, 2>()));
+            RSD_CUDA_TRY(cudaFuncSetAttribute(k_bwd_sweep<T, A, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sweep_dsm<T, 2>()));
+        }
         done = true;
     }
     return RSD_OK;
 }
 
+// Launch the upward / downward sweep kernel with the level's group size.
+template <typename T, typename A>
+void launch_fwd(int gd, int grid, cudaStream_t st, const FrontDesc* fr, const int* items, int n, int* tk, int* err) {
+    if constexpr (sizeof(T) == 4) {
+        if (gd == 2) { k_fwd_sweep<T, A, 2><<<grid, AT, sweep_dsm<T, 2>(), st>>>(fr, items, n, tk, err); return; }
+    }
+    k_fwd_sweep<T, A, 1><<<grid, AT, sweep_dsm<T, 1>(), st>>>(fr, items, n, tk, err);
+}
+
+template <typename T, typename A>
+void launch_bwd(int gd, int grid, cudaStream_t st, const FrontDesc* fr, const int* items, int n, int* tk, int* err,
+                double* z) {
+    if constexpr (sizeof(T) == 4) {
+        if (gd == 2) { k_bwd_sweep<T, A, 2><<<grid, AT, sweep_dsm<T, 2>(), st>>>(fr, items, n, tk, err, z); return; }
+    }
+    k_bwd_sweep<T, A, 1><<<grid, AT, sweep_dsm<T, 1>(), st>>>(fr, items, n, tk, err, z);
+}
+
 template <typename T, typename A>
 int sweep_level(Handle& h, int li, bool forward, const double* r, double* z, int tk) {
     RSD_TRY((sweep_smem_setup<T, A>()));
-    const int dsm = NB * NB * (int)sizeof(T);
     Level& L = h.levels[li];
     const int nf = (int)L.fronts.size();
     double gbytes = 0;
@@ -364,19 +529,22 @@ int sweep_level(Handle& h, int li, bool forward, const double* r, double* z, int
     const int grid = std::max(1, std::min(forward ? L.n_fwd_items : L.n_bwd_items, h.num_sms * 4));
     if (forward) {
         const int gi = prof_begin(h, K_GATHER);
+        // split each front into ranges of ~2048 positions when there are few fronts
+        const dim3 gg((unsigned)nf, (unsigned)std::max(1, std::min(64, std::min((L.max_N + 2047) / 2048,
+                                                                                   (2 * h.num_sms + nf - 1) / nf))));
         if (li + 1 < (int)h.levels.size()) {
             const Level& Lc = h.levels[li + 1];
-            if (is_fp64(Lc.prec)) k_fwd_gather<A, double><<<nf, 256, 0, h.stream>>>(L.d_fronts, Lc.d_fronts, L.d_child_slots, r);
-            else k_fwd_gather<A, float><<<nf, 256, 0, h.stream>>>(L.d_fronts, Lc.d_fronts, L.d_child_slots, r);
+            if (is_fp64(Lc.prec)) k_fwd_gather<A, double><<<gg, 256, 0, h.stream>>>(L.d_fronts, Lc.d_fronts, L.d_child_slots, r);
+            else k_fwd_gather<A, float><<<gg, 256, 0, h.stream>>>(L.d_fronts, Lc.d_fronts, L.d_child_slots, r);
         } else {
-            k_fwd_gather<A, A><<<nf, 256, 0, h.stream>>>(L.d_fronts, L.d_fronts, L.d_child_slots, r);
+            k_fwd_gather<A, A><<<gg, 256, 0, h.stream>>>(L.d_fronts, L.d_fronts, L.d_child_slots, r);
         }
         count_launch();
         prof_end(h, gi, 0.0, gbytes);
         RSD_CUDA_TRY(cudaGetLastError());
         if (L.n_fwd_items) {
             const int pi = prof_begin(h, K_FWD);
-            k_fwd_sweep<T, A><<<grid, AT, dsm, h.stream>>>(L.d_fronts, L.d_fwd_items, L.n_fwd_items, h.d_ticket + tk, h.d_err);
+            launch_fwd<T, A>(sweep_group(L), grid, h.stream, L.d_fronts, L.d_fwd_items, L.n_fwd_items, h.d_ticket + tk, h.d_err);
             count_launch();
             prof_end(h, pi, fbytes / sizeof(T) * 2.0, fbytes);
         }
@@ -388,7 +556,7 @@ int sweep_level(Handle& h, int li, bool forward, const double* r, double* z, int
         RSD_CUDA_TRY(cudaGetLastError());
         if (L.n_bwd_items) {
             const int pi = prof_begin(h, K_BWD);
-            k_bwd_sweep<T, A><<<grid, AT, dsm, h.stream>>>(L.d_fronts, L.d_bwd_items, L.n_bwd_items, h.d_ticket + tk, h.d_err, z);
+            launch_bwd<T, A>(sweep_group(L), grid, h.stream, L.d_fronts, L.d_bwd_items, L.n_bwd_items, h.d_ticket + tk, h.d_err, z);
             count_launch();
             prof_end(h, pi, fbytes / sizeof(T) * 2.0, fbytes);
         }
@@ -437,7 +605,6 @@ template <typename T, typename A>
 int sweep_level_static(Handle& h, int li, bool forward, const double* r, double* z, int* ticket,
                        FrontDesc* const* lvl_fronts) {
     RSD_TRY((sweep_smem_setup<T, A>()));
-    const int dsm = NB * NB * (int)sizeof(T);
     Level& L = h.levels[li];
     const int nf = (int)L.fronts.size();
     FrontDesc* fr = lvl_fronts[li];
@@ -453,7 +620,7 @@ int sweep_level_static(Handle& h, int li, bool forward, const double* r, double*
         count_launch();
         RSD_CUDA_TRY(cudaGetLastError());
         if (L.n_fwd_items) {
-            k_fwd_sweep<T, A><<<grid, AT, dsm, h.stream>>>(fr, L.d_fwd_items, L.n_fwd_items, ticket, h.d_err);
+            launch_fwd<T, A>(sweep_group(L), grid, h.stream, fr, L.d_fwd_items, L.n_fwd_items, ticket, h.d_err);
             count_launch();
         }
     } else {
@@ -461,7 +628,7 @@ int sweep_level_static(Handle& h, int li, bool forward, const double* r, double*
         count_launch();
         RSD_CUDA_TRY(cudaGetLastError());
         if (L.n_bwd_items) {
-            k_bwd_sweep<T, A><<<grid, AT, dsm, h.stream>>>(fr, L.d_bwd_items, L.n_bwd_items, ticket, h.d_err, z);
+            launch_bwd<T, A>(sweep_group(L), grid, h.stream, fr, L.d_bwd_items, L.n_bwd_items, ticket, h.d_err, z);
             count_launch();
         }
     }
@@ -539,7 +706,6 @@ int sweep_with(Handle& h, int li, bool forward, const FrontDesc* fronts, const i
     const int nf = (int)L.fronts.size();
     const int grid = std::max(1, std::min(n_items, h.num_sms * 4));
     const bool f64 = is_fp64(L.prec);
-    const int dsm = NB * NB * (f64 ? 8 : 4);
     if (f64) { RSD_TRY((sweep_smem_setup<double, double>())); } else { RSD_TRY((sweep_smem_setup<float, float>())); }
     if (forward) {
         if (f64) k_fwd_gather<double, double><<<nf, 256, 0, h.stream>>>(fronts, fronts, L.d_child_slots, in);
@@ -547,13 +713,13 @@ int sweep_with(Handle& h, int li, bool forward, const FrontDesc* fronts, const i
         count_launch();
         RSD_CUDA_TRY(cudaGetLastError());
         if (n_items) {
-            if (f64) k_fwd_sweep<double, double><<<grid, AT, dsm, h.stream>>>(fronts, items, n_items, ticket, h.d_err);
-            else k_fwd_sweep<float, float><<<grid, AT, dsm, h.stream>>>(fronts, items, n_items, ticket, h.d_err);
+            if (f64) launch_fwd<double, double>(sweep_group(L), grid, h.stream, fronts, items, n_items, ticket, h.d_err);
+            else launch_fwd<float, float>(sweep_group(L), grid, h.stream, fronts, items, n_items, ticket, h.d_err);
             count_launch();
         }
     } else if (n_items) {
-        if (f64) k_bwd_sweep<double, double><<<grid, AT, dsm, h.stream>>>(fronts, items, n_items, ticket, h.d_err, out);
-        else k_bwd_sweep<float, float><<<grid, AT, dsm, h.stream>>>(fronts, items, n_items, ticket, h.d_err, out);
+        if (f64) launch_bwd<double, double>(sweep_group(L), grid, h.stream, fronts, items, n_items, ticket, h.d_err, out);
+        else launch_bwd<float, float>(sweep_group(L), grid, h.stream, fronts, items, n_items, ticket, h.d_err, out);
         count_launch();
     }
     RSD_CUDA_TRY(cudaGetLastError());

@@ -37,6 +37,7 @@ void set_last_error(const std::string& msg);
 inline int elem_bytes(int prec) { return prec == RSD_PREC_FP64 ? 8 : 4; }
 inline bool is_fp64(int prec) { return prec == RSD_PREC_FP64; }
 
+
 // One tree node's dense front and factor, as the kernels see it.
 // P is row-major N x ldp with N = s + b: rows 0..s-1 hold L (lower triangle; the
 // diagonal NB x NB blocks are also kept inverted in Dinv), rows s..N-1 hold X = K_BI L^-T.
@@ -116,6 +117,12 @@ struct Level {
     int* d_fwd_items_solve = nullptr;
     int n_fwd_items_solve = 0;
 };
+
+// Diagonal blocks per substitution-sweep item: a single-front FP32 level (a root) pairs
+// its blocks, halving the hand-offs of its long dependency chain; levels with many
+// fronts keep one block per item, whose smaller footprint lets more CTAs stream the
+// factor at once (an FP64 pair would not fit in shared memory).
+inline int sweep_group(const Level& L) { return (!is_fp64(L.prec) && L.fronts.size() == 1) ? 2 : 1; }
 
 // Per tree node: where its front lives (paper-mode scatter of leaf updates).
 struct NodeRef {
