@@ -75,24 +75,102 @@ __global__ void k_scatter_K(const FrontDesc* __restrict__ fronts, const int64_t*
 
 // Extend-add of child number `ci` of every front of the level: U_c (lower) is added at
 // the parent positions ea_c, into P (column inside I) or U (both in B).  One launch per
-// child index keeps the accumulation order fixed and race-free.
+// child index keeps the accumulation order fixed and race-free (within one child the
+// targets of distinct entries are distinct: ea_c is injective).
+//
+// U_c is taken in 32 x 32 tiles; a work unit is a run of up to EA_CH tiles of one tile
+// row, walked by one CTA.  Entry (i, j), j <= i, lands at
+// (max(p_i, p_j), min(p_i, p_j)); the entries with p_j <= p_i are written by a warp per tile
+// row (target row p_i, columns p_j increasing along the warp), the others, through a
+// shared-memory transpose, by a warp per tile column (target row p_j, columns p_i), so
+// both kinds of update run along parent rows (p restricted to the child's DOFs inside
+// I_p or inside B_p is increasing).  Each thread issues all reads of its 8 targets before
+// writing, and the next tile is loaded while the current one is added.
+constexpr int EA_T = 32;
+constexpr int EA_CH = 16;
+
 template <typename Tc, typename Tp>
-__global__ void k_extend_add(const FrontDesc* __restrict__ parents, const FrontDesc* __restrict__ kids,
-                             const int* __restrict__ child_slots, int ci) {
+__global__ void __launch_bounds__(256, 4) k_extend_add(const FrontDesc* __restrict__ parents, const FrontDesc* __restrict__ kids,
+                                                    const int* __restrict__ child_slots, int ci) {
+    __shared__ Tp tile[2][EA_T][EA_T + 1];
     const FrontDesc fp = parents[blockIdx.y];
     if (ci >= fp.child_count) return;
     const FrontDesc fc = kids[child_slots[fp.child_begin + ci]];
     const Tc* U = (const Tc*)fc.U;
     Tp* P = (Tp*)fp.P;
     Tp* Up = (Tp*)fp.U;
-    for (int i = blockIdx.x; i < fc.b; i += gridDim.x) {
-        const int pi = fc.ea[i];
-        for (int j = threadIdx.x; j <= i; j += blockDim.x) {
-            const int pj = fc.ea[j];
-            const Tp v = (Tp)U[(int64_t)i * fc.ldu + j];
-            const int r = max(pi, pj), c = min(pi, pj);
-            if (c < fp.s) P[(int64_t)r * fp.ldp + c] += v;
-            else Up[(int64_t)(r - fp.s) * fp.ldu + (c - fp.s)] += v;
+    const int b = fc.b;
+    const int nt = (b + EA_T - 1) / EA_T;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    auto at = [&](int r, int c) -> Tp* {
+        return c < fp.s ? P + (int64_t)r * fp.ldp + c : Up + (int64_t)(r - fp.s) * fp.ldu + (c - fp.s);
+    };
+    int buf = 0;
+    const int nch = (nt + EA_CH - 1) / EA_CH;
+    for (int64_t unit = blockIdx.x; unit < (int64_t)nt * nch; unit += gridDim.x) {
+        const int I = (int)(unit / nch), Jb = (int)(unit % nch) * EA_CH;
+        if (Jb > I) continue;
+        const int Je = min(I, Jb + EA_CH - 1);
+        {
+            const int i0 = I * EA_T;
+            const int pi_lane = i0 + lane < b ? fc.ea[i0 + lane] : -1;      // row i0 + lane
+            int pi_q[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + warp + 8 * u;
+                pi_q[u] = i < b ? fc.ea[i] : -1;
+            }
+            // tile (I, J): this thread's entries (i0 + warp + 8u, j0 + lane)
+            Tp cur[4];
+            int pj_lane, pj_q[4];
+            auto load = [&](int J, Tp* v, int& pl, int* pq) {
+                const int j0 = J * EA_T;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = i0 + warp + 8 * u, j = j0 + lane;
+                    v[u] = (i < b && j <= i) ? (Tp)U[(int64_t)i * fc.ldu + j] : (Tp)0;
+                    pq[u] = j0 + warp + 8 * u < b ? fc.ea[j0 + warp + 8 * u] : -1;
+                }
+                pl = j0 + lane < b ? fc.ea[j0 + lane] : -1;
+            };
+            load(Jb, cur, pj_lane, pj_q);
+            for (int J = Jb; J <= Je; ++J) {
+                const int j0 = J * EA_T;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) tile[buf][warp + 8 * u][lane] = cur[u];
+                __syncthreads();
+                Tp nxt[4];
+                int nl = -1, nq[4] = {-1, -1, -1, -1};
+                if (J < Je) load(J + 1, nxt, nl, nq);
+                Tp* dst[8];
+                Tp val[8];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int q = warp + 8 * u;
+                    {                                      // rows: p_j <= p_i
+                        const int i = i0 + q, j = j0 + lane;
+                        const bool ok = i < b && j <= i && pj_lane <= pi_q[u];
+                        dst[u] = ok ? at(pi_q[u], pj_lane) : nullptr;
+                        val[u] = cur[u];
+                    }
+                    {                                      // columns: p_j > p_i
+                        const int i = i0 + lane, j = j0 + q;
+                        const bool ok = i < b && j <= i && pj_q[u] > pi_lane;
+                        dst[4 + u] = ok ? at(pj_q[u], pi_lane) : nullptr;
+                        val[4 + u] = tile[buf][lane][q];
+                    }
+                }
+                Tp old[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) old[u] = dst[u] ? *dst[u] : (Tp)0;
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (dst[u]) *dst[u] = old[u] + val[u];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) { cur[u] = nxt[u]; pj_q[u] = nq[u]; }
+                pj_lane = nl;
+                buf ^= 1;
+            }
         }
     }
 }
@@ -249,15 +327,17 @@ __global__ void __launch_bounds__(256) k_potrf_diag(const FrontDesc* __restrict_
             T d = col[j];
             if (!(d > (T)0)) { bad = 1; d = (T)1; }
             const T inv = rsqrt_t(d), inv2 = inv * inv;
+            // rows and columns before block jb see a zero column entry, and entries right
+            // of the diagonal block (b > a) are never read: update the rest only
             T ci[8], ck[8];
 #pragma unroll
-            for (int a = 0; a < 8; ++a) ci[a] = col[16 * a + tr] * inv2;
+            for (int a = jb; a < 8; ++a) ci[a] = col[16 * a + tr] * inv2;
 #pragma unroll
-            for (int b = 0; b < 8; ++b) ck[b] = col[16 * b + tc];
+            for (int b = jb; b < 8; ++b) ck[b] = col[16 * b + tc];
 #pragma unroll
-            for (int a = 0; a < 8; ++a)
+            for (int a = jb; a < 8; ++a)
 #pragma unroll
-                for (int b = 0; b < 8; ++b) e[a][b] -= ci[a] * ck[b];
+                for (int b = jb; b <= a; ++b) e[a][b] -= ci[a] * ck[b];
             if (tc == jj) {
 #pragma unroll
                 for (int a = 0; a < 8; ++a) {
@@ -300,15 +380,17 @@ __global__ void __launch_bounds__(256) k_potrf_diag(const FrontDesc* __restrict_
                 }
             }
             __syncthreads();
+            // X[i][c] -= L[i][r] X[r][c] touches rows i > r (blocks a >= rb) and columns
+            // c <= r (blocks b <= rb) only
             T li[8], xr[8];
 #pragma unroll
-            for (int a = 0; a < 8; ++a) li[a] = (16 * a + tr > r) ? A[(16 * a + tr) * DLD + r] : (T)0;
+            for (int a = rb; a < 8; ++a) li[a] = (16 * a + tr > r) ? A[(16 * a + tr) * DLD + r] : (T)0;
 #pragma unroll
-            for (int b = 0; b < 8; ++b) xr[b] = row[16 * b + tc];
+            for (int b = 0; b <= rb; ++b) xr[b] = row[16 * b + tc];
 #pragma unroll
-            for (int a = 0; a < 8; ++a)
+            for (int a = rb; a < 8; ++a)
 #pragma unroll
-                for (int b = 0; b < 8; ++b) e[a][b] -= li[a] * xr[b];
+                for (int b = 0; b <= rb; ++b) e[a][b] -= li[a] * xr[b];
         }
     }
     T* D = (T*)f.Dinv + (int64_t)(k / NB) * NB * NB;
@@ -454,7 +536,11 @@ int launch_extend_add(Handle& h, int li) {
     Level& Lc = h.levels[li + 1];
     if (Lp.fronts.empty() || Lc.fronts.empty()) return RSD_OK;
     const bool p64 = is_fp64(Lp.prec), c64 = is_fp64(Lc.prec);
-    dim3 grid((unsigned)std::max(1, std::min(4096, Lc.max_b)), (unsigned)Lp.fronts.size());
+    const int64_t ntl = (Lc.max_b + EA_T - 1) / EA_T;
+    const int64_t units = ntl * ((ntl + EA_CH - 1) / EA_CH);
+    const int per_parent = (int)std::max<int64_t>(1, std::min<int64_t>(units,
+                                                                       (8LL * h.num_sms + (int64_t)Lp.fronts.size() - 1) / (int64_t)Lp.fronts.size()));
+    dim3 grid((unsigned)per_parent, (unsigned)Lp.fronts.size());
     double ea_bytes = 0;
     for (auto& f : Lc.fronts) ea_bytes += 0.5 * f.b * (f.b + 1.0) * (elem_bytes(Lc.prec) + 2.0 * elem_bytes(Lp.prec));
     ea_bytes /= std::max(1, Lp.max_children);

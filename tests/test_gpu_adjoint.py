@@ -61,7 +61,7 @@ def _gpu_grad(rsd, n, depth, m, b, u_obs, precs, tol=1e-12):
     u = rsd.diffusion_solve(mt, bt, n, depth, tol=tol, precs=precs)
     L = 0.5 * ((u - torch.tensor(u_obs, device="cuda")) ** 2).sum()
     L.backward()
-    return float(L), u.detach().cpu().numpy(), mt.grad.cpu().numpy(), bt.grad.cpu().numpy()
+    return float(L.detach()), u.detach().cpu().numpy(), mt.grad.cpu().numpy(), bt.grad.cpu().numpy()
 
 
 def _gpu_loss(rsd, n, depth, m, b, u_obs, precs, tol=1e-12):
