@@ -235,7 +235,7 @@ def main() -> None:
             if isinstance(v, dict) and "ms" in v:
                 for f in ("launches", "ms", "flops", "bytes"):
                     a[k][f] += v[f]
-            elif k == "host_analysis_ms":
+            elif k in ("host_analysis_ms", "host_issue_ms"):
                 a[k] += v
             elif k == "host_parts_ms":
                 a[k] = {q: a[k][q] + v[q] for q in v}
@@ -323,13 +323,13 @@ def main() -> None:
     agg = {}
     for p in profs:
         for k, v in p.items():
-            if k in ("host_analysis_ms", "host_parts_ms"):
+            if k in ("host_analysis_ms", "host_parts_ms", "host_issue_ms"):
                 agg.setdefault(k, []).append(v)
                 continue
             a = agg.setdefault(k, dict(launches=0, ms=0.0, flops=0.0, bytes=0.0))
             for f in ("launches", "ms", "flops", "bytes"):
                 a[f] += v[f]
-    classes = {k: v for k, v in agg.items() if k not in ("host_analysis_ms", "host_parts_ms")}
+    classes = {k: v for k, v in agg.items() if k not in ("host_analysis_ms", "host_parts_ms", "host_issue_ms")}
     dom = max(classes, key=lambda k: classes[k]["ms"])
     d = classes[dom]
     pk, src = peaks()
@@ -379,6 +379,7 @@ def main() -> None:
         "detail": {"iterations": [s["iterations"] for s in stats], "relres": [s["relres"] for s in stats],
                    "ms_by_kernel_class": phase,
                    "host_analysis_ms": statistics.median(agg["host_analysis_ms"]),
+                   "host_issue_ms": statistics.median(agg["host_issue_ms"]),
                    "host_parts_ms": agg["host_parts_ms"][-1],
                    "apply_sweeps_gbs": sw_gbs, "factor_bytes": info["factor_bytes"],
                    "setup_flops": info["setup_flops"], "device_bytes": info["device_bytes"]},

@@ -126,17 +126,21 @@ typedef struct {
     double  host_parts_ms[6];    /* of which: structure copy to the host, ownership sort,
                                     Eq. 3.1 check, interface sets, extend-add maps, and the
                                     memory plan with its uploads                          */
+    double  host_issue_ms;       /* host time spent issuing the numeric setup's launches
+                                    (the device may still be working when it ends)        */
 } rsd_profile_t;
 
 /* one profiled launch (rsd_profile_trace): its class (as above), the stream it ran on
  * (0 = the caller's stream, 1 = the library's look-ahead stream used while factoring
- * levels with few fronts), start and end in ms from the first recorded launch, and its
- * algorithmic flops and bytes.                                                        */
+ * levels with few fronts), device start and end in ms from the first recorded launch,
+ * its algorithmic flops and bytes, and when the host issued it (ms from the first
+ * record's issue; host and device times share no origin).                             */
 typedef struct {
     int32_t cls;
     int32_t stream;
     double  start_ms, end_ms;
     double  flops, bytes;
+    double  issue_ms;
 } rsd_trace_rec;
 
 typedef struct rsd_handle_s* rsd_handle;

@@ -212,6 +212,7 @@ class RSD:
                for i, name in enumerate(_lib.PROFILE_CLASSES)}
         out["host_analysis_ms"] = p.host_analysis_ms
         out["host_parts_ms"] = dict(zip(["copy", "sort", "check", "sets", "maps", "plan"], list(p.host_parts_ms)))
+        out["host_issue_ms"] = p.host_issue_ms
         return out
 
     def trace(self) -> list[dict]:
@@ -223,7 +224,7 @@ class RSD:
         recs = (_lib.rsd_trace_rec * max(n.value, 1))()
         check(lib.rsd_profile_trace(self._h, recs, n.value, C.byref(n)), "rsd_profile_trace")
         return [dict(cls=_lib.PROFILE_CLASSES[r.cls], stream=r.stream, start_ms=r.start_ms, end_ms=r.end_ms,
-                     flops=r.flops, bytes=r.bytes) for r in recs[: n.value]]
+                     flops=r.flops, bytes=r.bytes, issue_ms=r.issue_ms) for r in recs[: n.value]]
 
     def info(self) -> dict:
         inf = _lib.rsd_info_t()

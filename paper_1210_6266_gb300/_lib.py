@@ -74,12 +74,13 @@ PROFILE_CLASSES = ["assemble", "extend_add", "gemm_tcgen05", "gemm_simt", "diag_
 class rsd_profile_t(C.Structure):
     _fields_ = [("launches", C.c_int64 * 10), ("ms", C.c_double * 10), ("flops", C.c_double * 10),
                 ("bytes", C.c_double * 10), ("host_analysis_ms", C.c_double),
-                ("host_parts_ms", C.c_double * 6)]
+                ("host_parts_ms", C.c_double * 6), ("host_issue_ms", C.c_double)]
 
 
 class rsd_trace_rec(C.Structure):
     _fields_ = [("cls", C.c_int32), ("stream", C.c_int32), ("start_ms", C.c_double),
-                ("end_ms", C.c_double), ("flops", C.c_double), ("bytes", C.c_double)]
+                ("end_ms", C.c_double), ("flops", C.c_double), ("bytes", C.c_double),
+                ("issue_ms", C.c_double)]
 
 
 _lib = None

@@ -55,20 +55,21 @@ static char* arena_take(size_t bytes, int dev, size_t* got) {
     return p;
 }
 
+// Pinned staging blocks (64 MB or more), cached across handles: a handle takes blocks
+// as its uploads need them and gives them back when it is destroyed.
 static std::mutex g_pin_mu;
-static char* g_pin_ptr = nullptr;
-static size_t g_pin_bytes = 0;
+static std::vector<std::pair<char*, size_t>> g_pin_free;
 
 static char* pinned_take(size_t bytes, size_t* got) {
     {
         std::lock_guard<std::mutex> lk(g_pin_mu);
-        if (g_pin_ptr && g_pin_bytes >= bytes) {
-            char* p = g_pin_ptr;
-            *got = g_pin_bytes;
-            g_pin_ptr = nullptr;
-            g_pin_bytes = 0;
-            return p;
-        }
+        for (size_t i = 0; i < g_pin_free.size(); ++i)
+            if (g_pin_free[i].second >= bytes) {
+                char* p = g_pin_free[i].first;
+                *got = g_pin_free[i].second;
+                g_pin_free.erase(g_pin_free.begin() + (int64_t)i);
+                return p;
+            }
     }
     char* p = nullptr;
     if (cudaMallocHost((void**)&p, bytes) != cudaSuccess) { cudaGetLastError(); return nullptr; }
@@ -78,10 +79,8 @@ static char* pinned_take(size_t bytes, size_t* got) {
 
 static void pinned_give(char* p, size_t bytes) {
     std::lock_guard<std::mutex> lk(g_pin_mu);
-    if (g_pin_ptr && g_pin_bytes >= bytes) { cudaFreeHost(p); return; }
-    if (g_pin_ptr) cudaFreeHost(g_pin_ptr);
-    g_pin_ptr = p;
-    g_pin_bytes = bytes;
+    if (g_pin_free.size() >= 4) { cudaFreeHost(p); return; }
+    g_pin_free.push_back({p, bytes});
 }
 
 // Second one-slot pinned cache: host copies of a device CSR structure for the analysis.
@@ -116,22 +115,30 @@ static void pinned2_give(char* p, size_t bytes) {
 
 const void* stage_host(Handle& h, const void* src, size_t bytes) {
     const size_t need = (bytes + 255) & ~(size_t)255;
-    if (h.stage_off + need > h.stage_cap) {
-        cudaStreamSynchronize(h.stream);              // every earlier copy has completed
-        if (h.chain) cudaStreamSynchronize(h.chain);
-        h.stage_off = 0;
-        if (need > h.stage_cap) {
-            if (h.stage) pinned_give(h.stage, h.stage_cap);
-            size_t got = 0;
-            h.stage = pinned_take(std::max(need, (size_t)64 << 20), &got);
-            h.stage_cap = h.stage ? got : 0;
-            if (!h.stage) return src;                  // fall back to a pageable (staged) copy
+    for (;;) {
+        if (h.stage_cur < h.stage_blocks.size()) {
+            auto& blk = h.stage_blocks[h.stage_cur];
+            if (h.stage_off + need <= blk.second) break;
+            if (h.stage_cur + 1 < h.stage_blocks.size()) { ++h.stage_cur; h.stage_off = 0; continue; }
         }
+        // every block is in use by copies that may still be pending: add one
+        size_t got = 0;
+        char* p = pinned_take(std::max(need, (size_t)64 << 20), &got);
+        if (!p) return src;                            // fall back to a pageable (staged) copy
+        h.stage_blocks.push_back({p, got});
+        h.stage_cur = h.stage_blocks.size() - 1;
+        h.stage_off = 0;
+        break;
     }
-    char* dst = h.stage + h.stage_off;
+    char* dst = h.stage_blocks[h.stage_cur].first + h.stage_off;
     std::memcpy(dst, src, bytes);
     h.stage_off += need;
     return dst;
+}
+
+void stage_reset(Handle& h) {
+    h.stage_cur = 0;
+    h.stage_off = 0;
 }
 
 static void arena_give(char* p, size_t bytes, int dev) {
@@ -146,7 +153,8 @@ void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 int prof_begin(Handle& h, int cls, cudaStream_t stream) {
     if (!h.prof.on) return -1;
-    Prof::Rec r{cls, 0.0, 0.0, nullptr, nullptr, (h.chain && stream == h.chain) ? 1 : 0};
+    const double host_us = std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now().time_since_epoch()).count();
+    Prof::Rec r{cls, 0.0, 0.0, nullptr, nullptr, (h.chain && stream == h.chain) ? 1 : 0, host_us};
     for (cudaEvent_t* e : {&r.a, &r.b}) {
         if (!h.prof.pool.empty()) { *e = h.prof.pool.back(); h.prof.pool.pop_back(); }
         else if (cudaEventCreate(e) != cudaSuccess) { cudaGetLastError(); return -1; }
@@ -932,11 +940,13 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
     h.prof.host_part[5] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_plan).count();
     // ---- numeric setup, deepest level first ----
     if (!paper) {
+        const auto t_issue = std::chrono::steady_clock::now();
         for (int d = nl - 1; d >= 0; --d) {
             RSD_TRY(launch_assemble_fronts(h, d, h.d_rowptr, h.d_col, h.d_val, d_owner, d_rank, d_tin, d_tout));
             RSD_TRY(launch_extend_add(h, d));
             RSD_TRY(run_factor_level(h, d));
         }
+        h.prof.host_issue_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_issue).count();
     } else {
         // every interface front is K_II plus leaf updates: assemble all, factor the
         // leaves, scatter their updates into S~, then factor the interfaces
@@ -947,6 +957,7 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
         for (int d = nl - 2; d >= 0; --d) RSD_TRY(run_factor_level(h, d));
     }
     RSD_CUDA_TRY(cudaStreamSynchronize(st));
+    stage_reset(h);                                   // every staged upload has completed
     int err[ERR_SLOTS];
     RSD_CUDA_TRY(cudaMemcpy(err, h.d_err, sizeof(err), cudaMemcpyDeviceToHost));
     if (err[ERR_NOT_SPD]) {
@@ -992,9 +1003,8 @@ extern "C" void rsd_release_cache(void) {
     }
     {
         std::lock_guard<std::mutex> lk(g_pin_mu);
-        if (g_pin_ptr) cudaFreeHost(g_pin_ptr);
-        g_pin_ptr = nullptr;
-        g_pin_bytes = 0;
+        for (auto& blk : g_pin_free) cudaFreeHost(blk.first);
+        g_pin_free.clear();
     }
     std::lock_guard<std::mutex> lk(g_cache_mu);
     int cur = 0;
@@ -1023,6 +1033,7 @@ extern "C" int rsd_profile(rsd_handle hh, rsd_profile_t* out, int32_t reset) {
     }
     out->host_analysis_ms = h.prof.host_ms + h.prof.host_part[5];
     for (int i = 0; i < 6; ++i) out->host_parts_ms[i] = h.prof.host_part[i];
+    out->host_issue_ms = h.prof.host_issue_ms;
     if (reset) {
         for (auto& r : h.prof.recs) { h.prof.pool.push_back(r.a); h.prof.pool.push_back(r.b); }
         h.prof.recs.clear();
@@ -1041,7 +1052,8 @@ extern "C" int rsd_profile_trace(rsd_handle hh, rsd_trace_rec* out, int64_t cap,
         float t0 = 0, t1 = 0;
         if (cudaEventElapsedTime(&t0, h.prof.recs[0].a, r.a) != cudaSuccess) { cudaGetLastError(); t0 = 0; }
         if (cudaEventElapsedTime(&t1, h.prof.recs[0].a, r.b) != cudaSuccess) { cudaGetLastError(); t1 = 0; }
-        out[i] = rsd_trace_rec{r.cls, r.stream, t0, t1, r.flops, r.bytes};
+        out[i] = rsd_trace_rec{r.cls, r.stream, t0, t1, r.flops, r.bytes,
+                               (r.host_us - h.prof.recs[0].host_us) / 1000.0};
     }
     return RSD_OK;
 }
@@ -1060,7 +1072,7 @@ extern "C" void rsd_destroy(rsd_handle hh) {
     for (auto& r : h.prof.recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : h.prof.pool) cudaEventDestroy(e);
     if (h.arena) arena_give(h.arena, h.arena_capacity, h.device);
-    if (h.stage) pinned_give(h.stage, h.stage_cap);
+    for (auto& blk : h.stage_blocks) pinned_give(blk.first, blk.second);
     if (h.h_scal) cudaFreeHost(h.h_scal);
     delete hh;
 }

@@ -575,15 +575,17 @@ int launch_extend_add(Handle& h, int li) {
 // (many thin, memory-bound GEMMs) by two K = W GEMMs.
 //
 // Levels with few fronts (the root and the level below it) also look ahead: the
-// diagonal-block work (a)-(c) and (e) runs on a high-priority stream (the "chain"),
-// beside the bulk stream (the caller's), which meanwhile applies the part of the NEXT
-// panel's outer update whose K range [0, K0) covers finished panels only; the remaining
-// range [K0, K0+W) runs once panel p is complete.  The bulk persistent GEMM leaves a few
-// SMs to the chain.  Every entry receives the same products in either order; only the
-// outer update's K range is summed in two parts.
+// diagonal-block work runs on a high-priority stream (the "chain") beside the bulk
+// stream (the caller's), and the chain also takes the small steps that link one
+// diagonal block to the next (the last K range of the next block's outer update, and
+// the solve of the next block's rows), so that it never waits for the bulk's large
+// GEMMs except the next panel's long outer update, which the bulk runs while the chain
+// factors.  The bulk persistent GEMM leaves a wave of SMs to the chain.  Every entry
+// receives the same products in either order; only the outer update's K range is
+// summed in two parts, and the rows below a diagonal block are solved in two groups.
 constexpr int LOOKAHEAD_FRONTS = 16;
 constexpr int64_t SCR_MT = 512 * 512, SCR_TT = 512 * 128, SCR_LINV = 512 * 512;
-constexpr int64_t SCR_FRONT = SCR_MT + SCR_TT + SCR_LINV;        // floats per front slot
+constexpr int64_t SCR_FRONT = SCR_MT + SCR_TT + 2 * SCR_LINV;    // floats per front slot (two Linv)
 static_assert(WOUT == 512, "scratch blocks are sized for 512-wide outer panels");
 
 // Mt's diagonal blocks: Mt[j, j] = Dinv_j^T (upper triangular), j < ceil(W / NB).
@@ -604,12 +606,12 @@ __global__ void k_mt_diag(const FrontDesc* __restrict__ fronts, int K0, float* _
 }
 
 // Linv = Mt^T on the W x W block, zero elsewhere in the 512 x 512 slot.
-__global__ void k_linv_transpose(const FrontDesc* __restrict__ fronts, int K0, float* __restrict__ scr) {
+__global__ void k_linv_transpose(const FrontDesc* __restrict__ fronts, int K0, float* __restrict__ scr, int which) {
     const FrontDesc f = fronts[blockIdx.z];
     if (f.s <= K0) return;
     const int W = min(WOUT, f.s - K0);
     const float* Mt = scr + (int64_t)blockIdx.z * SCR_FRONT;
-    float* Li = scr + (int64_t)blockIdx.z * SCR_FRONT + SCR_MT + SCR_TT;
+    float* Li = scr + (int64_t)blockIdx.z * SCR_FRONT + SCR_MT + SCR_TT + which * SCR_LINV;
     __shared__ float t[32][33];
     const int bx = blockIdx.x, by = blockIdx.y;               // 16 x 16 tiles of 32 x 32
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
@@ -640,22 +642,25 @@ static int factor_level_tc(Handle& h, int li, bool lookahead) {
     if (lookahead) RSD_TRY(ensure_chain(h));
     cudaStream_t B = h.stream, Cs = lookahead ? h.chain : h.stream;
     const int cslot = lookahead ? 1 : 0;
-    const int bulk_ctas = lookahead ? h.num_sms - std::min(h.num_sms / 4, nf + 1) : 0;
+    // the bulk persistent GEMM leaves SMs for the chain's diagonal blocks and its small
+    // GEMMs (one wave of them)
+    const int bulk_ctas = lookahead ? h.num_sms - std::min(h.num_sms / 4, std::max(8, 2 * nf)) : 0;
     // per-front scratch: Mt, Tt, Linv (Mt's lower part stays zero)
     float* scr = nullptr;
     RSD_CUDA_TRY(cudaMallocAsync((void**)&scr, sizeof(float) * SCR_FRONT * nf, B));
     RSD_CUDA_TRY(cudaMemsetAsync(scr, 0, sizeof(float) * SCR_FRONT * nf, B));
-    std::vector<float*> mt(nf), tt(nf), lv(nf);
+    std::vector<float*> mt(nf), tt(nf), lv0(nf), lv1(nf);
     for (int i = 0; i < nf; ++i) {
         mt[i] = scr + SCR_FRONT * i;
         tt[i] = mt[i] + SCR_MT;
-        lv[i] = tt[i] + SCR_TT;
+        lv0[i] = tt[i] + SCR_TT;
+        lv1[i] = lv0[i] + SCR_LINV;
     }
     int mbase = 0;
-    RSD_TRY(gemm_tc_scratch_maps(h, mt, tt, lv, B, &mbase));
-    auto map_mt = [&](int i) { return mbase + 3 * i; };
-    auto map_tt = [&](int i) { return mbase + 3 * i + 1; };
-    auto map_lv = [&](int i) { return mbase + 3 * i + 2; };
+    RSD_TRY(gemm_tc_scratch_maps(h, mt, tt, lv0, lv1, B, &mbase));
+    auto map_mt = [&](int i) { return mbase + TC_SCR_MAPS * i; };
+    auto map_tt = [&](int i) { return mbase + TC_SCR_MAPS * i + 1; };
+    auto map_lv = [&](int i, int which) { return mbase + TC_SCR_MAPS * i + 2 + which; };
 
     std::vector<GemmTask> tasks;
     auto wend = [](const FrontDesc& f, int K0) { return std::min(K0 + WOUT, f.s); };
@@ -684,16 +689,16 @@ static int factor_level_tc(Handle& h, int li, bool lookahead) {
         t.a_r0 = r0; t.a_c0 = k; t.b_r0 = (k / NB) * NB; t.b_c0 = 0;
         tasks.push_back(t);
     };
-    // (a0) the panel at K0, all its rows, from the columns [kb, ke)
-    auto add_outer = [&](const FrontDesc& f, int K0, int kb, int ke) {
-        if (f.s <= K0 || ke <= kb) return;
+    // (a0) rows [r0, r1) of the panel at K0 from the columns [kb, ke)
+    auto add_outer = [&](const FrontDesc& f, int K0, int kb, int ke, int r0, int r1) {
+        if (f.s <= K0 || ke <= kb || r1 <= r0) return;
         GemmTask t{};
-        t.A = P(f, K0, kb); t.B = t.A; t.C = P(f, K0, K0);
+        t.A = P(f, r0, kb); t.B = P(f, K0, kb); t.C = P(f, r0, K0);
         t.lda = t.ldb = t.ldc = f.ldp;
-        t.M = f.N - K0; t.N = std::min(WOUT, f.s - K0); t.K = ke - kb;
+        t.M = r1 - r0; t.N = std::min(WOUT, f.s - K0); t.K = ke - kb;
         t.lower = 0; t.beta = 1;
         t.map_a = t.map_b = f.node;
-        t.a_r0 = K0; t.a_c0 = kb; t.b_r0 = K0; t.b_c0 = kb;
+        t.a_r0 = r0; t.a_c0 = kb; t.b_r0 = K0; t.b_c0 = kb;
         tasks.push_back(t);
     };
     auto general = [&](int ma, int a_r0, int a_c0, int mb, int b_r0, int b_c0, void* C, int ldc,
@@ -706,44 +711,40 @@ static int factor_level_tc(Handle& h, int li, bool lookahead) {
         tasks.push_back(t);
     };
 
-    const int np = (L.max_s + WOUT - 1) / WOUT;
-    if (lookahead) RSD_CUDA_TRY(cudaEventRecord(h.ev_ready, B));     // the fronts are assembled
-    for (int p = 0; p < np; ++p) {
-        const int K0 = p * WOUT;
-        // (a0) bulk: this panel's outer update (with look-ahead only its K range
-        //      [K0-W, K0); the rest ran one panel earlier), then release the panel
-        if (p >= 1) {
-            tasks.clear();
-            for (auto& f : L.fronts) add_outer(f, K0, lookahead ? K0 - WOUT : 0, K0);
-            RSD_TRY(gemm_tc_launch(h, li, tasks, 3, B, 0, bulk_ctas));
-        }
-        if (lookahead) {
-            RSD_CUDA_TRY(cudaEventRecord(h.ev_ready, B));
-            RSD_CUDA_TRY(cudaStreamWaitEvent(Cs, h.ev_ready, 0));
-        }
-        // (a)-(c) chain: the diagonal W x W block of every front
+    // (a)-(c) and (e) for the diagonal block of every front at K0, on stream cs; the
+    // block inverse goes to Linv buffer `which`
+    // The level is issued twice: a dry pass in which the GEMM launcher only records each
+    // launch's task and tile lists (and nothing else is launched), then, after one upload
+    // of everything recorded, the real pass.  Per-launch uploads would stall the issuing
+    // thread behind the streams' queues and serialise copies between the chain's kernels.
+    bool dry = false;
+    auto factor_block = [&](int K0, int which, cudaStream_t cs, int slot) -> int {
         for (int j = 0; j < WOUT / NB; ++j) {
             const int k = K0 + j * NB;
             if (k >= L.max_s) break;
             tasks.clear();
             for (auto& f : L.fronts) add_update(f, k, K0, k, wend(f, K0));
-            RSD_TRY(gemm_tc_launch(h, li, tasks, 0, Cs, cslot));
+            RSD_TRY(gemm_tc_launch(h, li, tasks, 0, cs, slot));
             double pf = 0, pb = 0;
             for (auto& f : L.fronts)
                 if (f.s > k) { const double w = std::min(NB, f.s - k); pf += 2.0 * w * w * w / 3.0; pb += (2.0 * w * w + NB * NB) * es; }
-            const int ppi = prof_begin(h, K_POTRF, Cs);
-            k_potrf_diag<float><<<(unsigned)nf, 256, potrf_smem, Cs>>>(L.d_fronts, k, h.d_err, 1);
-            count_launch();
-            prof_end(h, ppi, pf, pb, Cs);
-            RSD_CUDA_TRY(cudaGetLastError());
+            if (!dry) {
+                const int ppi = prof_begin(h, K_POTRF, cs);
+                k_potrf_diag<float><<<(unsigned)nf, 256, potrf_smem, cs>>>(L.d_fronts, k, h.d_err, 1);
+                count_launch();
+                prof_end(h, ppi, pf, pb, cs);
+                RSD_CUDA_TRY(cudaGetLastError());
+            }
             tasks.clear();
             for (auto& f : L.fronts) add_solve(f, k, k + std::min(NB, std::max(0, f.s - k)), wend(f, K0));
-            RSD_TRY(gemm_tc_launch(h, li, tasks, 1, Cs, cslot));
+            RSD_TRY(gemm_tc_launch(h, li, tasks, 1, cs, slot));
         }
-        // (e) chain: Mt = L_pp^-T, then Linv = Mt^T
-        k_mt_diag<<<dim3(16, WOUT / NB, (unsigned)nf), dim3(32, 8), 0, Cs>>>(L.d_fronts, K0, scr);
-        count_launch();
-        RSD_CUDA_TRY(cudaGetLastError());
+        // (e) Mt = L_pp^-T, then Linv = Mt^T
+        if (!dry) {
+            k_mt_diag<<<dim3(16, WOUT / NB, (unsigned)nf), dim3(32, 8), 0, cs>>>(L.d_fronts, K0, scr);
+            count_launch();
+            RSD_CUDA_TRY(cudaGetLastError());
+        }
         for (int i = 1; i < WOUT / NB; ++i) {
             const int k = K0 + i * NB;
             if (k >= L.max_s) break;
@@ -754,7 +755,7 @@ static int factor_level_tc(Handle& h, int li, bool lookahead) {
                 general(map_mt(q), 0, 0, tc_map_panel(f.node), k, K0, tt[q], 128,
                         i * NB, std::min(NB, f.s - k), i * NB, 1.0f);
             }
-            RSD_TRY(gemm_tc_launch(h, li, tasks, TC_GENERAL, Cs, cslot));
+            RSD_TRY(gemm_tc_launch(h, li, tasks, TC_GENERAL, cs, slot));
             tasks.clear();                              // Mt[0:i NB, i] = -Tt Dinv_i^T
             for (int q = 0; q < nf; ++q) {
                 const FrontDesc& f = L.fronts[q];
@@ -763,40 +764,109 @@ static int factor_level_tc(Handle& h, int li, bool lookahead) {
                 general(map_tt(q), 0, 0, tc_map_dinv(f.node), k, 0, mt[q] + i * NB, 512,
                         i * NB, w, w, -1.0f);
             }
-            RSD_TRY(gemm_tc_launch(h, li, tasks, TC_GENERAL, Cs, cslot));
+            RSD_TRY(gemm_tc_launch(h, li, tasks, TC_GENERAL, cs, slot));
         }
-        k_linv_transpose<<<dim3(16, 16, (unsigned)nf), dim3(32, 8), 0, Cs>>>(L.d_fronts, K0, scr);
-        count_launch();
-        RSD_CUDA_TRY(cudaGetLastError());
-        if (lookahead) {
-            RSD_CUDA_TRY(cudaEventRecord(h.ev_diag[0], Cs));
-            // bulk, one panel ahead: the K range [0, K0) of the next panel's outer update
-            if (p + 1 < np && K0 > 0) {
-                tasks.clear();
-                for (auto& f : L.fronts) add_outer(f, K0 + WOUT, 0, K0);
-                RSD_TRY(gemm_tc_launch(h, li, tasks, 3, B, 0, bulk_ctas));
-            }
-            RSD_CUDA_TRY(cudaStreamWaitEvent(B, h.ev_diag[0], 0));
+        if (!dry) {
+            k_linv_transpose<<<dim3(16, 16, (unsigned)nf), dim3(32, 8), 0, cs>>>(L.d_fronts, K0, scr, which);
+            count_launch();
+            RSD_CUDA_TRY(cudaGetLastError());
         }
-        // (f) bulk: X = A Linv^T for the rows below the diagonal block, in place
+        return RSD_OK;
+    };
+    // (f) X = A Linv^T in place for rows [rlo(f), rhi(f)) of the panel at K0: the column
+    // tile [256, W) first (it reads A[:, 0:W]), then [0, 256) (it reads only A[:, 0:256])
+    auto solve_rows = [&](int K0, int which, auto rlo, auto rhi, cudaStream_t cs, int slot, int ctas) -> int {
         for (int half = 1; half >= 0; --half) {
             tasks.clear();
             for (int q = 0; q < nf; ++q) {
                 const FrontDesc& f = L.fronts[q];
                 if (f.s <= K0) continue;
-                const int W = std::min(WOUT, f.s - K0), r0 = K0 + W;
+                const int W = std::min(WOUT, f.s - K0), r0 = rlo(f), r1 = rhi(f);
                 const int c0 = half * 256, c1 = std::min(W, c0 + 256);
-                if (c1 <= c0 || f.N <= r0) continue;
-                general(tc_map_panel(f.node), r0, K0, map_lv(q), c0, 0, P(f, r0, K0 + c0), f.ldp,
-                        f.N - r0, c1 - c0, c1, 1.0f);
+                if (c1 <= c0 || r1 <= r0) continue;
+                general(tc_map_panel(f.node), r0, K0, map_lv(q, which), c0, 0, P(f, r0, K0 + c0), f.ldp,
+                        r1 - r0, c1 - c0, c1, 1.0f);
             }
-            RSD_TRY(gemm_tc_launch(h, li, tasks, TC_GENERAL, B, 0, bulk_ctas));
+            RSD_TRY(gemm_tc_launch(h, li, tasks, TC_GENERAL, cs, slot, ctas));
         }
-    }
-    if (lookahead) {
-        RSD_CUDA_TRY(cudaEventRecord(h.ev_join, Cs));
-        RSD_CUDA_TRY(cudaStreamWaitEvent(B, h.ev_join, 0));
-    }
+        return RSD_OK;
+    };
+    auto rows_to_end = [](const FrontDesc& f) { return f.N; };
+
+    auto issue = [&]() -> int {
+        const int np = (L.max_s + WOUT - 1) / WOUT;
+        if (!lookahead) {
+            for (int p = 0; p < np; ++p) {
+                const int K0 = p * WOUT;
+                if (p >= 1) {                                   // (a0) the whole outer update
+                    tasks.clear();
+                    for (auto& f : L.fronts) add_outer(f, K0, 0, K0, K0, f.N);
+                    RSD_TRY(gemm_tc_launch(h, li, tasks, 3, B, 0));
+                }
+                RSD_TRY(factor_block(K0, 0, B, 0));
+                RSD_TRY(solve_rows(K0, 0, [&](const FrontDesc& f) { return wend(f, K0); }, rows_to_end, B, 0, 0));
+            }
+        } else {
+            // Look-ahead.  Chain(p): the part of panel p's outer update with K in [K0-W, K0)
+            // restricted to its diagonal block, the block's factorisation and inverse, and the
+            // solve of the next panel's diagonal-block rows ("X_next").  Bulk, meanwhile: the
+            // K range [0, K0) of panel p+1's outer update (all its rows; it needs no result of
+            // panels p-1 or p held by the chain), then, once the chain has them, the solve of
+            // the remaining rows below and the K range [K0, K0+W) of panel p+1's outer update
+            // for its rows below the diagonal block.  Events: ev_ready (bulk: panel p+1's long
+            // update done), ev_diag[0] (chain: Linv of panel p), ev_diag[1 + p % 2] (chain:
+            // X_next of panel p).  Linv alternates between two buffers, so the chain can
+            // build panel p+1's while the bulk still solves with panel p's.
+            cudaEvent_t& ev_linv = h.ev_diag[0];
+            if (!dry) RSD_CUDA_TRY(cudaEventRecord(h.ev_ready, B));             // the fronts are assembled
+            for (int p = 0; p < np; ++p) {
+                const int K0 = p * WOUT, K0n = K0 + WOUT, which = p & 1;
+                cudaEvent_t& ev_xnext = h.ev_diag[1 + which];
+                // ---- chain(p)
+                if (!dry) RSD_CUDA_TRY(cudaStreamWaitEvent(Cs, h.ev_ready, 0));
+                if (p >= 1) {
+                    tasks.clear();
+                    for (auto& f : L.fronts) add_outer(f, K0, K0 - WOUT, K0, K0, wend(f, K0));
+                    RSD_TRY(gemm_tc_launch(h, li, tasks, 3, Cs, cslot));
+                }
+                RSD_TRY(factor_block(K0, which, Cs, cslot));
+                if (!dry) RSD_CUDA_TRY(cudaEventRecord(ev_linv, Cs));
+                auto next_lo = [&](const FrontDesc& f) { return wend(f, K0); };
+                auto next_hi = [&](const FrontDesc& f) { return f.s > K0n ? wend(f, K0n) : wend(f, K0); };
+                if (p + 1 < np) RSD_TRY(solve_rows(K0, which, next_lo, next_hi, Cs, cslot, 0));
+                if (!dry) RSD_CUDA_TRY(cudaEventRecord(ev_xnext, Cs));
+                // ---- bulk, panel p
+                if (p + 1 < np) {
+                    if (K0 > 0) {
+                        tasks.clear();
+                        for (auto& f : L.fronts) add_outer(f, K0n, 0, K0, K0n, f.N);
+                        RSD_TRY(gemm_tc_launch(h, li, tasks, 3, B, 0, bulk_ctas));
+                    }
+                    if (!dry) RSD_CUDA_TRY(cudaEventRecord(h.ev_ready, B));
+                }
+                if (!dry) RSD_CUDA_TRY(cudaStreamWaitEvent(B, ev_linv, 0));
+                RSD_TRY(solve_rows(K0, which, next_hi, rows_to_end, B, 0, bulk_ctas));
+                if (p + 1 < np) {
+                    if (!dry) RSD_CUDA_TRY(cudaStreamWaitEvent(B, ev_xnext, 0));
+                    tasks.clear();
+                    for (auto& f : L.fronts)
+                        if (f.s > K0n) add_outer(f, K0n, K0, K0n, wend(f, K0n), f.N);
+                    RSD_TRY(gemm_tc_launch(h, li, tasks, 3, B, 0, bulk_ctas));
+                }
+            }
+            if (!dry) RSD_CUDA_TRY(cudaEventRecord(h.ev_join, Cs));
+            if (!dry) RSD_CUDA_TRY(cudaStreamWaitEvent(B, h.ev_join, 0));
+        }
+        return RSD_OK;
+    };
+    dry = true;
+    RSD_TRY(gemm_tc_record_begin(h));
+    RSD_TRY(issue());
+    RSD_TRY(gemm_tc_record_end(h, B));
+    dry = false;
+    const int rc_issue = issue();
+    gemm_tc_replay_end(h, B);
+    RSD_TRY(rc_issue);
     cudaFreeAsync(scr, B);
     return RSD_OK;
 }

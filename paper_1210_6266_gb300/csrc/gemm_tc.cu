@@ -52,6 +52,61 @@ struct TcTask {               // device view of one GEMM task
     int round_tf32;           // round stored results to the nearest TF32 value
 };
 
+// A launch's task list travels inside the parameters of a small expansion kernel that
+// writes the tasks, the tile list and the split-K reductions into the launch buffers:
+// a kernel launch is cheap to issue even when the stream is far behind, where a small
+// host-to-device copy blocks the issuing thread.  (Launches with more tasks, or with
+// lower-triangular tiles, upload the host-built lists instead.)
+constexpr int EXP_MAXT = 256;
+template <int MT>
+struct ExpandArgs {
+    int n_tasks, n_tiles, n_reds, pad;
+    TcTask task[MT];
+    int tile_begin[MT + 1];                // first tile of each task
+    int red_begin[MT + 1];                 // first split-K reduction of each task
+    int slot_begin[MT];                    // first split-K workspace slot of each task
+    int tn[MT];                            // output tiles along N
+    int ns[MT];                            // K splits of each output tile
+};
+static_assert(sizeof(ExpandArgs<EXP_MAXT>) < 32000, "kernel parameter space");
+
+__device__ __forceinline__ int last_le(const int* begin, int n, int t) {   // last i with begin[i] <= t
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (begin[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int MT>
+__global__ void k_expand_tiles(const __grid_constant__ ExpandArgs<MT> a, TcTask* __restrict__ tasks,
+                               TcTile* __restrict__ tiles, TcRed* __restrict__ reds) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < a.n_tasks) tasks[t] = a.task[t];
+    if (t < a.n_tiles) {
+        const int k = last_le(a.tile_begin, a.n_tasks, t);
+        const int local = t - a.tile_begin[k], ns = a.ns[k], tn = a.tn[k];
+        const int out = local / ns, sp = local % ns;
+        const int nkb = (a.task[k].K + BK - 1) / BK;
+        TcTile x;
+        x.task = k; x.tm = out / tn; x.tn = out % tn;
+        x.kb0 = (int)((int64_t)nkb * sp / ns);
+        x.kb1 = (int)((int64_t)nkb * (sp + 1) / ns);
+        x.ws_slot = ns > 1 ? a.slot_begin[k] + out * ns + sp : -1;
+        x.pad0 = x.pad1 = 0;
+        tiles[t] = x;
+    }
+    if (t < a.n_reds) {
+        const int k = last_le(a.red_begin, a.n_tasks, t);
+        const int local = t - a.red_begin[k], tn = a.tn[k], ns = a.ns[k];
+        TcRed r;
+        r.task = k; r.tm = local / tn; r.tn = local % tn; r.slot0 = a.slot_begin[k] + local * ns; r.nsplit = ns;
+        r.pad0 = r.pad1 = r.pad2 = 0;
+        reds[t] = r;
+    }
+}
+
 // Round to the nearest TF32 value (10-bit mantissa), kept as an FP32 bit pattern.
 __device__ __forceinline__ float tf32_rn(float x) {
     uint32_t r;
@@ -516,9 +571,18 @@ struct TcBuf {
 
 struct TcState {
     CUtensorMap* d_maps = nullptr;      // 2 per tree node: [L; X] panel, inverted diagonal blocks;
-                                        // then 3 per front slot of the widest level (scratch)
+                                        // then TC_SCR_MAPS per front slot of the widest level
     int scr_base = 0, scr_slots = 0;
     TcBuf buf[TC_SLOTS];
+    ExpandArgs<EXP_MAXT> expand;        // host-side parameter block of the expansion kernel
+    // recorded launches (gemm_tc_record_begin/end): lists built by a dry pass, uploaded
+    // once, consumed in order by the real pass
+    struct Rec { size_t o_tasks, o_tiles, o_reds; int n_tasks, n_tiles, n_reds, bn, max_kb; double fl, by; };
+    int mode = 0;                       // 0 direct, 1 recording, 2 replaying
+    std::vector<char> rec_buf;
+    std::vector<Rec> recs;
+    size_t cursor = 0;
+    char* d_meta = nullptr;
     int ws_slots = 0;                   // split-K capacity per slot, in BM x 256 tiles
     bool attr_set = false;
 };
@@ -540,7 +604,7 @@ int gemm_tc_prepare(Handle& h) {
         if (L.prec == RSD_PREC_TF32) widest = std::max(widest, (int)L.fronts.size());
     st->scr_base = 2 * h.n_nodes;
     st->scr_slots = widest;
-    std::vector<CUtensorMap> maps(2 * (size_t)h.n_nodes + 3 * (size_t)widest);
+    std::vector<CUtensorMap> maps(2 * (size_t)h.n_nodes + TC_SCR_MAPS * (size_t)widest);
     std::memset(maps.data(), 0, maps.size() * sizeof(CUtensorMap));
     for (auto& L : h.levels) {
         if (L.prec != RSD_PREC_TF32) continue;
@@ -558,21 +622,55 @@ int gemm_tc_prepare(Handle& h) {
 }
 
 int gemm_tc_scratch_maps(Handle& h, const std::vector<float*>& mt, const std::vector<float*>& tt,
-                         const std::vector<float*>& linv, cudaStream_t stream, int* base) {
+                         const std::vector<float*>& linv0, const std::vector<float*>& linv1,
+                         cudaStream_t stream, int* base) {
     TcState* st = state_of(h);
     const size_t n = mt.size();
-    if (!st || tt.size() != n || linv.size() != n || (int)n > st->scr_slots) return RSD_ERR_ARG;
-    std::vector<CUtensorMap> maps(3 * n);
+    if (!st || tt.size() != n || linv0.size() != n || linv1.size() != n || (int)n > st->scr_slots) return RSD_ERR_ARG;
+    std::vector<CUtensorMap> maps(TC_SCR_MAPS * n);
     for (size_t i = 0; i < n; ++i) {
-        RSD_TRY(encode_2d(&maps[3 * i + 0], mt[i], 512, 512, 512));
-        RSD_TRY(encode_2d(&maps[3 * i + 1], tt[i], 128, 512, 128));
-        RSD_TRY(encode_2d(&maps[3 * i + 2], linv[i], 512, 512, 512));
+        RSD_TRY(encode_2d(&maps[TC_SCR_MAPS * i + 0], mt[i], 512, 512, 512));
+        RSD_TRY(encode_2d(&maps[TC_SCR_MAPS * i + 1], tt[i], 128, 512, 128));
+        RSD_TRY(encode_2d(&maps[TC_SCR_MAPS * i + 2], linv0[i], 512, 512, 512));
+        RSD_TRY(encode_2d(&maps[TC_SCR_MAPS * i + 3], linv1[i], 512, 512, 512));
     }
     if (n)
         RSD_CUDA_TRY(cudaMemcpyAsync(st->d_maps + st->scr_base, stage_host(h, maps.data(), maps.size() * sizeof(CUtensorMap)),
                                      maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, stream));
     *base = st->scr_base;
     return RSD_OK;
+}
+
+int gemm_tc_record_begin(Handle& h) {
+    TcState* st = state_of(h);
+    if (!st || st->mode != 0) return RSD_ERR_ARG;
+    st->mode = 1;
+    st->rec_buf.clear();
+    st->recs.clear();
+    st->cursor = 0;
+    return RSD_OK;
+}
+
+int gemm_tc_record_end(Handle& h, cudaStream_t stream) {
+    TcState* st = state_of(h);
+    if (!st || st->mode != 1) return RSD_ERR_ARG;
+    st->mode = 2;
+    st->d_meta = nullptr;
+    if (st->rec_buf.empty()) return RSD_OK;
+    RSD_CUDA_TRY(cudaMallocAsync((void**)&st->d_meta, st->rec_buf.size(), stream));
+    RSD_CUDA_TRY(cudaMemcpyAsync(st->d_meta, stage_host(h, st->rec_buf.data(), st->rec_buf.size()),
+                                 st->rec_buf.size(), cudaMemcpyHostToDevice, stream));
+    return RSD_OK;
+}
+
+void gemm_tc_replay_end(Handle& h, cudaStream_t stream) {
+    TcState* st = state_of(h);
+    if (!st) return;
+    if (st->d_meta) cudaFreeAsync(st->d_meta, stream);
+    st->d_meta = nullptr;
+    st->mode = 0;
+    st->recs.clear();
+    st->cursor = 0;
 }
 
 void gemm_tc_release(Handle& h) {
@@ -645,6 +743,42 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
         for (int sp = 0; sp < ns; ++sp)
             tl.push_back({o[0], o[1], o[2], (int)((int64_t)nkb * sp / ns), (int)((int64_t)nkb * (sp + 1) / ns), slot++, 0, 0});
     }
+    double fl = 0, by = 0;
+    for (auto& g : tasks) {
+        const double c = g.lower ? 0.5 * g.M * (g.M + 1.0) : (double)g.M * g.N;
+        fl += 2.0 * c * g.K;
+        by += 4.0 * ((double)g.M * g.K + (g.lower ? 0.0 : (double)g.N * g.K) + c * (g.beta ? 2 : 1));
+    }
+    if (st->mode == 1) {                                   // dry pass: record only
+        auto put = [&](const void* p, size_t bytes) {
+            const size_t o = (st->rec_buf.size() + 255) & ~(size_t)255;
+            st->rec_buf.resize(o + bytes);
+            if (bytes) std::memcpy(st->rec_buf.data() + o, p, bytes);
+            return o;
+        };
+        TcState::Rec r{};
+        r.o_tasks = put(tt.data(), tt.size() * sizeof(TcTask));
+        r.o_tiles = put(tl.data(), tl.size() * sizeof(TcTile));
+        r.o_reds = put(rd.data(), rd.size() * sizeof(TcRed));
+        r.n_tasks = (int)tt.size(); r.n_tiles = (int)tl.size(); r.n_reds = (int)rd.size();
+        r.bn = bn; r.max_kb = max_kb; r.fl = fl; r.by = by;
+        st->recs.push_back(r);
+        return RSD_OK;
+    }
+    TcTask* d_tasks = nullptr;
+    TcTile* d_tiles = nullptr;
+    TcRed* d_reds = nullptr;
+    if (st->mode == 2) {                                   // real pass: the recorded lists
+        if (st->cursor >= st->recs.size()) { set_last_error("recorded launch list exhausted"); return RSD_ERR_ARG; }
+        const TcState::Rec& r = st->recs[st->cursor++];
+        if (r.n_tasks != (int)tt.size() || r.n_tiles != (int)tl.size() || r.n_reds != (int)rd.size()) {
+            set_last_error("recorded launch does not match");
+            return RSD_ERR_ARG;
+        }
+        d_tasks = (TcTask*)(st->d_meta + r.o_tasks);
+        d_tiles = (TcTile*)(st->d_meta + r.o_tiles);
+        d_reds = (TcRed*)(st->d_meta + r.o_reds);
+    }
     auto grow = [&](auto*& ptr, size_t& cap, size_t need, size_t elem) -> int {
         if (need <= cap) return RSD_OK;
         cudaFreeAsync(ptr, stream);
@@ -652,16 +786,73 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
         RSD_CUDA_TRY(cudaMallocAsync((void**)&ptr, cap * elem, stream));
         return RSD_OK;
     };
+    if (st->mode == 0) {
     RSD_TRY(grow(bf.d_tasks, bf.cap_tasks, tt.size(), sizeof(TcTask)));
     RSD_TRY(grow(bf.d_tiles, bf.cap_tiles, tl.size(), sizeof(TcTile)));
     if (!rd.empty()) RSD_TRY(grow(bf.d_reds, bf.cap_reds, rd.size(), sizeof(TcRed)));
-    RSD_CUDA_TRY(cudaMemcpyAsync(bf.d_tasks, stage_host(h, tt.data(), tt.size() * sizeof(TcTask)),
-                                 tt.size() * sizeof(TcTask), cudaMemcpyHostToDevice, stream));
-    RSD_CUDA_TRY(cudaMemcpyAsync(bf.d_tiles, stage_host(h, tl.data(), tl.size() * sizeof(TcTile)),
-                                 tl.size() * sizeof(TcTile), cudaMemcpyHostToDevice, stream));
-    if (!rd.empty())
-        RSD_CUDA_TRY(cudaMemcpyAsync(bf.d_reds, stage_host(h, rd.data(), rd.size() * sizeof(TcRed)),
-                                     rd.size() * sizeof(TcRed), cudaMemcpyHostToDevice, stream));
+    d_tasks = bf.d_tasks;
+    d_tiles = bf.d_tiles;
+    d_reds = bf.d_reds;
+    bool any_lower = false;
+    for (auto& g : tasks) any_lower |= g.lower != 0;
+    if (!any_lower && (int)tasks.size() <= EXP_MAXT) {
+        ExpandArgs<EXP_MAXT>* ea = &st->expand;
+        ea->n_tasks = (int)tasks.size();
+        ea->n_tiles = (int)tl.size();
+        ea->n_reds = (int)rd.size();
+        int tb = 0, rb = 0, sb = 0;
+        for (size_t i = 0; i < tasks.size(); ++i) {
+            const GemmTask& g = tasks[i];
+            const int tm = (g.M + BM - 1) / BM, tn = (g.N + bn - 1) / bn;
+            const int nkb = (g.K + BK - 1) / BK;
+            const int ns = std::max(1, std::min(nsplit, nkb / SPLIT_MIN_KB));
+            ea->task[i] = tt[i];
+            ea->tile_begin[i] = tb;
+            ea->red_begin[i] = rb;
+            ea->slot_begin[i] = sb;
+            ea->tn[i] = std::max(tn, 1);
+            ea->ns[i] = ns;
+            tb += tm * tn * ns;
+            if (ns > 1) { rb += tm * tn; sb += tm * tn * ns; }
+        }
+        ea->tile_begin[tasks.size()] = tb;
+        ea->red_begin[tasks.size()] = rb;
+        if (tb != (int)tl.size() || rb != (int)rd.size()) { set_last_error("tile list mismatch"); return RSD_ERR_ARG; }
+        const int nthr = std::max({ea->n_tasks, ea->n_tiles, ea->n_reds});
+        const unsigned g = (unsigned)((nthr + 255) / 256);
+        // launch with the smallest parameter block that holds the tasks
+        auto shrink = [&](auto& small) {
+            constexpr int M = sizeof(small.task) / sizeof(TcTask);
+            small.n_tasks = ea->n_tasks; small.n_tiles = ea->n_tiles; small.n_reds = ea->n_reds; small.pad = 0;
+            for (int i = 0; i < ea->n_tasks; ++i) {
+                small.task[i] = ea->task[i]; small.slot_begin[i] = ea->slot_begin[i];
+                small.tn[i] = ea->tn[i]; small.ns[i] = ea->ns[i];
+            }
+            for (int i = 0; i <= ea->n_tasks; ++i) { small.tile_begin[i] = ea->tile_begin[i]; small.red_begin[i] = ea->red_begin[i]; }
+            (void)M;
+        };
+        if (ea->n_tasks <= 16) {
+            ExpandArgs<16> a16;
+            shrink(a16);
+            k_expand_tiles<16><<<g, 256, 0, stream>>>(a16, bf.d_tasks, bf.d_tiles, bf.d_reds);
+        } else if (ea->n_tasks <= 64) {
+            ExpandArgs<64> a64;
+            shrink(a64);
+            k_expand_tiles<64><<<g, 256, 0, stream>>>(a64, bf.d_tasks, bf.d_tiles, bf.d_reds);
+        } else {
+            k_expand_tiles<EXP_MAXT><<<g, 256, 0, stream>>>(*ea, bf.d_tasks, bf.d_tiles, bf.d_reds);
+        }
+        count_launch();
+    } else {
+        RSD_CUDA_TRY(cudaMemcpyAsync(bf.d_tasks, stage_host(h, tt.data(), tt.size() * sizeof(TcTask)),
+                                     tt.size() * sizeof(TcTask), cudaMemcpyHostToDevice, stream));
+        RSD_CUDA_TRY(cudaMemcpyAsync(bf.d_tiles, stage_host(h, tl.data(), tl.size() * sizeof(TcTile)),
+                                     tl.size() * sizeof(TcTile), cudaMemcpyHostToDevice, stream));
+        if (!rd.empty())
+            RSD_CUDA_TRY(cudaMemcpyAsync(bf.d_reds, stage_host(h, rd.data(), rd.size() * sizeof(TcRed)),
+                                         rd.size() * sizeof(TcRed), cudaMemcpyHostToDevice, stream));
+    }
+    }
     if (!st->attr_set) {
         RSD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<128, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<128, 3>::TOTAL));
         RSD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<128, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<128, 6>::TOTAL));
@@ -669,28 +860,22 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
         RSD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc_persist<256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<256, 4>::TOTAL));
         st->attr_set = true;
     }
-    double fl = 0, by = 0;
-    for (auto& g : tasks) {
-        const double c = g.lower ? 0.5 * g.M * (g.M + 1.0) : (double)g.M * g.N;
-        fl += 2.0 * c * g.K;
-        by += 4.0 * ((double)g.M * g.K + (g.lower ? 0.0 : (double)g.N * g.K) + c * (g.beta ? 2 : 1));
-    }
     const int pi = prof_begin(h, K_GEMM_TC, stream);
     // short K (inner panel update, panel solve): 3-stage ring, two CTAs per SM so one
     // tile's epilogue overlaps the other's main loop; long K: deeper rings, one CTA per SM
     if (bn == 128 && max_kb <= 16)
-        k_gemm_tc<128, 3><<<(unsigned)tl.size(), TC_THREADS, Smem<128, 3>::TOTAL, stream>>>(bf.d_tasks, bf.d_tiles, st->d_maps, bf.d_ws, h.d_err);
+        k_gemm_tc<128, 3><<<(unsigned)tl.size(), TC_THREADS, Smem<128, 3>::TOTAL, stream>>>(d_tasks, d_tiles, st->d_maps, bf.d_ws, h.d_err);
     else if (bn == 128)
-        k_gemm_tc<128, 6><<<(unsigned)tl.size(), TC_THREADS, Smem<128, 6>::TOTAL, stream>>>(bf.d_tasks, bf.d_tiles, st->d_maps, bf.d_ws, h.d_err);
+        k_gemm_tc<128, 6><<<(unsigned)tl.size(), TC_THREADS, Smem<128, 6>::TOTAL, stream>>>(d_tasks, d_tiles, st->d_maps, bf.d_ws, h.d_err);
     else {
         const int ctas = std::min((int)tl.size(), sms);
         k_gemm_tc_persist<256, 4><<<(unsigned)ctas, TC_THREADS, Smem<256, 4>::TOTAL, stream>>>(
-            bf.d_tasks, bf.d_tiles, (int)tl.size(), st->d_maps, bf.d_ws, h.d_err);
+            d_tasks, d_tiles, (int)tl.size(), st->d_maps, bf.d_ws, h.d_err);
     }
     count_launch();
     if (!rd.empty()) {
-        if (bn == 128) k_splitk_reduce<128><<<(unsigned)rd.size(), 256, 0, stream>>>(bf.d_tasks, bf.d_reds, bf.d_ws);
-        else k_splitk_reduce<256><<<(unsigned)rd.size(), 256, 0, stream>>>(bf.d_tasks, bf.d_reds, bf.d_ws);
+        if (bn == 128) k_splitk_reduce<128><<<(unsigned)rd.size(), 256, 0, stream>>>(d_tasks, d_reds, bf.d_ws);
+        else k_splitk_reduce<256><<<(unsigned)rd.size(), 256, 0, stream>>>(d_tasks, d_reds, bf.d_ws);
         count_launch();
     }
     prof_end(h, pi, fl, by, stream);

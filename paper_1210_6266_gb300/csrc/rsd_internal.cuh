@@ -84,11 +84,12 @@ enum KClass { K_ASSEMBLE = 0, K_EXTEND, K_GEMM_TC, K_GEMM_SIMT, K_POTRF, K_TRSM,
 // flops and bytes of that launch; reduced on demand by rsd_profile().
 struct Prof {
     bool on = false;
-    struct Rec { int cls; double flops, bytes; cudaEvent_t a, b; int stream; };
+    struct Rec { int cls; double flops, bytes; cudaEvent_t a, b; int stream; double host_us; };
     std::vector<Rec> recs;
     std::vector<cudaEvent_t> pool;
     double host_ms = 0;                  // host-side analysis time of the last setup
     double host_part[6] = {0, 0, 0, 0, 0, 0};   // copy, sort, check, sets, maps, plan
+    double host_issue_ms = 0;            // issuing the numeric setup's launches
 };
 
 void count_launch(int n = 1);
@@ -174,8 +175,8 @@ struct Handle {
     double *d_pg = nullptr, *d_pw = nullptr, *d_pz = nullptr;   // g, w and leaf-solve scratch
     int* d_ticket_paper = nullptr;
     // pinned host staging for per-launch uploads (append-only; see stage_host)
-    char* stage = nullptr;
-    size_t stage_cap = 0, stage_off = 0;
+    std::vector<std::pair<char*, size_t>> stage_blocks;
+    size_t stage_cur = 0, stage_off = 0;
     // look-ahead factorisation of levels with few fronts: a high-priority stream runs the
     // diagonal-block chain beside the bulk updates on `stream` (created on first use)
     cudaStream_t chain = nullptr;
@@ -185,8 +186,10 @@ struct Handle {
 
 // Copy `bytes` from host memory into the handle's pinned staging area and return the
 // pinned copy, so that a following cudaMemcpyAsync is truly asynchronous.  The area is
-// used append-only; when it is full the stream is synchronised and it restarts.
+// used append-only (another pinned block is added when it is full, never waiting for
+// the device); stage_reset() rewinds it once every staged copy is known to be done.
 const void* stage_host(Handle& h, const void* src, size_t bytes);
+void stage_reset(Handle& h);
 
 // Profile helpers: prof_begin records the start event (if profiling) and returns a
 // record index; prof_end records the stop event and the launch's algorithmic work.
@@ -201,11 +204,21 @@ inline void prof_end(Handle& h, int idx, double flops, double bytes) { prof_end(
 // max_ctas > 0 caps the CTAs of the persistent kernel (leaving SMs to another stream).
 constexpr int TC_SLOTS = 2;
 constexpr int TC_GENERAL = 4;        // kind: explicit map indices, alpha and rounding
+// Recorded launches: between record_begin and record_end, gemm_tc_launch only records
+// each launch's task and tile lists; record_end uploads them in one copy on `stream`,
+// and the next gemm_tc_launch calls, which must repeat the recorded sequence, launch
+// from the uploaded lists; replay_end frees them (stream-ordered on `stream`).
+int gemm_tc_record_begin(Handle& h);
+int gemm_tc_record_end(Handle& h, cudaStream_t stream);
+void gemm_tc_replay_end(Handle& h, cudaStream_t stream);
 // Tensor maps for per-front scratch of the level being factored (the block-inverse panel
-// solve): three per front slot -- Mt (512 x 512), Tt (512 x 128), Linv (512 x 512) --
-// encoded and uploaded on `stream`; returns the index of slot 0's first map.
+// solve): TC_SCR_MAPS per front slot -- Mt (512 x 512), Tt (512 x 128) and two Linv
+// (512 x 512, alternating panels) -- encoded and uploaded on `stream`; returns the index
+// of slot 0's first map.
+constexpr int TC_SCR_MAPS = 4;
 int gemm_tc_scratch_maps(Handle& h, const std::vector<float*>& mt, const std::vector<float*>& tt,
-                         const std::vector<float*>& linv, cudaStream_t stream, int* base);
+                         const std::vector<float*>& linv0, const std::vector<float*>& linv1,
+                         cudaStream_t stream, int* base);
 // map index of a node's [L; X] panel (P) and of its inverted diagonal blocks
 inline int tc_map_panel(int node) { return 2 * node; }
 inline int tc_map_dinv(int node) { return 2 * node + 1; }
