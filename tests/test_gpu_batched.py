@@ -73,3 +73,28 @@ def test_batched_handle_reports_each_front(rsd, batch):
     assert inf["n"] == sum(p["n_dof"] for p in probs)
     assert inf["n_nodes"] == 1 + sum(len(p["parent"]) for p in probs)
     assert h.front_dims(0)[:2] == (0, 0)                # the empty super-root
+
+
+def test_batched_tf32_factors_track_fp32_on_uneven_fronts(rsd, batch):
+    """The problem roots form one level of fronts of uneven size (331 to 919 interface
+    DOFs), factored with the look-ahead schedule in tensor cores: every front must match the
+    FP32 CUDA-core factorisation of the same hierarchy to TF32 rounding."""
+    probs, _ = batch
+    h32 = rsd.RSD.setup_batched(probs, prec_leaf=rsd.RSD_PREC_FP32, prec_mid=rsd.RSD_PREC_FP32,
+                                prec_root=rsd.RSD_PREC_FP32)
+    htf = rsd.RSD.setup_batched(probs, prec_leaf=rsd.RSD_PREC_TF32, prec_mid=rsd.RSD_PREC_TF32,
+                                prec_root=rsd.RSD_PREC_TF32)
+    n_nodes = h32.info()["n_nodes"]
+    big = 0
+    for t in range(1, n_nodes):
+        s, b, _ = h32.front_dims(t)
+        if s == 0:
+            continue
+        big += s > 512
+        a, c = h32.front_factor(t), htf.front_factor(t)
+        scale = np.abs(a).max()
+        assert np.abs(a - c).max() <= 5e-3 * scale, (t, np.abs(a - c).max() / scale)
+    assert big >= 1                                     # some fronts span several 512-wide panels
+    b = torch.cat([p["b"] for p in probs])
+    _, st = htf.solve(b, tol=1e-8)
+    assert st["iterations"] <= 10, st                   # TF32 factors keep PCG short

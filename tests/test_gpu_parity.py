@@ -217,3 +217,26 @@ def test_tf32_tensor_core_factors_track_fp32(rsd, n, depth):
         assert np.abs(a - b).max() <= 5e-3 * scale, (t, np.abs(a - b).max() / scale)
     u, st = htf.solve(prob["b"], tol=1e-8)
     assert st["relres"] <= 1e-8, st
+
+
+def test_profile_trace_matches_profile(rsd):
+    """rsd_profile_trace lists the launches rsd_profile sums: same count per class, ends
+    after starts, and the look-ahead stream in use for a single large front."""
+    w = _work(26, 1, True)
+    prob = rsd.grid_problem(26, 1, w["kappa"], w["f"])
+    h = rsd.RSD.setup(prob["rowptr"], prob["col"], prob["val"], prob["dof_node"], prob["parent"],
+                      prec_leaf=rsd.RSD_PREC_TF32, prec_mid=rsd.RSD_PREC_TF32, prec_root=rsd.RSD_PREC_TF32,
+                      profile=True)
+    h.solve(prob["b"], tol=1e-8)
+    tr = h.trace()
+    prof = h.profile()
+    counts = {}
+    for r in tr:
+        counts[r["cls"]] = counts.get(r["cls"], 0) + 1
+        assert r["end_ms"] >= r["start_ms"] >= 0.0
+        assert r["stream"] in (0, 1)
+    for cls, v in prof.items():
+        if isinstance(v, dict) and "launches" in v:
+            assert counts.get(cls, 0) == v["launches"], cls
+    assert any(r["stream"] == 1 for r in tr)           # the root's diagonal-block chain
+    assert prof["host_issue_ms"] > 0
