@@ -1068,6 +1068,7 @@ extern "C" void rsd_destroy(rsd_handle hh) {
     }
     for (cudaEvent_t e : {h.ev_ready, h.ev_join, h.ev_diag[0], h.ev_diag[1], h.ev_diag[2], h.ev_diag[3]})
         if (e) cudaEventDestroy(e);
+    if (h.apply_exec) cudaGraphExecDestroy(h.apply_exec);
     gemm_tc_release(h);
     for (auto& r : h.prof.recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : h.prof.pool) cudaEventDestroy(e);

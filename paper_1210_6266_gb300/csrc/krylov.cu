@@ -131,8 +131,43 @@ int spmv(Handle& h, const double* x, double* y) {
     return RSD_OK;
 }
 
+// PCG's preconditioner application on its fixed vectors r -> z as a CUDA graph, for a
+// handle that solves more than once (an adjoint solve, a sequence of right-hand sides):
+// the second solve captures run_apply (on a private stream: the caller's stream may be
+// the legacy default stream, which cannot be captured) and every later application
+// replays it on the caller's stream.  A first solve keeps direct launches (capturing and
+// instantiating would cost more than it saves once), as do a profiled handle, whose
+// launch records are host-side, and paper mode.
+static int pcg_apply(Handle& h, const double* r, double* z) {
+    if (h.paper) return run_apply_paper(h, r, z);
+    if (h.prof.on || h.solve_calls < 2) return run_apply(h, r, z);
+    if (!h.apply_exec) {
+        cudaStream_t cap = nullptr;
+        RSD_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaStream_t user = h.stream;
+        const int64_t l0 = rsd_launch_count();
+        h.stream = cap;
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        int rc = e == cudaSuccess ? run_apply(h, r, z) : RSD_ERR_CUDA;
+        cudaGraph_t g = nullptr;
+        if (e == cudaSuccess) e = cudaStreamEndCapture(cap, &g);
+        h.stream = user;
+        cudaStreamDestroy(cap);
+        h.apply_graph_launches = (int)(rsd_launch_count() - l0);
+        count_launch(-h.apply_graph_launches);            // counted when replayed
+        if (rc == RSD_OK && e == cudaSuccess) e = cudaGraphInstantiate(&h.apply_exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (rc != RSD_OK) return rc;
+        if (e != cudaSuccess) { cudaGetLastError(); h.apply_exec = nullptr; set_last_error("apply graph capture failed"); return RSD_ERR_CUDA; }
+    }
+    RSD_CUDA_TRY(cudaGraphLaunch(h.apply_exec, h.stream));
+    count_launch(h.apply_graph_launches);
+    return RSD_OK;
+}
+
 // Scalar slots: 0 rz (even iterations), 1 pq, 2 rr, 3 rz (odd iterations), 4 ff, 5 true rr
 int pcg(Handle& h, const double* f, double* u, double tol, rsd_stats* st) {
+    ++h.solve_calls;
     const int64_t n = h.n;
     double* r = h.d_r;
     double* p = h.d_p;
@@ -150,7 +185,7 @@ int pcg(Handle& h, const double* f, double* u, double tol, rsd_stats* st) {
     const double fnorm = std::sqrt(ff);
     S->history[0] = 1.0;
     if (fnorm == 0.0) { S->relres = 0; return RSD_OK; }
-    RSD_TRY(h.paper ? run_apply_paper(h, r, z) : run_apply(h, r, z));
+    RSD_TRY(pcg_apply(h, r, z));
     RSD_CUDA_TRY(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, h.stream));
     RSD_TRY(dot(h, r, z, 0));
     int it = 0;
@@ -172,7 +207,7 @@ int pcg(Handle& h, const double* f, double* u, double tol, rsd_stats* st) {
         if (it < 64) S->history[it] = rel;
         if (!(rel == rel)) { rc = RSD_ERR_NOT_SPD; break; }
         if (rel <= tol) { rc = RSD_OK; break; }
-        RSD_TRY(h.paper ? run_apply_paper(h, r, z) : run_apply(h, r, z));
+        RSD_TRY(pcg_apply(h, r, z));
         RSD_TRY(dot(h, r, z, new_slot));
         const int pd = prof_begin(h, K_KRYLOV);
         k_cg_direction<<<RED_BLOCKS, RT, 0, h.stream>>>(n, h.d_scal, new_slot, old_slot, z, p);

@@ -182,6 +182,9 @@ struct Handle {
     cudaStream_t chain = nullptr;
     cudaEvent_t ev_ready = nullptr, ev_join = nullptr;
     cudaEvent_t ev_diag[4] = {nullptr, nullptr, nullptr, nullptr};
+    // PCG's preconditioner application as a captured graph (see pcg_apply)
+    cudaGraphExec_t apply_exec = nullptr;
+    int solve_calls = 0, apply_graph_launches = 0;
 };
 
 // Copy `bytes` from host memory into the handle's pinned staging area and return the

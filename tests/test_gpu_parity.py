@@ -240,3 +240,23 @@ def test_profile_trace_matches_profile(rsd):
             assert counts.get(cls, 0) == v["launches"], cls
     assert any(r["stream"] == 1 for r in tr)           # the root's diagonal-block chain
     assert prof["host_issue_ms"] > 0
+
+
+def test_graph_replayed_apply_matches_direct_launches(rsd):
+    """Without profiling, a handle's second and later solves replay the preconditioner
+    application from a captured CUDA graph; the iterates must be bitwise those of the
+    directly launched solves."""
+    w = _work(20, 2, True)
+    prob = rsd.grid_problem(20, 2, w["kappa"], w["f"])
+    kw = dict(prec_leaf=rsd.RSD_PREC_TF32, prec_mid=rsd.RSD_PREC_TF32, prec_root=rsd.RSD_PREC_TF32)
+    hg = rsd.RSD.setup(prob["rowptr"], prob["col"], prob["val"], prob["dof_node"], prob["parent"], **kw)
+    hd = rsd.RSD.setup(prob["rowptr"], prob["col"], prob["val"], prob["dof_node"], prob["parent"],
+                       profile=True, **kw)
+    ug, sg = hg.solve(prob["b"], tol=1e-10)
+    ud, sd = hd.solve(prob["b"], tol=1e-10)
+    assert sg["iterations"] == sd["iterations"] >= 3
+    assert torch.equal(ug, ud)
+    for _ in range(2):                                     # captured, then replayed
+        ug2, sg2 = hg.solve(prob["b"], tol=1e-10)
+        assert sg2["iterations"] == sg["iterations"]
+        assert torch.equal(ug2, ug)
