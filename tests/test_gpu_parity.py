@@ -154,9 +154,9 @@ def test_host_csr_input_matches_device_input(rsd):
     assert torch.equal(h1.apply(r), h2.apply(r))
 
 
-def test_device_structure_pass_matches_host_pass(rsd):
-    """A device CSR goes through the GPU structure pass (Eq. 3.1 check, B-set bitmaps), a
-    host CSR through the host pass: identical interface sets and extend-add maps."""
+def test_host_and_device_csr_give_the_same_structure(rsd):
+    """A device CSR goes straight to the GPU structure pass (Eq. 3.1 check, B-set bitmaps);
+    a host CSR is uploaded first: identical interface sets and extend-add maps."""
     w = _work(20, 2, True)
     prob = rsd.grid_problem(20, 2, w["kappa"], w["f"])
     hd = _setup(rsd, prob, rsd.RSD_PREC_FP64)
