@@ -126,8 +126,9 @@ __global__ void k_fwd_gather(const FrontDesc* __restrict__ fronts, const FrontDe
 // factor tile of a column block is requested before waiting for that block's y); a B
 // block then stores its contribution v_row - acc_row.  A diagonal group finishes its
 // blocks inside the CTA -- t_g = v_g - acc_g - sum_{g' < g} P[g, g'] y_g', y_g = Dinv_g t_g
-// -- and publishes the front's progress counter once for the whole group, so the
-// dependency chain between CTAs has one hand-off per GD blocks.
+// -- publishing the front's progress counter after each block, so the dependency chain
+// between CTAs waits on one item per GD blocks while the next item already consumes
+// the group's first block.
 template <typename T, typename A, int GD>
 __global__ void __launch_bounds__(AT, GD == 1 ? 2 : 1) k_fwd_sweep(const FrontDesc* __restrict__ fronts,
                                                      const int* __restrict__ items, int n_items,
@@ -284,9 +285,10 @@ __global__ void __launch_bounds__(AT, GD == 1 ? 2 : 1) k_fwd_sweep(const FrontDe
                     }
                 }
             }
-            __syncthreads();
+            // each block is published as soon as it is done, so the next item can take
+            // this block's column while the second block of the pair is solved
+            publish_flag(&f.flag[0], blk + g + 1, lane == 0);
         }
-        publish_flag(&f.flag[0], blk + nb, lane == 0);
         __syncthreads();
     }
 }
@@ -304,7 +306,8 @@ __global__ void k_bwd_gather(const FrontDesc* __restrict__ fronts, const double*
 // P[rows, group columns]^T x_rows (ancestor rows first, then the interface row blocks
 // above hi as their owners finish; each row group's factor rows are requested before
 // waiting for its x); then inside the CTA x_hi = Dinv_hi^T t_hi,
-// t_lo -= P[hi rows, lo columns]^T x_hi, x_lo = Dinv_lo^T t_lo, and one publish.
+// t_lo -= P[hi rows, lo columns]^T x_hi, x_lo = Dinv_lo^T t_lo, each block published
+// as soon as it is done.
 template <typename T, typename A, int GD>
 __global__ void __launch_bounds__(AT, GD == 1 ? 2 : 1) k_bwd_sweep(const FrontDesc* __restrict__ fronts,
                                                      const int* __restrict__ items, int n_items,
@@ -468,9 +471,8 @@ __global__ void __launch_bounds__(AT, GD == 1 ? 2 : 1) k_bwd_sweep(const FrontDe
                 z[f.I[c0 + g * NB + c]] = (double)sum;
                 s_x[c] = sum;
             }
-            __syncthreads();
+            publish_flag(&f.flag[1], f.nd - hi + k, true);   // blocks >= hi - k are done
         }
-        publish_flag(&f.flag[1], f.nd - lo, true);
         __syncthreads();
     }
 }
