@@ -52,61 +52,6 @@ struct TcTask {               // device view of one GEMM task
     int round_tf32;           // round stored results to the nearest TF32 value
 };
 
-// A launch's task list travels inside the parameters of a small expansion kernel that
-// writes the tasks, the tile list and the split-K reductions into the launch buffers:
-// a kernel launch is cheap to issue even when the stream is far behind, where a small
-// host-to-device copy blocks the issuing thread.  (Launches with more tasks, or with
-// lower-triangular tiles, upload the host-built lists instead.)
-constexpr int EXP_MAXT = 256;
-template <int MT>
-struct ExpandArgs {
-    int n_tasks, n_tiles, n_reds, pad;
-    TcTask task[MT];
-    int tile_begin[MT + 1];                // first tile of each task
-    int red_begin[MT + 1];                 // first split-K reduction of each task
-    int slot_begin[MT];                    // first split-K workspace slot of each task
-    int tn[MT];                            // output tiles along N
-    int ns[MT];                            // K splits of each output tile
-};
-static_assert(sizeof(ExpandArgs<EXP_MAXT>) < 32000, "kernel parameter space");
-
-__device__ __forceinline__ int last_le(const int* begin, int n, int t) {   // last i with begin[i] <= t
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (begin[mid] <= t) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
-template <int MT>
-__global__ void k_expand_tiles(const __grid_constant__ ExpandArgs<MT> a, TcTask* __restrict__ tasks,
-                               TcTile* __restrict__ tiles, TcRed* __restrict__ reds) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < a.n_tasks) tasks[t] = a.task[t];
-    if (t < a.n_tiles) {
-        const int k = last_le(a.tile_begin, a.n_tasks, t);
-        const int local = t - a.tile_begin[k], ns = a.ns[k], tn = a.tn[k];
-        const int out = local / ns, sp = local % ns;
-        const int nkb = (a.task[k].K + BK - 1) / BK;
-        TcTile x;
-        x.task = k; x.tm = out / tn; x.tn = out % tn;
-        x.kb0 = (int)((int64_t)nkb * sp / ns);
-        x.kb1 = (int)((int64_t)nkb * (sp + 1) / ns);
-        x.ws_slot = ns > 1 ? a.slot_begin[k] + out * ns + sp : -1;
-        x.pad0 = x.pad1 = 0;
-        tiles[t] = x;
-    }
-    if (t < a.n_reds) {
-        const int k = last_le(a.red_begin, a.n_tasks, t);
-        const int local = t - a.red_begin[k], tn = a.tn[k], ns = a.ns[k];
-        TcRed r;
-        r.task = k; r.tm = local / tn; r.tn = local % tn; r.slot0 = a.slot_begin[k] + local * ns; r.nsplit = ns;
-        r.pad0 = r.pad1 = r.pad2 = 0;
-        reds[t] = r;
-    }
-}
-
 // Round to the nearest TF32 value (10-bit mantissa), kept as an FP32 bit pattern.
 __device__ __forceinline__ float tf32_rn(float x) {
     uint32_t r;
@@ -574,7 +519,6 @@ struct TcState {
                                         // then TC_SCR_MAPS per front slot of the widest level
     int scr_base = 0, scr_slots = 0;
     TcBuf buf[TC_SLOTS];
-    ExpandArgs<EXP_MAXT> expand;        // host-side parameter block of the expansion kernel
     // recorded launches (gemm_tc_record_begin/end): lists built by a dry pass, uploaded
     // once, consumed in order by the real pass
     struct Rec { size_t o_tasks, o_tiles, o_reds; int n_tasks, n_tiles, n_reds, bn, max_kb; double fl, by; };
@@ -786,72 +730,20 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
         RSD_CUDA_TRY(cudaMallocAsync((void**)&ptr, cap * elem, stream));
         return RSD_OK;
     };
-    if (st->mode == 0) {
-    RSD_TRY(grow(bf.d_tasks, bf.cap_tasks, tt.size(), sizeof(TcTask)));
-    RSD_TRY(grow(bf.d_tiles, bf.cap_tiles, tl.size(), sizeof(TcTile)));
-    if (!rd.empty()) RSD_TRY(grow(bf.d_reds, bf.cap_reds, rd.size(), sizeof(TcRed)));
-    d_tasks = bf.d_tasks;
-    d_tiles = bf.d_tiles;
-    d_reds = bf.d_reds;
-    bool any_lower = false;
-    for (auto& g : tasks) any_lower |= g.lower != 0;
-    if (!any_lower && (int)tasks.size() <= EXP_MAXT) {
-        ExpandArgs<EXP_MAXT>* ea = &st->expand;
-        ea->n_tasks = (int)tasks.size();
-        ea->n_tiles = (int)tl.size();
-        ea->n_reds = (int)rd.size();
-        int tb = 0, rb = 0, sb = 0;
-        for (size_t i = 0; i < tasks.size(); ++i) {
-            const GemmTask& g = tasks[i];
-            const int tm = (g.M + BM - 1) / BM, tn = (g.N + bn - 1) / bn;
-            const int nkb = (g.K + BK - 1) / BK;
-            const int ns = std::max(1, std::min(nsplit, nkb / SPLIT_MIN_KB));
-            ea->task[i] = tt[i];
-            ea->tile_begin[i] = tb;
-            ea->red_begin[i] = rb;
-            ea->slot_begin[i] = sb;
-            ea->tn[i] = std::max(tn, 1);
-            ea->ns[i] = ns;
-            tb += tm * tn * ns;
-            if (ns > 1) { rb += tm * tn; sb += tm * tn * ns; }
-        }
-        ea->tile_begin[tasks.size()] = tb;
-        ea->red_begin[tasks.size()] = rb;
-        if (tb != (int)tl.size() || rb != (int)rd.size()) { set_last_error("tile list mismatch"); return RSD_ERR_ARG; }
-        const int nthr = std::max({ea->n_tasks, ea->n_tiles, ea->n_reds});
-        const unsigned g = (unsigned)((nthr + 255) / 256);
-        // launch with the smallest parameter block that holds the tasks
-        auto shrink = [&](auto& small) {
-            constexpr int M = sizeof(small.task) / sizeof(TcTask);
-            small.n_tasks = ea->n_tasks; small.n_tiles = ea->n_tiles; small.n_reds = ea->n_reds; small.pad = 0;
-            for (int i = 0; i < ea->n_tasks; ++i) {
-                small.task[i] = ea->task[i]; small.slot_begin[i] = ea->slot_begin[i];
-                small.tn[i] = ea->tn[i]; small.ns[i] = ea->ns[i];
-            }
-            for (int i = 0; i <= ea->n_tasks; ++i) { small.tile_begin[i] = ea->tile_begin[i]; small.red_begin[i] = ea->red_begin[i]; }
-            (void)M;
-        };
-        if (ea->n_tasks <= 16) {
-            ExpandArgs<16> a16;
-            shrink(a16);
-            k_expand_tiles<16><<<g, 256, 0, stream>>>(a16, bf.d_tasks, bf.d_tiles, bf.d_reds);
-        } else if (ea->n_tasks <= 64) {
-            ExpandArgs<64> a64;
-            shrink(a64);
-            k_expand_tiles<64><<<g, 256, 0, stream>>>(a64, bf.d_tasks, bf.d_tiles, bf.d_reds);
-        } else {
-            k_expand_tiles<EXP_MAXT><<<g, 256, 0, stream>>>(*ea, bf.d_tasks, bf.d_tiles, bf.d_reds);
-        }
-        count_launch();
-    } else {
-        RSD_CUDA_TRY(cudaMemcpyAsync(bf.d_tasks, stage_host(h, tt.data(), tt.size() * sizeof(TcTask)),
+    if (st->mode == 0) {                                   // direct: upload this launch's lists
+        RSD_TRY(grow(bf.d_tasks, bf.cap_tasks, tt.size(), sizeof(TcTask)));
+        RSD_TRY(grow(bf.d_tiles, bf.cap_tiles, tl.size(), sizeof(TcTile)));
+        if (!rd.empty()) RSD_TRY(grow(bf.d_reds, bf.cap_reds, rd.size(), sizeof(TcRed)));
+        d_tasks = bf.d_tasks;
+        d_tiles = bf.d_tiles;
+        d_reds = bf.d_reds;
+        RSD_CUDA_TRY(cudaMemcpyAsync(d_tasks, stage_host(h, tt.data(), tt.size() * sizeof(TcTask)),
                                      tt.size() * sizeof(TcTask), cudaMemcpyHostToDevice, stream));
-        RSD_CUDA_TRY(cudaMemcpyAsync(bf.d_tiles, stage_host(h, tl.data(), tl.size() * sizeof(TcTile)),
+        RSD_CUDA_TRY(cudaMemcpyAsync(d_tiles, stage_host(h, tl.data(), tl.size() * sizeof(TcTile)),
                                      tl.size() * sizeof(TcTile), cudaMemcpyHostToDevice, stream));
         if (!rd.empty())
-            RSD_CUDA_TRY(cudaMemcpyAsync(bf.d_reds, stage_host(h, rd.data(), rd.size() * sizeof(TcRed)),
+            RSD_CUDA_TRY(cudaMemcpyAsync(d_reds, stage_host(h, rd.data(), rd.size() * sizeof(TcRed)),
                                          rd.size() * sizeof(TcRed), cudaMemcpyHostToDevice, stream));
-    }
     }
     if (!st->attr_set) {
         RSD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<128, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<128, 3>::TOTAL));
