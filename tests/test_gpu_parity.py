@@ -260,3 +260,27 @@ def test_graph_replayed_apply_matches_direct_launches(rsd):
         ug2, sg2 = hg.solve(prob["b"], tol=1e-10)
         assert sg2["iterations"] == sg["iterations"]
         assert torch.equal(ug2, ug)
+
+
+def test_lookahead_setup_is_deterministic(rsd):
+    """The two-stream look-ahead factorisation of a root with many 512-wide panels gives
+    bitwise the same factors on every setup, profiled (an event around each launch) or
+    not: every read of a panel block is ordered after all writes to it."""
+    n, depth = 41, 1
+    w = _work(n, depth, True)
+    prob = rsd.grid_problem(n, depth, w["kappa"], w["f"])
+    kw = dict(prec_leaf=rsd.RSD_PREC_TF32, prec_mid=rsd.RSD_PREC_TF32, prec_root=rsd.RSD_PREC_TF32)
+    root = [t for t, p in enumerate(prob["parent"]) if p < 0][0]
+    ref = None
+    for profile in (True, False, False, False):
+        h = rsd.RSD.setup(prob["rowptr"], prob["col"], prob["val"], prob["dof_node"], prob["parent"],
+                          profile=profile, **kw)
+        assert h.front_dims(root)[0] > 3 * 512
+        u, st = h.solve(prob["b"], tol=1e-10)
+        got = (h.front_factor(root), st["iterations"], u.cpu())
+        if ref is None:
+            ref = got
+            continue
+        assert np.array_equal(got[0], ref[0])
+        assert got[1] == ref[1]
+        assert torch.equal(got[2], ref[2])
