@@ -815,11 +815,11 @@ static int factor_level_tc(Handle& h, int li, bool lookahead) {
             // the remaining rows below and the K range [K0, K0+W) of panel p+1's outer update
             // for its rows below the diagonal block.  Events: ev_ready (bulk: panel p+1's long
             // update done), ev_diag[0] (chain: Linv of panel p), ev_diag[1 + p % 2] (chain:
-            // X_next of panel p), ev_diag[3] (bulk: panel p's contribution to the rows of
-            // panel p+2's diagonal block in panel p+1, which chain(p+1)'s X_next overwrites).
-            // The bulk solves and updates those rows first, so the chain rarely waits for
-            // them.  Linv alternates between two buffers, so the chain can build panel p+1's
-            // while the bulk still solves with panel p's.
+            // X_next of panel p), ev_diag[3] (bulk: panel p's contribution to panel p+1 below
+            // its diagonal block, which includes the rows chain(p+1)'s X_next overwrites; the
+            // two short bulk launches before it finish while the chain factors its block).
+            // Linv alternates between two buffers, so the chain can build panel p+1's while
+            // the bulk still solves with panel p's.
             cudaEvent_t& ev_linv = h.ev_diag[0];
             cudaEvent_t& ev_rest = h.ev_diag[3];
             if (!dry) RSD_CUDA_TRY(cudaEventRecord(h.ev_ready, B));             // the fronts are assembled
@@ -837,8 +837,6 @@ static int factor_level_tc(Handle& h, int li, bool lookahead) {
                 if (!dry) RSD_CUDA_TRY(cudaEventRecord(ev_linv, Cs));
                 auto next_lo = [&](const FrontDesc& f) { return wend(f, K0); };
                 auto next_hi = [&](const FrontDesc& f) { return f.s > K0n ? wend(f, K0n) : wend(f, K0); };
-                // end of the rows of panel p+2's diagonal block (empty past the front's end)
-                auto next2_hi = [&](const FrontDesc& f) { return std::max(next_hi(f), wend(f, K0n + WOUT)); };
                 if (p + 1 < np) {
                     // X_next overwrites rows that panel p-1's bulk update also writes
                     if (p >= 1 && !dry) RSD_CUDA_TRY(cudaStreamWaitEvent(Cs, ev_rest, 0));
@@ -855,23 +853,14 @@ static int factor_level_tc(Handle& h, int li, bool lookahead) {
                     if (!dry) RSD_CUDA_TRY(cudaEventRecord(h.ev_ready, B));
                 }
                 if (!dry) RSD_CUDA_TRY(cudaStreamWaitEvent(B, ev_linv, 0));
-                // the rows of panel p+2's diagonal block first: solve, then panel p's part of
-                // their update in panel p+1 (chain(p+1) waits for it before its X_next)
-                RSD_TRY(solve_rows(K0, which, next_hi, next2_hi, B, 0, bulk_ctas));
+                RSD_TRY(solve_rows(K0, which, next_hi, rows_to_end, B, 0, bulk_ctas));
                 if (p + 1 < np) {
                     if (!dry) RSD_CUDA_TRY(cudaStreamWaitEvent(B, ev_xnext, 0));
                     tasks.clear();
                     for (auto& f : L.fronts)
-                        if (f.s > K0n) add_outer(f, K0n, K0, K0n, wend(f, K0n), next2_hi(f));
+                        if (f.s > K0n) add_outer(f, K0n, K0, K0n, wend(f, K0n), f.N);
                     RSD_TRY(gemm_tc_launch(h, li, tasks, 3, B, 0, bulk_ctas));
                     if (!dry) RSD_CUDA_TRY(cudaEventRecord(ev_rest, B));
-                }
-                RSD_TRY(solve_rows(K0, which, next2_hi, rows_to_end, B, 0, bulk_ctas));
-                if (p + 1 < np) {
-                    tasks.clear();
-                    for (auto& f : L.fronts)
-                        if (f.s > K0n) add_outer(f, K0n, K0, K0n, next2_hi(f), f.N);
-                    RSD_TRY(gemm_tc_launch(h, li, tasks, 3, B, 0, bulk_ctas));
                 }
             }
             if (!dry) RSD_CUDA_TRY(cudaEventRecord(h.ev_join, Cs));

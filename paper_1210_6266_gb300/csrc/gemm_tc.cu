@@ -34,6 +34,7 @@ constexpr int BK = 32;                       // FP32 elements per 128-byte swizz
 constexpr int TC_THREADS = 192;
 constexpr long long TC_WAIT_CYCLES = 2000000000LL;   // ~1 s
 constexpr int SPLIT_MIN_KB = 16;             // at least 16 x 32 K per split-K slice
+constexpr int TILE_BAND = 16;                // row blocks per band of a wide output's tile order
 
 // One CTA's work: output tile (tm, tn) of a task over K blocks [kb0, kb1).  ws_slot < 0:
 // write C directly; otherwise write the raw partial product to workspace slot ws_slot
@@ -659,11 +660,18 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
         // panel-solve results are final factor entries
         t.round_tf32 = kind == TC_GENERAL ? g.round : (kind == 1);
         const int tm = (g.M + BM - 1) / BM, tn = (g.N + bn - 1) / bn;
-        for (int a = 0; a < tm; ++a)
-            for (int b = 0; b < tn; ++b) {
-                if (g.lower && b * bn > a * BM + BM - 1) continue;
-                out.push_back({(int)i, a, b});
-            }
+        // The persistent kernel runs consecutive tiles at the same time.  Wide outputs
+        // (U -= X X^T) are walked in bands of TILE_BAND row blocks, column block by
+        // column block, so the tiles in flight share TILE_BAND A row blocks and a run of
+        // B row blocks instead of one A row block and up to a wave of distinct B row
+        // blocks, each as long as K.
+        const int band = tn > 2 ? TILE_BAND : 1;
+        for (int a0 = 0; a0 < tm; a0 += band)
+            for (int b = 0; b < tn; ++b)
+                for (int a = a0; a < std::min(tm, a0 + band); ++a) {
+                    if (g.lower && b * bn > a * BM + BM - 1) continue;
+                    out.push_back({(int)i, a, b});
+                }
     }
     if (out.empty()) return RSD_OK;
     // split K when the output tiles cannot fill the GPU (never for the in-place panel solve)
