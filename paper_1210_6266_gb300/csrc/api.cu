@@ -939,19 +939,22 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
     RSD_TRY(gemm_tc_prepare(h));
     h.prof.host_part[5] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_plan).count();
     // ---- numeric setup, deepest level first ----
+    // Every level's fronts (disjoint arena regions) are zeroed and receive their K entries
+    // up front, leaves first: the device does this while the host plans the leaf level.
+    for (int d = nl - 1; d >= 0; --d) {
+        RSD_TRY(launch_zero_fronts(h, d));
+        RSD_TRY(launch_assemble_fronts(h, d, h.d_rowptr, h.d_col, h.d_val, d_owner, d_rank, d_tin, d_tout));
+    }
     if (!paper) {
         const auto t_issue = std::chrono::steady_clock::now();
         for (int d = nl - 1; d >= 0; --d) {
-            RSD_TRY(launch_assemble_fronts(h, d, h.d_rowptr, h.d_col, h.d_val, d_owner, d_rank, d_tin, d_tout));
             RSD_TRY(launch_extend_add(h, d));
             RSD_TRY(run_factor_level(h, d));
         }
         h.prof.host_issue_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_issue).count();
     } else {
-        // every interface front is K_II plus leaf updates: assemble all, factor the
-        // leaves, scatter their updates into S~, then factor the interfaces
-        for (int d = nl - 1; d >= 0; --d)
-            RSD_TRY(launch_assemble_fronts(h, d, h.d_rowptr, h.d_col, h.d_val, d_owner, d_rank, d_tin, d_tout));
+        // every interface front is K_II plus leaf updates: factor the leaves, scatter
+        // their updates into S~, then factor the interfaces
         RSD_TRY(run_factor_level(h, nl - 1));
         RSD_TRY(paper_extend_add(h));
         for (int d = nl - 2; d >= 0; --d) RSD_TRY(run_factor_level(h, d));

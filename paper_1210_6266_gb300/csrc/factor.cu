@@ -507,13 +507,19 @@ int finalize_tasks(std::vector<GemmTask>& tasks, int tile_m, int tile_n) {
 
 }  // namespace
 
+int launch_zero_fronts(Handle& h, int li) {
+    Level& L = h.levels[li];
+    if (L.fronts.empty()) return RSD_OK;
+    RSD_CUDA_TRY(cudaMemsetAsync(L.fronts[0].P, 0, L.bytes_P, h.stream));
+    if (L.bytes_U) RSD_CUDA_TRY(cudaMemsetAsync(L.fronts[0].U, 0, L.bytes_U, h.stream));
+    return RSD_OK;
+}
+
 int launch_assemble_fronts(Handle& h, int li, const int64_t* rowptr, const int* col,
                            const double* val, const int* owner, const int* rank, const int* tin,
                            const int* tout) {
     Level& L = h.levels[li];
     if (L.fronts.empty()) return RSD_OK;
-    RSD_CUDA_TRY(cudaMemsetAsync(L.fronts[0].P, 0, L.bytes_P, h.stream));
-    if (L.bytes_U) RSD_CUDA_TRY(cudaMemsetAsync(L.fronts[0].U, 0, L.bytes_U, h.stream));
     dim3 grid((unsigned)std::max(1, std::min(64, (L.max_s + 7) / 8)), (unsigned)L.fronts.size());
     const int pi = prof_begin(h, K_ASSEMBLE);
     if (is_fp64(L.prec))

@@ -229,6 +229,8 @@ int gemm_tc_launch(Handle& h, int li, const std::vector<GemmTask>& tasks, int ki
                    int slot = 0, int max_ctas = 0);
 
 // ---- kernels launched from the host orchestration -------------------------------
+// Zero the P and U storage of every front of level li (before its assembly).
+int launch_zero_fronts(Handle& h, int li);
 int launch_assemble_fronts(Handle& h, int li, const int64_t* rowptr, const int* col,
                            const double* val, const int* owner, const int* rank,
                            const int* tin, const int* tout);
