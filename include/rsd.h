@@ -115,8 +115,9 @@ typedef struct {
  * substitution sweeps read every stored factor element once).  Classes:
  * 0 front assembly, 1 extend-add, 2 tcgen05 GEMM, 3 CUDA-core GEMM, 4 diagonal block
  * factor+inverse, 5 CUDA-core panel solve, 6 upward sweep, 7 downward sweep,
- * 8 sweep gathers, 9 Krylov vector/SpMV kernels.                                    */
-#define RSD_PROFILE_CLASSES 10
+ * 8 sweep gathers, 9 Krylov vector/SpMV kernels, 10 FP16 copy of a TF32 level's factor
+ * (the entries the sweeps read).                                                      */
+#define RSD_PROFILE_CLASSES 11
 typedef struct {
     int64_t launches[RSD_PROFILE_CLASSES];
     double  ms[RSD_PROFILE_CLASSES];
@@ -242,6 +243,16 @@ int rsd_front_map(rsd_handle h, int32_t node, int32_t* out);
  * the Cholesky factor of the interface Schur complement (lower triangle, zeros above);
  * rows s..s+b-1 hold X_t = K~_BI L_t^-T, the coupling to the ancestors.              */
 int rsd_front_factor(rsd_handle h, int32_t node, double* out);
+/* FP16 copy of that factor which the substitution sweeps of a TF32 level read, unscaled
+ * to FP64 in the same (s + b) x s layout: the entries below the NB x NB diagonal blocks
+ * of L_t and all of X_t (Eq. 3.2 and 3.3 use L_t through its inverted diagonal blocks
+ * and these entries); zeros elsewhere.  Row i is stored as rs_i times the entry, rs_i a
+ * power of two with sqrt(K_ii) rs_i in [2^13, 2^14); every stored entry is a TF32 value
+ * and |entry| <= sqrt(K_ii), so the copy equals rsd_front_factor except for entries
+ * below 2^-27 sqrt(K_ii), which it holds to 2^-38 sqrt(K_ii).
+ * Errors: RSD_ERR_ARG for a bad node or a node whose level has no copy (FP32 / FP64
+ * fronts, paper mode).                                                                */
+int rsd_front_factor16(rsd_handle h, int32_t node, double* out);
 
 /* rsd_profile -- synchronise the handle's stream and sum the profile recorded since
  * setup or the last reset (all zeros unless rsd_options.profile was set).  reset != 0

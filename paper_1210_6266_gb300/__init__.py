@@ -254,6 +254,13 @@ class RSD:
         check(_lib.load().rsd_front_factor(self._h, node, out.ctypes.data), "rsd_front_factor")
         return out[: (s + b) * s].reshape(s + b, s)
 
+    def front_factor16(self, node: int) -> np.ndarray:
+        """The FP16 factor copy a TF32 level's sweeps read, unscaled (rsd_front_factor16)."""
+        s, b, _ = self.front_dims(node)
+        out = np.empty((s + b) * max(s, 1), dtype=np.float64)
+        check(_lib.load().rsd_front_factor16(self._h, node, out.ctypes.data), "rsd_front_factor16")
+        return out[: (s + b) * s].reshape(s + b, s)
+
 
 class DiffusionSolve(torch.autograd.Function):
     """u = K(exp(m))^-1 b for -div(kappa grad u) = f on the n^3 grid, differentiable in the

@@ -32,7 +32,7 @@ RSD_MEM_DEVICE = 1
 # every function include/rsd.h declares (checked by the tests)
 EXPORTS = [
     "rsd_setup", "rsd_apply", "rsd_solve", "rsd_check", "rsd_destroy", "rsd_strerror",
-    "rsd_get_info", "rsd_front_dims", "rsd_front_dofs", "rsd_front_map", "rsd_front_factor",
+    "rsd_get_info", "rsd_front_dims", "rsd_front_dofs", "rsd_front_map", "rsd_front_factor", "rsd_front_factor16",
     "rsd_grid_sizes", "rsd_grid_assemble", "rsd_grid_load", "rsd_grid_partition",
     "rsd_profile", "rsd_launch_count", "rsd_apply_static", "rsd_last_error_detail",
     "rsd_release_cache", "rsd_setup_batched", "rsd_solve_adjoint", "rsd_grid_exp",
@@ -68,12 +68,12 @@ class rsd_info_t(C.Structure):
 
 
 PROFILE_CLASSES = ["assemble", "extend_add", "gemm_tcgen05", "gemm_simt", "diag_factor",
-                   "panel_solve_simt", "sweep_up", "sweep_down", "sweep_gather", "krylov"]
+                   "panel_solve_simt", "sweep_up", "sweep_down", "sweep_gather", "krylov", "factor_copy16"]
 
 
 class rsd_profile_t(C.Structure):
-    _fields_ = [("launches", C.c_int64 * 10), ("ms", C.c_double * 10), ("flops", C.c_double * 10),
-                ("bytes", C.c_double * 10), ("host_analysis_ms", C.c_double),
+    _fields_ = [("launches", C.c_int64 * 11), ("ms", C.c_double * 11), ("flops", C.c_double * 11),
+                ("bytes", C.c_double * 11), ("host_analysis_ms", C.c_double),
                 ("host_parts_ms", C.c_double * 6), ("host_issue_ms", C.c_double)]
 
 
@@ -108,6 +108,7 @@ def load() -> C.CDLL:
             "rsd_front_dofs": (C.c_int, [P, C.c_int32, P]),
             "rsd_front_map": (C.c_int, [P, C.c_int32, P]),
             "rsd_front_factor": (C.c_int, [P, C.c_int32, P]),
+            "rsd_front_factor16": (C.c_int, [P, C.c_int32, P]),
             "rsd_grid_sizes": (C.c_int, [C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
             "rsd_grid_assemble": (C.c_int, [C.c_int32, P, P, P, P, P]),
             "rsd_grid_load": (C.c_int, [C.c_int32, P, P, P]),

@@ -20,6 +20,8 @@
 #include <numeric>
 #include <thread>
 
+#include <cuda_fp16.h>
+
 #include "rsd_internal.cuh"
 
 namespace rsd {
@@ -715,13 +717,14 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
     const size_t o_B = take(sizeof(int) * std::max<size_t>(1, h.B_dofs.size()));
     const size_t o_ea = take(sizeof(int) * std::max<size_t>(1, ea_all.size()));
     const size_t o_flags = take(sizeof(int) * 2 * a.n_nodes);
-    struct FrontPlan { size_t P, U, D, V; };
+    struct FrontPlan { size_t P, U, D, V, H, R; };
     std::vector<FrontPlan> fp(a.n_nodes);
     std::vector<size_t> lvlP(nl), lvlU(nl);
     h.factor_elems = 0; h.factor_bytes = 0; h.setup_flops = 0;
     for (int d = nl - 1; d >= 0; --d) {
         Level& L = h.levels[d];
         const size_t es = elem_bytes(L.prec);
+        L.h16 = L.prec == RSD_PREC_TF32 && !paper;
         // P regions of a level are contiguous, then the U regions
         lvlP[d] = off;
         for (int t : L.nodes) {
@@ -746,6 +749,13 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
             fp[t].D = take((size_t)std::max(1, nd) * NB * NB * es);
             fp[t].V = take((size_t)(s + b + 32) * es);
         }
+        if (L.h16)                                   // FP16 factor copies after the level's other regions
+            for (int t : L.nodes) {
+                const int s = a.I_off[t + 1] - a.I_off[t], b = beff(t);
+                const int ldp = std::max(32, round_up(s, 32));
+                fp[t].H = take((size_t)(s + b) * ldp * 2);
+                fp[t].R = take((size_t)2 * (s + b) * sizeof(float));
+            }
     }
     const size_t o_fronts = take(sizeof(FrontDesc) * a.n_nodes);
     size_t n_items = 16;
@@ -844,6 +854,9 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
             f.U = A + fp[t].U;
             f.Dinv = A + fp[t].D;
             f.vec = A + fp[t].V;
+            f.P16 = L.h16 ? A + fp[t].H : nullptr;
+            f.rs = L.h16 ? (const float*)(A + fp[t].R) : nullptr;
+            f.ri = L.h16 ? f.rs + f.N : nullptr;
             f.I = d_I + a.I_off[t];
             f.Bd = d_B + h.B_off[t];
             f.ea = d_ea + h.B_off[t];
@@ -950,6 +963,7 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
         for (int d = nl - 1; d >= 0; --d) {
             RSD_TRY(launch_extend_add(h, d));
             RSD_TRY(run_factor_level(h, d));
+            RSD_TRY(launch_factor_copy16(h, d));
         }
         h.prof.host_issue_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_issue).count();
     } else {
@@ -1020,6 +1034,8 @@ extern "C" void rsd_release_cache(void) {
     }
     cudaSetDevice(cur);
 }
+
+static_assert(K_CLASSES == RSD_PROFILE_CLASSES, "profile classes of the ABI and the kernels differ");
 
 extern "C" int rsd_profile(rsd_handle hh, rsd_profile_t* out, int32_t reset) {
     if (!hh || !out) return RSD_ERR_ARG;
@@ -1243,6 +1259,25 @@ extern "C" int rsd_front_map(rsd_handle hh, int32_t node, int32_t* out) {
     const FrontDesc& f = L.fronts[h.node_slot[node]];
     if (f.b == 0) return RSD_OK;
     RSD_CUDA_TRY(cudaMemcpy(out, f.ea, sizeof(int) * f.b, cudaMemcpyDeviceToHost));
+    return RSD_OK;
+}
+
+extern "C" int rsd_front_factor16(rsd_handle hh, int32_t node, double* out) {
+    if (!hh || !out || node < 0 || node >= hh->h.n_nodes) return RSD_ERR_ARG;
+    Handle& h = hh->h;
+    const Level& L = h.levels[h.node_level[node]];
+    const FrontDesc& f = L.fronts[h.node_slot[node]];
+    if (!f.P16) return RSD_ERR_ARG;
+    RSD_CUDA_TRY(cudaStreamSynchronize(h.stream));
+    std::vector<__half> q((size_t)f.N * f.ldp);
+    std::vector<float> rs((size_t)2 * f.N);
+    if (!q.empty()) RSD_CUDA_TRY(cudaMemcpy(q.data(), f.P16, q.size() * sizeof(__half), cudaMemcpyDeviceToHost));
+    if (!rs.empty()) RSD_CUDA_TRY(cudaMemcpy(rs.data(), f.rs, rs.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    for (int r = 0; r < f.N; ++r)
+        for (int c = 0; c < f.s; ++c) {
+            const bool read = r >= f.s || c / NB < r / NB;       // what the sweeps read
+            out[(size_t)r * f.s + c] = read ? (double)__half2float(q[(size_t)r * f.ldp + c]) * (double)rs[f.N + r] : 0.0;
+        }
     return RSD_OK;
 }
 

@@ -13,7 +13,10 @@
 // co-residency).  A block that consumes a result from another block polls that front's
 // progress counter with a bounded wait; on timeout it raises ERR_TIMEOUT and proceeds.
 // The factor is streamed once per sweep with 16-byte non-coherent loads.
+#include <cuda_fp16.h>
+
 #include <algorithm>
+#include <climits>
 
 #include "rsd_internal.cuh"
 
@@ -36,6 +39,36 @@ template <> __device__ __forceinline__ float ld_cg(const float* p) { return __ld
 template <> __device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
 
 __device__ __forceinline__ int ld_volatile(const int* p) { return *(volatile const int*)p; }
+
+// A level with the FP16 factor copy (H = true, T = float) streams it instead of P: row i
+// holds rs[i] P[i, :] with rs[i] a power of two, so a sweep multiplies a row's partial
+// sum by ri[i] (forward) or the row's x by ri[i] (backward) -- the products and sums of
+// the FP32 factor, scaled by powers of two, except for entries below 2^-27 sqrt(K_ii),
+// which the copy holds as FP16 subnormals.  A lane reads 8 entries (16 B) per load, so
+// a step covers two column blocks (forward) or two row blocks (backward) with as many
+// bytes in flight as the FP32 loop.
+template <typename T, bool H> struct PType { using type = T; };
+template <typename T> struct PType<T, true> { using type = __half; };
+
+// Two FP16 entries packed in a word (lower address in the low half) widened to FP32.
+__device__ __forceinline__ float h_lo(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu))); }
+__device__ __forceinline__ float h_hi(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w >> 16))); }
+
+__device__ __forceinline__ void h8_to_f(const uint4& u, float (&o)[8]) {
+    o[0] = h_lo(u.x); o[1] = h_hi(u.x); o[2] = h_lo(u.y); o[3] = h_hi(u.y);
+    o[4] = h_lo(u.z); o[5] = h_hi(u.z); o[6] = h_lo(u.w); o[7] = h_hi(u.w);
+}
+
+// Shared-memory factor block entries as V (four entries; FP16 widened).
+template <typename T, bool H>
+__device__ __forceinline__ typename Vec<T>::V lds_v(const typename PType<T, H>::type* p) {
+    if constexpr (H) {
+        const uint2 u = *reinterpret_cast<const uint2*>(p);
+        return make_float4(h_lo(u.x), h_hi(u.x), h_lo(u.y), h_hi(u.y));
+    } else {
+        return *reinterpret_cast<const typename Vec<T>::V*>(p);
+    }
+}
 
 // Asynchronous copies into shared memory (16 B per cp.async, L2 only), committed by
 // cp_async_commit() and completed by cp_async_wait() before use: `count` consecutive
@@ -129,20 +162,22 @@ __global__ void k_fwd_gather(const FrontDesc* __restrict__ fronts, const FrontDe
 // -- publishing the front's progress counter after each block, so the dependency chain
 // between CTAs waits on one item per GD blocks while the next item already consumes
 // the group's first block.
-template <typename T, typename A, int GD>
+template <typename T, typename A, int GD, bool H>
 __global__ void __launch_bounds__(AT, GD == 1 ? 2 : 1) k_fwd_sweep(const FrontDesc* __restrict__ fronts,
                                                      const int* __restrict__ items, int n_items,
                                                      int* __restrict__ ticket, int* __restrict__ err) {
     using V = typename Vec<T>::V;
+    using PT = typename PType<T, H>::type;
     constexpr int VW = Vec<T>::W;
     constexpr int PASSES = NB / (32 * VW);
     constexpr int RPW = NB / AW;                 // rows per warp and block
     __shared__ int s_item, s_flag;
     __shared__ __align__(16) A s_t[GD * NB];
     __shared__ __align__(16) A s_y[NB];
+    __shared__ float s_ri[H ? GD * NB : 1];      // row factors of the item's rows (FP16 copy)
     extern __shared__ __align__(16) unsigned char sweep_smem[];
     T* Ds = (T*)sweep_smem;                      // GD inverted diagonal blocks
-    T* Ls = Ds + GD * NB * NB;                   // P[block b0+1 rows, block b0 columns]
+    PT* Ls = (PT*)(Ds + GD * NB * NB);           // P[block b0+1 rows, block b0 columns]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(ticket, 1);
@@ -154,7 +189,7 @@ __global__ void __launch_bounds__(AT, GD == 1 ? 2 : 1) k_fwd_sweep(const FrontDe
         const FrontDesc f = fronts[slot];
         const bool diag = blk < f.nd;
         const int nb = diag ? min(GD, f.nd - blk) : 1;
-        const T* P = (const T*)f.P;
+        const PT* P = (const PT*)(H ? f.P16 : f.P);
         A* v = (A*)f.vec;
         const int r0 = diag ? blk * NB : f.s + (blk - f.nd) * NB;
         const int r1 = diag ? min(r0 + nb * NB, f.s) : min(r0 + NB, f.N);
@@ -164,6 +199,9 @@ __global__ void __launch_bounds__(AT, GD == 1 ? 2 : 1) k_fwd_sweep(const FrontDe
             cp_async_commit();
         }
         for (int q = threadIdx.x; q < GD * NB; q += AT) s_t[q] = (r0 + q < r1) ? ld_cg(v + r0 + q) : (A)0;
+        if constexpr (H) {
+            for (int q = threadIdx.x; q < GD * NB; q += AT) s_ri[q] = (r0 + q < r1) ? f.ri[r0 + q] : 0.f;
+        }
         const int ncb = diag ? blk : f.nd;
         A acc[GD][RPW];
 #pragma unroll
@@ -171,6 +209,36 @@ __global__ void __launch_bounds__(AT, GD == 1 ? 2 : 1) k_fwd_sweep(const FrontDe
 #pragma unroll
             for (int u = 0; u < RPW; ++u) acc[g][u] = 0;
         int seen = 0;
+        if constexpr (H) {
+            const int cend = min(ncb * NB, f.s);
+            for (int cb = 0; cb < ncb; cb += 2) {
+                const int c0 = cb * NB, cw = min(2 * NB, cend - c0), cl = lane * 8;
+                uint4 l[GD][RPW];
+#pragma unroll
+                for (int g = 0; g < GD; ++g)
+#pragma unroll
+                    for (int u = 0; u < RPW; ++u) {
+                        const int row = r0 + g * NB + warp + AW * u;
+                        l[g][u] = (g < nb && row < r1 && cl < cw) ? __ldg((const uint4*)(P + (int64_t)row * f.ldp + c0 + cl))
+                                                                  : make_uint4(0u, 0u, 0u, 0u);
+                    }
+                const int need = min(cb + 2, ncb);
+                if (seen < need) seen = wait_flag(&f.flag[0], need, err, &s_flag);
+                float y[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) y[e] = (cl + e < cw) ? ld_cg(v + c0 + cl + e) : 0.f;
+                const int valid = cw - cl;               // entries of this lane's eight inside the step
+#pragma unroll
+                for (int g = 0; g < GD; ++g)
+#pragma unroll
+                    for (int u = 0; u < RPW; ++u) {
+                        float pv[8];
+                        h8_to_f(l[g][u], pv);
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) acc[g][u] += (e < valid ? pv[e] : 0.f) * y[e];
+                    }
+            }
+        } else {
         for (int cb = 0; cb < ncb; ++cb) {
             const int c0 = cb * NB;
             const int cw = min(NB, f.s - c0);
@@ -197,6 +265,7 @@ __global__ void __launch_bounds__(AT, GD == 1 ? 2 : 1) k_fwd_sweep(const FrontDe
                         for (int e = 0; e < VW; ++e) acc[g][u] += (A)vget(l[g][u], e) * y[e];
             }
         }
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
@@ -210,7 +279,11 @@ __global__ void __launch_bounds__(AT, GD == 1 ? 2 : 1) k_fwd_sweep(const FrontDe
 #pragma unroll
                 for (int u = 0; u < RPW; ++u) {
                     const int q = g * NB + warp + AW * u;
-                    if (r0 + q < r1) s_t[q] -= acc[g][u];
+                    if constexpr (H) {
+                        if (r0 + q < r1) s_t[q] -= acc[g][u] * s_ri[q];
+                    } else {
+                        if (r0 + q < r1) s_t[q] -= acc[g][u];
+                    }
                 }
         }
         __syncthreads();
@@ -236,7 +309,7 @@ __global__ void __launch_bounds__(AT, GD == 1 ? 2 : 1) k_fwd_sweep(const FrontDe
                     for (int e = 0; e < VW; ++e) yv[e] = s_y[cl + e];
 #pragma unroll
                     for (int u = 0; u < RPW; ++u) {
-                        const V d = *(const V*)(Ls + (warp + AW * u) * NB + cl);
+                        const V d = lds_v<T, H>(Ls + (warp + AW * u) * NB + cl);
 #pragma unroll
                         for (int e = 0; e < VW; ++e) part[u] += (A)vget(d, e) * yv[e];
                     }
@@ -249,7 +322,11 @@ __global__ void __launch_bounds__(AT, GD == 1 ? 2 : 1) k_fwd_sweep(const FrontDe
 #pragma unroll
                     for (int u = 0; u < RPW; ++u) {
                         const int rr = warp + AW * u;
-                        if (rr < w) s_t[g * NB + rr] -= part[u];
+                        if constexpr (H) {
+                            if (rr < w) s_t[g * NB + rr] -= part[u] * s_ri[g * NB + rr];
+                        } else {
+                            if (rr < w) s_t[g * NB + rr] -= part[u];
+                        }
                     }
                 }
                 __syncthreads();
@@ -308,12 +385,13 @@ __global__ void k_bwd_gather(const FrontDesc* __restrict__ fronts, const double*
 // waiting for its x); then inside the CTA x_hi = Dinv_hi^T t_hi,
 // t_lo -= P[hi rows, lo columns]^T x_hi, x_lo = Dinv_lo^T t_lo, each block published
 // as soon as it is done.
-template <typename T, typename A, int GD>
+template <typename T, typename A, int GD, bool H>
 __global__ void __launch_bounds__(AT, GD == 1 ? 2 : 1) k_bwd_sweep(const FrontDesc* __restrict__ fronts,
                                                      const int* __restrict__ items, int n_items,
                                                      int* __restrict__ ticket, int* __restrict__ err,
                                                      double* __restrict__ z) {
     using V = typename Vec<T>::V;
+    using PT = typename PType<T, H>::type;
     constexpr int VW = Vec<T>::W;
     constexpr int PASSES = NB / (32 * VW);
     constexpr int RB = 16 / PASSES;              // rows per warp per batch (a whole row block for FP32)
@@ -321,9 +399,10 @@ __global__ void __launch_bounds__(AT, GD == 1 ? 2 : 1) k_bwd_sweep(const FrontDe
     __shared__ A s_red[AW][GD * NB];
     __shared__ A s_t[GD * NB];
     __shared__ A s_x[NB];
+    __shared__ float s_rih[H && GD > 1 ? NB : 1];   // row factors of block hi (FP16 copy)
     extern __shared__ __align__(16) unsigned char sweep_smem[];
     T* Ds = (T*)sweep_smem;                      // Dinv_hi, Dinv_lo
-    T* Ls = Ds + GD * NB * NB;                   // P[hi rows, lo columns]
+    PT* Ls = (PT*)(Ds + GD * NB * NB);           // P[hi rows, lo columns]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(ticket, 1);
@@ -334,7 +413,7 @@ __global__ void __launch_bounds__(AT, GD == 1 ? 2 : 1) k_bwd_sweep(const FrontDe
         const int slot = items[it] >> 16, hi = items[it] & 0xffff;
         const FrontDesc f = fronts[slot];
         const int nb = min(GD, hi + 1), lo = hi - nb + 1;
-        const T* P = (const T*)f.P;
+        const PT* P = (const PT*)(H ? f.P16 : f.P);
         A* v = (A*)f.vec;
         const int c0 = lo * NB, c1 = min((hi + 1) * NB, f.s), cw = c1 - c0;
         const int whi = min(NB, f.s - hi * NB);
@@ -344,6 +423,65 @@ __global__ void __launch_bounds__(AT, GD == 1 ? 2 : 1) k_bwd_sweep(const FrontDe
             prefetch_rows(Ls, P + (int64_t)hi * NB * f.ldp + lo * NB, f.ldp, whi);
         }
         cp_async_commit();
+        if constexpr (H && GD > 1) {
+            for (int q = threadIdx.x; q < NB; q += AT) s_rih[q] = q < whi ? f.ri[hi * NB + q] : 0.f;
+        }
+        int seen = 0;
+        const int n_groups_B = (f.b + NB - 1) / NB;
+        const int n_groups = n_groups_B + (f.nd - 1 - hi);
+        if constexpr (H) {
+            // row groups HW at a time (consecutive groups are adjacent row ranges); for a
+            // single block the two half-warps take alternate rows, 16 lanes x 8 entries each
+            constexpr int HW = GD == 1 ? 2 : 1;
+            const int sub = GD == 1 ? lane >> 4 : 0;
+            const int cl = GD == 1 ? (lane & 15) * 8 : lane * 8;
+            float acc8[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) acc8[e] = 0.f;
+            for (int gr = 0; gr < n_groups; gr += HW) {
+                int rlo = INT_MAX, rhi = 0, need = 0;
+                for (int k = 0; k < HW && gr + k < n_groups; ++k) {
+                    const int gk = gr + k;
+                    int g0, g1;
+                    if (gk < n_groups_B) {
+                        g0 = f.s + (n_groups_B - 1 - gk) * NB; g1 = min(g0 + NB, f.N);
+                    } else {
+                        const int rb = f.nd - 1 - (gk - n_groups_B);
+                        need = max(need, f.nd - rb);
+                        g0 = rb * NB; g1 = min(g0 + NB, f.s);
+                    }
+                    rlo = min(rlo, g0);
+                    rhi = max(rhi, g1);
+                }
+                uint4 l[RB];
+                float rsc[RB];
+#pragma unroll
+                for (int u = 0; u < RB; ++u) {
+                    const int row = rlo + (warp + AW * u) * HW + sub;
+                    const bool in = row < rhi;
+                    l[u] = (in && cl < cw) ? __ldg((const uint4*)(P + (int64_t)row * f.ldp + c0 + cl)) : make_uint4(0u, 0u, 0u, 0u);
+                    rsc[u] = in ? f.ri[row] : 0.f;
+                }
+                if (seen < need) seen = wait_flag(&f.flag[1], need, err, &s_flag);
+#pragma unroll
+                for (int u = 0; u < RB; ++u) {
+                    const int row = rlo + (warp + AW * u) * HW + sub;
+                    const float x = row < rhi ? ld_cg(v + row) * rsc[u] : 0.f;
+                    float pv[8];
+                    h8_to_f(l[u], pv);
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) acc8[e] += pv[e] * x;
+                }
+            }
+            if (GD == 1) {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) acc8[e] += __shfl_xor_sync(0xffffffffu, acc8[e], 16);
+            }
+            if (GD > 1 || lane < 16) {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) s_red[warp][cl + e] = acc8[e];
+            }
+        } else {
         A acc[GD][PASSES][VW];
 #pragma unroll
         for (int g = 0; g < GD; ++g)
@@ -351,9 +489,6 @@ __global__ void __launch_bounds__(AT, GD == 1 ? 2 : 1) k_bwd_sweep(const FrontDe
             for (int ps = 0; ps < PASSES; ++ps)
 #pragma unroll
                 for (int e = 0; e < VW; ++e) acc[g][ps][e] = 0;
-        int seen = 0;
-        const int n_groups_B = (f.b + NB - 1) / NB;
-        const int n_groups = n_groups_B + (f.nd - 1 - hi);
         for (int gr = 0; gr < n_groups; ++gr) {
             int g0, g1, need = 0;
             if (gr < n_groups_B) {
@@ -399,6 +534,7 @@ __global__ void __launch_bounds__(AT, GD == 1 ? 2 : 1) k_bwd_sweep(const FrontDe
             for (int ps = 0; ps < PASSES; ++ps)
 #pragma unroll
                 for (int e = 0; e < VW; ++e) s_red[warp][g * NB + ps * 32 * VW + lane * VW + e] = acc[g][ps][e];
+        }
         __syncthreads();
         for (int c = threadIdx.x; c < GD * NB; c += AT) {
             A sum = 0;
@@ -421,10 +557,11 @@ __global__ void __launch_bounds__(AT, GD == 1 ? 2 : 1) k_bwd_sweep(const FrontDe
 #pragma unroll
                     for (int e = 0; e < VW; ++e) part[ps][e] = 0;
                 for (int rr = warp; rr < whi; rr += AW) {
-                    const A xr = s_x[rr];
+                    A xr = s_x[rr];
+                    if constexpr (H) xr *= s_rih[rr];
 #pragma unroll
                     for (int ps = 0; ps < PASSES; ++ps) {
-                        const V d = *(const V*)(Ls + rr * NB + ps * 32 * VW + lane * VW);
+                        const V d = lds_v<T, H>(Ls + rr * NB + ps * 32 * VW + lane * VW);
 #pragma unroll
                         for (int e = 0; e < VW; ++e) part[ps][e] += (A)vget(d, e) * xr;
                     }
@@ -477,47 +614,71 @@ __global__ void __launch_bounds__(AT, GD == 1 ? 2 : 1) k_bwd_sweep(const FrontDe
     }
 }
 
+// Bytes one sweep streams from the factor: the off-diagonal blocks of L and X (FP16 for a
+// level with the FP16 copy) and the inverted diagonal blocks.
 double level_factor_bytes(const Level& L) {
-    double e = 0;
-    for (auto& f : L.fronts) e += 0.5 * f.s * (f.s + 1.0) + (double)f.s * f.b;
-    return e * elem_bytes(L.prec);
+    double e = 0, d = 0;
+    for (auto& f : L.fronts) {
+        e += 0.5 * f.s * (f.s + 1.0) + (double)f.s * f.b;
+        for (int k = 0; k < f.nd; ++k) {
+            const double w = std::min(NB, f.s - k * NB);
+            e -= 0.5 * w * (w + 1.0);
+        }
+        d += (double)f.nd * NB * NB;
+    }
+    return e * (L.h16 ? 2.0 : (double)elem_bytes(L.prec)) + d * elem_bytes(L.prec);
 }
 
 // Dynamic shared memory of the sweep kernels: GD inverted diagonal blocks plus, for
-// GD = 2, one factor block.
-template <typename T, int GD> constexpr int sweep_dsm() { return (GD + (GD > 1 ? 1 : 0)) * NB * NB * (int)sizeof(T); }
+// GD = 2, one factor block (FP16 when read from the copy).
+template <typename T, int GD, bool H> constexpr int sweep_dsm() {
+    return GD * NB * NB * (int)sizeof(T) + (GD > 1 ? NB * NB * (int)sizeof(typename PType<T, H>::type) : 0);
+}
+
+template <typename T, typename A, int GD, bool H>
+int sweep_attr() {
+    RSD_CUDA_TRY(cudaFuncSetAttribute(k_fwd_sweep<T, A, GD, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, sweep_dsm<T, GD, H>()));
+    RSD_CUDA_TRY(cudaFuncSetAttribute(k_bwd_sweep<T, A, GD, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, sweep_dsm<T, GD, H>()));
+    return RSD_OK;
+}
 
 template <typename T, typename A>
 int sweep_smem_setup() {
     static bool done = false;
     if (!done) {
-        RSD_CUDA_TRY(cudaFuncSetAttribute(k_fwd_sweep<T, A, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sweep_dsm<T, 1>()));
-        RSD_CUDA_TRY(cudaFuncSetAttribute(k_bwd_sweep<T, A, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sweep_dsm<T, 1>()));
+        RSD_TRY((sweep_attr<T, A, 1, false>()));
         if constexpr (sizeof(T) == 4) {
-            RSD_CUDA_TRY(cudaFuncSetAttribute(k_fwd_sweep<T, A, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sweep_dsm<T, 2>()));
-            RSD_CUDA_TRY(cudaFuncSetAttribute(k_bwd_sweep<T, A, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sweep_dsm<T, 2>()));
+            RSD_TRY((sweep_attr<T, A, 2, false>()));
+            RSD_TRY((sweep_attr<T, A, 1, true>()));
+            RSD_TRY((sweep_attr<T, A, 2, true>()));
         }
         done = true;
     }
     return RSD_OK;
 }
 
-// Launch the upward / downward sweep kernel with the level's group size.
+// Launch the upward / downward sweep kernel with the level's group size, reading the
+// FP16 factor copy when the level has one.
 template <typename T, typename A>
-void launch_fwd(int gd, int grid, cudaStream_t st, const FrontDesc* fr, const int* items, int n, int* tk, int* err) {
+void launch_fwd(int gd, bool h16, int grid, cudaStream_t st, const FrontDesc* fr, const int* items, int n, int* tk,
+                int* err) {
     if constexpr (sizeof(T) == 4) {
-        if (gd == 2) { k_fwd_sweep<T, A, 2><<<grid, AT, sweep_dsm<T, 2>(), st>>>(fr, items, n, tk, err); return; }
+        if (h16 && gd == 2) { k_fwd_sweep<T, A, 2, true><<<grid, AT, sweep_dsm<T, 2, true>(), st>>>(fr, items, n, tk, err); return; }
+        if (h16) { k_fwd_sweep<T, A, 1, true><<<grid, AT, sweep_dsm<T, 1, true>(), st>>>(fr, items, n, tk, err); return; }
+        if (gd == 2) { k_fwd_sweep<T, A, 2, false><<<grid, AT, sweep_dsm<T, 2, false>(), st>>>(fr, items, n, tk, err); return; }
     }
-    k_fwd_sweep<T, A, 1><<<grid, AT, sweep_dsm<T, 1>(), st>>>(fr, items, n, tk, err);
+    k_fwd_sweep<T, A, 1, false><<<grid, AT, sweep_dsm<T, 1, false>(), st>>>(fr, items, n, tk, err);
 }
 
 template <typename T, typename A>
-void launch_bwd(int gd, int grid, cudaStream_t st, const FrontDesc* fr, const int* items, int n, int* tk, int* err,
-                double* z) {
+void launch_bwd(int gd, bool h16, int grid, cudaStream_t st, const FrontDesc* fr, const int* items, int n, int* tk,
+                int* err, double* z) {
     if constexpr (sizeof(T) == 4) {
-        if (gd == 2) { k_bwd_sweep<T, A, 2><<<grid, AT, sweep_dsm<T, 2>(), st>>>(fr, items, n, tk, err, z); return; }
+        if (h16 && gd == 2) { k_bwd_sweep<T, A, 2, true><<<grid, AT, sweep_dsm<T, 2, true>(), st>>>(fr, items, n, tk, err, z); return; }
+        if (h16) { k_bwd_sweep<T, A, 1, true><<<grid, AT, sweep_dsm<T, 1, true>(), st>>>(fr, items, n, tk, err, z); return; }
+        if (gd == 2) { k_bwd_sweep<T, A, 2, false><<<grid, AT, sweep_dsm<T, 2, false>(), st>>>(fr, items, n, tk, err, z); return; }
     }
-    k_bwd_sweep<T, A, 1><<<grid, AT, sweep_dsm<T, 1>(), st>>>(fr, items, n, tk, err, z);
+    k_bwd_sweep<T, A, 1, false><<<grid, AT, sweep_dsm<T, 1, false>(), st>>>(fr, items, n, tk, err, z);
 }
 
 template <typename T, typename A>
@@ -546,7 +707,7 @@ int sweep_level(Handle& h, int li, bool forward, const double* r, double* z, int
         RSD_CUDA_TRY(cudaGetLastError());
         if (L.n_fwd_items) {
             const int pi = prof_begin(h, K_FWD);
-            launch_fwd<T, A>(sweep_group(L), grid, h.stream, L.d_fronts, L.d_fwd_items, L.n_fwd_items, h.d_ticket + tk, h.d_err);
+            launch_fwd<T, A>(sweep_group(L), L.h16, grid, h.stream, L.d_fronts, L.d_fwd_items, L.n_fwd_items, h.d_ticket + tk, h.d_err);
             count_launch();
             prof_end(h, pi, fbytes / sizeof(T) * 2.0, fbytes);
         }
@@ -558,7 +719,7 @@ int sweep_level(Handle& h, int li, bool forward, const double* r, double* z, int
         RSD_CUDA_TRY(cudaGetLastError());
         if (L.n_bwd_items) {
             const int pi = prof_begin(h, K_BWD);
-            launch_bwd<T, A>(sweep_group(L), grid, h.stream, L.d_fronts, L.d_bwd_items, L.n_bwd_items, h.d_ticket + tk, h.d_err, z);
+            launch_bwd<T, A>(sweep_group(L), L.h16, grid, h.stream, L.d_fronts, L.d_bwd_items, L.n_bwd_items, h.d_ticket + tk, h.d_err, z);
             count_launch();
             prof_end(h, pi, fbytes / sizeof(T) * 2.0, fbytes);
         }
@@ -622,7 +783,7 @@ int sweep_level_static(Handle& h, int li, bool forward, const double* r, double*
         count_launch();
         RSD_CUDA_TRY(cudaGetLastError());
         if (L.n_fwd_items) {
-            launch_fwd<T, A>(sweep_group(L), grid, h.stream, fr, L.d_fwd_items, L.n_fwd_items, ticket, h.d_err);
+            launch_fwd<T, A>(sweep_group(L), L.h16, grid, h.stream, fr, L.d_fwd_items, L.n_fwd_items, ticket, h.d_err);
             count_launch();
         }
     } else {
@@ -630,7 +791,7 @@ int sweep_level_static(Handle& h, int li, bool forward, const double* r, double*
         count_launch();
         RSD_CUDA_TRY(cudaGetLastError());
         if (L.n_bwd_items) {
-            launch_bwd<T, A>(sweep_group(L), grid, h.stream, fr, L.d_bwd_items, L.n_bwd_items, ticket, h.d_err, z);
+            launch_bwd<T, A>(sweep_group(L), L.h16, grid, h.stream, fr, L.d_bwd_items, L.n_bwd_items, ticket, h.d_err, z);
             count_launch();
         }
     }
@@ -715,13 +876,13 @@ int sweep_with(Handle& h, int li, bool forward, const FrontDesc* fronts, const i
         count_launch();
         RSD_CUDA_TRY(cudaGetLastError());
         if (n_items) {
-            if (f64) launch_fwd<double, double>(sweep_group(L), grid, h.stream, fronts, items, n_items, ticket, h.d_err);
-            else launch_fwd<float, float>(sweep_group(L), grid, h.stream, fronts, items, n_items, ticket, h.d_err);
+            if (f64) launch_fwd<double, double>(sweep_group(L), false, grid, h.stream, fronts, items, n_items, ticket, h.d_err);
+            else launch_fwd<float, float>(sweep_group(L), L.h16, grid, h.stream, fronts, items, n_items, ticket, h.d_err);
             count_launch();
         }
     } else if (n_items) {
-        if (f64) launch_bwd<double, double>(sweep_group(L), grid, h.stream, fronts, items, n_items, ticket, h.d_err, out);
-        else launch_bwd<float, float>(sweep_group(L), grid, h.stream, fronts, items, n_items, ticket, h.d_err, out);
+        if (f64) launch_bwd<double, double>(sweep_group(L), false, grid, h.stream, fronts, items, n_items, ticket, h.d_err, out);
+        else launch_bwd<float, float>(sweep_group(L), L.h16, grid, h.stream, fronts, items, n_items, ticket, h.d_err, out);
         count_launch();
     }
     RSD_CUDA_TRY(cudaGetLastError());

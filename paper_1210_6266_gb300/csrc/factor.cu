@@ -21,6 +21,8 @@
 #include <cmath>
 #include <type_traits>
 
+#include <cuda_fp16.h>
+
 #include "rsd_internal.cuh"
 
 namespace rsd {
@@ -507,6 +509,78 @@ int finalize_tasks(std::vector<GemmTask>& tasks, int tile_m, int tile_n) {
 
 }  // namespace
 
+// Row scales of the FP16 factor copy: with sqrt(K_ii) = m 2^x, m in [0.5, 1), rs[i] =
+// 2^(14 - x) puts sqrt(K_ii) rs[i] in [2^13, 2^14), a factor 4 below FP16's largest
+// value, which bounds every entry of the row (the front's diagonal entry is a Schur
+// complement's, at most K_ii).  ri[i] = 1 / rs[i] follows rs in memory.
+__global__ void k_row_scale(const FrontDesc* __restrict__ fronts, const int64_t* __restrict__ rowptr,
+                            const int* __restrict__ col, const double* __restrict__ val) {
+    const FrontDesc f = fronts[blockIdx.x];
+    float* rs = (float*)f.rs;
+    for (int i = blockIdx.y * blockDim.x + threadIdx.x; i < f.N; i += gridDim.y * blockDim.x) {
+        const int dof = i < f.s ? f.I[i] : f.Bd[i - f.s];
+        double kii = 0.0;
+        for (int64_t k = rowptr[dof]; k < rowptr[dof + 1]; ++k)
+            if (col[k] == dof) { kii = val[k]; break; }
+        int x = 0;
+        if (kii > 0.0 && kii <= 1e300) frexp(sqrt(kii), &x);
+        const int e = max(-120, min(120, 14 - x));
+        rs[i] = ldexpf(1.0f, e);
+        rs[f.N + i] = ldexpf(1.0f, -e);
+    }
+}
+
+// Two values rounded to FP16 and packed in a word, the first in the low half (the lower
+// address).
+__device__ __forceinline__ uint32_t pack_h2(float lo, float hi) {
+    return (uint32_t)__half_as_ushort(__float2half_rn(lo)) | ((uint32_t)__half_as_ushort(__float2half_rn(hi)) << 16);
+}
+
+// FP16 copy of the factor entries the sweeps read: row i, columns below its diagonal
+// block (i < s) or all s columns (B rows), each scaled by rs[i].  One warp per row,
+// eight entries (32 B in, 16 B out) per lane and step.  The entries are TF32 values, so
+// the copy is exact wherever the scaled value is an FP16 normal.
+__global__ void __launch_bounds__(256) k_copy16(const FrontDesc* __restrict__ fronts) {
+    const FrontDesc f = fronts[blockIdx.x];
+    const float* P = (const float*)f.P;
+    __half* Q = (__half*)f.P16;
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int i = blockIdx.y * wpb + (threadIdx.x >> 5); i < f.N; i += gridDim.y * wpb) {
+        const int cend = i < f.s ? (i / NB) * NB : f.s;
+        const float sc = f.rs[i];
+        const float* src = P + (int64_t)i * f.ldp;
+        __half* dst = Q + (int64_t)i * f.ldp;
+        for (int c = lane * 8; c < cend; c += 256) {
+            if (c + 8 <= cend) {
+                const float4 a = __ldcs((const float4*)(src + c)), b = __ldcs((const float4*)(src + c + 4));
+                uint4 o;
+                o.x = pack_h2(a.x * sc, a.y * sc);
+                o.y = pack_h2(a.z * sc, a.w * sc);
+                o.z = pack_h2(b.x * sc, b.y * sc);
+                o.w = pack_h2(b.z * sc, b.w * sc);
+                *reinterpret_cast<uint4*>(dst + c) = o;
+            } else {
+                for (int e = 0; c + e < cend; ++e) dst[c + e] = __float2half_rn(src[c + e] * sc);
+            }
+        }
+    }
+}
+
+int launch_factor_copy16(Handle& h, int li) {
+    Level& L = h.levels[li];
+    if (!L.h16 || L.fronts.empty()) return RSD_OK;
+    const int nf = (int)L.fronts.size();
+    double bytes = 0;
+    for (auto& f : L.fronts) bytes += 6.0 * (0.5 * f.s * (f.s + 1.0) + (double)f.s * f.b);
+    const dim3 g((unsigned)nf, (unsigned)std::max(1, std::min((L.max_N + 7) / 8, (h.num_sms * 8 + nf - 1) / nf)));
+    const int pi = prof_begin(h, K_COPY16);
+    k_copy16<<<g, 256, 0, h.stream>>>(L.d_fronts);
+    count_launch();
+    prof_end(h, pi, 0.0, bytes);
+    RSD_CUDA_TRY(cudaGetLastError());
+    return RSD_OK;
+}
+
 int launch_zero_fronts(Handle& h, int li) {
     Level& L = h.levels[li];
     if (L.fronts.empty()) return RSD_OK;
@@ -527,6 +601,11 @@ int launch_assemble_fronts(Handle& h, int li, const int64_t* rowptr, const int* 
     else
         k_scatter_K<float><<<grid, 256, 0, h.stream>>>(L.d_fronts, rowptr, col, val, owner, rank, tin, tout);
     count_launch();
+    if (L.h16) {
+        const dim3 g((unsigned)L.fronts.size(), (unsigned)std::max(1, std::min(16, (L.max_N + 1023) / 1024)));
+        k_row_scale<<<g, 256, 0, h.stream>>>(L.d_fronts, rowptr, col, val);
+        count_launch();
+    }
     {
         double rows = 0;
         for (auto& f : L.fronts) rows += f.s;

@@ -55,6 +55,15 @@ struct FrontDesc {
     void* vec;                 // apply: front vector (N entries, level accumulator type)
     int* flag;                 // apply: progress counters [forward, backward]
     int child_begin, child_count;   // into the level's child-slot table (previous level)
+    // TF32 levels: FP16 copy of the factor entries the substitution sweeps read (the
+    // off-diagonal blocks of L and X, same layout and ldp as P), row i scaled by the power
+    // of two rs[i]; ri[i] = 1 / rs[i].  Every entry is TF32-rounded when final, and
+    // |P_ij| <= sqrt(K_ii) (a Schur complement's diagonal never exceeds K's), so with
+    // sqrt(K_ii) rs[i] in [2^13, 2^14) the copy is exact down to 2^-27 sqrt(K_ii).
+    // nullptr elsewhere.
+    void* P16;
+    const float* rs;
+    const float* ri;
 };
 
 // Batched GEMM task: C = beta*C - A * B^T over an M x N block (row-major operands,
@@ -78,7 +87,7 @@ struct GemmTask {
 
 // Kernel classes for launch counting and the optional CUDA-event profile.
 enum KClass { K_ASSEMBLE = 0, K_EXTEND, K_GEMM_TC, K_GEMM_SIMT, K_POTRF, K_TRSM, K_FWD, K_BWD,
-              K_GATHER, K_KRYLOV, K_CLASSES };
+              K_GATHER, K_KRYLOV, K_COPY16, K_CLASSES };
 
 // Per-handle profile: one event pair per launch of a class, with the algorithmic
 // flops and bytes of that launch; reduced on demand by rsd_profile().
@@ -111,6 +120,7 @@ struct Level {
     // the level below
     int* d_child_slots = nullptr;
     size_t bytes_P = 0, bytes_U = 0;
+    bool h16 = false;                    // fronts carry the FP16 factor copy (P16, rs, ri)
     // paper mode: descriptors of the same fronts restricted to their interface block
     // (b = 0, no children) and forward items over interface blocks only, used by the
     // leaf and interface solves of the level-wise Algorithm 2
@@ -231,6 +241,8 @@ int gemm_tc_launch(Handle& h, int li, const std::vector<GemmTask>& tasks, int ki
 // ---- kernels launched from the host orchestration -------------------------------
 // Zero the P and U storage of every front of level li (before its assembly).
 int launch_zero_fronts(Handle& h, int li);
+// FP16 copy of level li's factor (after its factorisation), read by the sweeps.
+int launch_factor_copy16(Handle& h, int li);
 int launch_assemble_fronts(Handle& h, int li, const int64_t* rowptr, const int* col,
                            const double* val, const int* owner, const int* rank,
                            const int* tin, const int* tout);

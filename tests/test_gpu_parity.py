@@ -284,3 +284,31 @@ def test_lookahead_setup_is_deterministic(rsd):
         assert np.array_equal(got[0], ref[0])
         assert got[1] == ref[1]
         assert torch.equal(got[2], ref[2])
+
+
+@pytest.mark.parametrize("n,depth", [(17, 2), (26, 1), (20, 2)])
+def test_fp16_factor_copy_holds_the_tf32_factor(rsd, n, depth):
+    """A TF32 level's sweeps read an FP16 copy of the factor, row i scaled by a power of two
+    set from sqrt(K_ii).  Every entry they read is bounded by sqrt(K_ii) (a Cholesky row's
+    2-norm is the square root of a Schur complement's diagonal entry, at most K_ii), and
+    the copy equals the TF32 factor exactly except for entries below 2^-27 sqrt(K_ii)
+    (FP16 subnormals after scaling), which it holds to 2^-38 sqrt(K_ii)."""
+    w = _work(n, depth, True)
+    A, b, owner, parent, sym, _ = _oracle(w)
+    prob = rsd.grid_problem(n, depth, w["kappa"], w["f"])
+    h = _setup(rsd, prob, rsd.RSD_PREC_TF32, root=rsd.RSD_PREC_TF32)
+    sq = np.sqrt(A.diagonal())
+    for t in range(len(prob["parent"])):
+        s, bb, _ = h.front_dims(t)
+        P, Q = h.front_factor(t), h.front_factor16(t)
+        bound = np.repeat(sq[h.front_dofs(t)][:, None], s, axis=1)
+        rows, cols = np.arange(s + bb)[:, None], np.arange(s)[None, :]
+        read = (rows >= s) | (cols // 128 < rows // 128)
+        assert np.all(Q[~read] == 0.0)
+        assert np.all(np.abs(P[read]) <= bound[read] * 1.01), t
+        big = read & (np.abs(P) >= 2.0**-27 * bound)
+        assert np.array_equal(Q[big], P[big]), t
+        assert np.all(np.abs(Q - P)[read] <= 2.0**-38 * bound[read]), t
+    h32 = _setup(rsd, prob, rsd.RSD_PREC_FP32, root=rsd.RSD_PREC_FP32)
+    with pytest.raises(rsd.RSDError):
+        h32.front_factor16(0)
