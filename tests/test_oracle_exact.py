@@ -81,3 +81,29 @@ def test_leaf_update_is_negative_schur_term():
     L, X = fac.L[t], fac.X[t]
     assert np.abs((-X @ X.T) - Uref).max() <= 1e-12 * np.abs(Uref).max()
     assert np.abs(L @ L.T - KII).max() <= 1e-13 * np.abs(KII).max()
+
+
+@pytest.mark.parametrize("n,depth,logn", CASES)
+def test_factor_rows_bounded_by_sqrt_diagonal(n, depth, logn):
+    """Every row of a front's factor [L_t; X_t] has 2-norm at most sqrt(K_ii), i the row's
+    DOF.  For L_t the squared row norm is the diagonal entry of the interface Schur
+    complement S_t (Eq. 3.2); for X_t it is at most -U_t[i, i], and K_BB + U_t is the Schur
+    complement left on B_t after the subtree is eliminated.  A Schur complement of an SPD
+    matrix is SPD with diagonal at most K's, so both are bounded by K_ii.  The GPU path
+    scales each factor row by a power of two chosen from sqrt(K_ii) before storing it in
+    FP16, which relies on this bound."""
+    A, sym = _case(n, depth, logn)
+    fac = ExactFactor(A, sym)
+    d = A.diagonal()
+    checked = 0
+    for t in range(sym.n_nodes):
+        I, Bt = np.asarray(sym.I[t]), np.asarray(sym.B[t])
+        if fac.L[t].size:
+            rn = np.linalg.norm(fac.L[t], axis=1)
+            assert np.all(rn <= np.sqrt(d[I]) * (1 + 1e-12)), t
+            assert np.allclose(rn ** 2, np.diag(fac.S[t]), rtol=1e-10)
+            checked += len(I)
+        if fac.X[t].size:
+            assert np.all(np.linalg.norm(fac.X[t], axis=1) <= np.sqrt(d[Bt]) * (1 + 1e-12)), t
+            checked += len(Bt)
+    assert checked > A.shape[0]
