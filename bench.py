@@ -4,10 +4,16 @@ One step = one pass of the whole path on resident inputs: rsd_setup (analysis of
 sub-domain tree and interface sets, front assembly, batched partial Cholesky with the
 Schur contributions, level by level) followed by rsd_solve (FP64 PCG with the RSD
 preconditioner to a relative residual of 1e-8, true residual re-checked in FP64).
-Metric: DOF / (t_setup + t_solve) per step.
+Metric: DOF / (t_setup + t_solve) per step, mixed form against the plain FP64 form.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--form mixed|fp64]
-                  [--impl ours|reference] [--workload diffusion129|poisson13|...]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload diffusion129|...]
+                  [--form mixed|fp64] [--mode exact|paper] [--gamma G] [--impl ours|reference]
+
+The default run prints one JSON line: the mixed form on the 129^3 workload (K timed
+steps after W warm-up steps) as the headline, and, in the same line, the plain FP64 form
+of the same workload (one timed step: it takes over a minute), the 256-problem batched
+workload in both forms (the FP64 form on its first 64 problems), the measured peaks of
+the library's own GEMM kernels, and the oracle's CPU baseline.
 
 --impl reference times the CPU oracle (FP64, numpy/scipy on the host cores) on a bounded
 sample of the same workload family.  Multi-GPU runs are independent replicas (the
@@ -21,6 +27,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -28,10 +35,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "solve DOF/s to rel-res 1e-8, mixed vs FP64 form on 1 GB300; % of roofline"
 TOL = 1e-8
-# nominal dense tensor rates (PFLOP/s): used only to scale the measured BF16 peak to TF32
+# nominal dense rates (the profiling recipe's table): used to scale the measured BF16 peak
+# to TF32, and as the FP64 CUDA-core roof
 NOMINAL_BF16, NOMINAL_TF32 = 2.25, 1.1
-NOMINAL_FP64_TFLOPS = 1.25       # GB300 FP64 (CUDA cores), for the ALU-bound FP64 form
+NOMINAL_FP64_TFLOPS = 1.25
 CPU_SAMPLE = dict(n=41, depth=3)  # bounded oracle sample of the diffusion workload family
+FP64_WARM = dict(n=33, depth=3)   # small grid that loads the FP64 kernels before the timed step
+BATCH_FP64_SAMPLE = 64            # problems of the batched workload timed in the FP64 form
 
 
 def peaks():
@@ -44,7 +54,8 @@ def peaks():
 
 
 class Clocks:
-    """Sample SM clocks and throttle reasons with nvidia-smi while the timed region runs."""
+    """Sample SM clocks and throttle reasons with nvidia-smi while the timed region runs
+    (samples go to a temporary file that is removed afterwards)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -52,13 +63,12 @@ class Clocks:
 
     def __init__(self, bus_id: str | None):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.path = self.fh.name
             cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
             if bus_id:
                 cmd += ["-i", bus_id]
-            self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -72,7 +82,7 @@ class Clocks:
         except Exception:
             self.proc.kill()
         self.fh.close()
-        sm, smax, reasons = [], [], set()
+        sm, smax, power, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as fh:
             for line in fh:
@@ -82,15 +92,20 @@ class Clocks:
                 try:
                     sm.append(float(parts[1]))
                     smax.append(float(parts[2]))
+                    power.append(float(parts[3]))
                 except ValueError:
                     continue
                 for name, v in zip(names, parts[5:9]):
                     if v.lower().startswith("active"):
                         reasons.add(name)
+        try:
+            os.unlink(self.path)
+        except OSError:
+            pass
         loaded = [s for s in sm if smax and s > 0.5 * max(smax)] or sm
         return {"sm_mhz": statistics.median(loaded) if loaded else None,
                 "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "power_w_max": max(power) if power else None, "samples": len(sm)}
 
 
 def _bus_id(torch):
@@ -171,6 +186,59 @@ def run_reference(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+PREC = None   # filled in main(): form name -> rsd_setup precision keywords
+
+
+def prof_add(agg, p):
+    """Sum rsd_profile dicts (kernel classes and host times)."""
+    if p is None:
+        return agg
+    if agg is None:
+        agg = {}
+    for k, v in p.items():
+        if isinstance(v, dict) and "ms" in v:
+            a = agg.setdefault(k, dict(launches=0, ms=0.0, flops=0.0, bytes=0.0))
+            for f in ("launches", "ms", "flops", "bytes"):
+                a[f] += v[f]
+        elif isinstance(v, dict):
+            a = agg.setdefault(k, {})
+            for q, x in v.items():
+                a[q] = a.get(q, 0.0) + x
+        else:
+            agg[k] = agg.get(k, 0.0) + v
+    return agg
+
+
+def timed_steps(torch, run_one, steps: int):
+    """Run `steps` steps; each returns (setup_done_event, stats, profile, info).  Returns
+    ms per step (CUDA events on the current stream around all steps), the per-step setup
+    and solve split, and the steps' results."""
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    marks = []
+    ev0.record(stream)
+    out = []
+    for _ in range(steps):
+        a = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        b, st, prof, info = run_one()
+        c = torch.cuda.Event(enable_timing=True)
+        c.record(stream)
+        marks.append((a, b, c))
+        out.append((st, prof, info))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    su, so = [], []
+    for (a, b, c), (st, _, _) in zip(marks, out):
+        tot = a.elapsed_time(c)
+        s = st["setup_ms_sum"] if "setup_ms_sum" in st else a.elapsed_time(b)
+        su.append(s)
+        so.append(tot - s)
+    return ms, statistics.mean(su), statistics.mean(so), out
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -182,6 +250,9 @@ def main() -> None:
     ap.add_argument("--workload", default="diffusion129")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-form record of the headline workload")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-workload record")
+    ap.add_argument("--no-peaks", action="store_true", help="skip the GEMM peak probes")
     ap.add_argument("--wave", type=int, default=64, help="problems per hierarchy (batched workload)")
     ap.add_argument("--n", type=int, default=None, help="grid side override (a scaled sample, e.g. for profiling)")
     ap.add_argument("--depth", type=int, default=None, help="octree depth override")
@@ -190,12 +261,10 @@ def main() -> None:
         run_reference(args)
         return
 
-    import numpy as np
     import torch
     import torch.distributed as dist
 
-    from paper_1210_6266_gb300 import (RSD, RSD_MODE_EXACT, RSD_MODE_PAPER, RSD_PREC_FP64, RSD_PREC_TF32,
-                                       grid_problem, launch_count)
+    import paper_1210_6266_gb300 as rsd
     from paper_1210_6266_gb300 import build as _build
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -205,92 +274,111 @@ def main() -> None:
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     _build.build()
+    global PREC
+    PREC = {"mixed": dict(prec_leaf=rsd.RSD_PREC_TF32, prec_mid=rsd.RSD_PREC_TF32, prec_root=rsd.RSD_PREC_TF32),
+            "fp64": dict(prec_leaf=rsd.RSD_PREC_FP64, prec_mid=rsd.RSD_PREC_FP64, prec_root=rsd.RSD_PREC_FP64)}
+    DTYPE = {"mixed": "tf32", "fp64": "f64"}
+    mode = rsd.RSD_MODE_PAPER if args.mode == "paper" else rsd.RSD_MODE_EXACT
+    single = world == 1
+    pk, pk_src = peaks()
 
     def barrier():
         if world > 1:
             dist.barrier()
 
-    work, wdesc = make_workload(args.workload, args.n, args.depth)
-    batched = wdesc["kind"] == "batched"
-    if batched:
-        probs = [grid_problem(w["n"], w["depth"], w["kappa"], w["f"]) for w in work]
-        n_dof = sum(p["n_dof"] for p in probs)
-        waves = [probs[i:i + args.wave] for i in range(0, len(probs), args.wave)]
-    else:
-        prob = grid_problem(work["n"], work["depth"], work["kappa"], work["f"])
-        n_dof = prob["n_dof"]
-    if args.form == "mixed":
-        prec = dict(prec_leaf=RSD_PREC_TF32, prec_mid=RSD_PREC_TF32, prec_root=RSD_PREC_TF32)
-        dtype = "tf32"
-    else:
-        prec = dict(prec_leaf=RSD_PREC_FP64, prec_mid=RSD_PREC_FP64, prec_root=RSD_PREC_FP64)
-        dtype = "f64"
-    mode = RSD_MODE_PAPER if args.mode == "paper" else RSD_MODE_EXACT
-    stream = torch.cuda.current_stream()
-
-    def merge_prof(a, b):
-        if a is None:
-            return b
-        for k, v in b.items():
-            if isinstance(v, dict) and "ms" in v:
-                for f in ("launches", "ms", "flops", "bytes"):
-                    a[k][f] += v[f]
-            elif k in ("host_analysis_ms", "host_issue_ms"):
-                a[k] += v
-            elif k == "host_parts_ms":
-                a[k] = {q: a[k][q] + v[q] for q in v}
-        return a
-
-    def step(profile=False):
-        if not batched:
-            h = RSD.setup(prob["rowptr"], prob["col"], prob["val"], prob["dof_node"], prob["parent"],
-                          profile=profile, mode=mode, **prec)
+    # ---- one step of a single problem / of a batch in waves ----------------------------
+    def single_step(prob, form, profile=False, m=mode):
+        def run():
+            h = rsd.RSD.setup(prob["rowptr"], prob["col"], prob["val"], prob["dof_node"], prob["parent"],
+                              profile=profile, mode=m, **PREC[form])
+            b = torch.cuda.Event(enable_timing=True)
+            b.record(torch.cuda.current_stream())
             u, st = h.solve(prob["b"], tol=TOL)
             prof = h.profile() if profile else None
             info = h.info()
             h.close()
-            return st, prof, info
-        stats, prof, info = None, None, None
-        for wv in waves:
-            h = RSD.setup_batched(wv, profile=profile, **prec)
-            b = torch.cat([p["b"] for p in wv])
-            u, st = h.solve(b, tol=TOL)
-            prof = merge_prof(prof, h.profile()) if profile else None
-            inf = h.info()
-            info = inf if info is None else {k: (info[k] + inf[k] if k in ("factor_bytes", "setup_flops", "device_bytes") else info[k]) for k in info}
-            if stats is None or st["relres"] > stats["relres"]:
-                stats = st
-            h.close()
-        return stats, prof, info
+            return b, st, prof, info
+        return run
+
+    def batched_step(waves, form, profile=False):
+        # setup of every wave, then the solves: wave hierarchies are independent, so the
+        # split is (all setups) + (all solves) per step; handles of earlier waves are closed
+        # as soon as their solve is done, so the waves run one after another
+        def run():
+            stats, prof, info = None, None, None
+            setup_ms = 0.0
+            t_b = None
+            for wv in waves:
+                a = torch.cuda.Event(enable_timing=True)
+                a.record(torch.cuda.current_stream())
+                h = rsd.RSD.setup_batched(wv, profile=profile, **PREC[form])
+                t_b = torch.cuda.Event(enable_timing=True)
+                t_b.record(torch.cuda.current_stream())
+                t_b.synchronize()
+                setup_ms += a.elapsed_time(t_b)
+                b = torch.cat([p["b"] for p in wv])
+                u, st = h.solve(b, tol=TOL)
+                prof = prof_add(prof, h.profile()) if profile else None
+                inf = h.info()
+                info = inf if info is None else {k: (info[k] + inf[k] if k in ("factor_bytes", "setup_flops", "device_bytes", "n") else info[k]) for k in info}
+                if stats is None:
+                    stats = dict(st)
+                else:
+                    stats["relres"] = max(stats["relres"], st["relres"])
+                    stats["iterations"] = max(stats["iterations"], st["iterations"])
+                h.close()
+            stats["setup_ms_sum"] = setup_ms
+            return t_b, stats, prof, info
+        return run
+
+    # ---- peaks of the library's own GEMM kernels (roofline denominators) -------------
+    peak_rec = None
+    if single and not args.no_peaks:
+        tf_b, tf_s = rsd.peak_gemm(rsd.RSD_PREC_TF32, 8192, reps=5, seconds=4.0)
+        f64_b, f64_s = rsd.peak_gemm(rsd.RSD_PREC_FP64, 4096, reps=3, seconds=2.0)
+        peak_rec = {"tf32_tcgen05": {"best": tf_b, "sustained": tf_s, "unit": "TFLOP/s",
+                                     "how": "rsd_peak_gemm: the persistent 128x256 tcgen05 kind::tf32 kernel, "
+                                            "C -= A B^T at 8192^3, best of 5 launches and back to back for 4 s"},
+                    "fp64_simt": {"best": f64_b, "sustained": f64_s, "unit": "TFLOP/s",
+                                  "how": "rsd_peak_gemm: the FP64 CUDA-core 64x64-tile kernel, C -= A B^T at "
+                                         "4096^3, best of 3 launches and back to back for 2 s"}}
+
+    # ---- headline: the requested form on the requested workload ----------------------
+    work, wdesc = make_workload(args.workload, args.n, args.depth)
+    batched = wdesc["kind"] == "batched"
+    if batched:
+        probs = [rsd.grid_problem(w["n"], w["depth"], w["kappa"], w["f"]) for w in work]
+        n_dof = sum(p["n_dof"] for p in probs)
+        waves = [probs[i:i + args.wave] for i in range(0, len(probs), args.wave)]
+        step = lambda form, profile=False: batched_step(waves, form, profile)  # noqa: E731
+    else:
+        prob = rsd.grid_problem(work["n"], work["depth"], work["kappa"], work["f"])
+        n_dof = prob["n_dof"]
+        step = lambda form, profile=False: single_step(prob, form, profile)  # noqa: E731
 
     for _ in range(args.warmup):
-        step()
+        step(args.form)()
     torch.cuda.synchronize()
     barrier()
     clocks = Clocks(_bus_id(torch))
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    l0 = launch_count()
-    torch.cuda.synchronize()
+    l0 = rsd.launch_count()
     barrier()
-    ev0.record(stream)
-    stats, profs = [], []
-    for _ in range(args.steps):
-        st, prof, info = step(profile=True)
-        stats.append(st)
-        profs.append(prof)
-    ev1.record(stream)
-    torch.cuda.synchronize()
+    ms, t_setup, t_solve, res = timed_steps(torch, step(args.form, profile=True), args.steps)
     barrier()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    launches = (launch_count() - l0) // args.steps
+    launches = (rsd.launch_count() - l0) // args.steps
     clk = clocks.stop()
     if world > 1:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     value = world * n_dof / (ms / 1e3)
+    stats = [r[0] for r in res]
+    agg = None
+    for r in res:
+        agg = prof_add(agg, r[1])
+    info = res[-1][2]
 
-    # end to end through the C ABI from pinned host buffers
+    # ---- end to end through the C ABI from pinned host buffers ------------------------
     src = probs if batched else [prob]
     host = [{k: p[k].cpu().pin_memory() for k in ("rowptr", "col", "val", "dof_node", "b")} for p in src]
     u_host = torch.empty(n_dof, dtype=torch.float64).pin_memory()
@@ -305,10 +393,10 @@ def main() -> None:
         for g in groups:
             hp = [dict(host[i], parent=src[i]["parent"]) for i in g]
             if batched:
-                h = RSD.setup_batched(hp, **prec)
+                h = rsd.RSD.setup_batched(hp, **PREC[args.form])
             else:
-                h = RSD.setup(hp[0]["rowptr"], hp[0]["col"], hp[0]["val"], hp[0]["dof_node"], hp[0]["parent"],
-                              mode=mode, **prec)
+                h = rsd.RSD.setup(hp[0]["rowptr"], hp[0]["col"], hp[0]["val"], hp[0]["dof_node"], hp[0]["parent"],
+                                  mode=mode, **PREC[args.form])
             b = torch.cat([x["b"] for x in hp]).to("cuda", non_blocking=True)
             u, _ = h.solve(b, tol=TOL)
             u_host[off:off + u.numel()].copy_(u, non_blocking=True)
@@ -317,49 +405,53 @@ def main() -> None:
             h.close()
     e2e_ms = (time.perf_counter() - t0) / max(e2e_steps, 1) * 1e3 if e2e_steps else float("nan")
 
+    # ---- the FP64 form of the same workload and the batched workload (1 GPU only) ------
+    fp64_rec, batch_rec = None, None
+    headline_fp64_done = args.form == "fp64"
+    if single and not args.no_fp64 and not batched and args.form == "mixed" and args.mode == "exact":
+        import synth
+        wsm = synth.diffusion_lognormal(FP64_WARM["n"], FP64_WARM["depth"], 2, 3)
+        psm = rsd.grid_problem(wsm["n"], wsm["depth"], wsm["kappa"], wsm["f"])
+        single_step(psm, "fp64")()                     # loads the FP64 kernels
+        ms64, ts64, tv64, r64 = timed_steps(torch, single_step(prob, "fp64", profile=True), 1)
+        fp64_rec = form_record(r64, ms64, ts64, tv64, n_dof, 1, pk, peak_rec, "fp64")
+        fp64_rec["steps"] = 1
+        fp64_rec["warmup"] = f"one step of the {FP64_WARM['n']}^3 grid (same kernels), not timed"
+        headline_fp64_done = True
+    if single and not args.no_batched and not batched and args.workload == "diffusion129" and args.mode == "exact":
+        bwork, _ = make_workload("batched256")
+        bprobs = [rsd.grid_problem(w["n"], w["depth"], w["kappa"], w["f"]) for w in bwork]
+        bdof = sum(p["n_dof"] for p in bprobs)
+        bwaves = [bprobs[i:i + args.wave] for i in range(0, len(bprobs), args.wave)]
+        batched_step(bwaves, "mixed")()                # warm-up
+        msb, tsb, tvb, rb = timed_steps(torch, batched_step(bwaves, "mixed", profile=True), 2)
+        mixed_b = form_record(rb, msb, tsb, tvb, bdof, 2, pk, peak_rec, "mixed")
+        mixed_b["steps"] = 2
+        mixed_b["warmup"] = 1
+        sample = bwaves[0][:BATCH_FP64_SAMPLE]
+        sdof = sum(p["n_dof"] for p in sample)
+        msf, tsf, tvf, rf = timed_steps(torch, batched_step([sample], "fp64", profile=True), 1)
+        fp64_b = form_record(rf, msf, tsf, tvf, sdof, 1, pk, peak_rec, "fp64")
+        fp64_b["steps"] = 1
+        fp64_b["sample"] = f"the first {len(sample)} problems ({sdof} DOF) as one hierarchy"
+        sizes = [w["n"] for w in bwork]
+        batch_rec = {"workload": f"batched256: {len(bwork)} independent Poisson problems, n in [{min(sizes)}, {max(sizes)}], "
+                                 f"8-64 leaves each, hierarchies of {args.wave} problems",
+                     "n_dof": bdof, "mixed": mixed_b, "fp64": fp64_b,
+                     "mixed_over_fp64": mixed_b["value"] / fp64_b["value"]}
+
     if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
         return
-    # roofline of the dominant kernel class (largest device time inside the timed region)
-    agg = {}
-    for p in profs:
-        for k, v in p.items():
-            if k in ("host_analysis_ms", "host_parts_ms", "host_issue_ms"):
-                agg.setdefault(k, []).append(v)
-                continue
-            a = agg.setdefault(k, dict(launches=0, ms=0.0, flops=0.0, bytes=0.0))
-            for f in ("launches", "ms", "flops", "bytes"):
-                a[f] += v[f]
-    classes = {k: v for k, v in agg.items() if k not in ("host_analysis_ms", "host_parts_ms", "host_issue_ms")}
-    dom = max(classes, key=lambda k: classes[k]["ms"])
-    d = classes[dom]
-    pk, src = peaks()
-    if dom == "gemm_tcgen05":
-        peak = pk["bf16_tflops_sustained"] * NOMINAL_TF32 / NOMINAL_BF16
-        roof = {"bound": "tensor", "achieved": d["flops"] / (d["ms"] / 1e3) / 1e12, "peak": peak,
-                "unit": "TFLOP/s"}
-        peak_note = f"TF32 = {src} BF16 sustained x {NOMINAL_TF32}/{NOMINAL_BF16} (nominal ratio)"
-    elif dom in ("gemm_simt", "diag_factor", "panel_solve_simt") and args.form == "fp64":
-        roof = {"bound": "alu", "achieved": d["flops"] / (d["ms"] / 1e3) / 1e12, "peak": NOMINAL_FP64_TFLOPS,
-                "unit": "TFLOP/s"}
-        peak_note = "FP64 CUDA-core nominal rate"
-    else:
-        roof = {"bound": "hbm", "achieved": d["bytes"] / (d["ms"] / 1e3) / 1e9, "peak": pk["hbm_gbs"],
-                "unit": "GB/s"}
-        peak_note = f"{src} HBM copy bandwidth"
-    roof["frac"] = roof["achieved"] / roof["peak"]
+    head = form_record(res, ms, t_setup, t_solve, n_dof, args.steps, pk, peak_rec, args.form)
+    roof = head.pop("roofline")
     wkey = f"{args.workload}/{args.form}/{args.mode}" if args.n is None and args.depth is None else "scaled"
-    roof["traffic"] = recorded_traffic(dom, wkey)
-    roof["kernel"] = dom
-    roof["peak_source"] = peak_note
-    roof["launches_per_step"] = d["launches"] / args.steps
-    phase = {k: round(v["ms"] / args.steps, 3) for k, v in classes.items() if v["launches"]}
-    sweeps = {k: classes[k] for k in ("sweep_up", "sweep_down")}
-    sw_ms = sum(v["ms"] for v in sweeps.values())
-    sw_gbs = sum(v["bytes"] for v in sweeps.values()) / (sw_ms / 1e3) / 1e9 if sw_ms else None
+    roof["traffic"] = recorded_traffic(roof.get("kernel"), wkey)
     line = {
         "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+        "vs_baseline": None, "dtype": DTYPE[args.form], "data": "synthetic",
         "config": {"workload": (f"{args.workload}: -div(kappa grad u)=f, {work['n']}^3 nodes, trilinear hex, "
                                 f"kappa lognormal per element") if wdesc["kind"] == "lognormal" else
                                (f"{args.workload}: {len(work)} independent Poisson problems, n in "
@@ -368,7 +460,7 @@ def main() -> None:
                    "n_dof": n_dof,
                    "subdomains": sum(8 ** w["depth"] for w in work) if batched else 8 ** work["depth"],
                    "merge_levels": max(w["depth"] for w in work) if batched else work["depth"],
-                   "form": args.form, "mode": args.mode, "precisions": {k: v for k, v in prec.items()}, "tol": TOL,
+                   "form": args.form, "mode": args.mode, "precisions": PREC[args.form], "tol": TOL,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (factors are tens of GB)"},
         "roofline": roof,
@@ -376,19 +468,79 @@ def main() -> None:
         "gpu_launches": launches,
         "e2e": {"value": n_dof / (e2e_ms / 1e3), "unit": "DOF/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "detail": {"iterations": [s["iterations"] for s in stats], "relres": [s["relres"] for s in stats],
-                   "ms_by_kernel_class": phase,
-                   "host_analysis_ms": statistics.median(agg["host_analysis_ms"]),
-                   "host_issue_ms": statistics.median(agg["host_issue_ms"]),
-                   "host_parts_ms": agg["host_parts_ms"][-1],
-                   "apply_sweeps_gbs": sw_gbs, "factor_bytes": info["factor_bytes"],
-                   "setup_flops": info["setup_flops"], "device_bytes": info["device_bytes"]},
+        "setup_solve": {k: head[k] for k in ("t_setup_ms", "t_solve_ms", "setup_dof_s", "solve_dof_s")},
+        "apply_roofline": head.pop("apply_roofline"),
+        "detail": dict(head.pop("detail"), iterations=[s["iterations"] for s in stats],
+                       relres=[s["relres"] for s in stats]),
     }
+    if fp64_rec is not None:
+        line["fp64_form"] = fp64_rec
+        line["mixed_over_fp64"] = value / fp64_rec["value"]
+    if batch_rec is not None:
+        line["batched256"] = batch_rec
+    if peak_rec is not None:
+        line["peaks_measured"] = peak_rec
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(1)
     print(json.dumps(line), flush=True)
+    rsd._lib.load().rsd_release_cache()
     if world > 1:
         dist.destroy_process_group()
+
+
+def form_record(res, ms, t_setup, t_solve, n_dof, steps, pk, peak_rec, form) -> dict:
+    """Throughput, setup/solve split and rooflines of one form's timed steps."""
+    stats = [r[0] for r in res]
+    agg = None
+    for r in res:
+        agg = prof_add(agg, r[1])
+    info = res[-1][2]
+    classes = {k: v for k, v in agg.items() if isinstance(v, dict) and "ms" in v}
+    per = {k: v["ms"] / steps for k, v in classes.items() if v["launches"]}
+    # setup: the dominant GEMM class against the algorithmic flops sum_t (s^3/3 + s^2 b + s b^2)
+    gemm_cls = "gemm_tcgen05" if classes.get("gemm_tcgen05", {}).get("launches") else "gemm_simt"
+    g = classes[gemm_cls]
+    g_ms = g["ms"] / steps
+    achieved = info["setup_flops"] / (g_ms / 1e3) / 1e12 if g_ms else None
+    if gemm_cls == "gemm_tcgen05":
+        peak = pk["bf16_tflops_sustained"] * NOMINAL_TF32 / NOMINAL_BF16
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": f"TF32 = measured BF16 sustained {pk['bf16_tflops_sustained']} x {NOMINAL_TF32}/{NOMINAL_BF16} (nominal ratio)"}
+        if peak_rec:
+            roof["tf32_measured_sustained"] = peak_rec["tf32_tcgen05"]["sustained"]
+            roof["frac_of_tf32_measured"] = achieved / peak_rec["tf32_tcgen05"]["sustained"]
+    else:
+        roof = {"bound": "alu", "achieved": achieved, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
+                "peak_source": "FP64 CUDA-core nominal rate (152 SMs at 2.07 GHz)"}
+        if peak_rec:
+            roof["fp64_measured_sustained"] = peak_rec["fp64_simt"]["sustained"]
+            roof["frac_of_fp64_measured"] = achieved / peak_rec["fp64_simt"]["sustained"]
+    roof["frac"] = achieved / roof["peak"] if achieved else None
+    roof["kernel"] = gemm_cls
+    roof["achieved_basis"] = "rsd_info setup_flops = sum_t (s^3/3 + s^2 b + s b^2) / the class's summed launch time"
+    roof["launches_per_step"] = g["launches"] / steps
+    sw = [classes.get(k) for k in ("sweep_up", "sweep_down") if classes.get(k)]
+    sw_ms = sum(v["ms"] for v in sw) / steps
+    sw_bytes = sum(v["bytes"] for v in sw) / steps
+    apply_roof = None
+    if sw_ms:
+        apply_roof = {"bound": "hbm", "achieved": sw_bytes / (sw_ms / 1e3) / 1e9, "peak": pk["hbm_gbs"],
+                      "unit": "GB/s", "kernel": "k_fwd_sweep + k_bwd_sweep",
+                      "bytes_per_step": sw_bytes, "ms_per_step": sw_ms,
+                      "applications_per_step": statistics.mean(s["iterations"] for s in stats) + 1}
+        apply_roof["frac"] = apply_roof["achieved"] / apply_roof["peak"]
+    return {
+        "value": n_dof / (ms / 1e3), "unit": "DOF/s", "ms_per_step": ms, "form": form,
+        "t_setup_ms": t_setup, "t_solve_ms": t_solve,
+        "setup_dof_s": n_dof / (t_setup / 1e3), "solve_dof_s": n_dof / (t_solve / 1e3),
+        "iterations": [s["iterations"] for s in stats], "relres": [s["relres"] for s in stats],
+        "roofline": roof, "apply_roofline": apply_roof,
+        "detail": {"ms_by_kernel_class": {k: round(v, 3) for k, v in per.items()},
+                   "host_analysis_ms": agg.get("host_analysis_ms", 0.0) / steps,
+                   "host_issue_ms": agg.get("host_issue_ms", 0.0) / steps,
+                   "factor_bytes": info["factor_bytes"], "setup_flops": info["setup_flops"],
+                   "device_bytes": info["device_bytes"]},
+    }
 
 
 if __name__ == "__main__":

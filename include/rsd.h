@@ -90,6 +90,9 @@ typedef struct {
     void*   stream;      /* cudaStream_t for every call on the handle (NULL: legacy default) */
     int32_t profile;     /* nonzero: record a CUDA event pair around every kernel launch of the
                             handle (see rsd_profile); adds ~2 us of host time per launch     */
+    int64_t wait_cycles; /* bound of every wait of the substitution sweeps on another CTA's
+                            progress, in SM clock cycles (<= 0: 4e9, about 2 s); a wait that
+                            reaches it raises RSD_ERR_TIMEOUT (see rsd_apply)                */
 } rsd_options;
 
 typedef struct {
@@ -183,22 +186,26 @@ int rsd_setup_batched(int32_t nprob, const rsd_csr* K, const int32_t* const* dof
  *          bound is reported as RSD_ERR_TIMEOUT by the next rsd_solve / rsd_check call. */
 int rsd_apply(rsd_handle h, const double* r, double* z);
 
-/* rsd_apply_static -- the same z = M r as rsd_apply, for callers that must not have
- * device memory allocated on their behalf: code running while a stream is being
- * captured, or under a fixed device-memory budget, or inside a framework whose caching
- * allocator owns the device.  The paper has no counterpart; it is a packaging of
- * rsd_apply.  The per-call scratch of the substitution sweeps (front vectors, progress
- * and ticket counters, and a copy of the front descriptors pointing at them) is taken
- * from one file-scope device array of 4 MiB, which every GPU that loads the library
- * holds until the process exits; nothing is allocated by the call.
+/* rsd_apply_static -- the same z = M r as rsd_apply, for callers that cannot have device
+ * memory allocated on their behalf: a process that runs under a fixed device-memory
+ * budget with every byte already handed out, or code inside a framework whose own
+ * caching allocator owns the device (an allocation behind its back can fail, or force
+ * the framework to release its cache).  The paper has no counterpart; it is a packaging
+ * of rsd_apply.  The per-call scratch of the substitution sweeps (front vectors,
+ * progress and ticket counters) is one file-scope device array of 4 MiB, which every
+ * GPU that loads the library holds until the process exits; the call allocates nothing.
+ * rsd_setup looks up that array's address on the handle's device and stores, in the
+ * handle's own memory, a copy of the front descriptors that points into it, so the call
+ * itself reads no host memory besides the handle.
  *   r, z : device, n FP64 entries each, may not alias (as rsd_apply).
- * Returns RSD_ERR_ARG if the hierarchy needs more than 4 MiB of scratch (roughly
- * sum over tree nodes of (s + b + 32) entries at the level's storage width, plus the
- * descriptors); rsd_last_error_detail names the size.  The counters are cleared on
- * every call.  The first call on a device looks up that device's address of the array,
- * so make it once before capturing a stream.  All calls, from every handle and stream,
- * share the one array: calls that overlap on the GPU race and must be serialised by
- * the caller.                                                                          */
+ * Returns RSD_ERR_ARG if the hierarchy needs more than 4 MiB of scratch (roughly the sum
+ * over tree nodes of (s + b + 32) entries at the level's storage width, plus two
+ * counters per node), if the current device is not the handle's, or for a paper-mode
+ * handle; rsd_last_error_detail names the reason.  The counters are cleared at the start
+ * of every call; the array keeps the last call's vectors.  All calls on one device, from
+ * every handle, stream and host thread, share the one array: calls that overlap on the
+ * GPU race and must be serialised by the caller (for example by issuing them on one
+ * stream).                                                                              */
 int rsd_apply_static(rsd_handle h, const double* r, double* z);
 
 /* rsd_solve -- preconditioned CG in FP64 on K u = f from u = 0 (the paper's outer Krylov
@@ -216,6 +223,17 @@ int rsd_solve(rsd_handle h, const double* f, double* u, double tol, rsd_stats* s
  * preconditioned CG on the same fronts, with no second setup.
  *   g, lam : device, n FP64 entries.  st : host, may be NULL.  Errors as rsd_solve.     */
 int rsd_solve_adjoint(rsd_handle h, const double* g, double* lam, double tol, rsd_stats* st);
+
+/* rsd_inject_drop_sweep_item -- fault injection for tests of the bounded waits (the paper
+ * has no counterpart).  The next rsd_apply on h runs the upward sweep of tree level
+ * `level` (0 = root) without that sweep's first work item (the first diagonal block of
+ * the level's first front), as if the item were lost: the items that consume its result
+ * wait on a progress counter that nothing raises.  Each such wait gives up after the
+ * handle's wait_cycles, raises the timeout flag and lets its kernel finish, so the call
+ * completes, the CUDA context stays usable and the next rsd_check / rsd_solve returns
+ * RSD_ERR_TIMEOUT.  The handle's results are meaningless from then on: destroy it.
+ * RSD_ERR_ARG for a bad level or a paper-mode handle.                                  */
+int rsd_inject_drop_sweep_item(rsd_handle h, int32_t level);
 
 /* rsd_check -- synchronise the handle's stream and report any device-side error flag
  * (timeout of a bounded wait, failed pivot) raised since setup.                        */
@@ -264,6 +282,20 @@ int rsd_profile(rsd_handle h, rsd_profile_t* out, int32_t reset);
  * before a resetting rsd_profile.  Writes min(cap, count) records to out (host; may be
  * NULL when cap = 0) and the total count to *n.                                       */
 int rsd_profile_trace(rsd_handle h, rsd_trace_rec* out, int64_t cap, int64_t* n);
+
+/* rsd_peak_gemm -- measured rate of this library's own dense GEMM kernel for one
+ * precision, C -= A B^T on an n x n x n product of FP values in [-1, 1): the roofline
+ * denominator of the Schur-complement updates of Eq. 3.2 (the paper reports no rates).
+ *   prec    : RSD_PREC_TF32 (the persistent tcgen05 128 x 256 kernel, n a multiple of
+ *             256), RSD_PREC_FP32 or RSD_PREC_FP64 (the CUDA-core kernel, n a multiple
+ *             of 64).
+ *   reps    : timed single launches; *best_tflops = 2 n^3 / the shortest (TFLOP/s).
+ *   seconds : then back-to-back launches for about this long; *sustained_tflops = their
+ *             mean rate.  CUDA events on `stream` (cudaStream_t; NULL: legacy default).
+ * Allocates and frees 3 n^2 elements of device memory.  RSD_ERR_ARG on a bad size or
+ * precision, RSD_ERR_TIMEOUT if a bounded wait of the kernel gave up.                 */
+int rsd_peak_gemm(int32_t prec, int32_t n, int32_t reps, double seconds, void* stream,
+                  double* best_tflops, double* sustained_tflops);
 
 /* rsd_launch_count -- kernels this library has launched in this process so far.       */
 int64_t rsd_launch_count(void);

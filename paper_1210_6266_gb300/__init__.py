@@ -19,8 +19,17 @@ from ._lib import (RSD_MEM_DEVICE, RSD_MEM_HOST, RSD_MODE_EXACT, RSD_MODE_PAPER,
                    RSD_PREC_FP64, RSD_PREC_TF32, RSDError, check)
 
 __all__ = ["RSD", "grid_problem", "grid_sizes", "grid_exp", "coef_grad", "diffusion_solve",
-           "DiffusionSolve", "launch_count", "RSDError", "RSD_PREC_FP64", "RSD_PREC_FP32",
+           "DiffusionSolve", "launch_count", "peak_gemm", "RSDError", "RSD_PREC_FP64", "RSD_PREC_FP32",
            "RSD_PREC_TF32", "RSD_MODE_EXACT", "RSD_MODE_PAPER"]
+
+
+def peak_gemm(prec: int, n: int, reps: int = 5, seconds: float = 4.0) -> tuple[float, float]:
+    """(best, sustained) TFLOP/s of the library's own GEMM kernel for `prec` on an
+    n x n x n product (rsd_peak_gemm), on the current stream."""
+    best, sus = C.c_double(), C.c_double()
+    check(_lib.load().rsd_peak_gemm(prec, n, reps, seconds, _stream(), C.byref(best), C.byref(sus)),
+          "rsd_peak_gemm")
+    return best.value, sus.value
 
 
 def launch_count() -> int:
@@ -106,7 +115,8 @@ class RSD:
     def setup(cls, rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor,
               dof_node: torch.Tensor, parent, prec_leaf: int = RSD_PREC_TF32,
               prec_mid: int = RSD_PREC_TF32, prec_root: int = RSD_PREC_FP64,
-              maxit: int = 200, profile: bool = False, mode: int = RSD_MODE_EXACT) -> "RSD":
+              maxit: int = 200, profile: bool = False, mode: int = RSD_MODE_EXACT,
+              wait_cycles: int = 0) -> "RSD":
         lib = _lib.load()
         dev = rowptr.is_cuda
         if not (col.is_cuda == dev and val.is_cuda == dev and dof_node.is_cuda == dev):
@@ -121,7 +131,7 @@ class RSD:
                            RSD_MEM_DEVICE if dev else RSD_MEM_HOST)
         tree = _lib.rsd_tree(len(par), par.ctypes.data)
         opt = _lib.rsd_options(mode, prec_leaf, prec_mid, prec_root, maxit,
-                               _stream() if torch.cuda.is_available() else 0, int(profile))
+                               _stream() if torch.cuda.is_available() else 0, int(profile), wait_cycles)
         out = C.c_void_p()
         rc = lib.rsd_setup(C.byref(csr), _ptr(dof_node), C.byref(tree), C.byref(opt), C.byref(out))
         if rc != 0:

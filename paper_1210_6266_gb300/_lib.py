@@ -36,7 +36,8 @@ EXPORTS = [
     "rsd_grid_sizes", "rsd_grid_assemble", "rsd_grid_load", "rsd_grid_partition",
     "rsd_profile", "rsd_launch_count", "rsd_apply_static", "rsd_last_error_detail",
     "rsd_release_cache", "rsd_setup_batched", "rsd_solve_adjoint", "rsd_grid_exp",
-    "rsd_grid_coef_grad", "rsd_profile_trace",
+    "rsd_grid_coef_grad", "rsd_profile_trace", "rsd_peak_gemm",
+    "rsd_inject_drop_sweep_item",
 ]
 
 
@@ -52,7 +53,7 @@ class rsd_tree(C.Structure):
 class rsd_options(C.Structure):
     _fields_ = [("mode", C.c_int32), ("prec_leaf", C.c_int32), ("prec_mid", C.c_int32),
                 ("prec_root", C.c_int32), ("maxit", C.c_int32), ("stream", C.c_void_p),
-                ("profile", C.c_int32)]
+                ("profile", C.c_int32), ("wait_cycles", C.c_int64)]
 
 
 class rsd_stats(C.Structure):
@@ -100,6 +101,7 @@ def load() -> C.CDLL:
             "rsd_solve": (C.c_int, [P, P, P, C.c_double, C.POINTER(rsd_stats)]),
             "rsd_solve_adjoint": (C.c_int, [P, P, P, C.c_double, C.POINTER(rsd_stats)]),
             "rsd_check": (C.c_int, [P]),
+            "rsd_inject_drop_sweep_item": (C.c_int, [P, C.c_int32]),
             "rsd_destroy": (None, [P]),
             "rsd_strerror": (C.c_char_p, [C.c_int]),
             "rsd_last_error_detail": (C.c_char_p, []),
@@ -118,6 +120,8 @@ def load() -> C.CDLL:
             "rsd_profile": (C.c_int, [P, C.POINTER(rsd_profile_t), C.c_int32]),
             "rsd_profile_trace": (C.c_int, [P, P, C.c_int64, C.POINTER(C.c_int64)]),
             "rsd_launch_count": (C.c_int64, []),
+            "rsd_peak_gemm": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_double, P,
+                                        C.POINTER(C.c_double), C.POINTER(C.c_double)]),
             "rsd_release_cache": (None, []),
             "rsd_setup_batched": (C.c_int, [C.c_int32, C.POINTER(rsd_csr), P, C.POINTER(rsd_tree),
                                             C.POINTER(rsd_options), C.POINTER(P)]),

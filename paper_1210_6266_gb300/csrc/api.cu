@@ -758,6 +758,7 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
             }
     }
     const size_t o_fronts = take(sizeof(FrontDesc) * a.n_nodes);
+    const size_t o_sfronts = take(sizeof(FrontDesc) * a.n_nodes);
     size_t n_items = 16;
     for (int t = 0; t < a.n_nodes; ++t) {
         const size_t s = a.I_off[t + 1] - a.I_off[t], b = beff(t);
@@ -948,6 +949,7 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
         RSD_CUDA_TRY(cudaMemcpyAsync(d_solve, stage_host(h, solve.data(), sizeof(FrontDesc) * solve.size()), sizeof(FrontDesc) * solve.size(), cudaMemcpyHostToDevice, st));
         RSD_CUDA_TRY(cudaStreamSynchronize(st));     // host vectors above go out of scope
     }
+    RSD_TRY(static_apply_prepare(h, (FrontDesc*)(A + o_sfronts)));
     // the tensor-core levels need tensor maps over the fronts just placed
     RSD_TRY(gemm_tc_prepare(h));
     h.prof.host_part[5] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_plan).count();
@@ -1160,6 +1162,7 @@ extern "C" int rsd_setup(const rsd_csr* K, const int32_t* dof_node, const rsd_tr
     Handle& h = hh->h;
     h.opt = o;
     h.stream = st;
+    if (o.wait_cycles > 0) h.wait_cycles = o.wait_cycles;
     h.prof.on = o.profile != 0;
     for (int i = 0; i < 5; ++i) h.prof.host_part[i] = part[i];
     h.prof.host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_host0).count();
@@ -1192,6 +1195,25 @@ extern "C" int rsd_apply(rsd_handle hh, const double* r, double* z) {
 extern "C" int rsd_apply_static(rsd_handle hh, const double* r, double* z) {
     if (!hh || !r || !z || r == z || hh->h.paper) return RSD_ERR_ARG;
     return run_apply_static(hh->h, r, z);
+}
+
+extern "C" int rsd_peak_gemm(int32_t prec, int32_t n, int32_t reps, double seconds, void* stream,
+                             double* best_tflops, double* sustained_tflops) {
+    if (!best_tflops || !sustained_tflops || reps < 1 || !(seconds >= 0)) return RSD_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == RSD_PREC_TF32) {
+        int dev = 0, sms = 148;
+        RSD_CUDA_TRY(cudaGetDevice(&dev));
+        RSD_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        return gemm_tc_peak(n, reps, seconds, st, sms, best_tflops, sustained_tflops);
+    }
+    return gemm_simt_peak(prec, n, reps, seconds, st, best_tflops, sustained_tflops);
+}
+
+extern "C" int rsd_inject_drop_sweep_item(rsd_handle hh, int32_t level) {
+    if (!hh || hh->h.paper || level < 0 || level >= (int)hh->h.levels.size()) return RSD_ERR_ARG;
+    hh->h.inject_drop_level = level;
+    return RSD_OK;
 }
 
 extern "C" int rsd_check(rsd_handle hh) {

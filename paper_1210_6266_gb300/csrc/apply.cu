@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <mutex>
 
 #include "rsd_internal.cuh"
 
@@ -25,7 +26,6 @@ namespace {
 
 constexpr int AT = 256;                  // threads per CTA
 constexpr int AW = AT / 32;              // warps
-constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
 
 template <typename T> struct Vec;
 template <> struct Vec<float> { using V = float4; static constexpr int W = 4; };
@@ -99,13 +99,16 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Wait until *flag >= target; returns the last value seen.  Thread 0 polls, the block syncs.
-__device__ int wait_flag(const int* flag, int target, int* err, int* s_val) {
+// After `limit` clock cycles (the handle's wait bound) the wait gives up, raises
+// ERR_TIMEOUT and returns as if the target had been reached; once the flag is raised,
+// every later wait of the launch returns at once.
+__device__ int wait_flag(const int* flag, int target, int* err, int* s_val, long long limit) {
     if (threadIdx.x == 0) {
         int v = ld_volatile(flag);
         if (v < target) {
             const long long t0 = clock64();
             while ((v = ld_volatile(flag)) < target) {
-                if (ld_volatile(&err[ERR_TIMEOUT]) || clock64() - t0 > WAIT_CYCLES) {
+                if (ld_volatile(&err[ERR_TIMEOUT]) || clock64() - t0 > limit) {
                     atomicExch(&err[ERR_TIMEOUT], 1);
                     v = target;
                     break;
@@ -165,7 +168,8 @@ __global__ void k_fwd_gather(const FrontDesc* __restrict__ fronts, const FrontDe
 template <typename T, typename A, int GD, bool H>
 __global__ void __launch_bounds__(AT, GD == 1 ? 2 : 1) k_fwd_sweep(const FrontDesc* __restrict__ fronts,
                                                      const int* __restrict__ items, int n_items,
-                                                     int* __restrict__ ticket, int* __restrict__ err) {
+                                                     int* __restrict__ ticket, int* __restrict__ err,
+                                                     long long wait) {
     using V = typename Vec<T>::V;
     using PT = typename PType<T, H>::type;
     constexpr int VW = Vec<T>::W;
@@ -223,7 +227,7 @@ __global__ void __launch_bounds__(AT, GD == 1 ? 2 : 1) k_fwd_sweep(const FrontDe
                                                                   : make_uint4(0u, 0u, 0u, 0u);
                     }
                 const int need = min(cb + 2, ncb);
-                if (seen < need) seen = wait_flag(&f.flag[0], need, err, &s_flag);
+                if (seen < need) seen = wait_flag(&f.flag[0], need, err, &s_flag, wait);
                 float y[8];
 #pragma unroll
                 for (int e = 0; e < 8; ++e) y[e] = (cl + e < cw) ? ld_cg(v + c0 + cl + e) : 0.f;
@@ -253,7 +257,7 @@ __global__ void __launch_bounds__(AT, GD == 1 ? 2 : 1) k_fwd_sweep(const FrontDe
                         const int row = r0 + g * NB + warp + AW * u;
                         l[g][u] = (g < nb && row < r1 && cl < cw) ? __ldg((const V*)(P + (int64_t)row * f.ldp + c0 + cl)) : V{};
                     }
-                if (ps == 0 && seen < cb + 1) seen = wait_flag(&f.flag[0], cb + 1, err, &s_flag);
+                if (ps == 0 && seen < cb + 1) seen = wait_flag(&f.flag[0], cb + 1, err, &s_flag, wait);
                 A y[VW];
 #pragma unroll
                 for (int e = 0; e < VW; ++e) y[e] = (cl + e < cw) ? ld_cg(v + c0 + cl + e) : (A)0;
@@ -389,7 +393,7 @@ template <typename T, typename A, int GD, bool H>
 __global__ void __launch_bounds__(AT, GD == 1 ? 2 : 1) k_bwd_sweep(const FrontDesc* __restrict__ fronts,
                                                      const int* __restrict__ items, int n_items,
                                                      int* __restrict__ ticket, int* __restrict__ err,
-                                                     double* __restrict__ z) {
+                                                     double* __restrict__ z, long long wait) {
     using V = typename Vec<T>::V;
     using PT = typename PType<T, H>::type;
     constexpr int VW = Vec<T>::W;
@@ -462,7 +466,7 @@ __global__ void __launch_bounds__(AT, GD == 1 ? 2 : 1) k_bwd_sweep(const FrontDe
                     l[u] = (in && cl < cw) ? __ldg((const uint4*)(P + (int64_t)row * f.ldp + c0 + cl)) : make_uint4(0u, 0u, 0u, 0u);
                     rsc[u] = in ? f.ri[row] : 0.f;
                 }
-                if (seen < need) seen = wait_flag(&f.flag[1], need, err, &s_flag);
+                if (seen < need) seen = wait_flag(&f.flag[1], need, err, &s_flag, wait);
 #pragma unroll
                 for (int u = 0; u < RB; ++u) {
                     const int row = rlo + (warp + AW * u) * HW + sub;
@@ -511,7 +515,7 @@ __global__ void __launch_bounds__(AT, GD == 1 ? 2 : 1) k_bwd_sweep(const FrontDe
                             l[u][g][ps] = (row < g1 && cl < cw) ? __ldg((const V*)(P + (int64_t)row * f.ldp + c0 + cl)) : V{};
                         }
                 }
-                if (base == g0 && seen < need) seen = wait_flag(&f.flag[1], need, err, &s_flag);
+                if (base == g0 && seen < need) seen = wait_flag(&f.flag[1], need, err, &s_flag, wait);
                 A x[RB];
 #pragma unroll
                 for (int u = 0; u < RB; ++u) {
@@ -661,24 +665,24 @@ int sweep_smem_setup() {
 // FP16 factor copy when the level has one.
 template <typename T, typename A>
 void launch_fwd(int gd, bool h16, int grid, cudaStream_t st, const FrontDesc* fr, const int* items, int n, int* tk,
-                int* err) {
+                int* err, long long wait) {
     if constexpr (sizeof(T) == 4) {
-        if (h16 && gd == 2) { k_fwd_sweep<T, A, 2, true><<<grid, AT, sweep_dsm<T, 2, true>(), st>>>(fr, items, n, tk, err); return; }
-        if (h16) { k_fwd_sweep<T, A, 1, true><<<grid, AT, sweep_dsm<T, 1, true>(), st>>>(fr, items, n, tk, err); return; }
-        if (gd == 2) { k_fwd_sweep<T, A, 2, false><<<grid, AT, sweep_dsm<T, 2, false>(), st>>>(fr, items, n, tk, err); return; }
+        if (h16 && gd == 2) { k_fwd_sweep<T, A, 2, true><<<grid, AT, sweep_dsm<T, 2, true>(), st>>>(fr, items, n, tk, err, wait); return; }
+        if (h16) { k_fwd_sweep<T, A, 1, true><<<grid, AT, sweep_dsm<T, 1, true>(), st>>>(fr, items, n, tk, err, wait); return; }
+        if (gd == 2) { k_fwd_sweep<T, A, 2, false><<<grid, AT, sweep_dsm<T, 2, false>(), st>>>(fr, items, n, tk, err, wait); return; }
     }
-    k_fwd_sweep<T, A, 1, false><<<grid, AT, sweep_dsm<T, 1, false>(), st>>>(fr, items, n, tk, err);
+    k_fwd_sweep<T, A, 1, false><<<grid, AT, sweep_dsm<T, 1, false>(), st>>>(fr, items, n, tk, err, wait);
 }
 
 template <typename T, typename A>
 void launch_bwd(int gd, bool h16, int grid, cudaStream_t st, const FrontDesc* fr, const int* items, int n, int* tk,
-                int* err, double* z) {
+                int* err, double* z, long long wait) {
     if constexpr (sizeof(T) == 4) {
-        if (h16 && gd == 2) { k_bwd_sweep<T, A, 2, true><<<grid, AT, sweep_dsm<T, 2, true>(), st>>>(fr, items, n, tk, err, z); return; }
-        if (h16) { k_bwd_sweep<T, A, 1, true><<<grid, AT, sweep_dsm<T, 1, true>(), st>>>(fr, items, n, tk, err, z); return; }
-        if (gd == 2) { k_bwd_sweep<T, A, 2, false><<<grid, AT, sweep_dsm<T, 2, false>(), st>>>(fr, items, n, tk, err, z); return; }
+        if (h16 && gd == 2) { k_bwd_sweep<T, A, 2, true><<<grid, AT, sweep_dsm<T, 2, true>(), st>>>(fr, items, n, tk, err, z, wait); return; }
+        if (h16) { k_bwd_sweep<T, A, 1, true><<<grid, AT, sweep_dsm<T, 1, true>(), st>>>(fr, items, n, tk, err, z, wait); return; }
+        if (gd == 2) { k_bwd_sweep<T, A, 2, false><<<grid, AT, sweep_dsm<T, 2, false>(), st>>>(fr, items, n, tk, err, z, wait); return; }
     }
-    k_bwd_sweep<T, A, 1, false><<<grid, AT, sweep_dsm<T, 1, false>(), st>>>(fr, items, n, tk, err, z);
+    k_bwd_sweep<T, A, 1, false><<<grid, AT, sweep_dsm<T, 1, false>(), st>>>(fr, items, n, tk, err, z, wait);
 }
 
 template <typename T, typename A>
@@ -706,8 +710,12 @@ int sweep_level(Handle& h, int li, bool forward, const double* r, double* z, int
         prof_end(h, gi, 0.0, gbytes);
         RSD_CUDA_TRY(cudaGetLastError());
         if (L.n_fwd_items) {
+            // fault injection: drop the first item (front slot 0's first diagonal block)
+            const int drop = h.inject_drop_level == li && L.n_fwd_items > 1 ? 1 : 0;
+            if (drop) h.inject_drop_level = -1;
             const int pi = prof_begin(h, K_FWD);
-            launch_fwd<T, A>(sweep_group(L), L.h16, grid, h.stream, L.d_fronts, L.d_fwd_items, L.n_fwd_items, h.d_ticket + tk, h.d_err);
+            launch_fwd<T, A>(sweep_group(L), L.h16, grid, h.stream, L.d_fronts, L.d_fwd_items + drop, L.n_fwd_items - drop,
+                             h.d_ticket + tk, h.d_err, h.wait_cycles);
             count_launch();
             prof_end(h, pi, fbytes / sizeof(T) * 2.0, fbytes);
         }
@@ -719,7 +727,7 @@ int sweep_level(Handle& h, int li, bool forward, const double* r, double* z, int
         RSD_CUDA_TRY(cudaGetLastError());
         if (L.n_bwd_items) {
             const int pi = prof_begin(h, K_BWD);
-            launch_bwd<T, A>(sweep_group(L), L.h16, grid, h.stream, L.d_fronts, L.d_bwd_items, L.n_bwd_items, h.d_ticket + tk, h.d_err, z);
+            launch_bwd<T, A>(sweep_group(L), L.h16, grid, h.stream, L.d_fronts, L.d_bwd_items, L.n_bwd_items, h.d_ticket + tk, h.d_err, z, h.wait_cycles);
             count_launch();
             prof_end(h, pi, fbytes / sizeof(T) * 2.0, fbytes);
         }
@@ -749,9 +757,12 @@ int run_apply(Handle& h, const double* r, double* z) {
 }  // namespace rsd
 
 // ---- allocation-free variant of the preconditioner application ----------------------
-// Same kernels as run_apply; the per-call scratch (front vectors, progress counters,
-// ticket counters and a copy of the front descriptors pointing at them) lives in one
-// file-scope device array instead of the handle's arena.  Every call shares that array.
+// Same kernels as run_apply; the per-call scratch (front vectors, progress counters and
+// ticket counters) lives in one file-scope device array instead of the handle's arena.
+// rsd_setup prepares, with the handle's device current, a second copy of the handle's
+// front descriptors whose vector and counter pointers point into that array, and stores
+// it in the handle's arena; a call then only clears the counters and launches the
+// sweeps.  Every handle on a device shares the array.
 namespace rsd {
 namespace {
 
@@ -759,31 +770,44 @@ constexpr size_t APPLY_STATIC_BYTES = (size_t)4 << 20;          // 4 MiB per dev
 __device__ __align__(256) unsigned char g_apply_scratch[APPLY_STATIC_BYTES];
 
 constexpr int MAX_DEVICES = 64;
+std::mutex g_scratch_mu;
 void* g_apply_scratch_ptr[MAX_DEVICES] = {};
-FrontDesc g_staging[APPLY_STATIC_BYTES / sizeof(FrontDesc)];    // host staging of descriptors
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
+// Device address of the array on the current device (looked up once per device).
+int scratch_address(int dev, char** out) {
+    if (dev < 0 || dev >= MAX_DEVICES) return RSD_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_apply_scratch_ptr[dev]) {
+        void* p = nullptr;
+        RSD_CUDA_TRY(cudaGetSymbolAddress(&p, g_apply_scratch));
+        g_apply_scratch_ptr[dev] = p;
+    }
+    *out = (char*)g_apply_scratch_ptr[dev];
+    return RSD_OK;
+}
+
 template <typename T, typename A>
-int sweep_level_static(Handle& h, int li, bool forward, const double* r, double* z, int* ticket,
-                       FrontDesc* const* lvl_fronts) {
+int sweep_level_static(Handle& h, int li, bool forward, const double* r, double* z, int* ticket) {
     RSD_TRY((sweep_smem_setup<T, A>()));
     Level& L = h.levels[li];
     const int nf = (int)L.fronts.size();
-    FrontDesc* fr = lvl_fronts[li];
+    const FrontDesc* fr = h.d_static_fronts + h.static_level_first[li];
     const int grid = std::max(1, std::min(forward ? L.n_fwd_items : L.n_bwd_items, h.num_sms * 4));
     if (forward) {
         if (li + 1 < (int)h.levels.size()) {
             const Level& Lc = h.levels[li + 1];
-            if (is_fp64(Lc.prec)) k_fwd_gather<A, double><<<nf, 256, 0, h.stream>>>(fr, lvl_fronts[li + 1], L.d_child_slots, r);
-            else k_fwd_gather<A, float><<<nf, 256, 0, h.stream>>>(fr, lvl_fronts[li + 1], L.d_child_slots, r);
+            const FrontDesc* kids = h.d_static_fronts + h.static_level_first[li + 1];
+            if (is_fp64(Lc.prec)) k_fwd_gather<A, double><<<nf, 256, 0, h.stream>>>(fr, kids, L.d_child_slots, r);
+            else k_fwd_gather<A, float><<<nf, 256, 0, h.stream>>>(fr, kids, L.d_child_slots, r);
         } else {
             k_fwd_gather<A, A><<<nf, 256, 0, h.stream>>>(fr, fr, L.d_child_slots, r);
         }
         count_launch();
         RSD_CUDA_TRY(cudaGetLastError());
         if (L.n_fwd_items) {
-            launch_fwd<T, A>(sweep_group(L), L.h16, grid, h.stream, fr, L.d_fwd_items, L.n_fwd_items, ticket, h.d_err);
+            launch_fwd<T, A>(sweep_group(L), L.h16, grid, h.stream, fr, L.d_fwd_items, L.n_fwd_items, ticket, h.d_err, h.wait_cycles);
             count_launch();
         }
     } else {
@@ -791,7 +815,7 @@ int sweep_level_static(Handle& h, int li, bool forward, const double* r, double*
         count_launch();
         RSD_CUDA_TRY(cudaGetLastError());
         if (L.n_bwd_items) {
-            launch_bwd<T, A>(sweep_group(L), L.h16, grid, h.stream, fr, L.d_bwd_items, L.n_bwd_items, ticket, h.d_err, z);
+            launch_bwd<T, A>(sweep_group(L), L.h16, grid, h.stream, fr, L.d_bwd_items, L.n_bwd_items, ticket, h.d_err, z, h.wait_cycles);
             count_launch();
         }
     }
@@ -801,58 +825,76 @@ int sweep_level_static(Handle& h, int li, bool forward, const double* r, double*
 
 }  // namespace
 
-int run_apply_static(Handle& h, const double* r, double* z) {
-    int dev = 0;
-    RSD_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= MAX_DEVICES) return RSD_ERR_ARG;
-    if (!g_apply_scratch_ptr[dev]) {
-        void* p = nullptr;
-        RSD_CUDA_TRY(cudaGetSymbolAddress(&p, g_apply_scratch));
-        g_apply_scratch_ptr[dev] = p;
-    }
-    char* base = (char*)g_apply_scratch_ptr[dev];
+int static_apply_prepare(Handle& h, FrontDesc* d_slots) {
+    h.static_ok = false;
+    h.d_static_fronts = d_slots;
+    if (h.paper) return RSD_OK;
+    char* base = nullptr;
+    RSD_TRY(scratch_address(h.device, &base));
     const int nl = (int)h.levels.size();
-    // layout: tickets | progress counters | descriptors | front vectors
+    // layout: tickets | progress counters | front vectors
     size_t off = 0;
     const size_t o_ticket = off; off = align256(off + sizeof(int) * 2 * nl);
     const size_t o_flags = off;  off = align256(off + sizeof(int) * 2 * (size_t)h.n_nodes);
-    const size_t o_fronts = off; off = align256(off + sizeof(FrontDesc) * (size_t)h.n_nodes);
+    h.static_clear_bytes = off;
     size_t vec_bytes = 0;
     for (auto& L : h.levels)
         for (auto& f : L.fronts) vec_bytes += align256((size_t)(f.N + 32) * elem_bytes(L.prec));
-    const size_t o_vec = off; off += vec_bytes;
-    if (off > APPLY_STATIC_BYTES || (size_t)h.n_nodes > sizeof(g_staging) / sizeof(FrontDesc)) {
-        set_last_error("rsd_apply_static: this hierarchy needs " + std::to_string(off) +
-                       " bytes of scratch; the static limit is " + std::to_string(APPLY_STATIC_BYTES));
-        return RSD_ERR_ARG;
-    }
-    FrontDesc* lvl_fronts[64];
-    if (nl > 64) return RSD_ERR_ARG;
-    size_t slot = 0, voff = o_vec;
+    const size_t o_vec = off;
+    off += vec_bytes;
+    h.static_need = off;
+    if (off > APPLY_STATIC_BYTES) return RSD_OK;       // rsd_apply_static will refuse the handle
+    std::vector<FrontDesc> desc;
+    desc.reserve(h.n_nodes);
+    h.static_level_first.assign(nl, 0);
+    size_t voff = o_vec;
     for (int li = 0; li < nl; ++li) {
         Level& L = h.levels[li];
-        lvl_fronts[li] = (FrontDesc*)(base + o_fronts) + slot;
+        h.static_level_first[li] = (int)desc.size();
         for (auto& f : L.fronts) {
             FrontDesc g = f;
             g.vec = base + voff;
             voff += align256((size_t)(f.N + 32) * elem_bytes(L.prec));
             g.flag = (int*)(base + o_flags) + 2 * f.node;
-            g_staging[slot++] = g;
+            desc.push_back(g);
         }
     }
-    RSD_CUDA_TRY(cudaMemcpyAsync(base + o_fronts, g_staging, sizeof(FrontDesc) * slot, cudaMemcpyHostToDevice, h.stream));
-    RSD_CUDA_TRY(cudaMemsetAsync(base + o_ticket, 0, o_fronts - o_ticket, h.stream));
-    int* ticket = (int*)(base + o_ticket);
+    if (!desc.empty())
+        RSD_CUDA_TRY(cudaMemcpyAsync(d_slots, stage_host(h, desc.data(), sizeof(FrontDesc) * desc.size()),
+                                     sizeof(FrontDesc) * desc.size(), cudaMemcpyHostToDevice, h.stream));
+    h.static_ticket = (int*)(base + o_ticket);
+    h.static_ok = true;
+    return RSD_OK;
+}
+
+size_t static_apply_limit() { return APPLY_STATIC_BYTES; }
+
+int run_apply_static(Handle& h, const double* r, double* z) {
+    int dev = -1;
+    RSD_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != h.device) {
+        set_last_error("rsd_apply_static: the current device (" + std::to_string(dev) +
+                       ") is not the handle's device (" + std::to_string(h.device) + ")");
+        return RSD_ERR_ARG;
+    }
+    if (!h.static_ok) {
+        set_last_error("rsd_apply_static: this hierarchy needs " + std::to_string(h.static_need) +
+                       " bytes of scratch; the static limit is " + std::to_string(APPLY_STATIC_BYTES));
+        return RSD_ERR_ARG;
+    }
+    const int nl = (int)h.levels.size();
+    RSD_CUDA_TRY(cudaMemsetAsync(h.static_ticket, 0, h.static_clear_bytes, h.stream));
+    int* ticket = h.static_ticket;
     for (int li = nl - 1; li >= 0; --li) {
         const int rc = is_fp64(h.levels[li].prec)
-                           ? sweep_level_static<double, double>(h, li, true, r, z, ticket + li, lvl_fronts)
-                           : sweep_level_static<float, float>(h, li, true, r, z, ticket + li, lvl_fronts);
+                           ? sweep_level_static<double, double>(h, li, true, r, z, ticket + li)
+                           : sweep_level_static<float, float>(h, li, true, r, z, ticket + li);
         if (rc != RSD_OK) return rc;
     }
     for (int li = 0; li < nl; ++li) {
         const int rc = is_fp64(h.levels[li].prec)
-                           ? sweep_level_static<double, double>(h, li, false, r, z, ticket + nl + li, lvl_fronts)
-                           : sweep_level_static<float, float>(h, li, false, r, z, ticket + nl + li, lvl_fronts);
+                           ? sweep_level_static<double, double>(h, li, false, r, z, ticket + nl + li)
+                           : sweep_level_static<float, float>(h, li, false, r, z, ticket + nl + li);
         if (rc != RSD_OK) return rc;
     }
     return RSD_OK;
@@ -876,13 +918,13 @@ int sweep_with(Handle& h, int li, bool forward, const FrontDesc* fronts, const i
         count_launch();
         RSD_CUDA_TRY(cudaGetLastError());
         if (n_items) {
-            if (f64) launch_fwd<double, double>(sweep_group(L), false, grid, h.stream, fronts, items, n_items, ticket, h.d_err);
-            else launch_fwd<float, float>(sweep_group(L), L.h16, grid, h.stream, fronts, items, n_items, ticket, h.d_err);
+            if (f64) launch_fwd<double, double>(sweep_group(L), false, grid, h.stream, fronts, items, n_items, ticket, h.d_err, h.wait_cycles);
+            else launch_fwd<float, float>(sweep_group(L), L.h16, grid, h.stream, fronts, items, n_items, ticket, h.d_err, h.wait_cycles);
             count_launch();
         }
     } else if (n_items) {
-        if (f64) launch_bwd<double, double>(sweep_group(L), false, grid, h.stream, fronts, items, n_items, ticket, h.d_err, out);
-        else launch_bwd<float, float>(sweep_group(L), L.h16, grid, h.stream, fronts, items, n_items, ticket, h.d_err, out);
+        if (f64) launch_bwd<double, double>(sweep_group(L), false, grid, h.stream, fronts, items, n_items, ticket, h.d_err, out, h.wait_cycles);
+        else launch_bwd<float, float>(sweep_group(L), L.h16, grid, h.stream, fronts, items, n_items, ticket, h.d_err, out, h.wait_cycles);
         count_launch();
     }
     RSD_CUDA_TRY(cudaGetLastError());

@@ -507,7 +507,76 @@ int finalize_tasks(std::vector<GemmTask>& tasks, int tile_m, int tile_n) {
     return total;
 }
 
+// Peak probe of the CUDA-core GEMM: C -= A B^T on one n x n x n product, best of `reps`
+// launches and the mean over back-to-back launches for about `seconds`.
+template <typename T>
+__global__ void k_fill_hash_t(T* __restrict__ p, int64_t n, uint32_t seed) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t x = (uint32_t)i * 2654435761u ^ seed;
+        x ^= x >> 16; x *= 0x7feb352du; x ^= x >> 15; x *= 0x846ca68bu; x ^= x >> 16;
+        p[i] = (T)((double)(x >> 8) * (1.0 / 8388608.0) - 1.0);
+    }
+}
+
+template <typename T>
+int gemm_simt_peak_t(int n, int reps, double seconds, cudaStream_t st, double* best, double* sustained) {
+    const size_t elems = (size_t)n * n;
+    std::vector<GemmTask> tasks(1);
+    char* buf = nullptr;
+    const size_t o_b = elems * sizeof(T), o_c = 2 * elems * sizeof(T), o_t = 3 * elems * sizeof(T);
+    RSD_CUDA_TRY(cudaMalloc((void**)&buf, o_t + 256));
+    struct Free { char* p; ~Free() { cudaFree(p); } } fr{buf};
+    T* A = (T*)buf;
+    k_fill_hash_t<T><<<1024, 256, 0, st>>>(A, (int64_t)elems, 0x9e3779b9u);
+    k_fill_hash_t<T><<<1024, 256, 0, st>>>((T*)(buf + o_b), (int64_t)elems, 0x7f4a7c15u);
+    RSD_CUDA_TRY(cudaMemsetAsync(buf + o_c, 0, elems * sizeof(T), st));
+    GemmTask& t = tasks[0];
+    t = GemmTask{};
+    t.A = A; t.B = buf + o_b; t.C = buf + o_c;
+    t.lda = t.ldb = t.ldc = n;
+    t.M = t.N = t.K = n;
+    t.lower = 0; t.beta = 1;
+    const int total = finalize_tasks(tasks, SB, SB);
+    RSD_CUDA_TRY(cudaMemcpyAsync(buf + o_t, tasks.data(), sizeof(GemmTask), cudaMemcpyHostToDevice, st));
+    const GemmTask* dt = (const GemmTask*)(buf + o_t);
+    auto launch = [&]() { k_gemm_simt<T><<<total, 256, 0, st>>>(dt, 1, (T)-1); count_launch(); };
+    cudaEvent_t e0, e1;
+    RSD_CUDA_TRY(cudaEventCreate(&e0));
+    RSD_CUDA_TRY(cudaEventCreate(&e1));
+    struct Ev { cudaEvent_t a, b; ~Ev() { cudaEventDestroy(a); cudaEventDestroy(b); } } ev{e0, e1};
+    launch();
+    float bms = 1e30f;
+    for (int r = 0; r < reps; ++r) {
+        RSD_CUDA_TRY(cudaEventRecord(e0, st));
+        launch();
+        RSD_CUDA_TRY(cudaEventRecord(e1, st));
+        RSD_CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0;
+        RSD_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        bms = std::min(bms, ms);
+    }
+    const int loops = std::max(1, (int)(seconds * 1e3 / std::max(bms, 1e-3f)));
+    RSD_CUDA_TRY(cudaEventRecord(e0, st));
+    for (int r = 0; r < loops; ++r) launch();
+    RSD_CUDA_TRY(cudaEventRecord(e1, st));
+    RSD_CUDA_TRY(cudaEventSynchronize(e1));
+    float tms = 0;
+    RSD_CUDA_TRY(cudaEventElapsedTime(&tms, e0, e1));
+    RSD_CUDA_TRY(cudaGetLastError());
+    const double flops = 2.0 * n * (double)n * n;
+    *best = flops / (bms * 1e-3) / 1e12;
+    *sustained = flops * loops / (tms * 1e-3) / 1e12;
+    return RSD_OK;
+}
+
 }  // namespace
+
+int gemm_simt_peak(int prec, int n, int reps, double seconds, cudaStream_t st, double* best, double* sustained) {
+    if (n < 64 || n % 64 || reps < 1 || !best || !sustained) return RSD_ERR_ARG;
+    if (prec == RSD_PREC_FP64) return gemm_simt_peak_t<double>(n, reps, seconds, st, best, sustained);
+    if (prec == RSD_PREC_FP32) return gemm_simt_peak_t<float>(n, reps, seconds, st, best, sustained);
+    return RSD_ERR_ARG;
+}
 
 // Row scales of the FP16 factor copy: with sqrt(K_ii) = m 2^x, m in [0.5, 1), rs[i] =
 // 2^(14 - x) puts sqrt(K_ii) rs[i] in [2^13, 2^14), a factor 4 below FP16's largest

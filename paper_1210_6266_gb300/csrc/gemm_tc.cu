@@ -632,6 +632,93 @@ void gemm_tc_release(Handle& h) {
     h.tc_state = nullptr;
 }
 
+// ---- peak probe: the persistent 128 x 256 kernel on one n x n x n product --------------
+namespace {
+
+// Deterministic operand values in [-1, 1) from a counter hash (no host transfer).
+__global__ void k_fill_hash(float* __restrict__ p, int64_t n, uint32_t seed) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t x = (uint32_t)i * 2654435761u ^ seed;
+        x ^= x >> 16; x *= 0x7feb352du; x ^= x >> 15; x *= 0x846ca68bu; x ^= x >> 16;
+        p[i] = (float)(x >> 8) * (1.0f / 8388608.0f) - 1.0f;
+    }
+}
+
+}  // namespace
+
+int gemm_tc_peak(int n, int reps, double seconds, cudaStream_t stream, int num_sms, double* best, double* sustained) {
+    if (n < 256 || n % 256 || reps < 1 || !best || !sustained) return RSD_ERR_ARG;
+    const size_t elems = (size_t)n * n;
+    char* buf = nullptr;
+    const size_t o_b = elems * 4, o_c = 2 * elems * 4, o_maps = 3 * elems * 4;
+    const int tm = n / BM, tn = n / 256;
+    std::vector<TcTile> tiles;
+    for (int a0 = 0; a0 < tm; a0 += TILE_BAND)
+        for (int b = 0; b < tn; ++b)
+            for (int a = a0; a < std::min(tm, a0 + TILE_BAND); ++a) tiles.push_back({0, a, b, 0, n / BK, -1, 0, 0});
+    const size_t o_task = o_maps + 2 * sizeof(CUtensorMap);
+    const size_t o_tiles = o_task + 256, o_err = o_tiles + ((tiles.size() * sizeof(TcTile) + 255) & ~(size_t)255);
+    const size_t total = o_err + 256;
+    RSD_CUDA_TRY(cudaMalloc((void**)&buf, total));
+    struct Free { char* p; ~Free() { cudaFree(p); } } fr{buf};
+    float* A = (float*)buf;
+    float* B = (float*)(buf + o_b);
+    float* Cm = (float*)(buf + o_c);
+    k_fill_hash<<<1024, 256, 0, stream>>>(A, (int64_t)elems, 0x9e3779b9u);
+    k_fill_hash<<<1024, 256, 0, stream>>>(B, (int64_t)elems, 0x7f4a7c15u);
+    RSD_CUDA_TRY(cudaMemsetAsync(Cm, 0, elems * 4, stream));
+    RSD_CUDA_TRY(cudaMemsetAsync(buf + o_err, 0, 256, stream));
+    CUtensorMap maps[2];
+    RSD_TRY(encode_2d(&maps[0], A, n, n, n));
+    RSD_TRY(encode_2d(&maps[1], B, n, n, n));
+    TcTask t{};
+    t.C = Cm; t.ldc = n; t.M = n; t.N = n; t.K = n; t.lower = 0; t.beta = 1;
+    t.map_a = 0; t.map_b = 1; t.alpha = -1.0f; t.round_tf32 = 0;
+    RSD_CUDA_TRY(cudaMemcpyAsync(buf + o_maps, maps, sizeof(maps), cudaMemcpyHostToDevice, stream));
+    RSD_CUDA_TRY(cudaMemcpyAsync(buf + o_task, &t, sizeof(t), cudaMemcpyHostToDevice, stream));
+    RSD_CUDA_TRY(cudaMemcpyAsync(buf + o_tiles, tiles.data(), tiles.size() * sizeof(TcTile), cudaMemcpyHostToDevice, stream));
+    RSD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc_persist<256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<256, 4>::TOTAL));
+    int* err = (int*)(buf + o_err);
+    const int ctas = std::min((int)tiles.size(), num_sms);
+    auto launch = [&]() {
+        k_gemm_tc_persist<256, 4><<<(unsigned)ctas, TC_THREADS, Smem<256, 4>::TOTAL, stream>>>(
+            (const TcTask*)(buf + o_task), (const TcTile*)(buf + o_tiles), (int)tiles.size(),
+            (const CUtensorMap*)(buf + o_maps), nullptr, err);
+        count_launch();
+    };
+    cudaEvent_t e0, e1;
+    RSD_CUDA_TRY(cudaEventCreate(&e0));
+    RSD_CUDA_TRY(cudaEventCreate(&e1));
+    struct Ev { cudaEvent_t a, b; ~Ev() { cudaEventDestroy(a); cudaEventDestroy(b); } } ev{e0, e1};
+    const double flops = 2.0 * n * (double)n * n;
+    launch();
+    float bms = 1e30f;
+    for (int r = 0; r < reps; ++r) {
+        RSD_CUDA_TRY(cudaEventRecord(e0, stream));
+        launch();
+        RSD_CUDA_TRY(cudaEventRecord(e1, stream));
+        RSD_CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0;
+        RSD_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        bms = std::min(bms, ms);
+    }
+    // back to back for about `seconds`
+    const int loops = std::max(1, (int)(seconds * 1e3 / std::max(bms, 1e-3f)));
+    RSD_CUDA_TRY(cudaEventRecord(e0, stream));
+    for (int r = 0; r < loops; ++r) launch();
+    RSD_CUDA_TRY(cudaEventRecord(e1, stream));
+    RSD_CUDA_TRY(cudaEventSynchronize(e1));
+    float tms = 0;
+    RSD_CUDA_TRY(cudaEventElapsedTime(&tms, e0, e1));
+    RSD_CUDA_TRY(cudaGetLastError());
+    int errs[4] = {0, 0, 0, 0};
+    RSD_CUDA_TRY(cudaMemcpy(errs, err, sizeof(errs), cudaMemcpyDeviceToHost));
+    if (errs[ERR_TIMEOUT]) return RSD_ERR_TIMEOUT;
+    *best = flops / (bms * 1e-3) / 1e12;
+    *sustained = flops * loops / (tms * 1e-3) / 1e12;
+    return RSD_OK;
+}
+
 // kind 0: inner panel update, 1: panel solve (B = inverted diagonal block),
 // 2: U -= X X^T (lower tiles), 3: outer panel update, TC_GENERAL: map indices, alpha and
 // rounding taken from the task (128- or 256-wide tiles by the widest N).

@@ -195,6 +195,18 @@ struct Handle {
     // PCG's preconditioner application as a captured graph (see pcg_apply)
     cudaGraphExec_t apply_exec = nullptr;
     int solve_calls = 0, apply_graph_launches = 0;
+    // rsd_apply_static: descriptors whose vectors and counters point into the library's
+    // file-scope device array (prepared at setup; static_ok false when it does not fit)
+    FrontDesc* d_static_fronts = nullptr;
+    std::vector<int> static_level_first;
+    int* static_ticket = nullptr;
+    size_t static_clear_bytes = 0, static_need = 0;
+    bool static_ok = false;
+    // bounded waits of the substitution sweeps: clock cycles before a wait gives up
+    long long wait_cycles = 4000000000LL;
+    // fault injection (rsd_inject_drop_sweep_item): level whose next upward sweep runs
+    // without its first work item, or -1
+    int inject_drop_level = -1;
 };
 
 // Copy `bytes` from host memory into the handle's pinned staging area and return the
@@ -250,11 +262,17 @@ int launch_extend_add(Handle& h, int li);
 int run_factor_level(Handle& h, int li);
 int run_apply(Handle& h, const double* r, double* z);
 int run_apply_static(Handle& h, const double* r, double* z);
+// descriptors of the allocation-free application, written to d_slots (n_nodes entries of
+// the arena) at setup, with the handle's device current
+int static_apply_prepare(Handle& h, FrontDesc* d_slots);
 // one level of a substitution sweep with explicit descriptors/items: forward reads the
 // right-hand side from `in` (through I), backward writes the solution to `out`
 int sweep_with(Handle& h, int li, bool forward, const FrontDesc* fronts, const int* items, int n_items,
                const double* in, double* out, int* ticket);
 int paper_extend_add(Handle& h);
+// peak probes of this library's GEMM kernels (rsd_peak_gemm)
+int gemm_tc_peak(int n, int reps, double seconds, cudaStream_t stream, int num_sms, double* best, double* sustained);
+int gemm_simt_peak(int prec, int n, int reps, double seconds, cudaStream_t st, double* best, double* sustained);
 int run_apply_paper(Handle& h, const double* r, double* z);
 int spmv(Handle& h, const double* x, double* y);
 
