@@ -53,12 +53,22 @@ extern "C" {
                               V-hat = V limit of Algorithm 2): the preconditioner is K^-1
                               up to the rounding of the stored factors                  */
 #define RSD_MODE_PAPER 1   /* Algorithm 2 with the V-hat truncation of Sec. 3.2: each
-                              interface solves S~ u_I = g exactly, S~ = K_II minus the
-                              leaf terms sum_l K_Il K_ll^-1 K_lI (Algorithm 1 with V-hat =
-                              the leaves coupled to I); g and the back-substitution use
-                              leaf unknowns only.  Needs every leaf on the deepest level.
-                              Not symmetric in general; PCG still converges on the SPD
-                              systems here, GMRES is the paper's outer solver.           */
+                              interface solves S~ u_I = g, S~ = K_II minus the leaf terms
+                              sum_l K_Il K_ll^-1 K_lI (Algorithm 1 with V-hat = the leaves
+                              coupled to I), exactly (rsd_options.gamma = 0) or by gamma
+                              GMRES iterations; g and the back-substitution use leaf
+                              unknowns only.  Needs every leaf on the deepest level.
+                              Not symmetric in general, and not linear for gamma > 0
+                              (rsd_solve then runs FGMRES, the paper's outer GMRES in
+                              flexible form); with gamma = 0 PCG still converges on the
+                              SPD systems here.                                          */
+
+/* outer Krylov method of rsd_solve */
+#define RSD_KRYLOV_AUTO   0  /* PCG, except FGMRES for paper mode with gamma > 0           */
+#define RSD_KRYLOV_PCG    1  /* preconditioned CG (needs a fixed SPD preconditioner)     */
+#define RSD_KRYLOV_FGMRES 2  /* flexible right-preconditioned GMRES(restart), modified
+                                Gram-Schmidt: the preconditioner may change from one
+                                application to the next (finite gamma)                 */
 
 #define RSD_MEM_HOST   0
 #define RSD_MEM_DEVICE 1
@@ -93,6 +103,14 @@ typedef struct {
     int64_t wait_cycles; /* bound of every wait of the substitution sweeps on another CTA's
                             progress, in SM clock cycles (<= 0: 4e9, about 2 s); a wait that
                             reaches it raises RSD_ERR_TIMEOUT (see rsd_apply)                */
+    int32_t gamma;       /* paper mode only: 0 = each interface system S~ u = g is solved
+                            exactly by a dense factorisation of S~ (formed at setup);
+                            gamma > 0 = gamma GMRES iterations on it (Sec. 3.2, Algorithm 2),
+                            x0 = 0, no restart, modified Gram-Schmidt, no inner
+                            preconditioner, S~ applied matrix-free (Algorithm 1): no
+                            interface front is formed or factored                          */
+    int32_t krylov;      /* RSD_KRYLOV_*                                                    */
+    int32_t restart;     /* FGMRES restart length (<= 0: 30)                                */
 } rsd_options;
 
 typedef struct {
@@ -119,8 +137,9 @@ typedef struct {
  * 0 front assembly, 1 extend-add, 2 tcgen05 GEMM, 3 CUDA-core GEMM, 4 diagonal block
  * factor+inverse, 5 CUDA-core panel solve, 6 upward sweep, 7 downward sweep,
  * 8 sweep gathers, 9 Krylov vector/SpMV kernels, 10 FP16 copy of a TF32 level's factor
- * (the entries the sweeps read).                                                      */
-#define RSD_PROFILE_CLASSES 11
+ * (the entries the sweeps read), 11 inner GMRES of paper mode with gamma > 0 (matrix-free
+ * S-MatVecs and Arnoldi steps of one interface level; bytes = the X rows streamed).     */
+#define RSD_PROFILE_CLASSES 12
 typedef struct {
     int64_t launches[RSD_PROFILE_CLASSES];
     double  ms[RSD_PROFILE_CLASSES];

@@ -15,12 +15,14 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (RSD_MEM_DEVICE, RSD_MEM_HOST, RSD_MODE_EXACT, RSD_MODE_PAPER, RSD_PREC_FP32,
-                   RSD_PREC_FP64, RSD_PREC_TF32, RSDError, check)
+from ._lib import (RSD_KRYLOV_AUTO, RSD_KRYLOV_FGMRES, RSD_KRYLOV_PCG, RSD_MEM_DEVICE, RSD_MEM_HOST,
+                   RSD_MODE_EXACT, RSD_MODE_PAPER, RSD_PREC_FP32, RSD_PREC_FP64, RSD_PREC_TF32, RSDError,
+                   check)
 
 __all__ = ["RSD", "grid_problem", "grid_sizes", "grid_exp", "coef_grad", "diffusion_solve",
            "DiffusionSolve", "launch_count", "peak_gemm", "RSDError", "RSD_PREC_FP64", "RSD_PREC_FP32",
-           "RSD_PREC_TF32", "RSD_MODE_EXACT", "RSD_MODE_PAPER"]
+           "RSD_PREC_TF32", "RSD_MODE_EXACT", "RSD_MODE_PAPER", "RSD_KRYLOV_AUTO", "RSD_KRYLOV_PCG",
+           "RSD_KRYLOV_FGMRES"]
 
 
 def peak_gemm(prec: int, n: int, reps: int = 5, seconds: float = 4.0) -> tuple[float, float]:
@@ -116,7 +118,7 @@ class RSD:
               dof_node: torch.Tensor, parent, prec_leaf: int = RSD_PREC_TF32,
               prec_mid: int = RSD_PREC_TF32, prec_root: int = RSD_PREC_FP64,
               maxit: int = 200, profile: bool = False, mode: int = RSD_MODE_EXACT,
-              wait_cycles: int = 0) -> "RSD":
+              wait_cycles: int = 0, gamma: int = 0, krylov: int = 0, restart: int = 0) -> "RSD":
         lib = _lib.load()
         dev = rowptr.is_cuda
         if not (col.is_cuda == dev and val.is_cuda == dev and dof_node.is_cuda == dev):
@@ -131,7 +133,8 @@ class RSD:
                            RSD_MEM_DEVICE if dev else RSD_MEM_HOST)
         tree = _lib.rsd_tree(len(par), par.ctypes.data)
         opt = _lib.rsd_options(mode, prec_leaf, prec_mid, prec_root, maxit,
-                               _stream() if torch.cuda.is_available() else 0, int(profile), wait_cycles)
+                               _stream() if torch.cuda.is_available() else 0, int(profile), wait_cycles,
+                               gamma, krylov, restart)
         out = C.c_void_p()
         rc = lib.rsd_setup(C.byref(csr), _ptr(dof_node), C.byref(tree), C.byref(opt), C.byref(out))
         if rc != 0:

@@ -24,6 +24,10 @@ RSD_PREC_FP64 = 0
 RSD_PREC_FP32 = 1
 RSD_PREC_TF32 = 2
 
+RSD_KRYLOV_AUTO = 0
+RSD_KRYLOV_PCG = 1
+RSD_KRYLOV_FGMRES = 2
+
 RSD_MODE_EXACT = 0
 RSD_MODE_PAPER = 1
 RSD_MEM_HOST = 0
@@ -53,7 +57,8 @@ class rsd_tree(C.Structure):
 class rsd_options(C.Structure):
     _fields_ = [("mode", C.c_int32), ("prec_leaf", C.c_int32), ("prec_mid", C.c_int32),
                 ("prec_root", C.c_int32), ("maxit", C.c_int32), ("stream", C.c_void_p),
-                ("profile", C.c_int32), ("wait_cycles", C.c_int64)]
+                ("profile", C.c_int32), ("wait_cycles", C.c_int64), ("gamma", C.c_int32),
+                ("krylov", C.c_int32), ("restart", C.c_int32)]
 
 
 class rsd_stats(C.Structure):
@@ -69,12 +74,13 @@ class rsd_info_t(C.Structure):
 
 
 PROFILE_CLASSES = ["assemble", "extend_add", "gemm_tcgen05", "gemm_simt", "diag_factor",
-                   "panel_solve_simt", "sweep_up", "sweep_down", "sweep_gather", "krylov", "factor_copy16"]
+                   "panel_solve_simt", "sweep_up", "sweep_down", "sweep_gather", "krylov", "factor_copy16",
+                   "gamma_gmres"]
 
 
 class rsd_profile_t(C.Structure):
-    _fields_ = [("launches", C.c_int64 * 11), ("ms", C.c_double * 11), ("flops", C.c_double * 11),
-                ("bytes", C.c_double * 11), ("host_analysis_ms", C.c_double),
+    _fields_ = [("launches", C.c_int64 * 12), ("ms", C.c_double * 12), ("flops", C.c_double * 12),
+                ("bytes", C.c_double * 12), ("host_analysis_ms", C.c_double),
                 ("host_parts_ms", C.c_double * 6), ("host_issue_ms", C.c_double)]
 
 

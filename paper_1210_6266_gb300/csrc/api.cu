@@ -677,6 +677,11 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
     const int nl = a.max_depth + 1;
     const bool paper = h.opt.mode == RSD_MODE_PAPER;
     h.paper = paper;
+    // paper mode with gamma inner GMRES iterations: only the leaf fronts are stored
+    const bool gmode = paper && h.opt.gamma > 0;
+    h.gamma = gmode ? h.opt.gamma : 0;
+    h.krylov = h.opt.krylov == RSD_KRYLOV_AUTO ? (gmode ? RSD_KRYLOV_FGMRES : RSD_KRYLOV_PCG) : h.opt.krylov;
+    h.restart = h.opt.restart > 0 ? h.opt.restart : 30;
     // paper mode keeps only the interface block of internal fronts (V-hat truncation);
     // leaves keep their coupling block, which yields the updates scattered into S~
     auto beff = [&](int t) { return (paper && !a.children[t].empty()) ? 0 : (int)a.B[t].size(); };
@@ -702,6 +707,7 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
         for (int t : L.nodes) leaves &= a.children[t].empty();
         L.prec = level_precision(h.opt, d, leaves);
         if (!valid_prec(L.prec)) return RSD_ERR_ARG;
+        L.factored = !(gmode && d < nl - 1);
     }
     // ---- memory plan ----
     size_t off = 0;
@@ -723,7 +729,7 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
     h.factor_elems = 0; h.factor_bytes = 0; h.setup_flops = 0;
     for (int d = nl - 1; d >= 0; --d) {
         Level& L = h.levels[d];
-        const size_t es = elem_bytes(L.prec);
+        const size_t es = L.factored ? elem_bytes(L.prec) : 0;   // unfactored: no storage
         L.h16 = L.prec == RSD_PREC_TF32 && !paper;
         // P regions of a level are contiguous, then the U regions
         lvlP[d] = off;
@@ -731,6 +737,7 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
             const int s = a.I_off[t + 1] - a.I_off[t], b = beff(t);
             const int ldp = std::max(32, round_up(s, 32));
             fp[t].P = take((size_t)(s + b) * ldp * es);
+            if (!L.factored) continue;
             h.factor_elems += (int64_t)s * (s + 1) / 2 + (int64_t)s * b;
             h.factor_bytes += ((int64_t)s * (s + 1) / 2 + (int64_t)s * b) * (int64_t)es;
             h.setup_flops += (double)s * s * s / 3.0 + (double)s * s * b + (double)s * b * b;
@@ -746,7 +753,7 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
         for (int t : L.nodes) {
             const int s = a.I_off[t + 1] - a.I_off[t], b = beff(t);
             const int nd = (s + NB - 1) / NB;
-            fp[t].D = take((size_t)std::max(1, nd) * NB * NB * es);
+            fp[t].D = take((size_t)(L.factored ? std::max(1, nd) : 0) * NB * NB * es);
             fp[t].V = take((size_t)(s + b + 32) * es);
         }
         if (L.h16)                                   // FP16 factor copies after the level's other regions
@@ -768,10 +775,120 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
     // paper mode extras
     const size_t o_pvec = paper ? take(sizeof(double) * 3 * (size_t)a.n) : 0;
     const size_t o_nref = paper ? take(sizeof(NodeRef) * a.n_nodes) : 0;
+    // paper mode, gamma = 0: colour the leaves so that no two leaves of a class share an
+    // interface DOF (greedy, in slot order); their updates are added into S~ class by class
+    std::vector<int> color_slots;
+    if (paper && !gmode) {
+        const Level& Ll = h.levels[nl - 1];
+        const int nleaf = (int)Ll.nodes.size();
+        std::vector<int> cnt(a.n + 1, 0);
+        for (int t : Ll.nodes)
+            for (int dof : a.B[t]) cnt[dof + 1]++;
+        for (int i = 0; i < a.n; ++i) cnt[i + 1] += cnt[i];
+        std::vector<int> lst(cnt[a.n]), fill(cnt.begin(), cnt.end() - 1);
+        for (int l = 0; l < nleaf; ++l)
+            for (int dof : a.B[Ll.nodes[l]]) lst[fill[dof]++] = l;
+        std::vector<int> color(nleaf, 0), stamp;
+        int ncol = 0;
+        for (int l = 0; l < nleaf; ++l) {
+            for (int dof : a.B[Ll.nodes[l]])
+                for (int q = cnt[dof]; q < cnt[dof + 1] && lst[q] < l; ++q) {
+                    const int c = color[lst[q]];
+                    if ((int)stamp.size() <= c) stamp.resize(c + 1, -1);
+                    stamp[c] = l;
+                }
+            int c = 0;
+            while (c < (int)stamp.size() && stamp[c] == l) ++c;
+            color[l] = c;
+            ncol = std::max(ncol, c + 1);
+        }
+        h.paper_color_off.assign(ncol + 1, 0);
+        for (int l = 0; l < nleaf; ++l) h.paper_color_off[color[l] + 1]++;
+        for (int c = 0; c < ncol; ++c) h.paper_color_off[c + 1] += h.paper_color_off[c];
+        color_slots.resize(nleaf);
+        std::vector<int> pos(h.paper_color_off.begin(), h.paper_color_off.end() - 1);
+        for (int l = 0; l < nleaf; ++l) color_slots[pos[color[l]]++] = l;
+    }
+    const size_t o_pcolor = take(sizeof(int) * std::max<size_t>(1, color_slots.size()));
     const size_t o_nleaf = paper ? take(a.n_nodes) : 0;
     const size_t o_ndepth = paper ? take(sizeof(int) * a.n_nodes) : 0;
     const size_t o_fsolve = paper ? take(sizeof(FrontDesc) * a.n_nodes) : 0;
     const size_t o_tpaper = paper ? take(sizeof(int) * (2 + 4 * nl)) : 0;
+    // paper mode with gamma > 0: packed interface vectors and leaf couplings per level
+    struct GammaHost { std::vector<int> if_off, if_dofs, cl_ptr, cl_row, cl_pos, ci_ptr, ci_leaf, ci_row; double xbytes = 0; };
+    std::vector<GammaHost> gh;
+    std::vector<int> pk_pos, tl_off;
+    size_t o_gamma = 0, gamma_bytes = 0, gm_maxS = 0, gm_maxIf = 0;
+    if (gmode) {
+        if (h.gamma > 32) { set_last_error("gamma > 32"); return RSD_ERR_ARG; }
+        gh.resize(nl - 1);
+        pk_pos.assign(a.n, -1);
+        const Level& Ll = h.levels[nl - 1];
+        const size_t les = elem_bytes(Ll.prec);
+        for (int d = 0; d < nl - 1; ++d) {
+            GammaHost& G = gh[d];
+            G.if_off.assign(1, 0);
+            for (int t : h.levels[d].nodes) {
+                for (int q = a.I_off[t]; q < a.I_off[t + 1]; ++q) {
+                    pk_pos[a.I_dofs[q]] = (int)G.if_dofs.size();
+                    G.if_dofs.push_back(a.I_dofs[q]);
+                }
+                G.if_off.push_back((int)G.if_dofs.size());
+            }
+            gm_maxS = std::max(gm_maxS, G.if_dofs.size());
+            gm_maxIf = std::max(gm_maxIf, h.levels[d].nodes.size());
+        }
+        tl_off.assign(1, 0);
+        for (int t : Ll.nodes) tl_off.push_back(tl_off.back() + (a.I_off[t + 1] - a.I_off[t]));
+        for (int d = 0; d < nl - 1; ++d) {
+            GammaHost& G = gh[d];
+            const int S = (int)G.if_dofs.size();
+            G.cl_ptr.assign(1, 0);
+            std::vector<int> cnt(S + 1, 0);
+            for (int t : Ll.nodes) {
+                const int sl = a.I_off[t + 1] - a.I_off[t];
+                for (size_t r = 0; r < a.B[t].size(); ++r) {
+                    const int dof = a.B[t][r];
+                    if (a.depth[a.owner[dof]] != d) continue;
+                    G.cl_row.push_back((int)r);
+                    G.cl_pos.push_back(pk_pos[dof]);
+                    cnt[pk_pos[dof] + 1]++;
+                    G.xbytes += 2.0 * sl * (double)les;
+                }
+                G.cl_ptr.push_back((int)G.cl_row.size());
+            }
+            for (int p = 0; p < S; ++p) cnt[p + 1] += cnt[p];
+            G.ci_ptr = cnt;
+            G.ci_leaf.resize(G.cl_row.size());
+            G.ci_row.resize(G.cl_row.size());
+            std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+            for (size_t l = 0; l < Ll.nodes.size(); ++l)
+                for (int k = G.cl_ptr[l]; k < G.cl_ptr[l + 1]; ++k) {
+                    const int q = fill[G.cl_pos[k]]++;
+                    G.ci_leaf[q] = (int)l;
+                    G.ci_row[q] = G.cl_row[k];
+                }
+        }
+        size_t gb = 0;
+        auto acc = [&](size_t bytes) { gb += align_up(std::max<size_t>(bytes, 4), 256); };
+        for (auto& G : gh)
+            for (auto* v : {&G.if_off, &G.if_dofs, &G.cl_ptr, &G.cl_row, &G.cl_pos, &G.ci_ptr, &G.ci_leaf, &G.ci_row})
+                acc(sizeof(int) * v->size());
+        acc(sizeof(int) * pk_pos.size());
+        acc(sizeof(int) * tl_off.size());
+        acc(sizeof(double) * (size_t)tl_off.back());
+        acc(sizeof(double) * gm_maxS);
+        acc(sizeof(double) * gm_maxS * (h.gamma + 1));
+        acc(sizeof(double) * gm_maxIf * (h.gamma + 1) * h.gamma);
+        acc(sizeof(double) * gm_maxIf);
+        acc(sizeof(int) * gm_maxIf);
+        gamma_bytes = gb;
+        o_gamma = take(gamma_bytes);
+    }
+    const bool fg = h.krylov == RSD_KRYLOV_FGMRES;
+    const int m = h.restart;
+    if (fg && m > 64) { set_last_error("FGMRES restart > 64"); return RSD_ERR_ARG; }
+    const size_t o_fg = fg ? take(sizeof(double) * ((size_t)(2 * m + 1) * a.n + (size_t)(m + 1) * m + m + 64)) : 0;
     const size_t o_child = take(sizeof(int) * a.n_nodes);
     const size_t o_vecs = take(sizeof(double) * 4 * (size_t)a.n + 4096);
     const size_t o_partial = take(sizeof(double) * 2048);
@@ -949,6 +1066,66 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
         RSD_CUDA_TRY(cudaMemcpyAsync(d_solve, stage_host(h, solve.data(), sizeof(FrontDesc) * solve.size()), sizeof(FrontDesc) * solve.size(), cudaMemcpyHostToDevice, st));
         RSD_CUDA_TRY(cudaStreamSynchronize(st));     // host vectors above go out of scope
     }
+    if (!color_slots.empty()) {
+        h.d_paper_color_slots = (int*)(A + o_pcolor);
+        RSD_CUDA_TRY(cudaMemcpyAsync(h.d_paper_color_slots, stage_host(h, color_slots.data(), sizeof(int) * color_slots.size()),
+                                     sizeof(int) * color_slots.size(), cudaMemcpyHostToDevice, st));
+    }
+    if (gmode) {
+        char* cur = A + o_gamma;
+        auto put = [&](const std::vector<int>& v) -> int* {
+            int* d = (int*)cur;
+            cur += align_up(std::max<size_t>(sizeof(int) * v.size(), 4), 256);
+            return d;
+        };
+        auto upload = [&](int* d, const std::vector<int>& v) -> int {
+            if (!v.empty())
+                RSD_CUDA_TRY(cudaMemcpyAsync(d, stage_host(h, v.data(), sizeof(int) * v.size()), sizeof(int) * v.size(),
+                                             cudaMemcpyHostToDevice, st));
+            return RSD_OK;
+        };
+        h.gamma_levels.assign(nl - 1, GammaLevel{});
+        for (int d = 0; d < nl - 1; ++d) {
+            GammaHost& G = gh[d];
+            GammaLevel& D = h.gamma_levels[d];
+            D.n_if = (int)h.levels[d].nodes.size();
+            D.S = (int)G.if_dofs.size();
+            D.xbytes = G.xbytes;
+            int** dst[8] = {&D.d_if_off, &D.d_if_dofs, &D.d_cl_ptr, &D.d_cl_row, &D.d_cl_pos, &D.d_ci_ptr, &D.d_ci_leaf, &D.d_ci_row};
+            const std::vector<int>* src[8] = {&G.if_off, &G.if_dofs, &G.cl_ptr, &G.cl_row, &G.cl_pos, &G.ci_ptr, &G.ci_leaf, &G.ci_row};
+            for (int q = 0; q < 8; ++q) {
+                *dst[q] = put(*src[q]);
+                RSD_TRY(upload(*dst[q], *src[q]));
+            }
+        }
+        h.d_pk_pos = put(pk_pos);
+        RSD_TRY(upload(h.d_pk_pos, pk_pos));
+        h.d_tl_off = put(tl_off);
+        RSD_TRY(upload(h.d_tl_off, tl_off));
+        auto dput = [&](size_t count) {
+            double* d = (double*)cur;
+            cur += align_up(std::max<size_t>(sizeof(double) * count, 4), 256);
+            return d;
+        };
+        h.d_tl = dput((size_t)tl_off.back());
+        h.d_gm_w = dput(gm_maxS);
+        h.d_gm_V = dput(gm_maxS * (h.gamma + 1));
+        h.d_gm_H = dput(gm_maxIf * (h.gamma + 1) * h.gamma);
+        h.d_gm_beta = dput(gm_maxIf);
+        h.d_gm_kused = (int*)cur;
+        cur += align_up(sizeof(int) * std::max<size_t>(gm_maxIf, 1), 256);
+        if ((size_t)(cur - (A + o_gamma)) > gamma_bytes) { set_last_error("gamma plan overflow"); return RSD_ERR_ARG; }
+    }
+    if (fg) {
+        h.d_fg_V = (double*)(A + o_fg);
+        h.d_fg_Z = h.d_fg_V + (size_t)(m + 1) * a.n;
+        h.d_fg_H = h.d_fg_Z + (size_t)m * a.n;
+        h.d_fg_y = h.d_fg_H + (size_t)(m + 1) * m;
+        if (!h.h_fg && cudaMallocHost((void**)&h.h_fg, sizeof(double) * 256) != cudaSuccess) {
+            cudaGetLastError();
+            return RSD_ERR_NOMEM;
+        }
+    }
     RSD_TRY(static_apply_prepare(h, (FrontDesc*)(A + o_sfronts)));
     // the tensor-core levels need tensor maps over the fronts just placed
     RSD_TRY(gemm_tc_prepare(h));
@@ -957,6 +1134,7 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
     // Every level's fronts (disjoint arena regions) are zeroed and receive their K entries
     // up front, leaves first: the device does this while the host plans the leaf level.
     for (int d = nl - 1; d >= 0; --d) {
+        if (!h.levels[d].factored) continue;
         RSD_TRY(launch_zero_fronts(h, d));
         RSD_TRY(launch_assemble_fronts(h, d, h.d_rowptr, h.d_col, h.d_val, d_owner, d_rank, d_tin, d_tout));
     }
@@ -972,8 +1150,10 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
         // every interface front is K_II plus leaf updates: factor the leaves, scatter
         // their updates into S~, then factor the interfaces
         RSD_TRY(run_factor_level(h, nl - 1));
-        RSD_TRY(paper_extend_add(h));
-        for (int d = nl - 2; d >= 0; --d) RSD_TRY(run_factor_level(h, d));
+        if (!gmode) {
+            RSD_TRY(paper_extend_add(h));
+            for (int d = nl - 2; d >= 0; --d) RSD_TRY(run_factor_level(h, d));
+        }
     }
     RSD_CUDA_TRY(cudaStreamSynchronize(st));
     stage_reset(h);                                   // every staged upload has completed
@@ -1096,6 +1276,7 @@ extern "C" void rsd_destroy(rsd_handle hh) {
     if (h.arena) arena_give(h.arena, h.arena_capacity, h.device);
     for (auto& blk : h.stage_blocks) pinned_give(blk.first, blk.second);
     if (h.h_scal) cudaFreeHost(h.h_scal);
+    if (h.h_fg) cudaFreeHost(h.h_fg);
     delete hh;
 }
 
@@ -1113,6 +1294,12 @@ extern "C" int rsd_setup(const rsd_csr* K, const int32_t* dof_node, const rsd_tr
     o.maxit = 200;
     if (opt) o = *opt;
     if (o.mode != RSD_MODE_EXACT && o.mode != RSD_MODE_PAPER) return RSD_ERR_ARG;
+    if (o.gamma < 0 || (o.gamma > 0 && o.mode != RSD_MODE_PAPER)) return RSD_ERR_ARG;
+    if (o.krylov < RSD_KRYLOV_AUTO || o.krylov > RSD_KRYLOV_FGMRES) return RSD_ERR_ARG;
+    if (o.krylov == RSD_KRYLOV_PCG && o.gamma > 0) {
+        set_last_error("PCG needs a fixed preconditioner: gamma > 0 makes it change with its input");
+        return RSD_ERR_ARG;
+    }
     const auto t_host0 = std::chrono::steady_clock::now();
     Analysis a;
     a.n = K->n;
@@ -1229,7 +1416,7 @@ extern "C" int rsd_check(rsd_handle hh) {
 
 extern "C" int rsd_solve(rsd_handle hh, const double* f, double* u, double tol, rsd_stats* st) {
     if (!hh || !f || !u || !(tol > 0)) return RSD_ERR_ARG;
-    const int rc = pcg(hh->h, f, u, tol, st);
+    const int rc = hh->h.krylov == RSD_KRYLOV_FGMRES ? fgmres(hh->h, f, u, tol, st) : pcg(hh->h, f, u, tol, st);
     const int chk = rsd_check(hh);
     if (chk != RSD_OK) return chk;
     return rc;
@@ -1308,6 +1495,7 @@ extern "C" int rsd_front_factor(rsd_handle hh, int32_t node, double* out) {
     Handle& h = hh->h;
     RSD_CUDA_TRY(cudaStreamSynchronize(h.stream));
     const Level& L = h.levels[h.node_level[node]];
+    if (!L.factored) return RSD_ERR_ARG;
     const FrontDesc& f = L.fronts[h.node_slot[node]];
     const size_t es = elem_bytes(L.prec);
     std::vector<char> buf((size_t)f.N * f.ldp * es);

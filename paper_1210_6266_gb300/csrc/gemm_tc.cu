@@ -540,19 +540,19 @@ TcState* state_of(Handle& h) { return (TcState*)h.tc_state; }
 
 int gemm_tc_prepare(Handle& h) {
     bool any = false;
-    for (auto& L : h.levels) any |= L.prec == RSD_PREC_TF32;
+    for (auto& L : h.levels) any |= L.prec == RSD_PREC_TF32 && L.factored;
     if (!any) return RSD_OK;
     auto* st = new TcState();
     h.tc_state = st;
     int widest = 0;
     for (auto& L : h.levels)
-        if (L.prec == RSD_PREC_TF32) widest = std::max(widest, (int)L.fronts.size());
+        if (L.prec == RSD_PREC_TF32 && L.factored) widest = std::max(widest, (int)L.fronts.size());
     st->scr_base = 2 * h.n_nodes;
     st->scr_slots = widest;
     std::vector<CUtensorMap> maps(2 * (size_t)h.n_nodes + TC_SCR_MAPS * (size_t)widest);
     std::memset(maps.data(), 0, maps.size() * sizeof(CUtensorMap));
     for (auto& L : h.levels) {
-        if (L.prec != RSD_PREC_TF32) continue;
+        if (L.prec != RSD_PREC_TF32 || !L.factored) continue;
         for (auto& f : L.fronts) {
             RSD_TRY(encode_2d(&maps[2 * (size_t)f.node], f.P, f.s, f.N, f.ldp));
             RSD_TRY(encode_2d(&maps[2 * (size_t)f.node + 1], f.Dinv, NB, std::max(1, f.nd) * NB, NB));

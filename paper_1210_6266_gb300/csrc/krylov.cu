@@ -4,6 +4,7 @@
 // Dot products use a fixed grid and a fixed-order second pass, so results are
 // bitwise reproducible run to run.  Step lengths stay on the device.
 #include <cmath>
+#include <vector>
 
 #include "rsd_internal.cuh"
 
@@ -102,6 +103,45 @@ __global__ void k_residual(int n, const int64_t* __restrict__ rowptr, const int*
     if (row < n && sub == 0) r[row] = f[row] - s;
 }
 
+// One modified Gram-Schmidt step of FGMRES, fused with the next inner product:
+// w -= h v (h read from the device, skipped when v is null), then per-block partial sums
+// of w . next (next = w gives ||w||^2 after the update).
+__global__ void k_mgs_step(int64_t n, const double* __restrict__ hval, const double* __restrict__ v,
+                           double* __restrict__ w, const double* __restrict__ next, double* __restrict__ partial) {
+    const double hv = v ? *hval : 0.0;
+    double s = 0;
+    for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) {
+        double wi = w[i];
+        if (v) {
+            wi -= hv * v[i];
+            w[i] = wi;
+        }
+        s += wi * (next == w ? wi : next[i]);
+    }
+    s = block_sum(s);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// dst = src / sqrt(*nrm2) (left unchanged when the norm is zero); *hout = sqrt(*nrm2)
+__global__ void k_scale_by_norm(int64_t n, const double* __restrict__ nrm2, const double* __restrict__ src,
+                                double* __restrict__ dst, double* __restrict__ hout) {
+    const double nv = sqrt(fmax(*nrm2, 0.0));
+    if (blockIdx.x == 0 && threadIdx.x == 0 && hout) *hout = nv;
+    if (!(nv > 0.0)) return;
+    const double inv = 1.0 / nv;
+    for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) dst[i] = src[i] * inv;
+}
+
+// x += sum_q y_q Z_q, q = 0 .. k-1 in order
+__global__ void k_fg_update(int64_t n, int k, const double* __restrict__ y, const double* __restrict__ Z,
+                            double* __restrict__ x) {
+    for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) {
+        double a = x[i];
+        for (int q = 0; q < k; ++q) a += y[q] * Z[(int64_t)q * n + i];
+        x[i] = a;
+    }
+}
+
 int dot(Handle& h, const double* a, const double* b, int slot) {
     const int pi = prof_begin(h, K_KRYLOV);
     k_dot_partial<<<RED_BLOCKS, RT, 0, h.stream>>>(h.n, a, b, h.d_partial);
@@ -165,7 +205,132 @@ static int pcg_apply(Handle& h, const double* r, double* z) {
     return RSD_OK;
 }
 
-// Scalar slots: 0 rz (even iterations), 1 pq, 2 rr, 3 rz (odd iterations), 4 ff, 5 true rr
+// Flexible right-preconditioned GMRES(m) in FP64 from x = 0 (the outer solver when the
+// preconditioner changes with its input, as paper mode's gamma inner iterations make it):
+// per cycle r = f - K x, v_0 = r / ||r||; per step z_j = M v_j, w = K z_j, modified
+// Gram-Schmidt against v_0..v_j, v_{j+1} = w / h_{j+1,j}; the Hessenberg columns come to
+// the host (one synchronisation per step), where Givens rotations give the least-squares
+// residual estimate |g_{j+1}| / ||f|| tested against tol; at the end of a cycle
+// x += Z y.  Stops on the estimate, then recomputes the true residual in FP64.
+int fgmres(Handle& h, const double* f, double* x, double tol, rsd_stats* st) {
+    ++h.solve_calls;
+    const int64_t n = h.n;
+    const int m = h.restart;
+    const int maxit = h.opt.maxit > 0 ? h.opt.maxit : 200;
+    rsd_stats local{};
+    rsd_stats* S = st ? st : &local;
+    *S = rsd_stats{};
+    double* V = h.d_fg_V;
+    double* Z = h.d_fg_Z;
+    double* Hd = h.d_fg_H;                       // column j at Hd + j (m + 1)
+    double* w = h.d_q;
+    RSD_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n, h.stream));
+    RSD_TRY(dot(h, f, f, 4));
+    double ff;
+    RSD_TRY(fetch(h, 4, &ff));
+    const double fnorm = std::sqrt(ff);
+    S->history[0] = 1.0;
+    if (fnorm == 0.0) { S->relres = 0; return RSD_OK; }
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+    int it = 0;
+    double est = 1.0;
+    int rc = RSD_ERR_NOCONV;
+    bool first = true;
+    while (it < maxit) {
+        // r = f - K x into v_0 and beta = ||r||
+        if (first) {
+            RSD_CUDA_TRY(cudaMemcpyAsync(V, f, sizeof(double) * n, cudaMemcpyDeviceToDevice, h.stream));
+            RSD_CUDA_TRY(cudaMemcpyAsync(h.d_scal + 6, h.d_scal + 4, sizeof(double), cudaMemcpyDeviceToDevice, h.stream));
+        } else {
+            const int64_t threads = n * 4;
+            k_residual<<<(unsigned)((threads + RT - 1) / RT), RT, 0, h.stream>>>(h.n, h.d_rowptr, h.d_col, h.d_val, x, f, V);
+            count_launch();
+            RSD_TRY(dot(h, V, V, 6));
+        }
+        double bb;
+        RSD_TRY(fetch(h, 6, &bb));
+        const double beta = std::sqrt(std::max(bb, 0.0));
+        if (!first && beta / fnorm <= tol) { rc = RSD_OK; break; }
+        first = false;
+        k_scale_by_norm<<<RED_BLOCKS, RT, 0, h.stream>>>(n, h.d_scal + 6, V, V, nullptr);
+        count_launch();
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int jl = -1;
+        bool done = false;
+        for (int j = 0; j < m; ++j) {
+            double* zj = Z + (int64_t)j * n;
+            const double* vj = V + (int64_t)j * n;
+            RSD_TRY(h.paper ? run_apply_paper(h, vj, zj) : run_apply(h, vj, zj));
+            RSD_TRY(spmv(h, zj, w));
+            double* hc = Hd + (int64_t)j * (m + 1);
+            const int pk = prof_begin(h, K_KRYLOV);
+            for (int i = 0; i <= j + 1; ++i) {
+                // step i: subtract h_{i-1,j} v_{i-1} (i > 0), then w . v_i (or ||w||^2 at i = j + 1)
+                const double* vprev = i > 0 ? V + (int64_t)(i - 1) * n : nullptr;
+                const double* nxt = i <= j ? V + (int64_t)i * n : w;
+                k_mgs_step<<<RED_BLOCKS, RT, 0, h.stream>>>(n, i > 0 ? hc + i - 1 : nullptr, vprev, w, nxt, h.d_partial);
+                k_reduce_final<<<1, RT, 0, h.stream>>>(h.d_partial, RED_BLOCKS, i <= j ? hc + i : h.d_scal + 7);
+                count_launch(2);
+            }
+            k_scale_by_norm<<<RED_BLOCKS, RT, 0, h.stream>>>(n, h.d_scal + 7, w, V + (int64_t)(j + 1) * n, hc + j + 1);
+            count_launch();
+            prof_end(h, pk, (4.0 * (j + 2)) * n, (24.0 * (j + 2) + 16.0) * n);
+            RSD_CUDA_TRY(cudaGetLastError());
+            RSD_CUDA_TRY(cudaMemcpyAsync(h.h_fg, hc, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, h.stream));
+            RSD_CUDA_TRY(cudaStreamSynchronize(h.stream));
+            for (int i = 0; i <= j + 1; ++i) H[(size_t)i * m + j] = h.h_fg[i];
+            for (int i = 0; i < j; ++i) {             // earlier rotations
+                const double t0 = H[(size_t)i * m + j], t1 = H[(size_t)(i + 1) * m + j];
+                H[(size_t)i * m + j] = cs[i] * t0 + sn[i] * t1;
+                H[(size_t)(i + 1) * m + j] = -sn[i] * t0 + cs[i] * t1;
+            }
+            const double a = H[(size_t)j * m + j], b = H[(size_t)(j + 1) * m + j];
+            const double den = std::hypot(a, b);
+            cs[j] = den > 0 ? a / den : 1.0;
+            sn[j] = den > 0 ? b / den : 0.0;
+            H[(size_t)j * m + j] = den;
+            H[(size_t)(j + 1) * m + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            ++it;
+            jl = j;
+            est = std::fabs(g[j + 1]) / fnorm;
+            if (it < 64) S->history[it] = est;
+            if (!(est == est)) { rc = RSD_ERR_NOT_SPD; done = true; break; }
+            if (est <= tol || it >= maxit || !(b > 0.0)) break;
+        }
+        if (jl >= 0) {
+            for (int r = jl; r >= 0; --r) {
+                double t = g[r];
+                for (int c = r + 1; c <= jl; ++c) t -= H[(size_t)r * m + c] * y[c];
+                y[r] = H[(size_t)r * m + r] != 0.0 ? t / H[(size_t)r * m + r] : 0.0;
+            }
+            for (int q = 0; q <= jl; ++q) h.h_fg[128 + q] = y[q];
+            RSD_CUDA_TRY(cudaMemcpyAsync(h.d_fg_y, h.h_fg + 128, sizeof(double) * (jl + 1), cudaMemcpyHostToDevice, h.stream));
+            k_fg_update<<<RED_BLOCKS, RT, 0, h.stream>>>(n, jl + 1, h.d_fg_y, Z, x);
+            count_launch();
+            RSD_CUDA_TRY(cudaGetLastError());
+            RSD_CUDA_TRY(cudaStreamSynchronize(h.stream));    // h_fg is rewritten by the next cycle
+        }
+        if (done) break;
+        if (est <= tol) { rc = RSD_OK; break; }
+    }
+    S->iterations = it;
+    S->relres_recursive = est;
+    const int64_t threads = n * 4;
+    k_residual<<<(unsigned)((threads + RT - 1) / RT), RT, 0, h.stream>>>(h.n, h.d_rowptr, h.d_col, h.d_val, x, f, w);
+    count_launch();
+    RSD_CUDA_TRY(cudaGetLastError());
+    RSD_TRY(dot(h, w, w, 5));
+    double tr;
+    RSD_TRY(fetch(h, 5, &tr));
+    S->relres = std::sqrt(tr) / fnorm;
+    return rc;
+}
+
+// Scalar slots: 0 rz (even iterations), 1 pq, 2 rr, 3 rz (odd iterations), 4 ff, 5 true rr,
+// 6 FGMRES ||r||^2, 7 FGMRES ||w||^2
 int pcg(Handle& h, const double* f, double* u, double tol, rsd_stats* st) {
     ++h.solve_calls;
     const int64_t n = h.n;

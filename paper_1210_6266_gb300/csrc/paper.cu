@@ -1,5 +1,6 @@
-// Paper mode: Algorithm 2 with the V-hat truncation of Sec. 3.2, interface systems solved
-// exactly (dense S~, the gamma -> infinity limit of the inner solve).
+// Paper mode: Algorithm 2 with the V-hat truncation of Sec. 3.2.  With gamma = 0 the
+// interface systems are solved exactly (dense S~, the gamma -> infinity limit of the inner
+// solve; this file); with gamma > 0 by gamma GMRES iterations (paper_gamma.cu).
 //
 // Setup: every leaf l is factored as in exact mode, which also yields its update
 // U_l = -K_{B l} K_ll^-1 K_{l B}.  An interface t's front is only its s_t x s_t block
@@ -23,11 +24,15 @@ namespace rsd {
 namespace {
 
 // Leaf updates into the interface fronts: U_l(i, j) is added to S~_t when both B_l[i]
-// and B_l[j] belong to t.  Several leaves feed the same entries, so the adds are atomic.
+// and B_l[j] belong to t.  Leaves that share an interface DOF feed the same entries, so
+// the leaves are split into colour classes with no shared DOF (setup) and added class by
+// class, one launch per class: within a launch every target has one writer, and every
+// entry receives its leaves' terms in a fixed order.
 template <typename Tu>
-__global__ void k_paper_extend_add(const FrontDesc* __restrict__ leaves, const NodeRef* __restrict__ refs,
-                                   const int* __restrict__ owner, const int* __restrict__ rank) {
-    const FrontDesc f = leaves[blockIdx.y];
+__global__ void k_paper_extend_add(const FrontDesc* __restrict__ leaves, const int* __restrict__ slots,
+                                   const NodeRef* __restrict__ refs, const int* __restrict__ owner,
+                                   const int* __restrict__ rank) {
+    const FrontDesc f = leaves[slots[blockIdx.y]];
     const Tu* U = (const Tu*)f.U;
     for (int i = blockIdx.x; i < f.b; i += gridDim.x) {
         const int gi = f.Bd[i];
@@ -38,9 +43,9 @@ __global__ void k_paper_extend_add(const FrontDesc* __restrict__ leaves, const N
             if (owner[gj] != oi) continue;
             const int rj = rank[gj];
             const int r = max(ri, rj), c = min(ri, rj);
-            const double v = (double)U[(int64_t)i * f.ldu + j];
-            if (ref.f64) atomicAdd((double*)ref.P + (int64_t)r * ref.ldp + c, v);
-            else atomicAdd((float*)ref.P + (int64_t)r * ref.ldp + c, (float)v);
+            const Tu v = U[(int64_t)i * f.ldu + j];
+            if (ref.f64) ((double*)ref.P)[(int64_t)r * ref.ldp + c] += (double)v;
+            else ((float*)ref.P)[(int64_t)r * ref.ldp + c] += (float)v;
         }
     }
 }
@@ -100,13 +105,19 @@ int paper_extend_add(Handle& h) {
     const int dl = (int)h.levels.size() - 1;              // all leaves live on the deepest level
     Level& L = h.levels[dl];
     if (L.fronts.empty() || L.max_b == 0) return RSD_OK;
-    dim3 grid((unsigned)std::max(1, std::min(4096, L.max_b)), (unsigned)L.fronts.size());
     const int pi = prof_begin(h, K_EXTEND);
-    if (is_fp64(L.prec))
-        k_paper_extend_add<double><<<grid, 256, 0, h.stream>>>(L.d_fronts, h.d_node_ref, h.d_owner, h.d_rank);
-    else
-        k_paper_extend_add<float><<<grid, 256, 0, h.stream>>>(L.d_fronts, h.d_node_ref, h.d_owner, h.d_rank);
-    count_launch();
+    for (size_t c = 0; c + 1 < h.paper_color_off.size(); ++c) {
+        const int n = h.paper_color_off[c + 1] - h.paper_color_off[c];
+        if (n == 0) continue;
+        const int* slots = h.d_paper_color_slots + h.paper_color_off[c];
+        dim3 grid((unsigned)std::max(1, std::min(4096, L.max_b)), (unsigned)n);
+        if (is_fp64(L.prec))
+            k_paper_extend_add<double><<<grid, 256, 0, h.stream>>>(L.d_fronts, slots, h.d_node_ref, h.d_owner, h.d_rank);
+        else
+            k_paper_extend_add<float><<<grid, 256, 0, h.stream>>>(L.d_fronts, slots, h.d_node_ref, h.d_owner, h.d_rank);
+        count_launch();
+        RSD_CUDA_TRY(cudaGetLastError());
+    }
     double bytes = 0;
     for (auto& f : L.fronts) bytes += 0.5 * f.b * (f.b + 1.0) * 3.0 * elem_bytes(L.prec);
     prof_end(h, pi, 0.0, bytes);
@@ -147,9 +158,14 @@ int run_apply_paper(Handle& h, const double* r, double* z) {
                                             h.d_node_leaf, r, z, h.d_pg);
         count_launch();
         RSD_CUDA_TRY(cudaGetLastError());
-        // u = S~^-1 g, written into z on the level's interfaces
-        RSD_TRY(sweep_with(h, d, true, L.d_fronts_solve, L.d_fwd_items_solve, L.n_fwd_items_solve, h.d_pg, z, ticket++));
-        RSD_TRY(sweep_with(h, d, false, L.d_fronts_solve, L.d_bwd_items, L.n_bwd_items, h.d_pg, z, ticket++));
+        // u = S~^-1 g (dense factor) or gamma GMRES iterations on S~ u = g, written into z
+        // on the level's interfaces
+        if (h.gamma > 0) {
+            RSD_TRY(gamma_interface_solve(h, d, z));
+        } else {
+            RSD_TRY(sweep_with(h, d, true, L.d_fronts_solve, L.d_fwd_items_solve, L.n_fwd_items_solve, h.d_pg, z, ticket++));
+            RSD_TRY(sweep_with(h, d, false, L.d_fronts_solve, L.d_bwd_items, L.n_bwd_items, h.d_pg, z, ticket++));
+        }
         // leaf corrections
         dim3 gw((unsigned)std::max(1, std::min(64, (Lleaf.max_s + 7) / 8)), (unsigned)nleaf);
         k_paper_w<<<gw, 256, 0, h.stream>>>(Lleaf.d_fronts_solve, h.d_rowptr, h.d_col, h.d_val, h.d_owner,

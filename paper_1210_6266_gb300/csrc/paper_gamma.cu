@@ -1,0 +1,248 @@
+// Paper mode with gamma inner GMRES iterations (Sec. 3.2, Algorithms 1 and 2): every
+// interface system S~_t u_t = g_t of a tree level is solved approximately by gamma
+// GMRES iterations from u = 0 (no restart, modified Gram-Schmidt, no preconditioner),
+// all interfaces of the level at once; S~ is never formed.
+//
+// S-MatVec (Algorithm 1) for interface t:
+//     y = K_{I_t I_t} x - sum_{l in V-hat_t} K_{I_t l} K_ll^-1 K_{l I_t} x.
+// Setup factors every leaf front [K_ll K_lB; K_Bl .] into L_l and X_l = K_{B_l l} L_l^-T
+// (rows: the ancestor DOFs B_l coupled to l), so with R = the rows of X_l that lie in I_t,
+//     K_{I_t l} K_ll^-1 K_{l I_t} = (K_{I_t l} L_l^-T)(L_l^-1 K_{l I_t}) = X_l[R] X_l[R]^T:
+// the two leaf solves of Algorithm 1 become two streaming products with X_l[R], the
+// second of which sums, per interface DOF, the leaves that touch it in a fixed order.
+// V-hat_t is exactly the set of leaves with a nonempty R for t (a leaf couples to its
+// ancestors' DOFs only, Eq. 3.1).
+//
+// Vectors of a level are packed: interface slot i of the level owns positions
+// [if_off[i], if_off[i+1]) in I_t order (pk_pos maps a global DOF to its position).
+// Every reduction has a fixed order, so results are bitwise reproducible.
+#include <algorithm>
+#include <cmath>
+
+#include "rsd_internal.cuh"
+
+namespace rsd {
+namespace {
+
+constexpr int GT = 512;           // threads of the per-interface GMRES kernels
+constexpr int GAMMA_MAX = 32;     // largest gamma (inner iterations) the kernels hold
+
+// Block-wide sum in a fixed order; every thread receives the result.
+__device__ double block_sum_all(double v, double* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        double t = lane < nw ? red[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) red[32] = t;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+// t_l = X_l[R_l]^T x for every leaf with rows coupled to the level; one CTA per
+// (leaf, 256 columns), rows walked in ascending order, four partial sums per thread.
+template <typename T>
+__global__ void __launch_bounds__(256) k_smv_leaf(const FrontDesc* __restrict__ leaves, const int* __restrict__ cl_ptr,
+                                                  const int* __restrict__ cl_row, const int* __restrict__ cl_pos,
+                                                  const int* __restrict__ tl_off, const double* __restrict__ x,
+                                                  double* __restrict__ tl) {
+    const int l = blockIdx.x;
+    const int k0 = cl_ptr[l], k1 = cl_ptr[l + 1];
+    if (k0 == k1) return;
+    const int s = leaves[l].s, ldp = leaves[l].ldp;
+    const T* X = (const T*)leaves[l].P + (int64_t)s * ldp;
+    const int c = blockIdx.y * blockDim.x + threadIdx.x;
+    if (c >= s) return;
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    int k = k0;
+    for (; k + 4 <= k1; k += 4) {
+        const double v0 = (double)X[(int64_t)cl_row[k] * ldp + c], v1 = (double)X[(int64_t)cl_row[k + 1] * ldp + c];
+        const double v2 = (double)X[(int64_t)cl_row[k + 2] * ldp + c], v3 = (double)X[(int64_t)cl_row[k + 3] * ldp + c];
+        a0 += v0 * x[cl_pos[k]];
+        a1 += v1 * x[cl_pos[k + 1]];
+        a2 += v2 * x[cl_pos[k + 2]];
+        a3 += v3 * x[cl_pos[k + 3]];
+    }
+    for (; k < k1; ++k) a0 += (double)X[(int64_t)cl_row[k] * ldp + c] * x[cl_pos[k]];
+    tl[tl_off[l] + c] = (a0 + a1) + (a2 + a3);
+}
+
+// y_p = (K_{I_t I_t} x)_p - sum over the (leaf, row) pairs of position p of X_l[row] . t_l;
+// one warp per packed position.
+template <typename T>
+__global__ void __launch_bounds__(256) k_smv_iface(int S, const int* __restrict__ if_dofs, const int64_t* __restrict__ rowptr,
+                                                   const int* __restrict__ col, const double* __restrict__ val,
+                                                   const int* __restrict__ owner, const int* __restrict__ pk_pos,
+                                                   const int* __restrict__ ci_ptr, const int* __restrict__ ci_leaf,
+                                                   const int* __restrict__ ci_row, const FrontDesc* __restrict__ leaves,
+                                                   const int* __restrict__ tl_off, const double* __restrict__ tl,
+                                                   const double* __restrict__ x, double* __restrict__ y) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; p < S; p += warps) {
+        const int dof = if_dofs[p];
+        const int o = owner[dof];
+        double acc = 0;
+        for (int64_t k = rowptr[dof] + lane; k < rowptr[dof + 1]; k += 32) {
+            const int j = col[k];
+            if (owner[j] == o) acc += val[k] * x[pk_pos[j]];
+        }
+        for (int q = ci_ptr[p]; q < ci_ptr[p + 1]; ++q) {
+            const int l = ci_leaf[q];
+            const int s = leaves[l].s, ldp = leaves[l].ldp;
+            const T* row = (const T*)leaves[l].P + (int64_t)(s + ci_row[q]) * ldp;
+            const double* t = tl + tl_off[l];
+            double d = 0;
+            for (int c = lane; c < s; c += 32) d += (double)row[c] * t[c];
+            acc -= d;
+        }
+#pragma unroll
+        for (int o2 = 16; o2 > 0; o2 >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o2);
+        if (lane == 0) y[p] = acc;
+    }
+}
+
+// v_0 = g / beta on every interface of the level (g indexed by global DOF).
+__global__ void __launch_bounds__(GT) k_gm_init(const int* __restrict__ if_off, const int* __restrict__ if_dofs,
+                                                const double* __restrict__ g, double* __restrict__ V,
+                                                double* __restrict__ beta, int* __restrict__ kused) {
+    __shared__ double red[33];
+    const int i = blockIdx.x;
+    const int o = if_off[i], s = if_off[i + 1] - o;
+    double a = 0;
+    for (int e = threadIdx.x; e < s; e += blockDim.x) { const double v = g[if_dofs[o + e]]; a += v * v; }
+    const double b = sqrt(block_sum_all(a, red));
+    if (threadIdx.x == 0) { beta[i] = b; kused[i] = b > 0.0 ? 0 : -1; }
+    const double inv = b > 0.0 ? 1.0 / b : 0.0;
+    for (int e = threadIdx.x; e < s; e += blockDim.x) V[o + e] = g[if_dofs[o + e]] * inv;
+}
+
+// Arnoldi step j with modified Gram-Schmidt on w = S~ v_j, per interface: h_qj = <w, v_q>,
+// w -= h_qj v_q for q = 0..j in turn, h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j}.  An
+// interface whose h_{j+1,j} falls to 1e-14 beta (exact breakdown) stops with j + 1
+// columns; one that completes min(gamma, s) steps stops with that many.
+__global__ void __launch_bounds__(GT) k_gm_mgs(int j, int gamma, int S, const int* __restrict__ if_off,
+                                               double* __restrict__ w, double* __restrict__ V, double* __restrict__ H,
+                                               const double* __restrict__ beta, int* __restrict__ kused) {
+    __shared__ double red[33];
+    const int i = blockIdx.x;
+    const int o = if_off[i], s = if_off[i + 1] - o;
+    const int m = min(gamma, s);
+    if (kused[i] != 0 || j >= m) return;
+    double* Hi = H + (int64_t)i * (gamma + 1) * gamma;
+    for (int q = 0; q <= j; ++q) {
+        const double* vq = V + (int64_t)q * S + o;
+        double a = 0;
+        for (int e = threadIdx.x; e < s; e += blockDim.x) a += w[o + e] * vq[e];
+        const double hq = block_sum_all(a, red);
+        for (int e = threadIdx.x; e < s; e += blockDim.x) w[o + e] -= hq * vq[e];
+        if (threadIdx.x == 0) Hi[q * gamma + j] = hq;
+    }
+    double a = 0;
+    for (int e = threadIdx.x; e < s; e += blockDim.x) a += w[o + e] * w[o + e];
+    const double nrm = sqrt(block_sum_all(a, red));
+    if (threadIdx.x == 0) Hi[(j + 1) * gamma + j] = nrm;
+    if (nrm <= 1e-14 * beta[i]) {
+        if (threadIdx.x == 0) kused[i] = j + 1;
+        return;
+    }
+    double* vn = V + (int64_t)(j + 1) * S + o;
+    for (int e = threadIdx.x; e < s; e += blockDim.x) vn[e] = w[o + e] / nrm;
+    if (j + 1 == m && threadIdx.x == 0) kused[i] = m;
+}
+
+// u_t = V_k y with y the least-squares solution of min || beta e1 - H_k y || (H_k the
+// (k+1) x k Hessenberg matrix; Givens rotations), written to z on the interface DOFs.
+__global__ void __launch_bounds__(GT) k_gm_finish(int gamma, int S, const int* __restrict__ if_off,
+                                                  const int* __restrict__ if_dofs, const double* __restrict__ V,
+                                                  const double* __restrict__ H, const double* __restrict__ beta,
+                                                  const int* __restrict__ kused, double* __restrict__ z) {
+    __shared__ double y[GAMMA_MAX];
+    __shared__ double R[GAMMA_MAX + 1][GAMMA_MAX];      // rotated Hessenberg
+    __shared__ double gv[GAMMA_MAX + 1];
+    const int i = blockIdx.x;
+    const int o = if_off[i], s = if_off[i + 1] - o;
+    const int ku = kused[i];
+    const int k = ku < 0 ? 0 : (ku == 0 ? min(gamma, s) : ku);
+    if (threadIdx.x == 0 && k > 0) {
+        const double* Hi = H + (int64_t)i * (gamma + 1) * gamma;
+        for (int r = 0; r <= k; ++r)
+            for (int c = 0; c < k; ++c) R[r][c] = (r <= c + 1) ? Hi[r * gamma + c] : 0.0;
+        for (int r = 0; r <= k; ++r) gv[r] = 0.0;
+        gv[0] = beta[i];
+        for (int c = 0; c < k; ++c) {
+            const double a = R[c][c], b = R[c + 1][c];
+            const double den = hypot(a, b);
+            const double cs = den > 0 ? a / den : 1.0, sn = den > 0 ? b / den : 0.0;
+            for (int cc = c; cc < k; ++cc) {
+                const double t0 = R[c][cc], t1 = R[c + 1][cc];
+                R[c][cc] = cs * t0 + sn * t1;
+                R[c + 1][cc] = -sn * t0 + cs * t1;
+            }
+            const double g0 = gv[c], g1 = gv[c + 1];
+            gv[c] = cs * g0 + sn * g1;
+            gv[c + 1] = -sn * g0 + cs * g1;
+        }
+        for (int r = k - 1; r >= 0; --r) {
+            double t = gv[r];
+            for (int c = r + 1; c < k; ++c) t -= R[r][c] * y[c];
+            y[r] = R[r][r] != 0.0 ? t / R[r][r] : 0.0;
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < s; e += blockDim.x) {
+        double u = 0;
+        for (int q = 0; q < k; ++q) u += y[q] * V[(int64_t)q * S + o + e];
+        z[if_dofs[o + e]] = u;
+    }
+}
+
+}  // namespace
+
+// Apply-time launches of one level's inner GMRES: reads g (global DOF order, h.d_pg) on
+// the level's interface DOFs and writes u_t = GMRES_gamma(S~_t, g_t) into z there.
+int gamma_interface_solve(Handle& h, int li, double* z) {
+    GammaLevel& G = h.gamma_levels[li];
+    if (G.n_if == 0 || G.S == 0) return RSD_OK;
+    const Level& Ll = h.levels.back();
+    const int nleaf = (int)Ll.fronts.size();
+    const bool f64 = is_fp64(Ll.prec);
+    const int gam = h.gamma;
+    const int pi = prof_begin(h, K_GAMMA);
+    k_gm_init<<<G.n_if, GT, 0, h.stream>>>(G.d_if_off, G.d_if_dofs, h.d_pg, h.d_gm_V, h.d_gm_beta, h.d_gm_kused);
+    count_launch();
+    const dim3 gl((unsigned)nleaf, (unsigned)std::max(1, (Ll.max_s + 255) / 256));
+    const unsigned gi = (unsigned)std::max(1, std::min(h.num_sms * 8, (G.S + 7) / 8));
+    double bytes = 0;
+    for (int j = 0; j < gam; ++j) {
+        const double* vj = h.d_gm_V + (int64_t)j * G.S;
+        if (f64) {
+            k_smv_leaf<double><<<gl, 256, 0, h.stream>>>(Ll.d_fronts, G.d_cl_ptr, G.d_cl_row, G.d_cl_pos, h.d_tl_off, vj, h.d_tl);
+            k_smv_iface<double><<<gi, 256, 0, h.stream>>>(G.S, G.d_if_dofs, h.d_rowptr, h.d_col, h.d_val, h.d_owner, h.d_pk_pos,
+                                                          G.d_ci_ptr, G.d_ci_leaf, G.d_ci_row, Ll.d_fronts, h.d_tl_off, h.d_tl,
+                                                          vj, h.d_gm_w);
+        } else {
+            k_smv_leaf<float><<<gl, 256, 0, h.stream>>>(Ll.d_fronts, G.d_cl_ptr, G.d_cl_row, G.d_cl_pos, h.d_tl_off, vj, h.d_tl);
+            k_smv_iface<float><<<gi, 256, 0, h.stream>>>(G.S, G.d_if_dofs, h.d_rowptr, h.d_col, h.d_val, h.d_owner, h.d_pk_pos,
+                                                         G.d_ci_ptr, G.d_ci_leaf, G.d_ci_row, Ll.d_fronts, h.d_tl_off, h.d_tl,
+                                                         vj, h.d_gm_w);
+        }
+        k_gm_mgs<<<G.n_if, GT, 0, h.stream>>>(j, gam, G.S, G.d_if_off, h.d_gm_w, h.d_gm_V, h.d_gm_H, h.d_gm_beta, h.d_gm_kused);
+        count_launch(3);
+        bytes += G.xbytes;
+    }
+    k_gm_finish<<<G.n_if, GT, 0, h.stream>>>(gam, G.S, G.d_if_off, G.d_if_dofs, h.d_gm_V, h.d_gm_H, h.d_gm_beta,
+                                             h.d_gm_kused, z);
+    count_launch();
+    prof_end(h, pi, 0.0, bytes);
+    RSD_CUDA_TRY(cudaGetLastError());
+    return RSD_OK;
+}
+
+}  // namespace rsd

@@ -87,7 +87,7 @@ struct GemmTask {
 
 // Kernel classes for launch counting and the optional CUDA-event profile.
 enum KClass { K_ASSEMBLE = 0, K_EXTEND, K_GEMM_TC, K_GEMM_SIMT, K_POTRF, K_TRSM, K_FWD, K_BWD,
-              K_GATHER, K_KRYLOV, K_COPY16, K_CLASSES };
+              K_GATHER, K_KRYLOV, K_COPY16, K_GAMMA, K_CLASSES };
 
 // Per-handle profile: one event pair per launch of a class, with the algorithmic
 // flops and bytes of that launch; reduced on demand by rsd_profile().
@@ -127,6 +127,22 @@ struct Level {
     FrontDesc* d_fronts_solve = nullptr;
     int* d_fwd_items_solve = nullptr;
     int n_fwd_items_solve = 0;
+    // false for the interface levels of paper mode with gamma > 0: no front is stored
+    bool factored = true;
+};
+
+// Paper mode with gamma inner GMRES iterations: one interface level's packed vectors and
+// its couplings to the leaves (see paper_gamma.cu).  Interface slot i owns positions
+// [if_off[i], if_off[i+1]); if_dofs maps a position to its global DOF.  cl_*: per leaf
+// (CSR over leaf slots), the rows r of the leaf's X block that lie in the level's
+// interfaces and their packed positions; ci_*: per packed position (CSR), the (leaf, row)
+// pairs that touch it, leaves ascending.
+struct GammaLevel {
+    int n_if = 0, S = 0;
+    int *d_if_off = nullptr, *d_if_dofs = nullptr;
+    int *d_cl_ptr = nullptr, *d_cl_row = nullptr, *d_cl_pos = nullptr;
+    int *d_ci_ptr = nullptr, *d_ci_leaf = nullptr, *d_ci_row = nullptr;
+    double xbytes = 0;            // bytes of X one S-MatVec streams (its rows read twice)
 };
 
 // Diagonal blocks per substitution-sweep item: a single-front FP32 level (a root) pairs
@@ -184,6 +200,10 @@ struct Handle {
     NodeRef* d_node_ref = nullptr;
     double *d_pg = nullptr, *d_pw = nullptr, *d_pz = nullptr;   // g, w and leaf-solve scratch
     int* d_ticket_paper = nullptr;
+    // leaf slots by colour class (no two leaves of a class share an interface DOF) for the
+    // fixed-order accumulation of the leaf updates into S~
+    std::vector<int> paper_color_off;
+    int* d_paper_color_slots = nullptr;
     // pinned host staging for per-launch uploads (append-only; see stage_host)
     std::vector<std::pair<char*, size_t>> stage_blocks;
     size_t stage_cur = 0, stage_off = 0;
@@ -202,6 +222,18 @@ struct Handle {
     int* static_ticket = nullptr;
     size_t static_clear_bytes = 0, static_need = 0;
     bool static_ok = false;
+    // paper mode, gamma > 0 (see GammaLevel); gamma_levels[d] for interface level d
+    int gamma = 0;
+    std::vector<GammaLevel> gamma_levels;
+    int* d_pk_pos = nullptr;             // global DOF -> position in its level's packed vectors
+    int* d_tl_off = nullptr;             // leaf slot -> offset of its t_l in d_tl
+    double* d_tl = nullptr;              // X_l^T x per leaf
+    double *d_gm_w = nullptr, *d_gm_V = nullptr, *d_gm_H = nullptr, *d_gm_beta = nullptr;
+    int* d_gm_kused = nullptr;
+    // outer Krylov method (RSD_KRYLOV_PCG or RSD_KRYLOV_FGMRES) and FGMRES storage
+    int krylov = RSD_KRYLOV_PCG, restart = 30;
+    double *d_fg_V = nullptr, *d_fg_Z = nullptr, *d_fg_H = nullptr, *d_fg_y = nullptr;
+    double* h_fg = nullptr;              // pinned host mirror of H columns and y
     // bounded waits of the substitution sweeps: clock cycles before a wait gives up
     long long wait_cycles = 4000000000LL;
     // fault injection (rsd_inject_drop_sweep_item): level whose next upward sweep runs
@@ -274,6 +306,8 @@ int paper_extend_add(Handle& h);
 int gemm_tc_peak(int n, int reps, double seconds, cudaStream_t stream, int num_sms, double* best, double* sustained);
 int gemm_simt_peak(int prec, int n, int reps, double seconds, cudaStream_t st, double* best, double* sustained);
 int run_apply_paper(Handle& h, const double* r, double* z);
+int gamma_interface_solve(Handle& h, int li, double* z);
+int fgmres(Handle& h, const double* f, double* u, double tol, rsd_stats* st);
 int spmv(Handle& h, const double* x, double* y);
 
 }  // namespace rsd

@@ -1,0 +1,151 @@
+"""Paper mode with gamma inner GMRES iterations (Sec. 3.2, Algorithms 1-2) on the GPU,
+with FGMRES outside, against the oracle's literal recursive Algorithm 2 (PaperRSD with
+gamma > 0: matrix-free S-MatVec, MGS-GMRES from x0 = 0) and its flexible GMRES.
+
+Also: paper mode's fixed-order accumulation of the leaf updates into S~ (gamma = 0) and
+the gamma-mode application are bitwise reproducible."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import fem, fem2d, partition
+from oracle.krylov import fgmres
+from oracle.rsd_exact import ExactFactor
+from oracle.rsd_paper import PaperRSD
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rsd():
+    from paper_1210_6266_gb300 import build
+    build.build()
+    import paper_1210_6266_gb300 as m
+    return m
+
+
+def _case(n, depth, seed=95):
+    kappa = np.exp(synth.normal(seed, (n - 1) ** 3))
+    f = synth.uniform(seed + 1, (n - 2) ** 3)
+    A = fem.assemble(n, kappa)
+    sym = partition.Symbolic(A, partition.octree_owner(n, depth, fem.interior_coords(n)),
+                             partition.octree_parent(depth))
+    return kappa, f, A, sym
+
+
+def _setup(rsd, prob, prec, gamma, **kw):
+    return rsd.RSD.setup(prob["rowptr"], prob["col"], prob["val"], prob["dof_node"], prob["parent"],
+                         prec_leaf=prec, prec_mid=prec, prec_root=prec, mode=rsd.RSD_MODE_PAPER,
+                         gamma=gamma, **kw)
+
+
+@pytest.mark.parametrize("n,depth", [(14, 2), (17, 2), (23, 3)])
+@pytest.mark.parametrize("gamma", [2, 4, 8])
+def test_gamma_apply_matches_oracle_recursion(rsd, n, depth, gamma):
+    kappa, f, A, sym = _case(n, depth)
+    R = PaperRSD(A, sym, gamma)
+    prob = rsd.grid_problem(n, depth, kappa, f)
+    h = _setup(rsd, prob, rsd.RSD_PREC_FP64, gamma)
+    for seed in (97, 98):
+        r = synth.uniform(seed, A.shape[0])
+        z = h.apply(torch.as_tensor(r, device="cuda")).cpu().numpy()
+        zr = R.apply_recursive(r)
+        assert np.abs(z - zr).max() <= 1e-10 * np.abs(zr).max(), (seed, np.abs(z - zr).max() / np.abs(zr).max())
+    h.check()
+    h.close()
+
+
+@pytest.mark.parametrize("n,depth,gamma", [(17, 2, 4), (23, 3, 8)])
+def test_gamma_fgmres_matches_oracle_iterations(rsd, n, depth, gamma):
+    kappa, f, A, sym = _case(n, depth)
+    prob = rsd.grid_problem(n, depth, kappa, f)
+    b = fem.load_vector(n, f)
+    R = PaperRSD(A, sym, gamma)
+    _, it_ref, _ = fgmres(A, b, R.apply_recursive, 1e-10, restart=30)
+    h = _setup(rsd, prob, rsd.RSD_PREC_FP64, gamma, maxit=400)
+    u, st = h.solve(prob["b"], tol=1e-10)
+    assert np.linalg.norm(b - A @ u.cpu().numpy()) <= 1e-9 * np.linalg.norm(b)
+    assert abs(st["iterations"] - it_ref) <= 1, (st["iterations"], it_ref)
+    h.close()
+    # the mixed form: TF32 leaf factors, FP64 inner GMRES and FGMRES
+    h = _setup(rsd, prob, rsd.RSD_PREC_TF32, gamma, maxit=400)
+    u, st = h.solve(prob["b"], tol=1e-8)
+    assert st["relres"] <= 1e-8
+    assert np.linalg.norm(b - A @ u.cpu().numpy()) <= 1e-8 * np.linalg.norm(b)
+    assert st["iterations"] <= it_ref + 3, (st["iterations"], it_ref)
+    h.close()
+
+
+@pytest.mark.parametrize("N,P", [(17, 8), (33, 8), (17, 128)])
+def test_gamma_2d_strip_iterations_match_oracle(rsd, N, P):
+    """The paper's own setting (Sec. 4, Problem 1): a strip of P sub-domains, binary tree,
+    random exact solution, rtol 1e-12.  The GPU's outer iteration counts equal the
+    oracle's (which reproduces Table 1 within 30 %) up to one iteration."""
+    A, coords = fem2d.strip_poisson(N, P)
+    owner = fem2d.binary_owner(N, P, coords)
+    parent = fem2d.binary_parent(int(np.log2(P)))
+    sym = partition.Symbolic(A, owner, parent)
+    f = A @ synth.uniform(11, A.shape[0])
+    rowptr = torch.as_tensor(A.indptr.astype(np.int64))
+    col = torch.as_tensor(A.indices.astype(np.int32))
+    val = torch.as_tensor(A.data.astype(np.float64))
+    dof_node = torch.as_tensor(owner.astype(np.int32))
+    fd = torch.as_tensor(f, device="cuda")
+    for gamma in (2, 4, 8):
+        _, it_ref, _ = fgmres(A, f, PaperRSD(A, sym, gamma).apply_recursive, 1e-12, restart=30)
+        h = rsd.RSD.setup(rowptr, col, val, dof_node, parent, prec_leaf=rsd.RSD_PREC_FP64,
+                          prec_mid=rsd.RSD_PREC_FP64, prec_root=rsd.RSD_PREC_FP64,
+                          mode=rsd.RSD_MODE_PAPER, gamma=gamma, maxit=500)
+        u, st = h.solve(fd, tol=1e-12)
+        assert np.linalg.norm(f - A @ u.cpu().numpy()) <= 1e-11 * np.linalg.norm(f)
+        assert abs(st["iterations"] - it_ref) <= 1, (N, P, gamma, st["iterations"], it_ref)
+        h.close()
+
+
+def test_gamma_apply_is_deterministic(rsd):
+    n, depth, gamma = 20, 2, 4
+    kappa, f, A, sym = _case(n, depth)
+    prob = rsd.grid_problem(n, depth, kappa, f)
+    r = torch.as_tensor(synth.uniform(99, A.shape[0]), device="cuda")
+    outs = []
+    for _ in range(2):
+        h = _setup(rsd, prob, rsd.RSD_PREC_TF32, gamma)
+        outs += [h.apply(r).clone(), h.apply(r).clone()]
+        h.close()
+    assert all(torch.equal(outs[0], z) for z in outs[1:])
+
+
+def test_paper_gamma0_setup_and_apply_are_bitwise_repeatable(rsd):
+    """gamma = 0: the leaf updates are added into every S~ in a fixed order (colour
+    classes of leaves that share no interface DOF), so repeated setups give identical
+    interface factors and applications."""
+    n, depth = 20, 2
+    kappa, f, A, sym = _case(n, depth)
+    prob = rsd.grid_problem(n, depth, kappa, f)
+    r = torch.as_tensor(synth.uniform(100, A.shape[0]), device="cuda")
+    interfaces = [t for t in range(sym.n_nodes) if sym.children[t]]
+    facs, zs = [], []
+    for _ in range(2):
+        h = _setup(rsd, prob, rsd.RSD_PREC_TF32, 0)
+        facs.append([h.front_factor(t) for t in interfaces])
+        zs.append(h.apply(r).clone())
+        h.close()
+    for a, b in zip(*facs):
+        assert np.array_equal(a, b)
+    assert torch.equal(zs[0], zs[1])
+
+
+def test_fgmres_with_exact_preconditioner_converges_in_one_iteration(rsd):
+    n, depth = 17, 2
+    kappa, f, A, sym = _case(n, depth)
+    prob = rsd.grid_problem(n, depth, kappa, f)
+    h = rsd.RSD.setup(prob["rowptr"], prob["col"], prob["val"], prob["dof_node"], prob["parent"],
+                      prec_leaf=rsd.RSD_PREC_FP64, prec_mid=rsd.RSD_PREC_FP64, prec_root=rsd.RSD_PREC_FP64,
+                      krylov=rsd.RSD_KRYLOV_FGMRES)
+    u, st = h.solve(prob["b"], tol=1e-10)
+    assert st["iterations"] == 1, st
+    b = fem.load_vector(n, f)
+    uref = ExactFactor(A, sym).apply(b)
+    assert np.abs(u.cpu().numpy() - uref).max() <= 1e-10 * np.abs(uref).max()
+    h.close()
