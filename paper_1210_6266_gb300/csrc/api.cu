@@ -815,10 +815,10 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
     const size_t o_fsolve = paper ? take(sizeof(FrontDesc) * a.n_nodes) : 0;
     const size_t o_tpaper = paper ? take(sizeof(int) * (2 + 4 * nl)) : 0;
     // paper mode with gamma > 0: packed interface vectors and leaf couplings per level
-    struct GammaHost { std::vector<int> if_off, if_dofs, cl_ptr, cl_row, cl_pos, ci_ptr, ci_leaf, ci_row; double xbytes = 0; };
+    struct GammaHost { std::vector<int> if_off, if_dofs, cl_ptr, cl_row, cl_pos, cl_leaf, ci_ptr, ci_k; double xbytes = 0; };
     std::vector<GammaHost> gh;
     std::vector<int> pk_pos, tl_off;
-    size_t o_gamma = 0, gamma_bytes = 0, gm_maxS = 0, gm_maxIf = 0;
+    size_t o_gamma = 0, gamma_bytes = 0, gm_maxS = 0, gm_maxIf = 0, gm_maxK = 0;
     if (gmode) {
         if (h.gamma > 32) { set_last_error("gamma > 32"); return RSD_ERR_ARG; }
         gh.resize(nl - 1);
@@ -852,6 +852,7 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
                     if (a.depth[a.owner[dof]] != d) continue;
                     G.cl_row.push_back((int)r);
                     G.cl_pos.push_back(pk_pos[dof]);
+                    G.cl_leaf.push_back((int)(G.cl_ptr.size() - 1));
                     cnt[pk_pos[dof] + 1]++;
                     G.xbytes += 2.0 * sl * (double)les;
                 }
@@ -859,20 +860,15 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
             }
             for (int p = 0; p < S; ++p) cnt[p + 1] += cnt[p];
             G.ci_ptr = cnt;
-            G.ci_leaf.resize(G.cl_row.size());
-            G.ci_row.resize(G.cl_row.size());
+            G.ci_k.resize(G.cl_row.size());
             std::vector<int> fill(cnt.begin(), cnt.end() - 1);
-            for (size_t l = 0; l < Ll.nodes.size(); ++l)
-                for (int k = G.cl_ptr[l]; k < G.cl_ptr[l + 1]; ++k) {
-                    const int q = fill[G.cl_pos[k]]++;
-                    G.ci_leaf[q] = (int)l;
-                    G.ci_row[q] = G.cl_row[k];
-                }
+            for (size_t k = 0; k < G.cl_row.size(); ++k) G.ci_k[fill[G.cl_pos[k]]++] = (int)k;
+            gm_maxK = std::max(gm_maxK, G.cl_row.size());
         }
         size_t gb = 0;
         auto acc = [&](size_t bytes) { gb += align_up(std::max<size_t>(bytes, 4), 256); };
         for (auto& G : gh)
-            for (auto* v : {&G.if_off, &G.if_dofs, &G.cl_ptr, &G.cl_row, &G.cl_pos, &G.ci_ptr, &G.ci_leaf, &G.ci_row})
+            for (auto* v : {&G.if_off, &G.if_dofs, &G.cl_ptr, &G.cl_row, &G.cl_pos, &G.cl_leaf, &G.ci_ptr, &G.ci_k})
                 acc(sizeof(int) * v->size());
         acc(sizeof(int) * pk_pos.size());
         acc(sizeof(int) * tl_off.size());
@@ -882,6 +878,7 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
         acc(sizeof(double) * gm_maxIf * (h.gamma + 1) * h.gamma);
         acc(sizeof(double) * gm_maxIf);
         acc(sizeof(int) * gm_maxIf);
+        acc(sizeof(double) * gm_maxK);
         gamma_bytes = gb;
         o_gamma = take(gamma_bytes);
     }
@@ -1091,8 +1088,9 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
             D.n_if = (int)h.levels[d].nodes.size();
             D.S = (int)G.if_dofs.size();
             D.xbytes = G.xbytes;
-            int** dst[8] = {&D.d_if_off, &D.d_if_dofs, &D.d_cl_ptr, &D.d_cl_row, &D.d_cl_pos, &D.d_ci_ptr, &D.d_ci_leaf, &D.d_ci_row};
-            const std::vector<int>* src[8] = {&G.if_off, &G.if_dofs, &G.cl_ptr, &G.cl_row, &G.cl_pos, &G.ci_ptr, &G.ci_leaf, &G.ci_row};
+            D.nk = (int)G.cl_row.size();
+            int** dst[8] = {&D.d_if_off, &D.d_if_dofs, &D.d_cl_ptr, &D.d_cl_row, &D.d_cl_pos, &D.d_cl_leaf, &D.d_ci_ptr, &D.d_ci_k};
+            const std::vector<int>* src[8] = {&G.if_off, &G.if_dofs, &G.cl_ptr, &G.cl_row, &G.cl_pos, &G.cl_leaf, &G.ci_ptr, &G.ci_k};
             for (int q = 0; q < 8; ++q) {
                 *dst[q] = put(*src[q]);
                 RSD_TRY(upload(*dst[q], *src[q]));
@@ -1114,6 +1112,7 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
         h.d_gm_beta = dput(gm_maxIf);
         h.d_gm_kused = (int*)cur;
         cur += align_up(sizeof(int) * std::max<size_t>(gm_maxIf, 1), 256);
+        h.d_gm_yl = dput(gm_maxK);
         if ((size_t)(cur - (A + o_gamma)) > gamma_bytes) { set_last_error("gamma plan overflow"); return RSD_ERR_ARG; }
     }
     if (fg) {

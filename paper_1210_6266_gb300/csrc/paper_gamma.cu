@@ -8,8 +8,9 @@
 // Setup factors every leaf front [K_ll K_lB; K_Bl .] into L_l and X_l = K_{B_l l} L_l^-T
 // (rows: the ancestor DOFs B_l coupled to l), so with R = the rows of X_l that lie in I_t,
 //     K_{I_t l} K_ll^-1 K_{l I_t} = (K_{I_t l} L_l^-T)(L_l^-1 K_{l I_t}) = X_l[R] X_l[R]^T:
-// the two leaf solves of Algorithm 1 become two streaming products with X_l[R], the
-// second of which sums, per interface DOF, the leaves that touch it in a fixed order.
+// the two leaf solves of Algorithm 1 become two streaming products with X_l[R]: t_l =
+// X_l[R]^T x (column-parallel), then one row product X_l[row] . t_l per coupling, summed
+// per interface DOF over the leaves that touch it in a fixed order.
 // V-hat_t is exactly the set of leaves with a nonempty R for t (a leaf couples to its
 // ancestors' DOFs only, Eq. 3.1).
 //
@@ -18,6 +19,7 @@
 // Every reduction has a fixed order, so results are bitwise reproducible.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "rsd_internal.cuh"
 
@@ -73,16 +75,44 @@ __global__ void __launch_bounds__(256) k_smv_leaf(const FrontDesc* __restrict__ 
     tl[tl_off[l] + c] = (a0 + a1) + (a2 + a3);
 }
 
-// y_p = (K_{I_t I_t} x)_p - sum over the (leaf, row) pairs of position p of X_l[row] . t_l;
-// one warp per packed position.
+// yl_k = X_l[row_k] . t_l for every coupling k (a row of a leaf's X block that lies in the
+// level's interfaces); one warp per coupling, 16-byte loads along the row.
 template <typename T>
+__global__ void __launch_bounds__(256) k_smv_rows(int nk, const int* __restrict__ cl_leaf, const int* __restrict__ cl_row,
+                                                  const FrontDesc* __restrict__ leaves, const int* __restrict__ tl_off,
+                                                  const double* __restrict__ tl, double* __restrict__ yl) {
+    using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    constexpr int W = 16 / (int)sizeof(T);
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; k < nk; k += warps) {
+        const int l = cl_leaf[k];
+        const int s = leaves[l].s, ldp = leaves[l].ldp;
+        const T* row = (const T*)leaves[l].P + (int64_t)(s + cl_row[k]) * ldp;
+        const double* t = tl + tl_off[l];
+        double d = 0;
+        const int sv = s / W * W;
+        for (int c = lane * W; c < sv; c += 32 * W) {
+            const V v = __ldg((const V*)(row + c));
+            const T* e = (const T*)&v;
+#pragma unroll
+            for (int q = 0; q < W; ++q) d += (double)e[q] * t[c + q];
+        }
+        for (int c = sv + lane; c < s; c += 32) d += (double)row[c] * t[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        if (lane == 0) yl[k] = d;
+    }
+}
+
+// y_p = (K_{I_t I_t} x)_p - sum of yl_k over the couplings k of position p (leaves
+// ascending); one warp per packed position.
 __global__ void __launch_bounds__(256) k_smv_iface(int S, const int* __restrict__ if_dofs, const int64_t* __restrict__ rowptr,
                                                    const int* __restrict__ col, const double* __restrict__ val,
                                                    const int* __restrict__ owner, const int* __restrict__ pk_pos,
-                                                   const int* __restrict__ ci_ptr, const int* __restrict__ ci_leaf,
-                                                   const int* __restrict__ ci_row, const FrontDesc* __restrict__ leaves,
-                                                   const int* __restrict__ tl_off, const double* __restrict__ tl,
-                                                   const double* __restrict__ x, double* __restrict__ y) {
+                                                   const int* __restrict__ ci_ptr, const int* __restrict__ ci_k,
+                                                   const double* __restrict__ yl, const double* __restrict__ x,
+                                                   double* __restrict__ y) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; p < S; p += warps) {
@@ -93,18 +123,12 @@ __global__ void __launch_bounds__(256) k_smv_iface(int S, const int* __restrict_
             const int j = col[k];
             if (owner[j] == o) acc += val[k] * x[pk_pos[j]];
         }
-        for (int q = ci_ptr[p]; q < ci_ptr[p + 1]; ++q) {
-            const int l = ci_leaf[q];
-            const int s = leaves[l].s, ldp = leaves[l].ldp;
-            const T* row = (const T*)leaves[l].P + (int64_t)(s + ci_row[q]) * ldp;
-            const double* t = tl + tl_off[l];
-            double d = 0;
-            for (int c = lane; c < s; c += 32) d += (double)row[c] * t[c];
-            acc -= d;
-        }
 #pragma unroll
         for (int o2 = 16; o2 > 0; o2 >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o2);
-        if (lane == 0) y[p] = acc;
+        if (lane == 0) {
+            for (int q = ci_ptr[p]; q < ci_ptr[p + 1]; ++q) acc -= yl[ci_k[q]];
+            y[p] = acc;
+        }
     }
 }
 
@@ -222,19 +246,18 @@ int gamma_interface_solve(Handle& h, int li, double* z) {
     double bytes = 0;
     for (int j = 0; j < gam; ++j) {
         const double* vj = h.d_gm_V + (int64_t)j * G.S;
+        const unsigned gr = (unsigned)std::max(1, std::min(h.num_sms * 8, (G.nk + 7) / 8));
         if (f64) {
             k_smv_leaf<double><<<gl, 256, 0, h.stream>>>(Ll.d_fronts, G.d_cl_ptr, G.d_cl_row, G.d_cl_pos, h.d_tl_off, vj, h.d_tl);
-            k_smv_iface<double><<<gi, 256, 0, h.stream>>>(G.S, G.d_if_dofs, h.d_rowptr, h.d_col, h.d_val, h.d_owner, h.d_pk_pos,
-                                                          G.d_ci_ptr, G.d_ci_leaf, G.d_ci_row, Ll.d_fronts, h.d_tl_off, h.d_tl,
-                                                          vj, h.d_gm_w);
+            k_smv_rows<double><<<gr, 256, 0, h.stream>>>(G.nk, G.d_cl_leaf, G.d_cl_row, Ll.d_fronts, h.d_tl_off, h.d_tl, h.d_gm_yl);
         } else {
             k_smv_leaf<float><<<gl, 256, 0, h.stream>>>(Ll.d_fronts, G.d_cl_ptr, G.d_cl_row, G.d_cl_pos, h.d_tl_off, vj, h.d_tl);
-            k_smv_iface<float><<<gi, 256, 0, h.stream>>>(G.S, G.d_if_dofs, h.d_rowptr, h.d_col, h.d_val, h.d_owner, h.d_pk_pos,
-                                                         G.d_ci_ptr, G.d_ci_leaf, G.d_ci_row, Ll.d_fronts, h.d_tl_off, h.d_tl,
-                                                         vj, h.d_gm_w);
+            k_smv_rows<float><<<gr, 256, 0, h.stream>>>(G.nk, G.d_cl_leaf, G.d_cl_row, Ll.d_fronts, h.d_tl_off, h.d_tl, h.d_gm_yl);
         }
+        k_smv_iface<<<gi, 256, 0, h.stream>>>(G.S, G.d_if_dofs, h.d_rowptr, h.d_col, h.d_val, h.d_owner, h.d_pk_pos,
+                                              G.d_ci_ptr, G.d_ci_k, h.d_gm_yl, vj, h.d_gm_w);
         k_gm_mgs<<<G.n_if, GT, 0, h.stream>>>(j, gam, G.S, G.d_if_off, h.d_gm_w, h.d_gm_V, h.d_gm_H, h.d_gm_beta, h.d_gm_kused);
-        count_launch(3);
+        count_launch(4);
         bytes += G.xbytes;
     }
     k_gm_finish<<<G.n_if, GT, 0, h.stream>>>(gam, G.S, G.d_if_off, G.d_if_dofs, h.d_gm_V, h.d_gm_H, h.d_gm_beta,

@@ -135,13 +135,15 @@ struct Level {
 // its couplings to the leaves (see paper_gamma.cu).  Interface slot i owns positions
 // [if_off[i], if_off[i+1]); if_dofs maps a position to its global DOF.  cl_*: per leaf
 // (CSR over leaf slots), the rows r of the leaf's X block that lie in the level's
-// interfaces and their packed positions; ci_*: per packed position (CSR), the (leaf, row)
-// pairs that touch it, leaves ascending.
+// interfaces and their packed positions; ci_*: per packed position (CSR), the couplings
+// (cl indices) that touch it, leaves ascending.
 struct GammaLevel {
     int n_if = 0, S = 0;
     int *d_if_off = nullptr, *d_if_dofs = nullptr;
     int *d_cl_ptr = nullptr, *d_cl_row = nullptr, *d_cl_pos = nullptr;
-    int *d_ci_ptr = nullptr, *d_ci_leaf = nullptr, *d_ci_row = nullptr;
+    int* d_cl_leaf = nullptr;     // leaf slot of every coupling (cl index)
+    int *d_ci_ptr = nullptr, *d_ci_k = nullptr;   // couplings (cl indices) per packed position
+    int nk = 0;                   // couplings of the level
     double xbytes = 0;            // bytes of X one S-MatVec streams (its rows read twice)
 };
 
@@ -229,6 +231,7 @@ struct Handle {
     int* d_tl_off = nullptr;             // leaf slot -> offset of its t_l in d_tl
     double* d_tl = nullptr;              // X_l^T x per leaf
     double *d_gm_w = nullptr, *d_gm_V = nullptr, *d_gm_H = nullptr, *d_gm_beta = nullptr;
+    double* d_gm_yl = nullptr;           // per coupling: X_l[row] . t_l
     int* d_gm_kused = nullptr;
     // outer Krylov method (RSD_KRYLOV_PCG or RSD_KRYLOV_FGMRES) and FGMRES storage
     int krylov = RSD_KRYLOV_PCG, restart = 30;
