@@ -47,32 +47,56 @@ __device__ double block_sum_all(double v, double* red) {
     return red[32];
 }
 
-// t_l = X_l[R_l]^T x for every leaf with rows coupled to the level; one CTA per
-// (leaf, 256 columns), rows walked in ascending order, four partial sums per thread.
+// Products with a leaf's X block accumulate in the block's own precision (A = T): FP32
+// blocks of the mixed form in FP32, as the substitution sweeps do, FP64 blocks in FP64.
+template <typename T> struct VecOf;
+template <> struct VecOf<float> { using V = float4; };
+template <> struct VecOf<double> { using V = double2; };
+
+// t_l = X_l[R_l]^T x for every leaf with rows coupled to the level; one CTA per (leaf,
+// 256 x W columns), W columns per thread read with one 16-byte load per row; the rows'
+// offsets and x values are staged in shared memory, 256 at a time, and walked in order.
 template <typename T>
 __global__ void __launch_bounds__(256) k_smv_leaf(const FrontDesc* __restrict__ leaves, const int* __restrict__ cl_ptr,
                                                   const int* __restrict__ cl_row, const int* __restrict__ cl_pos,
                                                   const int* __restrict__ tl_off, const double* __restrict__ x,
-                                                  double* __restrict__ tl) {
+                                                  T* __restrict__ tl) {
+    using V = typename VecOf<T>::V;
+    constexpr int W = 16 / (int)sizeof(T);
+    __shared__ int s_row[256];
+    __shared__ T s_x[256];
     const int l = blockIdx.x;
     const int k0 = cl_ptr[l], k1 = cl_ptr[l + 1];
     if (k0 == k1) return;
     const int s = leaves[l].s, ldp = leaves[l].ldp;
     const T* X = (const T*)leaves[l].P + (int64_t)s * ldp;
-    const int c = blockIdx.y * blockDim.x + threadIdx.x;
-    if (c >= s) return;
-    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-    int k = k0;
-    for (; k + 4 <= k1; k += 4) {
-        const double v0 = (double)X[(int64_t)cl_row[k] * ldp + c], v1 = (double)X[(int64_t)cl_row[k + 1] * ldp + c];
-        const double v2 = (double)X[(int64_t)cl_row[k + 2] * ldp + c], v3 = (double)X[(int64_t)cl_row[k + 3] * ldp + c];
-        a0 += v0 * x[cl_pos[k]];
-        a1 += v1 * x[cl_pos[k + 1]];
-        a2 += v2 * x[cl_pos[k + 2]];
-        a3 += v3 * x[cl_pos[k + 3]];
+    const int c = (blockIdx.y * blockDim.x + threadIdx.x) * W;
+    T acc[W];
+#pragma unroll
+    for (int e = 0; e < W; ++e) acc[e] = 0;
+    for (int kb = k0; kb < k1; kb += 256) {
+        const int nb = min(256, k1 - kb);
+        __syncthreads();
+        if ((int)threadIdx.x < nb) {
+            s_row[threadIdx.x] = cl_row[kb + threadIdx.x];
+            s_x[threadIdx.x] = (T)x[cl_pos[kb + threadIdx.x]];
+        }
+        __syncthreads();
+        if (c < s) {
+#pragma unroll 4
+            for (int q = 0; q < nb; ++q) {
+                const V v = __ldg((const V*)(X + (int64_t)s_row[q] * ldp + c));
+                const T* e = (const T*)&v;
+                const T xv = s_x[q];
+#pragma unroll
+                for (int u = 0; u < W; ++u) acc[u] += e[u] * xv;
+            }
+        }
     }
-    for (; k < k1; ++k) a0 += (double)X[(int64_t)cl_row[k] * ldp + c] * x[cl_pos[k]];
-    tl[tl_off[l] + c] = (a0 + a1) + (a2 + a3);
+    T* out = tl + tl_off[l];
+#pragma unroll
+    for (int e = 0; e < W; ++e)
+        if (c + e < s) out[c + e] = acc[e];
 }
 
 // yl_k = X_l[row_k] . t_l for every coupling k (a row of a leaf's X block that lies in the
@@ -80,8 +104,8 @@ __global__ void __launch_bounds__(256) k_smv_leaf(const FrontDesc* __restrict__ 
 template <typename T>
 __global__ void __launch_bounds__(256) k_smv_rows(int nk, const int* __restrict__ cl_leaf, const int* __restrict__ cl_row,
                                                   const FrontDesc* __restrict__ leaves, const int* __restrict__ tl_off,
-                                                  const double* __restrict__ tl, double* __restrict__ yl) {
-    using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+                                                  const T* __restrict__ tl, double* __restrict__ yl) {
+    using V = typename VecOf<T>::V;
     constexpr int W = 16 / (int)sizeof(T);
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -89,19 +113,19 @@ __global__ void __launch_bounds__(256) k_smv_rows(int nk, const int* __restrict_
         const int l = cl_leaf[k];
         const int s = leaves[l].s, ldp = leaves[l].ldp;
         const T* row = (const T*)leaves[l].P + (int64_t)(s + cl_row[k]) * ldp;
-        const double* t = tl + tl_off[l];
-        double d = 0;
+        const T* t = tl + tl_off[l];
+        T d = 0;
         const int sv = s / W * W;
         for (int c = lane * W; c < sv; c += 32 * W) {
             const V v = __ldg((const V*)(row + c));
             const T* e = (const T*)&v;
 #pragma unroll
-            for (int q = 0; q < W; ++q) d += (double)e[q] * t[c + q];
+            for (int q = 0; q < W; ++q) d += e[q] * t[c + q];
         }
-        for (int c = sv + lane; c < s; c += 32) d += (double)row[c] * t[c];
+        for (int c = sv + lane; c < s; c += 32) d += row[c] * t[c];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-        if (lane == 0) yl[k] = d;
+        if (lane == 0) yl[k] = (double)d;
     }
 }
 
@@ -241,7 +265,8 @@ int gamma_interface_solve(Handle& h, int li, double* z) {
     const int pi = prof_begin(h, K_GAMMA);
     k_gm_init<<<G.n_if, GT, 0, h.stream>>>(G.d_if_off, G.d_if_dofs, h.d_pg, h.d_gm_V, h.d_gm_beta, h.d_gm_kused);
     count_launch();
-    const dim3 gl((unsigned)nleaf, (unsigned)std::max(1, (Ll.max_s + 255) / 256));
+    const int wcol = f64 ? 2 : 4;                 // columns per thread of k_smv_leaf
+    const dim3 gl((unsigned)nleaf, (unsigned)std::max(1, (Ll.max_s + 256 * wcol - 1) / (256 * wcol)));
     const unsigned gi = (unsigned)std::max(1, std::min(h.num_sms * 8, (G.S + 7) / 8));
     double bytes = 0;
     for (int j = 0; j < gam; ++j) {
@@ -249,10 +274,12 @@ int gamma_interface_solve(Handle& h, int li, double* z) {
         const unsigned gr = (unsigned)std::max(1, std::min(h.num_sms * 8, (G.nk + 7) / 8));
         if (f64) {
             k_smv_leaf<double><<<gl, 256, 0, h.stream>>>(Ll.d_fronts, G.d_cl_ptr, G.d_cl_row, G.d_cl_pos, h.d_tl_off, vj, h.d_tl);
-            k_smv_rows<double><<<gr, 256, 0, h.stream>>>(G.nk, G.d_cl_leaf, G.d_cl_row, Ll.d_fronts, h.d_tl_off, h.d_tl, h.d_gm_yl);
+            k_smv_rows<double><<<gr, 256, 0, h.stream>>>(G.nk, G.d_cl_leaf, G.d_cl_row, Ll.d_fronts, h.d_tl_off, h.d_tl,
+                                                         h.d_gm_yl);
         } else {
-            k_smv_leaf<float><<<gl, 256, 0, h.stream>>>(Ll.d_fronts, G.d_cl_ptr, G.d_cl_row, G.d_cl_pos, h.d_tl_off, vj, h.d_tl);
-            k_smv_rows<float><<<gr, 256, 0, h.stream>>>(G.nk, G.d_cl_leaf, G.d_cl_row, Ll.d_fronts, h.d_tl_off, h.d_tl, h.d_gm_yl);
+            float* tl32 = (float*)h.d_tl;
+            k_smv_leaf<float><<<gl, 256, 0, h.stream>>>(Ll.d_fronts, G.d_cl_ptr, G.d_cl_row, G.d_cl_pos, h.d_tl_off, vj, tl32);
+            k_smv_rows<float><<<gr, 256, 0, h.stream>>>(G.nk, G.d_cl_leaf, G.d_cl_row, Ll.d_fronts, h.d_tl_off, tl32, h.d_gm_yl);
         }
         k_smv_iface<<<gi, 256, 0, h.stream>>>(G.S, G.d_if_dofs, h.d_rowptr, h.d_col, h.d_val, h.d_owner, h.d_pk_pos,
                                               G.d_ci_ptr, G.d_ci_k, h.d_gm_yl, vj, h.d_gm_w);
