@@ -248,6 +248,8 @@ def main() -> None:
     ap.add_argument("--form", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--mode", default="exact", choices=["exact", "paper"])
     ap.add_argument("--gamma", type=int, default=0, help="paper mode: inner GMRES iterations (0: dense S~)")
+    ap.add_argument("--mixed-prec", default="tf32", choices=["tf32", "fp16", "bf16"],
+                    help="factor precision of the mixed form (FP64 PCG in every form)")
     ap.add_argument("--workload", default="diffusion129")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -276,9 +278,10 @@ def main() -> None:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     _build.build()
     global PREC
-    PREC = {"mixed": dict(prec_leaf=rsd.RSD_PREC_TF32, prec_mid=rsd.RSD_PREC_TF32, prec_root=rsd.RSD_PREC_TF32),
+    mp = {"tf32": rsd.RSD_PREC_TF32, "fp16": rsd.RSD_PREC_FP16, "bf16": rsd.RSD_PREC_BF16}[args.mixed_prec]
+    PREC = {"mixed": dict(prec_leaf=mp, prec_mid=mp, prec_root=mp),
             "fp64": dict(prec_leaf=rsd.RSD_PREC_FP64, prec_mid=rsd.RSD_PREC_FP64, prec_root=rsd.RSD_PREC_FP64)}
-    DTYPE = {"mixed": "tf32", "fp64": "f64"}
+    DTYPE = {"mixed": args.mixed_prec, "fp64": "f64"}
     mode = rsd.RSD_MODE_PAPER if args.mode == "paper" else rsd.RSD_MODE_EXACT
     single = world == 1
     pk, pk_src = peaks()

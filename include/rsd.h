@@ -48,6 +48,22 @@ extern "C" {
 #define RSD_PREC_FP32  1   /* FP32 storage, FP32 arithmetic on CUDA cores                */
 #define RSD_PREC_TF32  2   /* FP32 storage; GEMM/TRSM updates on tcgen05 tensor cores in
                               TF32 with FP32 accumulation; diagonal blocks in FP32       */
+#define RSD_PREC_FP16  3   /* as TF32, but the long Schur-complement updates (a panel's
+                              update by all earlier panels, and U -= X X^T) read a 16-bit
+                              copy of the finished panels on tcgen05 kind::f16 at twice the
+                              TF32 rate: FP16, row i scaled by a power of two rs_i with
+                              sqrt(K_ii) rs_i in [2^13, 2^14) (a symmetric diagonal scaling
+                              of the front), FP32 accumulation, the scaling undone on the
+                              result.  The factor entries are TF32 values (10-bit mantissa,
+                              FP16's), so the copy holds them exactly down to 2^-27 sqrt(K_ii)
+                              and the products equal TF32's.  The substitution sweeps read
+                              the same copy.                                             */
+#define RSD_PREC_BF16  4   /* as FP16 with a BF16 copy (8-bit mantissa) for those updates;
+                              the sweeps read the FP32 factor.  A front whose pivot fails
+                              (<= 0 or NaN) is factored again one precision up (BF16 or
+                              FP16 -> TF32 -> FP32 on CUDA cores), with every ancestor that
+                              consumed its Schur contribution; rsd_info_t.promoted counts
+                              them.                                                      */
 
 #define RSD_MODE_EXACT 0   /* exact recursive Schur complements (gamma -> infinity,
                               V-hat = V limit of Algorithm 2): the preconditioner is K^-1
@@ -129,6 +145,8 @@ typedef struct {
     double  setup_flops;     /* sum_t (s_t^3/3 + s_t^2 b_t + s_t b_t^2)                    */
     int64_t device_bytes;    /* bytes of device memory the handle holds                   */
     int32_t notspd_node;     /* first node whose pivot failed, or -1                      */
+    int32_t promoted;        /* fronts factored again one precision up after a failed pivot
+                                in a BF16 / FP16 / TF32 front (see RSD_PREC_BF16)          */
 } rsd_info_t;
 
 /* Per kernel class: launches, summed device time (CUDA events on the handle's stream)

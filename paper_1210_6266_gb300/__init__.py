@@ -16,12 +16,12 @@ import torch
 
 from . import _lib
 from ._lib import (RSD_KRYLOV_AUTO, RSD_KRYLOV_FGMRES, RSD_KRYLOV_PCG, RSD_MEM_DEVICE, RSD_MEM_HOST,
-                   RSD_MODE_EXACT, RSD_MODE_PAPER, RSD_PREC_FP32, RSD_PREC_FP64, RSD_PREC_TF32, RSDError,
-                   check)
+                   RSD_MODE_EXACT, RSD_MODE_PAPER, RSD_PREC_BF16, RSD_PREC_FP16, RSD_PREC_FP32, RSD_PREC_FP64,
+                   RSD_PREC_TF32, RSDError, check)
 
 __all__ = ["RSD", "grid_problem", "grid_sizes", "grid_exp", "coef_grad", "diffusion_solve",
            "DiffusionSolve", "launch_count", "peak_gemm", "RSDError", "RSD_PREC_FP64", "RSD_PREC_FP32",
-           "RSD_PREC_TF32", "RSD_MODE_EXACT", "RSD_MODE_PAPER", "RSD_KRYLOV_AUTO", "RSD_KRYLOV_PCG",
+           "RSD_PREC_TF32", "RSD_PREC_FP16", "RSD_PREC_BF16", "RSD_MODE_EXACT", "RSD_MODE_PAPER", "RSD_KRYLOV_AUTO", "RSD_KRYLOV_PCG",
            "RSD_KRYLOV_FGMRES"]
 
 

@@ -23,6 +23,8 @@ RSD_ERR_NOCONV = -7
 RSD_PREC_FP64 = 0
 RSD_PREC_FP32 = 1
 RSD_PREC_TF32 = 2
+RSD_PREC_FP16 = 3
+RSD_PREC_BF16 = 4
 
 RSD_KRYLOV_AUTO = 0
 RSD_KRYLOV_PCG = 1
@@ -70,7 +72,7 @@ class rsd_info_t(C.Structure):
     _fields_ = [("n", C.c_int32), ("n_nodes", C.c_int32), ("n_levels", C.c_int32),
                 ("factor_elems", C.c_int64), ("factor_bytes", C.c_int64),
                 ("setup_flops", C.c_double), ("device_bytes", C.c_int64),
-                ("notspd_node", C.c_int32)]
+                ("notspd_node", C.c_int32), ("promoted", C.c_int32)]
 
 
 PROFILE_CLASSES = ["assemble", "extend_add", "gemm_tcgen05", "gemm_simt", "diag_factor",

@@ -654,9 +654,90 @@ int level_precision(const rsd_options& o, int depth, bool all_leaves) {
     return all_leaves ? o.prec_leaf : o.prec_mid;
 }
 
-bool valid_prec(int p) { return p == RSD_PREC_FP64 || p == RSD_PREC_FP32 || p == RSD_PREC_TF32; }
+bool valid_prec(int p) {
+    return p == RSD_PREC_FP64 || p == RSD_PREC_FP32 || p == RSD_PREC_TF32 || p == RSD_PREC_FP16 || p == RSD_PREC_BF16;
+}
 
 }  // namespace
+
+// Breakdown handling of the low-precision factorisations (failed pivot: <= 0 or NaN).
+// Every front whose pivot failed is factored again one precision up (BF16 / FP16 ->
+// TF32 -> FP32 on CUDA cores), and every ancestor, whose front consumed the failed
+// front's Schur contribution, again at its own precision; level by level from the
+// deepest, each group of one level and precision as a sub-level of those fronts only
+// (the other fronts, and the children's contributions, stay as they are).  Repeats while
+// pivots fail; a failure in an FP32 or FP64 front is final.
+static int promote_failed_fronts(Handle& h, int* d_owner, int* d_rank, int* d_tin, int* d_tout) {
+    cudaStream_t st = h.stream;
+    const int nl = (int)h.levels.size();
+    std::vector<int> node_prec(h.n_nodes);
+    for (int t = 0; t < h.n_nodes; ++t) node_prec[t] = h.levels[h.node_level[t]].prec;
+    for (int round = 0; round < 4; ++round) {
+        std::vector<int> bad(h.n_nodes);
+        RSD_CUDA_TRY(cudaStreamSynchronize(st));
+        RSD_CUDA_TRY(cudaMemcpy(bad.data(), h.d_front_bad, sizeof(int) * h.n_nodes, cudaMemcpyDeviceToHost));
+        std::vector<char> mark(h.n_nodes, 0);
+        bool any = false;
+        for (int t = 0; t < h.n_nodes; ++t) {
+            if (!bad[t]) continue;
+            int& p = node_prec[t];
+            if (p == RSD_PREC_BF16 || p == RSD_PREC_FP16) p = RSD_PREC_TF32;
+            else if (p == RSD_PREC_TF32) p = RSD_PREC_FP32;
+            else return RSD_OK;                       // FP32 / FP64 pivot: reported by the caller
+            ++h.promoted;
+            any = true;
+            for (int x = t; x >= 0; x = h.parent[x]) mark[x] = 1;
+        }
+        if (!any) return RSD_OK;
+        const int big = 0x7fffffff;
+        RSD_CUDA_TRY(cudaMemsetAsync(h.d_front_bad, 0, sizeof(int) * h.n_nodes, st));
+        RSD_CUDA_TRY(cudaMemsetAsync(h.d_err + ERR_NOT_SPD, 0, sizeof(int), st));
+        RSD_CUDA_TRY(cudaMemcpyAsync(h.d_err + ERR_NOT_SPD_NODE, &big, sizeof(int), cudaMemcpyHostToDevice, st));
+        for (int d = nl - 1; d >= 0; --d) {
+            Level& L = h.levels[d];
+            std::vector<std::pair<int, std::vector<int>>> groups;     // (precision, slots)
+            for (size_t sl = 0; sl < L.nodes.size(); ++sl) {
+                const int t = L.nodes[sl];
+                if (!mark[t]) continue;
+                auto it = std::find_if(groups.begin(), groups.end(), [&](auto& g) { return g.first == node_prec[t]; });
+                if (it == groups.end()) groups.push_back({node_prec[t], {(int)sl}});
+                else it->second.push_back((int)sl);
+            }
+            for (auto& [prec, slots] : groups) {
+                Level sub;
+                sub.depth = L.depth;
+                sub.prec = prec;
+                sub.h16 = L.h16;                      // the level's sweeps keep reading what they read
+                sub.op16 = prec == RSD_PREC_FP16 ? TC_OP_F16 : prec == RSD_PREC_BF16 ? TC_OP_BF16 : TC_OP_TF32;
+                sub.d_child_slots = L.d_child_slots;
+                for (int sl : slots) {
+                    const FrontDesc& f = L.fronts[sl];
+                    sub.nodes.push_back(L.nodes[sl]);
+                    sub.fronts.push_back(f);
+                    sub.max_s = std::max(sub.max_s, f.s);
+                    sub.max_b = std::max(sub.max_b, f.b);
+                    sub.max_N = std::max(sub.max_N, f.N);
+                    sub.max_children = std::max(sub.max_children, f.child_count);
+                    const size_t es = elem_bytes(L.prec);
+                    RSD_CUDA_TRY(cudaMemsetAsync(f.P, 0, (size_t)f.N * f.ldp * es, st));
+                    if (f.b) RSD_CUDA_TRY(cudaMemsetAsync(f.U, 0, (size_t)f.b * f.ldu * es, st));
+                }
+                RSD_CUDA_TRY(cudaMallocAsync((void**)&sub.d_fronts, sizeof(FrontDesc) * sub.fronts.size(), st));
+                RSD_CUDA_TRY(cudaMemcpyAsync(sub.d_fronts, stage_host(h, sub.fronts.data(), sizeof(FrontDesc) * sub.fronts.size()),
+                                             sizeof(FrontDesc) * sub.fronts.size(), cudaMemcpyHostToDevice, st));
+                std::swap(h.levels[d], sub);
+                int rc = launch_assemble_fronts(h, d, h.d_rowptr, h.d_col, h.d_val, d_owner, d_rank, d_tin, d_tout);
+                if (rc == RSD_OK) rc = launch_extend_add(h, d);
+                if (rc == RSD_OK) rc = run_factor_level(h, d);
+                if (rc == RSD_OK) rc = launch_factor_copy16(h, d);
+                std::swap(h.levels[d], sub);
+                cudaFreeAsync(sub.d_fronts, st);
+                RSD_TRY(rc);
+            }
+        }
+    }
+    return RSD_OK;
+}
 
 // Build the handle's levels, memory plan and device copies from an analysis.
 static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int* col, const double* val) {
@@ -730,7 +811,8 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
     for (int d = nl - 1; d >= 0; --d) {
         Level& L = h.levels[d];
         const size_t es = L.factored ? elem_bytes(L.prec) : 0;   // unfactored: no storage
-        L.h16 = L.prec == RSD_PREC_TF32 && !paper;
+        L.h16 = (L.prec == RSD_PREC_TF32 || L.prec == RSD_PREC_FP16) && !paper;
+        L.op16 = L.prec == RSD_PREC_FP16 ? TC_OP_F16 : L.prec == RSD_PREC_BF16 ? TC_OP_BF16 : TC_OP_TF32;
         // P regions of a level are contiguous, then the U regions
         lvlP[d] = off;
         for (int t : L.nodes) {
@@ -756,7 +838,7 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
             fp[t].D = take((size_t)(L.factored ? std::max(1, nd) : 0) * NB * NB * es);
             fp[t].V = take((size_t)(s + b + 32) * es);
         }
-        if (L.h16)                                   // FP16 factor copies after the level's other regions
+        if (copy16_level(L))                         // 16-bit factor copies after the level's other regions
             for (int t : L.nodes) {
                 const int s = a.I_off[t + 1] - a.I_off[t], b = beff(t);
                 const int ldp = std::max(32, round_up(s, 32));
@@ -891,6 +973,7 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
     const size_t o_partial = take(sizeof(double) * 2048);
     const size_t o_scal = take(sizeof(double) * 16);
     const size_t o_err = take(sizeof(int) * ERR_SLOTS);
+    const size_t o_bad = take(sizeof(int) * a.n_nodes);
     const size_t o_ticket = take(sizeof(int) * 2 * nl + 16);
     h.arena_bytes = off;
     {
@@ -910,6 +993,7 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
     h.d_col = (int*)(A + o_col);
     h.d_val = (double*)(A + o_val);
     h.d_err = (int*)(A + o_err);
+    h.d_front_bad = (int*)(A + o_bad);
     h.d_ticket = (int*)(A + o_ticket);
     h.d_partial = (double*)(A + o_partial);
     h.d_scal = (double*)(A + o_scal);
@@ -940,6 +1024,7 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
         RSD_CUDA_TRY(cudaMemcpyAsync(d_ea, stage_host(h, ea_all.data(), sizeof(int) * ea_all.size()), sizeof(int) * ea_all.size(), cudaMemcpyHostToDevice, st));
     }
     RSD_CUDA_TRY(cudaMemsetAsync(h.d_err, 0, sizeof(int) * ERR_SLOTS, st));
+    RSD_CUDA_TRY(cudaMemsetAsync(h.d_front_bad, 0, sizeof(int) * a.n_nodes, st));
     {
         const int big = 0x7fffffff;
         RSD_CUDA_TRY(cudaMemcpyAsync(h.d_err + ERR_NOT_SPD_NODE, &big, sizeof(int), cudaMemcpyHostToDevice, st));
@@ -969,9 +1054,10 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
             f.U = A + fp[t].U;
             f.Dinv = A + fp[t].D;
             f.vec = A + fp[t].V;
-            f.P16 = L.h16 ? A + fp[t].H : nullptr;
-            f.rs = L.h16 ? (const float*)(A + fp[t].R) : nullptr;
-            f.ri = L.h16 ? f.rs + f.N : nullptr;
+            const bool c16 = copy16_level(L);
+            f.P16 = c16 ? A + fp[t].H : nullptr;
+            f.rs = c16 ? (const float*)(A + fp[t].R) : nullptr;
+            f.ri = c16 ? f.rs + f.N : nullptr;
             f.I = d_I + a.I_off[t];
             f.Bd = d_B + h.B_off[t];
             f.ea = d_ea + h.B_off[t];
@@ -1158,6 +1244,12 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
     stage_reset(h);                                   // every staged upload has completed
     int err[ERR_SLOTS];
     RSD_CUDA_TRY(cudaMemcpy(err, h.d_err, sizeof(err), cudaMemcpyDeviceToHost));
+    if (err[ERR_NOT_SPD] && !paper) {
+        RSD_TRY(promote_failed_fronts(h, d_owner, d_rank, d_tin, d_tout));
+        RSD_CUDA_TRY(cudaStreamSynchronize(st));
+        stage_reset(h);
+        RSD_CUDA_TRY(cudaMemcpy(err, h.d_err, sizeof(err), cudaMemcpyDeviceToHost));
+    }
     if (err[ERR_NOT_SPD]) {
         h.notspd_node = err[ERR_NOT_SPD_NODE];
         set_last_error("pivot <= 0 in node " + std::to_string(h.notspd_node));
@@ -1438,6 +1530,7 @@ extern "C" int rsd_get_info(rsd_handle hh, rsd_info_t* out) {
     out->setup_flops = h.setup_flops;
     out->device_bytes = (int64_t)h.arena_bytes;
     out->notspd_node = h.notspd_node;
+    out->promoted = h.promoted;
     return RSD_OK;
 }
 
@@ -1475,7 +1568,7 @@ extern "C" int rsd_front_factor16(rsd_handle hh, int32_t node, double* out) {
     Handle& h = hh->h;
     const Level& L = h.levels[h.node_level[node]];
     const FrontDesc& f = L.fronts[h.node_slot[node]];
-    if (!f.P16) return RSD_ERR_ARG;
+    if (!f.P16 || !L.h16) return RSD_ERR_ARG;
     RSD_CUDA_TRY(cudaStreamSynchronize(h.stream));
     std::vector<__half> q((size_t)f.N * f.ldp);
     std::vector<float> rs((size_t)2 * f.N);

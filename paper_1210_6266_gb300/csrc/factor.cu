@@ -21,6 +21,7 @@
 #include <cmath>
 #include <type_traits>
 
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include "rsd_internal.cuh"
@@ -292,7 +293,7 @@ __device__ __forceinline__ float store_round(float x, bool rnd) {
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_potrf_diag(const FrontDesc* __restrict__ fronts, int k,
-                                                   int* __restrict__ err, int round_tf32) {
+                                                   int* __restrict__ err, int round_tf32, int* __restrict__ bad_front) {
     extern __shared__ unsigned char smem_raw[];
     T* A = (T*)smem_raw;                 // L after the factorisation (upper part zero)
     T* vb = A + NB * DLD;                // two broadcast vectors
@@ -352,6 +353,7 @@ __global__ void __launch_bounds__(256) k_potrf_diag(const FrontDesc* __restrict_
     if (bad) {
         atomicExch(&err[ERR_NOT_SPD], 1);
         atomicMin(&err[ERR_NOT_SPD_NODE], f.node);
+        bad_front[f.node] = 1;
     }
 #pragma unroll
     for (int a = 0; a < 8; ++a)
@@ -635,9 +637,67 @@ __global__ void __launch_bounds__(256) k_copy16(const FrontDesc* __restrict__ fr
     }
 }
 
+// 16-bit operand copy of one outer panel (columns [K0, K0 + WOUT)) of every front, once all
+// its entries are final: the entries below the NB x NB diagonal blocks and the X rows, row
+// i scaled by rs[i] (the same entries k_copy16 writes, panel by panel, so that the later
+// panels' long-K updates can read them).  OUT is __half or __nv_bfloat16.
+template <typename OUT> __device__ __forceinline__ unsigned short to16(float x);
+template <> __device__ __forceinline__ unsigned short to16<__half>(float x) { return __half_as_ushort(__float2half_rn(x)); }
+template <> __device__ __forceinline__ unsigned short to16<__nv_bfloat16>(float x) {
+    return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+
+template <typename OUT>
+__global__ void __launch_bounds__(256) k_copy16_panel(const FrontDesc* __restrict__ fronts, int K0) {
+    const FrontDesc f = fronts[blockIdx.x];
+    if (f.s <= K0) return;
+    const int c1 = min(K0 + WOUT, f.s);
+    const float* P = (const float*)f.P;
+    unsigned short* Q = (unsigned short*)f.P16;
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int i = K0 + blockIdx.y * wpb + (threadIdx.x >> 5); i < f.N; i += gridDim.y * wpb) {
+        const int cend = i < f.s ? min(c1, (i / NB) * NB) : c1;
+        if (cend <= K0) continue;
+        const float sc = f.rs[i];
+        const float* src = P + (int64_t)i * f.ldp;
+        unsigned short* dst = Q + (int64_t)i * f.ldp;
+        for (int c = K0 + lane * 8; c < cend; c += 256) {
+            if (c + 8 <= cend) {
+                const float4 a = *(const float4*)(src + c), b = *(const float4*)(src + c + 4);
+                uint4 o;
+                o.x = (uint32_t)to16<OUT>(a.x * sc) | ((uint32_t)to16<OUT>(a.y * sc) << 16);
+                o.y = (uint32_t)to16<OUT>(a.z * sc) | ((uint32_t)to16<OUT>(a.w * sc) << 16);
+                o.z = (uint32_t)to16<OUT>(b.x * sc) | ((uint32_t)to16<OUT>(b.y * sc) << 16);
+                o.w = (uint32_t)to16<OUT>(b.z * sc) | ((uint32_t)to16<OUT>(b.w * sc) << 16);
+                *reinterpret_cast<uint4*>(dst + c) = o;
+            } else {
+                for (int e = 0; c + e < cend; ++e) dst[c + e] = to16<OUT>(src[c + e] * sc);
+            }
+        }
+    }
+}
+
+int launch_copy16_panel(Handle& h, int li, int K0, cudaStream_t st) {
+    Level& L = h.levels[li];
+    if (L.op16 == TC_OP_TF32 || L.fronts.empty() || K0 >= L.max_s) return RSD_OK;
+    const int nf = (int)L.fronts.size();
+    double bytes = 0;
+    for (auto& f : L.fronts)
+        if (f.s > K0) bytes += 6.0 * (double)(f.N - K0) * std::min(WOUT, f.s - K0);
+    const dim3 g((unsigned)nf, (unsigned)std::max(1, std::min((L.max_N - K0 + 7) / 8, (h.num_sms * 8 + nf - 1) / nf)));
+    const int pi = prof_begin(h, K_COPY16, st);
+    if (L.op16 == TC_OP_BF16) k_copy16_panel<__nv_bfloat16><<<g, 256, 0, st>>>(L.d_fronts, K0);
+    else k_copy16_panel<__half><<<g, 256, 0, st>>>(L.d_fronts, K0);
+    count_launch();
+    prof_end(h, pi, 0.0, bytes, st);
+    RSD_CUDA_TRY(cudaGetLastError());
+    return RSD_OK;
+}
+
 int launch_factor_copy16(Handle& h, int li) {
     Level& L = h.levels[li];
-    if (!L.h16 || L.fronts.empty()) return RSD_OK;
+    // levels with 16-bit GEMM operands wrote their copy panel by panel
+    if (!L.h16 || L.op16 != TC_OP_TF32 || L.fronts.empty()) return RSD_OK;
     const int nf = (int)L.fronts.size();
     double bytes = 0;
     for (auto& f : L.fronts) bytes += 6.0 * (0.5 * f.s * (f.s + 1.0) + (double)f.s * f.b);
@@ -670,7 +730,7 @@ int launch_assemble_fronts(Handle& h, int li, const int64_t* rowptr, const int* 
     else
         k_scatter_K<float><<<grid, 256, 0, h.stream>>>(L.d_fronts, rowptr, col, val, owner, rank, tin, tout);
     count_launch();
-    if (L.h16) {
+    if (copy16_level(L)) {
         const dim3 g((unsigned)L.fronts.size(), (unsigned)std::max(1, std::min(16, (L.max_N + 1023) / 1024)));
         k_row_scale<<<g, 256, 0, h.stream>>>(L.d_fronts, rowptr, col, val);
         count_launch();
@@ -853,6 +913,8 @@ static int factor_level_tc(Handle& h, int li, bool lookahead) {
         t.lower = 0; t.beta = 1;
         t.map_a = t.map_b = f.node;
         t.a_r0 = r0; t.a_c0 = kb; t.b_r0 = K0; t.b_c0 = kb;
+        t.sa = f.ri ? f.ri + r0 : nullptr;             // 16-bit operands: 1 / row scales
+        t.sb = f.ri ? f.ri + K0 : nullptr;
         tasks.push_back(t);
     };
     auto general = [&](int ma, int a_r0, int a_c0, int mb, int b_r0, int b_c0, void* C, int ldc,
@@ -884,7 +946,7 @@ static int factor_level_tc(Handle& h, int li, bool lookahead) {
                 if (f.s > k) { const double w = std::min(NB, f.s - k); pf += 2.0 * w * w * w / 3.0; pb += (2.0 * w * w + NB * NB) * es; }
             if (!dry) {
                 const int ppi = prof_begin(h, K_POTRF, cs);
-                k_potrf_diag<float><<<(unsigned)nf, 256, potrf_smem, cs>>>(L.d_fronts, k, h.d_err, 1);
+                k_potrf_diag<float><<<(unsigned)nf, 256, potrf_smem, cs>>>(L.d_fronts, k, h.d_err, 1, h.d_front_bad);
                 count_launch();
                 prof_end(h, ppi, pf, pb, cs);
                 RSD_CUDA_TRY(cudaGetLastError());
@@ -955,10 +1017,11 @@ static int factor_level_tc(Handle& h, int li, bool lookahead) {
                 if (p >= 1) {                                   // (a0) the whole outer update
                     tasks.clear();
                     for (auto& f : L.fronts) add_outer(f, K0, 0, K0, K0, f.N);
-                    RSD_TRY(gemm_tc_launch(h, li, tasks, 3, B, 0));
+                    RSD_TRY(gemm_tc_launch(h, li, tasks, 3, B, 0, 0, L.op16));
                 }
                 RSD_TRY(factor_block(K0, 0, B, 0));
                 RSD_TRY(solve_rows(K0, 0, [&](const FrontDesc& f) { return wend(f, K0); }, rows_to_end, B, 0, 0));
+                if (!dry) RSD_TRY(launch_copy16_panel(h, li, K0, B));   // panel p is final
             }
         } else {
             // Look-ahead.  Chain(p): the part of panel p's outer update with K in [K0-W, K0)
@@ -1002,7 +1065,7 @@ static int factor_level_tc(Handle& h, int li, bool lookahead) {
                     if (K0 > 0) {
                         tasks.clear();
                         for (auto& f : L.fronts) add_outer(f, K0n, 0, K0, K0n, f.N);
-                        RSD_TRY(gemm_tc_launch(h, li, tasks, 3, B, 0, bulk_ctas));
+                        RSD_TRY(gemm_tc_launch(h, li, tasks, 3, B, 0, bulk_ctas, L.op16));
                     }
                     if (!dry) RSD_CUDA_TRY(cudaEventRecord(h.ev_ready, B));
                 }
@@ -1010,11 +1073,14 @@ static int factor_level_tc(Handle& h, int li, bool lookahead) {
                 RSD_TRY(solve_rows(K0, which, next_hi, rows_to_end, B, 0, bulk_ctas));
                 if (p + 1 < np) {
                     if (!dry) RSD_CUDA_TRY(cudaStreamWaitEvent(B, ev_xnext, 0));
+                    if (!dry) RSD_TRY(launch_copy16_panel(h, li, K0, B));   // panel p is final
                     tasks.clear();
                     for (auto& f : L.fronts)
                         if (f.s > K0n) add_outer(f, K0n, K0, K0n, wend(f, K0n), f.N);
                     RSD_TRY(gemm_tc_launch(h, li, tasks, 3, B, 0, bulk_ctas));
                     if (!dry) RSD_CUDA_TRY(cudaEventRecord(ev_rest, B));
+                } else if (!dry) {
+                    RSD_TRY(launch_copy16_panel(h, li, K0, B));          // the last panel is final
                 }
             }
             if (!dry) RSD_CUDA_TRY(cudaEventRecord(h.ev_join, Cs));
@@ -1039,7 +1105,7 @@ int run_factor_level(Handle& h, int li) {
     Level& L = h.levels[li];
     if (L.fronts.empty()) return RSD_OK;
     const bool f64 = is_fp64(L.prec);
-    const bool tc = L.prec == RSD_PREC_TF32;
+    const bool tc = tc_level(L);
     const size_t es = f64 ? 8 : 4;
     // task buffer for this level: one slot per front per launch kind
     GemmTask* d_tasks = nullptr;
@@ -1112,8 +1178,8 @@ int run_factor_level(Handle& h, int li) {
         for (auto& f : L.fronts)
             if (f.s > k) { const double w = std::min(NB, f.s - k); pf += 2.0 * w * w * w / 3.0; pb += (2.0 * w * w + NB * NB) * es; }
         const int ppi = prof_begin(h, K_POTRF);
-        if (f64) k_potrf_diag<double><<<(unsigned)L.fronts.size(), 256, potrf_smem, h.stream>>>(L.d_fronts, k, h.d_err, 0);
-        else k_potrf_diag<float><<<(unsigned)L.fronts.size(), 256, potrf_smem, h.stream>>>(L.d_fronts, k, h.d_err, tc ? 1 : 0);
+        if (f64) k_potrf_diag<double><<<(unsigned)L.fronts.size(), 256, potrf_smem, h.stream>>>(L.d_fronts, k, h.d_err, 0, h.d_front_bad);
+        else k_potrf_diag<float><<<(unsigned)L.fronts.size(), 256, potrf_smem, h.stream>>>(L.d_fronts, k, h.d_err, tc ? 1 : 0, h.d_front_bad);
         count_launch();
         prof_end(h, ppi, pf, pb);
         if (cudaGetLastError() != cudaSuccess) { rc = RSD_ERR_CUDA; break; }
@@ -1165,10 +1231,11 @@ int run_factor_level(Handle& h, int li) {
             t.lower = 1; t.beta = 1;
             t.map_a = t.map_b = f.node;
             t.a_r0 = f.s; t.a_c0 = 0; t.b_r0 = f.s; t.b_c0 = 0;
+            t.sa = t.sb = f.ri ? f.ri + f.s : nullptr;      // 16-bit operands: 1 / row scales
             tasks.push_back(t);
         }
         if (!tasks.empty()) {
-            if (tc) rc = gemm_tc_launch(h, li, tasks, 2, h.stream);
+            if (tc) rc = gemm_tc_launch(h, li, tasks, 2, h.stream, 0, 0, L.op16);
             else {
                 finalize_tasks(tasks, SB, SB);
                 rc = f64 ? launch_gemm_simt<double>(h, tasks, d_tasks, -1.0, h.stream)

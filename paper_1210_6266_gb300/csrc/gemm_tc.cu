@@ -31,6 +31,13 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int BK = 32;                       // FP32 elements per 128-byte swizzle row
+// Operand formats: TF32 (FP32 storage, kind::tf32, 8 K per MMA) or a 16-bit copy (FP16
+// or BF16, kind::f16, 16 K per MMA).  A K block is one 128-byte swizzle row either way:
+// 32 FP32 or 64 16-bit elements, four MMAs.
+template <int OP> struct OpT {
+    static constexpr int BKE = OP == TC_OP_TF32 ? 32 : 64;      // elements per K block
+    static constexpr uint32_t FMT = OP == TC_OP_TF32 ? 2u : (OP == TC_OP_BF16 ? 1u : 0u);
+};
 constexpr int TC_THREADS = 192;
 constexpr long long TC_WAIT_CYCLES = 2000000000LL;   // ~1 s
 constexpr int SPLIT_MIN_KB = 16;             // at least 16 x 32 K per split-K slice
@@ -51,6 +58,10 @@ struct TcTask {               // device view of one GEMM task
     int a_r0, a_c0, b_r0, b_c0;
     float alpha;
     int round_tf32;           // round stored results to the nearest TF32 value
+    // 16-bit operands: row i of A (B) was stored scaled by 1 / sa[i] (1 / sb[i]), so the
+    // product is multiplied by sa[row] sb[col]; null for TF32 operands
+    const float* sa;
+    const float* sb;
 };
 
 // Round to the nearest TF32 value (10-bit mantissa), kept as an FP32 bit pattern.
@@ -119,10 +130,12 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
     return d;
 }
 
-// Instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = bn.
-__host__ __device__ constexpr uint32_t idesc_tf32(int bn) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+// Instruction descriptor: D = F32, A = B of format fmt (TF32 2; F16 0; BF16 1), both
+// K-major, M = 128, N = bn.
+__host__ __device__ constexpr uint32_t idesc_of(uint32_t fmt, int bn) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
+__host__ __device__ constexpr uint32_t idesc_tf32(int bn) { return idesc_of(2u, bn); }
 
 __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
     asm volatile(
@@ -130,6 +143,20 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t da, uint64_t db
         " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
         ::"r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc)
         : "memory");
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+template <int OP>
+__device__ __forceinline__ void mma_op(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    if constexpr (OP == TC_OP_TF32) mma_tf32(tmem, da, db, idesc, acc);
+    else mma_f16(tmem, da, db, idesc, acc);
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -298,7 +325,7 @@ k_gemm_tc(const TcTask* __restrict__ tasks, const TcTile* __restrict__ tiles,
 // accumulator is double-buffered (2 x 256 columns), so the epilogue of one tile overlaps
 // the main loop of the next.  Barriers: full/empty per ring stage, and acc_full/acc_empty
 // per accumulator buffer (acc_empty counts the 128 epilogue threads).
-template <int BN, int ST>
+template <int BN, int ST, int OP = TC_OP_TF32>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_gemm_tc_persist(const TcTask* __restrict__ tasks, const TcTile* __restrict__ tiles, int n_tiles,
                   const CUtensorMap* __restrict__ maps, float* __restrict__ ws, int* __restrict__ err) {
@@ -353,17 +380,17 @@ k_gemm_tc_persist(const TcTask* __restrict__ tasks, const TcTile* __restrict__ t
                     const uint32_t sa = base + s * S::STAGE;
                     const uint32_t sb = sa + S::A_BYTES;
                     mbar_expect_tx(bar_full + 8 * s, S::STAGE);
-                    const int kx = kb * BK;
+                    const int kx = kb * OpT<OP>::BKE;
                     tma_load_2d(sa, ma, tk.a_c0 + kx, tk.a_r0 + m0, bar_full + 8 * s);
 #pragma unroll
                     for (int hh = 0; hh < BN / 128; ++hh)
-                        tma_load_2d(sb + hh * 128 * BK * 4, mb, tk.b_c0 + kx, tk.b_r0 + n0 + hh * 128, bar_full + 8 * s);
+                        tma_load_2d(sb + hh * 128 * 128, mb, tk.b_c0 + kx, tk.b_r0 + n0 + hh * 128, bar_full + 8 * s);
                 }
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_tf32(BN);
+            constexpr uint32_t idesc = idesc_of(OpT<OP>::FMT, BN);
             uint32_t it = 0, tcount = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++tcount) {
@@ -380,8 +407,8 @@ k_gemm_tc_persist(const TcTask* __restrict__ tasks, const TcTile* __restrict__ t
                     const uint32_t sa = base + s * S::STAGE;
                     const uint32_t sb = sa + S::A_BYTES;
 #pragma unroll
-                    for (int k = 0; k < BK / 8; ++k)
-                        mma_tf32(acc, smem_desc(sa + k * 32), smem_desc(sb + k * 32), idesc, (kb != tl.kb0 || k) ? 1u : 0u);
+                    for (int k = 0; k < 4; ++k)
+                        mma_op<OP>(acc, smem_desc(sa + k * 32), smem_desc(sb + k * 32), idesc, (kb != tl.kb0 || k) ? 1u : 0u);
                     mma_commit(bar_empty + 8 * s);
                 }
                 mma_commit(bar_accf + 8 * buf);
@@ -419,15 +446,24 @@ k_gemm_tc_persist(const TcTask* __restrict__ tasks, const TcTile* __restrict__ t
                 const int gc0 = n0 + c0;
                 if (gc0 >= tk.N) continue;
                 if (tk.lower && gc0 > gr) continue;
+                if constexpr (OP != TC_OP_TF32) {
+                    // undo the operands' row scales: entry (gr, gc) times sa[gr] sb[gc]
+                    const float ar = tk.alpha * tk.sa[gr];
+                    const int qe = min(32, tk.N - gc0);
+#pragma unroll
+                    for (int q = 0; q < 32; ++q)
+                        r[q] = __float_as_uint(q < qe ? __uint_as_float(r[q]) * ar * __ldg(tk.sb + gc0 + q) : 0.f);
+                }
+                const float al = OP != TC_OP_TF32 ? 1.0f : tk.alpha;
                 if (gc0 + 32 <= tk.N && (!tk.lower || gc0 + 31 <= gr)) {
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
                         float4* p = (float4*)(crow + gc0 + 4 * q);
                         float4 o = tk.beta ? *p : make_float4(0.f, 0.f, 0.f, 0.f);
-                        o.x += tk.alpha * __uint_as_float(r[4 * q + 0]);
-                        o.y += tk.alpha * __uint_as_float(r[4 * q + 1]);
-                        o.z += tk.alpha * __uint_as_float(r[4 * q + 2]);
-                        o.w += tk.alpha * __uint_as_float(r[4 * q + 3]);
+                        o.x += al * __uint_as_float(r[4 * q + 0]);
+                        o.y += al * __uint_as_float(r[4 * q + 1]);
+                        o.z += al * __uint_as_float(r[4 * q + 2]);
+                        o.w += al * __uint_as_float(r[4 * q + 3]);
                         if (tk.round_tf32) { o.x = tf32_rn(o.x); o.y = tf32_rn(o.y); o.z = tf32_rn(o.z); o.w = tf32_rn(o.w); }
                         *p = o;
                     }
@@ -437,7 +473,7 @@ k_gemm_tc_persist(const TcTask* __restrict__ tasks, const TcTile* __restrict__ t
                         const int gc = gc0 + q;
                         if (gc < tk.N && (!tk.lower || gc <= gr)) {
                             float* p = crow + gc;
-                            const float o = (tk.beta ? *p : 0.f) + tk.alpha * __uint_as_float(r[q]);
+                            const float o = (tk.beta ? *p : 0.f) + al * __uint_as_float(r[q]);
                             *p = tk.round_tf32 ? tf32_rn(o) : o;
                         }
                     }
@@ -468,6 +504,7 @@ __global__ void __launch_bounds__(256) k_splitk_reduce(const TcTask* __restrict_
         if (gr >= tk.M || gc >= tk.N || (tk.lower && gc > gr)) continue;
         float v = 0.f;
         for (int sp = 0; sp < rd.nsplit; ++sp) v += ws[((int64_t)(rd.slot0 + sp) * BM + row) * BN + col];
+        if (tk.sa) v *= tk.sa[gr] * tk.sb[gc];           // 16-bit operands: undo the row scales
         float* p = tk.C + (int64_t)gr * tk.ldc + gc;
         const float o = (tk.beta ? *p : 0.f) + tk.alpha * v;
         *p = tk.round_tf32 ? tf32_rn(o) : o;
@@ -491,14 +528,19 @@ EncodeFn get_encode() {
     return fn;
 }
 
-int encode_2d(CUtensorMap* m, void* base, int cols, int rows, int ld_elems) {
+// 2-D tensor map over a row-major matrix: boxes of 128 rows x 128 bytes (one swizzle
+// row: 32 FP32 or 64 16-bit elements), 128-byte swizzle.
+int encode_2d(CUtensorMap* m, void* base, int cols, int rows, int ld_elems, int op = TC_OP_TF32) {
     EncodeFn enc = get_encode();
     if (!enc) { set_last_error("cuTensorMapEncodeTiled unavailable"); return RSD_ERR_CUDA; }
+    const int es_b = op == TC_OP_TF32 ? 4 : 2;
     cuuint64_t dims[2] = {(cuuint64_t)std::max(cols, 1), (cuuint64_t)std::max(rows, 1)};
-    cuuint64_t strides[1] = {(cuuint64_t)ld_elems * 4};
-    cuuint32_t box[2] = {(cuuint32_t)BK, 128};
+    cuuint64_t strides[1] = {(cuuint64_t)ld_elems * es_b};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / es_b), 128};
     cuuint32_t es[2] = {1, 1};
-    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, es,
+    const CUtensorMapDataType dt = op == TC_OP_TF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : op == TC_OP_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    CUresult r = enc(m, dt, 2, base, dims, strides, box, es,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) { set_last_error("cuTensorMapEncodeTiled failed: " + std::to_string((int)r)); return RSD_ERR_CUDA; }
@@ -516,8 +558,9 @@ struct TcBuf {
 };
 
 struct TcState {
-    CUtensorMap* d_maps = nullptr;      // 2 per tree node: [L; X] panel, inverted diagonal blocks;
-                                        // then TC_SCR_MAPS per front slot of the widest level
+    CUtensorMap* d_maps = nullptr;      // TC_NODE_MAPS per tree node: [L; X] panel, inverted
+                                        // diagonal blocks, 16-bit copy; then TC_SCR_MAPS per
+                                        // front slot of the widest level
     int scr_base = 0, scr_slots = 0;
     TcBuf buf[TC_SLOTS];
     // recorded launches (gemm_tc_record_begin/end): lists built by a dry pass, uploaded
@@ -540,22 +583,23 @@ TcState* state_of(Handle& h) { return (TcState*)h.tc_state; }
 
 int gemm_tc_prepare(Handle& h) {
     bool any = false;
-    for (auto& L : h.levels) any |= L.prec == RSD_PREC_TF32 && L.factored;
+    for (auto& L : h.levels) any |= tc_level(L) && L.factored;
     if (!any) return RSD_OK;
     auto* st = new TcState();
     h.tc_state = st;
     int widest = 0;
     for (auto& L : h.levels)
-        if (L.prec == RSD_PREC_TF32 && L.factored) widest = std::max(widest, (int)L.fronts.size());
-    st->scr_base = 2 * h.n_nodes;
+        if (tc_level(L) && L.factored) widest = std::max(widest, (int)L.fronts.size());
+    st->scr_base = TC_NODE_MAPS * h.n_nodes;
     st->scr_slots = widest;
-    std::vector<CUtensorMap> maps(2 * (size_t)h.n_nodes + TC_SCR_MAPS * (size_t)widest);
+    std::vector<CUtensorMap> maps(TC_NODE_MAPS * (size_t)h.n_nodes + TC_SCR_MAPS * (size_t)widest);
     std::memset(maps.data(), 0, maps.size() * sizeof(CUtensorMap));
     for (auto& L : h.levels) {
-        if (L.prec != RSD_PREC_TF32 || !L.factored) continue;
+        if (!tc_level(L) || !L.factored) continue;
         for (auto& f : L.fronts) {
-            RSD_TRY(encode_2d(&maps[2 * (size_t)f.node], f.P, f.s, f.N, f.ldp));
-            RSD_TRY(encode_2d(&maps[2 * (size_t)f.node + 1], f.Dinv, NB, std::max(1, f.nd) * NB, NB));
+            RSD_TRY(encode_2d(&maps[tc_map_panel(f.node)], f.P, f.s, f.N, f.ldp));
+            RSD_TRY(encode_2d(&maps[tc_map_dinv(f.node)], f.Dinv, NB, std::max(1, f.nd) * NB, NB));
+            if (L.op16 != TC_OP_TF32) RSD_TRY(encode_2d(&maps[tc_map_panel16(f.node)], f.P16, f.s, f.N, f.ldp, L.op16));
         }
     }
     RSD_CUDA_TRY(cudaMalloc((void**)&st->d_maps, maps.size() * sizeof(CUtensorMap)));
@@ -723,7 +767,7 @@ int gemm_tc_peak(int n, int reps, double seconds, cudaStream_t stream, int num_s
 // 2: U -= X X^T (lower tiles), 3: outer panel update, TC_GENERAL: map indices, alpha and
 // rounding taken from the task (128- or 256-wide tiles by the widest N).
 int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, int kind, cudaStream_t stream,
-                   int buf_slot, int max_ctas) {
+                   int buf_slot, int max_ctas, int op) {
     TcState* st = state_of(h);
     if (!st || tasks.empty()) return st ? RSD_OK : RSD_ERR_ARG;
     if (buf_slot < 0 || buf_slot >= TC_SLOTS) return RSD_ERR_ARG;
@@ -732,6 +776,7 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
     int max_n = 0;
     for (auto& g : tasks) max_n = std::max(max_n, g.N);
     const int bn = (kind == 2 || kind == 3 || (kind == TC_GENERAL && max_n > 128)) ? 256 : 128;
+    if (op != TC_OP_TF32 && kind != 2 && kind != 3) return RSD_ERR_ARG;     // 16-bit: long-K updates only
     std::vector<TcTask> tt(tasks.size());
     std::vector<std::array<int, 3>> out;            // (task, tm, tn) output tiles
     for (size_t i = 0; i < tasks.size(); ++i) {
@@ -740,8 +785,11 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
         t.C = (float*)g.C;
         t.ldc = g.ldc; t.M = g.M; t.N = g.N; t.K = g.K;
         t.lower = g.lower; t.beta = g.beta;
-        t.map_a = kind == TC_GENERAL ? g.map_a : tc_map_panel(g.map_a);
-        t.map_b = kind == TC_GENERAL ? g.map_b : (kind == 1 ? tc_map_dinv(g.map_b) : tc_map_panel(g.map_b));
+        t.map_a = kind == TC_GENERAL ? g.map_a : (op != TC_OP_TF32 ? tc_map_panel16(g.map_a) : tc_map_panel(g.map_a));
+        t.map_b = kind == TC_GENERAL ? g.map_b : (kind == 1 ? tc_map_dinv(g.map_b)
+                                                            : op != TC_OP_TF32 ? tc_map_panel16(g.map_b) : tc_map_panel(g.map_b));
+        t.sa = op != TC_OP_TF32 ? g.sa : nullptr;
+        t.sb = op != TC_OP_TF32 ? g.sb : nullptr;
         t.a_r0 = g.a_r0; t.a_c0 = g.a_c0; t.b_r0 = g.b_r0; t.b_c0 = g.b_c0;
         t.alpha = kind == TC_GENERAL ? g.alpha : (kind == 1 ? 1.0f : -1.0f);
         // panel-solve results are final factor entries
@@ -762,8 +810,9 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
     }
     if (out.empty()) return RSD_OK;
     // split K when the output tiles cannot fill the GPU (never for the in-place panel solve)
+    const int bke = op != TC_OP_TF32 ? 64 : BK;            // elements per K block
     int max_kb = 0;
-    for (auto& g : tasks) max_kb = std::max(max_kb, (g.K + BK - 1) / BK);
+    for (auto& g : tasks) max_kb = std::max(max_kb, (g.K + bke - 1) / bke);
     int nsplit = 1;
     if (kind != 1 && kind != TC_GENERAL && (int)out.size() < sms)
         nsplit = std::max(1, std::min(sms / (int)out.size(), max_kb / SPLIT_MIN_KB));
@@ -772,7 +821,7 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
     std::vector<TcRed> rd;
     int slot = 0;
     for (auto& o : out) {
-        const int nkb = (tasks[o[0]].K + BK - 1) / BK;
+        const int nkb = (tasks[o[0]].K + bke - 1) / bke;
         const int ns = std::max(1, std::min(nsplit, nkb / SPLIT_MIN_KB));
         if (ns == 1) {
             tl.push_back({o[0], o[1], o[2], 0, nkb, -1, 0, 0});
@@ -786,7 +835,8 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
     for (auto& g : tasks) {
         const double c = g.lower ? 0.5 * g.M * (g.M + 1.0) : (double)g.M * g.N;
         fl += 2.0 * c * g.K;
-        by += 4.0 * ((double)g.M * g.K + (g.lower ? 0.0 : (double)g.N * g.K) + c * (g.beta ? 2 : 1));
+        by += (op != TC_OP_TF32 ? 2.0 : 4.0) * ((double)g.M * g.K + (g.lower ? 0.0 : (double)g.N * g.K)) +
+              4.0 * c * (g.beta ? 2 : 1);
     }
     if (st->mode == 1) {                                   // dry pass: record only
         auto put = [&](const void* p, size_t bytes) {
@@ -845,6 +895,8 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
         RSD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<128, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<128, 6>::TOTAL));
         RSD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<256, 4>::TOTAL));
         RSD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc_persist<256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<256, 4>::TOTAL));
+        RSD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc_persist<256, 4, TC_OP_F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<256, 4>::TOTAL));
+        RSD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc_persist<256, 4, TC_OP_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<256, 4>::TOTAL));
         st->attr_set = true;
     }
     const int pi = prof_begin(h, K_GEMM_TC, stream);
@@ -856,8 +908,15 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
         k_gemm_tc<128, 6><<<(unsigned)tl.size(), TC_THREADS, Smem<128, 6>::TOTAL, stream>>>(d_tasks, d_tiles, st->d_maps, bf.d_ws, h.d_err);
     else {
         const int ctas = std::min((int)tl.size(), sms);
-        k_gemm_tc_persist<256, 4><<<(unsigned)ctas, TC_THREADS, Smem<256, 4>::TOTAL, stream>>>(
-            d_tasks, d_tiles, (int)tl.size(), st->d_maps, bf.d_ws, h.d_err);
+        if (op == TC_OP_F16)
+            k_gemm_tc_persist<256, 4, TC_OP_F16><<<(unsigned)ctas, TC_THREADS, Smem<256, 4>::TOTAL, stream>>>(
+                d_tasks, d_tiles, (int)tl.size(), st->d_maps, bf.d_ws, h.d_err);
+        else if (op == TC_OP_BF16)
+            k_gemm_tc_persist<256, 4, TC_OP_BF16><<<(unsigned)ctas, TC_THREADS, Smem<256, 4>::TOTAL, stream>>>(
+                d_tasks, d_tiles, (int)tl.size(), st->d_maps, bf.d_ws, h.d_err);
+        else
+            k_gemm_tc_persist<256, 4><<<(unsigned)ctas, TC_THREADS, Smem<256, 4>::TOTAL, stream>>>(
+                d_tasks, d_tiles, (int)tl.size(), st->d_maps, bf.d_ws, h.d_err);
     }
     count_launch();
     if (!rd.empty()) {

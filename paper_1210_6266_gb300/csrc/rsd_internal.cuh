@@ -83,7 +83,15 @@ struct GemmTask {
     int a_r0, a_c0, b_r0, b_c0;   // operand origins inside the tensor maps
     float alpha;         // general tensor-core kind only: C = alpha A B^T + beta C
     int round;           // general kind only: round stored results to TF32
+    // 16-bit operand copies (TC_OP_F16 / TC_OP_BF16 launches): 1 / row scale of A's first
+    // row and of B's first row (the product is multiplied by sa[i] sb[j])
+    const float* sa;
+    const float* sb;
 };
+
+// Operand formats of the tensor-core GEMM: FP32 storage read as TF32 (kind::tf32), or the
+// row-scaled 16-bit copy of a front's factor (kind::f16 with FP16 or BF16 operands).
+enum { TC_OP_TF32 = 0, TC_OP_F16 = 1, TC_OP_BF16 = 2 };
 
 // Kernel classes for launch counting and the optional CUDA-event profile.
 enum KClass { K_ASSEMBLE = 0, K_EXTEND, K_GEMM_TC, K_GEMM_SIMT, K_POTRF, K_TRSM, K_FWD, K_BWD,
@@ -120,7 +128,10 @@ struct Level {
     // the level below
     int* d_child_slots = nullptr;
     size_t bytes_P = 0, bytes_U = 0;
-    bool h16 = false;                    // fronts carry the FP16 factor copy (P16, rs, ri)
+    bool h16 = false;                    // the sweeps read the FP16 factor copy (P16, rs, ri)
+    // operand format of the long-K Schur updates (TC_OP_*): with a 16-bit format the
+    // fronts carry its row-scaled copy (P16, rs, ri), written panel by panel
+    int op16 = TC_OP_TF32;
     // paper mode: descriptors of the same fronts restricted to their interface block
     // (b = 0, no children) and forward items over interface blocks only, used by the
     // leaf and interface solves of the level-wise Algorithm 2
@@ -146,6 +157,13 @@ struct GammaLevel {
     int nk = 0;                   // couplings of the level
     double xbytes = 0;            // bytes of X one S-MatVec streams (its rows read twice)
 };
+
+// Levels factored with tcgen05 GEMMs (TF32 on the FP32 panels, or 16-bit operand copies).
+inline bool tc_level(const Level& L) {
+    return L.prec == RSD_PREC_TF32 || L.prec == RSD_PREC_FP16 || L.prec == RSD_PREC_BF16;
+}
+// Levels whose fronts carry a row-scaled 16-bit copy of the factor (P16, rs, ri).
+inline bool copy16_level(const Level& L) { return L.h16 || L.op16 != TC_OP_TF32; }
 
 // Diagonal blocks per substitution-sweep item: a single-front FP32 level (a root) pairs
 // its blocks, halving the hand-offs of its long dependency chain; levels with many
@@ -176,6 +194,8 @@ struct Handle {
     size_t arena_capacity = 0;          // bytes of the block actually held (cache reuse)
     int device = 0;
     int* d_err = nullptr;
+    int* d_front_bad = nullptr;          // per node: a pivot of its factorisation failed
+    int promoted = 0;                    // fronts re-factored one precision up at setup
     int* d_ticket = nullptr;             // per-sweep ticket counters
     // CSR of K on the device (FP64), owned copy for the Krylov SpMV
     int64_t nnz = 0;
@@ -279,11 +299,16 @@ constexpr int TC_SCR_MAPS = 4;
 int gemm_tc_scratch_maps(Handle& h, const std::vector<float*>& mt, const std::vector<float*>& tt,
                          const std::vector<float*>& linv0, const std::vector<float*>& linv1,
                          cudaStream_t stream, int* base);
-// map index of a node's [L; X] panel (P) and of its inverted diagonal blocks
-inline int tc_map_panel(int node) { return 2 * node; }
-inline int tc_map_dinv(int node) { return 2 * node + 1; }
+// map index of a node's [L; X] panel (P), of its inverted diagonal blocks, and of its
+// 16-bit operand copy (P16)
+constexpr int TC_NODE_MAPS = 3;
+inline int tc_map_panel(int node) { return TC_NODE_MAPS * node; }
+inline int tc_map_dinv(int node) { return TC_NODE_MAPS * node + 1; }
+inline int tc_map_panel16(int node) { return TC_NODE_MAPS * node + 2; }
+// op: TC_OP_F16 / TC_OP_BF16 run kinds 2 and 3 on the nodes' 16-bit copies (tasks carry
+// sa / sb); TC_OP_TF32 on the FP32 panels.
 int gemm_tc_launch(Handle& h, int li, const std::vector<GemmTask>& tasks, int kind, cudaStream_t stream,
-                   int slot = 0, int max_ctas = 0);
+                   int slot = 0, int max_ctas = 0, int op = TC_OP_TF32);
 
 // ---- kernels launched from the host orchestration -------------------------------
 // Zero the P and U storage of every front of level li (before its assembly).
