@@ -9,11 +9,13 @@ Metric: DOF / (t_setup + t_solve) per step, mixed form against the plain FP64 fo
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload diffusion129|...]
                   [--form mixed|fp64] [--mode exact|paper] [--gamma G] [--impl ours|reference]
 
-The default run prints one JSON line: the mixed form on the 129^3 workload (K timed
-steps after W warm-up steps) as the headline, and, in the same line, the plain FP64 form
-of the same workload (one timed step: it takes over a minute), the 256-problem batched
-workload in both forms (the FP64 form on its first 64 problems), the measured peaks of
-the library's own GEMM kernels, and the oracle's CPU baseline.
+The default run prints one JSON line: the mixed form (factor entries rounded to TF32, the
+long Schur updates on FP16 operand copies, FP16 sweeps, FP64 PCG) on the 129^3 workload
+(K timed steps after W warm-up steps) as the headline, and, in the same line, the plain
+FP64 form of the same workload (one timed step: it takes over a minute), the 256-problem
+batched workload in both forms (BF16 operands; the FP64 form on its first 64 problems),
+paper mode with gamma = 8 inner GMRES iterations and FGMRES, the measured peaks of the
+library's own GEMM kernels, and the oracle's CPU baseline.
 
 --impl reference times the CPU oracle (FP64, numpy/scipy on the host cores) on a bounded
 sample of the same workload family.  Multi-GPU runs are independent replicas (the
@@ -248,7 +250,7 @@ def main() -> None:
     ap.add_argument("--form", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--mode", default="exact", choices=["exact", "paper"])
     ap.add_argument("--gamma", type=int, default=0, help="paper mode: inner GMRES iterations (0: dense S~)")
-    ap.add_argument("--mixed-prec", default="tf32", choices=["tf32", "fp16", "bf16"],
+    ap.add_argument("--mixed-prec", default="fp16", choices=["tf32", "fp16", "bf16"],
                     help="factor precision of the mixed form (FP64 PCG in every form)")
     ap.add_argument("--workload", default="diffusion129")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -256,6 +258,7 @@ def main() -> None:
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-form record of the headline workload")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-workload record")
     ap.add_argument("--no-peaks", action="store_true", help="skip the GEMM peak probes")
+    ap.add_argument("--no-paper", action="store_true", help="skip the paper-mode (gamma = 8) record")
     ap.add_argument("--wave", type=int, default=64, help="problems per hierarchy (batched workload)")
     ap.add_argument("--n", type=int, default=None, help="grid side override (a scaled sample, e.g. for profiling)")
     ap.add_argument("--depth", type=int, default=None, help="octree depth override")
@@ -281,7 +284,7 @@ def main() -> None:
     mp = {"tf32": rsd.RSD_PREC_TF32, "fp16": rsd.RSD_PREC_FP16, "bf16": rsd.RSD_PREC_BF16}[args.mixed_prec]
     PREC = {"mixed": dict(prec_leaf=mp, prec_mid=mp, prec_root=mp),
             "fp64": dict(prec_leaf=rsd.RSD_PREC_FP64, prec_mid=rsd.RSD_PREC_FP64, prec_root=rsd.RSD_PREC_FP64)}
-    DTYPE = {"mixed": args.mixed_prec, "fp64": "f64"}
+    DTYPE = {"mixed": {"tf32": "tf32", "fp16": "fp16+tf32", "bf16": "bf16+tf32"}[args.mixed_prec], "fp64": "f64"}
     mode = rsd.RSD_MODE_PAPER if args.mode == "paper" else rsd.RSD_MODE_EXACT
     single = world == 1
     pk, pk_src = peaks()
@@ -340,10 +343,14 @@ def main() -> None:
     peak_rec = None
     if single and not args.no_peaks:
         tf_b, tf_s = rsd.peak_gemm(rsd.RSD_PREC_TF32, 8192, reps=5, seconds=4.0)
+        h_b, h_s = rsd.peak_gemm(rsd.RSD_PREC_FP16, 8192, reps=5, seconds=4.0)
         f64_b, f64_s = rsd.peak_gemm(rsd.RSD_PREC_FP64, 4096, reps=3, seconds=2.0)
         peak_rec = {"tf32_tcgen05": {"best": tf_b, "sustained": tf_s, "unit": "TFLOP/s",
                                      "how": "rsd_peak_gemm: the persistent 128x256 tcgen05 kind::tf32 kernel, "
                                             "C -= A B^T at 8192^3, best of 5 launches and back to back for 4 s"},
+                    "fp16_tcgen05": {"best": h_b, "sustained": h_s, "unit": "TFLOP/s",
+                                     "how": "rsd_peak_gemm: the same kernel with FP16 operands (kind::f16), "
+                                            "8192^3, best of 5 launches and back to back for 4 s"},
                     "fp64_simt": {"best": f64_b, "sustained": f64_s, "unit": "TFLOP/s",
                                   "how": "rsd_peak_gemm: the FP64 CUDA-core 64x64-tile kernel, C -= A B^T at "
                                          "4096^3, best of 3 launches and back to back for 2 s"}}
@@ -429,9 +436,10 @@ def main() -> None:
         bprobs = [rsd.grid_problem(w["n"], w["depth"], w["kappa"], w["f"]) for w in bwork]
         bdof = sum(p["n_dof"] for p in bprobs)
         bwaves = [bprobs[i:i + args.wave] for i in range(0, len(bprobs), args.wave)]
-        batched_step(bwaves, "mixed")()                # warm-up
-        msb, tsb, tvb, rb = timed_steps(torch, batched_step(bwaves, "mixed", profile=True), 2)
-        mixed_b = form_record(rb, msb, tsb, tvb, bdof, 2, pk, peak_rec, "mixed")
+        PREC["batched"] = dict(prec_leaf=rsd.RSD_PREC_BF16, prec_mid=rsd.RSD_PREC_BF16, prec_root=rsd.RSD_PREC_BF16)
+        batched_step(bwaves, "batched")()              # warm-up
+        msb, tsb, tvb, rb = timed_steps(torch, batched_step(bwaves, "batched", profile=True), 2)
+        mixed_b = form_record(rb, msb, tsb, tvb, bdof, 2, pk, peak_rec, "mixed (BF16 operands)")
         mixed_b["steps"] = 2
         mixed_b["warmup"] = 1
         sample = bwaves[0][:BATCH_FP64_SAMPLE]
@@ -446,6 +454,12 @@ def main() -> None:
                      "n_dof": bdof, "mixed": mixed_b, "fp64": fp64_b,
                      "mixed_over_fp64": mixed_b["value"] / fp64_b["value"]}
 
+    paper_rec = None
+    if single and not args.no_paper and not batched and args.mode == "exact" and args.form == "mixed":
+        single_step(prob, "mixed", m=rsd.RSD_MODE_PAPER, gamma=8)()          # warm-up
+        msp, tsp, tvp, rp = timed_steps(torch, single_step(prob, "mixed", profile=True, m=rsd.RSD_MODE_PAPER, gamma=8), 1)
+        paper_rec = form_record(rp, msp, tsp, tvp, n_dof, 1, pk, peak_rec, "mixed")
+        paper_rec.update(mode="paper (Algorithm 2, V-hat truncation)", gamma=8, krylov="FGMRES(30)", steps=1, warmup=1)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -486,6 +500,8 @@ def main() -> None:
         line["mixed_over_fp64"] = value / fp64_rec["value"]
     if batch_rec is not None:
         line["batched256"] = batch_rec
+    if paper_rec is not None:
+        line["paper_gamma8"] = paper_rec
     if peak_rec is not None:
         line["peaks_measured"] = peak_rec
     if world == 1 and not args.no_cpu_baseline:
@@ -505,28 +521,53 @@ def form_record(res, ms, t_setup, t_solve, n_dof, steps, pk, peak_rec, form) -> 
     info = res[-1][2]
     classes = {k: v for k, v in agg.items() if isinstance(v, dict) and "ms" in v}
     per = {k: v["ms"] / steps for k, v in classes.items() if v["launches"]}
-    # setup: the dominant GEMM class against the algorithmic flops sum_t (s^3/3 + s^2 b + s b^2)
-    gemm_cls = "gemm_tcgen05" if classes.get("gemm_tcgen05", {}).get("launches") else "gemm_simt"
-    g = classes[gemm_cls]
-    g_ms = g["ms"] / steps
-    achieved = info["setup_flops"] / (g_ms / 1e3) / 1e12 if g_ms else None
-    if gemm_cls == "gemm_tcgen05":
-        peak = pk["bf16_tflops_sustained"] * NOMINAL_TF32 / NOMINAL_BF16
+    # setup: the tensor-core (or CUDA-core) GEMM classes against the algorithmic flops
+    # sum_t (s^3/3 + s^2 b + s b^2), shared between the classes in proportion to their
+    # counted flops; each class has the peak of its own operand type, and the roof of the
+    # whole is the sum of the classes' times at their peaks
+    tc_classes = [k for k in ("gemm_tcgen05_f16", "gemm_tcgen05") if classes.get(k, {}).get("launches")]
+    if tc_classes:
+        bf = pk["bf16_tflops_sustained"]
+        cls_peak = {"gemm_tcgen05": bf * NOMINAL_TF32 / NOMINAL_BF16, "gemm_tcgen05_f16": bf}
+        counted = sum(classes[k]["flops"] for k in tc_classes)
+        per_cls, t_min, t_act = {}, 0.0, 0.0
+        for k in tc_classes:
+            fl = info["setup_flops"] * classes[k]["flops"] / counted
+            ms_k = classes[k]["ms"] / steps
+            per_cls[k] = {"algorithmic_flops": fl, "ms": ms_k, "achieved": fl / (ms_k / 1e3) / 1e12,
+                          "peak": cls_peak[k], "frac": fl / (ms_k / 1e3) / 1e12 / cls_peak[k],
+                          "launches": classes[k]["launches"] / steps}
+            t_min += fl / (cls_peak[k] * 1e12)
+            t_act += ms_k / 1e3
+        achieved = info["setup_flops"] / t_act / 1e12
+        peak = info["setup_flops"] / t_min / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "peak_source": f"TF32 = measured BF16 sustained {pk['bf16_tflops_sustained']} x {NOMINAL_TF32}/{NOMINAL_BF16} (nominal ratio)"}
+                "peak_source": (f"measured BF16 sustained {bf} TFLOP/s for the kind::f16 launches (FP16 and BF16 "
+                                f"share the dense rate), x {NOMINAL_TF32}/{NOMINAL_BF16} (nominal ratio) for the "
+                                f"kind::tf32 launches; the peak is the flop-weighted combination"),
+                "classes": per_cls}
         if peak_rec:
-            roof["tf32_measured_sustained"] = peak_rec["tf32_tcgen05"]["sustained"]
-            roof["frac_of_tf32_measured"] = achieved / peak_rec["tf32_tcgen05"]["sustained"]
+            own = {"gemm_tcgen05": peak_rec["tf32_tcgen05"]["sustained"],
+                   "gemm_tcgen05_f16": peak_rec["fp16_tcgen05"]["sustained"]}
+            t_own = sum(per_cls[k]["algorithmic_flops"] / (own[k] * 1e12) for k in tc_classes)
+            roof["frac_of_own_kernel_peak"] = t_own / t_act
+        gemm_cls = "+".join(tc_classes)
+        g_launches = sum(classes[k]["launches"] for k in tc_classes)
     else:
+        g = classes["gemm_simt"]
+        g_ms = g["ms"] / steps
+        achieved = info["setup_flops"] / (g_ms / 1e3) / 1e12 if g_ms else None
         roof = {"bound": "alu", "achieved": achieved, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
                 "peak_source": "FP64 CUDA-core nominal rate (152 SMs at 2.07 GHz)"}
         if peak_rec:
             roof["fp64_measured_sustained"] = peak_rec["fp64_simt"]["sustained"]
             roof["frac_of_fp64_measured"] = achieved / peak_rec["fp64_simt"]["sustained"]
+        gemm_cls = "gemm_simt"
+        g_launches = g["launches"]
     roof["frac"] = achieved / roof["peak"] if achieved else None
     roof["kernel"] = gemm_cls
-    roof["achieved_basis"] = "rsd_info setup_flops = sum_t (s^3/3 + s^2 b + s b^2) / the class's summed launch time"
-    roof["launches_per_step"] = g["launches"] / steps
+    roof["achieved_basis"] = "rsd_info setup_flops = sum_t (s^3/3 + s^2 b + s b^2) / the classes' summed launch time"
+    roof["launches_per_step"] = g_launches / steps
     sw = [classes.get(k) for k in ("sweep_up", "sweep_down") if classes.get(k)]
     sw_ms = sum(v["ms"] for v in sw) / steps
     sw_bytes = sum(v["bytes"] for v in sw) / steps

@@ -156,8 +156,10 @@ typedef struct {
  * factor+inverse, 5 CUDA-core panel solve, 6 upward sweep, 7 downward sweep,
  * 8 sweep gathers, 9 Krylov vector/SpMV kernels, 10 FP16 copy of a TF32 level's factor
  * (the entries the sweeps read), 11 inner GMRES of paper mode with gamma > 0 (matrix-free
- * S-MatVecs and Arnoldi steps of one interface level; bytes = the X rows streamed).     */
-#define RSD_PROFILE_CLASSES 12
+ * S-MatVecs and Arnoldi steps of one interface level; bytes = the X rows streamed),
+ * 12 tcgen05 GEMM on 16-bit operand copies (kind::f16; class 2 is then the kind::tf32
+ * launches only).                                                                       */
+#define RSD_PROFILE_CLASSES 13
 typedef struct {
     int64_t launches[RSD_PROFILE_CLASSES];
     double  ms[RSD_PROFILE_CLASSES];
@@ -323,9 +325,9 @@ int rsd_profile_trace(rsd_handle h, rsd_trace_rec* out, int64_t cap, int64_t* n)
 /* rsd_peak_gemm -- measured rate of this library's own dense GEMM kernel for one
  * precision, C -= A B^T on an n x n x n product of FP values in [-1, 1): the roofline
  * denominator of the Schur-complement updates of Eq. 3.2 (the paper reports no rates).
- *   prec    : RSD_PREC_TF32 (the persistent tcgen05 128 x 256 kernel, n a multiple of
- *             256), RSD_PREC_FP32 or RSD_PREC_FP64 (the CUDA-core kernel, n a multiple
- *             of 64).
+ *   prec    : RSD_PREC_TF32 / RSD_PREC_FP16 / RSD_PREC_BF16 (the persistent tcgen05
+ *             128 x 256 kernel with FP32 / FP16 / BF16 operands, n a multiple of 256),
+ *             RSD_PREC_FP32 or RSD_PREC_FP64 (the CUDA-core kernel, n a multiple of 64).
  *   reps    : timed single launches; *best_tflops = 2 n^3 / the shortest (TFLOP/s).
  *   seconds : then back-to-back launches for about this long; *sustained_tflops = their
  *             mean rate.  CUDA events on `stream` (cudaStream_t; NULL: legacy default).

@@ -1479,11 +1479,12 @@ extern "C" int rsd_peak_gemm(int32_t prec, int32_t n, int32_t reps, double secon
                              double* best_tflops, double* sustained_tflops) {
     if (!best_tflops || !sustained_tflops || reps < 1 || !(seconds >= 0)) return RSD_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    if (prec == RSD_PREC_TF32) {
+    if (prec == RSD_PREC_TF32 || prec == RSD_PREC_FP16 || prec == RSD_PREC_BF16) {
         int dev = 0, sms = 148;
         RSD_CUDA_TRY(cudaGetDevice(&dev));
         RSD_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        return gemm_tc_peak(n, reps, seconds, st, sms, best_tflops, sustained_tflops);
+        const int op = prec == RSD_PREC_FP16 ? TC_OP_F16 : prec == RSD_PREC_BF16 ? TC_OP_BF16 : TC_OP_TF32;
+        return gemm_tc_peak(n, reps, seconds, st, sms, best_tflops, sustained_tflops, op);
     }
     return gemm_simt_peak(prec, n, reps, seconds, st, best_tflops, sustained_tflops);
 }

@@ -17,6 +17,8 @@
 // zero fill handles ragged edges.  Every mbarrier wait is bounded; on timeout the CTA
 // raises ERR_TIMEOUT, drains, frees its TMEM and exits.
 #include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <array>
@@ -690,18 +692,27 @@ __global__ void k_fill_hash(float* __restrict__ p, int64_t n, uint32_t seed) {
 
 }  // namespace
 
-int gemm_tc_peak(int n, int reps, double seconds, cudaStream_t stream, int num_sms, double* best, double* sustained) {
+// 16-bit operand values from FP32 ones (probe inputs)
+__global__ void k_to16(const float* __restrict__ src, unsigned short* __restrict__ dst, int64_t n, int bf16) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = bf16 ? __bfloat16_as_ushort(__float2bfloat16_rn(src[i])) : __half_as_ushort(__float2half_rn(src[i]));
+}
+
+int gemm_tc_peak(int n, int reps, double seconds, cudaStream_t stream, int num_sms, double* best, double* sustained,
+                 int op) {
     if (n < 256 || n % 256 || reps < 1 || !best || !sustained) return RSD_ERR_ARG;
     const size_t elems = (size_t)n * n;
     char* buf = nullptr;
     const size_t o_b = elems * 4, o_c = 2 * elems * 4, o_maps = 3 * elems * 4;
     const int tm = n / BM, tn = n / 256;
+    const int nkb = n / (op == TC_OP_TF32 ? BK : 64);
     std::vector<TcTile> tiles;
     for (int a0 = 0; a0 < tm; a0 += TILE_BAND)
         for (int b = 0; b < tn; ++b)
-            for (int a = a0; a < std::min(tm, a0 + TILE_BAND); ++a) tiles.push_back({0, a, b, 0, n / BK, -1, 0, 0});
+            for (int a = a0; a < std::min(tm, a0 + TILE_BAND); ++a) tiles.push_back({0, a, b, 0, nkb, -1, 0, 0});
     const size_t o_task = o_maps + 2 * sizeof(CUtensorMap);
-    const size_t o_tiles = o_task + 256, o_err = o_tiles + ((tiles.size() * sizeof(TcTile) + 255) & ~(size_t)255);
+    const size_t o_tiles = o_task + 256, o_ones = o_tiles + ((tiles.size() * sizeof(TcTile) + 255) & ~(size_t)255);
+    const size_t o_err = o_ones + (size_t)n * 4;
     const size_t total = o_err + 256;
     RSD_CUDA_TRY(cudaMalloc((void**)&buf, total));
     struct Free { char* p; ~Free() { cudaFree(p); } } fr{buf};
@@ -712,22 +723,51 @@ int gemm_tc_peak(int n, int reps, double seconds, cudaStream_t stream, int num_s
     k_fill_hash<<<1024, 256, 0, stream>>>(B, (int64_t)elems, 0x7f4a7c15u);
     RSD_CUDA_TRY(cudaMemsetAsync(Cm, 0, elems * 4, stream));
     RSD_CUDA_TRY(cudaMemsetAsync(buf + o_err, 0, 256, stream));
+    // 16-bit operands: converted copies in the C buffer's place before C is cleared
+    void* Aop = A;
+    void* Bop = B;
+    if (op != TC_OP_TF32) {
+        unsigned short* A16 = (unsigned short*)Cm;
+        unsigned short* B16 = A16 + elems;
+        k_to16<<<1024, 256, 0, stream>>>(A, A16, (int64_t)elems, op == TC_OP_BF16);
+        k_to16<<<1024, 256, 0, stream>>>(B, B16, (int64_t)elems, op == TC_OP_BF16);
+        RSD_CUDA_TRY(cudaMemcpyAsync(A, A16, elems * 2, cudaMemcpyDeviceToDevice, stream));
+        RSD_CUDA_TRY(cudaMemcpyAsync(B, B16, elems * 2, cudaMemcpyDeviceToDevice, stream));
+        RSD_CUDA_TRY(cudaMemsetAsync(Cm, 0, elems * 4, stream));
+    }
     CUtensorMap maps[2];
-    RSD_TRY(encode_2d(&maps[0], A, n, n, n));
-    RSD_TRY(encode_2d(&maps[1], B, n, n, n));
+    RSD_TRY(encode_2d(&maps[0], Aop, n, n, n, op));
+    RSD_TRY(encode_2d(&maps[1], Bop, n, n, n, op));
+    // unit row scales for the 16-bit epilogue
+    float* ones = (float*)(buf + o_tiles) + ((tiles.size() * sizeof(TcTile) + 255) & ~(size_t)255) / 4;
     TcTask t{};
     t.C = Cm; t.ldc = n; t.M = n; t.N = n; t.K = n; t.lower = 0; t.beta = 1;
     t.map_a = 0; t.map_b = 1; t.alpha = -1.0f; t.round_tf32 = 0;
+    t.sa = op != TC_OP_TF32 ? ones : nullptr;
+    t.sb = t.sa;
+    if (op != TC_OP_TF32) {
+        std::vector<float> one((size_t)n, 1.0f);
+        RSD_CUDA_TRY(cudaMemcpyAsync(ones, one.data(), sizeof(float) * n, cudaMemcpyHostToDevice, stream));
+        RSD_CUDA_TRY(cudaStreamSynchronize(stream));
+    }
     RSD_CUDA_TRY(cudaMemcpyAsync(buf + o_maps, maps, sizeof(maps), cudaMemcpyHostToDevice, stream));
     RSD_CUDA_TRY(cudaMemcpyAsync(buf + o_task, &t, sizeof(t), cudaMemcpyHostToDevice, stream));
     RSD_CUDA_TRY(cudaMemcpyAsync(buf + o_tiles, tiles.data(), tiles.size() * sizeof(TcTile), cudaMemcpyHostToDevice, stream));
     RSD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc_persist<256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<256, 4>::TOTAL));
+    RSD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc_persist<256, 4, TC_OP_F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<256, 4>::TOTAL));
+    RSD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc_persist<256, 4, TC_OP_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<256, 4>::TOTAL));
     int* err = (int*)(buf + o_err);
     const int ctas = std::min((int)tiles.size(), num_sms);
     auto launch = [&]() {
-        k_gemm_tc_persist<256, 4><<<(unsigned)ctas, TC_THREADS, Smem<256, 4>::TOTAL, stream>>>(
-            (const TcTask*)(buf + o_task), (const TcTile*)(buf + o_tiles), (int)tiles.size(),
-            (const CUtensorMap*)(buf + o_maps), nullptr, err);
+        const TcTask* tk = (const TcTask*)(buf + o_task);
+        const TcTile* tl = (const TcTile*)(buf + o_tiles);
+        const CUtensorMap* mp = (const CUtensorMap*)(buf + o_maps);
+        if (op == TC_OP_F16)
+            k_gemm_tc_persist<256, 4, TC_OP_F16><<<(unsigned)ctas, TC_THREADS, Smem<256, 4>::TOTAL, stream>>>(tk, tl, (int)tiles.size(), mp, nullptr, err);
+        else if (op == TC_OP_BF16)
+            k_gemm_tc_persist<256, 4, TC_OP_BF16><<<(unsigned)ctas, TC_THREADS, Smem<256, 4>::TOTAL, stream>>>(tk, tl, (int)tiles.size(), mp, nullptr, err);
+        else
+            k_gemm_tc_persist<256, 4><<<(unsigned)ctas, TC_THREADS, Smem<256, 4>::TOTAL, stream>>>(tk, tl, (int)tiles.size(), mp, nullptr, err);
         count_launch();
     };
     cudaEvent_t e0, e1;
@@ -899,7 +939,7 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
         RSD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc_persist<256, 4, TC_OP_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<256, 4>::TOTAL));
         st->attr_set = true;
     }
-    const int pi = prof_begin(h, K_GEMM_TC, stream);
+    const int pi = prof_begin(h, op != TC_OP_TF32 ? K_GEMM_TC16 : K_GEMM_TC, stream);
     // short K (inner panel update, panel solve): 3-stage ring, two CTAs per SM so one
     // tile's epilogue overlaps the other's main loop; long K: deeper rings, one CTA per SM
     if (bn == 128 && max_kb <= 16)

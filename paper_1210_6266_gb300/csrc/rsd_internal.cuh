@@ -95,7 +95,7 @@ enum { TC_OP_TF32 = 0, TC_OP_F16 = 1, TC_OP_BF16 = 2 };
 
 // Kernel classes for launch counting and the optional CUDA-event profile.
 enum KClass { K_ASSEMBLE = 0, K_EXTEND, K_GEMM_TC, K_GEMM_SIMT, K_POTRF, K_TRSM, K_FWD, K_BWD,
-              K_GATHER, K_KRYLOV, K_COPY16, K_GAMMA, K_CLASSES };
+              K_GATHER, K_KRYLOV, K_COPY16, K_GAMMA, K_GEMM_TC16, K_CLASSES };
 
 // Per-handle profile: one event pair per launch of a class, with the algorithmic
 // flops and bytes of that launch; reduced on demand by rsd_profile().
@@ -331,7 +331,8 @@ int sweep_with(Handle& h, int li, bool forward, const FrontDesc* fronts, const i
                const double* in, double* out, int* ticket);
 int paper_extend_add(Handle& h);
 // peak probes of this library's GEMM kernels (rsd_peak_gemm)
-int gemm_tc_peak(int n, int reps, double seconds, cudaStream_t stream, int num_sms, double* best, double* sustained);
+int gemm_tc_peak(int n, int reps, double seconds, cudaStream_t stream, int num_sms, double* best, double* sustained,
+                 int op);
 int gemm_simt_peak(int prec, int n, int reps, double seconds, cudaStream_t st, double* best, double* sustained);
 int run_apply_paper(Handle& h, const double* r, double* z);
 int gamma_interface_solve(Handle& h, int li, double* z);
