@@ -44,6 +44,7 @@ NOMINAL_FP64_TFLOPS = 1.25
 CPU_SAMPLE = dict(n=41, depth=3)  # bounded oracle sample of the diffusion workload family
 FP64_WARM = dict(n=33, depth=3)   # small grid that loads the FP64 kernels before the timed step
 BATCH_FP64_SAMPLE = 64            # problems of the batched workload timed in the FP64 form
+ELASTIC_NU = 0.3                  # Poisson's ratio of the elasticity workload
 
 
 def peaks():
@@ -142,6 +143,13 @@ def make_workload(name: str, n: int | None = None, depth: int | None = None):
         if n is not None or depth is not None:
             raise SystemExit("--n/--depth apply to single-problem workloads only")
         return synth.batched_poisson(w["count"], w["size_seed"], w["f_seed0"]), w
+    if w["kind"] == "elasticity":
+        if n is not None:
+            w["n"] = n
+        if depth is not None:
+            w["depth"] = depth
+        return dict(n=w["n"], depth=w["depth"], E_leaf=synth.elasticity_moduli(8 ** w["depth"], w["e_seed"]),
+                    f=synth.uniform(w["f_seed"], 3 * (w["n"] - 2) ** 3)), w
     if w["kind"] not in ("poisson", "lognormal"):
         raise SystemExit(f"workload {name} is not built yet")
     if n is not None:
@@ -259,6 +267,7 @@ def main() -> None:
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-workload record")
     ap.add_argument("--no-peaks", action="store_true", help="skip the GEMM peak probes")
     ap.add_argument("--no-paper", action="store_true", help="skip the paper-mode (gamma = 8) record")
+    ap.add_argument("--no-elastic", action="store_true", help="skip the elasticity-workload record")
     ap.add_argument("--wave", type=int, default=64, help="problems per hierarchy (batched workload)")
     ap.add_argument("--n", type=int, default=None, help="grid side override (a scaled sample, e.g. for profiling)")
     ap.add_argument("--depth", type=int, default=None, help="octree depth override")
@@ -363,6 +372,10 @@ def main() -> None:
         n_dof = sum(p["n_dof"] for p in probs)
         waves = [probs[i:i + args.wave] for i in range(0, len(probs), args.wave)]
         step = lambda form, profile=False: batched_step(waves, form, profile)  # noqa: E731
+    elif wdesc["kind"] == "elasticity":
+        prob = rsd.grid_problem_elastic(work["n"], work["depth"], work["E_leaf"], ELASTIC_NU, work["f"])
+        n_dof = prob["n_dof"]
+        step = lambda form, profile=False: single_step(prob, form, profile)  # noqa: E731
     else:
         prob = rsd.grid_problem(work["n"], work["depth"], work["kappa"], work["f"])
         n_dof = prob["n_dof"]
@@ -454,6 +467,19 @@ def main() -> None:
                      "n_dof": bdof, "mixed": mixed_b, "fp64": fp64_b,
                      "mixed_over_fp64": mixed_b["value"] / fp64_b["value"]}
 
+    elastic_rec = None
+    if single and not args.no_elastic and args.workload == "diffusion129" and args.mode == "exact" and args.form == "mixed":
+        ework, _ = make_workload("elasticity97")
+        eprob = rsd.grid_problem_elastic(ework["n"], ework["depth"], ework["E_leaf"], ELASTIC_NU, ework["f"])
+        single_step(eprob, "mixed")()                 # warm-up
+        mse, tse, tve, re_ = timed_steps(torch, single_step(eprob, "mixed", profile=True), 2)
+        elastic_rec = form_record(re_, mse, tse, tve, eprob["n_dof"], 2, pk, peak_rec, "mixed")
+        elastic_rec.update(workload=(f"elasticity97: 3-D linear elasticity (3 DOF/node), {ework['n']}^3 nodes, "
+                                     f"trilinear hex, E per leaf log-uniform [1, 1e3], nu = {ELASTIC_NU}, "
+                                     f"{8 ** ework['depth']} leaves (depth {ework['depth']})"),
+                           n_dof=eprob["n_dof"], steps=2, warmup=1,
+                           fp64_form="not timed: about 3.5e14 flops of FP64 factorisation, some 5 minutes")
+        del eprob
     paper_rec = None
     if single and not args.no_paper and not batched and args.mode == "exact" and args.form == "mixed":
         single_step(prob, "mixed", m=rsd.RSD_MODE_PAPER, gamma=8)()          # warm-up
@@ -474,6 +500,8 @@ def main() -> None:
         "vs_baseline": None, "dtype": DTYPE[args.form], "data": "synthetic",
         "config": {"workload": (f"{args.workload}: -div(kappa grad u)=f, {work['n']}^3 nodes, trilinear hex, "
                                 f"kappa lognormal per element") if wdesc["kind"] == "lognormal" else
+                               (f"{args.workload}: 3-D linear elasticity, {work['n']}^3 nodes, 3 DOF/node, E per leaf "
+                                f"log-uniform [1, 1e3], nu = {ELASTIC_NU}") if wdesc["kind"] == "elasticity" else
                                (f"{args.workload}: {len(work)} independent Poisson problems, n in "
                                 f"[{min(w['n'] for w in work)}, {max(w['n'] for w in work)}], 8-64 leaves each, "
                                 f"hierarchies of {args.wave} problems") if batched else args.workload,
@@ -502,6 +530,8 @@ def main() -> None:
         line["batched256"] = batch_rec
     if paper_rec is not None:
         line["paper_gamma8"] = paper_rec
+    if elastic_rec is not None:
+        line["elasticity97"] = elastic_rec
     if peak_rec is not None:
         line["peaks_measured"] = peak_rec
     if world == 1 and not args.no_cpu_baseline:

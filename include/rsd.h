@@ -371,6 +371,30 @@ int rsd_grid_exp(int32_t n, const double* m, double* kappa, void* stream);
 int rsd_grid_coef_grad(int32_t n, const double* u, const double* lam, const double* kappa,
                        double* dkappa, double* dm, void* stream);
 
+/* ---- 3-D linear elasticity on the same grids (three DOFs per node) ---------------- *
+ * -div sigma(u) = f with sigma = lam tr(eps) I + 2 mu eps: the SPD Navier-Lame form of
+ * Sec. 4's Problem 4 (Eq. 4.4, whose printed sign is read as this form), in 3-D.  DOF
+ * 3 * node + c (c = 0, 1, 2 the displacement component), node the interior-node id above;
+ * homogeneous Dirichlet on every component at the boundary.                           */
+
+/* sizes: n_dof = 3 (n-2)^3 and the nonzero count (81 per interior row).                  */
+int rsd_grid_elastic_sizes(int32_t n, int64_t* n_dof, int64_t* nnz);
+/* assemble K with Young's modulus constant per leaf sub-domain of the octree of the given
+ * depth (E_leaf device, 8^depth entries in breadth-first leaf order; an element spanning
+ * [e, e+1] per coordinate lies in a box's lower child when e < its mid-plane) and
+ * Poisson's ratio nu in (-1, 1/2); K_e = E_e h Khat(nu) with Khat the unit-cube element
+ * matrix (exact integrals of the trilinear shape functions).  rowptr/col/val device
+ * (n_dof + 1, nnz, nnz); one thread per row, deterministic.  RSD_ERR_ARG on bad sizes.  */
+int rsd_grid_elastic_assemble(int32_t n, int32_t depth, const double* E_leaf, double nu,
+                              int64_t* rowptr, int32_t* col, double* val, void* stream);
+/* lumped load b = h^3 f per DOF; both device, n_dof entries.                             */
+int rsd_grid_elastic_load(int32_t n, const double* f, double* b, void* stream);
+/* the octree decomposition of rsd_grid_partition with every DOF owned by its node's owner:
+ * dof_node device (n_dof), parent host (as rsd_grid_partition), node_scratch device
+ * ((n-2)^3 ints, overwritten).                                                          */
+int rsd_grid_elastic_partition(int32_t n, int32_t depth, int32_t* dof_node, int32_t* parent,
+                               int32_t* node_scratch, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

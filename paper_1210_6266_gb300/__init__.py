@@ -19,7 +19,7 @@ from ._lib import (RSD_KRYLOV_AUTO, RSD_KRYLOV_FGMRES, RSD_KRYLOV_PCG, RSD_MEM_D
                    RSD_MODE_EXACT, RSD_MODE_PAPER, RSD_PREC_BF16, RSD_PREC_FP16, RSD_PREC_FP32, RSD_PREC_FP64,
                    RSD_PREC_TF32, RSDError, check)
 
-__all__ = ["RSD", "grid_problem", "grid_sizes", "grid_exp", "coef_grad", "diffusion_solve",
+__all__ = ["RSD", "grid_problem", "grid_problem_elastic", "grid_sizes", "grid_exp", "coef_grad", "diffusion_solve",
            "DiffusionSolve", "launch_count", "peak_gemm", "RSDError", "RSD_PREC_FP64", "RSD_PREC_FP32",
            "RSD_PREC_TF32", "RSD_PREC_FP16", "RSD_PREC_BF16", "RSD_MODE_EXACT", "RSD_MODE_PAPER", "RSD_KRYLOV_AUTO", "RSD_KRYLOV_PCG",
            "RSD_KRYLOV_FGMRES"]
@@ -66,6 +66,34 @@ def grid_problem(n: int, depth: int, kappa, f, device: str = "cuda") -> dict:
     check(lib.rsd_grid_load(n, _ptr(fn), _ptr(b), _stream()), "rsd_grid_load")
     prob["b"] = b
     return prob
+
+
+def grid_problem_elastic(n: int, depth: int, E_leaf, nu: float, f, device: str = "cuda") -> dict:
+    """3-D linear elasticity on the n^3 grid (three DOFs per node): K with Young's modulus
+    E_leaf[l] on octree leaf l (8^depth values) and Poisson's ratio nu, b = h^3 f (f per
+    DOF, 3 (n-2)^3 values), the ownership (each DOF owned by its node's owner) and tree."""
+    lib = _lib.load()
+    nd, nz = C.c_int64(), C.c_int64()
+    check(lib.rsd_grid_elastic_sizes(n, C.byref(nd), C.byref(nz)), "rsd_grid_elastic_sizes")
+    nd, nz = nd.value, nz.value
+    E = torch.as_tensor(np.ascontiguousarray(E_leaf), dtype=torch.float64).to(device)
+    fn = torch.as_tensor(np.ascontiguousarray(f), dtype=torch.float64).to(device)
+    rowptr = torch.empty(nd + 1, dtype=torch.int64, device=device)
+    col = torch.empty(nz, dtype=torch.int32, device=device)
+    val = torch.empty(nz, dtype=torch.float64, device=device)
+    dof_node = torch.empty(nd, dtype=torch.int32, device=device)
+    scratch = torch.empty(nd // 3, dtype=torch.int32, device=device)
+    n_nodes = (8 ** (depth + 1) - 1) // 7
+    parent = np.empty(n_nodes, dtype=np.int32)
+    b = torch.empty(nd, dtype=torch.float64, device=device)
+    st = _stream()
+    check(lib.rsd_grid_elastic_assemble(n, depth, _ptr(E), nu, _ptr(rowptr), _ptr(col), _ptr(val), st),
+          "rsd_grid_elastic_assemble")
+    check(lib.rsd_grid_elastic_partition(n, depth, _ptr(dof_node), parent.ctypes.data, _ptr(scratch), st),
+          "rsd_grid_elastic_partition")
+    check(lib.rsd_grid_elastic_load(n, _ptr(fn), _ptr(b), st), "rsd_grid_elastic_load")
+    return dict(n=n, depth=depth, n_dof=nd, nnz=nz, rowptr=rowptr, col=col, val=val,
+                dof_node=dof_node, parent=parent, b=b)
 
 
 def _grid_system(n: int, depth: int, kappa: torch.Tensor) -> dict:

@@ -43,7 +43,8 @@ EXPORTS = [
     "rsd_profile", "rsd_launch_count", "rsd_apply_static", "rsd_last_error_detail",
     "rsd_release_cache", "rsd_setup_batched", "rsd_solve_adjoint", "rsd_grid_exp",
     "rsd_grid_coef_grad", "rsd_profile_trace", "rsd_peak_gemm",
-    "rsd_inject_drop_sweep_item",
+    "rsd_inject_drop_sweep_item", "rsd_grid_elastic_sizes", "rsd_grid_elastic_assemble",
+    "rsd_grid_elastic_load", "rsd_grid_elastic_partition",
 ]
 
 
@@ -124,6 +125,10 @@ def load() -> C.CDLL:
             "rsd_grid_load": (C.c_int, [C.c_int32, P, P, P]),
             "rsd_grid_partition": (C.c_int, [C.c_int32, C.c_int32, P, P, P]),
             "rsd_grid_exp": (C.c_int, [C.c_int32, P, P, P]),
+            "rsd_grid_elastic_sizes": (C.c_int, [C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+            "rsd_grid_elastic_assemble": (C.c_int, [C.c_int32, C.c_int32, P, C.c_double, P, P, P, P]),
+            "rsd_grid_elastic_load": (C.c_int, [C.c_int32, P, P, P]),
+            "rsd_grid_elastic_partition": (C.c_int, [C.c_int32, C.c_int32, P, P, P, P]),
             "rsd_grid_coef_grad": (C.c_int, [C.c_int32, P, P, P, P, P, P]),
             "rsd_profile": (C.c_int, [P, C.POINTER(rsd_profile_t), C.c_int32]),
             "rsd_profile_trace": (C.c_int, [P, P, C.c_int64, C.POINTER(C.c_int64)]),
