@@ -268,6 +268,8 @@ def main() -> None:
     ap.add_argument("--no-peaks", action="store_true", help="skip the GEMM peak probes")
     ap.add_argument("--no-paper", action="store_true", help="skip the paper-mode (gamma = 8) record")
     ap.add_argument("--no-elastic", action="store_true", help="skip the elasticity-workload record")
+    ap.add_argument("--tune", default="auto", choices=["auto", "off"],
+                    help="auto: run the tile autotuner first and set up every hierarchy with its table")
     ap.add_argument("--wave", type=int, default=64, help="problems per hierarchy (batched workload)")
     ap.add_argument("--n", type=int, default=None, help="grid side override (a scaled sample, e.g. for profiling)")
     ap.add_argument("--depth", type=int, default=None, help="octree depth override")
@@ -303,11 +305,19 @@ def main() -> None:
             dist.barrier()
 
     # ---- one step of a single problem / of a batch in waves ----------------------------
+    tune_path, tune_rec = None, None
+    if args.tune == "auto":
+        tune_path = os.path.join(tempfile.mkdtemp(prefix="rsd_tune_"), "tune.json")
+        secs = rsd.autotune(tune_path)
+        tune_rec = {"seconds": secs, "buckets": rsd.tune_entries(tune_path),
+                    "how": "rsd_autotune: tile width and split-K count of the tensor-core updates, per bucket of "
+                           "output tiles x K and operand format, best of 3 synthetic launches each"}
+
     def single_step(prob, form, profile=False, m=mode, gamma=args.gamma):
         def run():
             h = rsd.RSD.setup(prob["rowptr"], prob["col"], prob["val"], prob["dof_node"], prob["parent"],
                               profile=profile, mode=m, gamma=gamma if m == rsd.RSD_MODE_PAPER else 0,
-                              maxit=1000, **PREC[form])
+                              maxit=1000, tune_cache=tune_path, **PREC[form])
             b = torch.cuda.Event(enable_timing=True)
             b.record(torch.cuda.current_stream())
             u, st = h.solve(prob["b"], tol=TOL)
@@ -328,7 +338,7 @@ def main() -> None:
             for wv in waves:
                 a = torch.cuda.Event(enable_timing=True)
                 a.record(torch.cuda.current_stream())
-                h = rsd.RSD.setup_batched(wv, profile=profile, **PREC[form])
+                h = rsd.RSD.setup_batched(wv, profile=profile, tune_cache=tune_path, **PREC[form])
                 t_b = torch.cuda.Event(enable_timing=True)
                 t_b.record(torch.cuda.current_stream())
                 t_b.synchronize()
@@ -418,11 +428,11 @@ def main() -> None:
         for g in groups:
             hp = [dict(host[i], parent=src[i]["parent"]) for i in g]
             if batched:
-                h = rsd.RSD.setup_batched(hp, **PREC[args.form])
+                h = rsd.RSD.setup_batched(hp, tune_cache=tune_path, **PREC[args.form])
             else:
                 h = rsd.RSD.setup(hp[0]["rowptr"], hp[0]["col"], hp[0]["val"], hp[0]["dof_node"], hp[0]["parent"],
                                   mode=mode, gamma=args.gamma if mode == rsd.RSD_MODE_PAPER else 0, maxit=1000,
-                                  **PREC[args.form])
+                                  tune_cache=tune_path, **PREC[args.form])
             b = torch.cat([x["b"] for x in hp]).to("cuda", non_blocking=True)
             u, _ = h.solve(b, tol=TOL)
             u_host[off:off + u.numel()].copy_(u, non_blocking=True)
@@ -534,6 +544,7 @@ def main() -> None:
         line["elasticity97"] = elastic_rec
     if peak_rec is not None:
         line["peaks_measured"] = peak_rec
+    line["autotune"] = tune_rec
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(1)
     print(json.dumps(line), flush=True)

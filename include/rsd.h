@@ -127,6 +127,9 @@ typedef struct {
                             interface front is formed or factored                          */
     int32_t krylov;      /* RSD_KRYLOV_*                                                    */
     int32_t restart;     /* FGMRES restart length (<= 0: 30)                                */
+    const char* tune_cache; /* path of a table written by rsd_autotune (host string, read at
+                            setup): the tile width and split-K count of the tensor-core
+                            updates by size bucket; NULL = built-in rules                  */
 } rsd_options;
 
 typedef struct {
@@ -335,6 +338,21 @@ int rsd_profile_trace(rsd_handle h, rsd_trace_rec* out, int64_t cap, int64_t* n)
  * precision, RSD_ERR_TIMEOUT if a bounded wait of the kernel gave up.                 */
 int rsd_peak_gemm(int32_t prec, int32_t n, int32_t reps, double seconds, void* stream,
                   double* best_tflops, double* sustained_tflops);
+
+/* rsd_autotune -- measure this library's tensor-core GEMM configurations and write the
+ * fastest per size bucket to `path` (JSON: one object per bucket with the operand format
+ * (0 TF32, 1 FP16/BF16), output tiles of 128 x 256, K, tile width, split-K count and the
+ * measured and built-in-rule times in us).  The buckets: 1, 4, 16, 64, 256 tiles x K =
+ * 512, 2048, 8192, 24576; the candidates: tile width 128 or 256 (TF32; 256 for 16-bit
+ * operands) x 1..32 split-K slices of at least 4 K blocks; each timed as the best of 3
+ * launches of C -= A B^T on synthetic operands through the factorisation's own launcher.
+ * The paper has no counterpart (the tile shapes of the Schur-complement GEMMs of Eq. 3.2).
+ * Allocates and frees about 5 GB of device memory; *seconds receives the wall time.
+ * RSD_ERR_ARG if the file cannot be written.                                           */
+int rsd_autotune(const char* path, double* seconds, void* stream);
+/* rsd_tune_load -- parse and check a table written by rsd_autotune (host only, no GPU):
+ * *entries receives the number of buckets; RSD_ERR_ARG for a missing or malformed file.  */
+int rsd_tune_load(const char* path, int32_t* entries);
 
 /* rsd_launch_count -- kernels this library has launched in this process so far.       */
 int64_t rsd_launch_count(void);

@@ -20,7 +20,7 @@ from ._lib import (RSD_KRYLOV_AUTO, RSD_KRYLOV_FGMRES, RSD_KRYLOV_PCG, RSD_MEM_D
                    RSD_PREC_TF32, RSDError, check)
 
 __all__ = ["RSD", "grid_problem", "grid_problem_elastic", "grid_sizes", "grid_exp", "coef_grad", "diffusion_solve",
-           "DiffusionSolve", "launch_count", "peak_gemm", "RSDError", "RSD_PREC_FP64", "RSD_PREC_FP32",
+           "DiffusionSolve", "launch_count", "peak_gemm", "autotune", "tune_entries", "RSDError", "RSD_PREC_FP64", "RSD_PREC_FP32",
            "RSD_PREC_TF32", "RSD_PREC_FP16", "RSD_PREC_BF16", "RSD_MODE_EXACT", "RSD_MODE_PAPER", "RSD_KRYLOV_AUTO", "RSD_KRYLOV_PCG",
            "RSD_KRYLOV_FGMRES"]
 
@@ -32,6 +32,22 @@ def peak_gemm(prec: int, n: int, reps: int = 5, seconds: float = 4.0) -> tuple[f
     check(_lib.load().rsd_peak_gemm(prec, n, reps, seconds, _stream(), C.byref(best), C.byref(sus)),
           "rsd_peak_gemm")
     return best.value, sus.value
+
+
+def autotune(path: str) -> float:
+    """Time the tensor-core GEMM configurations per size bucket and write the fastest to
+    `path` (rsd_autotune); returns the seconds taken.  Pass the path as tune_cache to
+    RSD.setup to use it."""
+    secs = C.c_double()
+    check(_lib.load().rsd_autotune(path.encode(), C.byref(secs), _stream()), "rsd_autotune")
+    return secs.value
+
+
+def tune_entries(path: str) -> int:
+    """Number of buckets in a table written by autotune (rsd_tune_load; host only)."""
+    n = C.c_int32()
+    check(_lib.load().rsd_tune_load(path.encode(), C.byref(n)), "rsd_tune_load")
+    return n.value
 
 
 def launch_count() -> int:
@@ -146,7 +162,8 @@ class RSD:
               dof_node: torch.Tensor, parent, prec_leaf: int = RSD_PREC_TF32,
               prec_mid: int = RSD_PREC_TF32, prec_root: int = RSD_PREC_FP64,
               maxit: int = 200, profile: bool = False, mode: int = RSD_MODE_EXACT,
-              wait_cycles: int = 0, gamma: int = 0, krylov: int = 0, restart: int = 0) -> "RSD":
+              wait_cycles: int = 0, gamma: int = 0, krylov: int = 0, restart: int = 0,
+              tune_cache: str | None = None) -> "RSD":
         lib = _lib.load()
         dev = rowptr.is_cuda
         if not (col.is_cuda == dev and val.is_cuda == dev and dof_node.is_cuda == dev):
@@ -162,7 +179,7 @@ class RSD:
         tree = _lib.rsd_tree(len(par), par.ctypes.data)
         opt = _lib.rsd_options(mode, prec_leaf, prec_mid, prec_root, maxit,
                                _stream() if torch.cuda.is_available() else 0, int(profile), wait_cycles,
-                               gamma, krylov, restart)
+                               gamma, krylov, restart, tune_cache.encode() if tune_cache else None)
         out = C.c_void_p()
         rc = lib.rsd_setup(C.byref(csr), _ptr(dof_node), C.byref(tree), C.byref(opt), C.byref(out))
         if rc != 0:
@@ -173,7 +190,8 @@ class RSD:
 
     @classmethod
     def setup_batched(cls, problems, prec_leaf: int = RSD_PREC_TF32, prec_mid: int = RSD_PREC_TF32,
-                      prec_root: int = RSD_PREC_FP64, maxit: int = 200, profile: bool = False) -> "RSD":
+                      prec_root: int = RSD_PREC_FP64, maxit: int = 200, profile: bool = False,
+                      tune_cache: str | None = None) -> "RSD":
         """One hierarchy for several independent problems (dicts with rowptr, col, val,
         dof_node, parent, all on the device).  Vectors are the problems' concatenation."""
         lib = _lib.load()
@@ -196,7 +214,8 @@ class RSD:
             owners[i] = _ptr(ow)
             total += rp.numel() - 1
         opt = _lib.rsd_options(RSD_MODE_EXACT, prec_leaf, prec_mid, prec_root, maxit,
-                               _stream() if torch.cuda.is_available() else 0, int(profile))
+                               _stream() if torch.cuda.is_available() else 0, int(profile), 0, 0, 0, 0,
+                               tune_cache.encode() if tune_cache else None)
         out = C.c_void_p()
         rc = lib.rsd_setup_batched(n, csrs, owners, trees, C.byref(opt), C.byref(out))
         del keep

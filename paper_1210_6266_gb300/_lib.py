@@ -44,7 +44,7 @@ EXPORTS = [
     "rsd_release_cache", "rsd_setup_batched", "rsd_solve_adjoint", "rsd_grid_exp",
     "rsd_grid_coef_grad", "rsd_profile_trace", "rsd_peak_gemm",
     "rsd_inject_drop_sweep_item", "rsd_grid_elastic_sizes", "rsd_grid_elastic_assemble",
-    "rsd_grid_elastic_load", "rsd_grid_elastic_partition",
+    "rsd_grid_elastic_load", "rsd_grid_elastic_partition", "rsd_autotune", "rsd_tune_load",
 ]
 
 
@@ -61,7 +61,7 @@ class rsd_options(C.Structure):
     _fields_ = [("mode", C.c_int32), ("prec_leaf", C.c_int32), ("prec_mid", C.c_int32),
                 ("prec_root", C.c_int32), ("maxit", C.c_int32), ("stream", C.c_void_p),
                 ("profile", C.c_int32), ("wait_cycles", C.c_int64), ("gamma", C.c_int32),
-                ("krylov", C.c_int32), ("restart", C.c_int32)]
+                ("krylov", C.c_int32), ("restart", C.c_int32), ("tune_cache", C.c_char_p)]
 
 
 class rsd_stats(C.Structure):
@@ -133,6 +133,8 @@ def load() -> C.CDLL:
             "rsd_profile": (C.c_int, [P, C.POINTER(rsd_profile_t), C.c_int32]),
             "rsd_profile_trace": (C.c_int, [P, P, C.c_int64, C.POINTER(C.c_int64)]),
             "rsd_launch_count": (C.c_int64, []),
+            "rsd_autotune": (C.c_int, [C.c_char_p, C.POINTER(C.c_double), P]),
+            "rsd_tune_load": (C.c_int, [C.c_char_p, C.POINTER(C.c_int32)]),
             "rsd_peak_gemm": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_double, P,
                                         C.POINTER(C.c_double), C.POINTER(C.c_double)]),
             "rsd_release_cache": (None, []),

@@ -143,6 +143,20 @@ void stage_reset(Handle& h) {
     h.stage_off = 0;
 }
 
+void stage_release(Handle& h) {
+    if (h.stream) cudaStreamSynchronize(h.stream);
+    for (auto& blk : h.stage_blocks) pinned_give(blk.first, blk.second);
+    h.stage_blocks.clear();
+    stage_reset(h);
+}
+
+void prof_release(Handle& h) {
+    for (auto& r : h.prof.recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : h.prof.pool) cudaEventDestroy(e);
+    h.prof.recs.clear();
+    h.prof.pool.clear();
+}
+
 static void arena_give(char* p, size_t bytes, int dev) {
     std::lock_guard<std::mutex> lk(g_cache_mu);
     ArenaCache& c = g_cache[dev & 63];
@@ -1493,6 +1507,19 @@ extern "C" int rsd_inject_drop_sweep_item(rsd_handle hh, int32_t level) {
     if (!hh || hh->h.paper || level < 0 || level >= (int)hh->h.levels.size()) return RSD_ERR_ARG;
     hh->h.inject_drop_level = level;
     return RSD_OK;
+}
+
+extern "C" int rsd_autotune(const char* path, double* seconds, void* stream) {
+    if (!path || !seconds) return RSD_ERR_ARG;
+    int dev = 0, sms = 148;
+    RSD_CUDA_TRY(cudaGetDevice(&dev));
+    RSD_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    return gemm_tc_autotune(path, (cudaStream_t)stream, sms, seconds);
+}
+
+extern "C" int rsd_tune_load(const char* path, int32_t* entries) {
+    if (!path || !entries) return RSD_ERR_ARG;
+    return tune_read(path, nullptr, entries);
 }
 
 extern "C" int rsd_check(rsd_handle hh) {

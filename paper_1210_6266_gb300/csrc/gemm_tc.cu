@@ -22,6 +22,9 @@
 
 #include <algorithm>
 #include <array>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
@@ -559,7 +562,14 @@ struct TcBuf {
     size_t cap_tasks = 0, cap_tiles = 0, cap_reds = 0;
 };
 
+// Autotuned launch configurations (rsd_autotune / rsd_options.tune_cache): for an operand
+// format, a launch's output tiles (counted at 128 x 256) and its longest K, the tile width
+// and the split-K count that measured fastest on synthetic operands of that size.
+struct TuneEntry { int op, tiles, k, bn, split; float us, us_rule; };
+
 struct TcState {
+    std::vector<TuneEntry> tune;        // empty: the built-in rules
+    int force_bn = 0, force_split = 0;  // the tuner's candidate under measurement (0: none)
     CUtensorMap* d_maps = nullptr;      // TC_NODE_MAPS per tree node: [L; X] panel, inverted
                                         // diagonal blocks, 16-bit copy; then TC_SCR_MAPS per
                                         // front slot of the widest level
@@ -583,12 +593,58 @@ TcState* state_of(Handle& h) { return (TcState*)h.tc_state; }
 
 }  // namespace
 
+// Nearest tuned bucket (log distance in tiles and K) for the operand format; 0 when the
+// table has none for it.
+static void tune_lookup(const std::vector<TuneEntry>& tab, int op, int tiles, int k, int* bn, int* split) {
+    double best = 1e30;
+    *bn = 0;
+    *split = 0;
+    for (const TuneEntry& e : tab) {
+        if (e.op != op) continue;
+        const double d = std::fabs(std::log2((double)std::max(tiles, 1) / std::max(e.tiles, 1))) +
+                         std::fabs(std::log2((double)std::max(k, 1) / std::max(e.k, 1)));
+        if (d < best) { best = d; *bn = e.bn; *split = e.split; }
+    }
+}
+
+// Read a table written by rsd_autotune: one JSON object per line in its "entries" array.
+// out_table: a std::vector<TuneEntry>* to fill, or null to validate only.
+int tune_read(const char* path, void* out_table, int32_t* entries) {
+    std::vector<TuneEntry>* out = (std::vector<TuneEntry>*)out_table;
+    FILE* fp = std::fopen(path, "r");
+    if (!fp) { set_last_error(std::string("tune cache not readable: ") + path); return RSD_ERR_ARG; }
+    char line[512];
+    std::vector<TuneEntry> tab;
+    bool header = false;
+    while (std::fgets(line, sizeof line, fp)) {
+        if (std::strstr(line, "\"entries\"")) header = true;
+        const char* q = std::strstr(line, "{\"op\":");
+        if (!q) continue;
+        TuneEntry e{};
+        if (std::sscanf(q, "{\"op\": %d, \"tiles\": %d, \"k\": %d, \"bn\": %d, \"split\": %d, \"us\": %f, \"us_rule\": %f}",
+                        &e.op, &e.tiles, &e.k, &e.bn, &e.split, &e.us, &e.us_rule) != 7 ||
+            (e.bn != 128 && e.bn != 256) || e.split < 1 || e.split > 64 || e.tiles < 1 || e.k < 1 ||
+            (e.op != TC_OP_TF32 && e.op != TC_OP_F16)) {
+            std::fclose(fp);
+            set_last_error(std::string("malformed tune cache entry in ") + path);
+            return RSD_ERR_ARG;
+        }
+        tab.push_back(e);
+    }
+    std::fclose(fp);
+    if (!header || tab.empty()) { set_last_error(std::string("tune cache without entries: ") + path); return RSD_ERR_ARG; }
+    if (entries) *entries = (int32_t)tab.size();
+    if (out) *out = std::move(tab);
+    return RSD_OK;
+}
+
 int gemm_tc_prepare(Handle& h) {
     bool any = false;
     for (auto& L : h.levels) any |= tc_level(L) && L.factored;
     if (!any) return RSD_OK;
     auto* st = new TcState();
     h.tc_state = st;
+    if (h.opt.tune_cache) RSD_TRY(tune_read(h.opt.tune_cache, &st->tune, nullptr));
     int widest = 0;
     for (auto& L : h.levels)
         if (tc_level(L) && L.factored) widest = std::max(widest, (int)L.fronts.size());
@@ -815,8 +871,23 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
     const int sms = max_ctas > 0 ? std::min(max_ctas, h.num_sms) : h.num_sms;
     int max_n = 0;
     for (auto& g : tasks) max_n = std::max(max_n, g.N);
-    const int bn = (kind == 2 || kind == 3 || (kind == TC_GENERAL && max_n > 128)) ? 256 : 128;
+    int bn = (kind == 2 || kind == 3 || (kind == TC_GENERAL && max_n > 128)) ? 256 : 128;
     if (op != TC_OP_TF32 && kind != 2 && kind != 3) return RSD_ERR_ARG;     // 16-bit: long-K updates only
+    // tuned configuration of the update kinds (0, 2, 3): the tile width (TF32 outer and
+    // Schur updates; 16-bit operands run the 128 x 256 kernel only) and the split-K count
+    int tuned_split = 0;
+    if ((kind == 0 || kind == 2 || kind == 3) && (st->force_bn || !st->tune.empty())) {
+        int t256 = 0, maxk = 0;
+        for (auto& g : tasks) {
+            const int tm = (g.M + BM - 1) / BM, tn = (g.N + 255) / 256;
+            t256 += g.lower ? tm * (tn + 1) / 2 : tm * tn;
+            maxk = std::max(maxk, g.K);
+        }
+        int tbn = 0;
+        if (st->force_bn) { tbn = st->force_bn; tuned_split = st->force_split; }
+        else tune_lookup(st->tune, op == TC_OP_TF32 ? TC_OP_TF32 : TC_OP_F16, t256, maxk, &tbn, &tuned_split);
+        if (tbn && kind != 0 && op == TC_OP_TF32) bn = tbn;
+    }
     std::vector<TcTask> tt(tasks.size());
     std::vector<std::array<int, 3>> out;            // (task, tm, tn) output tiles
     for (size_t i = 0; i < tasks.size(); ++i) {
@@ -854,7 +925,8 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
     int max_kb = 0;
     for (auto& g : tasks) max_kb = std::max(max_kb, (g.K + bke - 1) / bke);
     int nsplit = 1;
-    if (kind != 1 && kind != TC_GENERAL && (int)out.size() < sms)
+    if (tuned_split > 0) nsplit = std::max(1, std::min(tuned_split, max_kb / 4));
+    else if (kind != 1 && kind != TC_GENERAL && (int)out.size() < sms)
         nsplit = std::max(1, std::min(sms / (int)out.size(), max_kb / SPLIT_MIN_KB));
     if ((int)out.size() * nsplit * (bn / 256 > 0 ? bn / 256 : 1) > st->ws_slots * (256 / bn)) nsplit = 1;
     std::vector<TcTile> tl;
@@ -862,7 +934,7 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
     int slot = 0;
     for (auto& o : out) {
         const int nkb = (tasks[o[0]].K + bke - 1) / bke;
-        const int ns = std::max(1, std::min(nsplit, nkb / SPLIT_MIN_KB));
+        const int ns = std::max(1, std::min(nsplit, nkb / (tuned_split > 0 ? 4 : SPLIT_MIN_KB)));
         if (ns == 1) {
             tl.push_back({o[0], o[1], o[2], 0, nkb, -1, 0, 0});
             continue;
@@ -966,6 +1038,126 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
     }
     prof_end(h, pi, fl, by, stream);
     RSD_CUDA_TRY(cudaGetLastError());
+    return RSD_OK;
+}
+
+// ---- autotuner ------------------------------------------------------------------------
+// For each operand format (TF32; FP16, which BF16 shares) and each bucket of output tiles
+// (1, 4, 16, 64, 256 tiles of 128 x 256) and K (512, 2048, 8192, 24576), time C -= A B^T
+// on synthetic operands (one task, M = 128 tiles, N = 256) with the built-in rules and
+// with every candidate tile width (TF32: 128 or 256; 16-bit operands: 256) and split-K
+// count (1 .. 32 slices of at least 4 K blocks, within the split-K workspace), through the
+// same launcher the factorisation uses (best of 3 launches, CUDA events around the GEMM and
+// its split-K reduction), and write the fastest per bucket to `path`.
+int gemm_tc_autotune(const char* path, cudaStream_t stream, int num_sms, double* secs) {
+    const auto t_start = std::chrono::steady_clock::now();
+    const int Ts[] = {1, 4, 16, 64, 256};
+    const int Ks[] = {512, 2048, 8192, 24576};
+    const int Mmax = 256 * BM, Kmax = 24576, Nn = 256;
+    const size_t a32 = (size_t)Mmax * Kmax * 4, b32 = (size_t)Nn * Kmax * 4, c32 = (size_t)Mmax * Nn * 4;
+    const size_t a16 = a32 / 2, b16 = b32 / 2;
+    const size_t o_b = a32, o_c = o_b + b32, o_a16 = o_c + c32, o_b16 = o_a16 + a16, o_one = o_b16 + b16;
+    const size_t o_err = o_one + (size_t)Mmax * 4, total = o_err + 256;
+    char* buf = nullptr;
+    RSD_CUDA_TRY(cudaMalloc((void**)&buf, total));
+    struct Free { char* p; ~Free() { cudaFree(p); } } fr{buf};
+    float* A = (float*)buf;
+    float* B = (float*)(buf + o_b);
+    float* Cm = (float*)(buf + o_c);
+    k_fill_hash<<<1024, 256, 0, stream>>>(A, (int64_t)Mmax * Kmax, 0x9e3779b9u);
+    k_fill_hash<<<1024, 256, 0, stream>>>(B, (int64_t)Nn * Kmax, 0x7f4a7c15u);
+    k_to16<<<1024, 256, 0, stream>>>(A, (unsigned short*)(buf + o_a16), (int64_t)Mmax * Kmax, 0);
+    k_to16<<<1024, 256, 0, stream>>>(B, (unsigned short*)(buf + o_b16), (int64_t)Nn * Kmax, 0);
+    RSD_CUDA_TRY(cudaMemsetAsync(Cm, 0, c32, stream));
+    RSD_CUDA_TRY(cudaMemsetAsync(buf + o_err, 0, 256, stream));
+    {
+        std::vector<float> one((size_t)Mmax, 1.0f);
+        RSD_CUDA_TRY(cudaMemcpyAsync(buf + o_one, one.data(), sizeof(float) * Mmax, cudaMemcpyHostToDevice, stream));
+        RSD_CUDA_TRY(cudaStreamSynchronize(stream));
+    }
+    // a stand-alone handle around the synthetic operands: node 0 is A, node 1 is B
+    Handle h;
+    h.stream = stream;
+    h.num_sms = num_sms;
+    h.prof.on = true;
+    h.d_err = (int*)(buf + o_err);
+    auto* st = new TcState();
+    h.tc_state = st;
+    struct Release { Handle& h; ~Release() { gemm_tc_release(h); stage_release(h); prof_release(h); } } rel{h};
+    std::vector<CUtensorMap> maps(2 * TC_NODE_MAPS);
+    std::memset(maps.data(), 0, maps.size() * sizeof(CUtensorMap));
+    RSD_TRY(encode_2d(&maps[tc_map_panel(0)], A, Kmax, Mmax, Kmax));
+    RSD_TRY(encode_2d(&maps[tc_map_panel16(0)], buf + o_a16, Kmax, Mmax, Kmax, TC_OP_F16));
+    RSD_TRY(encode_2d(&maps[tc_map_panel(1)], B, Kmax, Nn, Kmax));
+    RSD_TRY(encode_2d(&maps[tc_map_panel16(1)], buf + o_b16, Kmax, Nn, Kmax, TC_OP_F16));
+    RSD_CUDA_TRY(cudaMalloc((void**)&st->d_maps, maps.size() * sizeof(CUtensorMap)));
+    RSD_CUDA_TRY(cudaMemcpy(st->d_maps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
+    st->ws_slots = 2 * num_sms;
+    for (auto& b : st->buf) RSD_CUDA_TRY(cudaMalloc((void**)&b.d_ws, (size_t)st->ws_slots * BM * 256 * sizeof(float)));
+    auto time_one = [&](const GemmTask& t, int op, float* best) -> int {
+        *best = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            h.prof.recs.clear();
+            RSD_TRY(gemm_tc_launch(h, 0, std::vector<GemmTask>{t}, 3, stream, 0, 0, op));
+            RSD_CUDA_TRY(cudaStreamSynchronize(stream));
+            float ms = 0;
+            const Prof::Rec& r = h.prof.recs.back();
+            RSD_CUDA_TRY(cudaEventElapsedTime(&ms, r.a, r.b));
+            for (auto e : {r.a, r.b}) h.prof.pool.push_back(e);
+            *best = std::min(*best, ms * 1000.0f);
+        }
+        return RSD_OK;
+    };
+    std::vector<TuneEntry> tab;
+    for (int op : {TC_OP_TF32, TC_OP_F16}) {
+        const int bke = op == TC_OP_TF32 ? BK : 64;
+        for (int T : Ts)
+            for (int K : Ks) {
+                GemmTask t{};
+                t.M = T * BM; t.N = Nn; t.K = K;
+                t.C = Cm; t.ldc = Nn;
+                t.lower = 0; t.beta = 1;
+                t.map_a = 0; t.map_b = 1;
+                t.sa = (const float*)(buf + o_one);
+                t.sb = t.sa;
+                st->force_bn = 0;
+                float rule = 0;
+                RSD_TRY(time_one(t, op, &rule));
+                TuneEntry best{op, T, K, 256, 1, 1e30f, rule};
+                for (int bn : {256, 128}) {
+                    if (op != TC_OP_TF32 && bn != 256) continue;
+                    for (int sp : {1, 2, 4, 8, 16, 32}) {
+                        if (sp > 1 && sp > K / bke / 4) continue;
+                        if (T * (bn == 128 ? 2 : 1) * sp > st->ws_slots * (256 / bn)) continue;
+                        st->force_bn = bn;
+                        st->force_split = sp;
+                        float us = 0;
+                        RSD_TRY(time_one(t, op, &us));
+                        if (us < best.us) { best.us = us; best.bn = bn; best.split = sp; }
+                    }
+                }
+                st->force_bn = 0;
+                tab.push_back(best);
+            }
+    }
+    int errs[ERR_SLOTS];
+    RSD_CUDA_TRY(cudaMemcpy(errs, h.d_err, sizeof(errs), cudaMemcpyDeviceToHost));
+    if (errs[ERR_TIMEOUT]) return RSD_ERR_TIMEOUT;
+    FILE* fp = std::fopen(path, "w");
+    if (!fp) { set_last_error(std::string("cannot write tune cache ") + path); return RSD_ERR_ARG; }
+    cudaDeviceProp prop{};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaGetDeviceProperties(&prop, dev);
+    std::fprintf(fp, "{\"device\": \"%s\", \"sms\": %d, \"entries\": [\n", prop.name, num_sms);
+    for (size_t i = 0; i < tab.size(); ++i) {
+        const TuneEntry& e = tab[i];
+        std::fprintf(fp, "  {\"op\": %d, \"tiles\": %d, \"k\": %d, \"bn\": %d, \"split\": %d, \"us\": %.2f, \"us_rule\": %.2f}%s\n",
+                     e.op, e.tiles, e.k, e.bn, e.split, e.us, e.us_rule, i + 1 < tab.size() ? "," : "");
+    }
+    std::fprintf(fp, "]}\n");
+    std::fclose(fp);
+    *secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     return RSD_OK;
 }
 

@@ -270,6 +270,9 @@ struct Handle {
 // the device); stage_reset() rewinds it once every staged copy is known to be done.
 const void* stage_host(Handle& h, const void* src, size_t bytes);
 void stage_reset(Handle& h);
+// give the handle's staging blocks back to the pool / destroy its profiling events
+void stage_release(Handle& h);
+void prof_release(Handle& h);
 
 // Profile helpers: prof_begin records the start event (if profiling) and returns a
 // record index; prof_end records the stop event and the launch's algorithmic work.
@@ -334,6 +337,8 @@ int paper_extend_add(Handle& h);
 int gemm_tc_peak(int n, int reps, double seconds, cudaStream_t stream, int num_sms, double* best, double* sustained,
                  int op);
 int gemm_simt_peak(int prec, int n, int reps, double seconds, cudaStream_t st, double* best, double* sustained);
+int gemm_tc_autotune(const char* path, cudaStream_t stream, int num_sms, double* secs);
+int tune_read(const char* path, void* out_table, int32_t* entries);
 int run_apply_paper(Handle& h, const double* r, double* z);
 int gamma_interface_solve(Handle& h, int li, double* z);
 int fgmres(Handle& h, const double* f, double* u, double tol, rsd_stats* st);

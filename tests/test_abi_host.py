@@ -103,3 +103,24 @@ def test_null_arguments(lib):
     assert so.rsd_solve(None, None, None, 1e-8, None) == lib.RSD_ERR_ARG
     assert so.rsd_check(None) == lib.RSD_ERR_ARG
     so.rsd_destroy(None)
+
+
+def test_tune_cache_reader_accepts_autotune_format_and_rejects_malformed(tmp_path):
+    """rsd_tune_load parses the table rsd_autotune writes (host only, no GPU)."""
+    from paper_1210_6266_gb300 import _lib
+    import ctypes as C
+    lib = _lib.load()
+    good = tmp_path / "tune.json"
+    good.write_text('{"device": "x", "sms": 152, "entries": [\n'
+                    '  {"op": 0, "tiles": 1, "k": 512, "bn": 256, "split": 4, "us": 10.00, "us_rule": 12.00},\n'
+                    '  {"op": 1, "tiles": 64, "k": 8192, "bn": 256, "split": 1, "us": 99.50, "us_rule": 99.50}\n'
+                    ']}\n')
+    n = C.c_int32()
+    assert lib.rsd_tune_load(str(good).encode(), C.byref(n)) == 0 and n.value == 2
+    for text in ('{"entries": [\n  {"op": 0, "tiles": 1, "k": 512, "bn": 64, "split": 1, "us": 1.0, "us_rule": 1.0}\n]}\n',
+                 '{"entries": [\n]}\n',
+                 '{"entries": [\n  {"op": 0, "tiles": 1}\n]}\n'):
+        bad = tmp_path / "bad.json"
+        bad.write_text(text)
+        assert lib.rsd_tune_load(str(bad).encode(), C.byref(n)) == _lib.RSD_ERR_ARG
+    assert lib.rsd_tune_load(str(tmp_path / "missing.json").encode(), C.byref(n)) == _lib.RSD_ERR_ARG
