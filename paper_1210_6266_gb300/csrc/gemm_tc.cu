@@ -496,22 +496,38 @@ k_gemm_tc_persist(const TcTask* __restrict__ tasks, const TcTile* __restrict__ t
     }
 }
 
-// Split-K reduction: C = beta*C + alpha * sum_s partial_s, summed in slot order.
+// Split-K reduction: C = beta*C + alpha * sum_s partial_s, summed in slot order.  A CTA
+// takes RED_ROWS rows of one output tile (blockIdx.y), a thread the same column of
+// RED_ROWS * BN / 256 of those rows: all of its partial-product loads are issued before
+// its reads and writes of C.
+constexpr int RED_ROWS = 8;
 template <int BN>
 __global__ void __launch_bounds__(256) k_splitk_reduce(const TcTask* __restrict__ tasks, const TcRed* __restrict__ reds,
                                                        const float* __restrict__ ws) {
+    constexpr int PER = RED_ROWS * BN / 256;          // elements per thread
+    constexpr int RSTEP = 256 / BN;                    // rows between a thread's elements
     const TcRed rd = reds[blockIdx.x];
     const TcTask tk = tasks[rd.task];
     const int m0 = rd.tm * BM, n0 = rd.tn * BN;
-    for (int e = threadIdx.x; e < BM * BN; e += blockDim.x) {
-        const int row = e / BN, col = e % BN;
-        const int gr = m0 + row, gc = n0 + col;
+    const int col = threadIdx.x % BN;
+    const int rbase = blockIdx.y * RED_ROWS + threadIdx.x / BN;
+    float v[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) v[q] = 0.f;
+    for (int sp = 0; sp < rd.nsplit; ++sp) {
+        const float* w = ws + (int64_t)(rd.slot0 + sp) * BM * BN;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) v[q] += w[(int64_t)(rbase + RSTEP * q) * BN + col];
+    }
+    const int gc = n0 + col;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int gr = m0 + rbase + RSTEP * q;
         if (gr >= tk.M || gc >= tk.N || (tk.lower && gc > gr)) continue;
-        float v = 0.f;
-        for (int sp = 0; sp < rd.nsplit; ++sp) v += ws[((int64_t)(rd.slot0 + sp) * BM + row) * BN + col];
-        if (tk.sa) v *= tk.sa[gr] * tk.sb[gc];           // 16-bit operands: undo the row scales
+        float x = v[q];
+        if (tk.sa) x *= tk.sa[gr] * tk.sb[gc];        // 16-bit operands: undo the row scales
         float* p = tk.C + (int64_t)gr * tk.ldc + gc;
-        const float o = (tk.beta ? *p : 0.f) + tk.alpha * v;
+        const float o = (tk.beta ? *p : 0.f) + tk.alpha * x;
         *p = tk.round_tf32 ? tf32_rn(o) : o;
     }
 }
@@ -1032,8 +1048,9 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
     }
     count_launch();
     if (!rd.empty()) {
-        if (bn == 128) k_splitk_reduce<128><<<(unsigned)rd.size(), 256, 0, stream>>>(d_tasks, d_reds, bf.d_ws);
-        else k_splitk_reduce<256><<<(unsigned)rd.size(), 256, 0, stream>>>(d_tasks, d_reds, bf.d_ws);
+        const dim3 rg((unsigned)rd.size(), BM / RED_ROWS);
+        if (bn == 128) k_splitk_reduce<128><<<rg, 256, 0, stream>>>(d_tasks, d_reds, bf.d_ws);
+        else k_splitk_reduce<256><<<rg, 256, 0, stream>>>(d_tasks, d_reds, bf.d_ws);
         count_launch();
     }
     prof_end(h, pi, fl, by, stream);
@@ -1101,9 +1118,10 @@ int gemm_tc_autotune(const char* path, cudaStream_t stream, int num_sms, double*
             RSD_TRY(gemm_tc_launch(h, 0, std::vector<GemmTask>{t}, 3, stream, 0, 0, op));
             RSD_CUDA_TRY(cudaStreamSynchronize(stream));
             float ms = 0;
-            const Prof::Rec& r = h.prof.recs.back();
-            RSD_CUDA_TRY(cudaEventElapsedTime(&ms, r.a, r.b));
+            const Prof::Rec r = h.prof.recs.back();
+            h.prof.recs.clear();                    // its events go back to the pool, once
             for (auto e : {r.a, r.b}) h.prof.pool.push_back(e);
+            RSD_CUDA_TRY(cudaEventElapsedTime(&ms, r.a, r.b));
             *best = std::min(*best, ms * 1000.0f);
         }
         return RSD_OK;
