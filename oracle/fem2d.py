@@ -93,3 +93,70 @@ def binary_owner(N: int, P: int, coords: np.ndarray) -> np.ndarray:
         lo = np.where(go & right, mid, lo)
         hi = np.where(go & ~right, mid, hi)
     return owner
+
+
+def reference_mass_2d() -> np.ndarray:
+    """4x4 int_{[0,1]^2} phi_a phi_b (consistent bilinear mass), 2x2 Gauss."""
+    M = np.zeros((4, 4))
+    for gx in GAUSS2:
+        for gy in GAUSS2:
+            phi = np.array([(gx if a & 1 else 1 - gx) * (gy if (a >> 1) & 1 else 1 - gy) for a in range(4)])
+            M += 0.25 * np.outer(phi, phi)
+    return M
+
+
+def reference_stiffness_aniso(ax: float, ay: float) -> np.ndarray:
+    """4x4 int_{[0,1]^2} ax phi_a,x phi_b,x + ay phi_a,y phi_b,y, 2x2 Gauss (size-free in 2-D)."""
+    K = np.zeros((4, 4))
+    for gx in GAUSS2:
+        for gy in GAUSS2:
+            G = []
+            for a in range(4):
+                bx, by = a & 1, (a >> 1) & 1
+                lx = gx if bx else 1 - gx
+                ly = gy if by else 1 - gy
+                G.append([(1 if bx else -1) * ly, lx * (1 if by else -1)])
+            G = np.array(G)
+            K += 0.25 * (ax * np.outer(G[:, 0], G[:, 0]) + ay * np.outer(G[:, 1], G[:, 1]))
+    return K
+
+
+def strip_system(N: int, P: int, c: float) -> tuple[sp.csr_matrix, np.ndarray]:
+    """The paper's two-variable systems (Sec. 4, Eqs. 4.2 and 4.3) on the strip:
+        -u_xx/100 - u_yy + c v = f,   -c u - v_xx - v_yy/100 = g,
+    c = 1/100 (Eq. 4.2) or 100 (Eq. 4.3).  Bilinear elements; every true sub-domain is a
+    unit square of N x N nodes, so h = 1/(N-1): the stiffness of a square element does not
+    depend on h in 2-D, the consistent mass scales with h^2.  DOF 2 * node + component
+    (u = 0, v = 1), node ids as in strip_poisson; homogeneous Dirichlet on both variables.
+    The zero-order coupling is skew (+c M, -c M), so K is nonsymmetric with the symmetric
+    part blockdiag(K_u, K_v), which is positive definite."""
+    X, Y = P * (N - 1), N - 1
+    nx, ny = X - 1, Y - 1
+    h = 1.0 / (N - 1)
+    Ku = reference_stiffness_aniso(0.01, 1.0)
+    Kv = reference_stiffness_aniso(1.0, 0.01)
+    M = h * h * reference_mass_2d()
+    ex, ey = np.meshgrid(np.arange(X), np.arange(Y), indexing="ij")
+    ex, ey = ex.ravel(), ey.ravel()
+    rows, cols, vals = [], [], []
+    blocks = ((0, 0, Ku), (1, 1, Kv), (0, 1, c * M), (1, 0, -c * M))
+    for a in range(4):
+        xa, ya = ex + (a & 1), ey + ((a >> 1) & 1)
+        ia = (xa >= 1) & (xa <= nx) & (ya >= 1) & (ya <= ny)
+        for b in range(4):
+            xb, yb = ex + (b & 1), ey + ((b >> 1) & 1)
+            ib = (xb >= 1) & (xb <= nx) & (yb >= 1) & (yb <= ny)
+            k = ia & ib
+            na = (xa[k] - 1) + nx * (ya[k] - 1)
+            nb = (xb[k] - 1) + nx * (yb[k] - 1)
+            for ca, cb, E in blocks:
+                rows.append(2 * na + ca)
+                cols.append(2 * nb + cb)
+                vals.append(np.full(k.sum(), E[a, b]))
+    n = 2 * nx * ny
+    A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n)).tocsr()
+    A.sum_duplicates()
+    A.sort_indices()
+    ids = np.arange(nx * ny)
+    coords = np.stack([ids % nx + 1, ids // nx + 1], axis=1)
+    return A, coords

@@ -20,7 +20,8 @@ the subtree of t):
     U_t        = F_t[B, B] - X_t X_t^T             (what t contributes to ancestors)
 Apply z = K^-1 r: the forward pass computes g of Eq. 3.2 level by level
 (y_t = L_t^-1 (r_I + children's contributions), contribution_t = (...)_B - X_t y_t);
-the backward pass is Eq. 3.3 (x_I = L_t^-T (y_t - X_t^T x_B)).
+the backward pass is Eq. 3.3 (x_I = L_t^-T (y_t - X_t^T x_B)).  ExactFactorLU is the
+same recursion for a nonsymmetric K (LU without pivoting per front).
 """
 from __future__ import annotations
 
@@ -113,3 +114,89 @@ def subtree(sym: Symbolic, t: int) -> list[int]:
 def dense_solve(A: sp.csr_matrix, b: np.ndarray) -> np.ndarray:
     """Reference solve by dense partial-pivot LU (LAPACK gesv); n up to ~20k."""
     return np.linalg.solve(A.toarray(), b)
+
+
+def lu_nopivot(F: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Doolittle LU without row exchanges, F = L U with L unit lower, U upper (column by
+    column elimination as in Sec. 3's Gaussian elimination of a sub-domain block).
+    Raises ZeroDivisionError on an exactly zero pivot."""
+    n = F.shape[0]
+    A = F.astype(np.float64).copy()
+    for k in range(n):
+        if A[k, k] == 0.0:
+            raise ZeroDivisionError(f"zero pivot at {k}")
+        A[k + 1:, k] /= A[k, k]
+        A[k + 1:, k + 1:] -= np.outer(A[k + 1:, k], A[k, k + 1:])
+    L = np.tril(A, -1) + np.eye(n)
+    U = np.triu(A)
+    return L, U
+
+
+class ExactFactorLU:
+    """The exact recursion for a nonsymmetric K with a structurally symmetric pattern
+    (the two-variable systems of Sec. 4, Eqs. 4.2-4.3).  Per tree node t (postorder):
+        F_t        = K[I u B, I u B] entries owned by t + sum_c U_c at ea[c]
+        F_t[I, I]  = L_t U_t                        (no pivoting)
+        X_t        = F_t[B, I] U_t^-1,  Y_t = L_t^-1 F_t[I, B]
+        U_t'       = F_t[B, B] - X_t Y_t            (t's contribution to its ancestors)
+    apply: forward y_t = L_t^-1 (r_I + children), contribution v_B - X_t y_t; backward
+    x_I = U_t^-1 (y_t - Y_t x_B) (Eqs. 3.2-3.3 with the two off-diagonal blocks distinct)."""
+
+    def __init__(self, A: sp.csr_matrix, sym: Symbolic):
+        self.sym = sym
+        n_nodes = sym.n_nodes
+        self.L: list = [None] * n_nodes
+        self.Uf: list = [None] * n_nodes
+        self.X: list = [None] * n_nodes
+        self.Y: list = [None] * n_nodes
+        self.S: list = [None] * n_nodes
+        self.U: list = [None] * n_nodes
+        A = A.tocsr()
+        for t in sym.post:
+            I, Bt = sym.I[t], sym.B[t]
+            s, b = len(I), len(Bt)
+            F = np.zeros((s + b, s + b))
+            front = sym.front[t]
+            if s:
+                F[:s, :] = A[I][:, front].toarray()           # K[I, I u B]
+                F[s:, :s] = A[Bt][:, I].toarray()            # K[B, I]
+            for c in sym.children[t]:
+                pos = sym.ea[c]
+                F[np.ix_(pos, pos)] += self.U[c]
+                self.U[c] = None
+            self.S[t] = F[:s, :s].copy()
+            L, U = lu_nopivot(F[:s, :s]) if s else (np.zeros((0, 0)), np.zeros((0, 0)))
+            X = sla.solve_triangular(U, F[s:, :s].T, lower=False, trans="T").T if s and b else np.zeros((b, s))
+            Y = sla.solve_triangular(L, F[:s, s:], lower=True, unit_diagonal=True) if s and b else np.zeros((s, b))
+            self.L[t], self.Uf[t], self.X[t], self.Y[t] = L, U, X, Y
+            self.U[t] = F[s:, s:] - X @ Y
+
+    def apply(self, r: np.ndarray) -> np.ndarray:
+        sym = self.sym
+        y: list = [None] * sym.n_nodes
+        contrib: list = [None] * sym.n_nodes
+        for t in sym.post:
+            s, b = sym.s(t), sym.b(t)
+            v = np.zeros(s + b)
+            v[:s] = r[sym.I[t]]
+            for c in sym.children[t]:
+                np.add.at(v, sym.ea[c], contrib[c])
+            y[t] = sla.solve_triangular(self.L[t], v[:s], lower=True, unit_diagonal=True) if s else v[:0]
+            contrib[t] = v[s:] - self.X[t] @ y[t]
+        z = np.zeros_like(r, dtype=np.float64)
+        for t in reversed(sym.post):
+            if not sym.s(t):
+                continue
+            z[sym.I[t]] = sla.solve_triangular(self.Uf[t], y[t] - self.Y[t] @ z[sym.B[t]], lower=False)
+        return z
+
+
+def schur_direct_general(A: sp.csr_matrix, sym: Symbolic, t: int) -> np.ndarray:
+    """Eq. 3.2 for a nonsymmetric K: S = K_II - sum_c K_{I,V_c} K_{V_c V_c}^-1 K_{V_c,I}."""
+    A = A.tocsc()
+    I = sym.I[t]
+    S = A[I][:, I].toarray()
+    for c in sym.children[t]:
+        V = np.sort(np.concatenate([sym.I[d] for d in subtree(sym, c)]))
+        S -= A[I][:, V].toarray() @ spla.splu(A[V][:, V].tocsc()).solve(A[V][:, I].toarray())
+    return S

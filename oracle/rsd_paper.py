@@ -37,6 +37,7 @@ class PaperRSD:
         # V-hat_t and the couplings K_{I_t, l}
         self.vhat: dict[int, list[int]] = {}
         self.K_Il: dict[tuple[int, int], sp.csr_matrix] = {}
+        self.K_lI: dict[tuple[int, int], sp.csr_matrix] = {}
         for t in range(sym.n_nodes):
             if not sym.children[t]:
                 continue
@@ -48,6 +49,7 @@ class PaperRSD:
                     if blk.nnz:
                         hits.append(l)
                         self.K_Il[(t, l)] = blk.tocsr()
+                        self.K_lI[(t, l)] = self.A[sym.I[l]][:, I].tocsr()   # K_lI (K may be nonsymmetric)
             self.vhat[t] = hits
         self.S_dense: dict[int, np.ndarray] = {}
         if gamma == 0:
@@ -66,17 +68,15 @@ class PaperRSD:
         I = self.sym.I[t]
         y = self.A[I][:, I] @ x
         for l in self.vhat[t]:
-            K_Il = self.K_Il[(t, l)]
-            w = self.leaf_lu[l].solve(K_Il.T @ x)
-            y -= K_Il @ w
+            w = self.leaf_lu[l].solve(self.K_lI[(t, l)] @ x)
+            y -= self.K_Il[(t, l)] @ w
         return y
 
     def s_tilde(self, t: int) -> np.ndarray:
         I = self.sym.I[t]
         S = self.A[I][:, I].toarray()
         for l in self.vhat[t]:
-            K_Il = self.K_Il[(t, l)].toarray()
-            S -= K_Il @ self.leaf_lu[l].solve(K_Il.T.copy())
+            S -= self.K_Il[(t, l)].toarray() @ self.leaf_lu[l].solve(self.K_lI[(t, l)].toarray())
         return S
 
     def _interface_solve(self, t: int, g: np.ndarray) -> np.ndarray:
@@ -108,7 +108,7 @@ class PaperRSD:
         uI = self._interface_solve(t, g)
         u[I] = uI
         for l in self.vhat[t]:
-            u[sym.I[l]] -= self.leaf_lu[l].solve(self.K_Il[(t, l)].T @ uI)
+            u[sym.I[l]] -= self.leaf_lu[l].solve(self.K_lI[(t, l)] @ uI)
 
     # the same computation flattened into level-wise sweeps (bottom-up)
     def apply_levelwise(self, f: np.ndarray) -> np.ndarray:
