@@ -130,6 +130,13 @@ typedef struct {
     const char* tune_cache; /* path of a table written by rsd_autotune (host string, read at
                             setup): the tile width and split-K count of the tensor-core
                             updates by size bucket; NULL = built-in rules                  */
+    int32_t nonsymmetric;/* nonzero: K is not symmetric (its sparsity pattern must be): every
+                            front is factored F_II = L U without pivoting (Eqs. 3.2-3.3 with
+                            K_IL != K_LI^T, as the two-variable systems of Sec. 4, Eqs.
+                            4.2-4.3, need), X = F_BI U^-1, Y = L^-1 F_IB, U_t = F_BB - X Y;
+                            FP64 or FP32 on CUDA cores; rsd_solve runs FGMRES; exact mode, or
+                            paper mode with gamma > 0.  A zero or non-finite pivot is
+                            reported as RSD_ERR_NOT_SPD.                                    */
 } rsd_options;
 
 typedef struct {
@@ -262,7 +269,8 @@ int rsd_solve(rsd_handle h, const double* f, double* u, double tol, rsd_stats* s
  * u = K^-1 f (dL/df = lam, dL/dK = -lam u^T).  The paper has no counterpart: it is the
  * standard adjoint method applied to the solve above.  The hierarchy only holds
  * symmetric K (its fronts are Cholesky-factored), so K^T = K and the call runs the same
- * preconditioned CG on the same fronts, with no second setup.
+ * preconditioned CG on the same fronts, with no second setup.  RSD_ERR_ARG for a
+ * nonsymmetric hierarchy.
  *   g, lam : device, n FP64 entries.  st : host, may be NULL.  Errors as rsd_solve.     */
 int rsd_solve_adjoint(rsd_handle h, const double* g, double* lam, double tol, rsd_stats* st);
 
@@ -303,6 +311,10 @@ int rsd_front_map(rsd_handle h, int32_t node, int32_t* out);
  * the Cholesky factor of the interface Schur complement (lower triangle, zeros above);
  * rows s..s+b-1 hold X_t = K~_BI L_t^-T, the coupling to the ancestors.              */
 int rsd_front_factor(rsd_handle h, int32_t node, double* out);
+/* nonsymmetric fronts only: [U_t^T; Y_t^T] in the same (s + b) x s layout (rows 0..s-1 the
+ * transposed upper factor, lower triangle; rows s.. Y_t^T = (L_t^-1 F_IB)^T); rsd_front_factor
+ * returns [L_t; X_t] with the unit diagonal of L_t.  RSD_ERR_ARG for a symmetric hierarchy. */
+int rsd_front_factor_upper(rsd_handle h, int32_t node, double* out);
 /* FP16 copy of that factor which the substitution sweeps of a TF32 level read, unscaled
  * to FP64 in the same (s + b) x s layout: the entries below the NB x NB diagonal blocks
  * of L_t and all of X_t (Eq. 3.2 and 3.3 use L_t through its inverted diagonal blocks

@@ -163,7 +163,7 @@ class RSD:
               prec_mid: int = RSD_PREC_TF32, prec_root: int = RSD_PREC_FP64,
               maxit: int = 200, profile: bool = False, mode: int = RSD_MODE_EXACT,
               wait_cycles: int = 0, gamma: int = 0, krylov: int = 0, restart: int = 0,
-              tune_cache: str | None = None) -> "RSD":
+              tune_cache: str | None = None, nonsymmetric: bool = False) -> "RSD":
         lib = _lib.load()
         dev = rowptr.is_cuda
         if not (col.is_cuda == dev and val.is_cuda == dev and dof_node.is_cuda == dev):
@@ -179,7 +179,8 @@ class RSD:
         tree = _lib.rsd_tree(len(par), par.ctypes.data)
         opt = _lib.rsd_options(mode, prec_leaf, prec_mid, prec_root, maxit,
                                _stream() if torch.cuda.is_available() else 0, int(profile), wait_cycles,
-                               gamma, krylov, restart, tune_cache.encode() if tune_cache else None)
+                               gamma, krylov, restart, tune_cache.encode() if tune_cache else None,
+                               int(nonsymmetric))
         out = C.c_void_p()
         rc = lib.rsd_setup(C.byref(csr), _ptr(dof_node), C.byref(tree), C.byref(opt), C.byref(out))
         if rc != 0:
@@ -312,6 +313,13 @@ class RSD:
         s, b, _ = self.front_dims(node)
         out = np.empty((s + b) * max(s, 1), dtype=np.float64)
         check(_lib.load().rsd_front_factor(self._h, node, out.ctypes.data), "rsd_front_factor")
+        return out[: (s + b) * s].reshape(s + b, s)
+
+    def front_factor_upper(self, node: int) -> np.ndarray:
+        """Nonsymmetric fronts: [U^T; Y^T] (rsd_front_factor_upper)."""
+        s, b, _ = self.front_dims(node)
+        out = np.empty((s + b) * max(s, 1), dtype=np.float64)
+        check(_lib.load().rsd_front_factor_upper(self._h, node, out.ctypes.data), "rsd_front_factor_upper")
         return out[: (s + b) * s].reshape(s + b, s)
 
     def front_factor16(self, node: int) -> np.ndarray:

@@ -45,6 +45,7 @@ EXPORTS = [
     "rsd_grid_coef_grad", "rsd_profile_trace", "rsd_peak_gemm",
     "rsd_inject_drop_sweep_item", "rsd_grid_elastic_sizes", "rsd_grid_elastic_assemble",
     "rsd_grid_elastic_load", "rsd_grid_elastic_partition", "rsd_autotune", "rsd_tune_load",
+    "rsd_front_factor_upper",
 ]
 
 
@@ -61,7 +62,8 @@ class rsd_options(C.Structure):
     _fields_ = [("mode", C.c_int32), ("prec_leaf", C.c_int32), ("prec_mid", C.c_int32),
                 ("prec_root", C.c_int32), ("maxit", C.c_int32), ("stream", C.c_void_p),
                 ("profile", C.c_int32), ("wait_cycles", C.c_int64), ("gamma", C.c_int32),
-                ("krylov", C.c_int32), ("restart", C.c_int32), ("tune_cache", C.c_char_p)]
+                ("krylov", C.c_int32), ("restart", C.c_int32), ("tune_cache", C.c_char_p),
+                ("nonsymmetric", C.c_int32)]
 
 
 class rsd_stats(C.Structure):
@@ -120,6 +122,7 @@ def load() -> C.CDLL:
             "rsd_front_map": (C.c_int, [P, C.c_int32, P]),
             "rsd_front_factor": (C.c_int, [P, C.c_int32, P]),
             "rsd_front_factor16": (C.c_int, [P, C.c_int32, P]),
+            "rsd_front_factor_upper": (C.c_int, [P, C.c_int32, P]),
             "rsd_grid_sizes": (C.c_int, [C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
             "rsd_grid_assemble": (C.c_int, [C.c_int32, P, P, P, P, P]),
             "rsd_grid_load": (C.c_int, [C.c_int32, P, P, P]),

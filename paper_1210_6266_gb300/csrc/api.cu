@@ -775,7 +775,8 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
     // paper mode with gamma inner GMRES iterations: only the leaf fronts are stored
     const bool gmode = paper && h.opt.gamma > 0;
     h.gamma = gmode ? h.opt.gamma : 0;
-    h.krylov = h.opt.krylov == RSD_KRYLOV_AUTO ? (gmode ? RSD_KRYLOV_FGMRES : RSD_KRYLOV_PCG) : h.opt.krylov;
+    h.lu = h.opt.nonsymmetric != 0;
+    h.krylov = h.opt.krylov == RSD_KRYLOV_AUTO ? ((gmode || h.lu) ? RSD_KRYLOV_FGMRES : RSD_KRYLOV_PCG) : h.opt.krylov;
     h.restart = h.opt.restart > 0 ? h.opt.restart : 30;
     // paper mode keeps only the interface block of internal fronts (V-hat truncation);
     // leaves keep their coupling block, which yields the updates scattered into S~
@@ -818,7 +819,7 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
     const size_t o_B = take(sizeof(int) * std::max<size_t>(1, h.B_dofs.size()));
     const size_t o_ea = take(sizeof(int) * std::max<size_t>(1, ea_all.size()));
     const size_t o_flags = take(sizeof(int) * 2 * a.n_nodes);
-    struct FrontPlan { size_t P, U, D, V, H, R; };
+    struct FrontPlan { size_t P, U, D, V, H, R, PU, DU; };
     std::vector<FrontPlan> fp(a.n_nodes);
     std::vector<size_t> lvlP(nl), lvlU(nl);
     h.factor_elems = 0; h.factor_bytes = 0; h.setup_flops = 0;
@@ -838,6 +839,16 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
             h.factor_bytes += ((int64_t)s * (s + 1) / 2 + (int64_t)s * b) * (int64_t)es;
             h.setup_flops += (double)s * s * s / 3.0 + (double)s * s * b + (double)s * b * b;
         }
+        if (h.lu)                                    // [U^T; Y^T] panels right after the P panels
+            for (int t : L.nodes) {
+                const int s = a.I_off[t + 1] - a.I_off[t], b = beff(t);
+                const int ldp = std::max(32, round_up(s, 32));
+                fp[t].PU = take((size_t)(s + b) * ldp * es);
+                if (!L.factored) continue;
+                h.factor_elems += (int64_t)s * (s - 1) / 2 + (int64_t)s * b;
+                h.factor_bytes += ((int64_t)s * (s - 1) / 2 + (int64_t)s * b) * (int64_t)es;
+                h.setup_flops += (double)s * s * s / 3.0 + (double)s * s * b;
+            }
         L.bytes_P = off - lvlP[d];
         lvlU[d] = off;
         for (int t : L.nodes) {
@@ -850,6 +861,7 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
             const int s = a.I_off[t + 1] - a.I_off[t], b = beff(t);
             const int nd = (s + NB - 1) / NB;
             fp[t].D = take((size_t)(L.factored ? std::max(1, nd) : 0) * NB * NB * es);
+            if (h.lu) fp[t].DU = take((size_t)(L.factored ? std::max(1, nd) : 0) * NB * NB * es);
             fp[t].V = take((size_t)(s + b + 32) * es);
         }
         if (copy16_level(L))                         // 16-bit factor copies after the level's other regions
@@ -862,6 +874,8 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
     }
     const size_t o_fronts = take(sizeof(FrontDesc) * a.n_nodes);
     const size_t o_sfronts = take(sizeof(FrontDesc) * a.n_nodes);
+    const size_t o_bfronts = h.lu ? take(sizeof(FrontDesc) * a.n_nodes) : 0;          // backward sweeps
+    const size_t o_bsolve = h.lu && paper ? take(sizeof(FrontDesc) * a.n_nodes) : 0;   // backward leaf solves
     size_t n_items = 16;
     for (int t = 0; t < a.n_nodes; ++t) {
         const size_t s = a.I_off[t + 1] - a.I_off[t], b = beff(t);
@@ -1065,6 +1079,8 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
             f.nd = (f.s + NB - 1) / NB;
             f.parent_slot = a.parent[t] >= 0 ? h.node_slot[a.parent[t]] : -1;
             f.P = A + fp[t].P;
+            f.PU = h.lu ? A + fp[t].PU : nullptr;
+            f.DinvU = h.lu ? A + fp[t].DU : nullptr;
             f.U = A + fp[t].U;
             f.Dinv = A + fp[t].D;
             f.vec = A + fp[t].V;
@@ -1125,6 +1141,23 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
         Level& L = h.levels[d];
         RSD_CUDA_TRY(cudaMemcpyAsync(L.d_fronts, stage_host(h, L.fronts.data(), sizeof(FrontDesc) * L.fronts.size()), sizeof(FrontDesc) * L.fronts.size(), cudaMemcpyHostToDevice, st));
     }
+    if (h.lu) {
+        // the backward sweeps read [U^T; Y^T] with (U_kk^T)^-1: the same descriptors with
+        // P and Dinv exchanged for PU and DinvU
+        FrontDesc* d_b = (FrontDesc*)(A + o_bfronts);
+        std::vector<FrontDesc> bw;
+        for (int d = 0; d < nl; ++d) {
+            Level& L = h.levels[d];
+            L.d_fronts_bwd = d_b + bw.size();
+            for (FrontDesc g : L.fronts) {
+                g.P = g.PU;
+                g.Dinv = g.DinvU;
+                bw.push_back(g);
+            }
+        }
+        RSD_CUDA_TRY(cudaMemcpyAsync(d_b, stage_host(h, bw.data(), sizeof(FrontDesc) * bw.size()), sizeof(FrontDesc) * bw.size(),
+                                     cudaMemcpyHostToDevice, st));
+    }
     if (!items_all.empty())
         RSD_CUDA_TRY(cudaMemcpyAsync(d_items, stage_host(h, items_all.data(), sizeof(int) * items_all.size()), sizeof(int) * items_all.size(), cudaMemcpyHostToDevice, st));
     if (!child_tab.empty())
@@ -1142,11 +1175,13 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
         h.d_ticket_paper = (int*)(A + o_tpaper);
         std::vector<NodeRef> refs(a.n_nodes);
         std::vector<unsigned char> leaf(a.n_nodes);
-        std::vector<FrontDesc> solve;
+        std::vector<FrontDesc> solve, solve_b;
         FrontDesc* d_solve = (FrontDesc*)(A + o_fsolve);
+        FrontDesc* d_solve_b = h.lu ? (FrontDesc*)(A + o_bsolve) : nullptr;
         for (int d = 0; d < nl; ++d) {
             Level& L = h.levels[d];
             L.d_fronts_solve = d_solve + solve.size();
+            if (h.lu) L.d_fronts_solve_bwd = d_solve_b + solve.size();
             for (auto& f : L.fronts) {
                 refs[f.node] = NodeRef{f.P, f.ldp, is_fp64(L.prec) ? 1 : 0};
                 FrontDesc g = f;
@@ -1154,8 +1189,14 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
                 g.N = g.s;
                 g.child_count = 0;
                 solve.push_back(g);
+                g.P = g.PU;
+                g.Dinv = g.DinvU;
+                solve_b.push_back(g);
             }
         }
+        if (h.lu)
+            RSD_CUDA_TRY(cudaMemcpyAsync(d_solve_b, stage_host(h, solve_b.data(), sizeof(FrontDesc) * solve_b.size()),
+                                         sizeof(FrontDesc) * solve_b.size(), cudaMemcpyHostToDevice, st));
         for (int t = 0; t < a.n_nodes; ++t) leaf[t] = a.children[t].empty() ? 1 : 0;
         RSD_CUDA_TRY(cudaMemcpyAsync(h.d_node_ref, stage_host(h, refs.data(), sizeof(NodeRef) * refs.size()), sizeof(NodeRef) * refs.size(), cudaMemcpyHostToDevice, st));
         RSD_CUDA_TRY(cudaMemcpyAsync(h.d_node_leaf, stage_host(h, leaf.data(), leaf.size()), leaf.size(), cudaMemcpyHostToDevice, st));
@@ -1235,11 +1276,17 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
     for (int d = nl - 1; d >= 0; --d) {
         if (!h.levels[d].factored) continue;
         RSD_TRY(launch_zero_fronts(h, d));
-        RSD_TRY(launch_assemble_fronts(h, d, h.d_rowptr, h.d_col, h.d_val, d_owner, d_rank, d_tin, d_tout));
+        if (h.lu) RSD_TRY(launch_assemble_fronts_lu(h, d, h.d_rowptr, h.d_col, h.d_val, d_owner, d_rank, d_tin, d_tout));
+        else RSD_TRY(launch_assemble_fronts(h, d, h.d_rowptr, h.d_col, h.d_val, d_owner, d_rank, d_tin, d_tout));
     }
     if (!paper) {
         const auto t_issue = std::chrono::steady_clock::now();
         for (int d = nl - 1; d >= 0; --d) {
+            if (h.lu) {
+                RSD_TRY(launch_extend_add_lu(h, d));
+                RSD_TRY(run_factor_level_lu(h, d));
+                continue;
+            }
             RSD_TRY(launch_extend_add(h, d));
             RSD_TRY(run_factor_level(h, d));
             RSD_TRY(launch_factor_copy16(h, d));
@@ -1248,7 +1295,7 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
     } else {
         // every interface front is K_II plus leaf updates: factor the leaves, scatter
         // their updates into S~, then factor the interfaces
-        RSD_TRY(run_factor_level(h, nl - 1));
+        RSD_TRY(h.lu ? run_factor_level_lu(h, nl - 1) : run_factor_level(h, nl - 1));
         if (!gmode) {
             RSD_TRY(paper_extend_add(h));
             for (int d = nl - 2; d >= 0; --d) RSD_TRY(run_factor_level(h, d));
@@ -1258,7 +1305,7 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
     stage_reset(h);                                   // every staged upload has completed
     int err[ERR_SLOTS];
     RSD_CUDA_TRY(cudaMemcpy(err, h.d_err, sizeof(err), cudaMemcpyDeviceToHost));
-    if (err[ERR_NOT_SPD] && !paper) {
+    if (err[ERR_NOT_SPD] && !paper && !h.lu) {
         RSD_TRY(promote_failed_fronts(h, d_owner, d_rank, d_tin, d_tout));
         RSD_CUDA_TRY(cudaStreamSynchronize(st));
         stage_reset(h);
@@ -1401,6 +1448,18 @@ extern "C" int rsd_setup(const rsd_csr* K, const int32_t* dof_node, const rsd_tr
     if (o.mode != RSD_MODE_EXACT && o.mode != RSD_MODE_PAPER) return RSD_ERR_ARG;
     if (o.gamma < 0 || (o.gamma > 0 && o.mode != RSD_MODE_PAPER)) return RSD_ERR_ARG;
     if (o.krylov < RSD_KRYLOV_AUTO || o.krylov > RSD_KRYLOV_FGMRES) return RSD_ERR_ARG;
+    if (o.nonsymmetric) {
+        const int ps[3] = {o.prec_leaf, o.prec_mid, o.prec_root};
+        for (int p : ps)
+            if (p != RSD_PREC_FP64 && p != RSD_PREC_FP32) {
+                set_last_error("nonsymmetric fronts (LU) are factored in FP64 or FP32 on CUDA cores");
+                return RSD_ERR_ARG;
+            }
+        if (o.krylov == RSD_KRYLOV_PCG || (o.mode == RSD_MODE_PAPER && o.gamma == 0)) {
+            set_last_error("nonsymmetric K: FGMRES only, and paper mode needs gamma > 0");
+            return RSD_ERR_ARG;
+        }
+    }
     if (o.krylov == RSD_KRYLOV_PCG && o.gamma > 0) {
         set_last_error("PCG needs a fixed preconditioner: gamma > 0 makes it change with its input");
         return RSD_ERR_ARG;
@@ -1542,6 +1601,10 @@ extern "C" int rsd_solve(rsd_handle hh, const double* f, double* u, double tol, 
 }
 
 extern "C" int rsd_solve_adjoint(rsd_handle hh, const double* g, double* lam, double tol, rsd_stats* st) {
+    if (hh && hh->h.lu) {
+        set_last_error("rsd_solve_adjoint: the hierarchy holds a nonsymmetric K");
+        return RSD_ERR_ARG;
+    }
     // Every matrix the hierarchy holds is symmetric (its fronts are Cholesky-factored), so
     // K^T lam = g is the same system as K lam = g: same fronts, same PCG, no new setup.
     return rsd_solve(hh, g, lam, tol, st);
@@ -1606,6 +1669,25 @@ extern "C" int rsd_front_factor16(rsd_handle hh, int32_t node, double* out) {
         for (int c = 0; c < f.s; ++c) {
             const bool read = r >= f.s || c / NB < r / NB;       // what the sweeps read
             out[(size_t)r * f.s + c] = read ? (double)__half2float(q[(size_t)r * f.ldp + c]) * (double)rs[f.N + r] : 0.0;
+        }
+    return RSD_OK;
+}
+
+extern "C" int rsd_front_factor_upper(rsd_handle hh, int32_t node, double* out) {
+    if (!hh || !out || node < 0 || node >= hh->h.n_nodes || !hh->h.lu) return RSD_ERR_ARG;
+    Handle& h = hh->h;
+    RSD_CUDA_TRY(cudaStreamSynchronize(h.stream));
+    const Level& L = h.levels[h.node_level[node]];
+    if (!L.factored) return RSD_ERR_ARG;
+    const FrontDesc& f = L.fronts[h.node_slot[node]];
+    const size_t es = elem_bytes(L.prec);
+    std::vector<char> buf((size_t)f.N * f.ldp * es);
+    if (!buf.empty()) RSD_CUDA_TRY(cudaMemcpy(buf.data(), f.PU, buf.size(), cudaMemcpyDeviceToHost));
+    for (int r = 0; r < f.N; ++r)
+        for (int c = 0; c < f.s; ++c) {
+            const double v = es == 8 ? ((const double*)buf.data())[(size_t)r * f.ldp + c]
+                                     : (double)((const float*)buf.data())[(size_t)r * f.ldp + c];
+            out[(size_t)r * f.s + c] = (r < f.s && c > r) ? 0.0 : v;
         }
     return RSD_OK;
 }

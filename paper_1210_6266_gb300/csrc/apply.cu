@@ -726,8 +726,10 @@ int sweep_level(Handle& h, int li, bool forward, const double* r, double* z, int
         prof_end(h, gi, 0.0, gbytes);
         RSD_CUDA_TRY(cudaGetLastError());
         if (L.n_bwd_items) {
+            // nonsymmetric fronts: [U^T; Y^T] with (U_kk^T)^-1
+            const FrontDesc* bf = L.d_fronts_bwd ? L.d_fronts_bwd : L.d_fronts;
             const int pi = prof_begin(h, K_BWD);
-            launch_bwd<T, A>(sweep_group(L), L.h16, grid, h.stream, L.d_fronts, L.d_bwd_items, L.n_bwd_items, h.d_ticket + tk, h.d_err, z, h.wait_cycles);
+            launch_bwd<T, A>(sweep_group(L), L.h16, grid, h.stream, bf, L.d_bwd_items, L.n_bwd_items, h.d_ticket + tk, h.d_err, z, h.wait_cycles);
             count_launch();
             prof_end(h, pi, fbytes / sizeof(T) * 2.0, fbytes);
         }
@@ -828,7 +830,7 @@ int sweep_level_static(Handle& h, int li, bool forward, const double* r, double*
 int static_apply_prepare(Handle& h, FrontDesc* d_slots) {
     h.static_ok = false;
     h.d_static_fronts = d_slots;
-    if (h.paper) return RSD_OK;
+    if (h.paper || h.lu) return RSD_OK;
     char* base = nullptr;
     RSD_TRY(scratch_address(h.device, &base));
     const int nl = (int)h.levels.size();
@@ -875,6 +877,10 @@ int run_apply_static(Handle& h, const double* r, double* z) {
     if (dev != h.device) {
         set_last_error("rsd_apply_static: the current device (" + std::to_string(dev) +
                        ") is not the handle's device (" + std::to_string(h.device) + ")");
+        return RSD_ERR_ARG;
+    }
+    if (h.lu) {
+        set_last_error("rsd_apply_static: nonsymmetric (LU) hierarchies are not supported");
         return RSD_ERR_ARG;
     }
     if (!h.static_ok) {

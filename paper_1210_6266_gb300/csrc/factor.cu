@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(256) k_potrf_diag(const FrontDesc* __restrict_
 // ---------------------------------------------------------------------------------
 constexpr int TR_ROWS = 32;
 template <typename T>
-__global__ void __launch_bounds__(256) k_trsm_simt(const FrontDesc* __restrict__ fronts, int k) {
+__global__ void __launch_bounds__(256) k_trsm_simt(const FrontDesc* __restrict__ fronts, int k, int sel) {
     extern __shared__ unsigned char smem_raw[];
     T* D = (T*)smem_raw;                     // NB x NB
     T* R = D + NB * NB;                      // TR_ROWS x (NB + 1)
@@ -424,9 +424,10 @@ __global__ void __launch_bounds__(256) k_trsm_simt(const FrontDesc* __restrict__
     const int r0 = k + w + blockIdx.x * TR_ROWS;
     if (r0 >= f.N) return;
     const int nr = min(TR_ROWS, f.N - r0);
-    const T* Dg = (const T*)f.Dinv + (int64_t)(k / NB) * NB * NB;
+    // sel 0: (P, Dinv); nonsymmetric fronts: 1 = (P, DinvU), 2 = (PU, Dinv)
+    const T* Dg = (const T*)(sel == 1 ? f.DinvU : f.Dinv) + (int64_t)(k / NB) * NB * NB;
     for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) D[e] = Dg[e];
-    T* P = (T*)f.P;
+    T* P = (T*)(sel == 2 ? f.PU : f.P);
     for (int e = threadIdx.x; e < TR_ROWS * NB; e += blockDim.x) {
         const int r = e / NB, c = e % NB;
         R[r * LDR + c] = (r < nr && c < w) ? P[(int64_t)(r0 + r) * f.ldp + k + c] : (T)0;
@@ -1210,8 +1211,8 @@ int run_factor_level(Handle& h, int li) {
             for (auto& f : L.fronts)
                 if (f.s > k) { const double w = std::min(NB, f.s - k), m = f.N - k - w; tf += m * w * w; tb += 2.0 * m * w * es; }
             const int tpi = prof_begin(h, K_TRSM);
-            if (f64) k_trsm_simt<double><<<grid, 256, trsm_smem, h.stream>>>(L.d_fronts, k);
-            else k_trsm_simt<float><<<grid, 256, trsm_smem, h.stream>>>(L.d_fronts, k);
+            if (f64) k_trsm_simt<double><<<grid, 256, trsm_smem, h.stream>>>(L.d_fronts, k, 0);
+            else k_trsm_simt<float><<<grid, 256, trsm_smem, h.stream>>>(L.d_fronts, k, 0);
             count_launch();
             prof_end(h, tpi, tf, tb);
             if (cudaGetLastError() != cudaSuccess) { rc = RSD_ERR_CUDA; break; }
@@ -1245,6 +1246,38 @@ int run_factor_level(Handle& h, int li) {
     }
     cudaFreeAsync(d_tasks, h.stream);
     return rc;
+}
+
+// ---- CUDA-core kernels for the nonsymmetric (LU) fronts of factor_lu.cu -------------
+int lu_gemm(Handle& h, const std::vector<GemmTask>& tasks_in, bool f64, cudaStream_t st) {
+    if (tasks_in.empty()) return RSD_OK;
+    std::vector<GemmTask> tasks = tasks_in;
+    finalize_tasks(tasks, SB, SB);
+    GemmTask* d_tasks = nullptr;
+    RSD_CUDA_TRY(cudaMallocAsync((void**)&d_tasks, sizeof(GemmTask) * tasks.size(), st));
+    const int rc = f64 ? launch_gemm_simt<double>(h, tasks, d_tasks, -1.0, st)
+                       : launch_gemm_simt<float>(h, tasks, d_tasks, -1.0f, st);
+    cudaFreeAsync(d_tasks, st);
+    return rc;
+}
+
+int lu_trsm(Handle& h, int li, int k, int sel, bool f64, cudaStream_t st) {
+    Level& L = h.levels[li];
+    const size_t es = f64 ? 8 : 4;
+    const size_t trsm_smem = (size_t)NB * NB * es + (size_t)TR_ROWS * (NB + 1) * es;
+    if (f64) RSD_CUDA_TRY(cudaFuncSetAttribute(k_trsm_simt<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem));
+    else RSD_CUDA_TRY(cudaFuncSetAttribute(k_trsm_simt<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem));
+    dim3 grid((unsigned)std::max(1, (L.max_N - k + TR_ROWS - 1) / TR_ROWS), (unsigned)L.fronts.size());
+    double tf = 0, tb = 0;
+    for (auto& f : L.fronts)
+        if (f.s > k) { const double w = std::min(NB, f.s - k), m = f.N - k - w; tf += m * w * w; tb += 2.0 * m * w * es; }
+    const int tpi = prof_begin(h, K_TRSM, st);
+    if (f64) k_trsm_simt<double><<<grid, 256, trsm_smem, st>>>(L.d_fronts, k, sel);
+    else k_trsm_simt<float><<<grid, 256, trsm_smem, st>>>(L.d_fronts, k, sel);
+    count_launch();
+    prof_end(h, tpi, tf, tb, st);
+    RSD_CUDA_TRY(cudaGetLastError());
+    return RSD_OK;
 }
 
 }  // namespace rsd

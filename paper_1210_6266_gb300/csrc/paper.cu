@@ -134,7 +134,8 @@ static int leaf_solve(Handle& h, const double* in, double* out, int*& ticket) {
     for (auto& f : L.fronts) fb += 0.5 * f.s * (f.s + 1.0) * elem_bytes(L.prec);
     prof_end(h, p1, fb / elem_bytes(L.prec) * 2.0, fb);
     const int p2 = prof_begin(h, K_BWD);
-    RSD_TRY(sweep_with(h, dl, false, L.d_fronts_solve, L.d_bwd_items, L.n_bwd_items, in, out, ticket++));
+    RSD_TRY(sweep_with(h, dl, false, L.d_fronts_solve_bwd ? L.d_fronts_solve_bwd : L.d_fronts_solve, L.d_bwd_items,
+                       L.n_bwd_items, in, out, ticket++));
     prof_end(h, p2, fb / elem_bytes(L.prec) * 2.0, fb);
     return RSD_OK;
 }

@@ -260,6 +260,9 @@ int gamma_interface_solve(Handle& h, int li, double* z) {
     if (G.n_if == 0 || G.S == 0) return RSD_OK;
     const Level& Ll = h.levels.back();
     const int nleaf = (int)Ll.fronts.size();
+    // t_l = (L_l^-1 K_{l I})[:, R] x reads Y^T (the backward descriptors) for nonsymmetric
+    // leaves; for symmetric ones Y^T = X
+    const FrontDesc* ty = Ll.d_fronts_bwd ? Ll.d_fronts_bwd : Ll.d_fronts;
     const bool f64 = is_fp64(Ll.prec);
     const int gam = h.gamma;
     const int pi = prof_begin(h, K_GAMMA);
@@ -273,12 +276,12 @@ int gamma_interface_solve(Handle& h, int li, double* z) {
         const double* vj = h.d_gm_V + (int64_t)j * G.S;
         const unsigned gr = (unsigned)std::max(1, std::min(h.num_sms * 8, (G.nk + 7) / 8));
         if (f64) {
-            k_smv_leaf<double><<<gl, 256, 0, h.stream>>>(Ll.d_fronts, G.d_cl_ptr, G.d_cl_row, G.d_cl_pos, h.d_tl_off, vj, h.d_tl);
+            k_smv_leaf<double><<<gl, 256, 0, h.stream>>>(ty, G.d_cl_ptr, G.d_cl_row, G.d_cl_pos, h.d_tl_off, vj, h.d_tl);
             k_smv_rows<double><<<gr, 256, 0, h.stream>>>(G.nk, G.d_cl_leaf, G.d_cl_row, Ll.d_fronts, h.d_tl_off, h.d_tl,
                                                          h.d_gm_yl);
         } else {
             float* tl32 = (float*)h.d_tl;
-            k_smv_leaf<float><<<gl, 256, 0, h.stream>>>(Ll.d_fronts, G.d_cl_ptr, G.d_cl_row, G.d_cl_pos, h.d_tl_off, vj, tl32);
+            k_smv_leaf<float><<<gl, 256, 0, h.stream>>>(ty, G.d_cl_ptr, G.d_cl_row, G.d_cl_pos, h.d_tl_off, vj, tl32);
             k_smv_rows<float><<<gr, 256, 0, h.stream>>>(G.nk, G.d_cl_leaf, G.d_cl_row, Ll.d_fronts, h.d_tl_off, tl32, h.d_gm_yl);
         }
         k_smv_iface<<<gi, 256, 0, h.stream>>>(G.S, G.d_if_dofs, h.d_rowptr, h.d_col, h.d_val, h.d_owner, h.d_pk_pos,

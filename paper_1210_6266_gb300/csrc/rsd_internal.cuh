@@ -64,6 +64,11 @@ struct FrontDesc {
     void* P16;
     const float* rs;
     const float* ri;
+    // nonsymmetric fronts (LU without pivoting): PU is [U^T; Y^T], N x ldp like P, with
+    // F_II = L U (L unit lower in P), Y = L^-1 F_IB, X = F_BI U^-1 (rows s.. of P); DinvU
+    // holds (U_kk^T)^-1 per diagonal block (Dinv then holds L_kk^-1).  nullptr otherwise.
+    void* PU;
+    void* DinvU;
 };
 
 // Batched GEMM task: C = beta*C - A * B^T over an M x N block (row-major operands,
@@ -140,6 +145,10 @@ struct Level {
     int n_fwd_items_solve = 0;
     // false for the interface levels of paper mode with gamma > 0: no front is stored
     bool factored = true;
+    // nonsymmetric fronts: descriptors with P = PU and Dinv = DinvU for the backward sweeps
+    // (and, in paper mode, for the backward leaf solves); nullptr for symmetric fronts
+    FrontDesc* d_fronts_bwd = nullptr;
+    FrontDesc* d_fronts_solve_bwd = nullptr;
 };
 
 // Paper mode with gamma inner GMRES iterations: one interface level's packed vectors and
@@ -196,6 +205,7 @@ struct Handle {
     int* d_err = nullptr;
     int* d_front_bad = nullptr;          // per node: a pivot of its factorisation failed
     int promoted = 0;                    // fronts re-factored one precision up at setup
+    bool lu = false;                     // nonsymmetric K: LU fronts (FrontDesc::PU, DinvU)
     int* d_ticket = nullptr;             // per-sweep ticket counters
     // CSR of K on the device (FP64), owned copy for the Krylov SpMV
     int64_t nnz = 0;
@@ -323,6 +333,11 @@ int launch_assemble_fronts(Handle& h, int li, const int64_t* rowptr, const int* 
                            const int* tin, const int* tout);
 int launch_extend_add(Handle& h, int li);
 int run_factor_level(Handle& h, int li);
+// nonsymmetric fronts: assembly, extend-add and LU partial factorisation of level li
+int launch_assemble_fronts_lu(Handle& h, int li, const int64_t* rowptr, const int* col, const double* val,
+                              const int* owner, const int* rank, const int* tin, const int* tout);
+int launch_extend_add_lu(Handle& h, int li);
+int run_factor_level_lu(Handle& h, int li);
 int run_apply(Handle& h, const double* r, double* z);
 int run_apply_static(Handle& h, const double* r, double* z);
 // descriptors of the allocation-free application, written to d_slots (n_nodes entries of
