@@ -14,10 +14,12 @@
 // F_BI) and PU (entries above it, transposed, and F_IB transposed).
 //
 // Left-looking by NB-column blocks k (CUDA cores, FP64 or FP32):
-//   (a) P[k:N, blk]    -= P[k:N, 0:k]    PU[blk, 0:k]^T   (L and X columns; the full
-//                                                          diagonal block of F)
-//   (b) PU[k+w:N, blk] -= PU[k+w:N, 0:k] P[blk, 0:k]^T    (U^T and Y^T columns)
-//   (c) the diagonal block's LU and the inverses L_kk^-1, (U_kk^T)^-1
+//   (a) P[k:N, blk]    -= P[k:N, 0:k]    PU[blk, 0:k]^T   (L and X columns, with the
+//                                                          diagonal block's lower part)
+//   (b) PU[k:N, blk]   -= PU[k:N, 0:k]   P[blk, 0:k]^T    (U^T and Y^T columns, with the
+//                                                          diagonal block's upper part)
+//   (c) the diagonal block's LU (lower part from P, upper part from PU) and the inverses
+//       L_kk^-1, (U_kk^T)^-1
 //   (d) P[k+w:N, blk]  <- P[k+w:N, blk]  DinvU^T          (= F U_kk^-1)
 //       PU[k+w:N, blk] <- PU[k+w:N, blk] Dinv^T           (= (L_kk^-1 F)^T)
 // then U_t -= X Y = P[s:N, :] PU[s:N, :]^T (all b x b entries).
@@ -109,9 +111,9 @@ __global__ void k_extend_add_lu(const FrontDesc* __restrict__ parents, const Fro
 }
 
 // LU of the w x w diagonal block at k (w <= NB; one CTA per front), without pivoting.  The
-// full block of F sits in P[k:k+w, k:k+w] (updated by step (a)).  Writes L (unit) to P's
-// block, U^T to PU's block, L^-1 to Dinv and (U^T)^-1 = (U^-1)^T to DinvU (NB x NB, zero
-// padded).  A pivot that is zero or not finite marks the front (not factorable without
+// block of F (updated by steps (a) and (b)) is read from P on and below the diagonal and
+// from PU (transposed) above it.  Writes L (unit) to P's block, U^T to PU's block, L^-1 to
+// Dinv and (U^T)^-1 = (U^-1)^T to DinvU (NB x NB, zero padded).  A pivot that is zero or not finite marks the front (not factorable without
 // pivoting) and is replaced by 1 so the kernel finishes.
 template <typename T>
 __global__ void __launch_bounds__(256) k_getrf_diag(const FrontDesc* __restrict__ fronts, int k, int* __restrict__ err,
@@ -126,7 +128,8 @@ __global__ void __launch_bounds__(256) k_getrf_diag(const FrontDesc* __restrict_
     T* PU = (T*)f.PU;
     for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
         const int r = e / NB, c = e % NB;
-        A[r * LD + c] = (r < w && c < w) ? P[(int64_t)(k + r) * f.ldp + k + c] : (r == c ? (T)1 : (T)0);
+        A[r * LD + c] = (r < w && c < w) ? (c <= r ? P[(int64_t)(k + r) * f.ldp + k + c] : PU[(int64_t)(k + c) * f.ldp + k + r])
+                                         : (r == c ? (T)1 : (T)0);
     }
     __shared__ int s_bad;
     if (threadIdx.x == 0) s_bad = 0;
@@ -250,16 +253,15 @@ int run_factor_level_lu(Handle& h, int li) {
                 tasks.push_back(t);
             }
             RSD_TRY(lu_gemm(h, tasks, f64, h.stream));
-            // (b) U^T and Y^T columns below the diagonal block
+            // (b) U^T and Y^T columns, from the diagonal block down
             tasks.clear();
             for (auto& f : L.fronts) {
                 if (f.s <= k) continue;
                 const int w = std::min(NB, f.s - k);
-                if (f.N - k - w <= 0) continue;
                 GemmTask t{};
-                t.A = at(f.PU, f, k + w, 0); t.B = at(f.P, f, k, 0); t.C = at(f.PU, f, k + w, k);
+                t.A = at(f.PU, f, k, 0); t.B = at(f.P, f, k, 0); t.C = at(f.PU, f, k, k);
                 t.lda = t.ldb = t.ldc = f.ldp;
-                t.M = f.N - k - w; t.N = w; t.K = k;
+                t.M = f.N - k; t.N = w; t.K = k;
                 t.lower = 0; t.beta = 1;
                 tasks.push_back(t);
             }
