@@ -408,6 +408,152 @@ __global__ void __launch_bounds__(256) k_potrf_diag(const FrontDesc* __restrict_
 }
 
 // ---------------------------------------------------------------------------------
+// FP32 diagonal block, blocked by 32: the same result as k_potrf_diag (Cholesky of
+// P[k:k+w, k:k+w] written back, its inverse to Dinv_k), with a shorter dependency chain.
+// The block and its inverse live in shared memory (A, X: 128 x 129 floats).  For each
+// 32-wide panel J: one warp factors the 32 x 32 diagonal sub-block (warp barriers only)
+// and inverts it into X; all 8 warps then solve the rows below (A_IJ <- A_IJ X_JJ^T) and
+// update the trailing lower triangle (A_IK -= A_IJ A_KJ^T), a warp per 32 x 32 tile, each
+// lane holding one column's 32 operands in registers.  The inverse's off-diagonal blocks
+// follow from L X = I by block rows: X_IJ = -X_II sum_{J <= K < I} L_IK X_KJ.
+// ---------------------------------------------------------------------------------
+constexpr int DB = 32;                  // sub-block width
+constexpr int XLD = NB + 1;
+
+__device__ __forceinline__ float tf32_store(float x, bool rnd) {
+    if (!rnd) return x;
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+__global__ void __launch_bounds__(256) k_potrf_diag_blk(const FrontDesc* __restrict__ fronts, int k,
+                                                       int* __restrict__ err, int round_tf32, int* __restrict__ bad_front) {
+    extern __shared__ unsigned char smem_raw[];
+    float* A = (float*)smem_raw;                  // 128 x XLD, lower triangle used
+    float* X = A + NB * XLD;                      // 128 x XLD, the inverse
+    __shared__ int s_bad;
+    const FrontDesc f = fronts[blockIdx.x];
+    if (f.s <= k) return;
+    const int w = min(NB, f.s - k);
+    float* P = (float*)f.P;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_bad = 0;
+    for (int e = tid; e < NB * NB; e += 256) {
+        const int i = e / NB, c = e % NB;
+        A[i * XLD + c] = (i < w && c <= i) ? P[(int64_t)(k + i) * f.ldp + k + c] : (i == c ? 1.0f : 0.0f);
+        X[i * XLD + c] = 0.0f;
+    }
+    __syncthreads();
+    for (int J = 0; J < NB / DB; ++J) {
+        const int o = J * DB;
+        if (warp == 0) {
+            // (1) Cholesky of the 32 x 32 block at (o, o): lane i owns row o + i
+            const int i = lane;
+            for (int j = 0; j < DB; ++j) {
+                float d = A[(o + j) * XLD + o + j];
+                if (!(d > 0.0f)) { if (i == 0) s_bad = 1; d = 1.0f; }
+                const float inv = rsqrtf(d);
+                __syncwarp();
+                if (i > j) A[(o + i) * XLD + o + j] *= inv;
+                __syncwarp();
+                if (i > j) {
+                    const float lij = A[(o + i) * XLD + o + j];
+                    for (int q = j + 1; q <= i; ++q) A[(o + i) * XLD + o + q] -= lij * A[(o + q) * XLD + o + j];
+                }
+                __syncwarp();
+                if (i == j) A[(o + j) * XLD + o + j] = d * inv;
+                __syncwarp();
+            }
+            // (2) X_JJ = L_JJ^-1, lane c computes column c
+            const int c = lane;
+            X[(o + c) * XLD + o + c] = 1.0f / A[(o + c) * XLD + o + c];
+            for (int r = c + 1; r < DB; ++r) {
+                float acc = 0.0f;
+                for (int m = c; m < r; ++m) acc += A[(o + r) * XLD + o + m] * X[(o + m) * XLD + o + c];
+                X[(o + r) * XLD + o + c] = -acc / A[(o + r) * XLD + o + r];
+            }
+        }
+        __syncthreads();
+        const int nb_below = NB / DB - 1 - J;          // 32-row blocks below the panel
+        if (nb_below == 0) continue;
+        // (3) A_IJ <- A_IJ X_JJ^T for the blocks I below: warp per 32-row block, lane = column
+        for (int I = warp; I < nb_below; I += 8) {
+            const int ro = o + DB * (I + 1);
+            float xc[DB];
+#pragma unroll
+            for (int m = 0; m < DB; ++m) xc[m] = X[(o + lane) * XLD + o + m];      // row lane of X_JJ
+            for (int r = 0; r < DB; ++r) {
+                float acc = 0.0f;
+#pragma unroll
+                for (int m = 0; m < DB; ++m) acc += A[(ro + r) * XLD + o + m] * xc[m];
+                __syncwarp();                              // the row is read before it is overwritten
+                A[(ro + r) * XLD + o + lane] = acc;
+            }
+        }
+        __syncthreads();
+        // (4) trailing update of the lower triangle below the panel, warp per 32 x 32 tile
+        const int ntiles = nb_below * (nb_below + 1) / 2;
+        for (int tIdx = warp; tIdx < ntiles; tIdx += 8) {
+            int I = 0;
+            while ((I + 1) * (I + 2) / 2 <= tIdx) ++I;
+            const int K = tIdx - I * (I + 1) / 2;          // K <= I
+            const int ro = o + DB * (I + 1), co = o + DB * (K + 1);
+            float bc[DB];
+#pragma unroll
+            for (int m = 0; m < DB; ++m) bc[m] = A[(co + lane) * XLD + o + m];      // L_KJ row lane
+#pragma unroll 4
+            for (int r = 0; r < DB; ++r) {
+                if (I == K && lane > r) continue;
+                float acc = 0.0f;
+#pragma unroll
+                for (int m = 0; m < DB; ++m) acc += A[(ro + r) * XLD + o + m] * bc[m];
+                A[(ro + r) * XLD + co + lane] -= acc;
+            }
+        }
+        __syncthreads();
+    }
+    if (tid == 0 && s_bad) {
+        atomicExch(&err[ERR_NOT_SPD], 1);
+        atomicMin(&err[ERR_NOT_SPD_NODE], f.node);
+        bad_front[f.node] = 1;
+    }
+    // (5) off-diagonal blocks of X, block row by block row: T = sum_{J<=K<I} L_IK X_KJ into
+    // X_IJ, then X_IJ = -X_II T (a warp per block, lane = column)
+    for (int I = 1; I < NB / DB; ++I) {
+        for (int J = warp; J < I; J += 8) {
+            // T = sum_K L_IK X_KJ, accumulated in place in X_IJ (zero so far), lane = column
+            float* XIJ = X + (DB * I) * XLD + DB * J + lane;
+            for (int K = J; K < I; ++K) {
+                float xc[DB];
+#pragma unroll
+                for (int m = 0; m < DB; ++m) xc[m] = X[(DB * K + m) * XLD + DB * J + lane];
+                for (int r = 0; r < DB; ++r) {
+                    float acc = 0.0f;
+#pragma unroll
+                    for (int m = 0; m < DB; ++m) acc += A[(DB * I + r) * XLD + DB * K + m] * xc[m];
+                    XIJ[r * XLD] += acc;
+                }
+            }
+            // X_IJ = -X_II T, rows from the last up: row r needs T's rows m <= r only
+            for (int r = DB - 1; r >= 0; --r) {
+                float acc = 0.0f;
+                for (int m = 0; m <= r; ++m) acc += X[(DB * I + r) * XLD + DB * I + m] * XIJ[m * XLD];
+                XIJ[r * XLD] = -acc;
+            }
+        }
+        __syncthreads();
+    }
+    const bool rnd = round_tf32 != 0;
+    float* D = (float*)f.Dinv + (int64_t)(k / NB) * NB * NB;
+    for (int e = tid; e < NB * NB; e += 256) {
+        const int i = e / NB, c = e % NB;
+        if (i < w && c <= i) P[(int64_t)(k + i) * f.ldp + k + c] = tf32_store(A[i * XLD + c], rnd);
+        D[e] = (i < w && c <= i) ? tf32_store(X[i * XLD + c], rnd) : 0.0f;
+    }
+}
+
+// ---------------------------------------------------------------------------------
 // Panel solve in place: rows P[k+w:N, k:k+w] <- rows * Dinv_k^T (Dinv_k lower triangular).
 // Each CTA owns 32 full-width rows, so reading and overwriting them cannot race.
 // ---------------------------------------------------------------------------------
@@ -851,8 +997,8 @@ static int ensure_chain(Handle& h) {
 static int factor_level_tc(Handle& h, int li, bool lookahead) {
     Level& L = h.levels[li];
     const size_t es = 4;
-    const size_t potrf_smem = (size_t)NB * DLD * es + (size_t)2 * NB * es;
-    RSD_CUDA_TRY(cudaFuncSetAttribute(k_potrf_diag<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)potrf_smem));
+    const size_t potrf_smem = (size_t)2 * NB * XLD * sizeof(float);
+    RSD_CUDA_TRY(cudaFuncSetAttribute(k_potrf_diag_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)potrf_smem));
     const int nf = (int)L.fronts.size();
     if (lookahead) RSD_TRY(ensure_chain(h));
     cudaStream_t B = h.stream, Cs = lookahead ? h.chain : h.stream;
@@ -947,7 +1093,7 @@ static int factor_level_tc(Handle& h, int li, bool lookahead) {
                 if (f.s > k) { const double w = std::min(NB, f.s - k); pf += 2.0 * w * w * w / 3.0; pb += (2.0 * w * w + NB * NB) * es; }
             if (!dry) {
                 const int ppi = prof_begin(h, K_POTRF, cs);
-                k_potrf_diag<float><<<(unsigned)nf, 256, potrf_smem, cs>>>(L.d_fronts, k, h.d_err, 1, h.d_front_bad);
+                k_potrf_diag_blk<<<(unsigned)nf, 256, potrf_smem, cs>>>(L.d_fronts, k, h.d_err, 1, h.d_front_bad);
                 count_launch();
                 prof_end(h, ppi, pf, pb, cs);
                 RSD_CUDA_TRY(cudaGetLastError());
@@ -1111,13 +1257,13 @@ int run_factor_level(Handle& h, int li) {
     // task buffer for this level: one slot per front per launch kind
     GemmTask* d_tasks = nullptr;
     RSD_CUDA_TRY(cudaMallocAsync((void**)&d_tasks, sizeof(GemmTask) * L.fronts.size() * 2 + 64, h.stream));
-    const size_t potrf_smem = (size_t)NB * DLD * es + (size_t)2 * NB * es;
+    const size_t potrf_smem = f64 ? (size_t)NB * DLD * es + (size_t)2 * NB * es : (size_t)2 * NB * XLD * sizeof(float);
     const size_t trsm_smem = (size_t)NB * NB * es + (size_t)TR_ROWS * (NB + 1) * es;
     if (f64) {
         RSD_CUDA_TRY(cudaFuncSetAttribute(k_potrf_diag<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)potrf_smem));
         RSD_CUDA_TRY(cudaFuncSetAttribute(k_trsm_simt<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem));
     } else {
-        RSD_CUDA_TRY(cudaFuncSetAttribute(k_potrf_diag<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)potrf_smem));
+        RSD_CUDA_TRY(cudaFuncSetAttribute(k_potrf_diag_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)potrf_smem));
         RSD_CUDA_TRY(cudaFuncSetAttribute(k_trsm_simt<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem));
     }
     std::vector<GemmTask> tasks;
@@ -1180,7 +1326,7 @@ int run_factor_level(Handle& h, int li) {
             if (f.s > k) { const double w = std::min(NB, f.s - k); pf += 2.0 * w * w * w / 3.0; pb += (2.0 * w * w + NB * NB) * es; }
         const int ppi = prof_begin(h, K_POTRF);
         if (f64) k_potrf_diag<double><<<(unsigned)L.fronts.size(), 256, potrf_smem, h.stream>>>(L.d_fronts, k, h.d_err, 0, h.d_front_bad);
-        else k_potrf_diag<float><<<(unsigned)L.fronts.size(), 256, potrf_smem, h.stream>>>(L.d_fronts, k, h.d_err, tc ? 1 : 0, h.d_front_bad);
+        else k_potrf_diag_blk<<<(unsigned)L.fronts.size(), 256, potrf_smem, h.stream>>>(L.d_fronts, k, h.d_err, tc ? 1 : 0, h.d_front_bad);
         count_launch();
         prof_end(h, ppi, pf, pb);
         if (cudaGetLastError() != cudaSuccess) { rc = RSD_ERR_CUDA; break; }
