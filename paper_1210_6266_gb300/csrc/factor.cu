@@ -409,16 +409,32 @@ __global__ void __launch_bounds__(256) k_potrf_diag(const FrontDesc* __restrict_
 
 // ---------------------------------------------------------------------------------
 // FP32 diagonal block, blocked by 32: the same result as k_potrf_diag (Cholesky of
-// P[k:k+w, k:k+w] written back, its inverse to Dinv_k), with a shorter dependency chain.
-// The block and its inverse live in shared memory (A, X: 128 x 129 floats).  For each
-// 32-wide panel J: one warp factors the 32 x 32 diagonal sub-block (warp barriers only)
-// and inverts it into X; all 8 warps then solve the rows below (A_IJ <- A_IJ X_JJ^T) and
-// update the trailing lower triangle (A_IK -= A_IJ A_KJ^T), a warp per 32 x 32 tile, each
-// lane holding one column's 32 operands in registers.  The inverse's off-diagonal blocks
-// follow from L X = I by block rows: X_IJ = -X_II sum_{J <= K < I} L_IK X_KJ.
+// P[k:k+w, k:k+w] written back, its inverse to Dinv_k) with a short critical path.
+// Shared memory holds the block A (L in its lower triangle), the inverse X, the current
+// 32-column panel transposed (LT[m][r] = L[r][32J + m]), the current diagonal inverse
+// transposed (XT[c][r] = X_JJ[r][c]) and the columns of L_JJ, rotated so that row j
+// starts at the diagonal (LJ[j][p] = l_{j+p, j}, zero where j + p wraps past 31).
+// Per panel J the critical chain is
+//   (1) warp 0: Cholesky of the 32 x 32 diagonal sub-block, lane = row, right-looking;
+//       the lane row sits in registers rotated so that the current column is always
+//       a[0], and each finished column is published once to LJ;
+//   (2) rows below: y_c = (a_c - sum_{m<c} y_m l_cm) / l_cc, a warp per 32 rows (lane = row),
+//       while warp 7 forms X_JJ = L_JJ^-1 (lane = column) with the same rotated sweep;
+//   (3) the next diagonal tile, A_{J+1,J+1} -= L_{J+1,J} L_{J+1,J}^T, 8 rows per warp;
+// and while warp 0 factors panel J+1 the other seven warps finish panel J off the chain:
+//   - the remaining trailing tiles A_IK -= L_IJ L_KJ^T;
+//   - the inverse by block rows (from L X = I): X_JK = -X_JJ T_JK for K < J, then
+//     T_IK += L_IJ X_JK for I > J, K <= J, where T_IK = sum_{K<=M<I} L_IM X_MK collects in
+//     A's unused upper block (K, I);
+//   - the finished panel of L and row block of the inverse go out to global memory.
+// Tile products give each lane a 4 x 8 piece of the 32 x 32 result, three float4 shared
+// loads per 32 FMAs.  All per-column loops are rolled (the kernel runs from a cold
+// instruction cache between other kernels).
 // ---------------------------------------------------------------------------------
 constexpr int DB = 32;                  // sub-block width
-constexpr int XLD = NB + 1;
+constexpr int XLD = NB + 4;             // row stride of A, X and LT (16-byte rows, 4 banks apart)
+constexpr int XTLD = DB + 4;            // row stride of XT
+constexpr size_t POTRF_BLK_SMEM = (size_t)(2 * NB * XLD + DB * XLD + DB * XTLD + DB * DB) * sizeof(float);
 
 __device__ __forceinline__ float tf32_store(float x, bool rnd) {
     if (!rnd) return x;
@@ -427,129 +443,391 @@ __device__ __forceinline__ float tf32_store(float x, bool rnd) {
     return __uint_as_float(r);
 }
 
-__global__ void __launch_bounds__(256) k_potrf_diag_blk(const FrontDesc* __restrict__ fronts, int k,
+__device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void sts4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+
+__device__ __forceinline__ void load_row32(const float* __restrict__ row, float (&v)[DB]) {
+#pragma unroll
+    for (int t = 0; t < DB / 4; ++t) {
+        const float4 q = lds4(row + 4 * t);
+        v[4 * t + 0] = q.x; v[4 * t + 1] = q.y; v[4 * t + 2] = q.z; v[4 * t + 3] = q.w;
+    }
+}
+
+__device__ __forceinline__ void store_row32(float* __restrict__ row, const float (&v)[DB]) {
+#pragma unroll
+    for (int t = 0; t < DB / 4; ++t) sts4(row + 4 * t, make_float4(v[4 * t], v[4 * t + 1], v[4 * t + 2], v[4 * t + 3]));
+}
+
+// v[p-1] = v[p] - y * col[p] for p = 1..31 (col: a 16-byte aligned shared row), v[31] = y
+__device__ __forceinline__ void rotate_update32(float (&v)[DB], const float* __restrict__ col, float y) {
+#pragma unroll
+    for (int t = 0; t < DB / 4; ++t) {
+        const float4 c4 = lds4(col + 4 * t);
+        if (t > 0) v[4 * t - 1] = fmaf(-y, c4.x, v[4 * t]);
+        v[4 * t + 0] = fmaf(-y, c4.y, v[4 * t + 1]);
+        v[4 * t + 1] = fmaf(-y, c4.z, v[4 * t + 2]);
+        v[4 * t + 2] = fmaf(-y, c4.w, v[4 * t + 3]);
+    }
+    v[DB - 1] = y;
+}
+
+// v[p-1] = v[p] - y * c[p] for p = 1..31 (c: one column held in registers), v[31] = y
+__device__ __forceinline__ void rotate_update32_reg(float (&v)[DB], const float4 (&c)[DB / 4], float y) {
+#pragma unroll
+    for (int t = 0; t < DB / 4; ++t) {
+        if (t > 0) v[4 * t - 1] = fmaf(-y, c[t].x, v[4 * t]);
+        v[4 * t + 0] = fmaf(-y, c[t].y, v[4 * t + 1]);
+        v[4 * t + 1] = fmaf(-y, c[t].z, v[4 * t + 2]);
+        v[4 * t + 2] = fmaf(-y, c[t].w, v[4 * t + 3]);
+    }
+    v[DB - 1] = y;
+}
+
+__device__ __forceinline__ void load_col32(float4 (&c)[DB / 4], const float* __restrict__ col) {
+#pragma unroll
+    for (int t = 0; t < DB / 4; ++t) c[t] = lds4(col + 4 * t);
+}
+
+// Forward substitution with L_JJ, one right-hand side per lane: on entry v[p] = b_p, on
+// return v[p] = x_p with x_c = (b_c - sum_{m<c} l_cm x_m) * scale[c].  Two columns per
+// trip, each column's loads issued one step ahead of its use.
+__device__ __forceinline__ void fsub32(float (&v)[DB], const float* __restrict__ LJ, const float* __restrict__ scale) {
+    float4 ca[DB / 4], cb[DB / 4];
+    load_col32(ca, LJ);
+    float sa = scale[0], sb;
+#pragma unroll 1
+    for (int c = 0; c < DB; c += 2) {
+        load_col32(cb, LJ + (c + 1) * DB);
+        sb = scale[c + 1];
+        rotate_update32_reg(v, ca, v[0] * sa);
+        const int cn = (c + 2) & (DB - 1);            // the last trip prefetches column 0 again, unused
+        load_col32(ca, LJ + cn * DB);
+        sa = scale[cn];
+        rotate_update32_reg(v, cb, v[0] * sb);
+    }
+}
+
+// warp 0's step (1) for the diagonal sub-block at (o, o); returns 1 on a pivot that is not
+// positive (replaced by 1 so that the rest stays finite).
+// Lane i keeps A_j[i][j..], its row as updated by columns < j, rotated so that position p
+// holds column j + p; finished entries l_i0..l_ij collect at the top and rotate down with
+// the rest (the column entries that move them are zero).  The loop is software-pipelined:
+// step j + 1's pivot chain runs ahead of step j's bulk update.  It needs column j + 1 and
+// j + 2 after step j (a0n, a1n: from l_{j+1,j}, l_{j+2,j} by shuffle) and column j + 3 (one
+// entry of the bulk update); the next pivot comes from lane j + 1's own update.
+__device__ __forceinline__ int potrf_chol32(float* __restrict__ A, float* __restrict__ LJ, float* __restrict__ s_rs,
+                                            float* __restrict__ s_ri, int o, int lane) {
+    const unsigned full = 0xffffffffu;
+    float a[DB];
+    load_row32(A + (o + lane) * XLD + o, a);
+    int bad = 0;
+    float my_inv = 1.0f, my_ljj = 1.0f;
+    // step 0's chain
+    float d = __shfl_sync(full, a[0], 0);
+    if (!(d > 0.0f)) { bad = 1; d = 1.0f; }
+    float inv = rsqrtf(d);
+    float lij = lane > 0 ? a[0] * inv : (lane == 0 ? d * inv : 0.0f);
+    my_inv = lane == 0 ? inv : my_inv;
+    my_ljj = lane == 0 ? d * inv : my_ljj;
+    float dn = __shfl_sync(full, fmaf(-lij, lij, a[1]), 1);
+    float a0n = fmaf(-lij, __shfl_sync(full, lij, 1), a[1]);
+    float a1n = fmaf(-lij, __shfl_sync(full, lij, 2), a[2]);
+#pragma unroll 1
+    for (int j = 0; j < DB; ++j) {
+        // (A) publish column j, fetch it back
+        float* col = LJ + j * DB;
+        col[(lane - j) & (DB - 1)] = lij;
+        __syncwarp();
+        float4 c[DB / 4];
+#pragma unroll
+        for (int t = 0; t < DB / 4; ++t) c[t] = lds4(col + 4 * t);
+        // (B) step j + 1's chain (discarded after the last step)
+        const float a2n = fmaf(-lij, c[0].w, a[3]);              // column j + 3 after step j
+        const int j1 = j + 1;
+        float d1 = dn;
+        if (!(d1 > 0.0f)) { if (j1 < DB) bad = 1; d1 = 1.0f; }
+        const float inv1 = rsqrtf(d1);
+        const float ljj1 = d1 * inv1;
+        const float lij1 = lane > j1 ? a0n * inv1 : (lane == j1 ? ljj1 : 0.0f);
+        my_inv = lane == j1 ? inv1 : my_inv;
+        my_ljj = lane == j1 ? ljj1 : my_ljj;
+        dn = __shfl_sync(full, fmaf(-lij1, lij1, a1n), (j1 + 1) & (DB - 1));
+        const float l1 = __shfl_sync(full, lij1, (j1 + 1) & (DB - 1));
+        const float l2 = __shfl_sync(full, lij1, (j1 + 2) & (DB - 1));
+        // (C) step j's bulk update: columns j + 4 .. j + 31 move down one position
+#pragma unroll
+        for (int t = 1; t < DB / 4; ++t) {
+            a[4 * t - 1] = fmaf(-lij, c[t].x, a[4 * t]);
+            a[4 * t + 0] = fmaf(-lij, c[t].y, a[4 * t + 1]);
+            a[4 * t + 1] = fmaf(-lij, c[t].z, a[4 * t + 2]);
+            a[4 * t + 2] = fmaf(-lij, c[t].w, a[4 * t + 3]);
+        }
+        a[DB - 1] = lij;
+        a[0] = a0n;
+        a[1] = a1n;
+        a[2] = a2n;
+        // step j + 1's first two columns after its own update
+        a0n = fmaf(-lij1, l1, a1n);
+        a1n = fmaf(-lij1, l2, a2n);
+        lij = lij1;
+    }
+    s_rs[o + lane] = my_inv;
+    s_ri[o + lane] = 1.0f / my_ljj;
+    store_row32(A + (o + lane) * XLD + o, a);         // zero above the diagonal
+    return bad;
+}
+
+// C (32 x 32, row stride ldc) = [C +] sgn * sum_{m<32} AT[m][r] B[m][c]; lane tile rows
+// 4 (lane >> 2) + 0..3, columns 8 (lane & 3) + 0..7
+template <bool ACC>
+__device__ __forceinline__ void tile32_atb(const float* __restrict__ AT, int lda, const float* __restrict__ B, int ldb,
+                                           float* __restrict__ C, int ldc, float sgn, int lane) {
+    const int r0 = 4 * (lane >> 2), c0 = 8 * (lane & 3);
+    float acc[4][8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+#pragma unroll 4
+    for (int m = 0; m < DB; ++m) {
+        const float4 a = lds4(AT + m * lda + r0);
+        const float4 b0 = lds4(B + m * ldb + c0), b1 = lds4(B + m * ldb + c0 + 4);
+        const float av[4] = {a.x, a.y, a.z, a.w};
+        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float* row = C + (r0 + i) * ldc + c0;
+        float4 o0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), o1 = o0;
+        if (ACC) { o0 = lds4(row); o1 = lds4(row + 4); }
+        o0.x = fmaf(sgn, acc[i][0], o0.x); o0.y = fmaf(sgn, acc[i][1], o0.y);
+        o0.z = fmaf(sgn, acc[i][2], o0.z); o0.w = fmaf(sgn, acc[i][3], o0.w);
+        o1.x = fmaf(sgn, acc[i][4], o1.x); o1.y = fmaf(sgn, acc[i][5], o1.y);
+        o1.z = fmaf(sgn, acc[i][6], o1.z); o1.w = fmaf(sgn, acc[i][7], o1.w);
+        sts4(row, o0);
+        sts4(row + 4, o1);
+    }
+}
+
+// rows 8 ch + 0..7 of C (32 x 32) -= sum_m AT[m][r] B[m][c]; lane tile 2 rows x 4 columns
+__device__ __forceinline__ void chunk8_atb_sub(const float* __restrict__ AT, int lda, const float* __restrict__ B, int ldb,
+                                               float* __restrict__ C, int ldc, int ch, int lane) {
+    const int r0 = 8 * ch + 2 * (lane >> 3), c0 = 4 * (lane & 7);
+    float acc[2][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+#pragma unroll 8
+    for (int m = 0; m < DB; ++m) {
+        const float2 a = *reinterpret_cast<const float2*>(AT + m * lda + r0);
+        const float4 b = lds4(B + m * ldb + c0);
+        const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            acc[0][j] = fmaf(a.x, bv[j], acc[0][j]);
+            acc[1][j] = fmaf(a.y, bv[j], acc[1][j]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        float* row = C + (r0 + i) * ldc + c0;
+        float4 o = lds4(row);
+        o.x -= acc[i][0]; o.y -= acc[i][1]; o.z -= acc[i][2]; o.w -= acc[i][3];
+        sts4(row, o);
+    }
+}
+
+// Panel K of L (rows 32K..w-1, columns 32K..32K+31, on or below the diagonal) to P
+__device__ __forceinline__ void potrf_store_panel(const float* __restrict__ A, float* __restrict__ P, int64_t ldp, int k,
+                                                  int w, int K, bool rnd, int t0, int nt) {
+    const int r_lo = DB * K;
+    for (int e = t0; e < (NB - r_lo) * (DB / 4); e += nt) {
+        const int i = r_lo + e / (DB / 4), c = r_lo + 4 * (e % (DB / 4));
+        if (i >= w || c > i) continue;
+        const float4 l = lds4(A + i * XLD + c);
+        float* dst = P + (int64_t)(k + i) * ldp + k + c;
+        if (c + 3 <= i) {
+            *reinterpret_cast<float4*>(dst) = make_float4(tf32_store(l.x, rnd), tf32_store(l.y, rnd), tf32_store(l.z, rnd), tf32_store(l.w, rnd));
+        } else {
+            dst[0] = tf32_store(l.x, rnd);
+            if (c + 1 <= i) dst[1] = tf32_store(l.y, rnd);
+            if (c + 2 <= i) dst[2] = tf32_store(l.z, rnd);
+        }
+    }
+}
+
+// Row block K of the inverse (rows 32K..32K+31, all 128 columns, zero above the diagonal
+// and in rows past the front) to D
+__device__ __forceinline__ void potrf_store_inverse(const float* __restrict__ X, float* __restrict__ D, int w, int K,
+                                                    bool rnd, int t0, int nt) {
+    for (int e = t0; e < DB * (NB / 4); e += nt) {
+        const int i = DB * K + e / (NB / 4), c = 4 * (e % (NB / 4));
+        float4 dv = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (i < w && c <= i) {
+            const float4 x = lds4(X + i * XLD + c);
+            dv.x = tf32_store(x.x, rnd);
+            dv.y = c + 1 <= i ? tf32_store(x.y, rnd) : 0.0f;
+            dv.z = c + 2 <= i ? tf32_store(x.z, rnd) : 0.0f;
+            dv.w = c + 3 <= i ? tf32_store(x.w, rnd) : 0.0f;
+        }
+        *reinterpret_cast<float4*>(D + i * NB + c) = dv;
+    }
+}
+
+struct PotrfOut {
+    float* P;
+    int64_t ldp;
+    float* D;
+    int k, w;
+    bool rnd;
+};
+
+// panel K's work off the critical chain, by nw warps (index wi).  Part 1: trailing tiles
+// and the finalised X row block K (warps left over store panel K of L); a named barrier
+// over the nw warps (bar_id > 0); part 2: T accumulation (warps left over store row
+// block K of the inverse).  With K = 3 only part 1 runs and nothing is stored.
+__device__ __forceinline__ void potrf_background(float* __restrict__ A, float* __restrict__ X, const float* __restrict__ LT,
+                                                 const float* __restrict__ XT, const PotrfOut& out, int K, int wi, int nw,
+                                                 int bar_id, int lane) {
+    constexpr int NBB = NB / DB;
+    int ntrail = 0;                                   // trailing tiles except (K+1, K+1)
+    for (int bk = K + 1; bk < NBB; ++bk) ntrail += NBB - bk;
+    if (ntrail > 0) --ntrail;
+    const int n1 = ntrail + K;
+    for (int it = wi; it < n1; it += nw) {
+        if (it < ntrail) {
+            int cnt = 0, bi = 0, bk = 0;
+            for (int q = K + 1; q < NBB; ++q)
+                for (int p = q; p < NBB; ++p) {
+                    if (p == K + 1 && q == K + 1) continue;
+                    if (cnt == it) { bi = p; bk = q; }
+                    ++cnt;
+                }
+            tile32_atb<true>(LT + DB * bi, XLD, LT + DB * bk, XLD, A + DB * bi * XLD + DB * bk, XLD, -1.0f, lane);
+        } else {
+            const int J = it - ntrail;                    // X_KJ = -X_KK T_KJ, T_KJ in A's block (J, K)
+            tile32_atb<false>(XT, XTLD, A + DB * J * XLD + DB * K, XLD, X + DB * K * XLD + DB * J, XLD, -1.0f, lane);
+        }
+    }
+    if (K + 1 >= NBB) return;
+    if (wi >= n1) potrf_store_panel(A, out.P, out.ldp, out.k, out.w, K, out.rnd, 32 * (wi - n1) + lane, 32 * (nw - n1));
+    if (bar_id > 0) asm volatile("bar.sync %0, %1;" :: "r"(bar_id), "r"(32 * nw) : "memory");
+    const int n2 = (NBB - 1 - K) * (K + 1);           // T_IJ += L_IK X_KJ, I > K, J <= K
+    for (int it = wi; it < n2; it += nw) {
+        const int I = K + 1 + it / (K + 1), J = it % (K + 1);
+        tile32_atb<true>(LT + DB * I, XLD, X + DB * K * XLD + DB * J, XLD, A + DB * J * XLD + DB * I, XLD, 1.0f, lane);
+    }
+    if (wi >= n2) potrf_store_inverse(X, out.D, out.w, K, out.rnd, 32 * (wi - n2) + lane, 32 * (nw - n2));
+}
+
+// rows [r_lo, r_hi) of the block into A (lower part; zero above the diagonal; identity
+// rows past the front), float4 loads, nt threads (index ti), all loads before the stores
+template <int MAXV>
+__device__ __forceinline__ void potrf_load_rows(float* __restrict__ A, const float* __restrict__ P, int64_t ldp, int k, int w,
+                                                int r_lo, int r_hi, int ti, int nt) {
+    const int n4 = (r_hi - r_lo) * (NB / 4);
+    float4 v[MAXV];
+#pragma unroll
+    for (int u = 0; u < MAXV; ++u) {
+        const int e = ti + nt * u;
+        v[u] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (e < n4) {
+            const int i = r_lo + e / (NB / 4), c = 4 * (e % (NB / 4));
+            if (i < w && c <= i) v[u] = *reinterpret_cast<const float4*>(P + (int64_t)(k + i) * ldp + k + c);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < MAXV; ++u) {
+        const int e = ti + nt * u;
+        if (e < n4) {
+            const int i = r_lo + e / (NB / 4), c = 4 * (e % (NB / 4));
+            float4 q = v[u];
+            if (i < w) {
+                if (c + 0 > i) q.x = 0.0f;
+                if (c + 1 > i) q.y = 0.0f;
+                if (c + 2 > i) q.z = 0.0f;
+                if (c + 3 > i) q.w = 0.0f;
+            } else {
+                q = make_float4(c + 0 == i ? 1.0f : 0.0f, c + 1 == i ? 1.0f : 0.0f, c + 2 == i ? 1.0f : 0.0f, c + 3 == i ? 1.0f : 0.0f);
+            }
+            sts4(A + i * XLD + c, q);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256, 1) k_potrf_diag_blk(const FrontDesc* __restrict__ fronts, int k,
                                                        int* __restrict__ err, int round_tf32, int* __restrict__ bad_front) {
-    extern __shared__ unsigned char smem_raw[];
-    float* A = (float*)smem_raw;                  // 128 x XLD, lower triangle used
-    float* X = A + NB * XLD;                      // 128 x XLD, the inverse
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* A = (float*)smem_raw;                  // 128 x XLD
+    float* X = A + NB * XLD;                      // 128 x XLD
+    float* LT = X + NB * XLD;                     // 32 x XLD
+    float* XT = LT + DB * XLD;                    // 32 x XTLD
+    float* LJ = XT + DB * XTLD;                   // 32 x 32
+    __shared__ float s_rs[NB];                    // 1 / sqrt(pivot): scales the column below
+    __shared__ float s_ri[NB];                    // 1 / l_jj
     __shared__ int s_bad;
     const FrontDesc f = fronts[blockIdx.x];
     if (f.s <= k) return;
     const int w = min(NB, f.s - k);
-    float* P = (float*)f.P;
+    const PotrfOut out{(float*)f.P, (int64_t)f.ldp, (float*)f.Dinv + (int64_t)(k / NB) * NB * NB, k, w, round_tf32 != 0};
+    const float* P = (const float*)f.P;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_bad = 0;
-    for (int e = tid; e < NB * NB; e += 256) {
-        const int i = e / NB, c = e % NB;
-        A[i * XLD + c] = (i < w && c <= i) ? P[(int64_t)(k + i) * f.ldp + k + c] : (i == c ? 1.0f : 0.0f);
-        X[i * XLD + c] = 0.0f;
-    }
+    potrf_load_rows<4>(A, P, f.ldp, k, w, 0, DB, tid, 256);
     __syncthreads();
     for (int J = 0; J < NB / DB; ++J) {
         const int o = J * DB;
+        const int nb_below = NB / DB - 1 - J;
         if (warp == 0) {
-            // (1) Cholesky of the 32 x 32 block at (o, o): lane i owns row o + i
-            const int i = lane;
-            for (int j = 0; j < DB; ++j) {
-                float d = A[(o + j) * XLD + o + j];
-                if (!(d > 0.0f)) { if (i == 0) s_bad = 1; d = 1.0f; }
-                const float inv = rsqrtf(d);
-                __syncwarp();
-                if (i > j) A[(o + i) * XLD + o + j] *= inv;
-                __syncwarp();
-                if (i > j) {
-                    const float lij = A[(o + i) * XLD + o + j];
-                    for (int q = j + 1; q <= i; ++q) A[(o + i) * XLD + o + q] -= lij * A[(o + q) * XLD + o + j];
-                }
-                __syncwarp();
-                if (i == j) A[(o + j) * XLD + o + j] = d * inv;
-                __syncwarp();
-            }
-            // (2) X_JJ = L_JJ^-1, lane c computes column c
-            const int c = lane;
-            X[(o + c) * XLD + o + c] = 1.0f / A[(o + c) * XLD + o + c];
-            for (int r = c + 1; r < DB; ++r) {
-                float acc = 0.0f;
-                for (int m = c; m < r; ++m) acc += A[(o + r) * XLD + o + m] * X[(o + m) * XLD + o + c];
-                X[(o + r) * XLD + o + c] = -acc / A[(o + r) * XLD + o + r];
-            }
+            if (potrf_chol32(A, LJ, s_rs, s_ri, o, lane) && lane == 0) s_bad = 1;
+        } else if (J == 0) {
+            // rows 32..127 in three batches of 32 rows (1024 float4, five per thread)
+            for (int r0 = DB; r0 < NB; r0 += DB) potrf_load_rows<5>(A, P, f.ldp, k, w, r0, r0 + DB, tid - 32, 224);
+        } else {
+            potrf_background(A, X, LT, XT, out, J - 1, warp - 1, 7, 1, lane);
         }
         __syncthreads();
-        const int nb_below = NB / DB - 1 - J;          // 32-row blocks below the panel
-        if (nb_below == 0) continue;
-        // (3) A_IJ <- A_IJ X_JJ^T for the blocks I below: warp per 32-row block, lane = column
-        for (int I = warp; I < nb_below; I += 8) {
-            const int ro = o + DB * (I + 1);
-            float xc[DB];
+        if (warp < nb_below) {
+            // (2) rows o + 32 (warp + 1) + lane, into A and transposed into LT
+            const int r = o + DB * (warp + 1) + lane;
+            float y[DB];
+            load_row32(A + r * XLD + o, y);
+            fsub32(y, LJ, s_rs + o);
+            store_row32(A + r * XLD + o, y);
 #pragma unroll
-            for (int m = 0; m < DB; ++m) xc[m] = X[(o + lane) * XLD + o + m];      // row lane of X_JJ
-            for (int r = 0; r < DB; ++r) {
-                float acc = 0.0f;
+            for (int m = 0; m < DB; ++m) LT[m * XLD + r] = y[m];
+        } else if (warp == 7) {
+            // (2') X_JJ = L_JJ^-1, lane c forms column c
+            float x[DB];
 #pragma unroll
-                for (int m = 0; m < DB; ++m) acc += A[(ro + r) * XLD + o + m] * xc[m];
-                __syncwarp();                              // the row is read before it is overwritten
-                A[(ro + r) * XLD + o + lane] = acc;
-            }
+            for (int p = 0; p < DB; ++p) x[p] = p == lane ? 1.0f : 0.0f;
+            fsub32(x, LJ, s_ri + o);
+#pragma unroll
+            for (int r = 0; r < DB; ++r) X[(o + r) * XLD + o + lane] = x[r];
+            store_row32(XT + lane * XTLD, x);
         }
         __syncthreads();
-        // (4) trailing update of the lower triangle below the panel, warp per 32 x 32 tile
-        const int ntiles = nb_below * (nb_below + 1) / 2;
-        for (int tIdx = warp; tIdx < ntiles; tIdx += 8) {
-            int I = 0;
-            while ((I + 1) * (I + 2) / 2 <= tIdx) ++I;
-            const int K = tIdx - I * (I + 1) / 2;          // K <= I
-            const int ro = o + DB * (I + 1), co = o + DB * (K + 1);
-            float bc[DB];
-#pragma unroll
-            for (int m = 0; m < DB; ++m) bc[m] = A[(co + lane) * XLD + o + m];      // L_KJ row lane
-#pragma unroll 4
-            for (int r = 0; r < DB; ++r) {
-                if (I == K && lane > r) continue;
-                float acc = 0.0f;
-#pragma unroll
-                for (int m = 0; m < DB; ++m) acc += A[(ro + r) * XLD + o + m] * bc[m];
-                A[(ro + r) * XLD + co + lane] -= acc;
-            }
+        if (nb_below > 0) {
+            // (3) the next diagonal tile, 8 rows per warp
+            if (warp < 4) chunk8_atb_sub(LT + o + DB, XLD, LT + o + DB, XLD, A + (o + DB) * XLD + o + DB, XLD, warp, lane);
+            __syncthreads();
         }
-        __syncthreads();
     }
+    // the last X row block, the last panel of L (warps left over), then the last inverse rows
+    potrf_background(A, X, LT, XT, out, NB / DB - 1, warp, 8, 0, lane);
+    if (warp >= NB / DB - 1) potrf_store_panel(A, out.P, out.ldp, k, w, NB / DB - 1, out.rnd, 32 * (warp - (NB / DB - 1)) + lane, 32 * (8 - (NB / DB - 1)));
+    __syncthreads();
+    potrf_store_inverse(X, out.D, w, NB / DB - 1, out.rnd, tid, 256);
     if (tid == 0 && s_bad) {
         atomicExch(&err[ERR_NOT_SPD], 1);
         atomicMin(&err[ERR_NOT_SPD_NODE], f.node);
         bad_front[f.node] = 1;
-    }
-    // (5) off-diagonal blocks of X, block row by block row: T = sum_{J<=K<I} L_IK X_KJ into
-    // X_IJ, then X_IJ = -X_II T (a warp per block, lane = column)
-    for (int I = 1; I < NB / DB; ++I) {
-        for (int J = warp; J < I; J += 8) {
-            // T = sum_K L_IK X_KJ, accumulated in place in X_IJ (zero so far), lane = column
-            float* XIJ = X + (DB * I) * XLD + DB * J + lane;
-            for (int K = J; K < I; ++K) {
-                float xc[DB];
-#pragma unroll
-                for (int m = 0; m < DB; ++m) xc[m] = X[(DB * K + m) * XLD + DB * J + lane];
-                for (int r = 0; r < DB; ++r) {
-                    float acc = 0.0f;
-#pragma unroll
-                    for (int m = 0; m < DB; ++m) acc += A[(DB * I + r) * XLD + DB * K + m] * xc[m];
-                    XIJ[r * XLD] += acc;
-                }
-            }
-            // X_IJ = -X_II T, rows from the last up: row r needs T's rows m <= r only
-            for (int r = DB - 1; r >= 0; --r) {
-                float acc = 0.0f;
-                for (int m = 0; m <= r; ++m) acc += X[(DB * I + r) * XLD + DB * I + m] * XIJ[m * XLD];
-                XIJ[r * XLD] = -acc;
-            }
-        }
-        __syncthreads();
-    }
-    const bool rnd = round_tf32 != 0;
-    float* D = (float*)f.Dinv + (int64_t)(k / NB) * NB * NB;
-    for (int e = tid; e < NB * NB; e += 256) {
-        const int i = e / NB, c = e % NB;
-        if (i < w && c <= i) P[(int64_t)(k + i) * f.ldp + k + c] = tf32_store(A[i * XLD + c], rnd);
-        D[e] = (i < w && c <= i) ? tf32_store(X[i * XLD + c], rnd) : 0.0f;
     }
 }
 
@@ -997,7 +1275,7 @@ static int ensure_chain(Handle& h) {
 static int factor_level_tc(Handle& h, int li, bool lookahead) {
     Level& L = h.levels[li];
     const size_t es = 4;
-    const size_t potrf_smem = (size_t)2 * NB * XLD * sizeof(float);
+    const size_t potrf_smem = POTRF_BLK_SMEM;
     RSD_CUDA_TRY(cudaFuncSetAttribute(k_potrf_diag_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)potrf_smem));
     const int nf = (int)L.fronts.size();
     if (lookahead) RSD_TRY(ensure_chain(h));
@@ -1257,7 +1535,7 @@ int run_factor_level(Handle& h, int li) {
     // task buffer for this level: one slot per front per launch kind
     GemmTask* d_tasks = nullptr;
     RSD_CUDA_TRY(cudaMallocAsync((void**)&d_tasks, sizeof(GemmTask) * L.fronts.size() * 2 + 64, h.stream));
-    const size_t potrf_smem = f64 ? (size_t)NB * DLD * es + (size_t)2 * NB * es : (size_t)2 * NB * XLD * sizeof(float);
+    const size_t potrf_smem = f64 ? (size_t)NB * DLD * es + (size_t)2 * NB * es : POTRF_BLK_SMEM;
     const size_t trsm_smem = (size_t)NB * NB * es + (size_t)TR_ROWS * (NB + 1) * es;
     if (f64) {
         RSD_CUDA_TRY(cudaFuncSetAttribute(k_potrf_diag<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)potrf_smem));
