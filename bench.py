@@ -398,9 +398,13 @@ def main() -> None:
     clocks = Clocks(_bus_id(torch))
     l0 = rsd.launch_count()
     barrier()
-    ms, t_setup, t_solve, res = timed_steps(torch, step(args.form, profile=True), args.steps)
+    ms, t_setup, t_solve, res = timed_steps(torch, step(args.form), args.steps)
     barrier()
     launches = (rsd.launch_count() - l0) // args.steps
+    # the per-kernel breakdown and the roofline come from the same number of steps timed
+    # again with CUDA events around every launch (a few per cent slower, not the headline)
+    ms_prof, _, _, res_prof = timed_steps(torch, step(args.form, profile=True), args.steps)
+    barrier()
     clk = clocks.stop()
     if world > 1:
         t = torch.tensor([ms], device="cuda")
@@ -408,10 +412,6 @@ def main() -> None:
         ms = float(t.item())
     value = world * n_dof / (ms / 1e3)
     stats = [r[0] for r in res]
-    agg = None
-    for r in res:
-        agg = prof_add(agg, r[1])
-    info = res[-1][2]
 
     # ---- end to end through the C ABI from pinned host buffers ------------------------
     src = probs if batched else [prob]
@@ -461,8 +461,9 @@ def main() -> None:
         bwaves = [bprobs[i:i + args.wave] for i in range(0, len(bprobs), args.wave)]
         PREC["batched"] = dict(prec_leaf=rsd.RSD_PREC_BF16, prec_mid=rsd.RSD_PREC_BF16, prec_root=rsd.RSD_PREC_BF16)
         batched_step(bwaves, "batched")()              # warm-up
-        msb, tsb, tvb, rb = timed_steps(torch, batched_step(bwaves, "batched", profile=True), 2)
-        mixed_b = form_record(rb, msb, tsb, tvb, bdof, 2, pk, peak_rec, "mixed (BF16 operands)")
+        msb, tsb, tvb, rb = timed_steps(torch, batched_step(bwaves, "batched"), 2)
+        prof_b = timed_steps(torch, batched_step(bwaves, "batched", profile=True), 2)
+        mixed_b = form_record(rb, msb, tsb, tvb, bdof, 2, pk, peak_rec, "mixed (BF16 operands)", prof=(prof_b[3], prof_b[0]))
         mixed_b["steps"] = 2
         mixed_b["warmup"] = 1
         sample = bwaves[0][:BATCH_FP64_SAMPLE]
@@ -482,8 +483,9 @@ def main() -> None:
         ework, _ = make_workload("elasticity97")
         eprob = rsd.grid_problem_elastic(ework["n"], ework["depth"], ework["E_leaf"], ELASTIC_NU, ework["f"])
         single_step(eprob, "mixed")()                 # warm-up
-        mse, tse, tve, re_ = timed_steps(torch, single_step(eprob, "mixed", profile=True), 2)
-        elastic_rec = form_record(re_, mse, tse, tve, eprob["n_dof"], 2, pk, peak_rec, "mixed")
+        mse, tse, tve, re_ = timed_steps(torch, single_step(eprob, "mixed"), 2)
+        prof_e = timed_steps(torch, single_step(eprob, "mixed", profile=True), 2)
+        elastic_rec = form_record(re_, mse, tse, tve, eprob["n_dof"], 2, pk, peak_rec, "mixed", prof=(prof_e[3], prof_e[0]))
         elastic_rec.update(workload=(f"elasticity97: 3-D linear elasticity (3 DOF/node), {ework['n']}^3 nodes, "
                                      f"trilinear hex, E per leaf log-uniform [1, 1e3], nu = {ELASTIC_NU}, "
                                      f"{8 ** ework['depth']} leaves (depth {ework['depth']})"),
@@ -493,14 +495,15 @@ def main() -> None:
     paper_rec = None
     if single and not args.no_paper and not batched and args.mode == "exact" and args.form == "mixed":
         single_step(prob, "mixed", m=rsd.RSD_MODE_PAPER, gamma=8)()          # warm-up
-        msp, tsp, tvp, rp = timed_steps(torch, single_step(prob, "mixed", profile=True, m=rsd.RSD_MODE_PAPER, gamma=8), 1)
-        paper_rec = form_record(rp, msp, tsp, tvp, n_dof, 1, pk, peak_rec, "mixed")
+        msp, tsp, tvp, rp = timed_steps(torch, single_step(prob, "mixed", m=rsd.RSD_MODE_PAPER, gamma=8), 1)
+        prof_p = timed_steps(torch, single_step(prob, "mixed", profile=True, m=rsd.RSD_MODE_PAPER, gamma=8), 1)
+        paper_rec = form_record(rp, msp, tsp, tvp, n_dof, 1, pk, peak_rec, "mixed", prof=(prof_p[3], prof_p[0]))
         paper_rec.update(mode="paper (Algorithm 2, V-hat truncation)", gamma=8, krylov="FGMRES(30)", steps=1, warmup=1)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
-    head = form_record(res, ms, t_setup, t_solve, n_dof, args.steps, pk, peak_rec, args.form)
+    head = form_record(res, ms, t_setup, t_solve, n_dof, args.steps, pk, peak_rec, args.form, prof=(res_prof, ms_prof))
     roof = head.pop("roofline")
     wkey = f"{args.workload}/{args.form}/{args.mode}" if args.n is None and args.depth is None else "scaled"
     roof["traffic"] = recorded_traffic(roof.get("kernel"), wkey)
@@ -553,11 +556,13 @@ def main() -> None:
         dist.destroy_process_group()
 
 
-def form_record(res, ms, t_setup, t_solve, n_dof, steps, pk, peak_rec, form) -> dict:
-    """Throughput, setup/solve split and rooflines of one form's timed steps."""
+def form_record(res, ms, t_setup, t_solve, n_dof, steps, pk, peak_rec, form, prof=None) -> dict:
+    """Throughput, setup/solve split and rooflines of one form's timed steps.  prof = (results,
+    ms per step) of the same steps timed again with per-launch events: the kernel classes
+    come from there when given, else from `res` (which then carries the events itself)."""
     stats = [r[0] for r in res]
     agg = None
-    for r in res:
+    for r in (prof[0] if prof is not None else res):
         agg = prof_add(agg, r[1])
     info = res[-1][2]
     classes = {k: v for k, v in agg.items() if isinstance(v, dict) and "ms" in v}
@@ -626,6 +631,7 @@ def form_record(res, ms, t_setup, t_solve, n_dof, steps, pk, peak_rec, form) -> 
         "iterations": [s["iterations"] for s in stats], "relres": [s["relres"] for s in stats],
         "roofline": roof, "apply_roofline": apply_roof,
         "detail": {"ms_by_kernel_class": {k: round(v, 3) for k, v in per.items()},
+                   "ms_per_step_with_launch_events": prof[1] if prof is not None else ms,
                    "host_analysis_ms": agg.get("host_analysis_ms", 0.0) / steps,
                    "host_issue_ms": agg.get("host_issue_ms", 0.0) / steps,
                    "factor_bytes": info["factor_bytes"], "setup_flops": info["setup_flops"],
