@@ -326,6 +326,15 @@ int rsd_front_factor_upper(rsd_handle h, int32_t node, double* out);
  * fronts, paper mode).                                                                */
 int rsd_front_factor16(rsd_handle h, int32_t node, double* out);
 
+/* rsd_front_dinv -- the inverted diagonal blocks of node's front that the substitution
+ * sweeps apply (Eqs. 3.2-3.3 split into NB-row blocks, NB = 128): block k of L_t's
+ * diagonal, inverted, as stored (rounded to TF32 on tensor-core levels).  Writes
+ * nd x 128 x 128 doubles (host, caller-owned), block k row-major at k * 128 * 128, with
+ * nd = ceil(s / 128) and zeros above the diagonal and past s.  Synchronises the stream.
+ * Errors: RSD_ERR_ARG for a bad node or a level that is not factored (paper mode's leaf
+ * levels are; its interface levels are solved from S~).                              */
+int rsd_front_dinv(rsd_handle h, int32_t node, double* out);
+
 /* rsd_profile -- synchronise the handle's stream and sum the profile recorded since
  * setup or the last reset (all zeros unless rsd_options.profile was set).  reset != 0
  * clears it afterwards.                                                               */

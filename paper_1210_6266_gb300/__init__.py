@@ -330,6 +330,15 @@ class RSD:
         return out[: (s + b) * s].reshape(s + b, s)
 
 
+    def front_dinv(self, node: int) -> np.ndarray:
+        """The inverted 128 x 128 diagonal blocks the sweeps apply, shape (nd, 128, 128)
+        (rsd_front_dinv)."""
+        s, _, _ = self.front_dims(node)
+        nd = (s + 127) // 128
+        out = np.empty(max(nd, 1) * 128 * 128, dtype=np.float64)
+        check(_lib.load().rsd_front_dinv(self._h, node, out.ctypes.data), "rsd_front_dinv")
+        return out[: nd * 128 * 128].reshape(nd, 128, 128)
+
 class DiffusionSolve(torch.autograd.Function):
     """u = K(exp(m))^-1 b for -div(kappa grad u) = f on the n^3 grid, differentiable in the
     per-element log-coefficient m and the load b.  Forward: rsd_grid_exp, rsd_grid_assemble,

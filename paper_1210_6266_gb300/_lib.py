@@ -38,7 +38,7 @@ RSD_MEM_DEVICE = 1
 # every function include/rsd.h declares (checked by the tests)
 EXPORTS = [
     "rsd_setup", "rsd_apply", "rsd_solve", "rsd_check", "rsd_destroy", "rsd_strerror",
-    "rsd_get_info", "rsd_front_dims", "rsd_front_dofs", "rsd_front_map", "rsd_front_factor", "rsd_front_factor16",
+    "rsd_get_info", "rsd_front_dims", "rsd_front_dofs", "rsd_front_map", "rsd_front_factor", "rsd_front_factor16", "rsd_front_dinv",
     "rsd_grid_sizes", "rsd_grid_assemble", "rsd_grid_load", "rsd_grid_partition",
     "rsd_profile", "rsd_launch_count", "rsd_apply_static", "rsd_last_error_detail",
     "rsd_release_cache", "rsd_setup_batched", "rsd_solve_adjoint", "rsd_grid_exp",
@@ -122,6 +122,7 @@ def load() -> C.CDLL:
             "rsd_front_map": (C.c_int, [P, C.c_int32, P]),
             "rsd_front_factor": (C.c_int, [P, C.c_int32, P]),
             "rsd_front_factor16": (C.c_int, [P, C.c_int32, P]),
+            "rsd_front_dinv": (C.c_int, [P, C.c_int32, P]),
             "rsd_front_factor_upper": (C.c_int, [P, C.c_int32, P]),
             "rsd_grid_sizes": (C.c_int, [C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
             "rsd_grid_assemble": (C.c_int, [C.c_int32, P, P, P, P, P]),

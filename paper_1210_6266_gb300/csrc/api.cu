@@ -1106,7 +1106,9 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
         // forward items: key = block index (I blocks, then B blocks), fronts interleaved
         // a diagonal item covers gd consecutive blocks: forward groups start at multiples
         // of gd from the top-left, backward groups are counted from the last block up
-        const int gd = sweep_group(L);
+        L.cl_sweep = L.h16 && !h.lu && !L.fronts.empty() &&
+                     std::all_of(L.fronts.begin(), L.fronts.end(), [](const FrontDesc& f) { return f.b == 0; });
+        const int gd = sweep_item_blocks(L);
         std::vector<std::pair<int, int>> fw, bw;   // (key, item)
         for (size_t sidx = 0; sidx < L.fronts.size(); ++sidx) {
             const FrontDesc& f = L.fronts[sidx];
@@ -1670,6 +1672,25 @@ extern "C" int rsd_front_factor16(rsd_handle hh, int32_t node, double* out) {
             const bool read = r >= f.s || c / NB < r / NB;       // what the sweeps read
             out[(size_t)r * f.s + c] = read ? (double)__half2float(q[(size_t)r * f.ldp + c]) * (double)rs[f.N + r] : 0.0;
         }
+    return RSD_OK;
+}
+
+extern "C" int rsd_front_dinv(rsd_handle hh, int32_t node, double* out) {
+    if (!hh || !out || node < 0 || node >= hh->h.n_nodes) return RSD_ERR_ARG;
+    Handle& h = hh->h;
+    const Level& L = h.levels[h.node_level[node]];
+    if (!L.factored) return RSD_ERR_ARG;
+    const FrontDesc& f = L.fronts[h.node_slot[node]];
+    RSD_CUDA_TRY(cudaStreamSynchronize(h.stream));
+    const size_t n = (size_t)f.nd * NB * NB;
+    if (!n) return RSD_OK;
+    if (is_fp64(L.prec)) {
+        RSD_CUDA_TRY(cudaMemcpy(out, f.Dinv, n * sizeof(double), cudaMemcpyDeviceToHost));
+    } else {
+        std::vector<float> buf(n);
+        RSD_CUDA_TRY(cudaMemcpy(buf.data(), f.Dinv, n * sizeof(float), cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < n; ++i) out[i] = buf[i];
+    }
     return RSD_OK;
 }
 

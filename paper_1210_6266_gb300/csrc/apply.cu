@@ -618,6 +618,406 @@ __global__ void __launch_bounds__(AT, GD == 1 ? 2 : 1) k_bwd_sweep(const FrontDe
     }
 }
 
+// ---- cluster sweeps (levels of fronts without B rows, FP16 factor copy) ---------------
+// A front with many diagonal blocks (the root) makes the sweeps chain-bound: every block
+// waits for the previous one through global memory (the producer's fence, the flag poll,
+// the vector reread), several microseconds per block.  Here a cluster of SWEEP_CL CTAs
+// takes SWEEP_CL consecutive diagonal blocks, one each.  A CTA streams its own row block
+// (forward) or column block (backward) over the blocks of earlier clusters as the
+// per-CTA kernels do, waiting on the front's progress counter; the chain inside the
+// cluster then runs through distributed shared memory: a CTA stores its finished block
+// into the shared memory of each later CTA of the cluster and raises a per-sender counter
+// there with a cluster-scope release; a CTA waits on its own counters (bounded, like every
+// wait here) and reads the blocks locally.  The block, and the front's vector
+// right-hand side it needs, are in shared memory before the chain reaches the CTA, so a
+// hand-off costs a few hundred nanoseconds.  One hand-off in SWEEP_CL goes through global
+// memory: every block still raises the front's progress counter, in block order (after
+// its push and a fence), which the later clusters wait on.  Work items are taken with a ticket by the cluster's first CTA,
+// so a cluster only waits on items with smaller tickets, held by running clusters.
+
+__device__ __forceinline__ uint32_t cl_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// all threads of every CTA of the cluster (uniform control flow only)
+__device__ __forceinline__ void cl_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t cl_map(const void* p, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ int cl_ld(uint32_t a) {
+    int v;
+    asm volatile("ld.shared::cluster.b32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void cl_st_remote(uint32_t a, float v) {
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+
+__device__ __forceinline__ void cl_st_release_remote(uint32_t a, int v) {
+    asm volatile("st.release.cluster.shared::cluster.b32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int cl_ld_acquire_local(const int* p) {
+    int v;
+    asm volatile("ld.acquire.cluster.shared::cta.b32 %0, [%1];" : "=r"(v) : "r"((uint32_t)__cvta_generic_to_shared(p)) : "memory");
+    return v;
+}
+
+// A finished block goes to the later CTAs of the cluster: the thread holding entry `row`
+// (mine) stores it into in[rank][row] of each CTA rank + 1 .. last - 1 (distributed shared
+// memory), the next CTA first; after the barrier thread q raises got[rank] = ep in CTA
+// rank + 1 + q with a cluster-scope release, which orders the whole CTA's stores before
+// it (one thread per receiver, so no receiver waits for another's flag).
+__device__ void cl_push(float val, int row, bool mine, float (*in)[NB], int* got, uint32_t rank, int last, int ep) {
+    if (mine)
+        for (int m = (int)rank + 1; m < last; ++m) cl_st_remote(cl_map(&in[rank][row], (uint32_t)m), val);
+    __syncthreads();
+    const int m = (int)rank + 1 + (int)threadIdx.x;
+    if (m < last) cl_st_release_remote(cl_map(&got[rank], (uint32_t)m), ep);
+}
+
+// Wait (bounded) until CTA `peer` has pushed its block of epoch `ep` into in[peer].
+__device__ void cl_wait_in(const int* got, uint32_t peer, int ep, int* err, long long limit) {
+    if (threadIdx.x == 0 && cl_ld_acquire_local(&got[peer]) < ep) {
+        const long long t0 = clock64();
+        while (cl_ld_acquire_local(&got[peer]) < ep) {
+            if (ld_volatile(&err[ERR_TIMEOUT]) || clock64() - t0 > limit) {
+                atomicExch(&err[ERR_TIMEOUT], 1);
+                break;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// Raise a front's progress counter from `from` to `to` once it holds `from`: the blocks
+// publish in order, so a counter value covers every block below it (each block's stores
+// are fenced before its own step; a later block of the cluster can be done first, having
+// received its predecessor through shared memory).  Thread 0; bounded like every wait.
+__device__ void cl_publish_in_order(int* flag, int from, int to, int* err, long long limit) {
+    if (threadIdx.x != 0) return;
+    if (atomicCAS(flag, from, to) == from) return;
+    const long long t0 = clock64();
+    for (;;) {
+        if (ld_volatile(flag) == from && atomicCAS(flag, from, to) == from) return;
+        if (ld_volatile(&err[ERR_TIMEOUT]) || clock64() - t0 > limit) {
+            atomicExch(&err[ERR_TIMEOUT], 1);
+            atomicMax(flag, to);
+            return;
+        }
+        __nanosleep(32);
+    }
+}
+
+// The item of the cluster: the first CTA's ticket, read by every CTA (two cluster
+// barriers: the ticket is in place, then read everywhere before it changes).
+__device__ int cl_ticket(int* s_item, int* s_it, int* ticket, uint32_t rank) {
+    if (rank == 0 && threadIdx.x == 0) *s_item = atomicAdd(ticket, 1);
+    cl_sync();
+    if (threadIdx.x == 0) *s_it = cl_ld(cl_map(s_item, 0));
+    cl_sync();
+    return *s_it;
+}
+
+// The factor tiles a CTA streams (NB x NB FP16, row-major) pass through a ring of
+// CL_RING shared-memory stages filled with cp.async CL_RING - 1 steps ahead; a step's
+// consumer reads them with lanes over four columns and warps over 16 rows.  A stage also
+// carries the step's vector block (and its row factors, backward) when that block was
+// already published when the stage was filled, which it is for all but the last blocks.
+constexpr int CL_RING = 6;
+constexpr int CL_STAGE = NB * NB * 2 + 2 * NB * 4;    // tile, then two NB-float vectors
+constexpr int CL_SMEM = CL_RING * CL_STAGE;
+
+__device__ __forceinline__ void cp16(uint32_t dst, const void* src, bool in) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(in ? 16 : 0) : "memory");
+}
+
+// Tile rows [row0, row0 + NB) (those below row_end), columns [col0, col0 + NB) (those
+// starting below col_end) of the FP16 copy into a ring stage; the rest is zero-filled.
+// With nv > 0 the stage's vectors receive a[e0 .. e0 + NB) (and b[..], nv = 2); callers
+// pass whole blocks only (e0 + NB <= e_end).
+__device__ __forceinline__ void cl_issue_tile(unsigned char* stage, const FrontDesc& f, int row0, int row_end, int col0, int col_end,
+                                              int nv, const float* a, const float* b, int e0, int e_end) {
+    const uint32_t d0 = (uint32_t)__cvta_generic_to_shared(stage);
+    const __half* P = (const __half*)f.P16;
+    for (int c = threadIdx.x; c < NB * 16; c += AT) {
+        const int row = c >> 4, q = c & 15;
+        const bool in = row0 + row < row_end && col0 + 8 * q < col_end;
+        cp16(d0 + (uint32_t)(row * NB + 8 * q) * 2, in ? (const void*)(P + (int64_t)(row0 + row) * f.ldp + col0 + 8 * q) : (const void*)P, in);
+    }
+    // a (a front vector: 16-byte aligned, as is e0) in 16-byte chunks; b (row factors,
+    // which start N floats into their region, so only 4-byte aligned) entry by entry
+    if (nv >= 1 && (int)threadIdx.x < NB / 4)
+        cp16(d0 + (uint32_t)(NB * NB * 2 + 16 * threadIdx.x), a + e0 + 4 * threadIdx.x, true);
+    if (nv >= 2 && (int)threadIdx.x < NB)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d0 + (uint32_t)(NB * NB * 2 + NB * 4 + 4 * threadIdx.x)),
+                     "l"(b + e0 + threadIdx.x) : "memory");
+}
+
+// Forward: CTA `rank` solves diagonal block blk = g0 + rank of the item's front: steps
+// 0 .. blk-1 take the column blocks in order (those of earlier clusters after the front's
+// progress counter, those of this cluster from the earlier CTAs' shared memory); a lane
+// keeps partial sums of its warp's 16 rows over its four columns, reduced once:
+// acc_r = sum_c P16[r, c] y_c, t_r = v_r - ri_r acc_r, y = Dinv t (two threads per row).
+__global__ void __cluster_dims__(SWEEP_CL, 1, 1) __launch_bounds__(AT, 1)
+k_fwd_sweep_cl(const FrontDesc* __restrict__ fronts, const int* __restrict__ items, int n_items,
+               int* __restrict__ ticket, int* __restrict__ err, long long wait) {
+    __shared__ int s_item, s_it, s_flag;
+    __shared__ int s_got[SWEEP_CL];                  // epoch of the block pushed by each earlier CTA
+    __shared__ __align__(16) float s_in[SWEEP_CL][NB];   // the blocks pushed by the earlier CTAs
+    __shared__ __align__(16) float s_t[NB];
+    __shared__ float s_v[NB], s_ri[NB];              // the block's v and row factors, read early
+    extern __shared__ __align__(16) unsigned char cl_smem[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t rank = cl_rank();
+    if (tid < SWEEP_CL) s_got[tid] = 0;
+    if (tid == 0) s_item = 0;
+    int ep = 0;
+    for (;;) {
+        const int it = cl_ticket(&s_item, &s_it, ticket, rank);
+        ++ep;
+        if (it >= n_items) return;
+        const int slot = items[it] >> 16, g0 = items[it] & 0xffff;
+        const FrontDesc f = fronts[slot];
+        const int blk = g0 + (int)rank;
+        if (blk >= f.nd) continue;
+        const int r0 = blk * NB, w = min(NB, f.s - r0), rend = r0 + w;
+        float* v = (float*)f.vec;
+        const int r = tid >> 1, hf = tid & 1;
+        float4 dv[16];                                // Dinv_blk[r, 64 hf .. 64 hf + 63]
+        {
+            const float4* D = reinterpret_cast<const float4*>((const float*)f.Dinv + (int64_t)blk * NB * NB + r * NB + hf * 64);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) dv[k] = __ldg(D + k);
+        }
+        if (tid < NB) {                               // off the chain: loaded while the steps run
+            s_v[tid] = tid < w ? __ldcg(v + r0 + tid) : 0.f;
+            s_ri[tid] = tid < w ? f.ri[r0 + tid] : 0.f;
+        }
+        const int nsteps = blk;                       // column blocks 0 .. blk - 1
+        int seen = 0;
+        unsigned ymask = 0;                           // bit k: stage k holds its step's y block
+        auto issue = [&](int q) {
+            const int k = q % CL_RING;
+            const bool yin = q < g0 && seen >= q + 1;     // (blocks before g0 are whole)
+            cl_issue_tile(cl_smem + k * CL_STAGE, f, r0, rend, q * NB, f.s, yin ? 1 : 0, v, v, q * NB, f.s);
+            ymask = yin ? (ymask | (1u << k)) : (ymask & ~(1u << k));
+        };
+#pragma unroll
+        for (int q = 0; q < CL_RING - 1; ++q) {
+            if (q < nsteps) issue(q);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        }
+        float acc[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) acc[u] = 0.f;
+        for (int i = 0; i < nsteps; ++i) {
+            asm volatile("cp.async.wait_group %0;" ::"n"(CL_RING - 2) : "memory");
+            const unsigned char* stg = cl_smem + (i % CL_RING) * CL_STAGE;
+            float4 y;
+            if (i < g0) {
+                const bool yin = (ymask >> (i % CL_RING)) & 1u;
+                if (!yin && seen < i + 1) seen = wait_flag(&f.flag[0], i + 1, err, &s_flag, wait);
+                __syncthreads();                      // the stage of step i is in place
+                y = yin ? reinterpret_cast<const float4*>(stg + NB * NB * 2)[lane]
+                        : __ldcg(reinterpret_cast<const float4*>(v + i * NB) + lane);
+            } else {
+                cl_wait_in(s_got, (uint32_t)(i - g0), ep, err, wait);
+                y = reinterpret_cast<const float4*>(s_in[i - g0])[lane];
+            }
+            const int q = i + CL_RING - 1;            // refill the stage freed by step i - 1
+            if (q < nsteps) issue(q);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            const __half* st = reinterpret_cast<const __half*>(stg) + (warp * 16) * NB + lane * 4;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const uint2 pq = *reinterpret_cast<const uint2*>(st + u * NB);
+                acc[u] = fmaf(h_lo(pq.x), y.x, acc[u]);
+                acc[u] = fmaf(h_hi(pq.x), y.y, acc[u]);
+                acc[u] = fmaf(h_lo(pq.y), y.z, acc[u]);
+                acc[u] = fmaf(h_hi(pq.y), y.w, acc[u]);
+            }
+        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int u = 0; u < 16; ++u) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
+        __syncthreads();                              // s_v and s_ri (written at the item's start) are in place
+        {
+            float mine = acc[0];                      // lane u < 16 takes row 16 warp + u
+#pragma unroll
+            for (int u = 1; u < 16; ++u) mine = lane == u ? acc[u] : mine;
+            const int rr = warp * 16 + lane;
+            if (lane < 16) s_t[rr] = rr < w ? s_v[rr] - mine * s_ri[rr] : 0.f;
+        }
+        __syncthreads();
+        float yq[4] = {0.f, 0.f, 0.f, 0.f};
+        {
+            const float4* t4 = reinterpret_cast<const float4*>(s_t + hf * 64);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const float4 t = t4[k];
+                yq[0] = fmaf(dv[k].x, t.x, yq[0]); yq[1] = fmaf(dv[k].y, t.y, yq[1]);
+                yq[2] = fmaf(dv[k].z, t.z, yq[2]); yq[3] = fmaf(dv[k].w, t.w, yq[3]);
+            }
+        }
+        float yr = (yq[0] + yq[1]) + (yq[2] + yq[3]);
+        yr += __shfl_xor_sync(0xffffffffu, yr, 1);
+        const bool rin = r < w;
+        // the later CTAs of the cluster first, then the later clusters
+        cl_push(rin ? yr : 0.f, r, hf == 0, s_in, s_got, rank, min(SWEEP_CL, f.nd - g0), ep);
+        if (hf == 0 && rin) {
+            __stcg(v + r0 + r, yr);
+            __threadfence();
+        }
+        __syncthreads();
+        cl_publish_in_order(&f.flag[0], blk, blk + 1, err, wait);
+    }
+}
+
+// Backward: CTA `rank` solves column block cbk = hi - rank (the item's code is hi, the
+// highest block): steps take the row blocks below it from the last up (those of earlier
+// clusters after the front's progress counter, those of this cluster from the CTAs above
+// in the cluster); lanes over four columns, warps over 16 rows:
+// acc_c = sum_rows P16[row, c] (ri_row x_row), t = v - acc, x = Dinv^T t.  A CTA leaves
+// ri_row x_row of its block for the CTAs below it in the cluster.
+__global__ void __cluster_dims__(SWEEP_CL, 1, 1) __launch_bounds__(AT, 1)
+k_bwd_sweep_cl(const FrontDesc* __restrict__ fronts, const int* __restrict__ items, int n_items,
+               int* __restrict__ ticket, int* __restrict__ err, double* __restrict__ z, long long wait) {
+    __shared__ int s_item, s_it, s_flag;
+    __shared__ int s_got[SWEEP_CL];                  // epoch of the block pushed by each earlier CTA
+    __shared__ __align__(16) float s_in[SWEEP_CL][NB];   // ri x of the blocks pushed by the earlier CTAs
+    __shared__ __align__(16) float s_c[2][NB];       // ri x of the step's row block
+    __shared__ __align__(16) float s_t[NB];
+    __shared__ __align__(16) float s_red[AW][NB];
+    __shared__ float s_v[NB], s_ri[NB];              // the block's v and row factors, read early
+    extern __shared__ __align__(16) unsigned char cl_smem[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int c4 = lane * 4;                          // this thread's four columns of the block
+    const uint32_t rank = cl_rank();
+    if (tid < SWEEP_CL) s_got[tid] = 0;
+    if (tid == 0) s_item = 0;
+    int ep = 0;
+    for (;;) {
+        const int it = cl_ticket(&s_item, &s_it, ticket, rank);
+        ++ep;
+        if (it >= n_items) return;
+        const int slot = items[it] >> 16, hi = items[it] & 0xffff;
+        const FrontDesc f = fronts[slot];
+        const int cbk = hi - (int)rank;
+        if (cbk < 0) continue;
+        const int c0 = cbk * NB, wc = min(NB, f.s - c0);
+        float* v = (float*)f.vec;
+        float4 dv[16];                                // Dinv_cbk[16 warp + u, c4 .. c4 + 3]
+        {
+            const float* D = (const float*)f.Dinv + (int64_t)cbk * NB * NB + (warp * 16) * NB + c4;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) dv[u] = __ldg(reinterpret_cast<const float4*>(D + u * NB));
+        }
+        if (tid < NB) {                               // off the chain: loaded while the steps run
+            s_v[tid] = tid < wc ? __ldcg(v + c0 + tid) : 0.f;
+            s_ri[tid] = tid < wc ? f.ri[c0 + tid] : 0.f;
+        }
+        // step i takes row block rb(i): the earlier clusters' blocks nd-1 .. hi+1, then hi .. cbk+1
+        const int nsteps = f.nd - 1 - cbk, n_glob = f.nd - 1 - hi;
+        auto rb_of = [&](int i) { return f.nd - 1 - i; };
+        int seen = 0;
+        unsigned xmask = 0;                           // bit k: stage k holds its step's x and ri
+        auto issue = [&](int q) {
+            const int k = q % CL_RING, rb = rb_of(q);
+            const bool xin = q < n_glob && seen >= f.nd - rb && (rb + 1) * NB <= f.s;   // whole blocks only
+            cl_issue_tile(cl_smem + k * CL_STAGE, f, rb * NB, f.s, c0, f.s, xin ? 2 : 0, v, f.ri, rb * NB, f.s);
+            xmask = xin ? (xmask | (1u << k)) : (xmask & ~(1u << k));
+        };
+#pragma unroll
+        for (int q = 0; q < CL_RING - 1; ++q) {
+            if (q < nsteps) issue(q);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        }
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int i = 0; i < nsteps; ++i) {
+            asm volatile("cp.async.wait_group %0;" ::"n"(CL_RING - 2) : "memory");
+            const int rb = rb_of(i);
+            const unsigned char* stg = cl_smem + (i % CL_RING) * CL_STAGE;
+            const float* xs;                          // the step's x (ri applied when sc is null)
+            const float* sc = nullptr;
+            if (i < n_glob) {
+                const bool xin = (xmask >> (i % CL_RING)) & 1u;
+                if (xin) {
+                    xs = reinterpret_cast<const float*>(stg + NB * NB * 2);
+                    sc = xs + NB;
+                } else {
+                    const int need = f.nd - rb;
+                    if (seen < need) seen = wait_flag(&f.flag[1], need, err, &s_flag, wait);
+                    if (tid < NB) {
+                        const int row = rb * NB + tid;
+                        s_c[i & 1][tid] = row < f.s ? __ldcg(v + row) * f.ri[row] : 0.f;
+                    }
+                    xs = s_c[i & 1];
+                }
+                __syncthreads();                      // the stage and the x of step i are in place
+            } else {
+                cl_wait_in(s_got, (uint32_t)(i - n_glob), ep, err, wait);
+                xs = s_in[i - n_glob];
+            }
+            const int q = i + CL_RING - 1;
+            if (q < nsteps) issue(q);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            const __half* st = reinterpret_cast<const __half*>(stg) + (warp * 16) * NB + c4;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const uint2 pq = *reinterpret_cast<const uint2*>(st + u * NB);
+                const float x = sc ? xs[warp * 16 + u] * sc[warp * 16 + u] : xs[warp * 16 + u];
+                acc[0] = fmaf(h_lo(pq.x), x, acc[0]); acc[1] = fmaf(h_hi(pq.x), x, acc[1]);
+                acc[2] = fmaf(h_lo(pq.y), x, acc[2]); acc[3] = fmaf(h_hi(pq.y), x, acc[3]);
+            }
+        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        *reinterpret_cast<float4*>(&s_red[warp][c4]) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        __syncthreads();
+        if (tid < NB) {
+            float sum = 0.f;
+#pragma unroll
+            for (int q = 0; q < AW; ++q) sum += s_red[q][tid];
+            s_t[tid] = tid < wc ? s_v[tid] - sum : 0.f;
+        }
+        __syncthreads();
+        float xp[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const float t = s_t[warp * 16 + u];
+            xp[0] = fmaf(dv[u].x, t, xp[0]); xp[1] = fmaf(dv[u].y, t, xp[1]);
+            xp[2] = fmaf(dv[u].z, t, xp[2]); xp[3] = fmaf(dv[u].w, t, xp[3]);
+        }
+        *reinterpret_cast<float4*>(&s_red[warp][c4]) = make_float4(xp[0], xp[1], xp[2], xp[3]);
+        __syncthreads();
+        float x = 0.f;
+        if (tid < NB) {
+#pragma unroll
+            for (int q = 0; q < AW; ++q) x += s_red[q][tid];
+        }
+        // the later CTAs of the cluster first, then the later clusters
+        cl_push(tid < wc ? x * s_ri[tid] : 0.f, tid, tid < NB, s_in, s_got, rank, min(SWEEP_CL, hi + 1), ep);
+        if (tid < wc) {
+            __stcg(v + c0 + tid, x);
+            z[f.I[c0 + tid]] = (double)x;
+            __threadfence();
+        }
+        __syncthreads();
+        cl_publish_in_order(&f.flag[1], f.nd - 1 - cbk, f.nd - cbk, err, wait);
+    }
+}
+
 // Bytes one sweep streams from the factor: the off-diagonal blocks of L and X (FP16 for a
 // level with the FP16 copy) and the inverted diagonal blocks.
 double level_factor_bytes(const Level& L) {
@@ -685,6 +1085,61 @@ void launch_bwd(int gd, bool h16, int grid, cudaStream_t st, const FrontDesc* fr
     k_bwd_sweep<T, A, 1, false><<<grid, AT, sweep_dsm<T, 1, false>(), st>>>(fr, items, n, tk, err, z, wait);
 }
 
+// Clusters of the cluster sweeps resident at once on the current device (the persistent
+// grid), looked up once per device.
+int cl_grid(int n_items, int* out) {
+    static int max_cl[64] = {};
+    int dev = 0;
+    RSD_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return RSD_ERR_ARG;
+    if (!max_cl[dev]) {
+        RSD_CUDA_TRY(cudaFuncSetAttribute(k_fwd_sweep_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, CL_SMEM));
+        RSD_CUDA_TRY(cudaFuncSetAttribute(k_bwd_sweep_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, CL_SMEM));
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(SWEEP_CL * 64);
+        cfg.blockDim = dim3(AT);
+        cfg.dynamicSmemBytes = CL_SMEM;
+        int n1 = 0, n2 = 0;
+        RSD_CUDA_TRY(cudaOccupancyMaxActiveClusters(&n1, (void*)k_fwd_sweep_cl, &cfg));
+        RSD_CUDA_TRY(cudaOccupancyMaxActiveClusters(&n2, (void*)k_bwd_sweep_cl, &cfg));
+        max_cl[dev] = std::max(1, std::min(n1, n2));
+    }
+    *out = std::max(1, std::min(n_items, max_cl[dev]));
+    return RSD_OK;
+}
+
+// Upward / downward sweep kernel of a level: the cluster kernels on a cl_sweep level,
+// else the per-CTA kernels with the level's group size.
+template <typename T, typename A>
+int launch_fwd_level(const Level& L, int grid, cudaStream_t st, const FrontDesc* fr, const int* items, int n, int* tk,
+                     int* err, long long wait) {
+    if constexpr (sizeof(T) == 4) {
+        if (L.cl_sweep) {
+            int ncl = 0;
+            RSD_TRY(cl_grid(n, &ncl));
+            k_fwd_sweep_cl<<<ncl * SWEEP_CL, AT, CL_SMEM, st>>>(fr, items, n, tk, err, wait);
+            return RSD_OK;
+        }
+    }
+    launch_fwd<T, A>(sweep_group(L), L.h16, grid, st, fr, items, n, tk, err, wait);
+    return RSD_OK;
+}
+
+template <typename T, typename A>
+int launch_bwd_level(const Level& L, int grid, cudaStream_t st, const FrontDesc* fr, const int* items, int n, int* tk,
+                     int* err, double* z, long long wait) {
+    if constexpr (sizeof(T) == 4) {
+        if (L.cl_sweep) {
+            int ncl = 0;
+            RSD_TRY(cl_grid(n, &ncl));
+            k_bwd_sweep_cl<<<ncl * SWEEP_CL, AT, CL_SMEM, st>>>(fr, items, n, tk, err, z, wait);
+            return RSD_OK;
+        }
+    }
+    launch_bwd<T, A>(sweep_group(L), L.h16, grid, st, fr, items, n, tk, err, z, wait);
+    return RSD_OK;
+}
+
 template <typename T, typename A>
 int sweep_level(Handle& h, int li, bool forward, const double* r, double* z, int tk) {
     RSD_TRY((sweep_smem_setup<T, A>()));
@@ -714,8 +1169,8 @@ int sweep_level(Handle& h, int li, bool forward, const double* r, double* z, int
             const int drop = h.inject_drop_level == li && L.n_fwd_items > 1 ? 1 : 0;
             if (drop) h.inject_drop_level = -1;
             const int pi = prof_begin(h, K_FWD);
-            launch_fwd<T, A>(sweep_group(L), L.h16, grid, h.stream, L.d_fronts, L.d_fwd_items + drop, L.n_fwd_items - drop,
-                             h.d_ticket + tk, h.d_err, h.wait_cycles);
+            RSD_TRY((launch_fwd_level<T, A>(L, grid, h.stream, L.d_fronts, L.d_fwd_items + drop, L.n_fwd_items - drop,
+                                             h.d_ticket + tk, h.d_err, h.wait_cycles)));
             count_launch();
             prof_end(h, pi, fbytes / sizeof(T) * 2.0, fbytes);
         }
@@ -729,7 +1184,8 @@ int sweep_level(Handle& h, int li, bool forward, const double* r, double* z, int
             // nonsymmetric fronts: [U^T; Y^T] with (U_kk^T)^-1
             const FrontDesc* bf = L.d_fronts_bwd ? L.d_fronts_bwd : L.d_fronts;
             const int pi = prof_begin(h, K_BWD);
-            launch_bwd<T, A>(sweep_group(L), L.h16, grid, h.stream, bf, L.d_bwd_items, L.n_bwd_items, h.d_ticket + tk, h.d_err, z, h.wait_cycles);
+            RSD_TRY((launch_bwd_level<T, A>(L, grid, h.stream, bf, L.d_bwd_items, L.n_bwd_items, h.d_ticket + tk, h.d_err, z,
+                                             h.wait_cycles)));
             count_launch();
             prof_end(h, pi, fbytes / sizeof(T) * 2.0, fbytes);
         }
@@ -809,7 +1265,7 @@ int sweep_level_static(Handle& h, int li, bool forward, const double* r, double*
         count_launch();
         RSD_CUDA_TRY(cudaGetLastError());
         if (L.n_fwd_items) {
-            launch_fwd<T, A>(sweep_group(L), L.h16, grid, h.stream, fr, L.d_fwd_items, L.n_fwd_items, ticket, h.d_err, h.wait_cycles);
+            RSD_TRY((launch_fwd_level<T, A>(L, grid, h.stream, fr, L.d_fwd_items, L.n_fwd_items, ticket, h.d_err, h.wait_cycles)));
             count_launch();
         }
     } else {
@@ -817,7 +1273,7 @@ int sweep_level_static(Handle& h, int li, bool forward, const double* r, double*
         count_launch();
         RSD_CUDA_TRY(cudaGetLastError());
         if (L.n_bwd_items) {
-            launch_bwd<T, A>(sweep_group(L), L.h16, grid, h.stream, fr, L.d_bwd_items, L.n_bwd_items, ticket, h.d_err, z, h.wait_cycles);
+            RSD_TRY((launch_bwd_level<T, A>(L, grid, h.stream, fr, L.d_bwd_items, L.n_bwd_items, ticket, h.d_err, z, h.wait_cycles)));
             count_launch();
         }
     }

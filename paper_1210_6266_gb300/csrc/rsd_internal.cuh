@@ -134,6 +134,10 @@ struct Level {
     int* d_child_slots = nullptr;
     size_t bytes_P = 0, bytes_U = 0;
     bool h16 = false;                    // the sweeps read the FP16 factor copy (P16, rs, ri)
+    // every front of the level has no B rows (the root level) and the sweeps read the FP16
+    // copy: the sweeps run on clusters of SWEEP_CL CTAs, one diagonal block each, and the
+    // work lists group SWEEP_CL diagonal blocks per item
+    bool cl_sweep = false;
     // operand format of the long-K Schur updates (TC_OP_*): with a 16-bit format the
     // fronts carry its row-scaled copy (P16, rs, ri), written panel by panel
     int op16 = TC_OP_TF32;
@@ -179,6 +183,10 @@ inline bool copy16_level(const Level& L) { return L.h16 || L.op16 != TC_OP_TF32;
 // fronts keep one block per item, whose smaller footprint lets more CTAs stream the
 // factor at once (an FP64 pair would not fit in shared memory).
 inline int sweep_group(const Level& L) { return (!is_fp64(L.prec) && L.fronts.size() == 1) ? 2 : 1; }
+
+// CTAs per cluster of the cluster sweeps (diagonal blocks per work item of a cl_sweep level)
+constexpr int SWEEP_CL = 8;
+inline int sweep_item_blocks(const Level& L) { return L.cl_sweep ? SWEEP_CL : sweep_group(L); }
 
 // Per tree node: where its front lives (paper-mode scatter of leaf updates).
 struct NodeRef {
