@@ -768,6 +768,34 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
     for (int t = 0; t < a.n_nodes; ++t) std::copy(a.B[t].begin(), a.B[t].end(), h.B_dofs.begin() + h.B_off[t]);
     std::vector<int> ea_all(h.B_off.back());
     for (int t = 0; t < a.n_nodes; ++t) std::copy(a.ea[t].begin(), a.ea[t].end(), ea_all.begin() + h.B_off[t]);
+    // inverse of the extend-add maps: per node t and front position p, the contributions
+    // (child index, entry of the child's B) in the order of t's children
+    std::vector<int64_t> gp_off(a.n_nodes + 1, 0), gs_off(a.n_nodes + 1, 0);
+    for (int t = 0; t < a.n_nodes; ++t) {
+        gp_off[t + 1] = gp_off[t] + (a.I_off[t + 1] - a.I_off[t]) + (int64_t)a.B[t].size() + 1;
+        int64_t nb = 0;
+        for (int c : a.children[t]) nb += (int64_t)a.ea[c].size();
+        gs_off[t + 1] = gs_off[t] + nb;
+    }
+    std::vector<int> gptr_all(gp_off.back());
+    std::vector<int2> gsrc_all(std::max<int64_t>(1, gs_off.back()));
+    parallel_for(a.n_nodes, [&](int64_t tt) {
+        const int t = (int)tt;
+        const int Nt = (int)(gp_off[t + 1] - gp_off[t] - 1);
+        int* ptr = gptr_all.data() + gp_off[t];
+        std::fill(ptr, ptr + Nt + 1, 0);
+        for (int c : a.children[t])
+            for (int q : a.ea[c]) ++ptr[q + 1];
+        for (int q = 0; q < Nt; ++q) ptr[q + 1] += ptr[q];
+        std::vector<int> cur(ptr, ptr + Nt);
+        int2* src = gsrc_all.data() + gs_off[t];
+        int ci = 0;
+        for (int c : a.children[t]) {
+            const auto& m = a.ea[c];
+            for (int i = 0; i < (int)m.size(); ++i) src[cur[m[i]]++] = make_int2(ci, i);
+            ++ci;
+        }
+    });
 
     const int nl = a.max_depth + 1;
     const bool paper = h.opt.mode == RSD_MODE_PAPER;
@@ -818,6 +846,8 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
     const size_t o_I = take(sizeof(int) * a.n);
     const size_t o_B = take(sizeof(int) * std::max<size_t>(1, h.B_dofs.size()));
     const size_t o_ea = take(sizeof(int) * std::max<size_t>(1, ea_all.size()));
+    const size_t o_gptr = take(sizeof(int) * gptr_all.size());
+    const size_t o_gsrc = take(sizeof(int2) * gsrc_all.size());
     const size_t o_flags = take(sizeof(int) * 2 * a.n_nodes);
     struct FrontPlan { size_t P, U, D, V, H, R, PU, DU; };
     std::vector<FrontPlan> fp(a.n_nodes);
@@ -1034,6 +1064,8 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
     int* d_I = (int*)(A + o_I);
     int* d_B = (int*)(A + o_B);
     int* d_ea = (int*)(A + o_ea);
+    int* d_gptr = (int*)(A + o_gptr);
+    int2* d_gsrc = (int2*)(A + o_gsrc);
     int* d_flags = (int*)(A + o_flags);
     FrontDesc* d_fronts = (FrontDesc*)(A + o_fronts);
     int* d_items = (int*)(A + o_items);
@@ -1051,6 +1083,8 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
         RSD_CUDA_TRY(cudaMemcpyAsync(d_B, stage_host(h, h.B_dofs.data(), sizeof(int) * h.B_dofs.size()), sizeof(int) * h.B_dofs.size(), cudaMemcpyHostToDevice, st));
         RSD_CUDA_TRY(cudaMemcpyAsync(d_ea, stage_host(h, ea_all.data(), sizeof(int) * ea_all.size()), sizeof(int) * ea_all.size(), cudaMemcpyHostToDevice, st));
     }
+    RSD_CUDA_TRY(cudaMemcpyAsync(d_gptr, stage_host(h, gptr_all.data(), sizeof(int) * gptr_all.size()), sizeof(int) * gptr_all.size(), cudaMemcpyHostToDevice, st));
+    RSD_CUDA_TRY(cudaMemcpyAsync(d_gsrc, stage_host(h, gsrc_all.data(), sizeof(int2) * gsrc_all.size()), sizeof(int2) * gsrc_all.size(), cudaMemcpyHostToDevice, st));
     RSD_CUDA_TRY(cudaMemsetAsync(h.d_err, 0, sizeof(int) * ERR_SLOTS, st));
     RSD_CUDA_TRY(cudaMemsetAsync(h.d_front_bad, 0, sizeof(int) * a.n_nodes, st));
     {
@@ -1091,6 +1125,8 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
             f.I = d_I + a.I_off[t];
             f.Bd = d_B + h.B_off[t];
             f.ea = d_ea + h.B_off[t];
+            f.gptr = d_gptr + gp_off[t];
+            f.gsrc = d_gsrc + gs_off[t];
             f.flag = d_flags + 2 * t;
             f.child_begin = (int)(child_tab.size() - child_base);
             f.child_count = (int)a.children[t].size();

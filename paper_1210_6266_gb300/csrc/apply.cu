@@ -156,6 +156,27 @@ __global__ void k_fwd_gather(const FrontDesc* __restrict__ fronts, const FrontDe
     }
 }
 
+// The same vector from the inverse maps (gptr, gsrc): one thread per front position sums
+// r and its children's contributions in the children's order -- the sums of
+// k_fwd_gather, term for term, without every CTA scanning every child's map.
+template <typename A, typename Ac>
+__global__ void k_fwd_gather_inv(const FrontDesc* __restrict__ fronts, const FrontDesc* __restrict__ kids,
+                                 const int* __restrict__ child_slots, const double* __restrict__ r) {
+    const FrontDesc f = fronts[blockIdx.x];
+    A* v = (A*)f.vec;
+    if (blockIdx.y == 0 && threadIdx.x == 0) { f.flag[0] = 0; f.flag[1] = 0; }
+    for (int p = blockIdx.y * blockDim.x + threadIdx.x; p < f.N; p += gridDim.y * blockDim.x) {
+        A acc = p < f.s ? (A)r[f.I[p]] : (A)0;
+        const int k1 = f.gptr[p + 1];
+        for (int k = f.gptr[p]; k < k1; ++k) {
+            const int2 e = f.gsrc[k];
+            const int slot = child_slots[f.child_begin + e.x];
+            acc += (A)((const Ac*)kids[slot].vec)[kids[slot].s + e.y];
+        }
+        v[p] = acc;
+    }
+}
+
 // Forward item: either a group of up to GD consecutive diagonal row blocks [b0, b0 + nb)
 // of one front (item code = b0), or one NB-row block of its B rows.  The item first
 // streams acc_row = sum_{cb < ncb} P[row, cb] y_cb over the finished column blocks (the
@@ -379,7 +400,7 @@ template <typename A>
 __global__ void k_bwd_gather(const FrontDesc* __restrict__ fronts, const double* __restrict__ z) {
     const FrontDesc f = fronts[blockIdx.x];
     A* v = (A*)f.vec;
-    for (int i = threadIdx.x; i < f.b; i += blockDim.x) v[f.s + i] = (A)z[f.Bd[i]];
+    for (int i = blockIdx.y * blockDim.x + threadIdx.x; i < f.b; i += gridDim.y * blockDim.x) v[f.s + i] = (A)z[f.Bd[i]];
 }
 
 // Backward item: a group of up to GD consecutive column blocks [lo, hi] (item code = hi,
@@ -1152,14 +1173,13 @@ int sweep_level(Handle& h, int li, bool forward, const double* r, double* z, int
     if (forward) {
         const int gi = prof_begin(h, K_GATHER);
         // split each front into ranges of ~2048 positions when there are few fronts
-        const dim3 gg((unsigned)nf, (unsigned)std::max(1, std::min(64, std::min((L.max_N + 2047) / 2048,
-                                                                                   (2 * h.num_sms + nf - 1) / nf))));
+        const dim3 gg((unsigned)nf, (unsigned)std::max(1, std::min((L.max_N + 255) / 256, (4 * h.num_sms + nf - 1) / nf)));
         if (li + 1 < (int)h.levels.size()) {
             const Level& Lc = h.levels[li + 1];
-            if (is_fp64(Lc.prec)) k_fwd_gather<A, double><<<gg, 256, 0, h.stream>>>(L.d_fronts, Lc.d_fronts, L.d_child_slots, r);
-            else k_fwd_gather<A, float><<<gg, 256, 0, h.stream>>>(L.d_fronts, Lc.d_fronts, L.d_child_slots, r);
+            if (is_fp64(Lc.prec)) k_fwd_gather_inv<A, double><<<gg, 256, 0, h.stream>>>(L.d_fronts, Lc.d_fronts, L.d_child_slots, r);
+            else k_fwd_gather_inv<A, float><<<gg, 256, 0, h.stream>>>(L.d_fronts, Lc.d_fronts, L.d_child_slots, r);
         } else {
-            k_fwd_gather<A, A><<<gg, 256, 0, h.stream>>>(L.d_fronts, L.d_fronts, L.d_child_slots, r);
+            k_fwd_gather_inv<A, A><<<gg, 256, 0, h.stream>>>(L.d_fronts, L.d_fronts, L.d_child_slots, r);
         }
         count_launch();
         prof_end(h, gi, 0.0, gbytes);
@@ -1176,7 +1196,8 @@ int sweep_level(Handle& h, int li, bool forward, const double* r, double* z, int
         }
     } else {
         const int gi = prof_begin(h, K_GATHER);
-        k_bwd_gather<A><<<nf, 256, 0, h.stream>>>(L.d_fronts, z);
+        k_bwd_gather<A><<<dim3((unsigned)nf, (unsigned)std::max(1, std::min((L.max_b + 255) / 256, (4 * h.num_sms + nf - 1) / nf))),
+                          256, 0, h.stream>>>(L.d_fronts, z);
         count_launch();
         prof_end(h, gi, 0.0, gbytes);
         RSD_CUDA_TRY(cudaGetLastError());
@@ -1254,13 +1275,14 @@ int sweep_level_static(Handle& h, int li, bool forward, const double* r, double*
     const FrontDesc* fr = h.d_static_fronts + h.static_level_first[li];
     const int grid = std::max(1, std::min(forward ? L.n_fwd_items : L.n_bwd_items, h.num_sms * 4));
     if (forward) {
+        const dim3 gg((unsigned)nf, (unsigned)std::max(1, std::min((L.max_N + 255) / 256, (4 * h.num_sms + nf - 1) / nf)));
         if (li + 1 < (int)h.levels.size()) {
             const Level& Lc = h.levels[li + 1];
             const FrontDesc* kids = h.d_static_fronts + h.static_level_first[li + 1];
-            if (is_fp64(Lc.prec)) k_fwd_gather<A, double><<<nf, 256, 0, h.stream>>>(fr, kids, L.d_child_slots, r);
-            else k_fwd_gather<A, float><<<nf, 256, 0, h.stream>>>(fr, kids, L.d_child_slots, r);
+            if (is_fp64(Lc.prec)) k_fwd_gather_inv<A, double><<<gg, 256, 0, h.stream>>>(fr, kids, L.d_child_slots, r);
+            else k_fwd_gather_inv<A, float><<<gg, 256, 0, h.stream>>>(fr, kids, L.d_child_slots, r);
         } else {
-            k_fwd_gather<A, A><<<nf, 256, 0, h.stream>>>(fr, fr, L.d_child_slots, r);
+            k_fwd_gather_inv<A, A><<<gg, 256, 0, h.stream>>>(fr, fr, L.d_child_slots, r);
         }
         count_launch();
         RSD_CUDA_TRY(cudaGetLastError());
@@ -1269,7 +1291,8 @@ int sweep_level_static(Handle& h, int li, bool forward, const double* r, double*
             count_launch();
         }
     } else {
-        k_bwd_gather<A><<<nf, 256, 0, h.stream>>>(fr, z);
+        k_bwd_gather<A><<<dim3((unsigned)nf, (unsigned)std::max(1, std::min((L.max_b + 255) / 256, (4 * h.num_sms + nf - 1) / nf))),
+                          256, 0, h.stream>>>(fr, z);
         count_launch();
         RSD_CUDA_TRY(cudaGetLastError());
         if (L.n_bwd_items) {

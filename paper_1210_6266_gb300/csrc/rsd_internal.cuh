@@ -52,6 +52,11 @@ struct FrontDesc {
     const int* I;              // global DOFs of I_t (s)
     const int* Bd;             // global DOFs of B_t (b)
     const int* ea;             // positions of B_t in the parent front (b)
+    // the inverse of the children's ea maps (the upward sweep's gather): for front position
+    // p, gsrc[gptr[p] .. gptr[p + 1]) lists (child index, entry of that child's B), in the
+    // order of the children
+    const int* gptr;
+    const int2* gsrc;
     void* vec;                 // apply: front vector (N entries, level accumulator type)
     int* flag;                 // apply: progress counters [forward, backward]
     int child_begin, child_count;   // into the level's child-slot table (previous level)
