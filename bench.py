@@ -624,12 +624,21 @@ def form_record(res, ms, t_setup, t_solve, n_dof, steps, pk, peak_rec, form, pro
                       "bytes_per_step": sw_bytes, "ms_per_step": sw_ms,
                       "applications_per_step": statistics.mean(s["iterations"] for s in stats)}
         apply_roof["frac"] = apply_roof["achieved"] / apply_roof["peak"]
+    smv = classes.get("gamma_smv")
+    smv_roof = None
+    if smv and smv["ms"]:
+        # paper mode, gamma > 0: the S-MatVecs' leaf-coupling products stream the X rows
+        # of the leaves that couple to the interface level twice (X^T x, then X t)
+        smv_roof = {"bound": "hbm", "achieved": smv["bytes"] / (smv["ms"] / 1e3) / 1e9, "peak": pk["hbm_gbs"],
+                    "unit": "GB/s", "kernel": "k_smv_leaf + k_smv_rows", "bytes_per_step": smv["bytes"] / steps,
+                    "ms_per_step": smv["ms"] / steps, "launches_per_step": smv["launches"] / steps}
+        smv_roof["frac"] = smv_roof["achieved"] / smv_roof["peak"]
     return {
         "value": n_dof / (ms / 1e3), "unit": "DOF/s", "ms_per_step": ms, "form": form,
         "t_setup_ms": t_setup, "t_solve_ms": t_solve,
         "setup_dof_s": n_dof / (t_setup / 1e3), "solve_dof_s": n_dof / (t_solve / 1e3),
         "iterations": [s["iterations"] for s in stats], "relres": [s["relres"] for s in stats],
-        "roofline": roof, "apply_roofline": apply_roof,
+        "roofline": roof, "apply_roofline": apply_roof, **({"smv_roofline": smv_roof} if smv_roof else {}),
         "detail": {"ms_by_kernel_class": {k: round(v, 3) for k, v in per.items()},
                    "ms_per_step_with_launch_events": prof[1] if prof is not None else ms,
                    "host_analysis_ms": agg.get("host_analysis_ms", 0.0) / steps,

@@ -165,11 +165,13 @@ typedef struct {
  * 0 front assembly, 1 extend-add, 2 tcgen05 GEMM, 3 CUDA-core GEMM, 4 diagonal block
  * factor+inverse, 5 CUDA-core panel solve, 6 upward sweep, 7 downward sweep,
  * 8 sweep gathers, 9 Krylov vector/SpMV kernels, 10 FP16 copy of a TF32 level's factor
- * (the entries the sweeps read), 11 inner GMRES of paper mode with gamma > 0 (matrix-free
- * S-MatVecs and Arnoldi steps of one interface level; bytes = the X rows streamed),
- * 12 tcgen05 GEMM on 16-bit operand copies (kind::f16; class 2 is then the kind::tf32
- * launches only).                                                                       */
-#define RSD_PROFILE_CLASSES 13
+ * (the entries the sweeps read), 11 inner GMRES of paper mode with gamma > 0: its Arnoldi
+ * steps (start vector, modified Gram-Schmidt, least-squares finish) of one interface
+ * level, 12 tcgen05 GEMM on 16-bit operand copies (kind::f16; class 2 is then the
+ * kind::tf32 launches only), 13 the leaf-coupling products of paper mode's S-MatVecs
+ * (bytes = the X rows streamed), 14 the interface part of those S-MatVecs (K_II x less
+ * the coupling terms).                                                                  */
+#define RSD_PROFILE_CLASSES 15
 typedef struct {
     int64_t launches[RSD_PROFILE_CLASSES];
     double  ms[RSD_PROFILE_CLASSES];

@@ -80,12 +80,12 @@ class rsd_info_t(C.Structure):
 
 PROFILE_CLASSES = ["assemble", "extend_add", "gemm_tcgen05", "gemm_simt", "diag_factor",
                    "panel_solve_simt", "sweep_up", "sweep_down", "sweep_gather", "krylov", "factor_copy16",
-                   "gamma_gmres", "gemm_tcgen05_f16"]
+                   "gamma_gmres", "gemm_tcgen05_f16", "gamma_smv", "gamma_iface"]
 
 
 class rsd_profile_t(C.Structure):
-    _fields_ = [("launches", C.c_int64 * 13), ("ms", C.c_double * 13), ("flops", C.c_double * 13),
-                ("bytes", C.c_double * 13), ("host_analysis_ms", C.c_double),
+    _fields_ = [("launches", C.c_int64 * 15), ("ms", C.c_double * 15), ("flops", C.c_double * 15),
+                ("bytes", C.c_double * 15), ("host_analysis_ms", C.c_double),
                 ("host_parts_ms", C.c_double * 6), ("host_issue_ms", C.c_double)]
 
 

@@ -856,7 +856,9 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
     for (int d = nl - 1; d >= 0; --d) {
         Level& L = h.levels[d];
         const size_t es = L.factored ? elem_bytes(L.prec) : 0;   // unfactored: no storage
-        L.h16 = (L.prec == RSD_PREC_TF32 || L.prec == RSD_PREC_FP16) && !paper;
+        // paper mode: the leaves' solves read the copy too (its interface factors S~ are
+        // solved from the FP32 panels)
+        L.h16 = (L.prec == RSD_PREC_TF32 || L.prec == RSD_PREC_FP16) && (!paper || d == nl - 1);
         L.op16 = L.prec == RSD_PREC_FP16 ? TC_OP_F16 : L.prec == RSD_PREC_BF16 ? TC_OP_BF16 : TC_OP_TF32;
         // P regions of a level are contiguous, then the U regions
         lvlP[d] = off;
@@ -964,7 +966,7 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
         gh.resize(nl - 1);
         pk_pos.assign(a.n, -1);
         const Level& Ll = h.levels[nl - 1];
-        const size_t les = elem_bytes(Ll.prec);
+        const size_t les = Ll.op16 == TC_OP_F16 && !h.lu ? 2 : elem_bytes(Ll.prec);   // S-MatVec reads (smv_reads_fp16)
         for (int d = 0; d < nl - 1; ++d) {
             GammaHost& G = gh[d];
             G.if_off.assign(1, 0);
@@ -979,7 +981,8 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
             gm_maxIf = std::max(gm_maxIf, h.levels[d].nodes.size());
         }
         tl_off.assign(1, 0);
-        for (int t : Ll.nodes) tl_off.push_back(tl_off.back() + (a.I_off[t + 1] - a.I_off[t]));
+        for (int t : Ll.nodes)                       // slots of 8 elements: vector loads of t_l
+            tl_off.push_back(tl_off.back() + round_up(a.I_off[t + 1] - a.I_off[t], 8));
         for (int d = 0; d < nl - 1; ++d) {
             GammaHost& G = gh[d];
             const int S = (int)G.if_dofs.size();
@@ -1142,7 +1145,7 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
         // forward items: key = block index (I blocks, then B blocks), fronts interleaved
         // a diagonal item covers gd consecutive blocks: forward groups start at multiples
         // of gd from the top-left, backward groups are counted from the last block up
-        L.cl_sweep = L.h16 && !h.lu && !L.fronts.empty() &&
+        L.cl_sweep = L.h16 && !h.lu && !paper && !L.fronts.empty() &&
                      std::all_of(L.fronts.begin(), L.fronts.end(), [](const FrontDesc& f) { return f.b == 0; });
         const int gd = sweep_item_blocks(L);
         std::vector<std::pair<int, int>> fw, bw;   // (key, item)

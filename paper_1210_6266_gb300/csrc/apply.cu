@@ -1039,20 +1039,6 @@ k_bwd_sweep_cl(const FrontDesc* __restrict__ fronts, const int* __restrict__ ite
     }
 }
 
-// Bytes one sweep streams from the factor: the off-diagonal blocks of L and X (FP16 for a
-// level with the FP16 copy) and the inverted diagonal blocks.
-double level_factor_bytes(const Level& L) {
-    double e = 0, d = 0;
-    for (auto& f : L.fronts) {
-        e += 0.5 * f.s * (f.s + 1.0) + (double)f.s * f.b;
-        for (int k = 0; k < f.nd; ++k) {
-            const double w = std::min(NB, f.s - k * NB);
-            e -= 0.5 * w * (w + 1.0);
-        }
-        d += (double)f.nd * NB * NB;
-    }
-    return e * (L.h16 ? 2.0 : (double)elem_bytes(L.prec)) + d * elem_bytes(L.prec);
-}
 
 // Dynamic shared memory of the sweep kernels: GD inverted diagonal blocks plus, for
 // GD = 2, one factor block (FP16 when read from the copy).
@@ -1168,7 +1154,7 @@ int sweep_level(Handle& h, int li, bool forward, const double* r, double* z, int
     const int nf = (int)L.fronts.size();
     double gbytes = 0;
     for (auto& f : L.fronts) gbytes += (double)f.N * (sizeof(A) + 8.0);
-    const double fbytes = level_factor_bytes(L);
+    const double fbytes = level_factor_bytes(L, true);
     const int grid = std::max(1, std::min(forward ? L.n_fwd_items : L.n_bwd_items, h.num_sms * 4));
     if (forward) {
         const int gi = prof_begin(h, K_GATHER);
@@ -1216,6 +1202,22 @@ int sweep_level(Handle& h, int li, bool forward, const double* r, double* z, int
 }
 
 }  // namespace
+
+// Bytes one sweep streams from the factor: the off-diagonal blocks of L and X (FP16 for a
+// level with the FP16 copy) and the inverted diagonal blocks; with_x = false counts L alone
+// (the leaf solves of paper mode).
+double level_factor_bytes(const Level& L, bool with_x) {
+    double e = 0, d = 0;
+    for (auto& f : L.fronts) {
+        e += 0.5 * f.s * (f.s + 1.0) + (with_x ? (double)f.s * f.b : 0.0);
+        for (int k = 0; k < f.nd; ++k) {
+            const double w = std::min(NB, f.s - k * NB);
+            e -= 0.5 * w * (w + 1.0);
+        }
+        d += (double)f.nd * NB * NB;
+    }
+    return e * (L.h16 ? 2.0 : (double)elem_bytes(L.prec)) + d * elem_bytes(L.prec);
+}
 
 int run_apply(Handle& h, const double* r, double* z) {
     const int nl = (int)h.levels.size();

@@ -130,13 +130,14 @@ static int leaf_solve(Handle& h, const double* in, double* out, int*& ticket) {
     Level& L = h.levels[dl];
     const int p1 = prof_begin(h, K_FWD);
     RSD_TRY(sweep_with(h, dl, true, L.d_fronts_solve, L.d_fwd_items_solve, L.n_fwd_items_solve, in, out, ticket++));
-    double fb = 0;
-    for (auto& f : L.fronts) fb += 0.5 * f.s * (f.s + 1.0) * elem_bytes(L.prec);
-    prof_end(h, p1, fb / elem_bytes(L.prec) * 2.0, fb);
+    double fl = 0;
+    for (auto& f : L.fronts) fl += f.s * (f.s + 1.0);
+    const double fb = level_factor_bytes(L, false);
+    prof_end(h, p1, fl, fb);
     const int p2 = prof_begin(h, K_BWD);
     RSD_TRY(sweep_with(h, dl, false, L.d_fronts_solve_bwd ? L.d_fronts_solve_bwd : L.d_fronts_solve, L.d_bwd_items,
                        L.n_bwd_items, in, out, ticket++));
-    prof_end(h, p2, fb / elem_bytes(L.prec) * 2.0, fb);
+    prof_end(h, p2, fl, fb);
     return RSD_OK;
 }
 

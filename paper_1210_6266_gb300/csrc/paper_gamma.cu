@@ -17,6 +17,8 @@
 // Vectors of a level are packed: interface slot i of the level owns positions
 // [if_off[i], if_off[i+1]) in I_t order (pk_pos maps a global DOF to its position).
 // Every reduction has a fixed order, so results are bitwise reproducible.
+#include <cuda_fp16.h>
+
 #include <algorithm>
 #include <cmath>
 #include <type_traits>
@@ -49,28 +51,61 @@ __device__ double block_sum_all(double v, double* red) {
 
 // Products with a leaf's X block accumulate in the block's own precision (A = T): FP32
 // blocks of the mixed form in FP32, as the substitution sweeps do, FP64 blocks in FP64.
+// With H16 (T = float) they read the leaf's FP16 copy instead: row i of P scaled by the
+// power of two rs_i, so exactly the factor's TF32 values down to 2^-27 sqrt(K_ii); x enters
+// scaled by ri of its row and a row product is scaled by ri once, at half the bytes.
 template <typename T> struct VecOf;
 template <> struct VecOf<float> { using V = float4; };
 template <> struct VecOf<double> { using V = double2; };
 
-// t_l = X_l[R_l]^T x for every leaf with rows coupled to the level; one CTA per (leaf,
-// 256 x W columns), W columns per thread read with one 16-byte load per row; the rows'
-// offsets and x values are staged in shared memory, 256 at a time, and walked in order.
-template <typename T>
+template <typename T, bool H16> struct SmvElems { static constexpr int W = 16 / (int)sizeof(T); };
+template <> struct SmvElems<float, true> { static constexpr int W = 8; };
+
+// The W elements of one 16-byte load at p (a row of X, element offset c).
+template <typename T, bool H16>
+__device__ __forceinline__ void smv_load(const void* p, int64_t off, T (&o)[SmvElems<T, H16>::W]) {
+    if constexpr (H16) {
+        const uint4 u = __ldg((const uint4*)((const __half*)p + off));
+        const __half2* h = reinterpret_cast<const __half2*>(&u);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 f = __half22float2(h[k]);
+            o[2 * k] = f.x;
+            o[2 * k + 1] = f.y;
+        }
+    } else {
+        using V = typename VecOf<T>::V;
+        const V v = __ldg((const V*)((const T*)p + off));
+        const T* e = (const T*)&v;
+#pragma unroll
+        for (int k = 0; k < SmvElems<T, H16>::W; ++k) o[k] = e[k];
+    }
+}
+
+// t_l = X_l[R_l]^T x for every leaf with rows coupled to the level; one CTA per (leaf, 32 x W
+// columns), W columns per lane read with one 16-byte load per row.  The rows' offsets and x
+// values are staged in shared memory 256 at a time; the eight warps take every eighth row
+// (many loads in flight per column tile instead of one serial walk over the leaf's rows)
+// and their partial sums are added in warp order.
+template <typename T, bool H16>
 __global__ void __launch_bounds__(256) k_smv_leaf(const FrontDesc* __restrict__ leaves, const int* __restrict__ cl_ptr,
                                                   const int* __restrict__ cl_row, const int* __restrict__ cl_pos,
                                                   const int* __restrict__ tl_off, const double* __restrict__ x,
                                                   T* __restrict__ tl) {
-    using V = typename VecOf<T>::V;
-    constexpr int W = 16 / (int)sizeof(T);
+    constexpr int W = SmvElems<T, H16>::W, CT = 32 * W;
     __shared__ int s_row[256];
     __shared__ T s_x[256];
+    __shared__ T s_red[8][CT];
     const int l = blockIdx.x;
     const int k0 = cl_ptr[l], k1 = cl_ptr[l + 1];
-    if (k0 == k1) return;
     const int s = leaves[l].s, ldp = leaves[l].ldp;
-    const T* X = (const T*)leaves[l].P + (int64_t)s * ldp;
-    const int c = (blockIdx.y * blockDim.x + threadIdx.x) * W;
+    const int c0 = blockIdx.y * CT;
+    if (k0 == k1 || c0 >= s) return;
+    const void* X = H16 ? (const void*)((const __half*)leaves[l].P16 + (int64_t)s * ldp)
+                        : (const void*)((const T*)leaves[l].P + (int64_t)s * ldp);
+    const float* ri = H16 ? leaves[l].ri + s : nullptr;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = c0 + lane * W;
     T acc[W];
 #pragma unroll
     for (int e = 0; e < W; ++e) acc[e] = 0;
@@ -78,54 +113,120 @@ __global__ void __launch_bounds__(256) k_smv_leaf(const FrontDesc* __restrict__ 
         const int nb = min(256, k1 - kb);
         __syncthreads();
         if ((int)threadIdx.x < nb) {
-            s_row[threadIdx.x] = cl_row[kb + threadIdx.x];
-            s_x[threadIdx.x] = (T)x[cl_pos[kb + threadIdx.x]];
+            const int row = cl_row[kb + threadIdx.x];
+            s_row[threadIdx.x] = row;
+            const T xv = (T)x[cl_pos[kb + threadIdx.x]];
+            s_x[threadIdx.x] = H16 ? xv * (T)ri[row] : xv;
         }
         __syncthreads();
         if (c < s) {
 #pragma unroll 4
-            for (int q = 0; q < nb; ++q) {
-                const V v = __ldg((const V*)(X + (int64_t)s_row[q] * ldp + c));
-                const T* e = (const T*)&v;
+            for (int q = warp; q < nb; q += 8) {
+                T e[W];
+                smv_load<T, H16>(X, (int64_t)s_row[q] * ldp + c, e);
                 const T xv = s_x[q];
 #pragma unroll
                 for (int u = 0; u < W; ++u) acc[u] += e[u] * xv;
             }
         }
     }
-    T* out = tl + tl_off[l];
 #pragma unroll
-    for (int e = 0; e < W; ++e)
-        if (c + e < s) out[c + e] = acc[e];
+    for (int e = 0; e < W; ++e) s_red[warp][lane * W + e] = acc[e];
+    __syncthreads();
+    T* out = tl + tl_off[l];
+    for (int e = threadIdx.x; e < CT; e += blockDim.x) {
+        if (c0 + e >= s) break;
+        T v = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) v += s_red[w][e];
+        out[c0 + e] = v;
+    }
+}
+
+// The W entries of t at c (16- or 32-byte aligned: t_l slots start at multiples of 8
+// elements and c is a multiple of W).
+template <typename T, int W>
+__device__ __forceinline__ void smv_tload(const T* t, T (&o)[W]) {
+    if constexpr (sizeof(T) * W == 32) {
+        const float4 a = __ldg((const float4*)t), b = __ldg((const float4*)t + 1);
+        const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int q = 0; q < W; ++q) o[q] = v[q];
+    } else {
+        using V = typename VecOf<T>::V;
+        const V v = __ldg((const V*)t);
+        const T* e = (const T*)&v;
+#pragma unroll
+        for (int q = 0; q < W; ++q) o[q] = e[q];
+    }
 }
 
 // yl_k = X_l[row_k] . t_l for every coupling k (a row of a leaf's X block that lies in the
-// level's interfaces); one warp per coupling, 16-byte loads along the row.
-template <typename T>
+// level's interfaces).  One warp per group of R consecutive couplings: couplings are grouped
+// by leaf, so a group of one leaf reads each chunk of t_l once for its R rows (16-byte loads
+// along the rows); a group that straddles two leaves takes its rows one at a time.  Either
+// way a row's sum runs in the same order (lane-strided chunks, the ragged tail, then the
+// butterfly), so the result does not depend on the grouping.
+template <typename T, bool H16>
 __global__ void __launch_bounds__(256) k_smv_rows(int nk, const int* __restrict__ cl_leaf, const int* __restrict__ cl_row,
                                                   const FrontDesc* __restrict__ leaves, const int* __restrict__ tl_off,
                                                   const T* __restrict__ tl, double* __restrict__ yl) {
-    using V = typename VecOf<T>::V;
-    constexpr int W = 16 / (int)sizeof(T);
+    constexpr int W = SmvElems<T, H16>::W, R = 4;
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; k < nk; k += warps) {
-        const int l = cl_leaf[k];
-        const int s = leaves[l].s, ldp = leaves[l].ldp;
-        const T* row = (const T*)leaves[l].P + (int64_t)(s + cl_row[k]) * ldp;
-        const T* t = tl + tl_off[l];
-        T d = 0;
-        const int sv = s / W * W;
-        for (int c = lane * W; c < sv; c += 32 * W) {
-            const V v = __ldg((const V*)(row + c));
-            const T* e = (const T*)&v;
+    const int64_t ng = ((int64_t)nk + R - 1) / R;
+    for (int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; g < ng; g += warps) {
+        const int64_t k0 = g * R;
+        const int nr = (int)(nk - k0 < R ? nk - k0 : R);
+        const bool shared = nr == R && cl_leaf[k0] == cl_leaf[k0 + R - 1];
+        for (int r0 = 0; r0 < nr; r0 += shared ? R : 1) {
+            const int m = shared ? R : 1;            // rows summed together
+            const int l = cl_leaf[k0 + r0];
+            const int s = leaves[l].s, ldp = leaves[l].ldp;
+            const void* base = H16 ? (const void*)leaves[l].P16 : (const void*)leaves[l].P;
+            const T* t = tl + tl_off[l];
+            int64_t roff[R];
+            T d[R];
 #pragma unroll
-            for (int q = 0; q < W; ++q) d += e[q] * t[c + q];
+            for (int r = 0; r < R; ++r) {
+                roff[r] = r < m ? (int64_t)(s + cl_row[k0 + r0 + r]) * ldp : 0;
+                d[r] = 0;
+            }
+            const int sv = s / W * W;
+#pragma unroll 1
+            for (int c = lane * W; c < sv; c += 32 * W) {
+                T tv[W];
+                smv_tload<T, W>(t + c, tv);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if (r < m) {
+                        T e[W];
+                        smv_load<T, H16>(base, roff[r] + c, e);
+#pragma unroll
+                        for (int q = 0; q < W; ++q) d[r] += e[q] * tv[q];
+                    }
+                }
+            }
+            for (int c = sv + lane; c < s; c += 32) {
+                const T tv = t[c];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if (r < m) {
+                        const T v = H16 ? (T)__half2float(((const __half*)base)[roff[r] + c]) : ((const T*)base)[roff[r] + c];
+                        d[r] += v * tv;
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) d[r] += __shfl_xor_sync(0xffffffffu, d[r], o);
+                if (lane == 0 && r < m) {
+                    const int64_t k = k0 + r0 + r;
+                    yl[k] = H16 ? (double)(d[r] * (T)leaves[l].ri[s + cl_row[k]]) : (double)d[r];
+                }
+            }
         }
-        for (int c = sv + lane; c < s; c += 32) d += row[c] * t[c];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-        if (lane == 0) yl[k] = (double)d;
     }
 }
 
@@ -264,36 +365,54 @@ int gamma_interface_solve(Handle& h, int li, double* z) {
     // leaves; for symmetric ones Y^T = X
     const FrontDesc* ty = Ll.d_fronts_bwd ? Ll.d_fronts_bwd : Ll.d_fronts;
     const bool f64 = is_fp64(Ll.prec);
+    // the leaves' FP16 copy when they have one (16-bit operand levels; not the transposed
+    // upper factors of nonsymmetric leaves)
+    const bool c16 = smv_reads_fp16(Ll);
     const int gam = h.gamma;
-    const int pi = prof_begin(h, K_GAMMA);
+    int pi = prof_begin(h, K_GAMMA);
     k_gm_init<<<G.n_if, GT, 0, h.stream>>>(G.d_if_off, G.d_if_dofs, h.d_pg, h.d_gm_V, h.d_gm_beta, h.d_gm_kused);
     count_launch();
-    const int wcol = f64 ? 2 : 4;                 // columns per thread of k_smv_leaf
-    const dim3 gl((unsigned)nleaf, (unsigned)std::max(1, (Ll.max_s + 256 * wcol - 1) / (256 * wcol)));
+    prof_end(h, pi, 0.0, 0.0);
+    const int wcol = f64 ? 2 : (c16 ? 8 : 4);     // columns per lane of k_smv_leaf
+    const dim3 gl((unsigned)nleaf, (unsigned)std::max(1, (Ll.max_s + 32 * wcol - 1) / (32 * wcol)));
     const unsigned gi = (unsigned)std::max(1, std::min(h.num_sms * 8, (G.S + 7) / 8));
-    double bytes = 0;
     for (int j = 0; j < gam; ++j) {
         const double* vj = h.d_gm_V + (int64_t)j * G.S;
-        const unsigned gr = (unsigned)std::max(1, std::min(h.num_sms * 8, (G.nk + 7) / 8));
+        const unsigned gr = (unsigned)std::max(1, std::min(h.num_sms * 4, (G.nk + 31) / 32));   // 8 warps of 4 rows
+        pi = prof_begin(h, K_GAMMA_SMV);
         if (f64) {
-            k_smv_leaf<double><<<gl, 256, 0, h.stream>>>(ty, G.d_cl_ptr, G.d_cl_row, G.d_cl_pos, h.d_tl_off, vj, h.d_tl);
-            k_smv_rows<double><<<gr, 256, 0, h.stream>>>(G.nk, G.d_cl_leaf, G.d_cl_row, Ll.d_fronts, h.d_tl_off, h.d_tl,
-                                                         h.d_gm_yl);
+            k_smv_leaf<double, false><<<gl, 256, 0, h.stream>>>(ty, G.d_cl_ptr, G.d_cl_row, G.d_cl_pos, h.d_tl_off, vj,
+                                                                h.d_tl);
+            k_smv_rows<double, false><<<gr, 256, 0, h.stream>>>(G.nk, G.d_cl_leaf, G.d_cl_row, Ll.d_fronts, h.d_tl_off,
+                                                                h.d_tl, h.d_gm_yl);
+        } else if (c16) {
+            float* tl32 = (float*)h.d_tl;
+            k_smv_leaf<float, true><<<gl, 256, 0, h.stream>>>(Ll.d_fronts, G.d_cl_ptr, G.d_cl_row, G.d_cl_pos, h.d_tl_off,
+                                                              vj, tl32);
+            k_smv_rows<float, true><<<gr, 256, 0, h.stream>>>(G.nk, G.d_cl_leaf, G.d_cl_row, Ll.d_fronts, h.d_tl_off, tl32,
+                                                              h.d_gm_yl);
         } else {
             float* tl32 = (float*)h.d_tl;
-            k_smv_leaf<float><<<gl, 256, 0, h.stream>>>(ty, G.d_cl_ptr, G.d_cl_row, G.d_cl_pos, h.d_tl_off, vj, tl32);
-            k_smv_rows<float><<<gr, 256, 0, h.stream>>>(G.nk, G.d_cl_leaf, G.d_cl_row, Ll.d_fronts, h.d_tl_off, tl32, h.d_gm_yl);
+            k_smv_leaf<float, false><<<gl, 256, 0, h.stream>>>(ty, G.d_cl_ptr, G.d_cl_row, G.d_cl_pos, h.d_tl_off, vj,
+                                                               tl32);
+            k_smv_rows<float, false><<<gr, 256, 0, h.stream>>>(G.nk, G.d_cl_leaf, G.d_cl_row, Ll.d_fronts, h.d_tl_off,
+                                                               tl32, h.d_gm_yl);
         }
+        prof_end(h, pi, 0.0, G.xbytes);
+        pi = prof_begin(h, K_GAMMA_IFACE);
         k_smv_iface<<<gi, 256, 0, h.stream>>>(G.S, G.d_if_dofs, h.d_rowptr, h.d_col, h.d_val, h.d_owner, h.d_pk_pos,
                                               G.d_ci_ptr, G.d_ci_k, h.d_gm_yl, vj, h.d_gm_w);
+        prof_end(h, pi, 0.0, 0.0);
+        pi = prof_begin(h, K_GAMMA);
         k_gm_mgs<<<G.n_if, GT, 0, h.stream>>>(j, gam, G.S, G.d_if_off, h.d_gm_w, h.d_gm_V, h.d_gm_H, h.d_gm_beta, h.d_gm_kused);
+        prof_end(h, pi, 0.0, 0.0);
         count_launch(4);
-        bytes += G.xbytes;
     }
+    pi = prof_begin(h, K_GAMMA);
     k_gm_finish<<<G.n_if, GT, 0, h.stream>>>(gam, G.S, G.d_if_off, G.d_if_dofs, h.d_gm_V, h.d_gm_H, h.d_gm_beta,
                                              h.d_gm_kused, z);
     count_launch();
-    prof_end(h, pi, 0.0, bytes);
+    prof_end(h, pi, 0.0, 0.0);
     RSD_CUDA_TRY(cudaGetLastError());
     return RSD_OK;
 }

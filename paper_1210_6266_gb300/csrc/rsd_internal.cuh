@@ -105,7 +105,7 @@ enum { TC_OP_TF32 = 0, TC_OP_F16 = 1, TC_OP_BF16 = 2 };
 
 // Kernel classes for launch counting and the optional CUDA-event profile.
 enum KClass { K_ASSEMBLE = 0, K_EXTEND, K_GEMM_TC, K_GEMM_SIMT, K_POTRF, K_TRSM, K_FWD, K_BWD,
-              K_GATHER, K_KRYLOV, K_COPY16, K_GAMMA, K_GEMM_TC16, K_CLASSES };
+              K_GATHER, K_KRYLOV, K_COPY16, K_GAMMA, K_GEMM_TC16, K_GAMMA_SMV, K_GAMMA_IFACE, K_CLASSES };
 
 // Per-handle profile: one event pair per launch of a class, with the algorithmic
 // flops and bytes of that launch; reduced on demand by rsd_profile().
@@ -188,6 +188,11 @@ inline bool copy16_level(const Level& L) { return L.h16 || L.op16 != TC_OP_TF32;
 // fronts keep one block per item, whose smaller footprint lets more CTAs stream the
 // factor at once (an FP64 pair would not fit in shared memory).
 inline int sweep_group(const Level& L) { return (!is_fp64(L.prec) && L.fronts.size() == 1) ? 2 : 1; }
+
+// Paper mode with gamma > 0: the S-MatVec reads the leaves' FP16 copy (FP16 operand
+// levels; not BF16 copies, FP64 or FP32 leaves, or the transposed upper factors of
+// nonsymmetric leaves).
+inline bool smv_reads_fp16(const Level& Ll) { return Ll.op16 == TC_OP_F16 && !Ll.d_fronts_bwd && !is_fp64(Ll.prec); }
 
 // CTAs per cluster of the cluster sweeps (diagonal blocks per work item of a cl_sweep level)
 constexpr int SWEEP_CL = 8;
@@ -361,6 +366,8 @@ int static_apply_prepare(Handle& h, FrontDesc* d_slots);
 int sweep_with(Handle& h, int li, bool forward, const FrontDesc* fronts, const int* items, int n_items,
                const double* in, double* out, int* ticket);
 int paper_extend_add(Handle& h);
+// bytes one sweep of a level streams from its factor (with_x = false: L without X)
+double level_factor_bytes(const Level& L, bool with_x);
 // peak probes of this library's GEMM kernels (rsd_peak_gemm)
 int gemm_tc_peak(int n, int reps, double seconds, cudaStream_t stream, int num_sms, double* best, double* sustained,
                  int op);

@@ -68,13 +68,15 @@ def test_gamma_fgmres_matches_oracle_iterations(rsd, n, depth, gamma):
     assert np.linalg.norm(b - A @ u.cpu().numpy()) <= 1e-9 * np.linalg.norm(b)
     assert abs(st["iterations"] - it_ref) <= 1, (st["iterations"], it_ref)
     h.close()
-    # the mixed form: TF32 leaf factors, FP64 inner GMRES and FGMRES
-    h = _setup(rsd, prob, rsd.RSD_PREC_TF32, gamma, maxit=400)
-    u, st = h.solve(prob["b"], tol=1e-8)
-    assert st["relres"] <= 1e-8
-    assert np.linalg.norm(b - A @ u.cpu().numpy()) <= 1e-8 * np.linalg.norm(b)
-    assert st["iterations"] <= it_ref + 3, (st["iterations"], it_ref)
-    h.close()
+    # the mixed forms: TF32 leaf factors; FP16-operand updates, whose S-MatVec reads the
+    # leaves' row-scaled FP16 copy; FP64 inner GMRES and FGMRES
+    for prec in (rsd.RSD_PREC_TF32, rsd.RSD_PREC_FP16):
+        h = _setup(rsd, prob, prec, gamma, maxit=400)
+        u, st = h.solve(prob["b"], tol=1e-8)
+        assert st["relres"] <= 1e-8
+        assert np.linalg.norm(b - A @ u.cpu().numpy()) <= 1e-8 * np.linalg.norm(b)
+        assert st["iterations"] <= it_ref + 3, (prec, st["iterations"], it_ref)
+        h.close()
 
 
 @pytest.mark.parametrize("N,P", [(17, 8), (33, 8), (17, 128)])
@@ -108,12 +110,13 @@ def test_gamma_apply_is_deterministic(rsd):
     kappa, f, A, sym = _case(n, depth)
     prob = rsd.grid_problem(n, depth, kappa, f)
     r = torch.as_tensor(synth.uniform(99, A.shape[0]), device="cuda")
-    outs = []
-    for _ in range(2):
-        h = _setup(rsd, prob, rsd.RSD_PREC_TF32, gamma)
-        outs += [h.apply(r).clone(), h.apply(r).clone()]
-        h.close()
-    assert all(torch.equal(outs[0], z) for z in outs[1:])
+    for prec in (rsd.RSD_PREC_TF32, rsd.RSD_PREC_FP16):
+        outs = []
+        for _ in range(2):
+            h = _setup(rsd, prob, prec, gamma)
+            outs += [h.apply(r).clone(), h.apply(r).clone()]
+            h.close()
+        assert all(torch.equal(outs[0], z) for z in outs[1:]), prec
 
 
 def test_paper_gamma0_setup_and_apply_are_bitwise_repeatable(rsd):
@@ -148,4 +151,27 @@ def test_fgmres_with_exact_preconditioner_converges_in_one_iteration(rsd):
     b = fem.load_vector(n, f)
     uref = ExactFactor(A, sym).apply(b)
     assert np.abs(u.cpu().numpy() - uref).max() <= 1e-10 * np.abs(uref).max()
+    h.close()
+
+
+def test_paper_leaf_copy_holds_the_leaf_factor(rsd):
+    """Paper mode's leaf solves and S-MatVecs read the leaves' row-scaled FP16 copy: it
+    equals the leaf factor [L; X] exactly wherever the scaled entry is an FP16 normal
+    (entries >= 2^-27 sqrt(K_ii)) and within 2^-38 sqrt(K_ii) elsewhere."""
+    n, depth = 23, 2
+    kappa, f, A, sym = _case(n, depth)
+    prob = rsd.grid_problem(n, depth, kappa, f)
+    h = _setup(rsd, prob, rsd.RSD_PREC_FP16, 4)
+    sq = np.sqrt(A.diagonal())
+    leaves = [t for t in range(sym.n_nodes) if not sym.children[t]]
+    assert leaves
+    for t in leaves:
+        s, bb, _ = h.front_dims(t)
+        P, Q = h.front_factor(t), h.front_factor16(t)
+        bound = np.repeat(sq[h.front_dofs(t)][:, None], s, axis=1)
+        rows, cols = np.arange(s + bb)[:, None], np.arange(s)[None, :]
+        read = (rows >= s) | (cols // 128 < rows // 128)
+        big = read & (np.abs(P) >= 2.0**-27 * bound)
+        assert np.array_equal(Q[big], P[big]), t
+        assert np.all(np.abs(Q - P)[read] <= 2.0**-38 * bound[read]), t
     h.close()
