@@ -19,6 +19,7 @@
 #include <climits>
 #include <mutex>
 
+#include "cluster.cuh"
 #include "rsd_internal.cuh"
 
 namespace rsd {
@@ -655,29 +656,6 @@ __global__ void __launch_bounds__(AT, GD == 1 ? 2 : 1) k_bwd_sweep(const FrontDe
 // memory: every block still raises the front's progress counter, in block order (after
 // its push and a fence), which the later clusters wait on.  Work items are taken with a ticket by the cluster's first CTA,
 // so a cluster only waits on items with smaller tickets, held by running clusters.
-
-__device__ __forceinline__ uint32_t cl_rank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
-// all threads of every CTA of the cluster (uniform control flow only)
-__device__ __forceinline__ void cl_sync() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ uint32_t cl_map(const void* p, uint32_t rank) {
-    uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(rank));
-    return r;
-}
-
-__device__ __forceinline__ int cl_ld(uint32_t a) {
-    int v;
-    asm volatile("ld.shared::cluster.b32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
-    return v;
-}
 
 __device__ __forceinline__ void cl_st_remote(uint32_t a, float v) {
     asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");

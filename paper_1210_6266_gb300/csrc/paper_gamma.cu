@@ -23,6 +23,7 @@
 #include <cmath>
 #include <type_traits>
 
+#include "cluster.cuh"
 #include "rsd_internal.cuh"
 
 namespace rsd {
@@ -257,57 +258,120 @@ __global__ void __launch_bounds__(256) k_smv_iface(int S, const int* __restrict_
     }
 }
 
+// The GMRES vector kernels give each interface a cluster of GC CTAs, CTA r of the cluster
+// holding the r-th contiguous chunk of the interface's entries, so a long interface (the
+// root's) is spread over GC SMs instead of one.
+constexpr int GC = 8;
+
+struct GmChunk {
+    int i, o, s, lo, hi;        // interface, its offset and size; this CTA's entries [lo, hi)
+};
+
+__device__ __forceinline__ GmChunk gm_chunk(const int* __restrict__ if_off, int i, int r) {
+    GmChunk c;
+    c.i = i;
+    c.o = if_off[i];
+    c.s = if_off[i + 1] - c.o;
+    const int per = (c.s + GC - 1) / GC;
+    c.lo = min(c.s, r * per);
+    c.hi = min(c.s, c.lo + per);
+    return c;
+}
+
+// Sum over the cluster in a fixed order: each CTA's block sum (block_sum_all), then the GC
+// partials added in rank order by every CTA, so every thread of the cluster gets the same
+// bits.  part[] alternates between calls: a CTA rewrites part[p] only after the barrier of
+// the call in between, which every CTA passes after its reads of part[p].
+__device__ double cluster_sum_all(double v, double* red, double* part, double* tot, int& p) {
+    const double b = block_sum_all(v, red);
+    if (threadIdx.x == 0) part[p] = b;
+    cl_sync();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int r = 0; r < GC; ++r) t += cl_ld_f64(cl_map(&part[p], (uint32_t)r));
+        *tot = t;
+    }
+    __syncthreads();
+    p ^= 1;
+    return *tot;
+}
+
 // v_0 = g / beta on every interface of the level (g indexed by global DOF).
-__global__ void __launch_bounds__(GT) k_gm_init(const int* __restrict__ if_off, const int* __restrict__ if_dofs,
-                                                const double* __restrict__ g, double* __restrict__ V,
-                                                double* __restrict__ beta, int* __restrict__ kused) {
-    __shared__ double red[33];
-    const int i = blockIdx.x;
-    const int o = if_off[i], s = if_off[i + 1] - o;
+__global__ void __cluster_dims__(GC, 1, 1) __launch_bounds__(GT)
+    k_gm_init(const int* __restrict__ if_off, const int* __restrict__ if_dofs, const double* __restrict__ g,
+              double* __restrict__ V, double* __restrict__ beta, int* __restrict__ kused) {
+    __shared__ double red[33], part[2], tot;
+    const int r = (int)cl_rank();
+    const GmChunk c = gm_chunk(if_off, blockIdx.x / GC, r);
+    int p = 0;
     double a = 0;
-    for (int e = threadIdx.x; e < s; e += blockDim.x) { const double v = g[if_dofs[o + e]]; a += v * v; }
-    const double b = sqrt(block_sum_all(a, red));
-    if (threadIdx.x == 0) { beta[i] = b; kused[i] = b > 0.0 ? 0 : -1; }
+    for (int e = c.lo + threadIdx.x; e < c.hi; e += blockDim.x) { const double v = g[if_dofs[c.o + e]]; a += v * v; }
+    const double b = sqrt(cluster_sum_all(a, red, part, &tot, p));
+    if (r == 0 && threadIdx.x == 0) { beta[c.i] = b; kused[c.i] = b > 0.0 ? 0 : -1; }
     const double inv = b > 0.0 ? 1.0 / b : 0.0;
-    for (int e = threadIdx.x; e < s; e += blockDim.x) V[o + e] = g[if_dofs[o + e]] * inv;
+    for (int e = c.lo + threadIdx.x; e < c.hi; e += blockDim.x) V[c.o + e] = g[if_dofs[c.o + e]] * inv;
+    cl_sync();                                  // no CTA leaves while a peer reads its partials
 }
 
 // Arnoldi step j with modified Gram-Schmidt on w = S~ v_j, per interface: h_qj = <w, v_q>,
-// w -= h_qj v_q for q = 0..j in turn, h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j}.  An
-// interface whose h_{j+1,j} falls to 1e-14 beta (exact breakdown) stops with j + 1
-// columns; one that completes min(gamma, s) steps stops with that many.
-__global__ void __launch_bounds__(GT) k_gm_mgs(int j, int gamma, int S, const int* __restrict__ if_off,
-                                               double* __restrict__ w, double* __restrict__ V, double* __restrict__ H,
-                                               const double* __restrict__ beta, int* __restrict__ kused) {
-    __shared__ double red[33];
-    const int i = blockIdx.x;
-    const int o = if_off[i], s = if_off[i + 1] - o;
-    const int m = min(gamma, s);
-    if (kused[i] != 0 || j >= m) return;
-    double* Hi = H + (int64_t)i * (gamma + 1) * gamma;
-    for (int q = 0; q <= j; ++q) {
-        const double* vq = V + (int64_t)q * S + o;
-        double a = 0;
-        for (int e = threadIdx.x; e < s; e += blockDim.x) a += w[o + e] * vq[e];
-        const double hq = block_sum_all(a, red);
-        for (int e = threadIdx.x; e < s; e += blockDim.x) w[o + e] -= hq * vq[e];
-        if (threadIdx.x == 0) Hi[q * gamma + j] = hq;
-    }
+// w -= h_qj v_q for q = 0..j in turn, h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j}.  One pass
+// over the chunk per q: the update by v_q and the product with v_{q+1} (or w's norm after
+// the last) of the updated entries.  An interface whose h_{j+1,j} falls to 1e-14 beta
+// (exact breakdown) stops with j + 1 columns; one that completes min(gamma, s) steps stops
+// with that many.
+__global__ void __cluster_dims__(GC, 1, 1) __launch_bounds__(GT)
+    k_gm_mgs(int j, int gamma, int S, const int* __restrict__ if_off, double* __restrict__ w, double* __restrict__ V,
+             double* __restrict__ H, const double* __restrict__ beta, int* __restrict__ kused) {
+    __shared__ double red[33], part[2], tot;
+    const int r = (int)cl_rank();
+    const GmChunk c = gm_chunk(if_off, blockIdx.x / GC, r);
+    const int m = min(gamma, c.s);
+    if (kused[c.i] != 0 || j >= m) return;     // the whole cluster
+    const bool lead = r == 0 && threadIdx.x == 0;
+    double* Hi = H + (int64_t)c.i * (gamma + 1) * gamma;
+    double* wi = w + c.o;
+    int p = 0;
     double a = 0;
-    for (int e = threadIdx.x; e < s; e += blockDim.x) a += w[o + e] * w[o + e];
-    const double nrm = sqrt(block_sum_all(a, red));
-    if (threadIdx.x == 0) Hi[(j + 1) * gamma + j] = nrm;
-    if (nrm <= 1e-14 * beta[i]) {
-        if (threadIdx.x == 0) kused[i] = j + 1;
-        return;
+    for (int e = c.lo + threadIdx.x; e < c.hi; e += blockDim.x) a += wi[e] * V[c.o + e];
+    double hq = cluster_sum_all(a, red, part, &tot, p);
+    for (int q = 0; q <= j; ++q) {
+        if (lead) Hi[q * gamma + j] = hq;
+        const double* vq = V + (int64_t)q * S + c.o;
+        a = 0;
+        if (q < j) {
+            const double* vn = vq + S;
+#pragma unroll 4
+            for (int e = c.lo + threadIdx.x; e < c.hi; e += blockDim.x) {
+                const double x = wi[e] - hq * vq[e];
+                wi[e] = x;
+                a += x * vn[e];
+            }
+        } else {
+#pragma unroll 4
+            for (int e = c.lo + threadIdx.x; e < c.hi; e += blockDim.x) {
+                const double x = wi[e] - hq * vq[e];
+                wi[e] = x;
+                a += x * x;
+            }
+        }
+        hq = cluster_sum_all(a, red, part, &tot, p);
     }
-    double* vn = V + (int64_t)(j + 1) * S + o;
-    for (int e = threadIdx.x; e < s; e += blockDim.x) vn[e] = w[o + e] / nrm;
-    if (j + 1 == m && threadIdx.x == 0) kused[i] = m;
+    const double nrm = sqrt(hq);
+    if (lead) Hi[(j + 1) * gamma + j] = nrm;
+    if (nrm <= 1e-14 * beta[c.i]) {
+        if (lead) kused[c.i] = j + 1;
+    } else {
+        double* vn = V + (int64_t)(j + 1) * S + c.o;
+        for (int e = c.lo + threadIdx.x; e < c.hi; e += blockDim.x) vn[e] = wi[e] / nrm;
+        if (j + 1 == m && lead) kused[c.i] = m;
+    }
+    cl_sync();                                  // no CTA leaves while a peer reads its partials
 }
 
 // u_t = V_k y with y the least-squares solution of min || beta e1 - H_k y || (H_k the
 // (k+1) x k Hessenberg matrix; Givens rotations), written to z on the interface DOFs.
+// Every CTA of an interface solves the small problem itself (the same bits) and writes
+// its chunk.
 __global__ void __launch_bounds__(GT) k_gm_finish(int gamma, int S, const int* __restrict__ if_off,
                                                   const int* __restrict__ if_dofs, const double* __restrict__ V,
                                                   const double* __restrict__ H, const double* __restrict__ beta,
@@ -315,40 +379,39 @@ __global__ void __launch_bounds__(GT) k_gm_finish(int gamma, int S, const int* _
     __shared__ double y[GAMMA_MAX];
     __shared__ double R[GAMMA_MAX + 1][GAMMA_MAX];      // rotated Hessenberg
     __shared__ double gv[GAMMA_MAX + 1];
-    const int i = blockIdx.x;
-    const int o = if_off[i], s = if_off[i + 1] - o;
-    const int ku = kused[i];
-    const int k = ku < 0 ? 0 : (ku == 0 ? min(gamma, s) : ku);
+    const GmChunk c = gm_chunk(if_off, blockIdx.x / GC, blockIdx.x % GC);
+    const int ku = kused[c.i];
+    const int k = ku < 0 ? 0 : (ku == 0 ? min(gamma, c.s) : ku);
     if (threadIdx.x == 0 && k > 0) {
-        const double* Hi = H + (int64_t)i * (gamma + 1) * gamma;
+        const double* Hi = H + (int64_t)c.i * (gamma + 1) * gamma;
         for (int r = 0; r <= k; ++r)
-            for (int c = 0; c < k; ++c) R[r][c] = (r <= c + 1) ? Hi[r * gamma + c] : 0.0;
+            for (int cc = 0; cc < k; ++cc) R[r][cc] = (r <= cc + 1) ? Hi[r * gamma + cc] : 0.0;
         for (int r = 0; r <= k; ++r) gv[r] = 0.0;
-        gv[0] = beta[i];
-        for (int c = 0; c < k; ++c) {
-            const double a = R[c][c], b = R[c + 1][c];
+        gv[0] = beta[c.i];
+        for (int cc = 0; cc < k; ++cc) {
+            const double a = R[cc][cc], b = R[cc + 1][cc];
             const double den = hypot(a, b);
             const double cs = den > 0 ? a / den : 1.0, sn = den > 0 ? b / den : 0.0;
-            for (int cc = c; cc < k; ++cc) {
-                const double t0 = R[c][cc], t1 = R[c + 1][cc];
-                R[c][cc] = cs * t0 + sn * t1;
-                R[c + 1][cc] = -sn * t0 + cs * t1;
+            for (int c2 = cc; c2 < k; ++c2) {
+                const double t0 = R[cc][c2], t1 = R[cc + 1][c2];
+                R[cc][c2] = cs * t0 + sn * t1;
+                R[cc + 1][c2] = -sn * t0 + cs * t1;
             }
-            const double g0 = gv[c], g1 = gv[c + 1];
-            gv[c] = cs * g0 + sn * g1;
-            gv[c + 1] = -sn * g0 + cs * g1;
+            const double g0 = gv[cc], g1 = gv[cc + 1];
+            gv[cc] = cs * g0 + sn * g1;
+            gv[cc + 1] = -sn * g0 + cs * g1;
         }
         for (int r = k - 1; r >= 0; --r) {
             double t = gv[r];
-            for (int c = r + 1; c < k; ++c) t -= R[r][c] * y[c];
+            for (int c2 = r + 1; c2 < k; ++c2) t -= R[r][c2] * y[c2];
             y[r] = R[r][r] != 0.0 ? t / R[r][r] : 0.0;
         }
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < s; e += blockDim.x) {
+    for (int e = c.lo + threadIdx.x; e < c.hi; e += blockDim.x) {
         double u = 0;
-        for (int q = 0; q < k; ++q) u += y[q] * V[(int64_t)q * S + o + e];
-        z[if_dofs[o + e]] = u;
+        for (int q = 0; q < k; ++q) u += y[q] * V[(int64_t)q * S + c.o + e];
+        z[if_dofs[c.o + e]] = u;
     }
 }
 
@@ -370,7 +433,7 @@ int gamma_interface_solve(Handle& h, int li, double* z) {
     const bool c16 = smv_reads_fp16(Ll);
     const int gam = h.gamma;
     int pi = prof_begin(h, K_GAMMA);
-    k_gm_init<<<G.n_if, GT, 0, h.stream>>>(G.d_if_off, G.d_if_dofs, h.d_pg, h.d_gm_V, h.d_gm_beta, h.d_gm_kused);
+    k_gm_init<<<G.n_if * GC, GT, 0, h.stream>>>(G.d_if_off, G.d_if_dofs, h.d_pg, h.d_gm_V, h.d_gm_beta, h.d_gm_kused);
     count_launch();
     prof_end(h, pi, 0.0, 0.0);
     const int wcol = f64 ? 2 : (c16 ? 8 : 4);     // columns per lane of k_smv_leaf
@@ -404,12 +467,12 @@ int gamma_interface_solve(Handle& h, int li, double* z) {
                                               G.d_ci_ptr, G.d_ci_k, h.d_gm_yl, vj, h.d_gm_w);
         prof_end(h, pi, 0.0, 0.0);
         pi = prof_begin(h, K_GAMMA);
-        k_gm_mgs<<<G.n_if, GT, 0, h.stream>>>(j, gam, G.S, G.d_if_off, h.d_gm_w, h.d_gm_V, h.d_gm_H, h.d_gm_beta, h.d_gm_kused);
+        k_gm_mgs<<<G.n_if * GC, GT, 0, h.stream>>>(j, gam, G.S, G.d_if_off, h.d_gm_w, h.d_gm_V, h.d_gm_H, h.d_gm_beta, h.d_gm_kused);
         prof_end(h, pi, 0.0, 0.0);
         count_launch(4);
     }
     pi = prof_begin(h, K_GAMMA);
-    k_gm_finish<<<G.n_if, GT, 0, h.stream>>>(gam, G.S, G.d_if_off, G.d_if_dofs, h.d_gm_V, h.d_gm_H, h.d_gm_beta,
+    k_gm_finish<<<G.n_if * GC, GT, 0, h.stream>>>(gam, G.S, G.d_if_off, G.d_if_dofs, h.d_gm_V, h.d_gm_H, h.d_gm_beta,
                                              h.d_gm_kused, z);
     count_launch();
     prof_end(h, pi, 0.0, 0.0);
