@@ -231,30 +231,35 @@ __global__ void __launch_bounds__(256) k_smv_rows(int nk, const int* __restrict_
     }
 }
 
-// y_p = (K_{I_t I_t} x)_p - sum of yl_k over the couplings k of position p (leaves
-// ascending); one warp per packed position.
+// y_p = (K_{I_t I_t} x)_p - sum of yl_k over the couplings k of position p.  Eight lanes
+// per packed position (four positions per warp): the lanes take every eighth entry of the
+// row and every eighth coupling, and their partial sums meet in a fixed butterfly, so the
+// gathers of four rows are in flight at once.
 __global__ void __launch_bounds__(256) k_smv_iface(int S, const int* __restrict__ if_dofs, const int64_t* __restrict__ rowptr,
                                                    const int* __restrict__ col, const double* __restrict__ val,
                                                    const int* __restrict__ owner, const int* __restrict__ pk_pos,
                                                    const int* __restrict__ ci_ptr, const int* __restrict__ ci_k,
                                                    const double* __restrict__ yl, const double* __restrict__ x,
                                                    double* __restrict__ y) {
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, sub = lane & 7;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; p < S; p += warps) {
-        const int dof = if_dofs[p];
-        const int o = owner[dof];
+    // warp-uniform trip count: every lane reaches the shuffles
+    for (int64_t pw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; pw * 4 < S; pw += warps) {
+        const int64_t p = pw * 4 + (lane >> 3);
         double acc = 0;
-        for (int64_t k = rowptr[dof] + lane; k < rowptr[dof + 1]; k += 32) {
-            const int j = col[k];
-            if (owner[j] == o) acc += val[k] * x[pk_pos[j]];
+        if (p < S) {
+            const int dof = if_dofs[p];
+            const int o = owner[dof];
+            for (int64_t k = rowptr[dof] + sub; k < rowptr[dof + 1]; k += 8) {
+                const int j = col[k];
+                if (owner[j] == o) acc += val[k] * x[pk_pos[j]];
+            }
+            for (int q = ci_ptr[p] + sub; q < ci_ptr[p + 1]; q += 8) acc -= yl[ci_k[q]];
         }
-#pragma unroll
-        for (int o2 = 16; o2 > 0; o2 >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o2);
-        if (lane == 0) {
-            for (int q = ci_ptr[p]; q < ci_ptr[p + 1]; ++q) acc -= yl[ci_k[q]];
-            y[p] = acc;
-        }
+        acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        if (sub == 0 && p < S) y[p] = acc;
     }
 }
 
@@ -438,7 +443,7 @@ int gamma_interface_solve(Handle& h, int li, double* z) {
     prof_end(h, pi, 0.0, 0.0);
     const int wcol = f64 ? 2 : (c16 ? 8 : 4);     // columns per lane of k_smv_leaf
     const dim3 gl((unsigned)nleaf, (unsigned)std::max(1, (Ll.max_s + 32 * wcol - 1) / (32 * wcol)));
-    const unsigned gi = (unsigned)std::max(1, std::min(h.num_sms * 8, (G.S + 7) / 8));
+    const unsigned gi = (unsigned)std::max(1, std::min(h.num_sms * 8, (G.S + 31) / 32));   // 32 positions per CTA
     for (int j = 0; j < gam; ++j) {
         const double* vj = h.d_gm_V + (int64_t)j * G.S;
         const unsigned gr = (unsigned)std::max(1, std::min(h.num_sms * 4, (G.nk + 31) / 32));   // 8 warps of 4 rows
