@@ -11,7 +11,8 @@
 //                 thread, issues tcgen05.mma.kind::tf32 (M = 128, N = BN, K = 8) for each
 //                 K slice; tcgen05.commit frees ring slots and finally signals the epilogue.
 //   warps 2..5  : epilogue.  tcgen05.ld moves each accumulator row into registers (TMEM
-//                 lane = tile row), then C is read-modified-written with 16-byte accesses.
+//                 lane = tile row), then C is read-modified-written with 16-byte accesses
+//                 (the persistent variant below: warps 2..9, two per row, half a row each).
 // Operands stay in the front matrices: one 2-D tensor map per front covers its [L; X]
 // panel (N rows x s columns) and one covers its stacked inverted diagonal blocks; TMA's
 // zero fill handles ragged edges.  Every mbarrier wait is bounded; on timeout the CTA
@@ -44,6 +45,9 @@ template <int OP> struct OpT {
     static constexpr uint32_t FMT = OP == TC_OP_TF32 ? 2u : (OP == TC_OP_BF16 ? 1u : 0u);
 };
 constexpr int TC_THREADS = 192;
+// persistent kernel: producer, MMA issuer and eight epilogue warps (two per TMEM lane
+// quadrant, each taking half of the tile's columns)
+constexpr int TCP_THREADS = 320;
 constexpr long long TC_WAIT_CYCLES = 2000000000LL;   // ~1 s
 constexpr int SPLIT_MIN_KB = 16;             // at least 16 x 32 K per split-K slice
 constexpr int TILE_BAND = 16;                // row blocks per band of a wide output's tile order
@@ -329,9 +333,12 @@ k_gemm_tc(const TcTask* __restrict__ tasks, const TcTile* __restrict__ tiles,
 // with stride gridDim.x.  The smem ring runs continuously across tiles, and the TMEM
 // accumulator is double-buffered (2 x 256 columns), so the epilogue of one tile overlaps
 // the main loop of the next.  Barriers: full/empty per ring stage, and acc_full/acc_empty
-// per accumulator buffer (acc_empty counts the 128 epilogue threads).
+// per accumulator buffer (acc_empty counts the 256 epilogue threads).  The epilogue has
+// two warps per TMEM lane quadrant, one per half of the tile's columns, so twice as many
+// loads of C are in flight in the read-modify-write (at short K the tile's epilogue, not
+// its MMAs, sets the pace).
 template <int BN, int ST, int OP = TC_OP_TF32>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(TCP_THREADS, 1)
 k_gemm_tc_persist(const TcTask* __restrict__ tasks, const TcTile* __restrict__ tiles, int n_tiles,
                   const CUtensorMap* __restrict__ maps, float* __restrict__ ws, int* __restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
@@ -354,7 +361,7 @@ k_gemm_tc_persist(const TcTask* __restrict__ tasks, const TcTile* __restrict__ t
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(bar_accf + 8 * b, 1);
-            mbar_init(bar_acce + 8 * b, 128);
+            mbar_init(bar_acce + 8 * b, (TCP_THREADS / 32 - 2) * 32);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -422,6 +429,7 @@ k_gemm_tc_persist(const TcTask* __restrict__ tasks, const TcTile* __restrict__ t
     } else {
         const int quarter = warp & 3;
         const int row = quarter * 32 + lane;
+        const int cb = ((warp - 2) >> 2) * (BN / 2), ce = cb + BN / 2;   // this warp's columns
         uint32_t tcount = 0;
         for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++tcount) {
             const TcTile tl = tiles[t];
@@ -431,12 +439,12 @@ k_gemm_tc_persist(const TcTask* __restrict__ tasks, const TcTile* __restrict__ t
             const int gr = m0 + row;
             float* crow = tk.C + (int64_t)gr * tk.ldc;
             if (tk.beta && tl.ws_slot < 0 && gr < tk.M)
-                prefetch_c_row(crow, n0, min(n0 + BN, tk.lower ? min(tk.N, gr + 1) : tk.N));
+                prefetch_c_row(crow, n0 + cb, min(n0 + ce, tk.lower ? min(tk.N, gr + 1) : tk.N));
             const bool ok = mbar_wait(bar_accf + 8 * buf, use, err);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             float* wrow = tl.ws_slot >= 0 ? ws + ((int64_t)tl.ws_slot * BM + row) * BN : nullptr;
 #pragma unroll 1
-            for (int c0 = 0; c0 < BN; c0 += 32) {
+            for (int c0 = cb; c0 < ce; c0 += 32) {
                 uint32_t r[32];
                 tmem_ld32(tmem + buf * BN + ((uint32_t)(quarter * 32) << 16) + c0, r);
                 if (!ok) continue;
@@ -835,11 +843,11 @@ int gemm_tc_peak(int n, int reps, double seconds, cudaStream_t stream, int num_s
         const TcTile* tl = (const TcTile*)(buf + o_tiles);
         const CUtensorMap* mp = (const CUtensorMap*)(buf + o_maps);
         if (op == TC_OP_F16)
-            k_gemm_tc_persist<256, 4, TC_OP_F16><<<(unsigned)ctas, TC_THREADS, Smem<256, 4>::TOTAL, stream>>>(tk, tl, (int)tiles.size(), mp, nullptr, err);
+            k_gemm_tc_persist<256, 4, TC_OP_F16><<<(unsigned)ctas, TCP_THREADS, Smem<256, 4>::TOTAL, stream>>>(tk, tl, (int)tiles.size(), mp, nullptr, err);
         else if (op == TC_OP_BF16)
-            k_gemm_tc_persist<256, 4, TC_OP_BF16><<<(unsigned)ctas, TC_THREADS, Smem<256, 4>::TOTAL, stream>>>(tk, tl, (int)tiles.size(), mp, nullptr, err);
+            k_gemm_tc_persist<256, 4, TC_OP_BF16><<<(unsigned)ctas, TCP_THREADS, Smem<256, 4>::TOTAL, stream>>>(tk, tl, (int)tiles.size(), mp, nullptr, err);
         else
-            k_gemm_tc_persist<256, 4><<<(unsigned)ctas, TC_THREADS, Smem<256, 4>::TOTAL, stream>>>(tk, tl, (int)tiles.size(), mp, nullptr, err);
+            k_gemm_tc_persist<256, 4><<<(unsigned)ctas, TCP_THREADS, Smem<256, 4>::TOTAL, stream>>>(tk, tl, (int)tiles.size(), mp, nullptr, err);
         count_launch();
     };
     cudaEvent_t e0, e1;
@@ -1037,13 +1045,13 @@ int gemm_tc_launch(Handle& h, int /*li*/, const std::vector<GemmTask>& tasks, in
     else {
         const int ctas = std::min((int)tl.size(), sms);
         if (op == TC_OP_F16)
-            k_gemm_tc_persist<256, 4, TC_OP_F16><<<(unsigned)ctas, TC_THREADS, Smem<256, 4>::TOTAL, stream>>>(
+            k_gemm_tc_persist<256, 4, TC_OP_F16><<<(unsigned)ctas, TCP_THREADS, Smem<256, 4>::TOTAL, stream>>>(
                 d_tasks, d_tiles, (int)tl.size(), st->d_maps, bf.d_ws, h.d_err);
         else if (op == TC_OP_BF16)
-            k_gemm_tc_persist<256, 4, TC_OP_BF16><<<(unsigned)ctas, TC_THREADS, Smem<256, 4>::TOTAL, stream>>>(
+            k_gemm_tc_persist<256, 4, TC_OP_BF16><<<(unsigned)ctas, TCP_THREADS, Smem<256, 4>::TOTAL, stream>>>(
                 d_tasks, d_tiles, (int)tl.size(), st->d_maps, bf.d_ws, h.d_err);
         else
-            k_gemm_tc_persist<256, 4><<<(unsigned)ctas, TC_THREADS, Smem<256, 4>::TOTAL, stream>>>(
+            k_gemm_tc_persist<256, 4><<<(unsigned)ctas, TCP_THREADS, Smem<256, 4>::TOTAL, stream>>>(
                 d_tasks, d_tiles, (int)tl.size(), st->d_maps, bf.d_ws, h.d_err);
     }
     count_launch();
