@@ -45,9 +45,10 @@ template <int OP> struct OpT {
     static constexpr uint32_t FMT = OP == TC_OP_TF32 ? 2u : (OP == TC_OP_BF16 ? 1u : 0u);
 };
 constexpr int TC_THREADS = 192;
-// persistent kernel: producer, MMA issuer and eight epilogue warps (two per TMEM lane
-// quadrant, each taking half of the tile's columns)
-constexpr int TCP_THREADS = 320;
+// persistent kernel: producer, MMA issuer and 4 x TCP_SPLIT epilogue warps (TCP_SPLIT per
+// TMEM lane quadrant, each taking 1 / TCP_SPLIT of the tile's columns)
+constexpr int TCP_SPLIT = 2;
+constexpr int TCP_THREADS = 64 + 128 * TCP_SPLIT;
 constexpr long long TC_WAIT_CYCLES = 2000000000LL;   // ~1 s
 constexpr int SPLIT_MIN_KB = 16;             // at least 16 x 32 K per split-K slice
 constexpr int TILE_BAND = 16;                // row blocks per band of a wide output's tile order
@@ -429,7 +430,7 @@ k_gemm_tc_persist(const TcTask* __restrict__ tasks, const TcTile* __restrict__ t
     } else {
         const int quarter = warp & 3;
         const int row = quarter * 32 + lane;
-        const int cb = ((warp - 2) >> 2) * (BN / 2), ce = cb + BN / 2;   // this warp's columns
+        const int cb = ((warp - 2) >> 2) * (BN / TCP_SPLIT), ce = cb + BN / TCP_SPLIT;   // this warp's columns
         uint32_t tcount = 0;
         for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++tcount) {
             const TcTile tl = tiles[t];
