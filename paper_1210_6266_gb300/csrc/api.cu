@@ -1515,9 +1515,12 @@ extern "C" int rsd_setup(const rsd_csr* K, const int32_t* dof_node, const rsd_tr
     double part[6] = {0, 0, 0, 0, 0, 0};
     // A host CSR is uploaded first when a device is present, so that the structure pass
     // runs on the GPU too (the handle copies the uploaded structure, not the host one);
-    // without a device the host pass checks it.
+    // without a device the host pass checks it.  Its values follow once the structure pass
+    // is done, while the host plans the hierarchy (the device is idle then), so that the
+    // handle copies them device to device.
     const int64_t* rowptr_src = K->rowptr;
     const int* col_src = K->col;
+    const double* val_src = K->val;
     struct Tmp { char* p = nullptr; cudaStream_t s = nullptr; ~Tmp() { if (p) cudaFreeAsync(p, s); } } tmp;
     int ndev = 0;
     if (K->mem == RSD_MEM_HOST && (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)) { cudaGetLastError(); ndev = 0; }
@@ -1527,9 +1530,10 @@ extern "C" int rsd_setup(const rsd_csr* K, const int32_t* dof_node, const rsd_tr
         const auto t0 = clk::now();
         if (K->rowptr[0] != 0 || K->rowptr[K->n] != K->nnz) return RSD_ERR_ARG;
         const size_t b_rp = sizeof(int64_t) * ((size_t)K->n + 1), b_cl = sizeof(int) * (size_t)K->nnz;
-        const size_t b_ow = sizeof(int) * (size_t)K->n;
+        const size_t b_ow = sizeof(int) * (size_t)K->n, b_vl = sizeof(double) * (size_t)K->nnz;
         const size_t o_cl = (b_rp + 255) & ~(size_t)255, o_ow = (o_cl + b_cl + 255) & ~(size_t)255;
-        RSD_CUDA_TRY(cudaMallocAsync((void**)&tmp.p, o_ow + b_ow, st));
+        const size_t o_vl = (o_ow + b_ow + 255) & ~(size_t)255;
+        RSD_CUDA_TRY(cudaMallocAsync((void**)&tmp.p, o_vl + b_vl, st));
         tmp.s = st;
         RSD_CUDA_TRY(cudaMemcpyAsync(tmp.p, K->rowptr, b_rp, cudaMemcpyHostToDevice, st));
         RSD_CUDA_TRY(cudaMemcpyAsync(tmp.p + o_cl, K->col, b_cl, cudaMemcpyHostToDevice, st));
@@ -1543,6 +1547,8 @@ extern "C" int rsd_setup(const rsd_csr* K, const int32_t* dof_node, const rsd_tr
         const double up = ms_since(t0);
         RSD_TRY(analyse_structure_device(a, &Kd, (const int*)(tmp.p + o_ow), st, part));
         part[0] += up;
+        RSD_CUDA_TRY(cudaMemcpyAsync(tmp.p + o_vl, K->val, b_vl, cudaMemcpyHostToDevice, st));
+        val_src = (const double*)(tmp.p + o_vl);
     } else {
         const auto t0 = clk::now();
         if (K->rowptr[K->n] != K->nnz) return RSD_ERR_ARG;
@@ -1568,7 +1574,7 @@ extern "C" int rsd_setup(const rsd_csr* K, const int32_t* dof_node, const rsd_tr
         return RSD_ERR_NOMEM;
     }
     // numeric values come from the caller's memory directly (device or host)
-    const int rc = build_handle(h, a, rowptr_src, col_src, K->val);
+    const int rc = build_handle(h, a, rowptr_src, col_src, val_src);
     if (rc != RSD_OK) {
         h.notspd_node = h.notspd_node;
         if (rc == RSD_ERR_NOT_SPD) { *out = hh; return rc; }   // handle kept for introspection
