@@ -124,3 +124,37 @@ def test_tune_cache_reader_accepts_autotune_format_and_rejects_malformed(tmp_pat
         bad.write_text(text)
         assert lib.rsd_tune_load(str(bad).encode(), C.byref(n)) == _lib.RSD_ERR_ARG
     assert lib.rsd_tune_load(str(tmp_path / "missing.json").encode(), C.byref(n)) == _lib.RSD_ERR_ARG
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every structure the Python binding passes through the C ABI has the header's size
+    and field offsets (compiled against include/rsd.h with the host compiler), and the
+    profile's class list has the header's class count."""
+    import shutil
+    import subprocess
+    from paper_1210_6266_gb300 import _lib
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    structs = [_lib.rsd_csr, _lib.rsd_tree, _lib.rsd_options, _lib.rsd_stats, _lib.rsd_info_t,
+               _lib.rsd_profile_t, _lib.rsd_trace_rec]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rsd.h"', "int main(void) {",
+             '  printf("classes %d\\n", RSD_PROFILE_CLASSES);']
+    for s in structs:
+        n = s.__name__
+        lines.append(f'  printf("{n} sizeof %zu\\n", sizeof({n}));')
+        for f in s._fields_:
+            lines.append(f'  printf("{n} {f[0]} %zu\\n", offsetof({n}, {f[0]}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                        text=True).stdout.split("\n") if l)
+    assert int(out["classes"]) == len(_lib.PROFILE_CLASSES)
+    for s in structs:
+        n = s.__name__
+        assert int(out[f"{n} sizeof"]) == C.sizeof(s), n
+        for f in s._fields_:
+            assert int(out[f"{n} {f[0]}"]) == getattr(s, f[0]).offset, (n, f[0])
