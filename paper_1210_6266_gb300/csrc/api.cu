@@ -966,7 +966,7 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
         gh.resize(nl - 1);
         pk_pos.assign(a.n, -1);
         const Level& Ll = h.levels[nl - 1];
-        const size_t les = Ll.op16 == TC_OP_F16 && !h.lu ? 2 : elem_bytes(Ll.prec);   // S-MatVec reads (smv_reads_fp16)
+        const size_t les = (Ll.op16 == TC_OP_F16 || Ll.h16) && !h.lu ? 2 : elem_bytes(Ll.prec);   // smv_reads_fp16
         for (int d = 0; d < nl - 1; ++d) {
             GammaHost& G = gh[d];
             G.if_off.assign(1, 0);
@@ -1337,6 +1337,7 @@ static int build_handle(Handle& h, Analysis& a, const int64_t* rowptr, const int
         // every interface front is K_II plus leaf updates: factor the leaves, scatter
         // their updates into S~, then factor the interfaces
         RSD_TRY(h.lu ? run_factor_level_lu(h, nl - 1) : run_factor_level(h, nl - 1));
+        if (!h.lu) RSD_TRY(launch_factor_copy16(h, nl - 1));   // TF32 leaves: the copy their solves read
         if (!gmode) {
             RSD_TRY(paper_extend_add(h));
             for (int d = nl - 2; d >= 0; --d) RSD_TRY(run_factor_level(h, d));

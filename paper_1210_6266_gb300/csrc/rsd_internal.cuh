@@ -189,10 +189,12 @@ inline bool copy16_level(const Level& L) { return L.h16 || L.op16 != TC_OP_TF32;
 // factor at once (an FP64 pair would not fit in shared memory).
 inline int sweep_group(const Level& L) { return (!is_fp64(L.prec) && L.fronts.size() == 1) ? 2 : 1; }
 
-// Paper mode with gamma > 0: the S-MatVec reads the leaves' FP16 copy (FP16 operand
-// levels; not BF16 copies, FP64 or FP32 leaves, or the transposed upper factors of
-// nonsymmetric leaves).
-inline bool smv_reads_fp16(const Level& Ll) { return Ll.op16 == TC_OP_F16 && !Ll.d_fronts_bwd && !is_fp64(Ll.prec); }
+// Paper mode with gamma > 0: the S-MatVec reads the leaves' FP16 copy when they have one
+// (FP16-operand leaves, and TF32 leaves, whose solves read the copy too; not BF16 copies,
+// FP64 or FP32 leaves, or the transposed upper factors of nonsymmetric leaves).
+inline bool smv_reads_fp16(const Level& Ll) {
+    return (Ll.op16 == TC_OP_F16 || Ll.h16) && !Ll.d_fronts_bwd && !is_fp64(Ll.prec);
+}
 
 // CTAs per cluster of the cluster sweeps (diagonal blocks per work item of a cl_sweep level)
 constexpr int SWEEP_CL = 8;

@@ -154,14 +154,16 @@ def test_fgmres_with_exact_preconditioner_converges_in_one_iteration(rsd):
     h.close()
 
 
-def test_paper_leaf_copy_holds_the_leaf_factor(rsd):
-    """Paper mode's leaf solves and S-MatVecs read the leaves' row-scaled FP16 copy: it
+@pytest.mark.parametrize("prec", ["TF32", "FP16"])
+def test_paper_leaf_copy_holds_the_leaf_factor(rsd, prec):
+    """Paper mode's leaf solves and S-MatVecs read the leaves' row-scaled FP16 copy (TF32
+    leaves: written after their factorisation; FP16-operand leaves: panel by panel): it
     equals the leaf factor [L; X] exactly wherever the scaled entry is an FP16 normal
     (entries >= 2^-27 sqrt(K_ii)) and within 2^-38 sqrt(K_ii) elsewhere."""
     n, depth = 23, 2
     kappa, f, A, sym = _case(n, depth)
     prob = rsd.grid_problem(n, depth, kappa, f)
-    h = _setup(rsd, prob, rsd.RSD_PREC_FP16, 4)
+    h = _setup(rsd, prob, getattr(rsd, "RSD_PREC_" + prec), 4)
     sq = np.sqrt(A.diagonal())
     leaves = [t for t in range(sym.n_nodes) if not sym.children[t]]
     assert leaves
