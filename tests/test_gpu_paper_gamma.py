@@ -177,3 +177,25 @@ def test_paper_leaf_copy_holds_the_leaf_factor(rsd, prec):
         assert np.array_equal(Q[big], P[big]), t
         assert np.all(np.abs(Q - P)[read] <= 2.0**-38 * bound[read]), t
     h.close()
+
+
+def test_gamma_mixed_forms_on_multiblock_leaves_track_fp64(rsd):
+    """Leaves of 343 DOF (33^3, depth 2: three diagonal blocks each), so paper mode's leaf
+    solves read the off-diagonal part of the leaves' FP16 copy, not only their inverted
+    diagonal blocks: the TF32 and FP16 forms reach the residual in about as many FGMRES
+    iterations as the FP64 form (a leaf solve that dropped the off-diagonal blocks, or
+    read a stale copy, would not)."""
+    n, depth, gamma = 33, 2, 4
+    kappa, f, A, sym = _case(n, depth)
+    assert min(sym.s(t) for t in range(sym.n_nodes) if not sym.children[t]) > 128
+    prob = rsd.grid_problem(n, depth, kappa, f)
+    b = fem.load_vector(n, f)
+    its = {}
+    for prec in ("FP64", "TF32", "FP16"):
+        h = _setup(rsd, prob, getattr(rsd, "RSD_PREC_" + prec), gamma, maxit=400)
+        u, st = h.solve(prob["b"], tol=1e-8)
+        assert st["relres"] <= 1e-8, (prec, st)
+        assert np.linalg.norm(b - A @ u.cpu().numpy()) <= 1e-8 * np.linalg.norm(b), prec
+        its[prec] = st["iterations"]
+        h.close()
+    assert its["TF32"] <= its["FP64"] + 3 and its["FP16"] <= its["FP64"] + 3, its
