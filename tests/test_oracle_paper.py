@@ -82,6 +82,34 @@ def test_pcg_textbook_properties():
     assert np.allclose(x, np.linalg.solve(Ms, b), atol=1e-9)
 
 
+def test_fgmres_with_a_preconditioner_that_changes_every_step():
+    """The flexible variant keeps z_j = M_j(v_j) per step: with a preconditioner that
+    differs from call to call, n steps still reach the exact solution, and at every step
+    the iterate minimises ||b - A x|| over span{z_0 .. z_k} (checked by an independent
+    least-squares solve on the same z's)."""
+    rng = np.random.default_rng(5)
+    n = 12
+    A = rng.standard_normal((n, n)) + 8 * np.eye(n)
+    b = rng.standard_normal(n)
+    P = [np.linalg.inv(A + rng.standard_normal((n, n))), np.diag(1.0 / np.diag(A)), np.eye(n)]
+    calls = []
+
+    def M(v):
+        z = P[len(calls) % 3] @ v
+        calls.append(z)
+        return z
+
+    x, it, _ = fgmres(A, b, M, 1e-13, restart=n)
+    assert np.allclose(x, np.linalg.solve(A, b), atol=1e-10)
+    for k in (1, 3, 5):
+        calls.clear()
+        xk, itk, _ = fgmres(A, b, M, 1e-30, restart=k, maxit=k)
+        assert itk == k
+        Zk = np.stack(calls[:k], axis=1)
+        y, *_ = np.linalg.lstsq(A @ Zk, b, rcond=None)
+        assert np.allclose(xk, Zk @ y, atol=1e-10), k
+
+
 def _table1():
     rows = []
     with open(os.path.join(GOLDEN, "table1_poisson_iterations.txt")) as fh:
