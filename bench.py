@@ -47,6 +47,17 @@ BATCH_FP64_SAMPLE = 64            # problems of the batched workload timed in th
 ELASTIC_NU = 0.3                  # Poisson's ratio of the elasticity workload
 
 
+def job_rate(torch, dist, ms_local: float, units_per_rank: float, world: int, device: str):
+    """Whole-job throughput of `world` replicas: all ranks' units over the slowest rank's
+    time (the max over ranks of its ms per step).  Returns (units/s, ms)."""
+    ms = ms_local
+    if world > 1:
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return world * units_per_rank / (ms / 1e3), ms
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -406,11 +417,7 @@ def main() -> None:
     ms_prof, _, _, res_prof = timed_steps(torch, step(args.form, profile=True), args.steps)
     barrier()
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n_dof / (ms / 1e3)
+    value, ms = job_rate(torch, dist, ms, n_dof, world, "cuda")
     stats = [r[0] for r in res]
 
     # ---- end to end through the C ABI from pinned host buffers ------------------------

@@ -22,7 +22,8 @@ def lib():
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "rsd.h")).read()
+    with open(os.path.join(ROOT, "include", "rsd.h")) as fh:
+        src = fh.read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(rsd_[a-z_0-9]+)\s*\(", src)))
 
